@@ -1,0 +1,314 @@
+"""Counter-based random numbers, phase-space generators, cuts and the MC sum.
+
+Oracle module (test infrastructure only), numpy FP64.
+
+Random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) written
+from its published definition: ten rounds of
+    (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+with the key bumped by the Weyl constants between rounds.  Event i, attempt
+a, block j uses counter (i, a, j, 0) and key (seed, 0); each block gives four
+64-bit words, mapped to doubles in (0, 1) as ((x >> 11) + 1/2) 2^-53.
+
+Generators (the paper's own parametrisation, App. A, is replaced by the
+workload's stated generators; the Breit-Wigner mapping is the paper's Eq. 16):
+  two_to_two_massless : cos(theta) ~ U[-1,1], phi ~ U[0, 2 pi)
+  rambo_massless      : RAMBO (Kleiss, Stirling, Ellis 1986), flat n-body
+  ttbar_dilepton      : sqrt(s) ~ U[a,b], Breit-Wigner t, t~, W+, W- virtualities
+                        (Eq. 16, range |s-m^2|/(m Gamma) < min(20, m/Gamma),
+                        App. A.2), isotropic two-body decays in each rest frame
+  rambo_massive       : RAMBO with the massive rescaling (Kleiss et al. 1986)
+Cuts (Eqs. 8-11 in form): pT > pt_min, |eta| < eta_max, Delta R > dr_min.
+A point failing the cuts (or the kinematic limits) is redrawn with the next
+attempt number; the MC estimate divides by the number of tries (Eq. 4
+integrated with the efficiency included).
+
+Parity: pinned by tests/test_oracle_phasespace.py (Philox against numpy's
+library Philox4x64, RAMBO volume/momentum conservation/masslessness,
+two-body volume, Breit-Wigner Jacobian against direct integration, cut
+definitions by brute force).
+"""
+import math
+import numpy as np
+
+M0 = np.uint64(0xD2E7470EE14C6C93)
+M1 = np.uint64(0xCA5A826395121157)
+W0 = np.uint64(0x9E3779B97F4A7C15)
+W1 = np.uint64(0xBB67AE8584CAA73B)
+_M32 = np.uint64(0xFFFFFFFF)
+_S32 = np.uint64(32)
+
+
+def _mulhilo(a, b):
+    """(high, low) 64-bit halves of the 128-bit product of uint64 arrays."""
+    a_lo, a_hi = a & _M32, a >> _S32
+    b_lo, b_hi = b & _M32, b >> _S32
+    ll = a_lo * b_lo
+    lh = a_lo * b_hi
+    hl = a_hi * b_lo
+    hh = a_hi * b_hi
+    mid = (ll >> _S32) + (lh & _M32) + (hl & _M32)
+    hi = hh + (lh >> _S32) + (hl >> _S32) + (mid >> _S32)
+    lo = a * b
+    return hi, lo
+
+
+def philox4x64_10(ctr, key):
+    """ctr: uint64 [N, 4]; key: uint64 [N, 2] (or [2]); returns uint64 [N, 4]."""
+    with np.errstate(over="ignore"):
+        c = [ctr[:, k].astype(np.uint64) for k in range(4)]
+        key = np.broadcast_to(np.asarray(key, dtype=np.uint64), (ctr.shape[0], 2))
+        k0, k1 = key[:, 0].copy(), key[:, 1].copy()
+        for r in range(10):
+            hi0, lo0 = _mulhilo(M0, c[0])
+            hi1, lo1 = _mulhilo(M1, c[2])
+            c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]
+            if r < 9:
+                k0 = k0 + W0
+                k1 = k1 + W1
+        return np.stack(c, axis=1)
+
+
+def to_unit(x):
+    """uint64 -> double in (0, 1): ((x >> 11) + 0.5) * 2^-53."""
+    return ((x >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
+
+
+def uniforms(seed, event, attempt, nblocks):
+    """[N, 4 * nblocks] doubles for events `event` at attempts `attempt`."""
+    event = np.asarray(event, dtype=np.uint64)
+    attempt = np.asarray(attempt, dtype=np.uint64)
+    N = event.shape[0]
+    out = np.empty((N, 4 * nblocks))
+    for j in range(nblocks):
+        ctr = np.stack([event, attempt, np.full(N, j, dtype=np.uint64), np.zeros(N, dtype=np.uint64)], axis=1)
+        out[:, 4 * j:4 * j + 4] = to_unit(philox4x64_10(ctr, np.array([seed, 0], dtype=np.uint64)))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# generators
+# ---------------------------------------------------------------------------
+def incoming(w, N):
+    """Beam partons along +z and -z, each with energy w/2."""
+    pa = np.zeros((N, 4))
+    pb = np.zeros((N, 4))
+    pa[:, 0] = pa[:, 3] = 0.5 * w
+    pb[:, 0] = 0.5 * w
+    pb[:, 3] = -0.5 * w
+    return pa, pb
+
+
+def two_to_two_massless(w, u):
+    """Legs (a, b, 3, 4): leg 4 at (cos theta = 2u0-1, phi = 2 pi u1), leg 3 opposite.
+
+    Returns momenta [N, 4, 4] and the two-body volume 1/(8 pi)."""
+    N = u.shape[0]
+    c = 2.0 * u[:, 0] - 1.0
+    phi = 2.0 * math.pi * u[:, 1]
+    s = np.sqrt(np.maximum(1.0 - c * c, 0.0))
+    E = 0.5 * w
+    P = np.zeros((N, 4, 4))
+    P[:, 0], P[:, 1] = incoming(w, N)
+    n = np.stack([s * np.cos(phi), s * np.sin(phi), c], axis=1)
+    P[:, 3, 0] = E
+    P[:, 3, 1:] = E * n
+    P[:, 2, 0] = E
+    P[:, 2, 1:] = -E * n
+    return P, np.full(N, 1.0 / (8.0 * math.pi))
+
+
+def rambo_volume(w, n):
+    """Massless n-body volume with the (2 pi) factors of Eq. 5."""
+    return ((2 * math.pi) ** (4 - 3 * n) * (math.pi / 2) ** (n - 1) * w ** (2 * n - 4)
+            / (math.factorial(n - 1) * math.factorial(n - 2)))
+
+
+def rambo_massless(w, n, u):
+    """RAMBO: n massless momenta with total (w, 0, 0, 0); u [N, 4n] (4 per particle).
+
+    Particle k: c = 2u-1, phi = 2 pi u', q0 = -ln(u'' u'''), q = q0 (1, s cos phi,
+    s sin phi, c); then the conformal boost + scaling that brings sum q to (w,0,0,0).
+    """
+    N = u.shape[0]
+    q = np.zeros((N, n, 4))
+    for k in range(n):
+        c = 2.0 * u[:, 4 * k] - 1.0
+        phi = 2.0 * math.pi * u[:, 4 * k + 1]
+        q0 = -np.log(u[:, 4 * k + 2] * u[:, 4 * k + 3])
+        s = np.sqrt(np.maximum(1.0 - c * c, 0.0))
+        q[:, k, 0] = q0
+        q[:, k, 1] = q0 * s * np.cos(phi)
+        q[:, k, 2] = q0 * s * np.sin(phi)
+        q[:, k, 3] = q0 * c
+    Q = q.sum(axis=1)
+    M = np.sqrt(Q[:, 0] ** 2 - (Q[:, 1:] ** 2).sum(axis=1))
+    b = -Q[:, 1:] / M[:, None]
+    gam = Q[:, 0] / M
+    a = 1.0 / (1.0 + gam)
+    x = w / M
+    bq = np.einsum("nj,nkj->nk", b, q[:, :, 1:])
+    p = np.zeros_like(q)
+    p[:, :, 0] = x[:, None] * (gam[:, None] * q[:, :, 0] + bq)
+    p[:, :, 1:] = x[:, None, None] * (q[:, :, 1:] + b[:, None, :] * q[:, :, :1] + (a[:, None] * bq)[:, :, None] * b[:, None, :])
+    return p, np.full(N, rambo_volume(w, n))
+
+
+def rambo_massive(w, masses, u, iterations=40):
+    """Massive RAMBO: massless RAMBO followed by the rescaling p -> (sqrt(m^2 + xi^2 |p|^2), xi p)
+    with xi solved by Newton iteration from sum E = w; weight per Kleiss et al. (1986)."""
+    n = len(masses)
+    p, wt0 = rambo_massless(w, n, u)
+    m = np.asarray(masses, dtype=float)
+    if not np.any(m > 0):
+        return p, wt0
+    E0 = p[:, :, 0]
+    xi = np.full(p.shape[0], math.sqrt(max(1.0 - (m.sum() / w) ** 2, 0.0)))
+    for _ in range(iterations):
+        Ek = np.sqrt(m[None, :] ** 2 + (xi[:, None] * E0) ** 2)
+        f = Ek.sum(axis=1) - w
+        df = (xi[:, None] * E0 ** 2 / Ek).sum(axis=1)
+        xi = xi - f / df
+    Ek = np.sqrt(m[None, :] ** 2 + (xi[:, None] * E0) ** 2)
+    out = np.empty_like(p)
+    out[:, :, 0] = Ek
+    out[:, :, 1:] = xi[:, None, None] * p[:, :, 1:]
+    absk = xi[:, None] * E0
+    # Kleiss et al.: W_massive = W_massless * xi^(2n-3) * prod(|k|/E) * w / sum(|k|^2/E)
+    wt = wt0 * xi ** (2 * n - 3) * np.prod(absk / Ek, axis=1) * w / (absk ** 2 / Ek).sum(axis=1)
+    return out, wt
+
+
+def _lam(a, b, c):
+    return a * a + b * b + c * c - 2 * a * b - 2 * b * c - 2 * c * a
+
+
+def _boost_from_rest(pstar, P, M):
+    """Take pstar [N,4] from the rest frame of a system with lab momentum P [N,4], mass M [N]."""
+    E = (P[:, 0] * pstar[:, 0] + (P[:, 1:] * pstar[:, 1:]).sum(axis=1)) / M
+    coef = ((P[:, 1:] * pstar[:, 1:]).sum(axis=1) / (P[:, 0] + M) + pstar[:, 0]) / M
+    out = np.empty_like(pstar)
+    out[:, 0] = E
+    out[:, 1:] = pstar[:, 1:] + coef[:, None] * P[:, 1:]
+    return out
+
+
+def _iso_pair(M, m1, m2, c, phi):
+    """Two-body decay at rest: (p1*, p2*, |p*|) for daughter masses m1, m2, direction of 1."""
+    pabs = np.sqrt(np.maximum(_lam(M * M, m1 * m1, m2 * m2), 0.0)) / (2.0 * M)
+    s = np.sqrt(np.maximum(1.0 - c * c, 0.0))
+    n = np.stack([s * np.cos(phi), s * np.sin(phi), c], axis=1)
+    p1 = np.concatenate([np.sqrt(m1 * m1 + pabs * pabs)[:, None], pabs[:, None] * n], axis=1)
+    p2 = np.concatenate([np.sqrt(m2 * m2 + pabs * pabs)[:, None], -pabs[:, None] * n], axis=1)
+    return p1, p2, pabs
+
+
+def bw_range(m, w, cap=20.0):
+    """theta range of Eq. 16 for |s - m^2|/(m w) < min(cap, m/w) (App. A.2)."""
+    x = min(cap, m / w)
+    return -math.atan(x), math.atan(x)
+
+
+def bw_sample(m, w, u):
+    """s = m^2 + m w tan(theta), theta uniform in the App. A.2 range; returns (s, ds Jacobian / (2 pi))."""
+    t0, t1 = bw_range(m, w)
+    th = t0 + (t1 - t0) * u
+    s = m * m + m * w * np.tan(th)
+    jac = (t1 - t0) * ((s - m * m) ** 2 + (m * w) ** 2) / (m * w)
+    return s, jac / (2.0 * math.pi)
+
+
+def ttbar_dilepton(u, par, sqrt_s_range):
+    """g g > t t~ > (b e+ ve)(b~ e- ve~); u [N, 16]. Returns (P [N,8,4], weight [N], ok [N], shat [N]).
+
+    Draw order: sqrt(s), s_t, s_t~, s_W+, s_W-, top direction (cos, phi), b in
+    the t frame, e+ in the W+ frame, b~ in the t~ frame, e- in the W- frame.
+    weight = dPhi_2(s; t, t~) * prod ds/(2 pi) * dPhi_2(t; b, W+) dPhi_2(W+; e+, ve)
+             * dPhi_2(t~; b~, W-) dPhi_2(W-; e-, ve~)   (Eq. 15, App. A.2)
+    A point is kept only if sqrt(s_W) <= sqrt(s_t) for both tops and
+    sqrt(s_t) + sqrt(s_t~) <= sqrt(s).
+    """
+    N = u.shape[0]
+    lo, hi = sqrt_s_range
+    rs = lo + (hi - lo) * u[:, 0]
+    shat = rs * rs
+    st, jt = bw_sample(par.mt, par.wt, u[:, 1])
+    stb, jtb = bw_sample(par.mt, par.wt, u[:, 2])
+    swp, jwp = bw_sample(par.mW, par.wW, u[:, 3])
+    swm, jwm = bw_sample(par.mW, par.wW, u[:, 4])
+    ok = (st > 0) & (stb > 0) & (swp > 0) & (swm > 0)
+    st_ = np.where(ok, st, 1.0)
+    stb_ = np.where(ok, stb, 1.0)
+    swp_ = np.where(ok, swp, 1.0)
+    swm_ = np.where(ok, swm, 1.0)
+    mt_, mtb_, mwp_, mwm_ = np.sqrt(st_), np.sqrt(stb_), np.sqrt(swp_), np.sqrt(swm_)
+    ok &= (mwp_ <= mt_) & (mwm_ <= mtb_) & (mt_ + mtb_ <= rs)
+    two_pi = 2.0 * math.pi
+    zeros = np.zeros(N)
+    P = np.zeros((N, 8, 4))
+    P[:, 0], P[:, 1] = incoming(rs, N)
+    # production in the CM frame
+    pt_, ptb_, k_prod = _iso_pair(rs, mt_, mtb_, 2 * u[:, 5] - 1, two_pi * u[:, 6])
+    # t -> b W+
+    b_, wp_, k_t = _iso_pair(mt_, zeros, mwp_, 2 * u[:, 7] - 1, two_pi * u[:, 8])
+    b_ = _boost_from_rest(b_, pt_, mt_)
+    wp_ = _boost_from_rest(wp_, pt_, mt_)
+    # W+ -> e+ ve
+    ep_, ve_, k_wp = _iso_pair(mwp_, zeros, zeros, 2 * u[:, 9] - 1, two_pi * u[:, 10])
+    ep_ = _boost_from_rest(ep_, wp_, mwp_)
+    ve_ = _boost_from_rest(ve_, wp_, mwp_)
+    # t~ -> b~ W-
+    bb_, wm_, k_tb = _iso_pair(mtb_, zeros, mwm_, 2 * u[:, 11] - 1, two_pi * u[:, 12])
+    bb_ = _boost_from_rest(bb_, ptb_, mtb_)
+    wm_ = _boost_from_rest(wm_, ptb_, mtb_)
+    # W- -> e- ve~
+    em_, vb_, k_wm = _iso_pair(mwm_, zeros, zeros, 2 * u[:, 13] - 1, two_pi * u[:, 14])
+    em_ = _boost_from_rest(em_, wm_, mwm_)
+    vb_ = _boost_from_rest(vb_, wm_, mwm_)
+    for k, v in enumerate([b_, ep_, ve_, bb_, em_, vb_]):
+        P[:, 2 + k] = v
+
+    def phi2(k, M):
+        return k / (4.0 * math.pi * M)
+
+    wt = (phi2(k_prod, rs) * jt * jtb * jwp * jwm
+          * phi2(k_t, mt_) * phi2(k_wp, mwp_) * phi2(k_tb, mtb_) * phi2(k_wm, mwm_))
+    wt = np.where(ok, wt, 0.0)
+    return P, wt, ok, shat
+
+
+# ---------------------------------------------------------------------------
+# cuts
+# ---------------------------------------------------------------------------
+def pt(p):
+    return np.sqrt(p[..., 1] ** 2 + p[..., 2] ** 2)
+
+
+def eta(p):
+    """Pseudorapidity 1/2 ln((|p|+pz)/(|p|-pz))."""
+    a = np.sqrt(p[..., 1] ** 2 + p[..., 2] ** 2 + p[..., 3] ** 2)
+    return 0.5 * np.log((a + p[..., 3]) / (a - p[..., 3]))
+
+
+def phi(p):
+    return np.arctan2(p[..., 2], p[..., 1])
+
+
+def delta_r(p1, p2):
+    dphi = np.abs(phi(p1) - phi(p2))
+    dphi = np.where(dphi > math.pi, 2 * math.pi - dphi, dphi)
+    return np.sqrt((eta(p1) - eta(p2)) ** 2 + dphi ** 2)
+
+
+def pass_cuts(P, legs, pt_min, eta_max, dr_min):
+    """All of legs have pT > pt_min and |eta| < eta_max, every pair Delta R > dr_min."""
+    ok = np.ones(P.shape[0], dtype=bool)
+    for k in legs:
+        ptk = pt(P[:, k])
+        ok &= ptk > pt_min
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ok &= np.abs(eta(P[:, k])) < eta_max
+    for i in range(len(legs)):
+        for j in range(i + 1, len(legs)):
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ok &= delta_r(P[:, legs[i]], P[:, legs[j]]) > dr_min
+    return ok

@@ -1,0 +1,486 @@
+"""Spin- and colour-summed |M|^2 of the workload processes, from the plain definition.
+
+Oracle module (test infrastructure only).  For each process the Feynman
+diagrams are written out by hand from the vertices of Sect. 4.2, every
+helicity combination is evaluated (no pruning), and colour is summed over
+every explicit colour index (oracle/colour.py).  The result is averaged over
+the initial helicities and colours, Eq. 4:
+
+    |M|^2_avg = 1/(4 n_a n_b) sum_lambda sum_c |sum_diagrams M|^2 .
+
+No identical-particle factor is applied here (that belongs to the phase-space
+integral).  Momenta: array [N, n_ext, 4] of physical four-momenta (E, px, py,
+pz), incoming legs first, in the order of the process string.
+
+Functions and their pins (tests/test_oracle_processes.py):
+  uux_epem        u u~ > e+ e-   : closed-form dsigma/dcos(theta), exact per point
+  udx_epve        u d~ > e+ ve   : closed form (V-A), exact per point
+  udx_epvegg      u d~ > e+ ve g g : Ward identity, Bose symmetry, boosts,
+                   built from blocks pinned by the two cases above and q q~ > g g
+  uux_gg          u u~ > g g     : textbook closed form, exact per point
+  gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
+  gg_ttx_dilep    g g > t t~ > b e+ ve b~ e- ve~ (doubly resonant diagrams):
+                   Ward identity (zero widths), Bose symmetry, boosts
+  us_dchh         u s > d c h h  (WW fusion): boosts; parity unpinned beyond
+                   invariants (no external gauge boson, no closed form)
+  gluons          g g > g...g    : Berends-Giele, pinned by the gg > gg closed
+                   form, Parke-Taylor MHV amplitudes, Ward, Bose, boosts
+"""
+import itertools
+import numpy as np
+
+from . import colour
+from .feynman import (ffv_current, fermion_line, fermion_prop, scalar_prop, vector_insertion,
+                      vector_prop, vvv_out, den)
+from .lorentz import bar, mdot, polarisation, u_spinor, v_spinor
+from .sm import CHARGE, T3, SMParams
+
+HEL_F = (-1, 1)
+HEL_V = (-1, 1)
+
+_T = colour.T
+_F = colour.F
+_DELTA3 = np.eye(3, dtype=complex)
+
+
+def _z_couplings(f, par):
+    gl = par.gz * (T3[f] - CHARGE[f] * par.sw2)
+    gr = par.gz * (-CHARGE[f] * par.sw2)
+    return gl, gr
+
+
+def _a_coupling(f, par):
+    return par.e * CHARGE[f]
+
+
+# --------------------------------------------------------------------------
+# q q~ > l+ l- via photon and Z  (cfg: u u~ > e+ e-)
+# --------------------------------------------------------------------------
+def uux_epem(P, par=SMParams(), per_helicity=False, quark="u", lepton="e"):
+    p = [P[:, k] for k in range(4)]
+    q = p[0] + p[1]
+    tot = 0.0
+    ph = {}
+    for h in itertools.product(HEL_F, repeat=4):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        v = v_spinor(p[2], h[2])
+        ub = bar(u_spinor(p[3], h[3]))
+        iM = 0.0
+        # photon
+        ga_q, ga_l = _a_coupling(quark, par), _a_coupling(lepton, par)
+        Jq = ffv_current(vb, u, ga_q, ga_q)
+        Jl = ffv_current(ub, v, ga_l, ga_l)
+        iM = iM + mdot(vector_prop(q, Jq), Jl)
+        # Z
+        zq, zl = _z_couplings(quark, par), _z_couplings(lepton, par)
+        Jq = ffv_current(vb, u, *zq)
+        Jl = ffv_current(ub, v, *zl)
+        iM = iM + mdot(vector_prop(q, Jq, par.mZ, par.wZ), Jl)
+        M = iM / 1j
+        m2 = colour.colour_sum([M], [_DELTA3])
+        ph[h] = m2
+        tot = tot + m2
+    avg = tot / (4.0 * 9.0)
+    return (avg, ph) if per_helicity else avg
+
+
+# --------------------------------------------------------------------------
+# u d~ > e+ ve via W+  (closed-form pin of the W building block)
+# --------------------------------------------------------------------------
+def udx_epve(P, par=SMParams()):
+    p = [P[:, k] for k in range(4)]
+    gw = par.g / np.sqrt(2.0)
+    tot = 0.0
+    for h in itertools.product(HEL_F, repeat=4):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        v = v_spinor(p[2], h[2])
+        ub = bar(u_spinor(p[3], h[3]))
+        L = ffv_current(ub, v, gw, 0.0)
+        W = vector_prop(p[2] + p[3], L, par.mW, par.wW)
+        Jq = ffv_current(vb, u, gw, 0.0)
+        M = mdot(Jq, W) / 1j
+        tot = tot + colour.colour_sum([M], [_DELTA3])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
+# helpers shared by the quark-line processes
+# --------------------------------------------------------------------------
+def _colour_string(gluon_slots, n_gluons, with_f=None):
+    """Explicit colour tensor c[i_start, i_end, a_1..a_n] of one diagram.
+
+    gluon_slots: the sequence of colour insertions along the fermion arrow,
+    from the start (column spinor) to the end (row spinor); each entry is a
+    gluon label k (t^{a_k}) or "G" for an internal gluon attached to the
+    ggg vertex of gluons with_f = (k1, k2), giving f^{a_k1 a_k2 c} t^c.
+    The result is (t_last ... t_first)_{i_end, i_start} arranged with axes
+    (i_start, i_end, a_0, ..., a_{n-1}).
+    """
+    shape = (3, 3) + (8,) * n_gluons
+    out = np.zeros(shape, dtype=complex)
+    for a in itertools.product(range(8), repeat=n_gluons):
+        M = np.eye(3, dtype=complex)
+        for slot in gluon_slots:
+            if slot == "G":
+                k1, k2 = with_f
+                Tg = np.einsum("c,cij->ij", _F[a[k1], a[k2], :], _T)
+            else:
+                Tg = _T[a[slot]]
+            M = Tg @ M
+        out[(slice(None), slice(None)) + a] = M.T  # [i_start, i_end]
+    return out
+
+
+# --------------------------------------------------------------------------
+# q q~ > g g  (textbook closed-form pin of the qqg and ggg rules)
+# --------------------------------------------------------------------------
+def uux_gg(P, par=SMParams()):
+    p = [P[:, k] for k in range(4)]
+    gs = par.gs
+    cAB = _colour_string([0, 1], 2)
+    cBA = _colour_string([1, 0], 2)
+    cG = _colour_string(["G"], 2, with_f=(0, 1))
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_V, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        e2 = polarisation(p[2], h[2]).conj()
+        e3 = polarisation(p[3], h[3]).conj()
+        G2 = (vector_insertion(e2, gs, gs), p[2])
+        G3 = (vector_insertion(e3, gs, gs), p[3])
+        A23 = fermion_line(vb, u, p[0], [G2, G3])
+        A32 = fermion_line(vb, u, p[0], [G3, G2])
+        X = vvv_out(e2, -p[2], e3, -p[3], p[2] + p[3], gs)
+        Gint = vector_prop(p[2] + p[3], X)
+        AG = fermion_line(vb, u, p[0], [(vector_insertion(Gint, gs, gs), p[2] + p[3])])
+        tot = tot + colour.colour_sum([A23 / 1j, A32 / 1j, AG / 1j], [cAB, cBA, cG])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
+# u d~ > e+ ve g g   (W+ -> e+ ve, two gluons on the quark line or via ggg)
+# --------------------------------------------------------------------------
+def udx_epvegg(P, par=SMParams(), per_helicity=False, eps_override=None):
+    """Eight diagrams: the W and both gluons in all 3! orders along the quark
+    line, plus the W and the ggg-produced gluon pair in both orders.
+
+    eps_override: optional {leg: vector[N,4]} replacing a gluon polarisation
+    (used by the Ward-identity pin with eps -> k).
+    """
+    p = [P[:, k] for k in range(6)]
+    gs, gw = par.gs, par.g / np.sqrt(2.0)
+    colours = {}
+    for order in itertools.permutations(["W", 0, 1]):
+        colours[order] = _colour_string([s for s in order if s != "W"], 2)
+    cG = _colour_string(["G"], 2, with_f=(0, 1))
+    tot = 0.0
+    ph = {}
+    for h in itertools.product(HEL_F, HEL_F, HEL_F, HEL_F, HEL_V, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ve_ = v_spinor(p[2], h[2])
+        ubn = bar(u_spinor(p[3], h[3]))
+        eg = [polarisation(p[4], h[4]).conj(), polarisation(p[5], h[5]).conj()]
+        if eps_override:
+            for leg, vec in eps_override.items():
+                eg[leg - 4] = vec.astype(complex)
+        L = ffv_current(ubn, ve_, gw, 0.0)
+        qW = p[2] + p[3]
+        W = vector_prop(qW, L, par.mW, par.wW)
+        ins = {"W": (vector_insertion(W, gw, 0.0), qW),
+               0: (vector_insertion(eg[0], gs, gs), p[4]),
+               1: (vector_insertion(eg[1], gs, gs), p[5])}
+        amps, cols = [], []
+        for order, c in colours.items():
+            amps.append(fermion_line(vb, u, p[0], [ins[s] for s in order]) / 1j)
+            cols.append(c)
+        X = vvv_out(eg[0], -p[4], eg[1], -p[5], p[4] + p[5], gs)
+        Gint = vector_prop(p[4] + p[5], X)
+        insG = (vector_insertion(Gint, gs, gs), p[4] + p[5])
+        for order in (["W", "G"], ["G", "W"]):
+            amps.append(fermion_line(vb, u, p[0], [ins["W"] if s == "W" else insG for s in order]) / 1j)
+            cols.append(cG)
+        m2 = colour.colour_sum(amps, cols)
+        ph[h] = m2
+        tot = tot + m2
+    avg = tot / 36.0
+    return (avg, ph) if per_helicity else avg
+
+
+# --------------------------------------------------------------------------
+# g g > t t~ (on-shell tops; textbook closed-form pin of the massive line)
+# --------------------------------------------------------------------------
+def gg_ttx(P, par=SMParams()):
+    p = [P[:, k] for k in range(4)]
+    gs, mt = par.gs, par.mt
+    cAB = _colour_string([0, 1], 2)  # arrow starts at the t~ spinor: gluon 0 nearest t~
+    cBA = _colour_string([1, 0], 2)
+    cG = _colour_string(["G"], 2, with_f=(0, 1))
+    tot = 0.0
+    for h in itertools.product(HEL_V, HEL_V, HEL_F, HEL_F):
+        e0 = polarisation(p[0], h[0])
+        e1 = polarisation(p[1], h[1])
+        ubt = bar(u_spinor(p[2], h[2]))
+        vt = v_spinor(p[3], h[3])
+        G0 = (vector_insertion(e0, gs, gs), -p[0])
+        G1 = (vector_insertion(e1, gs, gs), -p[1])
+        A01 = fermion_line(ubt, vt, -p[3], [G0, G1], mt)
+        A10 = fermion_line(ubt, vt, -p[3], [G1, G0], mt)
+        X = vvv_out(e0, p[0], e1, p[1], -(p[0] + p[1]), gs)
+        Gint = vector_prop(p[0] + p[1], X)
+        AG = fermion_line(ubt, vt, -p[3], [(vector_insertion(Gint, gs, gs), -(p[0] + p[1]))], mt)
+        tot = tot + colour.colour_sum([A01 / 1j, A10 / 1j, AG / 1j], [cAB, cBA, cG])
+    return tot / (4.0 * 64.0)
+
+
+# --------------------------------------------------------------------------
+# g g > t t~ > (b e+ ve) (b~ e- ve~): the three doubly-resonant diagrams
+# --------------------------------------------------------------------------
+def gg_ttx_dilep(P, par=SMParams(), per_helicity=False, eps_override=None, all_attachments=False):
+    """Legs: g(0) g(1) b(2) e+(3) ve(4) b~(5) e-(6) ve~(7).
+
+    The fermion line runs from the outgoing b~ (v spinor) to the outgoing b
+    (u-bar spinor): W- emission, top propagator, the gluon insertions (two
+    orders, or the ggg-produced gluon), top propagator, W+ emission.  These
+    are the three doubly-resonant diagrams.  Fixed widths in every top and W
+    propagator.
+
+    all_attachments=True adds the diagrams with a gluon on the b or b~
+    segment of the line (15 in total).  That set, unlike the resonant
+    subset, is QCD gauge invariant at zero widths, which the Ward-identity
+    pin uses.
+    """
+    p = [P[:, k] for k in range(8)]
+    gs, gw, mt, wt = par.gs, par.g / np.sqrt(2.0), par.mt, par.wt
+    tot = 0.0
+    ph = {}
+    # insertion sequences along the arrow; the segment before "Wm" and after "Wp" is a b quark
+    if all_attachments:
+        seqs = []
+        for pos in itertools.permutations(range(4), 2):
+            seq = ["Wm", "Wp"]
+            rest = [x for x in range(4) if x not in pos]
+            full = [None] * 4
+            full[pos[0]], full[pos[1]] = 0, 1
+            full[rest[0]], full[rest[1]] = "Wm", "Wp"
+            seqs.append(full)
+        for slot in range(3):
+            seq = ["Wm", "Wp"]
+            seq.insert(slot, "G")
+            seqs.append(seq)
+    else:
+        seqs = [["Wm", 0, 1, "Wp"], ["Wm", 1, 0, "Wp"], ["Wm", "G", "Wp"]]
+    cols = []
+    for seq in seqs:
+        glu = [x for x in seq if x not in ("Wm", "Wp")]
+        cols.append(_colour_string(glu, 2, with_f=(0, 1)) if "G" in glu else _colour_string(glu, 2))
+    for h in itertools.product(HEL_V, HEL_V, *([HEL_F] * 6)):
+        e = [polarisation(p[0], h[0]), polarisation(p[1], h[1])]
+        if eps_override:
+            for leg, vec in eps_override.items():
+                e[leg] = vec.astype(complex)
+        ub_b = bar(u_spinor(p[2], h[2]))
+        v_ep = v_spinor(p[3], h[3])
+        ub_nu = bar(u_spinor(p[4], h[4]))
+        v_bb = v_spinor(p[5], h[5])
+        ub_em = bar(u_spinor(p[6], h[6]))
+        v_nub = v_spinor(p[7], h[7])
+        Wp = vector_prop(p[3] + p[4], ffv_current(ub_nu, v_ep, gw, 0.0), par.mW, par.wW)
+        Wm = vector_prop(p[6] + p[7], ffv_current(ub_em, v_nub, gw, 0.0), par.mW, par.wW)
+        X = vvv_out(e[0], p[0], e[1], p[1], -(p[0] + p[1]), gs)
+        Gint = vector_prop(p[0] + p[1], X)
+        ins = {"Wm": (vector_insertion(Wm, gw, 0.0), p[6] + p[7]),
+               "Wp": (vector_insertion(Wp, gw, 0.0), p[3] + p[4]),
+               0: (vector_insertion(e[0], gs, gs), -p[0]),
+               1: (vector_insertion(e[1], gs, gs), -p[1]),
+               "G": (vector_insertion(Gint, gs, gs), -(p[0] + p[1]))}
+        amps = []
+        for seq in seqs:
+            amps.append(_line_with_flavours(ub_b, v_bb, -p[5], [ins[x] for x in seq], seq, mt, wt) / 1j)
+        m2 = colour.colour_sum(amps, cols)
+        ph[h] = m2
+        tot = tot + m2
+    avg = tot / (4.0 * 64.0)
+    return (avg, ph) if per_helicity else avg
+
+
+def _line_with_flavours(row, col, p_start, inserts, seq, mt, wt):
+    """Fermion line whose propagators are massless b quarks outside the
+    W- ... W+ stretch and tops (mass mt, width wt) inside it."""
+    vec = col
+    q = p_start.copy()
+    inside = False
+    for k, ((G, Q), tag) in enumerate(zip(inserts, seq)):
+        vec = np.einsum("nij,nj->ni", G, vec)
+        q = q - Q
+        if tag == "Wm":
+            inside = True
+        elif tag == "Wp":
+            inside = False
+        if k < len(inserts) - 1:
+            S = fermion_prop(q, mt, wt) if inside else fermion_prop(q)
+            vec = np.einsum("nij,nj->ni", S, vec)
+    return np.einsum("ni,ni->n", row, vec)
+
+
+# --------------------------------------------------------------------------
+# u s > d c h h  (W+ W- fusion into a Higgs pair)
+# --------------------------------------------------------------------------
+def us_dchh(P, par=SMParams(), per_helicity=False):
+    """Four diagrams: WWHH contact, s-channel H with HHH, and t/u-channel W
+    exchange with two WWH vertices.  H wavefunctions are 1."""
+    p = [P[:, k] for k in range(6)]
+    g, mW, wW, mH, wH, v = par.g, par.mW, par.wW, par.mH, par.wH, par.vev
+    gw = g / np.sqrt(2.0)
+    gwwh = g * mW
+    gwwhh = g * g / 2.0
+    ghhh = -3.0 * mH * mH / v
+    q1 = p[0] - p[2]
+    q2 = p[1] - p[3]
+    tot = 0.0
+    ph = {}
+    for h in itertools.product(HEL_F, repeat=4):
+        J1 = ffv_current(bar(u_spinor(p[2], h[2])), u_spinor(p[0], h[0]), gw, 0.0)
+        J2 = ffv_current(bar(u_spinor(p[3], h[3])), u_spinor(p[1], h[1]), gw, 0.0)
+        W1 = vector_prop(q1, J1, mW, wW)
+        W2 = vector_prop(q2, J2, mW, wW)
+        w12 = mdot(W1, W2)
+        iM = 1j * gwwhh * w12
+        iM = iM + (1j * gwwh * w12) * scalar_prop(q1 + q2, mH, wH) * (1j * ghhh)
+        for hA in (4, 5):
+            k = q1 - p[hA]
+            Wst = vector_prop(k, 1j * gwwh * W1, mW, wW)
+            iM = iM + 1j * gwwh * mdot(Wst, W2)
+        M = iM / 1j
+        m2 = 9.0 * np.abs(M) ** 2
+        ph[h + (0, 0)] = m2
+        tot = tot + m2
+    avg = tot / 36.0
+    return (avg, ph) if per_helicity else avg
+
+
+# --------------------------------------------------------------------------
+# n gluons: colour-ordered Berends-Giele recursion + brute-force colour matrix
+# --------------------------------------------------------------------------
+_SQ2 = np.sqrt(2.0)
+
+
+def _v3_ordered(J1, k1, J2, k2, g):
+    """Colour-ordered three-gluon vertex with legs (1, 2, X) in cyclic order,
+    all momenta outgoing, legs 1 and 2 contracted; returns the vector of X.
+
+    V3 = (i g / sqrt2) [ g^{nu rho}(k1-k2)^mu + g^{rho mu}(k2-kX)^nu + g^{mu nu}(kX-k1)^rho ].
+    """
+    kX = -(k1 + k2)
+    return (1j * g / _SQ2) * (mdot(J1, J2)[..., None] * (k1 - k2)
+                               + J2 * mdot(k2 - kX, J1)[..., None]
+                               + J1 * mdot(kX - k1, J2)[..., None])
+
+
+def _v4_ordered(J1, J2, J3, g):
+    """Colour-ordered four-gluon vertex, legs (1,2,3,X) in cyclic order:
+    i g^2 g^{13} g^{2X} - (i g^2/2)(g^{12} g^{3X} + g^{1X} g^{23})."""
+    return (1j * g * g) * (mdot(J1, J3)[..., None] * J2
+                          - 0.5 * (mdot(J1, J2)[..., None] * J3 + mdot(J2, J3)[..., None] * J1))
+
+
+def gluon_partial_amplitudes(K, E, g):
+    """All colour-ordered amplitudes A(1, sigma_2..sigma_n) for one helicity.
+
+    K: [n, ..., 4] outgoing momenta (incoming legs carry -p); E: [n, ..., 4]
+    external wavefunctions.  Leg 0 is the root; the recursion runs over
+    ordered tuples of the other legs and every ordered tuple's current is
+    built from its consecutive splittings (Berends-Giele).  Returns
+    (orders, A[len(orders), ...]) with A the colour-ordered "i M".
+    """
+    n = K.shape[0]
+    cur = {}
+    mom = {}
+
+    def current(S):
+        if S in cur:
+            return cur[S]
+        if len(S) == 1:
+            cur[S] = E[S[0]]
+            mom[S] = K[S[0]]
+            return cur[S]
+        amp = amputated(S)
+        P = mom[S]
+        cur[S] = -1j * amp / mdot(P, P)[..., None]
+        return cur[S]
+
+    def amputated(S):
+        L = len(S)
+        P = sum(K[s] for s in S)
+        mom[S] = P
+        out = 0.0
+        for i in range(1, L):
+            S1, S2 = S[:i], S[i:]
+            J1, J2 = current(S1), current(S2)
+            out = out + _v3_ordered(J1, mom[S1], J2, mom[S2], g)
+        for i in range(1, L - 1):
+            for j in range(i + 1, L):
+                S1, S2, S3 = S[:i], S[i:j], S[j:]
+                out = out + _v4_ordered(current(S1), current(S2), current(S3), g)
+        return out
+
+    orders = [(0,) + q for q in itertools.permutations(range(1, n))]
+    A = []
+    for o in orders:
+        A.append(mdot(amputated(o[1:]), E[0]))
+    return orders, np.stack(A, axis=0)
+
+
+def gluons(P, n_in=2, par=SMParams(), per_helicity=False, eps_override=None, colour_matrix=None):
+    """g g > g ... g: sum over all helicities of sum_{sigma,tau} A_sigma C A_tau^*.
+
+    Full amplitude: i M = sum_sigma Tr(T^{a1} T^{a_sigma2} ...) A(1, sigma),
+    T^a = sqrt2 t^a, so the colour sum is A^T C A^* with the brute-force C
+    of oracle.colour.gluon_trace_matrix.  Averaged over 4 * 8 * 8.
+    """
+    N, n, _ = P.shape
+    g = par.gs
+    if colour_matrix is None:
+        orders, C = colour.gluon_trace_matrix(n)
+    else:
+        orders, C = colour_matrix
+    K = np.stack([(-P[:, k] if k < n_in else P[:, k]) for k in range(n)], axis=0)
+    tot = 0.0
+    ph = {}
+    for h in itertools.product(HEL_V, repeat=n):
+        E = []
+        for k in range(n):
+            eps = polarisation(P[:, k], h[k])
+            E.append(eps if k < n_in else eps.conj())
+        if eps_override:
+            for leg, vec in eps_override.items():
+                E[leg] = vec.astype(complex)
+        E = np.stack(E, axis=0)
+        o2, A = gluon_partial_amplitudes(K, E, g)
+        assert o2 == orders
+        m2 = np.real(np.einsum("sn,st,tn->n", A, C, A.conj()))
+        ph[h] = m2
+        tot = tot + m2
+    avg = tot / (4.0 * 64.0)
+    return (avg, ph) if per_helicity else avg
+
+
+PROCESSES = {
+    "u u~ > e+ e-": uux_epem,
+    "u d~ > e+ ve": udx_epve,
+    "u u~ > g g": uux_gg,
+    "u d~ > e+ ve g g": udx_epvegg,
+    "g g > t t~": gg_ttx,
+    "g g > t t~ > b e+ ve b~ e- ve~": gg_ttx_dilep,
+    "u s > d c h h": us_dchh,
+    "g g > g g": gluons,
+    "g g > g g g": gluons,
+    "g g > g g g g": gluons,
+}
+
+
+def me(process, P, par=SMParams()):
+    """|M|^2_avg for a process name of PROCESSES."""
+    return PROCESSES[process](P, par=par)

@@ -1,0 +1,165 @@
+"""Pins of the oracle's Philox stream, phase-space generators, cuts and MC estimate."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import phasespace as ps, xsec
+from oracle.lorentz import mdot
+from oracle.sm import SMParams
+
+PAR = SMParams()
+
+
+def test_philox_matches_numpy_library():
+    """numpy.random.Philox is Philox4x64-10; it increments its counter before each block."""
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        ctr = rng.integers(0, 2 ** 63, size=4, dtype=np.uint64)
+        ctr[0] = ctr[0] & np.uint64(0x7FFFFFFFFFFFFFF0)
+        key = rng.integers(0, 2 ** 63, size=2, dtype=np.uint64)
+        lib = np.random.Philox(counter=ctr, key=key).random_raw(8)
+        c1 = ctr.copy()
+        c1[0] += np.uint64(1)
+        c2 = ctr.copy()
+        c2[0] += np.uint64(2)
+        mine = ps.philox4x64_10(np.stack([c1, c2]), key)
+        assert np.array_equal(mine.ravel(), lib)
+
+
+def test_uniforms_range_and_moments():
+    u = ps.uniforms(7, np.arange(20000), np.zeros(20000), 2)
+    assert u.min() > 0 and u.max() < 1
+    assert abs(u.mean() - 0.5) < 0.005
+    assert abs((u * u).mean() - 1 / 3) < 0.005
+    # distinct attempts give distinct streams
+    u1 = ps.uniforms(7, np.arange(100), np.ones(100), 2)
+    assert not np.allclose(u[:100], u1)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 6])
+def test_rambo_massless(n):
+    w = 1000.0
+    u = ps.uniforms(1, np.arange(500), np.zeros(500), n)
+    p, wt = ps.rambo_massless(w, n, u)
+    tot = p.sum(axis=1)
+    assert np.allclose(tot, [w, 0, 0, 0], atol=1e-9 * w)
+    assert np.abs(mdot(p, p)).max() < 1e-9 * w * w
+    assert np.all(p[..., 0] > 0)
+    vol = (2 * math.pi) ** (4 - 3 * n) * (math.pi / 2) ** (n - 1) * w ** (2 * n - 4) / (
+        math.factorial(n - 1) * math.factorial(n - 2))
+    assert np.allclose(wt, vol)
+    if n == 2:
+        assert np.isclose(vol, 1 / (8 * math.pi))
+
+
+def test_rambo_flat_distributions():
+    """n=2: isotropic; n=3: flat Dalitz plot, <x_i> = 2/3, <x_i^2> = 1/2 (x = 2E/w)."""
+    N = 40000
+    u = ps.uniforms(2, np.arange(N), np.zeros(N), 2)
+    p, _ = ps.rambo_massless(500.0, 2, u)
+    c = p[:, 0, 3] / p[:, 0, 0]
+    assert abs(c.mean()) < 0.02 and abs((c * c).mean() - 1 / 3) < 0.01
+    u = ps.uniforms(3, np.arange(N), np.zeros(N), 3)
+    p, _ = ps.rambo_massless(500.0, 3, u)
+    x = 2 * p[:, :, 0] / 500.0
+    assert np.allclose(x.mean(axis=0), 2 / 3, atol=0.01)
+    assert np.allclose((x * x).mean(axis=0), 0.5, atol=0.01)
+
+
+def test_rambo_massive():
+    w = 1000.0
+    u = ps.uniforms(4, np.arange(200), np.zeros(200), 2)
+    m1, m2 = 125.0, 300.0
+    p, wt = ps.rambo_massive(w, [m1, m2], u)
+    assert np.allclose(p.sum(axis=1), [w, 0, 0, 0], atol=1e-9 * w)
+    assert np.allclose(mdot(p[:, 0], p[:, 0]), m1 * m1, rtol=1e-10)
+    assert np.allclose(mdot(p[:, 1], p[:, 1]), m2 * m2, rtol=1e-10)
+    k = math.sqrt((w * w - (m1 + m2) ** 2) * (w * w - (m1 - m2) ** 2)) / (2 * w)
+    assert np.allclose(wt, k / (4 * math.pi * w), rtol=1e-12)
+    # three massive bodies: volume against direct two-step integration
+    N = 200000
+    u = ps.uniforms(5, np.arange(N), np.zeros(N), 3)
+    ms = [125.0, 125.0, 0.0]
+    p, wt = ps.rambo_massive(w, ms, u)
+    vol_mc = wt.mean()
+    # dPhi_3 = int ds23/(2 pi) Phi_2(w; m1, sqrt(s23)) Phi_2(sqrt(s23); m2, m3)
+    s = np.linspace((ms[1] + ms[2]) ** 2, (w - ms[0]) ** 2, 200001)
+    lam = lambda a, b, c: a * a + b * b + c * c - 2 * a * b - 2 * b * c - 2 * a * c
+    f = (np.sqrt(np.maximum(lam(w * w, ms[0] ** 2, s), 0)) / (8 * math.pi * w * w)
+         * np.sqrt(np.maximum(lam(s, ms[1] ** 2, ms[2] ** 2), 0)) / (8 * math.pi * s)) / (2 * math.pi)
+    vol = np.trapezoid(f, s)
+    assert abs(vol_mc / vol - 1) < 0.01
+
+
+def test_breit_wigner_jacobian():
+    """Mean of the Eq. 16 Jacobian over uniform theta equals the s range / (2 pi)."""
+    m, w = 175.0, 1.5
+    u = (np.arange(200000) + 0.5) / 200000
+    s, jac = ps.bw_sample(m, w, u)
+    t0, t1 = ps.bw_range(m, w)
+    s_lo, s_hi = m * m + m * w * math.tan(t0), m * m + m * w * math.tan(t1)
+    assert np.isclose(jac.mean() * 2 * math.pi, s_hi - s_lo, rtol=1e-6)
+    assert np.isclose(s_hi - m * m, 20 * m * w)
+    # the range rule min(20, m/Gamma)
+    assert np.isclose(math.tan(ps.bw_range(10.0, 2.0)[1]), 5.0)
+
+
+def test_ttbar_chain_kinematics():
+    N = 2000
+    u = ps.uniforms(2, np.arange(N), np.zeros(N), 4)
+    P, wt, ok, shat = ps.ttbar_dilepton(u, PAR, (400.0, 2000.0))
+    P, wt, shat = P[ok], wt[ok], shat[ok]
+    assert ok.mean() > 0.5
+    fin = P[:, 2:].sum(axis=1)
+    ini = P[:, 0] + P[:, 1]
+    assert np.allclose(fin, ini, atol=1e-9 * 2000)
+    assert np.abs(mdot(P[:, 2:], P[:, 2:])).max() < 1e-8
+    t = P[:, 2] + P[:, 3] + P[:, 4]
+    tb = P[:, 5] + P[:, 6] + P[:, 7]
+    W = P[:, 3] + P[:, 4]
+    for v, m, g in ((t, PAR.mt, PAR.wt), (tb, PAR.mt, PAR.wt), (W, PAR.mW, PAR.wW)):
+        s = mdot(v, v)
+        assert np.all(np.abs(s - m * m) <= 20 * m * g * (1 + 1e-9))
+    assert np.all(wt > 0)
+    assert np.all((np.sqrt(shat) >= 400) & (np.sqrt(shat) <= 2000))
+
+
+def test_cut_definitions():
+    def mom(pt_, eta_, phi_):
+        return np.array([pt_ * math.cosh(eta_), pt_ * math.cos(phi_), pt_ * math.sin(phi_), pt_ * math.sinh(eta_)])
+
+    base = [mom(50, 0.0, 0.0), mom(50, 1.0, 2.0)]
+    P = np.array([[np.zeros(4), np.zeros(4)] + base])
+    assert ps.pass_cuts(P, [2, 3], 20.0, 2.5, 0.4)[0]
+    for bad in (mom(19.9, 0.5, 4.0), mom(50, 2.51, 4.0), mom(50, -2.51, 4.0), mom(50, 0.2, 0.3)):
+        P = np.array([[np.zeros(4), np.zeros(4)] + base + [bad]])
+        assert not ps.pass_cuts(P, [2, 3, 4], 20.0, 2.5, 0.4)[0]
+    # Delta R across the phi = +-pi seam
+    P = np.array([[np.zeros(4), np.zeros(4), mom(50, 0, math.pi - 0.1), mom(50, 0, -math.pi + 0.1)]])
+    assert not ps.pass_cuts(P, [2, 3], 20.0, 2.5, 0.4)[0]
+    assert np.isclose(ps.delta_r(P[:, 2], P[:, 3])[0], 0.2)
+
+
+def test_mc_estimate_two_body_closed_form():
+    """sigma-hat(u u~ > e+ e-) from the resampled generator against the integral of the
+    closed-form dsigma/dcos(theta) (Gauss-Legendre), within 4 standard errors."""
+    from oracle import processes as pr
+    kin = {"kind": "2to2", "sqrt_s": 500.0}
+    P, W, S, tries = xsec.generate(kin, PAR, 0, np.arange(20000))
+    me2 = pr.uux_epem(P, PAR)
+    sw, sw2, nacc, ntry = xsec.accumulate(me2, W, S, tries, 1.0)
+    sig, err = xsec.estimate(sw, sw2, ntry)
+    x, wq = np.polynomial.legendre.leggauss(64)
+    Q = np.zeros((64, 4, 4))
+    Q[:, 0] = [250, 0, 0, 250]
+    Q[:, 1] = [250, 0, 0, -250]
+    Q[:, 3, 0] = 250
+    Q[:, 3, 1] = 250 * np.sqrt(1 - x * x)
+    Q[:, 3, 3] = 250 * x
+    Q[:, 2, 0] = 250
+    Q[:, 2, 1:] = -Q[:, 3, 1:]
+    dsig = pr.uux_epem(Q, PAR) / (32 * math.pi * 500.0 ** 2) * 0.3893793721e9
+    exact = np.sum(wq * dsig)
+    assert abs(sig - exact) < 4 * err
+    assert err / sig < 0.02

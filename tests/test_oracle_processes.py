@@ -1,0 +1,278 @@
+"""Pins of the oracle's |M|^2: closed forms, Parke-Taylor, Ward identity, Bose symmetry, boosts."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import colour, phasespace as ps, processes as pr
+from oracle.lorentz import boost, mdot, rotate
+from oracle.sm import CHARGE, T3, SMParams
+
+PAR = SMParams()
+
+
+def two_to_two(sqrt_s, n, m3=0.0, m4=0.0, seed=0):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-0.95, 0.95, n)
+    phi = rng.uniform(0, 2 * np.pi, n)
+    s = sqrt_s ** 2
+    pabs = math.sqrt((s - (m3 + m4) ** 2) * (s - (m3 - m4) ** 2)) / (2 * sqrt_s)
+    P = np.zeros((n, 4, 4))
+    P[:, 0] = [sqrt_s / 2, 0, 0, sqrt_s / 2]
+    P[:, 1] = [sqrt_s / 2, 0, 0, -sqrt_s / 2]
+    nvec = np.stack([np.sqrt(1 - c * c) * np.cos(phi), np.sqrt(1 - c * c) * np.sin(phi), c], axis=1)
+    P[:, 2, 0] = math.sqrt(m3 * m3 + pabs * pabs)
+    P[:, 2, 1:] = pabs * nvec
+    P[:, 3, 0] = math.sqrt(m4 * m4 + pabs * pabs)
+    P[:, 3, 1:] = -pabs * nvec
+    return P
+
+
+def rambo_points(sqrt_s, n_final, n, seed=0):
+    u = np.random.default_rng(seed).uniform(0.01, 0.99, (n, 4 * n_final))
+    pf, _ = ps.rambo_massless(sqrt_s, n_final, u)
+    P = np.zeros((n, n_final + 2, 4))
+    P[:, 0], P[:, 1] = ps.incoming(sqrt_s, n)
+    P[:, 2:] = pf
+    return P
+
+
+def random_lorentz(P, seed):
+    rng = np.random.default_rng(seed)
+    beta = rng.normal(size=3)
+    beta *= 0.9 / np.linalg.norm(beta)
+    R, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    return rotate(boost(P, beta), R)
+
+
+# ---------------------------------------------------------------------------
+# closed forms
+# ---------------------------------------------------------------------------
+def test_uux_epem_closed_form():
+    """u u~ > gamma/Z > e+ e-: helicity-amplitude closed form, theta = angle(e-, u)."""
+    P = two_to_two(500.0, 64, seed=1)
+    s = 500.0 ** 2
+    c = P[:, 3, 3] / P[:, 3, 0]
+    sw2 = PAR.sw2
+    cw2 = 1 - sw2
+    e = PAR.e
+    prop = s / (s - PAR.mZ ** 2 + 1j * PAR.mZ * PAR.wZ)
+
+    def g(f, chir):
+        return T3[f] - CHARGE[f] * sw2 if chir == "L" else -CHARGE[f] * sw2
+
+    A = {(i, j): CHARGE["u"] * CHARGE["e"] + g("u", i) * g("e", j) / (sw2 * cw2) * prop
+         for i in "LR" for j in "LR"}
+    want = (e ** 4 / 12.0) * ((1 + c) ** 2 * (abs(A["L", "L"]) ** 2 + abs(A["R", "R"]) ** 2)
+                             + (1 - c) ** 2 * (abs(A["L", "R"]) ** 2 + abs(A["R", "L"]) ** 2))
+    got = pr.uux_epem(P)
+    assert np.allclose(got, want, rtol=1e-12, atol=0)
+    # QED limit: Z switched off
+    qed = PAR.with_(mZ=1e9, wZ=0.0)
+    want_qed = e ** 4 * CHARGE["u"] ** 2 * (1 + c * c) / 3.0
+    assert np.allclose(pr.uux_epem(P, qed), want_qed, rtol=1e-9)
+
+
+def test_udx_epve_closed_form():
+    """u d~ > W+ > e+ ve: avg|M|^2 = g^4/3 (p_u.p_e)(p_d.p_v) / |s - mW^2 + i mW GW|^2."""
+    P = two_to_two(300.0, 64, seed=2)
+    s = 300.0 ** 2
+    D = abs(s - PAR.mW ** 2 + 1j * PAR.mW * PAR.wW) ** 2
+    want = PAR.g ** 4 / 3.0 * mdot(P[:, 0], P[:, 2]) * mdot(P[:, 1], P[:, 3]) / D
+    assert np.allclose(pr.udx_epve(P), want, rtol=1e-12)
+
+
+def test_uux_gg_closed_form():
+    P = two_to_two(1000.0, 64, seed=3)
+    s = 1e6
+    t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
+    u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    want = PAR.gs ** 4 * ((32 / 27) * (t * t + u * u) / (t * u) - (8 / 3) * (t * t + u * u) / (s * s))
+    assert np.allclose(pr.uux_gg(P), want, rtol=1e-12)
+
+
+def test_gg_ttx_closed_form():
+    mt = PAR.mt
+    P = two_to_two(800.0, 64, m3=mt, m4=mt, seed=4)
+    s = 800.0 ** 2
+    t1 = 2 * mdot(P[:, 0], P[:, 2]) / s
+    t2 = 2 * mdot(P[:, 1], P[:, 2]) / s
+    rho = 4 * mt * mt / s
+    want = PAR.gs ** 4 * (1 / (6 * t1 * t2) - 3 / 8) * (t1 ** 2 + t2 ** 2 + rho - rho ** 2 / (4 * t1 * t2))
+    assert np.allclose(pr.gg_ttx(P), want, rtol=1e-12)
+
+
+def test_gg_gg_closed_form():
+    P = two_to_two(1500.0, 64, seed=5)
+    s = 1500.0 ** 2
+    t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
+    u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    want = 4.5 * PAR.gs ** 4 * (3 - t * u / s ** 2 - s * u / t ** 2 - s * t / u ** 2)
+    assert np.allclose(pr.gluons(P), want, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Parke-Taylor MHV amplitudes for 5 and 6 gluons
+# ---------------------------------------------------------------------------
+def _angle_products(K):
+    """<ij> for all-outgoing massless momenta K [n, N, 4] (negative energies continued by i)."""
+    n = K.shape[0]
+    lam = []
+    for k in range(n):
+        sgn = np.sign(K[k][:, 0])
+        q = K[k] * sgn[:, None]
+        kp = q[:, 0] + q[:, 3]
+        km = q[:, 0] - q[:, 3]
+        big = kp > km
+        kp_, km_ = np.where(big, kp, 1.0), np.where(big, 1.0, km)
+        # the two forms differ by a phase only; pick the one without a small denominator
+        l0 = np.where(big, np.sqrt(kp_) + 0j, (q[:, 1] - 1j * q[:, 2]) / np.sqrt(km_))
+        l1 = np.where(big, (q[:, 1] + 1j * q[:, 2]) / np.sqrt(kp_), np.sqrt(km_) + 0j)
+        fac = np.where(sgn < 0, 1j, 1.0)
+        lam.append(np.stack([l0 * fac, l1 * fac], axis=1))
+    ang = np.zeros((n, n, K.shape[1]), dtype=complex)
+    for i in range(n):
+        for j in range(n):
+            ang[i, j] = lam[i][:, 0] * lam[j][:, 1] - lam[i][:, 1] * lam[j][:, 0]
+    return ang
+
+
+@pytest.mark.parametrize("n_final", [3, 4])
+def test_mhv_parke_taylor(n_final):
+    n = n_final + 2
+    P = rambo_points(1500.0, n_final, 16, seed=6)
+    K = np.stack([-P[:, 0], -P[:, 1]] + [P[:, k] for k in range(2, n)], axis=0)
+    ang = _angle_products(K)
+    assert np.allclose(np.abs(ang[0, 2]) ** 2, np.abs(2 * mdot(K[0], K[2])), rtol=1e-10)
+    orders, C = colour.gluon_trace_matrix(n)
+    g = PAR.gs
+    for neg in [(0, 1), (0, 3), (2, 4)]:
+        # outgoing helicities: legs in `neg` negative, the rest positive
+        out_hel = [(-1 if k in neg else 1) for k in range(n)]
+        phys = [(-h if k < 2 else h) for k, h in enumerate(out_hel)]
+        E = []
+        from oracle.lorentz import polarisation
+        for k in range(n):
+            eps = polarisation(P[:, k], phys[k])
+            E.append(eps if k < 2 else eps.conj())
+        _, A = pr.gluon_partial_amplitudes(K, np.stack(E), g)
+        i, j = neg
+        pt = []
+        for o in orders:
+            d = 1.0
+            for a in range(n):
+                d = d * ang[o[a], o[(a + 1) % n]]
+            pt.append(g ** (n - 2) * ang[i, j] ** 4 / d)
+        pt = np.array(pt)
+        assert np.allclose(np.abs(A), np.abs(pt), rtol=1e-10)
+        m2_or = np.real(np.einsum("sn,st,tn->n", A, C, A.conj()))
+        m2_pt = np.real(np.einsum("sn,st,tn->n", pt, C, pt.conj()))
+        assert np.allclose(m2_or, m2_pt, rtol=1e-10)
+
+
+def test_all_plus_and_one_minus_vanish():
+    P = rambo_points(1500.0, 4, 8, seed=7)
+    _, ph = pr.gluons(P, per_helicity=True)
+    tot = sum(ph.values())
+    for h, v in ph.items():
+        out = [(-x if k < 2 else x) for k, x in enumerate(h)]
+        if sum(1 for x in out if x < 0) <= 1 or sum(1 for x in out if x > 0) <= 1:
+            assert np.all(v < 1e-20 * tot)
+
+
+# ---------------------------------------------------------------------------
+# gauge invariance, Bose symmetry, Lorentz invariance
+# ---------------------------------------------------------------------------
+def test_ward_identity_w2j():
+    P = rambo_points(1000.0, 4, 16, seed=8)
+    ref = pr.udx_epvegg(P)
+    for leg in (4, 5):
+        bad = pr.udx_epvegg(P, eps_override={leg: P[:, leg]})
+        # eps -> k scales the amplitude by ~E: amplitude-level residual below 1e-12
+        assert np.all(bad < 1e-24 * ref * P[:, leg, 0] ** 2)
+
+
+def test_ward_identity_gluons():
+    P = rambo_points(1500.0, 3, 8, seed=9)
+    ref = pr.gluons(P)
+    bad = pr.gluons(P, eps_override={3: P[:, 3]})
+    assert np.all(bad < 1e-24 * ref * P[:, 3, 0] ** 2)
+
+
+def _ttbar_points(n, seed, par=PAR):
+    u = np.random.default_rng(seed).uniform(0.02, 0.98, (4 * n, 16))
+    P, wt, ok, _ = ps.ttbar_dilepton(u, par, (400.0, 2000.0))
+    return P[ok][:n]
+
+
+def test_ward_identity_ttbar_zero_width():
+    """The resonant subset alone is not gauge invariant; the full set of gluon
+    attachments to the b~ -> t~ ... t -> b line is, at zero widths."""
+    par0 = PAR.with_(wt=0.0, wW=0.0)
+    # points drawn with broad resonances, away from the poles the zero-width amplitude has
+    P = _ttbar_points(8, 10, par=PAR.with_(wt=40.0, wW=25.0))
+    ref = pr.gg_ttx_dilep(P, par0, all_attachments=True)
+    for leg in (0, 1):
+        bad = pr.gg_ttx_dilep(P, par0, eps_override={leg: P[:, leg]}, all_attachments=True)
+        # near-collinear b-g propagators condition the cancellation; the resonant subset
+        # alone leaves residuals of order 1e-3 here, a wrong sign or vertex O(1)
+        assert np.all(bad < 1e-14 * ref * P[:, leg, 0] ** 2)
+
+
+def test_bose_symmetry():
+    P = rambo_points(1000.0, 4, 16, seed=11)
+    Q = P[:, [0, 1, 2, 3, 5, 4]]
+    assert np.allclose(pr.udx_epvegg(P), pr.udx_epvegg(Q), rtol=1e-12)
+    P = _ttbar_points(8, 12)
+    Q = P[:, [1, 0, 2, 3, 4, 5, 6, 7]]
+    assert np.allclose(pr.gg_ttx_dilep(P), pr.gg_ttx_dilep(Q), rtol=1e-11)
+    P = rambo_points(1500.0, 4, 4, seed=13)
+    ref = pr.gluons(P)
+    for perm in ([0, 1, 3, 2, 5, 4], [1, 0, 5, 4, 3, 2]):
+        assert np.allclose(pr.gluons(P[:, perm]), ref, rtol=1e-11)
+
+
+@pytest.mark.parametrize("name", ["u u~ > e+ e-", "u d~ > e+ ve g g", "g g > t t~ > b e+ ve b~ e- ve~",
+                                  "u s > d c h h", "g g > g g g"])
+def test_lorentz_invariance(name):
+    if name == "u u~ > e+ e-":
+        P = two_to_two(500.0, 16, seed=14)
+    elif name == "g g > t t~ > b e+ ve b~ e- ve~":
+        P = _ttbar_points(8, 15)
+    elif name == "u s > d c h h":
+        u = np.random.default_rng(16).uniform(0.02, 0.98, (16, 16))
+        pf, _ = ps.rambo_massive(1000.0, [0.0, 0.0, PAR.mH, PAR.mH], u)
+        P = np.zeros((16, 6, 4))
+        P[:, 0], P[:, 1] = ps.incoming(1000.0, 16)
+        P[:, 2:] = pf
+    elif name == "g g > g g g":
+        P = rambo_points(1500.0, 3, 8, seed=17)
+    else:
+        P = rambo_points(1000.0, 4, 16, seed=18)
+    f = pr.PROCESSES[name]
+    if name == "g g > t t~ > b e+ ve b~ e- ve~":
+        # the doubly-resonant subset is not gauge invariant, so its helicity sum depends on the
+        # frame that defines the gluon helicity vectors (eps^0 = 0): rotations only.  The full
+        # attachment set at zero widths is gauge invariant and boost invariant.
+        R, _ = np.linalg.qr(np.random.default_rng(19).normal(size=(3, 3)))
+        assert np.allclose(f(rotate(P, R)), f(P), rtol=5e-11)
+        par0 = PAR.with_(wt=0.0, wW=0.0)
+        P = _ttbar_points(8, 15, par=PAR.with_(wt=40.0, wW=25.0))
+        a = pr.gg_ttx_dilep(P, par0, all_attachments=True)
+        b = pr.gg_ttx_dilep(random_lorentz(P, 19), par0, all_attachments=True)
+        assert np.allclose(a, b, rtol=1e-8)
+        return
+    assert np.allclose(f(random_lorentz(P, 19)), f(P), rtol=5e-11)
+
+
+def test_us_dchh_positive_and_finite():
+    u = np.random.default_rng(20).uniform(0.02, 0.98, (32, 16))
+    pf, _ = ps.rambo_massive(1000.0, [0.0, 0.0, PAR.mH, PAR.mH], u)
+    P = np.zeros((32, 6, 4))
+    P[:, 0], P[:, 1] = ps.incoming(1000.0, 32)
+    P[:, 2:] = pf
+    m2 = pr.us_dchh(P)
+    assert np.all(np.isfinite(m2)) and np.all(m2 > 0)
+    # symmetric under exchange of the two Higgs bosons
+    assert np.allclose(pr.us_dchh(P[:, [0, 1, 2, 3, 5, 4]]), m2, rtol=1e-12)
