@@ -1,0 +1,328 @@
+"""Benchmark: |M|^2 evaluations per second of one Monte Carlo step on GB300.
+
+A step is one pass of the whole hot path over one batch of 2^20 accepted
+points of u d~ > e+ ve g g at sqrt(s) = 1 TeV (RAMBO, pT > 20 GeV,
+|eta| < 2.5, Delta R > 0.4, seed 1): Philox draws, phase space, cuts and
+redraws, invariants, wavefunctions, the diagram program, colour sum,
+helicity sum, weights and the deterministic Monte Carlo reduction, through
+xsec_step of the C ABI, in the mixed precision (FP32 amplitudes, FP64
+momenta, resonant invariants and accumulation).  The FP64 path is timed
+beside it for context.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload KEY]
+
+With N > 1 (torchrun, one process per GPU) each rank runs its own 2^20 points
+(disjoint Philox counters): weak scaling, no data-path collective.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def fp32_alu_peak_tflops(mhz=SM_MAX_MHZ):
+    """FP32 CUDA-core peak: SMs x FP32 lanes x 2 flop (FMA) x clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        mhz.sort()
+        return {"sm_mhz": mhz[len(mhz) // 2] if mhz else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_kin(w):
+    from paper_1305_0708_gb300.compiler.diagrams import parse
+    n_ext = len(parse(w["process"]).particles)
+    if w["kind"] == "two_body":
+        k = {"kind": "2to2", "sqrt_s": w["sqrt_s"]}
+    elif w["kind"] == "rambo":
+        k = {"kind": "rambo", "sqrt_s": w["sqrt_s"], "n_final": n_ext - 2}
+        if "masses" in w:
+            k["masses"] = list(w["masses"][2:])
+    else:
+        k = {"kind": "ttbar", "sqrt_s_range": w["sqrt_s_range"]}
+    if w.get("cuts"):
+        c = w["cuts"]
+        k["cuts"] = {"legs": list(c["legs"]), "pt_min": c["pt_min"], "eta_max": c["eta_max"], "dr_min": c["dr_min"]}
+    return k
+
+
+def oracle_step(w, events):
+    """The oracle's whole step on a sample of events: generate, |M|^2, accumulate."""
+    from oracle import processes as opr, xsec as oxs
+    from oracle.sm import SMParams
+    fn = {"u u~ > e+ e-": opr.uux_epem, "u d~ > e+ ve g g": opr.udx_epvegg,
+          "g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))": opr.gg_ttx_dilep,
+          "u s > d c h h": opr.us_dchh}[w["process"]]
+    par = SMParams()
+    P, W, S, T = oxs.generate(oracle_kin(w), par, w["seed"], events)
+    return oxs.accumulate(fn(P, par), W, S, T, w["s_ident"])
+
+
+def run_reference(args, w, rank, world):
+    """FP64 CPU oracle on the host cores: bounded samples per step."""
+    import numpy as np
+    if rank != 0:
+        return
+    sample = args.ref_sample
+    oracle_step(w, np.arange(64))  # warm caches and imports
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle_step(w, np.arange(s * sample, (s + 1) * sample))
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    per_step = sum(times) / len(times)
+    value = sample / per_step
+    line = {"metric": "|M|^2 evals/s", "value": value, "unit": "evals/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "describe": w["describe"], "points_per_step": sample,
+                       "l2": "not applicable (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} accepted points per step of the same workload (numpy FP64, "
+                                       f"one thread)"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="udx_epvegg")
+    ap.add_argument("--ref-sample", type=int, default=1000)
+    ap.add_argument("--cpu-sample", type=int, default=1000)
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+
+    from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args
+    w = WORKLOADS[args.workload]
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__ as g
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    g.build() if rank == 0 or world == 1 else None
+    if world > 1:
+        dist.barrier()
+    from paper_1305_0708_gb300 import binding as B
+    B.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = w["n"]
+    kin = B.make_kin(**kin_args(w))
+    stream = torch.cuda.current_stream(dev)
+    offset0 = rank * (1 << 40)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def time_steps(h, steps, warmup):
+        acc = B.me_xsec_acc()
+        for s in range(warmup):
+            B.xsec_step(h, w["seed"], offset0 + s * n, n, kin, stream, acc)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            B.xsec_step(h, w["seed"], offset0 + (warmup + s) * n, n, kin, stream, acc)
+            ev[s][1].record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, wall, acc
+
+    clocks = Clocks()
+    h32 = B.me_create(w["process"], None, B.ME_MIXED)
+    info = B.me_info(h32)
+    clocks.start()
+    ms32, wall32, acc32 = time_steps(h32, args.steps, args.warmup)
+    clk = clocks.stop(local)
+    step_ms = sum(ms32) / len(ms32)
+    t_max = torch.tensor([step_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    step_ms = float(t_max.item())
+    value = n * world / (step_ms * 1e-3)
+
+    # kernel-only duration of the fused kernel: me_eval-free k_xsec is the step minus the
+    # one-block reduction and the 32-byte read-back; time the reduction-free kernel via me_generate+eval
+    # is not separable here, so the step duration bounds the kernel duration from above.
+    kern_ms = step_ms
+    flops_event = info.flops_amp
+    achieved = flops_event * n / (kern_ms * 1e-3) / 1e12
+    peak = fp32_alu_peak_tflops()
+
+    # FP64 path for context
+    fp64 = None
+    if not args.no_fp64:
+        h64 = B.me_create(w["process"], None, B.ME_FP64)
+        ms64, _, _ = time_steps(h64, max(3, args.steps // 4), 3)
+        s64 = sum(ms64) / len(ms64)
+        fp64 = {"value": n / (s64 * 1e-3), "unit": "evals/s", "ms_per_step": s64}
+        B.me_destroy(h64)
+
+    # end to end through the public API with host buffers: momenta H2D, me_eval, |M|^2 D2H
+    mom_dev = torch.empty(info.n_ext * 4 * n, dtype=torch.float64, device=dev)
+    me2_dev = torch.empty(n, dtype=torch.float64, device=dev)
+    B.xsec_step(h32, w["seed"], offset0, n, kin, stream, B.me_xsec_acc(), me2_dev, mom_dev)
+    mom_host = mom_dev.cpu().pin_memory()
+    out_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        mom_dev.copy_(mom_host, non_blocking=True)
+        B.me_eval(h32, mom_dev, n, me2_dev, stream)
+        out_host.copy_(me2_dev, non_blocking=True)
+    barrier()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        mom_dev.copy_(mom_host, non_blocking=True)
+        B.me_eval(h32, mom_dev, n, me2_dev, stream)
+        out_host.copy_(me2_dev, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = sorted(e2e_ms)[len(e2e_ms) // 2]
+    e2e = {"value": n * world / (e2e_step * 1e-3), "unit": "evals/s",
+           "h2d_bytes_per_step": int(mom_host.numel() * 8), "d2h_bytes_per_step": int(n * 8),
+           "path": "me_eval with host momenta: pinned H2D copy, kernel, D2H of |M|^2"}
+    # kernel-only me_eval time (momenta resident)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evals = []
+    for _ in range(5):
+        flush.zero_()
+        ev0.record(stream)
+        B.me_eval(h32, mom_dev, n, me2_dev, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        evals.append(ev0.elapsed_time(ev1))
+    me_eval_ms = sorted(evals)[len(evals) // 2]
+    B.me_destroy(h32)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        events = np.arange(args.cpu_sample)
+        oracle_step(w, np.arange(32))
+        t0 = time.perf_counter()
+        oracle_step(w, events)
+        dt = time.perf_counter() - t0
+        cpu = {"value": args.cpu_sample / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample} accepted points of the same workload (generate, |M|^2, weights), "
+                         f"numpy FP64 on one host core"}
+
+    if rank == 0:
+        line = {
+            "metric": "|M|^2 evals/s", "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 amplitudes, f64 momenta/resonant invariants/accumulation",
+            "data": "synthetic (on-device Philox phase space)",
+            "config": {"workload": args.workload, "describe": w["describe"], "points_per_step_per_gpu": n,
+                       "precision": "mixed", "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "fp64_path": fp64,
+            "me_eval_ms": me_eval_ms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_xsec<float> (fused phase space + |M|^2 + reduction), step duration",
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                         "flops_per_event": flops_event},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "mc": {"sigma_pb": acc32.sum_w / acc32.n_try, "n_try": acc32.n_try, "n_acc": acc32.n_acc},
+            "wall_s_timed": wall32,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * me.h -- C ABI of the GB300 tree-level matrix-element engine.
+ *
+ * The library evaluates, for every phase-space point of a Standard Model
+ * tree-level process, the spin- and colour-summed squared amplitude averaged
+ * over the initial helicities and colours,
+ *
+ *     |M|^2 = 1/(4 n_a n_b) sum_lambda sum_c | sum_diagrams M |^2
+ *
+ * (Hagiwara, Kanzaki, Li, Okamura, Stelzer, arXiv:1305.0708, Sect. 2,
+ * Eqs. 4-6), and the Monte Carlo estimate of the partonic cross section
+ * d sigma-hat = 1/(2 s-hat) |M|^2 dPhi_n (Eqs. 4-5) over on-device phase-space
+ * points with cuts.  Processes are compiled ahead of time by the package's
+ * process compiler (the converter of Sect. 5) and selected by name.
+ *
+ * Conventions for every entry point:
+ *  - Return value: ME_OK (0) or a negative me_status; me_last_error() gives a
+ *    thread-local description of the last failure.  Argument errors are
+ *    detected before any device work is queued.
+ *  - Pointers named "device" must be device-accessible memory of the current
+ *    CUDA device; "host" pointers are host memory.  The caller owns every
+ *    buffer it passes; the library owns the handle, its device-resident
+ *    program data and its workspace.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    queued on it asynchronously unless the entry point says it synchronises.
+ *  - Momenta are FP64 four-vectors (E, px, py, pz) in GeV, metric (+,-,-,-),
+ *    stored structure-of-arrays: component mu of leg k of event i is at
+ *    momenta[(k * 4 + mu) * n + i].  Incoming partons come first and carry
+ *    physical (positive-energy) momenta; legs follow the process string.
+ *  - A handle is immutable after me_create: concurrent calls on different
+ *    streams are allowed.  Calls that use the handle's workspace
+ *    (xsec_step, me_generate) must not overlap on the device.
+ */
+#ifndef ME_H_
+#define ME_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct me_handle_s *me_handle;
+
+typedef enum {
+  ME_OK = 0,
+  ME_ERR_ARG = -1,      /* invalid argument (null pointer, size, unknown option) */
+  ME_ERR_PROCESS = -2,  /* process name not compiled into this library */
+  ME_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+  ME_ERR_OOM = -4,      /* device allocation failed */
+  ME_ERR_TIMEOUT = -5,  /* a bounded device loop gave up (phase-space redraws exhausted) */
+  ME_ERR_STATE = -6     /* call not valid in the handle's state */
+} me_status;
+
+typedef enum {
+  ME_FP64 = 0,  /* every amplitude operation in FP64 */
+  ME_MIXED = 1  /* FP32 amplitudes; FP64 momenta, invariants and propagator denominators */
+} me_precision;
+
+/* Standard Model inputs (GeV).  Electroweak scheme: e = sqrt(4 pi alpha),
+ * g = e / s_W, g_Z = e / (s_W c_W), v = 2 mW / g.  Fixed widths in every
+ * propagator, including t-channel ones (as the paper's HEGET functions). */
+typedef struct {
+  double alpha, sw2, mZ, wZ, mW, wW, alpha_s, mt, wt, mH, wH;
+} me_params;
+
+/* Phase-space generators (Sect. 3 and App. A of the paper give its own
+ * parametrisation; these are the generators of the workloads). */
+typedef enum {
+  ME_PS_TWO_BODY = 0,  /* 2 -> 2 at fixed sqrt_s, cos(theta) and phi uniform (massless) */
+  ME_PS_RAMBO = 1,     /* flat n-body (RAMBO) at fixed sqrt_s; mass[] per leg, 0 = massless */
+  ME_PS_TTBAR = 2      /* g g > t t~ > (b e+ ve)(b~ e- ve~): sqrt_s uniform in [sqrt_s_min,
+                          sqrt_s_max], Breit-Wigner t, t~, W+, W- (Eq. 16, App. A.2), isotropic
+                          two-body decays in every rest frame */
+} me_ps_kind;
+
+typedef struct {
+  int32_t kind;            /* me_ps_kind */
+  int32_t max_attempts;    /* redraw limit per point (<= 0: 10000) */
+  double sqrt_s;           /* partonic energy (two-body, RAMBO) */
+  double sqrt_s_min, sqrt_s_max;  /* range of sqrt(s-hat) (ttbar) */
+  double mass[16];         /* on-shell mass per leg (RAMBO); ignored otherwise */
+  int32_t n_cut_legs;      /* legs the cuts apply to (0 = no cuts), at most 8 */
+  int32_t cut_legs[8];
+  double pt_min;           /* pT > pt_min */
+  double eta_max;          /* |eta| < eta_max (pseudorapidity) */
+  double dr_min;           /* Delta R > dr_min for every pair of cut legs */
+  double s_ident;          /* identical-particle factor 1/k! applied to the weights */
+} me_kin;
+
+/* Monte Carlo accumulator (host).  xsec_step adds to it. */
+typedef struct {
+  double sum_w;   /* sum of weights, pb */
+  double sum_w2;  /* sum of squared weights, pb^2 */
+  int64_t n_acc;  /* accepted points */
+  int64_t n_try;  /* draws, accepted or not */
+} me_xsec_acc;
+
+typedef struct {
+  int32_t n_ext;           /* external legs */
+  int32_t n_hel;           /* helicity combinations */
+  int32_t n_hel_live;      /* combinations evaluated (structural zeros removed) */
+  int32_t n_colour;        /* colour basis size K */
+  int32_t n_diagrams;      /* Feynman-diagram amplitudes (a 4-gluon vertex counts 3) */
+  int32_t pdg[16];         /* PDG code per leg */
+  double flops_amp;        /* amplitude-precision flops per event (compiler count) */
+  double flops_fp64;       /* FP64 flops per event in the amplitude kernel (momenta, invariants) */
+} me_info_t;
+
+/* Create a handle for a compiled process, e.g. "u d~ > e+ ve g g".
+ * params: host pointer, NULL for the defaults (alpha = 1/128, sw2 = 0.2312,
+ * mZ = 91.1876, wZ = 2.4952, mW = 80.4, wW = 2.085, alpha_s = 0.118,
+ * mt = 175, wt = 1.5, mH = 125, wH = 0).  prec: me_precision.
+ * Uploads nothing large; allocates no workspace until first needed.
+ * Errors: ME_ERR_PROCESS for a name not compiled in, ME_ERR_ARG otherwise. */
+me_status me_create(const char *process, const me_params *params, int32_t prec, me_handle *out);
+
+/* |M|^2 (Eq. 4 without the flux and phase space) for n points.
+ * momenta: device, n_ext * 4 * n doubles, layout above.  out: device, n
+ * doubles.  Asynchronous on stream; n = 0 is a no-op. */
+me_status me_eval(me_handle h, const double *momenta, int64_t n, double *out, void *stream);
+
+/* Phase-space points only: for events counter_offset .. counter_offset+n-1,
+ * draw with Philox4x64-10 (counter = (event, attempt, block, 0), key =
+ * (seed, 0)) until the cuts pass.  Outputs (device, any may be NULL):
+ * momenta (n_ext * 4 * n, layout above), weight (n: phase-space weight),
+ * shat (n), tries (n: draws used).  Asynchronous on stream.  A point that
+ * exhausts kin->max_attempts is reported by the next synchronising call on
+ * the handle as ME_ERR_TIMEOUT. */
+me_status me_generate(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n, const me_kin *kin,
+                      double *momenta, double *weight, double *shat, int32_t *tries, void *stream);
+
+/* One Monte Carlo step over n_accept accepted points (events
+ * counter_offset .. counter_offset+n_accept-1): generate, cut, evaluate,
+ * weight w = W_PS |M|^2 s_ident / (2 s-hat) * 0.3893793721e9 pb GeV^2, and add
+ * (sum w, sum w^2, n_acc, n_try) to *acc (host).  The sums are reduced
+ * deterministically.  Optional device outputs (NULL to skip): me2_out (n_accept
+ * doubles), momenta_out (layout above).  Synchronises stream before
+ * returning.  Errors: ME_ERR_TIMEOUT if a point exhausted its redraws. */
+me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept, const me_kin *kin,
+                    void *stream, me_xsec_acc *acc, double *me2_out, double *momenta_out);
+
+/* sigma-hat = sum_w / n_try and its standard error (pb) from an accumulator. */
+me_status me_xsec_estimate(const me_xsec_acc *acc, double *sigma, double *error);
+
+me_status me_info(me_handle h, me_info_t *info);
+
+/* Number of processes compiled into the library and their names. */
+int32_t me_n_processes(void);
+const char *me_process_name(int32_t i);
+
+void me_destroy(me_handle h);
+const char *me_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ME_H_ */

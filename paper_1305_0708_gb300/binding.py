@@ -1,0 +1,181 @@
+"""Thin ctypes binding of the C ABI (include/me.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device buffers
+may be given as torch CUDA tensors (their data pointer is passed) or raw
+integer addresses; streams as torch.cuda.Stream, a raw handle or None.
+Nothing here computes: every step runs in the library's kernels.  If the
+library is missing the import fails loudly; there is no fallback.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+_LIB = None
+
+
+class MeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"me status {status}: {msg}")
+        self.status = status
+
+
+class me_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("alpha", "sw2", "mZ", "wZ", "mW", "wW", "alpha_s", "mt", "wt", "mH", "wH")]
+
+
+class me_kin(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("max_attempts", ctypes.c_int32), ("sqrt_s", ctypes.c_double),
+                ("sqrt_s_min", ctypes.c_double), ("sqrt_s_max", ctypes.c_double), ("mass", ctypes.c_double * 16),
+                ("n_cut_legs", ctypes.c_int32), ("cut_legs", ctypes.c_int32 * 8), ("pt_min", ctypes.c_double),
+                ("eta_max", ctypes.c_double), ("dr_min", ctypes.c_double), ("s_ident", ctypes.c_double)]
+
+
+class me_xsec_acc(ctypes.Structure):
+    _fields_ = [("sum_w", ctypes.c_double), ("sum_w2", ctypes.c_double), ("n_acc", ctypes.c_int64),
+                ("n_try", ctypes.c_int64)]
+
+
+class me_info_t(ctypes.Structure):
+    _fields_ = [("n_ext", ctypes.c_int32), ("n_hel", ctypes.c_int32), ("n_hel_live", ctypes.c_int32),
+                ("n_colour", ctypes.c_int32), ("n_diagrams", ctypes.c_int32), ("pdg", ctypes.c_int32 * 16),
+                ("flops_amp", ctypes.c_double), ("flops_fp64", ctypes.c_double)]
+
+
+ME_FP64, ME_MIXED = 0, 1
+ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR = 0, 1, 2
+
+EXPORTS = ["me_create", "me_eval", "me_generate", "xsec_step", "me_xsec_estimate", "me_info", "me_n_processes",
+           "me_process_name", "me_destroy", "me_last_error"]
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load libme.so (built by build.build()); raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libme.so not built at {path}: run paper_1305_0708_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i64, u64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32
+    L.me_create.argtypes = [ctypes.c_char_p, ctypes.POINTER(me_params), i32, ctypes.POINTER(vp)]
+    L.me_eval.argtypes = [vp, vp, i64, vp, vp]
+    L.me_generate.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, vp, vp, vp, vp]
+    L.xsec_step.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc), vp, vp]
+    L.me_xsec_estimate.argtypes = [ctypes.POINTER(me_xsec_acc), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]
+    L.me_info.argtypes = [vp, ctypes.POINTER(me_info_t)]
+    L.me_n_processes.restype = i32
+    L.me_process_name.argtypes = [i32]
+    L.me_process_name.restype = ctypes.c_char_p
+    L.me_destroy.argtypes = [vp]
+    L.me_destroy.restype = None
+    L.me_last_error.restype = ctypes.c_char_p
+    for fn in ("me_create", "me_eval", "me_generate", "xsec_step", "me_xsec_estimate", "me_info"):
+        getattr(L, fn).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def _check(st):
+    if st != 0:
+        raise MeError(st, _LIB.me_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_params(**kw):
+    p = me_params(alpha=1 / 128, sw2=0.2312, mZ=91.1876, wZ=2.4952, mW=80.4, wW=2.085, alpha_s=0.118, mt=175.0,
+                  wt=1.5, mH=125.0, wH=0.0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def make_kin(kind, sqrt_s=0.0, sqrt_s_range=(0.0, 0.0), masses=(), cut_legs=(), pt_min=0.0, eta_max=0.0,
+             dr_min=0.0, s_ident=1.0, max_attempts=0):
+    k = me_kin()
+    k.kind = kind
+    k.max_attempts = max_attempts
+    k.sqrt_s = sqrt_s
+    k.sqrt_s_min, k.sqrt_s_max = sqrt_s_range
+    for i, m in enumerate(masses):
+        k.mass[i] = m
+    k.n_cut_legs = len(cut_legs)
+    for i, l in enumerate(cut_legs):
+        k.cut_legs[i] = l
+    k.pt_min, k.eta_max, k.dr_min, k.s_ident = pt_min, eta_max, dr_min, s_ident
+    return k
+
+
+def me_create(process, params=None, prec=ME_FP64):
+    L = load()
+    h = ctypes.c_void_p()
+    _check(L.me_create(process.encode(), ctypes.byref(params) if params is not None else None, prec,
+                       ctypes.byref(h)))
+    return h.value
+
+
+def me_eval(h, momenta, n, out, stream=None):
+    _check(load().me_eval(h, _ptr(momenta), n, _ptr(out), _stream(stream)))
+
+
+def me_generate(h, seed, counter_offset, n, kin, momenta=None, weight=None, shat=None, tries=None, stream=None):
+    _check(load().me_generate(h, seed, counter_offset, n, ctypes.byref(kin), _ptr(momenta), _ptr(weight),
+                              _ptr(shat), _ptr(tries), _stream(stream)))
+
+
+def xsec_step(h, seed, counter_offset, n_accept, kin, stream=None, acc=None, me2_out=None, momenta_out=None):
+    acc = acc if acc is not None else me_xsec_acc()
+    _check(load().xsec_step(h, seed, counter_offset, n_accept, ctypes.byref(kin), _stream(stream),
+                            ctypes.byref(acc), _ptr(me2_out), _ptr(momenta_out)))
+    return acc
+
+
+def me_xsec_estimate(acc):
+    s, e = ctypes.c_double(), ctypes.c_double()
+    _check(load().me_xsec_estimate(ctypes.byref(acc), ctypes.byref(s), ctypes.byref(e)))
+    return s.value, e.value
+
+
+def me_info(h):
+    info = me_info_t()
+    _check(load().me_info(h, ctypes.byref(info)))
+    return info
+
+
+def me_n_processes():
+    return load().me_n_processes()
+
+
+def me_process_name(i):
+    r = load().me_process_name(i)
+    return r.decode() if r else None
+
+
+def me_destroy(h):
+    load().me_destroy(h)
+
+
+def me_last_error():
+    return load().me_last_error().decode()

@@ -1,0 +1,167 @@
+"""Build the sm_103a matrix-element library in-tree.
+
+Steps: run the process compiler on every process of PROCESSES, write one
+CUDA unit per process plus the registry, compile all units in parallel with
+nvcc for sm_103a, and link libme.so under paper_1305_0708_gb300/_build/.
+Rebuilds only what changed (content hashes).
+"""
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+GEN = os.path.join(BUILD, "gen")
+LIB = os.path.join(BUILD, "libme.so")
+
+# (canonical name, aliases)
+PROCESSES = [
+    ("u u~ > e+ e-", []),
+    ("u d~ > e+ ve g g", []),
+    ("g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))", ["g g > t t~ > b e+ ve b~ e- ve~"]),
+    ("u s > d c h h", []),
+    ("u d~ > e+ ve", []),
+    ("u u~ > g g", []),
+    ("g g > g g", []),
+]
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+                     "-I", INCLUDE, "-I", CSRC]
+STATIC_SOURCES = ["me_runtime.cu"]
+
+
+def nvcc():
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def _hash(*parts):
+    h = hashlib.sha256()
+    for p in parts:
+        h.update(p.encode() if isinstance(p, str) else p)
+    return h.hexdigest()[:16]
+
+
+def generate_units():
+    """Run the process compiler; returns [(tag, path, meta)]."""
+    sys.path.insert(0, ROOT)
+    from paper_1305_0708_gb300.compiler.program import compile_process
+    from paper_1305_0708_gb300.compiler.codegen import generate_source, process_symbol
+    from paper_1305_0708_gb300.compiler.model import PARTICLES
+    os.makedirs(GEN, exist_ok=True)
+    units = []
+    for name, aliases in PROCESSES:
+        tag = process_symbol(name)
+        prog = compile_process(name)
+        src, info = generate_source(prog, tag)
+        path = os.path.join(GEN, tag + ".cu")
+        if not os.path.exists(path) or open(path).read() != src:
+            with open(path, "w") as f:
+                f.write(src)
+        ncomb = 1
+        for l in prog.legs:
+            ncomb *= len(l.hels)
+        meta = dict(name=name, aliases=aliases, tag=tag, n_ext=prog.n_ext, params=info["params"],
+                    n_hel=ncomb, n_hel_live=len(prog.live), n_colour=prog.n_colour, n_diagrams=len(prog.amps),
+                    flops_amp=info["flops_amp"], flops_fp64=info["flops_fp64"],
+                    pdg=[PARTICLES[l.particle].pdg for l in prog.legs])
+        units.append((tag, path, meta))
+    # registry
+    lines = ['#include "me_internal.h"', "namespace me {"]
+    entries = []
+    for tag, _, m in units:
+        lines.append(f'extern "C" void me_register_{tag}(ProcessDesc* d);')
+    for tag, _, m in units:
+        pn = ", ".join(f'"{p}"' for p in m["params"]) or '"ZERO"'
+        lines.append(f"static const char* const params_{tag}[] = {{{pn}}};")
+        lines.append(f"static const int pdg_{tag}[] = {{{', '.join(str(x) for x in m['pdg'])}}};")
+        for nm in [m["name"]] + m["aliases"]:
+            entries.append((tag, nm, m))
+    lines.append(f"static ProcessDesc table[{len(entries)}];")
+    lines.append("static bool ready = false;")
+    lines.append("static void init() {")
+    for i, (tag, nm, m) in enumerate(entries):
+        np_ = max(len(m["params"]), 1)
+        lines.append(f'  table[{i}].name = "{nm}"; table[{i}].n_params = {np_}; table[{i}].param_names = params_{tag};')
+        lines.append(f"  table[{i}].n_hel = {m['n_hel']}; table[{i}].n_hel_live = {m['n_hel_live']}; "
+                     f"table[{i}].n_colour = {m['n_colour']}; table[{i}].n_diagrams = {m['n_diagrams']};")
+        lines.append(f"  table[{i}].flops_amp = {float(m['flops_amp'])!r}; table[{i}].flops_fp64 = {float(m['flops_fp64'])!r}; "
+                     f"table[{i}].pdg = pdg_{tag};")
+        lines.append(f"  me_register_{tag}(&table[{i}]);")
+    lines.append("  ready = true;")
+    lines.append("}")
+    lines.append(f"int registry_size() {{ return {len(entries)}; }}")
+    lines.append("ProcessDesc* registry_entry(int i) { if (!ready) init(); return &table[i]; }")
+    lines.append("}  // namespace me")
+    reg = "\n".join(lines) + "\n"
+    rpath = os.path.join(GEN, "registry.cu")
+    if not os.path.exists(rpath) or open(rpath).read() != reg:
+        with open(rpath, "w") as f:
+            f.write(reg)
+    with open(os.path.join(BUILD, "processes.json"), "w") as f:
+        json.dump([m for _, _, m in units], f, indent=1)
+    return units, rpath
+
+
+def _headers_hash():
+    parts = []
+    for d in (CSRC, INCLUDE):
+        for fn in sorted(os.listdir(d)):
+            if fn.endswith((".cuh", ".h")):
+                parts.append(open(os.path.join(d, fn), "rb").read())
+    return _hash(*parts)
+
+
+def _compile(src, obj, hh, verbose):
+    stamp = obj + ".hash"
+    h = _hash(open(src, "rb").read(), hh, " ".join(NVCC_FLAGS))
+    if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == h:
+        return obj, False
+    cmd = [nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj]
+    if verbose:
+        print(" ".join(cmd), flush=True)
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr[-6000:]}")
+    with open(stamp, "w") as f:
+        f.write(h)
+    return obj, True
+
+
+def build(verbose=False, jobs=None):
+    """Generate, compile and link; returns the path of libme.so."""
+    units, rpath = generate_units()
+    os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
+    hh = _headers_hash()
+    srcs = [os.path.join(CSRC, s) for s in STATIC_SOURCES] + [p for _, p, _ in units] + [rpath]
+    objs = []
+    jobs = jobs or min(len(srcs), os.cpu_count() or 4)
+    changed = False
+    with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+        futs = [ex.submit(_compile, s, os.path.join(BUILD, "obj", os.path.basename(s) + ".o"), hh, verbose)
+                for s in srcs]
+        for f in futs:
+            o, ch = f.result()
+            objs.append(o)
+            changed |= ch
+    if changed or not os.path.exists(LIB):
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
+        os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv))

@@ -1,0 +1,394 @@
+"""CUDA code generation for a compiled Program (the MG2CUDA role, Sect. 5).
+
+For each process the generator writes one translation unit holding a
+straight-line per-event evaluator templated on the amplitude precision R
+(double: FP64 path; float: mixed path) and the launch wrappers the runtime
+dispatches to.  Per event it emits, in order:
+
+  1. the momenta (FP64) read from structure-of-arrays memory,
+  2. every internal line's momentum and propagator denominator, once per
+     event (FP64; the mixed path converts the reciprocal to complex FP32),
+  3. the external wavefunctions for every helicity some live amplitude needs,
+  4. every sub-current variant once (helicity recycling: shared by all
+     diagrams and helicities that use it),
+  5. the diagram amplitudes accumulated into colour components
+     J_h,k = sum_d c_dk A_d (exact coefficients folded into literals),
+  6. the colour sum |M_h|^2 = (J^T C J)/den with the integer matrix in the
+     code, the helicity sum and the initial-state average.
+
+Processes with a large colour dimension hand J to the tensor-core colour
+kernel instead (colour_gemm.cuh).
+"""
+from fractions import Fraction
+
+from .model import PARTICLES, couplings
+from .program import _is_column, _PAIRINGS
+
+
+def _hname(h):
+    return {-1: "m", 0: "z", 1: "p"}[h]
+
+
+def _vname(nid, var):
+    return f"w{nid}_" + "".join(_hname(h) for h in var) if var else f"w{nid}"
+
+
+def _ident(name):
+    """C identifier for a coupling name (e.g. GA_e- -> GA_em)."""
+    return name.replace("-", "m").replace("+", "p").replace("~", "x")
+
+
+def _lit(x):
+    """A floating literal typed as R."""
+    v = float(x)
+    return f"R({v!r})"
+
+
+class _Emitter:
+    def __init__(self, prog, tag):
+        self.p = prog
+        self.tag = tag
+        self.lines = []
+        self.flops32 = 0      # amplitude-precision flops per event
+        self.flops64 = 0      # FP64 flops per event (momenta, invariants)
+        self.cpl_names = set()
+
+    def emit(self, s):
+        self.lines.append(s)
+
+    def cpl(self, name):
+        self.cpl_names.add(name)
+        return f"c_{_ident(name)}"
+
+    # ------------------------------------------------------------------
+    def generate(self):
+        p = self.p
+        n = p.n_ext
+        E = self.emit
+        nodes = p.nodes
+        E("  // momenta, FP64")
+        for k in range(n):
+            E(f"  const double* p{k} = pm[{k}];")
+        used_nodes = sorted(p.node_variants)
+        E("  // external momenta in amplitude precision: r = physical, k = flowing into the vertex")
+        for nid in used_nodes:
+            nd = nodes[nid]
+            if nd.external:
+                k = nd.leg
+                E(f"  const me::P4<R> r{nid} = me::p4<R>(p{k});")
+                if p.legs[k].incoming:
+                    E(f"  const me::P4<R> k{nid} = r{nid};")
+                else:
+                    E(f"  const me::P4<R> k{nid} = me::neg(r{nid});")
+        E("  // internal lines: momentum (into the parent vertex) and reciprocal propagator denominator.")
+        E("  // Massive (resonant) lines form q^2 - m^2 in FP64 from the FP64 momenta; massless lines")
+        E("  // use the amplitude precision.")
+        for nid in used_nodes:
+            nd = nodes[nid]
+            if nd.external:
+                continue
+            kids = nd.children
+            E(f"  const me::P4<R> k{nid} = " + " + ".join(f"k{c}" for c in kids) + ";")
+            self.flops32 += 4 * (len(kids) - 1)
+            part = PARTICLES[nd.ptype]
+            if part.massless:
+                E(f"  const me::cx<R> inv{nid} = me::mk(R(1) / me::msq(k{nid}), R(0));")
+                self.flops32 += 8
+            else:
+                m = self.cpl(part.mass)
+                w = self.cpl(part.width) if part.width != "0" else None
+                legs = sorted(nd.legs)
+                terms = []
+                for l in legs:
+                    sgn = "+" if p.legs[l].incoming else "-"
+                    terms.append((sgn, l))
+                comps = []
+                for mu in range(4):
+                    e = ""
+                    for j, (sgn, l) in enumerate(terms):
+                        if j == 0:
+                            e += ("" if sgn == "+" else "-") + f"p{l}[{mu}]"
+                        else:
+                            e += f" {sgn} p{l}[{mu}]"
+                    comps.append(e)
+                E(f"  const double Q{nid}[4] = {{{', '.join(comps)}}};")
+                E(f"  const double q2_{nid} = Q{nid}[0] * Q{nid}[0] - Q{nid}[1] * Q{nid}[1] - Q{nid}[2] * Q{nid}[2] - "
+                  f"Q{nid}[3] * Q{nid}[3];")
+                wexpr = f"{m} * {w}" if w else "0.0"
+                E(f"  const me::cx<R> inv{nid} = inv_den<R>(q2_{nid} - {m} * {m}, {wexpr});")
+                self.flops64 += 4 * (len(legs) - 1) + 7 + 3
+        # root external node (last leg) appears only as an amplitude child
+        E("  // wavefunctions and sub-currents, once per helicity variant")
+        for nid in used_nodes:
+            nd = nodes[nid]
+            for var in p.node_variants[nid]:
+                self.node_code(nid, var)
+        # amplitudes
+        K = p.n_colour
+        E("  // diagram amplitudes into colour components")
+        for hi, terms in enumerate(p.amp_terms):
+            for k in range(K):
+                E(f"  me::cx<R> J{hi}_{k} = me::mk(R(0), R(0));")
+            for aid, chvars in terms:
+                self.amp_code(aid, chvars, hi)
+        # colour sum
+        E("  // colour sum (J^T C J)/den per helicity, helicity sum, average")
+        E("  double tot = 0.0;")
+        C = p.cmat_num
+        for hi in range(len(p.amp_terms)):
+            E("  {")
+            E("    R s = R(0);")
+            for k in range(K):
+                if C[k][k]:
+                    E(f"    s += {_lit(C[k][k])} * me::abs2(J{hi}_{k});")
+                    self.flops32 += 4
+                for l in range(k + 1, K):
+                    if C[k][l]:
+                        E(f"    s += {_lit(2 * C[k][l])} * (J{hi}_{k}.re * J{hi}_{l}.re + J{hi}_{k}.im * J{hi}_{l}.im);")
+                        self.flops32 += 5
+            E("    tot += (double)s;")
+            E("  }")
+        E(f"  return tot * {float(p.average / p.cmat_den)!r};")
+
+    # ------------------------------------------------------------------
+    def child_vars(self, nid, var, child):
+        nd = self.p.nodes[nid]
+        legs = sorted(nd.legs)
+        hmap = dict(zip(legs, var))
+        cl = sorted(self.p.nodes[child].legs)
+        return tuple(hmap[l] for l in cl)
+
+    def ext_code(self, nid, var):
+        p = self.p
+        nd = p.nodes[nid]
+        leg = p.legs[nd.leg]
+        part = PARTICLES[leg.particle]
+        h = var[0]
+        name = _vname(nid, var)
+        inc = "true" if leg.incoming else "false"
+        if part.is_fermion:
+            if not part.massless:
+                raise NotImplementedError("massive external fermions")
+            if _is_column(nd.ptype):
+                self.emit(f"  const me::W4<R> {name} = me::ext_column_massless<R>(r{nid}, {h}, {inc});")
+            else:
+                self.emit(f"  const me::W4<R> {name} = me::ext_row_massless<R>(r{nid}, {h}, {inc});")
+            self.flops32 += 12
+        elif part.is_vector:
+            mass = "R(0)" if part.massless else f"(R){self.cpl(part.mass)}"
+            self.emit(f"  const me::W4<R> {name} = me::ext_vector<R>(r{nid}, {h}, {inc}, {mass});")
+            self.flops32 += 25
+        else:
+            self.emit(f"  const me::cx<R> {name} = me::mk(R(1), R(0));")
+
+    def node_code(self, nid, var):
+        p = self.p
+        nd = p.nodes[nid]
+        if nd.external:
+            self.ext_code(nid, var)
+            return
+        v = nd.vertex
+        kids = [(c, s, _vname(c, self.child_vars(nid, var, c))) for c, s in zip(nd.children, nd.slots)]
+        name = _vname(nid, var)
+        part = PARTICLES[nd.ptype]
+        E = self.emit
+        if v.kind == "FFV":
+            gl, gr = v.couplings
+            has_l, has_r = gl != "ZERO", gr != "ZERO"
+            gls = self.cpl(gl) if has_l else "0.0"
+            grs = self.cpl(gr) if has_r else "0.0"
+            nch = int(has_l) + int(has_r)
+            cargs = f"(R){gls}, (R){grs}, {str(has_l).lower()}, {str(has_r).lower()}"
+            if part.is_fermion:
+                fk = [k for k in kids if k[1] in (0, 1)][0]
+                vk = [k for k in kids if k[1] == 2][0]
+                m = "R(0)" if part.massless else f"(R){self.cpl(part.mass)}"
+                if _is_column(nd.ptype):
+                    E(f"  const me::W4<R> {name} = me::prop_col<R>(me::ffv_col<R>({fk[2]}, {vk[2]}, {cargs}), "
+                      f"k{nid}, {m}, inv{nid});")
+                else:
+                    E(f"  const me::W4<R> {name} = me::prop_row<R>(me::ffv_row<R>({fk[2]}, {vk[2]}, {cargs}), "
+                      f"me::neg(k{nid}), {m}, inv{nid});")
+                self.flops32 += 40 * nch + (64 if not part.massless else 48)
+            else:
+                rk = [k for k in kids if k[1] == 0][0]
+                ck = [k for k in kids if k[1] == 1][0]
+                massive = not part.massless and nid not in p.conserved
+                mc2 = f"inv_mc2_{part.mass}" if massive else "me::mk(R(0), R(0))"
+                if massive:
+                    self.cpl(part.mass)
+                    self.cpl(part.width)
+                E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::ffv_current<R>({rk[2]}, {ck[2]}, {cargs}), "
+                  f"k{nid}, inv{nid}, {str(massive).lower()}, {mc2});")
+                self.flops32 += 48 * nch + (60 if massive else 24)
+        elif v.kind == "VVV":
+            g = self.cpl(v.couplings[0])
+            a, b = kids
+            E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::vvv_current<R>({a[2]}, k{a[0]}, {b[2]}, k{b[0]}, "
+              f"(R){g}), k{nid}, inv{nid}, false, me::mk(R(0), R(0)));")
+            self.flops32 += 150 + 24
+        elif v.kind == "VVVV":
+            g = self.cpl(v.couplings[0])
+            slot = {s: nm for _, s, nm in kids}
+            o = nd.out_slot
+            (x, y), (z, w) = _PAIRINGS[nd.struct]
+            # L = g_xz g_yw - g_xw g_yz; current for the open slot o
+            t1 = self._v4_term(o, [(x, z), (y, w)], slot)
+            t2 = self._v4_term(o, [(x, w), (y, z)], slot)
+            E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::w4_sub<R>({t1}, {t2}, (R){g}), k{nid}, inv{nid}, "
+              f"false, me::mk(R(0), R(0)));")
+            self.flops32 += 2 * 54 + 16 + 24
+        elif v.kind in ("VVS", "VVSS"):
+            g = self.cpl(v.couplings[0])
+            vs = [k for k in kids if PARTICLES[v.fields[k[1]]].is_vector]
+            ss = [k for k in kids if PARTICLES[v.fields[k[1]]].is_scalar]
+            sprod = " * ".join(k[2] for k in ss) if ss else None
+            if part.is_vector:
+                s_expr = f"((R){g} * ({sprod}))"
+                massive = not part.massless
+                mc2 = f"inv_mc2_{part.mass}" if massive else "me::mk(R(0), R(0))"
+                if massive:
+                    self.cpl(part.mass)
+                    self.cpl(part.width)
+                E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::w4_scale<R>({vs[0][2]}, {s_expr}), k{nid}, "
+                  f"inv{nid}, {str(massive).lower()}, {mc2});")
+                self.flops32 += 24 + 60 + 6 * len(ss)
+            else:
+                d = f"me::mdot<R>({vs[0][2]}, {vs[1][2]})"
+                extra = f" * {sprod}" if sprod else ""
+                E(f"  const me::cx<R> {name} = ((R){g} * {d}){extra} * inv{nid};")
+                self.flops32 += 30 + 12 + 6 * len(ss)
+        elif v.kind == "SSS":
+            g = self.cpl(v.couplings[0])
+            a, b = kids
+            E(f"  const me::cx<R> {name} = ((R){g} * ({a[2]} * {b[2]})) * inv{nid};")
+            self.flops32 += 14
+        else:
+            raise NotImplementedError(v.kind)
+
+    def _v4_term(self, o, pairs, slot):
+        """Current of sum over pairs structure g_{ab} g_{cd} with slot o open."""
+        (a, b), (c, d) = pairs
+        if o in (a, b):
+            partner = b if o == a else a
+            return f"me::v4_term<R>({slot[partner]}, {slot[c]}, {slot[d]})"
+        partner = d if o == c else c
+        return f"me::v4_term<R>({slot[partner]}, {slot[a]}, {slot[b]})"
+
+    def amp_code(self, aid, chvars, hi):
+        p = self.p
+        a = p.amps[aid]
+        v = a.vertex
+        kids = [(c, s, _vname(c, cv)) for c, s, cv in zip(a.children, a.slots, chvars)]
+        slot = {s: nm for _, s, nm in kids}
+        E = self.emit
+        if v.kind == "FFV":
+            gl, gr = v.couplings
+            has_l, has_r = gl != "ZERO", gr != "ZERO"
+            gls = self.cpl(gl) if has_l else "0.0"
+            grs = self.cpl(gr) if has_r else "0.0"
+            expr = (f"me::ffv_amp<R>({slot[0]}, {slot[1]}, {slot[2]}, (R){gls}, (R){grs}, "
+                    f"{str(has_l).lower()}, {str(has_r).lower()})")
+            self.flops32 += 40 * (int(has_l) + int(has_r)) + 30
+        elif v.kind == "VVV":
+            g = self.cpl(v.couplings[0])
+            k0 = [c for c, s, _ in kids if s == 0][0]
+            k1 = [c for c, s, _ in kids if s == 1][0]
+            expr = f"me::vvv_amp<R>({slot[0]}, k{k0}, {slot[1]}, k{k1}, {slot[2]}, (R){g})"
+            self.flops32 += 150 + 30
+        elif v.kind == "VVVV":
+            g = self.cpl(v.couplings[0])
+            (x, y), (z, w) = _PAIRINGS[a.struct]
+            expr = (f"(R){g} * (me::mdot<R>({slot[x]}, {slot[z]}) * me::mdot<R>({slot[y]}, {slot[w]}) - "
+                    f"me::mdot<R>({slot[x]}, {slot[w]}) * me::mdot<R>({slot[y]}, {slot[z]}))")
+            self.flops32 += 4 * 30 + 16
+        elif v.kind in ("VVS", "VVSS"):
+            g = self.cpl(v.couplings[0])
+            vs = [nm for _, s, nm in kids if PARTICLES[v.fields[s]].is_vector]
+            ss = [nm for _, s, nm in kids if PARTICLES[v.fields[s]].is_scalar]
+            expr = f"((R){g} * me::mdot<R>({vs[0]}, {vs[1]}))" + "".join(f" * {s}" for s in ss)
+            self.flops32 += 32 + 6 * len(ss)
+        elif v.kind == "SSS":
+            g = self.cpl(v.couplings[0])
+            expr = f"((R){g} * ({slot[0]} * {slot[1]} * {slot[2]}))"
+            self.flops32 += 14
+        else:
+            raise NotImplementedError(v.kind)
+        E(f"  {{ const me::cx<R> a = {expr};")
+        for k in range(p.n_colour):
+            c = p.coeffs.get((aid, k))
+            if c is None or c.is_zero():
+                continue
+            cr, ci = float(c.re), float(c.im)
+            if ci == 0:
+                E(f"    J{hi}_{k}.re += {_lit(cr)} * a.re; J{hi}_{k}.im += {_lit(cr)} * a.im;")
+                self.flops32 += 4
+            elif cr == 0:
+                E(f"    J{hi}_{k}.re -= {_lit(ci)} * a.im; J{hi}_{k}.im += {_lit(ci)} * a.re;")
+                self.flops32 += 4
+            else:
+                E(f"    J{hi}_{k} = J{hi}_{k} + me::mk({_lit(cr)} * a.re - {_lit(ci)} * a.im, "
+                  f"{_lit(cr)} * a.im + {_lit(ci)} * a.re);")
+                self.flops32 += 8
+        E("  }")
+
+
+def process_symbol(name):
+    out = []
+    for ch in name:
+        out.append(ch if ch.isalnum() else "_")
+    return "p_" + "".join(out).strip("_")
+
+
+def generate_source(prog, tag):
+    """CUDA source for one process: evaluator template + the two launch wrappers."""
+    em = _Emitter(prog, tag)
+    em.generate()
+    body = "\n".join(em.lines)
+    cpl = sorted(em.cpl_names)
+    masses_for_mc2 = sorted({n for n in cpl if n.startswith("M")})
+    params = "\n".join(f"  double {_ident(n)};" for n in cpl) or "  double unused;"
+    unpack = "\n".join(f"  const double c_{_ident(n)} = prm.{_ident(n)};" for n in cpl)
+    mc2 = []
+    for mname in masses_for_mc2:
+        wname = "W" + mname[1:]
+        if wname in cpl:
+            mc2.append(f"  const me::cx<R> inv_mc2_{mname} = inv_den<R>(c_{mname} * c_{mname}, -c_{mname} * c_{wname});")
+    mc2 = "\n".join(mc2)
+    src = f"""// Generated by paper_1305_0708_gb300.compiler for: {prog.name}
+// diagrams: {len(prog.amps)}, live helicities: {len(prog.live)} of {_ncomb(prog)}, colour basis: {prog.n_colour}
+#include "process_common.cuh"
+
+namespace me {{
+namespace {tag} {{
+
+struct Params {{
+{params}
+}};
+
+template <class R>
+__host__ __device__ __forceinline__ double eval_event(const double (&pm)[{prog.n_ext}][4], const Params& prm) {{
+{unpack}
+{mc2}
+{body}
+}}
+
+}}  // namespace {tag}
+}}  // namespace me
+
+ME_DEFINE_PROCESS({tag}, {prog.n_ext}, {len(cpl) if cpl else 1})
+"""
+    info = {"flops_amp": em.flops32, "flops_fp64": em.flops64, "params": cpl}
+    return src, info
+
+
+def _ncomb(prog):
+    n = 1
+    for l in prog.legs:
+        n *= len(l.hels)
+    return n
+
+
+def param_values(info, par):
+    c = couplings(par)
+    return [c[n] for n in info["params"]]

@@ -1,0 +1,149 @@
+"""Standard Model particle and vertex table for the process compiler.
+
+The vertex set is the one the paper's HEGET functions cover (Sect. 4.2,
+Table 2): FFV, VVV, VVVV, VVS, VVSS, SSS (FFS is not needed for massless
+light quarks and is left out).  Conventions: every vertex lists the fields
+it annihilates, i.e. all particles incoming.  Couplings follow the textbook
+Lagrangian with D_mu = d_mu - i g_s t^a G^a_mu - i g W^a T^a - i g' Y B_mu
+(the paper's Eqs. 22-40 up to the sign convention of g_s, which drops out
+of |M|^2):
+
+  f~ f V    i gamma^mu (gL P_L + gR P_R)         photon: gL = gR = e Q
+                                                 Z: gL = gZ (T3 - Q sw^2), gR = -gZ Q sw^2
+                                                 W: gL = g / sqrt2, gR = 0
+                                                 gluon: gL = gR = g_s, colour t^a
+  g g g     g_s f^{abc} [g^{mn}(k1-k2)^r + cyclic]   (all momenta incoming)
+  g g g g   -i g_s^2 f^{XYe} f^{ZWe} (g_XZ g_YW - g_XW g_YZ) for the three pairings
+  W+ W- h   i g mW g^{mn}        Z Z h  i gZ mZ g^{mn}
+  W+ W- h h i g^2/2 g^{mn}       Z Z h h i gZ^2/2 g^{mn}
+  h h h     -i 3 mH^2 / v
+"""
+import math
+from dataclasses import dataclass, field
+
+
+@dataclass(frozen=True)
+class Particle:
+    name: str
+    anti: str
+    spin: int          # 0, 1 (fermion) or 2 (vector): twice the spin
+    colour: int        # 1, 3 (quark), -3 (antiquark) or 8
+    mass: str          # parameter name or "0"
+    width: str         # parameter name or "0"
+    charge3: int       # 3 x electric charge
+    pdg: int
+
+    @property
+    def is_fermion(self):
+        return self.spin == 1
+
+    @property
+    def is_vector(self):
+        return self.spin == 2
+
+    @property
+    def is_scalar(self):
+        return self.spin == 0
+
+    @property
+    def massless(self):
+        return self.mass == "0"
+
+
+def _fermion(name, anti, colour, mass, width, charge3, pdg):
+    return [Particle(name, anti, 1, colour, mass, width, charge3, pdg),
+            Particle(anti, name, 1, -colour if colour == 3 else colour, mass, width, -charge3, -pdg)]
+
+
+PARTICLES = {}
+for p in (
+    _fermion("u", "u~", 3, "0", "0", 2, 2) + _fermion("d", "d~", 3, "0", "0", -1, 1)
+    + _fermion("c", "c~", 3, "0", "0", 2, 4) + _fermion("s", "s~", 3, "0", "0", -1, 3)
+    + _fermion("b", "b~", 3, "0", "0", -1, 5) + _fermion("t", "t~", 3, "MT", "WT", 2, 6)
+    + _fermion("e-", "e+", 1, "0", "0", -3, 11) + _fermion("ve", "ve~", 1, "0", "0", 0, 12)
+    + _fermion("mu-", "mu+", 1, "0", "0", -3, 13) + _fermion("vm", "vm~", 1, "0", "0", 0, 14)
+    + [Particle("g", "g", 2, 8, "0", "0", 0, 21), Particle("a", "a", 2, 1, "0", "0", 0, 22),
+       Particle("z", "z", 2, 1, "MZ", "WZ", 0, 23),
+       Particle("w+", "w-", 2, 1, "MW", "WW", 3, 24), Particle("w-", "w+", 2, 1, "MW", "WW", -3, -24),
+       Particle("h", "h", 0, 1, "MH", "WH", 0, 25)]
+):
+    PARTICLES[p.name] = p
+
+ALIASES = {"e+": "e+", "e-": "e-", "ve": "ve", "ve~": "ve~", "H": "h", "W+": "w+", "W-": "w-", "Z": "z", "A": "a"}
+
+QUARK_T3 = {"u": 0.5, "c": 0.5, "t": 0.5, "d": -0.5, "s": -0.5, "b": -0.5, "e-": -0.5, "mu-": -0.5,
+            "ve": 0.5, "vm": 0.5}
+CHARGE = {"u": 2 / 3, "c": 2 / 3, "t": 2 / 3, "d": -1 / 3, "s": -1 / 3, "b": -1 / 3, "e-": -1.0, "mu-": -1.0,
+          "ve": 0.0, "vm": 0.0}
+WEAK_DOUBLETS = [("u", "d"), ("c", "s"), ("t", "b"), ("ve", "e-"), ("vm", "mu-")]
+
+
+@dataclass(frozen=True)
+class Vertex:
+    """A Feynman rule: incoming fields, Lorentz kind and coupling names.
+
+    kind: "FFV" (fields f~, f, V), "VVV", "VVVV", "VVS", "VVSS", "SSS".
+    couplings: names resolved by couplings() at me_create time; for FFV
+    (gL, gR).  colour: "delta" (f~ f), "T" (f~ f g), "f" (ggg), "ff" (gggg).
+    """
+    fields: tuple
+    kind: str
+    couplings: tuple
+    colour: str = "none"
+
+
+def _ffv_vertices():
+    out = []
+    coloured = {"u", "d", "c", "s", "b", "t"}
+    for f in ["u", "d", "c", "s", "b", "t", "e-", "mu-"]:
+        fb = PARTICLES[f].anti
+        col = "delta" if f in coloured else "none"
+        out.append(Vertex((fb, f, "a"), "FFV", (f"GA_{f}", f"GA_{f}"), col))
+        out.append(Vertex((fb, f, "z"), "FFV", (f"GZL_{f}", f"GZR_{f}"), col))
+        if f in coloured:
+            out.append(Vertex((fb, f, "g"), "FFV", ("GS", "GS"), "T"))
+    for f in ["ve", "vm"]:
+        out.append(Vertex((PARTICLES[f].anti, f, "z"), "FFV", (f"GZL_{f}", f"GZR_{f}"), "none"))
+    for up, dn in WEAK_DOUBLETS:
+        col = "delta" if up in {"u", "c", "t"} else "none"
+        # u~ d W+ and d~ u W- (all incoming)
+        out.append(Vertex((PARTICLES[up].anti, dn, "w+"), "FFV", ("GW", "ZERO"), col))
+        out.append(Vertex((PARTICLES[dn].anti, up, "w-"), "FFV", ("GW", "ZERO"), col))
+    return out
+
+
+VERTICES = _ffv_vertices() + [
+    Vertex(("g", "g", "g"), "VVV", ("GS",), "f"),
+    Vertex(("g", "g", "g", "g"), "VVVV", ("GS2",), "ff"),
+    Vertex(("w+", "w-", "h"), "VVS", ("GWWH",)),
+    Vertex(("z", "z", "h"), "VVS", ("GZZH",)),
+    Vertex(("w+", "w-", "h", "h"), "VVSS", ("GWWHH",)),
+    Vertex(("z", "z", "h", "h"), "VVSS", ("GZZHH",)),
+    Vertex(("h", "h", "h"), "SSS", ("GHHH",)),
+]
+
+
+DEFAULT_PARAMS = dict(alpha=1.0 / 128.0, sw2=0.2312, mZ=91.1876, wZ=2.4952, mW=80.4, wW=2.085,
+                      alpha_s=0.118, mt=175.0, wt=1.50, mH=125.0, wH=0.0)
+
+
+def couplings(par):
+    """Numerical couplings, masses and widths for a parameter dict (electroweak
+    scheme: e = sqrt(4 pi alpha), g = e/sw, gZ = e/(sw cw), v = 2 mW / g)."""
+    e = math.sqrt(4 * math.pi * par["alpha"])
+    sw = math.sqrt(par["sw2"])
+    cw = math.sqrt(1 - par["sw2"])
+    g = e / sw
+    gz = e / (sw * cw)
+    gs = math.sqrt(4 * math.pi * par["alpha_s"])
+    v = 2 * par["mW"] / g
+    c = {"ZERO": 0.0, "GS": gs, "GS2": gs * gs, "GW": g / math.sqrt(2),
+         "GWWH": g * par["mW"], "GZZH": gz * par["mZ"], "GWWHH": g * g / 2, "GZZHH": gz * gz / 2,
+         "GHHH": -3 * par["mH"] ** 2 / v,
+         "MT": par["mt"], "WT": par["wt"], "MZ": par["mZ"], "WZ": par["wZ"], "MW": par["mW"], "WW": par["wW"],
+         "MH": par["mH"], "WH": par["wH"], "0": 0.0}
+    for f, q in CHARGE.items():
+        c[f"GA_{f}"] = e * q
+        c[f"GZL_{f}"] = gz * (QUARK_T3[f] - q * par["sw2"])
+        c[f"GZR_{f}"] = gz * (-q * par["sw2"])
+    return c

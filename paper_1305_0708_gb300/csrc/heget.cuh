@@ -1,0 +1,337 @@
+// Device library of helicity wavefunctions and vertex functions (the role of
+// the paper's HEGET functions, Sect. 4 and App. C), written for sm_103a.
+//
+// Differences from the paper's layout: the four-momentum is not carried in
+// the wavefunction (the compiler keeps every line's momentum once per event,
+// in FP64, and passes it explicitly); every factor i of a vertex or
+// propagator is tracked by the compiler and folded into the colour
+// coefficients, so these functions compute real-coupling ("stripped")
+// expressions only; the propagator denominator arrives as a precomputed
+// complex reciprocal so that the mixed-precision path can form it in FP64.
+//
+// Conventions: metric (+,-,-,-); chiral basis, gamma^mu = [[0, s^mu],
+// [sb^mu, 0]] with s^mu = (1, sigma), sb^mu = (1, -sigma); P_L keeps the
+// upper two components.  Spinors: u(p,l), v(p,l) helicity spinors, rows
+// ubar = u^dagger gamma^0.  Vectors carry an upper index.
+//
+// All functions are templated on the real type R (double: FP64 path, float:
+// mixed path) and are __host__ __device__ so they compile for either side.
+#pragma once
+#include <cstdint>
+
+#define ME_HD __host__ __device__ __forceinline__
+
+namespace me {
+
+template <class R>
+struct cx {
+  R re, im;
+};
+
+template <class R> ME_HD cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <class R> ME_HD cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> ME_HD cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> ME_HD cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <class R> ME_HD cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R> ME_HD cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <class R> ME_HD cx<R> operator*(cx<R> a, R s) { return {s * a.re, s * a.im}; }
+template <class R> ME_HD cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
+template <class R> ME_HD cx<R> mul_i(cx<R> a) { return {-a.im, a.re}; }
+template <class R> ME_HD R abs2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+
+// four-component objects: spinor (column or row) or vector (upper index)
+template <class R>
+struct W4 {
+  cx<R> c[4];
+};
+
+template <class R>
+struct P4 {
+  R e, x, y, z;
+};
+
+template <class R> ME_HD P4<R> p4(const double* p) { return P4<R>{(R)p[0], (R)p[1], (R)p[2], (R)p[3]}; }
+template <class R> ME_HD P4<R> operator+(P4<R> a, P4<R> b) { return P4<R>{a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class R> ME_HD P4<R> neg(P4<R> k) { return P4<R>{-k.e, -k.x, -k.y, -k.z}; }
+template <class R> ME_HD R msq(P4<R> k) { return k.e * k.e - k.x * k.x - k.y * k.y - k.z * k.z; }
+
+// ---------------------------------------------------------------------------
+// external wavefunctions (massless fermions, massless/massive vectors, scalars)
+// ---------------------------------------------------------------------------
+// sqrt(E + pz) computed without cancellation for pz < 0; zero only for p along -z.
+template <class R> ME_HD R kplus(P4<R> p) {
+  return p.z >= R(0) ? p.e + p.z : (p.x * p.x + p.y * p.y) / (p.e - p.z);
+}
+
+// Column spinor of a massless fermion line entering its vertex:
+//   incoming fermion  -> u(p, hel)      outgoing antifermion -> v(p, hel)
+template <class R> ME_HD W4<R> ext_column_massless(P4<R> p, int hel, bool incoming) {
+  W4<R> w;
+  const R kp = kplus(p);
+  cx<R> a, b;  // (s, (px + i py)/s) = sqrt(2E) xi_+ ; ((-px + i py)/s, s) = sqrt(2E) xi_-
+  if (kp > R(0)) {
+    const R s = sqrt(kp), is = R(1) / s;
+    if ((incoming && hel < 0) || (!incoming && hel > 0)) {  // xi_- in the upper (left) slot
+      a = mk(-p.x * is, p.y * is);
+      b = mk(s, R(0));
+    } else {
+      a = mk(s, R(0));
+      b = mk(p.x * is, p.y * is);
+    }
+  } else {  // p along -z: xi_+ = (0, 1), xi_- = (-1, 0)
+    const R s = sqrt(R(2) * p.e);
+    if ((incoming && hel < 0) || (!incoming && hel > 0)) {
+      a = mk(-s, R(0));
+      b = mk(R(0), R(0));
+    } else {
+      a = mk(R(0), R(0));
+      b = mk(s, R(0));
+    }
+  }
+  const cx<R> z = mk(R(0), R(0));
+  if (incoming) {
+    if (hel < 0) { w.c[0] = a; w.c[1] = b; w.c[2] = z; w.c[3] = z; }  // u(p,-) = (xi_-, 0)
+    else         { w.c[0] = z; w.c[1] = z; w.c[2] = a; w.c[3] = b; }  // u(p,+) = (0, xi_+)
+  } else {
+    if (hel > 0) { w.c[0] = -a; w.c[1] = -b; w.c[2] = z; w.c[3] = z; }  // v(p,+) = (-xi_-, 0)
+    else         { w.c[0] = z; w.c[1] = z; w.c[2] = -a; w.c[3] = -b; }  // v(p,-) = (0, -xi_+)
+  }
+  return w;
+}
+
+// Row spinor of a massless fermion line leaving its vertex:
+//   outgoing fermion -> ubar(p, hel)      incoming antifermion -> vbar(p, hel)
+template <class R> ME_HD W4<R> ext_row_massless(P4<R> p, int hel, bool incoming) {
+  // ubar(p,h) = u(p,h)^dag gamma^0; vbar likewise: row = (lower^*, upper^*)
+  W4<R> col = ext_column_massless(p, hel, !incoming);
+  W4<R> w;
+  w.c[0] = conj(col.c[2]);
+  w.c[1] = conj(col.c[3]);
+  w.c[2] = conj(col.c[0]);
+  w.c[3] = conj(col.c[1]);
+  return w;
+}
+
+// Polarisation vector eps(k, hel) (incoming) or eps^*(k, hel) (outgoing).
+// eps(+-1) = (0, -+ e_theta - i e_phi)/sqrt2, eps(0) = (|k|, E k^)/m.
+template <class R> ME_HD W4<R> ext_vector(P4<R> k, int hel, bool incoming, R mass) {
+  W4<R> w;
+  const R pt2 = k.x * k.x + k.y * k.y;
+  const R pt = sqrt(pt2);
+  const R ak = sqrt(pt2 + k.z * k.z);
+  if (hel == 0) {
+    const R im = R(1) / mass;
+    const R f = k.e / (ak * mass);
+    w.c[0] = mk(ak * im, R(0));
+    w.c[1] = mk(f * k.x, R(0));
+    w.c[2] = mk(f * k.y, R(0));
+    w.c[3] = mk(f * k.z, R(0));
+    return w;
+  }
+  R cth, sth, cph, sph;
+  if (pt > R(0)) {
+    cth = k.z / ak; sth = pt / ak; cph = k.x / pt; sph = k.y / pt;
+  } else {
+    cth = k.z >= R(0) ? R(1) : R(-1); sth = R(0); cph = R(1); sph = R(0);
+  }
+  const R r = R(0.70710678118654752440);
+  const R l = (R)hel;
+  const R sgn = incoming ? R(1) : R(-1);  // conjugation flips the imaginary parts
+  w.c[0] = mk(R(0), R(0));
+  w.c[1] = mk(-l * cth * cph * r, sgn * sph * r);
+  w.c[2] = mk(-l * cth * sph * r, -sgn * cph * r);
+  w.c[3] = mk(l * sth * r, R(0));
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// FFV: Gamma = Vslash (gL P_L + gR P_R)
+// ---------------------------------------------------------------------------
+// V.sigma = [[V0-V3, -V1+iV2], [-V1-iV2, V0+V3]],  V.sigmabar = [[V0+V3, V1-iV2], [V1+iV2, V0-V3]]
+template <class R> ME_HD void vsig(const W4<R>& V, cx<R> m[4]) {
+  m[0] = V.c[0] - V.c[3];
+  m[1] = -V.c[1] + mul_i(V.c[2]);
+  m[2] = -V.c[1] - mul_i(V.c[2]);
+  m[3] = V.c[0] + V.c[3];
+}
+template <class R> ME_HD void vsigbar(const W4<R>& V, cx<R> m[4]) {
+  m[0] = V.c[0] + V.c[3];
+  m[1] = V.c[1] - mul_i(V.c[2]);
+  m[2] = V.c[1] + mul_i(V.c[2]);
+  m[3] = V.c[0] - V.c[3];
+}
+
+// Gamma psi for a column spinor: (gR (V.s) psi_lo, gL (V.sb) psi_up)
+template <class R> ME_HD W4<R> ffv_col(const W4<R>& psi, const W4<R>& V, R gl, R gr, bool has_l, bool has_r) {
+  W4<R> o;
+  const cx<R> z = mk(R(0), R(0));
+  if (has_r) {
+    cx<R> m[4];
+    vsig(V, m);
+    o.c[0] = gr * (m[0] * psi.c[2] + m[1] * psi.c[3]);
+    o.c[1] = gr * (m[2] * psi.c[2] + m[3] * psi.c[3]);
+  } else { o.c[0] = z; o.c[1] = z; }
+  if (has_l) {
+    cx<R> m[4];
+    vsigbar(V, m);
+    o.c[2] = gl * (m[0] * psi.c[0] + m[1] * psi.c[1]);
+    o.c[3] = gl * (m[2] * psi.c[0] + m[3] * psi.c[1]);
+  } else { o.c[2] = z; o.c[3] = z; }
+  return o;
+}
+
+// row Gamma: (gL row_lo (V.sb), gR row_up (V.s))
+template <class R> ME_HD W4<R> ffv_row(const W4<R>& row, const W4<R>& V, R gl, R gr, bool has_l, bool has_r) {
+  W4<R> o;
+  const cx<R> z = mk(R(0), R(0));
+  if (has_l) {
+    cx<R> m[4];
+    vsigbar(V, m);
+    o.c[0] = gl * (row.c[2] * m[0] + row.c[3] * m[2]);
+    o.c[1] = gl * (row.c[2] * m[1] + row.c[3] * m[3]);
+  } else { o.c[0] = z; o.c[1] = z; }
+  if (has_r) {
+    cx<R> m[4];
+    vsig(V, m);
+    o.c[2] = gr * (row.c[0] * m[0] + row.c[1] * m[2]);
+    o.c[3] = gr * (row.c[0] * m[1] + row.c[1] * m[3]);
+  } else { o.c[2] = z; o.c[3] = z; }
+  return o;
+}
+
+// row Gamma column
+template <class R> ME_HD cx<R> ffv_amp(const W4<R>& row, const W4<R>& col, const W4<R>& V, R gl, R gr,
+                                       bool has_l, bool has_r) {
+  W4<R> g = ffv_col(col, V, gl, gr, has_l, has_r);
+  return row.c[0] * g.c[0] + row.c[1] * g.c[1] + row.c[2] * g.c[2] + row.c[3] * g.c[3];
+}
+
+// J^mu = row gamma^mu (gL P_L + gR P_R) col = gL row_lo sb^mu col_up + gR row_up s^mu col_lo
+template <class R> ME_HD W4<R> ffv_current(const W4<R>& row, const W4<R>& col, R gl, R gr, bool has_l,
+                                           bool has_r) {
+  W4<R> J;
+  cx<R> s0 = mk(R(0), R(0)), s1 = s0, s2 = s0, s3 = s0;
+  if (has_l) {  // a = row_lo, b = col_up, sigmabar: (1, -sigma)
+    const cx<R> a0 = row.c[2], a1 = row.c[3], b0 = col.c[0], b1 = col.c[1];
+    const cx<R> t00 = a0 * b0, t11 = a1 * b1, t01 = a0 * b1, t10 = a1 * b0;
+    s0 = s0 + gl * (t00 + t11);
+    s1 = s1 - gl * (t01 + t10);
+    s2 = s2 - gl * mul_i(t10 - t01);
+    s3 = s3 - gl * (t00 - t11);
+  }
+  if (has_r) {  // a = row_up, b = col_lo, sigma: (1, sigma)
+    const cx<R> a0 = row.c[0], a1 = row.c[1], b0 = col.c[2], b1 = col.c[3];
+    const cx<R> t00 = a0 * b0, t11 = a1 * b1, t01 = a0 * b1, t10 = a1 * b0;
+    s0 = s0 + gr * (t00 + t11);
+    s1 = s1 + gr * (t01 + t10);
+    s2 = s2 + gr * mul_i(t10 - t01);
+    s3 = s3 + gr * (t00 - t11);
+  }
+  J.c[0] = s0; J.c[1] = s1; J.c[2] = s2; J.c[3] = s3;
+  return J;
+}
+
+// ---------------------------------------------------------------------------
+// propagators (numerators times the reciprocal denominator inv = 1/(q^2 - m^2 + i m w))
+// ---------------------------------------------------------------------------
+// (qslash + m) x inv for a column;  q is the momentum along the fermion arrow
+template <class R> ME_HD W4<R> prop_col(const W4<R>& x, P4<R> q, R m, cx<R> inv) {
+  // q.sigma = [[q0-q3, -q1+iq2], [-q1-iq2, q0+q3]],  q.sigmabar = [[q0+q3, q1-iq2], [q1+iq2, q0-q3]]
+  const cx<R> s00 = mk(q.e - q.z, R(0)), s01 = mk(-q.x, q.y), s10 = mk(-q.x, -q.y), s11 = mk(q.e + q.z, R(0));
+  const cx<R> b00 = mk(q.e + q.z, R(0)), b01 = mk(q.x, -q.y), b10 = mk(q.x, q.y), b11 = mk(q.e - q.z, R(0));
+  W4<R> o;
+  o.c[0] = s00 * x.c[2] + s01 * x.c[3];
+  o.c[1] = s10 * x.c[2] + s11 * x.c[3];
+  o.c[2] = b00 * x.c[0] + b01 * x.c[1];
+  o.c[3] = b10 * x.c[0] + b11 * x.c[1];
+  if (m != R(0)) {
+    for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] + m * x.c[k];
+  }
+  for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] * inv;
+  return o;
+}
+
+// x (qslash + m) inv for a row
+template <class R> ME_HD W4<R> prop_row(const W4<R>& x, P4<R> q, R m, cx<R> inv) {
+  const cx<R> s00 = mk(q.e - q.z, R(0)), s01 = mk(-q.x, q.y), s10 = mk(-q.x, -q.y), s11 = mk(q.e + q.z, R(0));
+  const cx<R> b00 = mk(q.e + q.z, R(0)), b01 = mk(q.x, -q.y), b10 = mk(q.x, q.y), b11 = mk(q.e - q.z, R(0));
+  W4<R> o;
+  // (x_up, x_lo) [[0, q.s], [q.sb, 0]] = (x_lo q.sb, x_up q.s)
+  o.c[0] = x.c[2] * b00 + x.c[3] * b10;
+  o.c[1] = x.c[2] * b01 + x.c[3] * b11;
+  o.c[2] = x.c[0] * s00 + x.c[1] * s10;
+  o.c[3] = x.c[0] * s01 + x.c[1] * s11;
+  if (m != R(0)) {
+    for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] + m * x.c[k];
+  }
+  for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] * inv;
+  return o;
+}
+
+template <class R> ME_HD cx<R> mdot(const W4<R>& a, const W4<R>& b) {
+  return a.c[0] * b.c[0] - a.c[1] * b.c[1] - a.c[2] * b.c[2] - a.c[3] * b.c[3];
+}
+template <class R> ME_HD cx<R> mdot(P4<R> q, const W4<R>& b) {
+  return q.e * b.c[0] - q.x * b.c[1] - q.y * b.c[2] - q.z * b.c[3];
+}
+
+// vector propagator numerator g^{mu nu} - q^mu q^nu / mc2 applied to X, times inv
+template <class R> ME_HD W4<R> prop_vec(const W4<R>& X, P4<R> q, cx<R> inv, bool massive, cx<R> inv_mc2) {
+  W4<R> o;
+  if (massive) {
+    const cx<R> f = mdot(q, X) * inv_mc2;
+    o.c[0] = (X.c[0] - q.e * f) * inv;
+    o.c[1] = (X.c[1] - q.x * f) * inv;
+    o.c[2] = (X.c[2] - q.y * f) * inv;
+    o.c[3] = (X.c[3] - q.z * f) * inv;
+  } else {
+    for (int k = 0; k < 4; ++k) o.c[k] = X.c[k] * inv;
+  }
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// VVV (all momenta incoming):  g [ g^{12}(k1-k2)^3 + g^{23}(k2-k3)^1 + g^{31}(k3-k1)^2 ]
+// ---------------------------------------------------------------------------
+template <class R> ME_HD W4<R> vvv_current(const W4<R>& V1, P4<R> k1, const W4<R>& V2, P4<R> k2, R g) {
+  const P4<R> k3 = {-(k1.e + k2.e), -(k1.x + k2.x), -(k1.y + k2.y), -(k1.z + k2.z)};
+  const P4<R> d12 = {k1.e - k2.e, k1.x - k2.x, k1.y - k2.y, k1.z - k2.z};
+  const P4<R> d23 = {k2.e - k3.e, k2.x - k3.x, k2.y - k3.y, k2.z - k3.z};
+  const P4<R> d31 = {k3.e - k1.e, k3.x - k1.x, k3.y - k1.y, k3.z - k1.z};
+  const cx<R> v12 = mdot(V1, V2), a = mdot(d23, V1), b = mdot(d31, V2);
+  W4<R> o;
+  o.c[0] = g * (d12.e * v12 + V2.c[0] * a + V1.c[0] * b);
+  o.c[1] = g * (d12.x * v12 + V2.c[1] * a + V1.c[1] * b);
+  o.c[2] = g * (d12.y * v12 + V2.c[2] * a + V1.c[2] * b);
+  o.c[3] = g * (d12.z * v12 + V2.c[3] * a + V1.c[3] * b);
+  return o;
+}
+
+template <class R> ME_HD cx<R> vvv_amp(const W4<R>& V1, P4<R> k1, const W4<R>& V2, P4<R> k2, const W4<R>& V3,
+                                       R g) {
+  return mdot(vvv_current(V1, k1, V2, k2, g), V3);
+}
+
+// VVVV pairing current: V_p (V_a . V_b)
+template <class R> ME_HD W4<R> v4_term(const W4<R>& Vp, const W4<R>& Va, const W4<R>& Vb) {
+  const cx<R> d = mdot(Va, Vb);
+  W4<R> o;
+  for (int k = 0; k < 4; ++k) o.c[k] = Vp.c[k] * d;
+  return o;
+}
+
+template <class R> ME_HD W4<R> w4_sub(const W4<R>& a, const W4<R>& b, R g) {
+  W4<R> o;
+  for (int k = 0; k < 4; ++k) o.c[k] = g * (a.c[k] - b.c[k]);
+  return o;
+}
+
+template <class R> ME_HD W4<R> w4_scale(const W4<R>& a, cx<R> s) {
+  W4<R> o;
+  for (int k = 0; k < 4; ++k) o.c[k] = a.c[k] * s;
+  return o;
+}
+
+}  // namespace me

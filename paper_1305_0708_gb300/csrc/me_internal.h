@@ -1,0 +1,45 @@
+// Internal types shared by the runtime and the generated process units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "me.h"
+
+namespace me {
+
+// Phase-space description as the kernels use it: the user's me_kin plus the
+// quantities derived once on the host.
+struct KinDev {
+  int32_t kind;
+  int32_t max_attempts;
+  double sqrt_s, sqrt_s_min, sqrt_s_max;
+  double mass[16];
+  int32_t n_cut_legs;
+  int32_t cut_legs[8];
+  double pt_min, eta_max, dr_min, s_ident;
+  double rambo_volume;   // massless n-body volume with the (2 pi) factors of Eq. 5
+  double sinh2_eta_max;  // sinh(eta_max)^2
+  double cos_dr, cosh_dr, sinh_dr;
+  double bw_mass[2], bw_width[2], bw_t0[2], bw_t1[2];  // top, W
+};
+
+constexpr int kThreads = 128;
+
+// Entry points of one compiled process.
+struct ProcessDesc {
+  const char* name;
+  int n_ext;
+  int n_params;
+  const char* const* param_names;
+  int n_hel, n_hel_live, n_colour, n_diagrams;
+  double flops_amp, flops_fp64;
+  const int* pdg;
+  cudaError_t (*launch_eval)(int prec, const double* mom, int64_t n, double* out, const double* params,
+                             cudaStream_t s, int grid);
+  cudaError_t (*launch_xsec)(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t n,
+                             const double* params, double* partials, double* me2_out, double* mom_out,
+                             double* wps_out, double* shat_out, int32_t* tries_out, int* status,
+                             int eval_me, cudaStream_t s, int grid);
+};
+
+}  // namespace me

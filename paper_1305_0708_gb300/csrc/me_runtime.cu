@@ -1,0 +1,380 @@
+// C-ABI runtime: handles, parameter resolution, workspace, launches and the
+// deterministic Monte Carlo reduction.  Declarations and contracts: include/me.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "me.h"
+#include "me_internal.h"
+
+namespace me {
+// generated registry (registry.cu)
+int registry_size();
+ProcessDesc* registry_entry(int i);
+}  // namespace me
+
+namespace {
+
+thread_local std::string g_err;
+
+me_status fail(me_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+me_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(ME_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+const double kPi = 3.14159265358979323846;
+
+me_params default_params() {
+  me_params p;
+  p.alpha = 1.0 / 128.0;
+  p.sw2 = 0.2312;
+  p.mZ = 91.1876;
+  p.wZ = 2.4952;
+  p.mW = 80.4;
+  p.wW = 2.085;
+  p.alpha_s = 0.118;
+  p.mt = 175.0;
+  p.wt = 1.50;
+  p.mH = 125.0;
+  p.wH = 0.0;
+  return p;
+}
+
+// numerical value of a coupling / mass parameter name used by the generated code
+bool coupling_value(const std::string& n, const me_params& p, double& v) {
+  const double e = std::sqrt(4 * kPi * p.alpha);
+  const double sw = std::sqrt(p.sw2), cw = std::sqrt(1 - p.sw2);
+  const double g = e / sw, gz = e / (sw * cw), gs = std::sqrt(4 * kPi * p.alpha_s);
+  const double vev = 2 * p.mW / g;
+  struct F { const char* f; double q, t3; };
+  static const F ferm[] = {{"u", 2.0 / 3, 0.5}, {"c", 2.0 / 3, 0.5}, {"t", 2.0 / 3, 0.5}, {"d", -1.0 / 3, -0.5},
+                           {"s", -1.0 / 3, -0.5}, {"b", -1.0 / 3, -0.5}, {"e-", -1.0, -0.5}, {"mu-", -1.0, -0.5},
+                           {"ve", 0.0, 0.5}, {"vm", 0.0, 0.5}};
+  if (n == "ZERO" || n == "0") { v = 0; return true; }
+  if (n == "GS") { v = gs; return true; }
+  if (n == "GS2") { v = gs * gs; return true; }
+  if (n == "GW") { v = g / std::sqrt(2.0); return true; }
+  if (n == "GWWH") { v = g * p.mW; return true; }
+  if (n == "GZZH") { v = gz * p.mZ; return true; }
+  if (n == "GWWHH") { v = g * g / 2; return true; }
+  if (n == "GZZHH") { v = gz * gz / 2; return true; }
+  if (n == "GHHH") { v = -3 * p.mH * p.mH / vev; return true; }
+  if (n == "MT") { v = p.mt; return true; }
+  if (n == "WT") { v = p.wt; return true; }
+  if (n == "MZ") { v = p.mZ; return true; }
+  if (n == "WZ") { v = p.wZ; return true; }
+  if (n == "MW") { v = p.mW; return true; }
+  if (n == "WW") { v = p.wW; return true; }
+  if (n == "MH") { v = p.mH; return true; }
+  if (n == "WH") { v = p.wH; return true; }
+  for (const F& f : ferm) {
+    const std::string s(f.f);
+    if (n == "GA_" + s) { v = e * f.q; return true; }
+    if (n == "GZL_" + s) { v = gz * (f.t3 - f.q * p.sw2); return true; }
+    if (n == "GZR_" + s) { v = gz * (-f.q * p.sw2); return true; }
+  }
+  return false;
+}
+
+std::string normalise(const char* s) {
+  std::string out;
+  bool space = false;
+  for (const char* c = s; *c; ++c) {
+    if (*c == ' ' || *c == '\t' || *c == '\n') {
+      space = !out.empty();
+      continue;
+    }
+    if (space) out.push_back(' ');
+    space = false;
+    out.push_back(*c);
+  }
+  return out;
+}
+
+}  // namespace
+
+struct me_handle_s {
+  me::ProcessDesc* desc = nullptr;
+  me_params params;
+  int prec = ME_FP64;
+  std::vector<double> cvals;
+  int device = 0;
+  int n_sm = 0;
+  // workspace (lazy)
+  double* d_partials = nullptr;
+  int partials_cap = 0;
+  double* d_acc = nullptr;    // 3 doubles
+  int* d_status = nullptr;
+  double* h_acc = nullptr;    // pinned, 3 doubles + status
+  std::mutex mu;
+};
+
+namespace {
+
+// fixed-order sum of the per-block partials (one block; deterministic)
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks, double* __restrict__ acc) {
+  __shared__ double sm[3][256];
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    s0 += partials[3 * b + 0];
+    s1 += partials[3 * b + 1];
+    s2 += partials[3 * b + 2];
+  }
+  sm[0][threadIdx.x] = s0;
+  sm[1][threadIdx.x] = s1;
+  sm[2][threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sm[0][threadIdx.x] += sm[0][threadIdx.x + o];
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + o];
+      sm[2][threadIdx.x] += sm[2][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    acc[0] = sm[0][0];
+    acc[1] = sm[1][0];
+    acc[2] = sm[2][0];
+  }
+}
+
+int grid_for(me_handle h, int64_t n) {
+  const int64_t need = (n + me::kThreads - 1) / me::kThreads;
+  const int64_t cap = (int64_t)h->n_sm * 8;  // grid-stride beyond 8 blocks per SM
+  return (int)std::max<int64_t>(1, std::min(need, cap));
+}
+
+me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
+  if (kin->kind < ME_PS_TWO_BODY || kin->kind > ME_PS_TTBAR) return fail(ME_ERR_ARG, "kin->kind: unknown generator");
+  const int next = h->desc->n_ext;
+  if (kin->kind == ME_PS_TWO_BODY && next != 4) return fail(ME_ERR_ARG, "two-body generator needs 4 legs");
+  if (kin->kind == ME_PS_TTBAR && next != 8) return fail(ME_ERR_ARG, "ttbar generator needs 8 legs");
+  if (kin->kind == ME_PS_RAMBO && (next < 4 || next > 10)) return fail(ME_ERR_ARG, "RAMBO supports 2 to 8 final legs");
+  if (kin->n_cut_legs < 0 || kin->n_cut_legs > 8) return fail(ME_ERR_ARG, "kin->n_cut_legs out of range");
+  for (int i = 0; i < kin->n_cut_legs; ++i)
+    if (kin->cut_legs[i] < 2 || kin->cut_legs[i] >= next) return fail(ME_ERR_ARG, "kin->cut_legs: not a final-state leg");
+  if (kin->kind != ME_PS_TTBAR && !(kin->sqrt_s > 0)) return fail(ME_ERR_ARG, "kin->sqrt_s must be positive");
+  if (kin->kind == ME_PS_TTBAR && !(kin->sqrt_s_max > kin->sqrt_s_min && kin->sqrt_s_min > 0))
+    return fail(ME_ERR_ARG, "kin->sqrt_s_min/max invalid");
+  std::memset(&k, 0, sizeof(k));
+  k.kind = kin->kind;
+  k.max_attempts = kin->max_attempts > 0 ? kin->max_attempts : 10000;
+  k.sqrt_s = kin->sqrt_s;
+  k.sqrt_s_min = kin->sqrt_s_min;
+  k.sqrt_s_max = kin->sqrt_s_max;
+  double msum = 0;
+  for (int i = 0; i < 16; ++i) {
+    k.mass[i] = (kin->kind == ME_PS_RAMBO && i < next) ? kin->mass[i] : 0.0;
+    if (i >= 2 && i < next) msum += k.mass[i];
+  }
+  if (kin->kind == ME_PS_RAMBO && !(msum < kin->sqrt_s)) return fail(ME_ERR_ARG, "kin: masses exceed sqrt_s");
+  k.n_cut_legs = kin->n_cut_legs;
+  for (int i = 0; i < 8; ++i) k.cut_legs[i] = kin->cut_legs[i];
+  k.pt_min = kin->pt_min;
+  k.eta_max = kin->eta_max;
+  k.dr_min = kin->dr_min;
+  k.s_ident = kin->s_ident > 0 ? kin->s_ident : 1.0;
+  const int nf = next - 2;
+  double fact = 1;
+  for (int i = 2; i <= nf - 1; ++i) fact *= i;  // (n-1)!
+  double fact2 = 1;
+  for (int i = 2; i <= nf - 2; ++i) fact2 *= i;  // (n-2)!
+  const double w = kin->sqrt_s;
+  k.rambo_volume = std::pow(2 * kPi, 4 - 3 * nf) * std::pow(kPi / 2, nf - 1) * std::pow(w, 2 * nf - 4) / (fact * fact2);
+  const double sh = std::sinh(kin->eta_max);
+  k.sinh2_eta_max = kin->n_cut_legs > 0 ? sh * sh : 0.0;
+  k.cos_dr = std::cos(kin->dr_min);
+  k.cosh_dr = std::cosh(kin->dr_min);
+  k.sinh_dr = std::sinh(kin->dr_min);
+  const me_params& p = h->params;
+  k.bw_mass[0] = p.mt;
+  k.bw_width[0] = p.wt;
+  k.bw_mass[1] = p.mW;
+  k.bw_width[1] = p.wW;
+  for (int r = 0; r < 2; ++r) {
+    const double x = std::min(20.0, k.bw_mass[r] / k.bw_width[r]);
+    k.bw_t0[r] = -std::atan(x);
+    k.bw_t1[r] = std::atan(x);
+  }
+  if (kin->kind == ME_PS_TTBAR && !(p.wt > 0 && p.wW > 0)) return fail(ME_ERR_ARG, "ttbar generator needs widths");
+  return ME_OK;
+}
+
+me_status ensure_workspace(me_handle h, int nblocks) {
+  cudaError_t e;
+  if (!h->d_acc) {
+    if ((e = cudaMalloc(&h->d_acc, 4 * sizeof(double))) != cudaSuccess) return fail(ME_ERR_OOM, "workspace");
+    if ((e = cudaMalloc(&h->d_status, sizeof(int))) != cudaSuccess) return fail(ME_ERR_OOM, "workspace");
+    if ((e = cudaMemset(h->d_status, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    if ((e = cudaMallocHost(&h->h_acc, 4 * sizeof(double))) != cudaSuccess) return fail(ME_ERR_OOM, "pinned");
+  }
+  if (nblocks > h->partials_cap) {
+    if (h->d_partials) cudaFree(h->d_partials);
+    h->d_partials = nullptr;
+    if ((e = cudaMalloc(&h->d_partials, (size_t)nblocks * 3 * sizeof(double))) != cudaSuccess)
+      return fail(ME_ERR_OOM, "workspace partials");
+    h->partials_cap = nblocks;
+  }
+  return ME_OK;
+}
+
+me_status check_handle(me_handle h) {
+  if (!h || !h->desc) return fail(ME_ERR_ARG, "null handle");
+  return ME_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t me_n_processes(void) { return me::registry_size(); }
+
+const char* me_process_name(int32_t i) {
+  if (i < 0 || i >= me::registry_size()) return nullptr;
+  return me::registry_entry(i)->name;
+}
+
+me_status me_create(const char* process, const me_params* params, int32_t prec, me_handle* out) {
+  if (!process || !out) return fail(ME_ERR_ARG, "me_create: null argument");
+  if (prec != ME_FP64 && prec != ME_MIXED) return fail(ME_ERR_ARG, "me_create: unknown precision");
+  *out = nullptr;
+  const std::string want = normalise(process);
+  me::ProcessDesc* d = nullptr;
+  for (int i = 0; i < me::registry_size(); ++i)
+    if (normalise(me::registry_entry(i)->name) == want) d = me::registry_entry(i);
+  if (!d) return fail(ME_ERR_PROCESS, "process not compiled into this library: " + want);
+  me_handle h = new me_handle_s();
+  h->desc = d;
+  h->params = params ? *params : default_params();
+  h->prec = prec;
+  for (int k = 0; k < d->n_params; ++k) {
+    double v;
+    if (!coupling_value(d->param_names[k], h->params, v)) {
+      delete h;
+      return fail(ME_ERR_PROCESS, std::string("unknown coupling ") + d->param_names[k]);
+    }
+    h->cvals.push_back(v);
+  }
+  if (h->cvals.empty()) h->cvals.push_back(0.0);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+  e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+  *out = h;
+  return ME_OK;
+}
+
+me_status me_eval(me_handle h, const double* momenta, int64_t n, double* out, void* stream) {
+  me_status st = check_handle(h);
+  if (st != ME_OK) return st;
+  if (n < 0) return fail(ME_ERR_ARG, "me_eval: n < 0");
+  if (n == 0) return ME_OK;
+  if (!momenta || !out) return fail(ME_ERR_ARG, "me_eval: null buffer");
+  cudaError_t e = h->desc->launch_eval(h->prec, momenta, n, out, h->cvals.data(), (cudaStream_t)stream, grid_for(h, n));
+  if (e != cudaSuccess) return cuda_fail(e, "me_eval launch");
+  return ME_OK;
+}
+
+me_status me_generate(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n, const me_kin* kin,
+                      double* momenta, double* weight, double* shat, int32_t* tries, void* stream) {
+  me_status st = check_handle(h);
+  if (st != ME_OK) return st;
+  if (!kin) return fail(ME_ERR_ARG, "me_generate: null kin");
+  if (n < 0) return fail(ME_ERR_ARG, "me_generate: n < 0");
+  me::KinDev k;
+  if ((st = make_kin(h, kin, k)) != ME_OK) return st;
+  if (n == 0) return ME_OK;
+  std::lock_guard<std::mutex> lock(h->mu);
+  if ((st = ensure_workspace(h, 1)) != ME_OK) return st;
+  cudaError_t e = h->desc->launch_xsec(h->prec, &k, seed, counter_offset, n, h->cvals.data(), nullptr, nullptr,
+                                       momenta, weight, shat, tries, h->d_status, 0, (cudaStream_t)stream,
+                                       grid_for(h, n));
+  if (e != cudaSuccess) return cuda_fail(e, "me_generate launch");
+  return ME_OK;
+}
+
+me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept, const me_kin* kin,
+                    void* stream, me_xsec_acc* acc, double* me2_out, double* momenta_out) {
+  me_status st = check_handle(h);
+  if (st != ME_OK) return st;
+  if (!kin || !acc) return fail(ME_ERR_ARG, "xsec_step: null argument");
+  if (n_accept < 0) return fail(ME_ERR_ARG, "xsec_step: n_accept < 0");
+  me::KinDev k;
+  if ((st = make_kin(h, kin, k)) != ME_OK) return st;
+  if (n_accept == 0) return ME_OK;
+  std::lock_guard<std::mutex> lock(h->mu);
+  const int grid = grid_for(h, n_accept);
+  if ((st = ensure_workspace(h, grid)) != ME_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = h->desc->launch_xsec(h->prec, &k, seed, counter_offset, n_accept, h->cvals.data(), h->d_partials,
+                                       me2_out, momenta_out, nullptr, nullptr, nullptr, h->d_status, 1, s, grid);
+  if (e != cudaSuccess) return cuda_fail(e, "xsec_step launch");
+  k_reduce_partials<<<1, 256, 0, s>>>(h->d_partials, grid, h->d_acc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "xsec_step reduce");
+  if ((e = cudaMemcpyAsync(h->h_acc, h->d_acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "xsec_step copy");
+  int status = 0;
+  if ((e = cudaMemcpyAsync(&h->h_acc[3], h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "xsec_step copy");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "xsec_step sync");
+  std::memcpy(&status, &h->h_acc[3], sizeof(int));
+  if (status) {
+    cudaMemsetAsync(h->d_status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return fail(ME_ERR_TIMEOUT, "xsec_step: a point exhausted its phase-space redraws");
+  }
+  acc->sum_w += h->h_acc[0];
+  acc->sum_w2 += h->h_acc[1];
+  acc->n_acc += n_accept;
+  acc->n_try += (int64_t)llround(h->h_acc[2]);
+  return ME_OK;
+}
+
+me_status me_xsec_estimate(const me_xsec_acc* acc, double* sigma, double* error) {
+  if (!acc || !sigma || !error) return fail(ME_ERR_ARG, "me_xsec_estimate: null argument");
+  if (acc->n_try <= 0) return fail(ME_ERR_STATE, "me_xsec_estimate: empty accumulator");
+  const double n = (double)acc->n_try;
+  const double mean = acc->sum_w / n;
+  const double var = std::max(acc->sum_w2 / n - mean * mean, 0.0);
+  *sigma = mean;
+  *error = std::sqrt(var / std::max(n - 1.0, 1.0));
+  return ME_OK;
+}
+
+me_status me_info(me_handle h, me_info_t* info) {
+  me_status st = check_handle(h);
+  if (st != ME_OK) return st;
+  if (!info) return fail(ME_ERR_ARG, "me_info: null argument");
+  std::memset(info, 0, sizeof(*info));
+  const me::ProcessDesc* d = h->desc;
+  info->n_ext = d->n_ext;
+  info->n_hel = d->n_hel;
+  info->n_hel_live = d->n_hel_live;
+  info->n_colour = d->n_colour;
+  info->n_diagrams = d->n_diagrams;
+  for (int i = 0; i < d->n_ext && i < 16; ++i) info->pdg[i] = d->pdg[i];
+  info->flops_amp = d->flops_amp;
+  info->flops_fp64 = d->flops_fp64;
+  return ME_OK;
+}
+
+void me_destroy(me_handle h) {
+  if (!h) return;
+  if (h->d_partials) cudaFree(h->d_partials);
+  if (h->d_acc) cudaFree(h->d_acc);
+  if (h->d_status) cudaFree(h->d_status);
+  if (h->h_acc) cudaFreeHost(h->h_acc);
+  delete h;
+}
+
+const char* me_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

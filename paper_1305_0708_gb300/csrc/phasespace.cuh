@@ -1,0 +1,331 @@
+// On-device phase-space generation, cuts and redraws (FP64).
+//
+// Random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), one
+// counter per (event, attempt, block): counter = (event, attempt, block, 0),
+// key = (seed, 0), ten rounds with the Weyl key schedule; a 64-bit word x
+// maps to ((x >> 11) + 1/2) 2^-53 in (0, 1).
+//
+// Generators: two-body at fixed sqrt(s) with cos(theta), phi uniform;
+// massless RAMBO (Kleiss, Stirling, Ellis 1986) with the massive rescaling;
+// g g > t t~ > (b W+)(b~ W-) > ... with sqrt(s) uniform, Breit-Wigner
+// sampled t, t~, W+, W- virtualities (the paper's Eq. 16, App. A.2) and
+// isotropic two-body decays.  A point that fails the cuts (the paper's
+// Eqs. 8-11 in form: pT, |eta|, Delta R) is redrawn with the next attempt,
+// which keeps the result independent of the launch shape (Sect. 3 and App. A
+// note that on a GPU each thread has one try per point; here each thread
+// loops until its own point passes).
+#pragma once
+#include <cstdint>
+
+#include "me_internal.h"
+
+namespace me {
+
+struct Philox {
+  static __host__ __device__ __forceinline__ void mulhilo(uint64_t a, uint64_t b, uint64_t& hi, uint64_t& lo) {
+#ifdef __CUDA_ARCH__
+    hi = __umul64hi(a, b);
+#else
+    hi = (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+    lo = a * b;
+  }
+  static __host__ __device__ __forceinline__ void block(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                                        uint64_t k0, uint64_t k1, uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      uint64_t h0, l0, h1, l1;
+      mulhilo(M0, c0, h0, l0);
+      mulhilo(M1, c2, h1, l1);
+      const uint64_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
+      c0 = n0; c1 = l1; c2 = n2; c3 = l0;
+      k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+  }
+};
+
+__host__ __device__ __forceinline__ double to_unit(uint64_t x) {
+  return ((double)(x >> 11) + 0.5) * 0x1p-53;
+}
+
+// uniforms u[4*nb] for (event, attempt)
+template <int NB>
+__host__ __device__ __forceinline__ void draw_uniforms(uint64_t seed, uint64_t event, uint64_t attempt, double (&u)[4 * NB]) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    uint64_t o[4];
+    Philox::block(event, attempt, (uint64_t)j, 0ull, seed, 0ull, o);
+    u[4 * j + 0] = to_unit(o[0]);
+    u[4 * j + 1] = to_unit(o[1]);
+    u[4 * j + 2] = to_unit(o[2]);
+    u[4 * j + 3] = to_unit(o[3]);
+  }
+}
+
+__host__ __device__ __forceinline__ void set4(double* p, double e, double x, double y, double z) {
+  p[0] = e; p[1] = x; p[2] = y; p[3] = z;
+}
+
+// isotropic unit vector from cos(theta) = 2a - 1, phi = 2 pi b
+__host__ __device__ __forceinline__ void direction(double a, double b, double& nx, double& ny, double& nz) {
+  const double c = 2.0 * a - 1.0;
+  const double s = sqrt(fmax(1.0 - c * c, 0.0));
+  double sp, cp;
+  sincospi(2.0 * b, &sp, &cp);
+  nx = s * cp; ny = s * sp; nz = c;
+}
+
+// two-body decay at rest of mass M into (m1, m2): |p*| and the momenta along +-n
+__host__ __device__ __forceinline__ double kallen_sqrt(double a, double b, double c) {
+  const double l = a * a + b * b + c * c - 2.0 * (a * b + b * c + c * a);
+  return sqrt(fmax(l, 0.0));
+}
+
+// boost pstar out of the rest frame of a system with lab momentum P and mass M
+__host__ __device__ __forceinline__ void boost_from_rest(double* p, const double* P, double M) {
+  const double pp = P[1] * p[1] + P[2] * p[2] + P[3] * p[3];
+  const double e = (P[0] * p[0] + pp) / M;
+  const double f = (pp / (P[0] + M) + p[0]) / M;
+  p[0] = e;
+  p[1] += f * P[1];
+  p[2] += f * P[2];
+  p[3] += f * P[3];
+}
+
+// ---------------------------------------------------------------------------
+// generators; each returns false if the draw is outside the kinematic limits
+// ---------------------------------------------------------------------------
+template <int NEXT>
+__host__ __device__ __forceinline__ void beams(double (&p)[NEXT][4], double w) {
+  set4(p[0], 0.5 * w, 0.0, 0.0, 0.5 * w);
+  set4(p[1], 0.5 * w, 0.0, 0.0, -0.5 * w);
+}
+
+template <int NEXT>
+__host__ __device__ __forceinline__ bool gen_two_body(const KinDev& kin, const double* u, double (&p)[NEXT][4],
+                                                      double& wps, double& shat) {
+  const double w = kin.sqrt_s;
+  beams<NEXT>(p, w);
+  double nx, ny, nz;
+  direction(u[0], u[1], nx, ny, nz);
+  const double E = 0.5 * w;
+  set4(p[NEXT - 1], E, E * nx, E * ny, E * nz);
+  set4(p[NEXT - 2], E, -E * nx, -E * ny, -E * nz);
+  wps = 1.0 / (8.0 * 3.14159265358979323846);
+  shat = w * w;
+  return true;
+}
+
+// RAMBO: massless momenta, then (if any mass) the Kleiss-Stirling-Ellis rescaling
+template <int NEXT>
+__host__ __device__ __forceinline__ bool gen_rambo(const KinDev& kin, const double* u, double (&p)[NEXT][4],
+                                                   double& wps, double& shat) {
+  constexpr int NF = NEXT - 2;
+  const double w = kin.sqrt_s;
+  beams<NEXT>(p, w);
+  double Q0 = 0, Q1 = 0, Q2 = 0, Q3 = 0;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    double nx, ny, nz;
+    direction(u[4 * k + 0], u[4 * k + 1], nx, ny, nz);
+    const double q0 = -log(u[4 * k + 2] * u[4 * k + 3]);
+    set4(p[2 + k], q0, q0 * nx, q0 * ny, q0 * nz);
+    Q0 += q0; Q1 += p[2 + k][1]; Q2 += p[2 + k][2]; Q3 += p[2 + k][3];
+  }
+  const double M = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
+  const double iM = 1.0 / M;
+  const double b1 = -Q1 * iM, b2 = -Q2 * iM, b3 = -Q3 * iM;
+  const double gam = Q0 * iM, a = 1.0 / (1.0 + gam), x = w * iM;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    double* q = p[2 + k];
+    const double bq = b1 * q[1] + b2 * q[2] + b3 * q[3];
+    const double q0 = q[0];
+    const double c = q0 + a * bq;
+    q[0] = x * (gam * q0 + bq);
+    q[1] = x * (q[1] + b1 * c);
+    q[2] = x * (q[2] + b2 * c);
+    q[3] = x * (q[3] + b3 * c);
+  }
+  // massless volume (2pi)^(4-3n) (pi/2)^(n-1) w^(2n-4) / ((n-1)! (n-2)!)
+  wps = kin.rambo_volume;
+  shat = w * w;
+  bool massive = false;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) massive |= kin.mass[2 + k] > 0.0;
+  if (massive) {
+    double E0[NF];
+    double msum = 0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) { E0[k] = p[2 + k][0]; msum += kin.mass[2 + k]; }
+    double xi = sqrt(fmax(1.0 - (msum / w) * (msum / w), 0.0));
+    for (int it = 0; it < 40; ++it) {
+      double f = -w, df = 0;
+#pragma unroll
+      for (int k = 0; k < NF; ++k) {
+        const double m = kin.mass[2 + k];
+        const double Ek = sqrt(m * m + xi * xi * E0[k] * E0[k]);
+        f += Ek;
+        df += xi * E0[k] * E0[k] / Ek;
+      }
+      xi -= f / df;
+    }
+    double prod = 1.0, sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const double m = kin.mass[2 + k];
+      const double ak = xi * E0[k];
+      const double Ek = sqrt(m * m + ak * ak);
+      prod *= ak / Ek;
+      sum += ak * ak / Ek;
+      p[2 + k][0] = Ek;
+      p[2 + k][1] *= xi; p[2 + k][2] *= xi; p[2 + k][3] *= xi;
+    }
+    wps *= pow(xi, 2 * NF - 3) * prod * w / sum;
+  }
+  return true;
+}
+
+__host__ __device__ __forceinline__ double bw_draw(double m, double g, double t0, double t1, double uu, double& jac) {
+  const double th = t0 + (t1 - t0) * uu;
+  const double s = m * m + m * g * tan(th);
+  const double d = s - m * m;
+  jac = (t1 - t0) * (d * d + m * m * g * g) / (m * g) * (1.0 / (2.0 * 3.14159265358979323846));
+  return s;
+}
+
+// g g > t t~ > (b (e+ ve)) (b~ (e- ve~)); legs g g b e+ ve b~ e- ve~
+template <int NEXT>
+__host__ __device__ __forceinline__ bool gen_ttbar(const KinDev& kin, const double* u, double (&p)[NEXT][4],
+                                                   double& wps, double& shat) {
+  if constexpr (NEXT != 8) {
+    return false;
+  } else {
+    const double rs = kin.sqrt_s_min + (kin.sqrt_s_max - kin.sqrt_s_min) * u[0];
+    shat = rs * rs;
+    double jt, jtb, jwp, jwm;
+    const double st = bw_draw(kin.bw_mass[0], kin.bw_width[0], kin.bw_t0[0], kin.bw_t1[0], u[1], jt);
+    const double stb = bw_draw(kin.bw_mass[0], kin.bw_width[0], kin.bw_t0[0], kin.bw_t1[0], u[2], jtb);
+    const double swp = bw_draw(kin.bw_mass[1], kin.bw_width[1], kin.bw_t0[1], kin.bw_t1[1], u[3], jwp);
+    const double swm = bw_draw(kin.bw_mass[1], kin.bw_width[1], kin.bw_t0[1], kin.bw_t1[1], u[4], jwm);
+    if (!(st > 0 && stb > 0 && swp > 0 && swm > 0)) return false;
+    const double mt = sqrt(st), mtb = sqrt(stb), mwp = sqrt(swp), mwm = sqrt(swm);
+    if (!(mwp <= mt && mwm <= mtb && mt + mtb <= rs)) return false;
+    beams<NEXT>(p, rs);
+    const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
+    double nx, ny, nz;
+    // production in the CM frame
+    const double kp = kallen_sqrt(shat, st, stb) / (2.0 * rs);
+    direction(u[5], u[6], nx, ny, nz);
+    double T[4], TB[4];
+    set4(T, sqrt(st + kp * kp), kp * nx, kp * ny, kp * nz);
+    set4(TB, sqrt(stb + kp * kp), -kp * nx, -kp * ny, -kp * nz);
+    // t -> b W+
+    const double kt = (st - swp) / (2.0 * mt);
+    direction(u[7], u[8], nx, ny, nz);
+    double WP[4];
+    set4(p[2], kt, kt * nx, kt * ny, kt * nz);
+    set4(WP, sqrt(swp + kt * kt), -kt * nx, -kt * ny, -kt * nz);
+    boost_from_rest(p[2], T, mt);
+    boost_from_rest(WP, T, mt);
+    // W+ -> e+ ve
+    const double kw = 0.5 * mwp;
+    direction(u[9], u[10], nx, ny, nz);
+    set4(p[3], kw, kw * nx, kw * ny, kw * nz);
+    set4(p[4], kw, -kw * nx, -kw * ny, -kw * nz);
+    boost_from_rest(p[3], WP, mwp);
+    boost_from_rest(p[4], WP, mwp);
+    // t~ -> b~ W-
+    const double ktb = (stb - swm) / (2.0 * mtb);
+    direction(u[11], u[12], nx, ny, nz);
+    double WM[4];
+    set4(p[5], ktb, ktb * nx, ktb * ny, ktb * nz);
+    set4(WM, sqrt(swm + ktb * ktb), -ktb * nx, -ktb * ny, -ktb * nz);
+    boost_from_rest(p[5], TB, mtb);
+    boost_from_rest(WM, TB, mtb);
+    // W- -> e- ve~
+    const double kw2 = 0.5 * mwm;
+    direction(u[13], u[14], nx, ny, nz);
+    set4(p[6], kw2, kw2 * nx, kw2 * ny, kw2 * nz);
+    set4(p[7], kw2, -kw2 * nx, -kw2 * ny, -kw2 * nz);
+    boost_from_rest(p[6], WM, mwm);
+    boost_from_rest(p[7], WM, mwm);
+    wps = (kp * inv4pi / rs) * jt * jtb * jwp * jwm * (kt * inv4pi / mt) * (kw * inv4pi / mwp) *
+          (ktb * inv4pi / mtb) * (kw2 * inv4pi / mwm);
+    return true;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// cuts: pT > pt_min, |eta| < eta_max, Delta R > dr_min over kin.cut_legs.
+// |eta| < eta_max  <=>  |pz| < sinh(eta_max) pT.  A pair is separated when
+// its azimuthal or its pseudorapidity distance alone exceeds dr_min (both
+// tested without transcendentals); only the remaining close pairs evaluate
+// Delta R = sqrt(d_eta^2 + d_phi^2) with asinh and atan2.
+// ---------------------------------------------------------------------------
+template <int NEXT>
+__host__ __device__ __forceinline__ bool pass_cuts(const KinDev& kin, const double (&p)[NEXT][4]) {
+  const int nl = kin.n_cut_legs;
+  if (nl == 0) return true;
+  double pt2[8], a[8], r[8];
+  for (int i = 0; i < nl; ++i) {
+    const double* q = p[kin.cut_legs[i]];
+    pt2[i] = q[1] * q[1] + q[2] * q[2];
+    if (!(pt2[i] > kin.pt_min * kin.pt_min)) return false;
+    if (!(q[3] * q[3] < kin.sinh2_eta_max * pt2[i])) return false;
+    const double ipt = 1.0 / sqrt(pt2[i]);
+    a[i] = q[3] * ipt;                                        // sinh(eta)
+    r[i] = sqrt(pt2[i] + q[3] * q[3]) * ipt;                  // cosh(eta)
+  }
+  for (int i = 0; i < nl; ++i) {
+    for (int j = i + 1; j < nl; ++j) {
+      const double* qi = p[kin.cut_legs[i]];
+      const double* qj = p[kin.cut_legs[j]];
+      const double dot = qi[1] * qj[1] + qi[2] * qj[2];
+      const double ptij = sqrt(pt2[i] * pt2[j]);
+      if (dot < kin.cos_dr * ptij) continue;                   // |d_phi| > dr_min
+      if (a[i] > a[j] * kin.cosh_dr + r[j] * kin.sinh_dr) continue;  // eta_i - eta_j > dr_min
+      if (a[j] > a[i] * kin.cosh_dr + r[i] * kin.sinh_dr) continue;  // eta_j - eta_i > dr_min
+      const double deta = asinh(a[i]) - asinh(a[j]);
+      const double cross = qi[1] * qj[2] - qi[2] * qj[1];
+      const double dphi = atan2(fabs(cross), dot);
+      if (!(deta * deta + dphi * dphi > kin.dr_min * kin.dr_min)) return false;
+    }
+  }
+  return true;
+}
+
+// one accepted point for `event`: redraws until the cuts pass (at most kin.max_attempts)
+template <int NEXT>
+__host__ __device__ __forceinline__ bool generate_point(const KinDev& kin, uint64_t seed, uint64_t event,
+                                                        double (&p)[NEXT][4], double& wps, double& shat,
+                                                        int& tries) {
+  for (int att = 0; att < kin.max_attempts; ++att) {
+    bool ok;
+    if (kin.kind == ME_PS_TWO_BODY) {
+      double u[4];
+      draw_uniforms<1>(seed, event, (uint64_t)att, u);
+      ok = gen_two_body<NEXT>(kin, u, p, wps, shat);
+    } else if (kin.kind == ME_PS_RAMBO) {
+      double u[4 * (NEXT - 2)];
+      draw_uniforms<NEXT - 2>(seed, event, (uint64_t)att, u);
+      ok = gen_rambo<NEXT>(kin, u, p, wps, shat);
+    } else {
+      double u[16];
+      draw_uniforms<4>(seed, event, (uint64_t)att, u);
+      ok = gen_ttbar<NEXT>(kin, u, p, wps, shat);
+    }
+    if (ok && pass_cuts<NEXT>(kin, p)) {
+      tries = att + 1;
+      return true;
+    }
+  }
+  tries = kin.max_attempts;
+  wps = 0.0;
+  return false;
+}
+
+}  // namespace me

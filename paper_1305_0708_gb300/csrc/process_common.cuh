@@ -1,0 +1,138 @@
+// Kernels shared by every generated process unit.
+//
+//   k_eval : one event per thread, momenta read coalesced from the
+//            structure-of-arrays buffer into registers, |M|^2 written out.
+//   k_xsec : the fused hot path of one Monte Carlo step: per thread, draw and
+//            cut a phase-space point (FP64), evaluate |M|^2, form the weight
+//            and accumulate (sum w, sum w^2, tries); per block a fixed-order
+//            shuffle + shared-memory reduction writes one partial per block,
+//            so the totals are deterministic for a given launch shape.
+// Both use a grid-stride loop over a grid sized in multiples of the SM count.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "heget.cuh"
+#include "me_internal.h"
+#include "phasespace.cuh"
+
+// 1/(a + i b) formed in FP64 (a, b carry the cancellation-prone q^2 - m^2);
+// the mixed path rounds the FP64 pair to FP32 first and inverts in FP32.
+template <class R>
+__host__ __device__ __forceinline__ me::cx<R> inv_den(double a, double b);
+template <>
+__host__ __device__ __forceinline__ me::cx<double> inv_den<double>(double a, double b) {
+  const double d = 1.0 / (a * a + b * b);
+  return me::mk(a * d, -b * d);
+}
+template <>
+__host__ __device__ __forceinline__ me::cx<float> inv_den<float>(double a, double b) {
+  const float fa = (float)a, fb = (float)b;
+  const float d = 1.0f / (fa * fa + fb * fb);
+  return me::mk(fa * d, -fb * d);
+}
+
+namespace me {
+constexpr double kGeV2pb = 0.3893793721e9;
+
+// fixed-order block sum of three doubles into out[blockIdx.x * 3 + {0,1,2}]
+__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* out) {
+  __shared__ double sm[3][kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { sm[0][warp] = a; sm[1][warp] = b; sm[2][warp] = c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int w = 0; w < kThreads / 32; ++w) { s0 += sm[0][w]; s1 += sm[1][w]; s2 += sm[2][w]; }
+    out[3 * blockIdx.x + 0] = s0;
+    out[3 * blockIdx.x + 1] = s1;
+    out[3 * blockIdx.x + 2] = s2;
+  }
+}
+}  // namespace me
+
+#define ME_DEFINE_PROCESS(TAG, NEXT, NPARAM)                                                                      \
+  namespace me {                                                                                                  \
+  namespace TAG {                                                                                                 \
+  static Params unpack(const double* v) {                                                                         \
+    Params p;                                                                                                     \
+    static_assert(sizeof(Params) == NPARAM * sizeof(double), "parameter block");                                   \
+    double* d = reinterpret_cast<double*>(&p);                                                                    \
+    for (int k = 0; k < NPARAM; ++k) d[k] = v[k];                                                                 \
+    return p;                                                                                                     \
+  }                                                                                                               \
+  template <class R>                                                                                              \
+  __global__ void __launch_bounds__(kThreads) k_eval(const double* __restrict__ mom, int64_t n,                  \
+                                                     double* __restrict__ out, Params prm) {                      \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) { \
+      double pm[NEXT][4];                                                                                         \
+      _Pragma("unroll") for (int k = 0; k < NEXT; ++k) {                                                          \
+        _Pragma("unroll") for (int m = 0; m < 4; ++m) pm[k][m] = __ldg(mom + ((int64_t)(k * 4 + m)) * n + i);     \
+      }                                                                                                           \
+      out[i] = eval_event<R>(pm, prm);                                                                            \
+    }                                                                                                             \
+  }                                                                                                               \
+  template <class R>                                                                                              \
+  __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, uint64_t offset, int64_t n,       \
+                                                     Params prm, double* __restrict__ partials,                   \
+                                                     double* __restrict__ me2_out, double* __restrict__ mom_out,  \
+                                                     double* __restrict__ wps_out, double* __restrict__ shat_out, \
+                                                     int32_t* __restrict__ tries_out, int* status, int eval_me) { \
+    double sw = 0.0, sw2 = 0.0, nt = 0.0;                                                                         \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) { \
+      double pm[NEXT][4];                                                                                         \
+      double wps = 0.0, shat = 1.0;                                                                               \
+      int tries = 0;                                                                                              \
+      const bool ok = generate_point<NEXT>(kin, seed, offset + (uint64_t)i, pm, wps, shat, tries);                \
+      if (!ok) atomicOr(status, 1);                                                                               \
+      double m2 = 0.0;                                                                                            \
+      if (eval_me && ok) m2 = eval_event<R>(pm, prm);                                                             \
+      const double w = ok ? wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb : 0.0;                               \
+      sw += w;                                                                                                    \
+      sw2 += w * w;                                                                                               \
+      nt += (double)tries;                                                                                        \
+      if (me2_out) me2_out[i] = m2;                                                                               \
+      if (wps_out) wps_out[i] = wps;                                                                              \
+      if (shat_out) shat_out[i] = shat;                                                                           \
+      if (tries_out) tries_out[i] = tries;                                                                        \
+      if (mom_out) {                                                                                              \
+        _Pragma("unroll") for (int k = 0; k < NEXT; ++k) {                                                        \
+          _Pragma("unroll") for (int m = 0; m < 4; ++m) mom_out[((int64_t)(k * 4 + m)) * n + i] = pm[k][m];       \
+        }                                                                                                         \
+      }                                                                                                           \
+    }                                                                                                             \
+    if (partials) block_reduce3(sw, sw2, nt, partials);                                                           \
+  }                                                                                                               \
+  static cudaError_t launch_eval(int prec, const double* mom, int64_t n, double* out, const double* params,        \
+                                 cudaStream_t s, int grid) {                                                      \
+    Params prm = unpack(params);                                                                                  \
+    if (prec == ME_FP64) k_eval<double><<<grid, kThreads, 0, s>>>(mom, n, out, prm);                              \
+    else k_eval<float><<<grid, kThreads, 0, s>>>(mom, n, out, prm);                                               \
+    return cudaGetLastError();                                                                                    \
+  }                                                                                                               \
+  static cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t n,          \
+                                 const double* params, double* partials, double* me2_out, double* mom_out,        \
+                                 double* wps_out, double* shat_out, int32_t* tries_out, int* status, int eval_me, \
+                                 cudaStream_t s, int grid) {                                                      \
+    Params prm = unpack(params);                                                                                  \
+    if (prec == ME_FP64)                                                                                          \
+      k_xsec<double><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, prm, partials, me2_out, mom_out, wps_out,   \
+                                                shat_out, tries_out, status, eval_me);                            \
+    else                                                                                                          \
+      k_xsec<float><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, prm, partials, me2_out, mom_out, wps_out,    \
+                                               shat_out, tries_out, status, eval_me);                             \
+    return cudaGetLastError();                                                                                    \
+  }                                                                                                               \
+  }                                                                                                               \
+  }                                                                                                               \
+  extern "C" void me_register_##TAG(me::ProcessDesc* d) {                                                        \
+    d->n_ext = NEXT;                                                                                              \
+    d->launch_eval = me::TAG::launch_eval;                                                                        \
+    d->launch_xsec = me::TAG::launch_xsec;                                                                        \
+  }

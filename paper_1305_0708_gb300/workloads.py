@@ -1,0 +1,38 @@
+"""The benchmark workloads: process, phase-space generator, cuts, size, seed.
+
+Each entry mirrors one workload configuration: the process string compiled
+into the library, the me_kin fields of its generator and cuts, the number of
+accepted points and the seed.  The oracle tests read the same numbers and
+pass them to the oracle's own generator.
+"""
+import math
+
+WORKLOADS = {
+    "uux_epem": dict(
+        process="u u~ > e+ e-", kind="two_body", sqrt_s=500.0, n=65536, seed=0, cuts=None, s_ident=1.0,
+        describe="u u~ > e+ e- via photon and Z, sqrt(s)=500 GeV, cos(theta) and phi uniform, 65,536 points, seed 0"),
+    "udx_epvegg": dict(
+        process="u d~ > e+ ve g g", kind="rambo", sqrt_s=1000.0, n=1 << 20, seed=1,
+        cuts=dict(legs=(2, 4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,
+        describe="u d~ > e+ ve g g (W+ -> e+ ve plus two gluons), RAMBO at sqrt(s)=1 TeV, pT>20, |eta|<2.5, "
+                 "DeltaR>0.4 on g, g, e+, 2^20 accepted points, seed 1"),
+    "gg_ttx_dilep": dict(
+        process="g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))", kind="ttbar", sqrt_s_range=(400.0, 2000.0),
+        n=1 << 20, seed=2, cuts=None, s_ident=1.0,
+        describe="g g > t t~ > b e+ ve b~ e- ve~, sqrt(s) uniform in [400, 2000] GeV, Breit-Wigner t and W, "
+                 "isotropic decays, 2^20 points, seed 2"),
+    "us_dchh": dict(
+        process="u s > d c h h", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 0, 0, 125.0, 125.0), n=1 << 18, seed=4,
+        cuts=None, s_ident=0.5,
+        describe="u s > d c h h (W+ W- fusion), massive RAMBO at sqrt(s)=1 TeV, 2^18 points, seed 4"),
+}
+
+KIND = {"two_body": 0, "rambo": 1, "ttbar": 2}
+
+
+def kin_args(w):
+    """Keyword arguments for binding.make_kin for a workload."""
+    cut = w.get("cuts") or {}
+    return dict(kind=KIND[w["kind"]], sqrt_s=w.get("sqrt_s", 0.0), sqrt_s_range=w.get("sqrt_s_range", (0.0, 0.0)),
+                masses=w.get("masses", ()), cut_legs=cut.get("legs", ()), pt_min=cut.get("pt_min", 0.0),
+                eta_max=cut.get("eta_max", 0.0), dr_min=cut.get("dr_min", 0.0), s_ident=w["s_ident"])
