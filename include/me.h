@@ -140,6 +140,31 @@ me_status me_generate(me_handle h, uint64_t seed, uint64_t counter_offset, int64
 me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept, const me_kin *kin,
                     void *stream, me_xsec_acc *acc, double *me2_out, double *momenta_out);
 
+/* xsec_step for callers that cannot allocate device memory: the same
+ * computation and arguments, but the step's scratch (per-block partial sums,
+ * totals, status flag) lives in a fixed array compiled into the library
+ * instead of memory the library would cudaMalloc.  Such callers include code
+ * running inside a host application that owns all device memory through its
+ * own pool or arena, or that forbids allocations after start-up; cudaMalloc
+ * there either fails or breaks the owner's accounting.  This entry point calls
+ * no cudaMalloc, cudaFree or allocating library routine.  (It has no
+ * counterpart in the paper; it exists for embedding.)
+ *  - Limit: the fused kernel's grid (at most 8 blocks per SM) must fit the
+ *    scratch's 4096 partial slots; larger launches are rejected with
+ *    ME_ERR_ARG.  The array occupies about 100 KB on every GPU that loads the
+ *    library, until the process exits.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture.
+ *  - Every call shares the one array: calls whose work overlaps on the GPU (on
+ *    different streams, or from several threads) race and corrupt each other's
+ *    sums.  Serialise them.  The array keeps the previous call's contents; the
+ *    call clears the status flag itself and overwrites the rest.
+ *  - me2_out, momenta_out: optional device outputs as in xsec_step.
+ * Synchronises stream before returning. */
+me_status xsec_step_noalloc(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept,
+                            const me_kin *kin, void *stream, me_xsec_acc *acc, double *me2_out,
+                            double *momenta_out);
+
 /* sigma-hat = sum_w / n_try and its standard error (pb) from an accumulator. */
 me_status me_xsec_estimate(const me_xsec_acc *acc, double *sigma, double *error);
 

@@ -46,7 +46,7 @@ class me_info_t(ctypes.Structure):
 ME_FP64, ME_MIXED = 0, 1
 ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR = 0, 1, 2
 
-EXPORTS = ["me_create", "me_eval", "me_generate", "xsec_step", "me_xsec_estimate", "me_info", "me_n_processes",
+EXPORTS = ["me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_xsec_estimate", "me_info", "me_n_processes",
            "me_process_name", "me_destroy", "me_last_error"]
 
 
@@ -68,6 +68,8 @@ def load(path=None):
     L.me_eval.argtypes = [vp, vp, i64, vp, vp]
     L.me_generate.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, vp, vp, vp, vp]
     L.xsec_step.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc), vp, vp]
+    L.xsec_step_noalloc.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc),
+                                    vp, vp]
     L.me_xsec_estimate.argtypes = [ctypes.POINTER(me_xsec_acc), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]
     L.me_info.argtypes = [vp, ctypes.POINTER(me_info_t)]
@@ -77,7 +79,8 @@ def load(path=None):
     L.me_destroy.argtypes = [vp]
     L.me_destroy.restype = None
     L.me_last_error.restype = ctypes.c_char_p
-    for fn in ("me_create", "me_eval", "me_generate", "xsec_step", "me_xsec_estimate", "me_info"):
+    for fn in ("me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_xsec_estimate",
+               "me_info"):
         getattr(L, fn).restype = ctypes.c_int
     _LIB = L
     return L
@@ -149,6 +152,15 @@ def xsec_step(h, seed, counter_offset, n_accept, kin, stream=None, acc=None, me2
     acc = acc if acc is not None else me_xsec_acc()
     _check(load().xsec_step(h, seed, counter_offset, n_accept, ctypes.byref(kin), _stream(stream),
                             ctypes.byref(acc), _ptr(me2_out), _ptr(momenta_out)))
+    return acc
+
+
+def xsec_step_noalloc(h, seed, counter_offset, n_accept, kin, stream=None, acc=None, me2_out=None,
+                      momenta_out=None):
+    """xsec_step without device allocations (scratch in a static device array; see include/me.h)."""
+    acc = acc if acc is not None else me_xsec_acc()
+    _check(load().xsec_step_noalloc(h, seed, counter_offset, n_accept, ctypes.byref(kin), _stream(stream),
+                                    ctypes.byref(acc), _ptr(me2_out), _ptr(momenta_out)))
     return acc
 
 

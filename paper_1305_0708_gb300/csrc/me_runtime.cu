@@ -233,6 +233,45 @@ me_status check_handle(me_handle h) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Scratch of xsec_step_noalloc: a file-scope device array, so that callers that
+// must not allocate device memory can still run a Monte Carlo step.  Every GPU
+// that loads this library holds it (about 100 KB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 4096;  // one partial (3 doubles) per block of the fused kernel
+
+struct NoAllocScratch {
+  double partials[kNoAllocMaxBlocks * 3];
+  double acc[4];
+  int status;
+};
+
+__device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device.  Host code may
+// not use &g_noalloc_scratch (that is a host-side stand-in); the address is
+// looked up once per device, with that device current.
+me_status noalloc_scratch(int device, NoAllocScratch** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(ME_ERR_ARG, "xsec_step_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    g_noalloc_ptr[device] = static_cast<NoAllocScratch*>(ptr);
+  }
+  *out = g_noalloc_ptr[device];
+  return ME_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int32_t me_n_processes(void) { return me::registry_size(); }
@@ -335,6 +374,48 @@ me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t
   acc->sum_w2 += h->h_acc[1];
   acc->n_acc += n_accept;
   acc->n_try += (int64_t)llround(h->h_acc[2]);
+  return ME_OK;
+}
+
+me_status xsec_step_noalloc(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept,
+                            const me_kin* kin, void* stream, me_xsec_acc* acc, double* me2_out,
+                            double* momenta_out) {
+  me_status st = check_handle(h);
+  if (st != ME_OK) return st;
+  if (!kin || !acc) return fail(ME_ERR_ARG, "xsec_step_noalloc: null argument");
+  if (n_accept < 0) return fail(ME_ERR_ARG, "xsec_step_noalloc: n_accept < 0");
+  me::KinDev k;
+  if ((st = make_kin(h, kin, k)) != ME_OK) return st;
+  if (n_accept == 0) return ME_OK;
+  const int grid = grid_for(h, n_accept);
+  if (grid > kNoAllocMaxBlocks)
+    return fail(ME_ERR_ARG, "xsec_step_noalloc: launch needs " + std::to_string(grid) +
+                                " blocks, beyond the static scratch maximum of " + std::to_string(kNoAllocMaxBlocks));
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  NoAllocScratch* scr = nullptr;
+  if ((st = noalloc_scratch(device, &scr)) != ME_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the status flag keeps the previous call's value: clear it; partials and totals are overwritten
+  if ((e = cudaMemsetAsync(&scr->status, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  e = h->desc->launch_xsec(h->prec, &k, seed, counter_offset, n_accept, h->cvals.data(), scr->partials, me2_out,
+                           momenta_out, nullptr, nullptr, nullptr, &scr->status, 1, s, grid);
+  if (e != cudaSuccess) return cuda_fail(e, "xsec_step_noalloc launch");
+  k_reduce_partials<<<1, 256, 0, s>>>(scr->partials, grid, scr->acc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "xsec_step_noalloc reduce");
+  double tot[3];
+  int status = 0;
+  if ((e = cudaMemcpyAsync(tot, scr->acc, sizeof(tot), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "xsec_step_noalloc copy");
+  if ((e = cudaMemcpyAsync(&status, &scr->status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "xsec_step_noalloc copy");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "xsec_step_noalloc sync");
+  if (status) return fail(ME_ERR_TIMEOUT, "xsec_step_noalloc: a point exhausted its phase-space redraws");
+  acc->sum_w += tot[0];
+  acc->sum_w2 += tot[1];
+  acc->n_acc += n_accept;
+  acc->n_try += (int64_t)llround(tot[2]);
   return ME_OK;
 }
 
