@@ -21,8 +21,10 @@ Functions and their pins (tests/test_oracle_processes.py):
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
   gg_ttx_dilep    g g > t t~ > b e+ ve b~ e- ve~ (doubly resonant diagrams):
                    Ward identity (zero widths), Bose symmetry, boosts
-  us_dchh         u s > d c h h  (WW fusion): boosts; parity unpinned beyond
-                   invariants (no external gauge boson, no closed form)
+  us_dchh         u s > d c h h  (WW fusion): Higgs-exchange symmetry, boosts;
+                   its W current is pinned by u d~ > e+ ve, its WWH/WWHH/HHH
+                   couplings and diagram set by the gauge cancellation of the
+                   longitudinal W+ W- > h h amplitude (wpwm_hh_amplitudes)
   gluons          g g > g...g    : Berends-Giele, pinned by the gg > gg closed
                    form, Parke-Taylor MHV amplitudes, Ward, Bose, boosts
 """
@@ -359,6 +361,28 @@ def us_dchh(P, par=SMParams(), per_helicity=False):
         tot = tot + m2
     avg = tot / 36.0
     return (avg, ph) if per_helicity else avg
+
+
+# --------------------------------------------------------------------------
+# W+ W- > h h with on-shell external W bosons (gauge-cancellation pin of the
+# WWH / WWHH / HHH couplings used by u s > d c h h)
+# --------------------------------------------------------------------------
+def wpwm_hh_amplitudes(P, hel, par=SMParams()):
+    """The four diagrams of W+(p0) W-(p1) > h(p2) h(p3) for fixed W helicities,
+    returned separately (contact, s-channel H, t- and u-channel W) as M values."""
+    p = [P[:, k] for k in range(4)]
+    g, mW, wW, mH, wH, v = par.g, par.mW, par.wW, par.mH, par.wH, par.vev
+    gwwh, gwwhh, ghhh = g * mW, g * g / 2.0, -3.0 * mH * mH / v
+    e0 = polarisation(p[0], hel[0], mass=mW)
+    e1 = polarisation(p[1], hel[1], mass=mW)
+    e01 = mdot(e0, e1)
+    out = [gwwhh * e01 * 1j,
+           (1j * gwwh * e01) * scalar_prop(p[0] + p[1], mH, wH) * (1j * ghhh)]
+    for hA in (2, 3):
+        k = p[0] - p[hA]
+        Wst = vector_prop(k, 1j * gwwh * e0, mW, wW)
+        out.append(1j * gwwh * mdot(Wst, e1))
+    return [x / 1j for x in out]
 
 
 # --------------------------------------------------------------------------

@@ -276,3 +276,35 @@ def test_us_dchh_positive_and_finite():
     assert np.all(np.isfinite(m2)) and np.all(m2 > 0)
     # symmetric under exchange of the two Higgs bosons
     assert np.allclose(pr.us_dchh(P[:, [0, 1, 2, 3, 5, 4]]), m2, rtol=1e-12)
+
+
+def _ww_hh_point(par, w, c=0.3, phi=0.7):
+    E = w / 2
+    pw = math.sqrt(E * E - par.mW ** 2)
+    ph = math.sqrt(E * E - par.mH ** 2)
+    s = math.sqrt(1 - c * c)
+    P = np.zeros((1, 4, 4))
+    P[0, 0] = [E, 0, 0, pw]
+    P[0, 1] = [E, 0, 0, -pw]
+    P[0, 2] = [E, ph * s * math.cos(phi), ph * s * math.sin(phi), ph * c]
+    P[0, 3] = [E, -P[0, 2, 1], -P[0, 2, 2], -P[0, 2, 3]]
+    return P
+
+
+def test_ww_hh_gauge_cancellation():
+    """W_L W_L > h h: each diagram grows like s/mW^2, their sum tends to a finite
+    constant (the Goldstone-boson amplitude of the equivalence theorem) only when the
+    couplings g mW, g^2/2 and -3 mH^2/v and the unitary-gauge propagator are mutually
+    consistent; a 10% error in any of them leaves a sum growing like s.  Zero W width:
+    a fixed width in the t-channel W propagator spoils the cancellation (the effect the
+    paper discusses for multi-Higgs production)."""
+    par0 = PAR.with_(wW=0.0)
+    vals = []
+    for w in (1e4, 1e5, 1e6):
+        amps = pr.wpwm_hh_amplitudes(_ww_hh_point(par0, w), (0, 0), par0)
+        tot = sum(amps)[0]
+        big = max(abs(a[0]) for a in amps)
+        assert abs(tot) < 1e-3 * big or w == 1e4
+        vals.append(tot)
+    assert abs(vals[-1] / vals[-2] - 1) < 0.01
+    assert abs(vals[-1]) < 10.0
