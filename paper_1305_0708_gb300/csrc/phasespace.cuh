@@ -261,35 +261,68 @@ __host__ __device__ __forceinline__ bool gen_ttbar(const KinDev& kin, const doub
 
 // ---------------------------------------------------------------------------
 // cuts: pT > pt_min, |eta| < eta_max, Delta R > dr_min over kin.cut_legs.
-// |eta| < eta_max  <=>  |pz| < sinh(eta_max) pT.  A pair is separated when
-// its azimuthal or its pseudorapidity distance alone exceeds dr_min (both
-// tested without transcendentals); only the remaining close pairs evaluate
-// Delta R = sqrt(d_eta^2 + d_phi^2) with asinh and atan2.
+// pT and |eta| (as |pz| < sinh(eta_max) pT) are exact FP64 comparisons.  A pair
+// is separated when its azimuthal or its pseudorapidity distance alone exceeds
+// dr_min; both tests run first in FP32 and decide only outside a 1e-5 relative
+// guard band around the boundary (FP32 rounding here is below 1e-6), else the
+// same test runs in FP64.  Only pairs close in both evaluate Delta R with asinh
+// and atan2 in FP64.  The decision therefore equals the FP64 one.
 // ---------------------------------------------------------------------------
+// returns +1 (certainly x > y), -1 (certainly x < y) or 0 (undecided) for float estimates
+__host__ __device__ __forceinline__ int fcmp(float x, float y, float scale) {
+  const float band = 1e-5f * scale;
+  if (x > y + band) return 1;
+  if (x < y - band) return -1;
+  return 0;
+}
+
 template <int NEXT>
 __host__ __device__ __forceinline__ bool pass_cuts(const KinDev& kin, const double (&p)[NEXT][4]) {
   const int nl = kin.n_cut_legs;
   if (nl == 0) return true;
-  double pt2[8], a[8], r[8];
+  double pt2[8];
+  float ptf[8], af[8], rf[8];
   for (int i = 0; i < nl; ++i) {
     const double* q = p[kin.cut_legs[i]];
     pt2[i] = q[1] * q[1] + q[2] * q[2];
     if (!(pt2[i] > kin.pt_min * kin.pt_min)) return false;
     if (!(q[3] * q[3] < kin.sinh2_eta_max * pt2[i])) return false;
-    const double ipt = 1.0 / sqrt(pt2[i]);
-    a[i] = q[3] * ipt;                                        // sinh(eta)
-    r[i] = sqrt(pt2[i] + q[3] * q[3]) * ipt;                  // cosh(eta)
+    const float p2f = (float)pt2[i], zf = (float)q[3];
+    ptf[i] = sqrtf(p2f);
+    const float ip = 1.0f / ptf[i];
+    af[i] = zf * ip;                          // sinh(eta)
+    rf[i] = sqrtf(p2f + zf * zf) * ip;        // cosh(eta)
   }
+  const float cdr = (float)kin.cos_dr, chd = (float)kin.cosh_dr, shd = (float)kin.sinh_dr;
   for (int i = 0; i < nl; ++i) {
     for (int j = i + 1; j < nl; ++j) {
       const double* qi = p[kin.cut_legs[i]];
       const double* qj = p[kin.cut_legs[j]];
+      // |d_phi| > dr_min  <=>  pT_i . pT_j < cos(dr_min) |pT_i| |pT_j|
+      const float dotf = (float)qi[1] * (float)qj[1] + (float)qi[2] * (float)qj[2];
+      const float ptijf = ptf[i] * ptf[j];
+      int c = fcmp(dotf, cdr * ptijf, ptijf);
+      if (c == 0) {
+        const double dot = qi[1] * qj[1] + qi[2] * qj[2];
+        c = dot < kin.cos_dr * sqrt(pt2[i] * pt2[j]) ? -1 : 1;
+      }
+      if (c < 0) continue;
+      // eta_i - eta_j > dr_min  <=>  sinh(eta_i) > sinh(eta_j) cosh(dr) + cosh(eta_j) sinh(dr), and i <-> j
+      const float sc = fabsf(af[i]) + fabsf(af[j]) + rf[i] + rf[j];
+      int e1 = fcmp(af[i], af[j] * chd + rf[j] * shd, sc);
+      int e2 = fcmp(af[j], af[i] * chd + rf[i] * shd, sc);
+      if (e1 == 0 || e2 == 0) {
+        const double ipi = 1.0 / sqrt(pt2[i]), ipj = 1.0 / sqrt(pt2[j]);
+        const double ai = qi[3] * ipi, aj = qj[3] * ipj;
+        const double ri = sqrt(pt2[i] + qi[3] * qi[3]) * ipi, rj = sqrt(pt2[j] + qj[3] * qj[3]) * ipj;
+        e1 = ai > aj * kin.cosh_dr + rj * kin.sinh_dr ? 1 : -1;
+        e2 = aj > ai * kin.cosh_dr + ri * kin.sinh_dr ? 1 : -1;
+      }
+      if (e1 > 0 || e2 > 0) continue;
+      // close in both: Delta R^2 = d_eta^2 + d_phi^2 in FP64
+      const double ipi = 1.0 / sqrt(pt2[i]), ipj = 1.0 / sqrt(pt2[j]);
+      const double deta = asinh(qi[3] * ipi) - asinh(qj[3] * ipj);
       const double dot = qi[1] * qj[1] + qi[2] * qj[2];
-      const double ptij = sqrt(pt2[i] * pt2[j]);
-      if (dot < kin.cos_dr * ptij) continue;                   // |d_phi| > dr_min
-      if (a[i] > a[j] * kin.cosh_dr + r[j] * kin.sinh_dr) continue;  // eta_i - eta_j > dr_min
-      if (a[j] > a[i] * kin.cosh_dr + r[i] * kin.sinh_dr) continue;  // eta_j - eta_i > dr_min
-      const double deta = asinh(a[i]) - asinh(a[j]);
       const double cross = qi[1] * qj[2] - qi[2] * qj[1];
       const double dphi = atan2(fabs(cross), dot);
       if (!(deta * deta + dphi * dphi > kin.dr_min * kin.dr_min)) return false;
@@ -298,34 +331,25 @@ __host__ __device__ __forceinline__ bool pass_cuts(const KinDev& kin, const doub
   return true;
 }
 
-// one accepted point for `event`: redraws until the cuts pass (at most kin.max_attempts)
+// one draw (attempt `att`) for `event`: false if outside the kinematic limits or the cuts
 template <int NEXT>
-__host__ __device__ __forceinline__ bool generate_point(const KinDev& kin, uint64_t seed, uint64_t event,
-                                                        double (&p)[NEXT][4], double& wps, double& shat,
-                                                        int& tries) {
-  for (int att = 0; att < kin.max_attempts; ++att) {
-    bool ok;
-    if (kin.kind == ME_PS_TWO_BODY) {
-      double u[4];
-      draw_uniforms<1>(seed, event, (uint64_t)att, u);
-      ok = gen_two_body<NEXT>(kin, u, p, wps, shat);
-    } else if (kin.kind == ME_PS_RAMBO) {
-      double u[4 * (NEXT - 2)];
-      draw_uniforms<NEXT - 2>(seed, event, (uint64_t)att, u);
-      ok = gen_rambo<NEXT>(kin, u, p, wps, shat);
-    } else {
-      double u[16];
-      draw_uniforms<4>(seed, event, (uint64_t)att, u);
-      ok = gen_ttbar<NEXT>(kin, u, p, wps, shat);
-    }
-    if (ok && pass_cuts<NEXT>(kin, p)) {
-      tries = att + 1;
-      return true;
-    }
+__host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t seed, uint64_t event, int att,
+                                                    double (&p)[NEXT][4], double& wps, double& shat) {
+  bool ok;
+  if (kin.kind == ME_PS_TWO_BODY) {
+    double u[4];
+    draw_uniforms<1>(seed, event, (uint64_t)att, u);
+    ok = gen_two_body<NEXT>(kin, u, p, wps, shat);
+  } else if (kin.kind == ME_PS_RAMBO) {
+    double u[4 * (NEXT - 2)];
+    draw_uniforms<NEXT - 2>(seed, event, (uint64_t)att, u);
+    ok = gen_rambo<NEXT>(kin, u, p, wps, shat);
+  } else {
+    double u[16];
+    draw_uniforms<4>(seed, event, (uint64_t)att, u);
+    ok = gen_ttbar<NEXT>(kin, u, p, wps, shat);
   }
-  tries = kin.max_attempts;
-  wps = 0.0;
-  return false;
+  return ok && pass_cuts<NEXT>(kin, p);
 }
 
 }  // namespace me

@@ -2,11 +2,16 @@
 //
 //   k_eval : one event per thread, momenta read coalesced from the
 //            structure-of-arrays buffer into registers, |M|^2 written out.
-//   k_xsec : the fused hot path of one Monte Carlo step: per thread, draw and
-//            cut a phase-space point (FP64), evaluate |M|^2, form the weight
-//            and accumulate (sum w, sum w^2, tries); per block a fixed-order
-//            shuffle + shared-memory reduction writes one partial per block,
-//            so the totals are deterministic for a given launch shape.
+//   k_xsec : the fused hot path of one Monte Carlo step, per tile of kThreads
+//            points: (1) phase space with redraws through a shared-memory work
+//            queue -- round r draws attempt r for every point still open, the
+//            failures are compacted into the next round's queue, so warps stay
+//            full instead of idling while single lanes redraw; accepted momenta
+//            land in shared memory; (2) every thread evaluates |M|^2 of its own
+//            point, forms the weight and accumulates (sum w, sum w^2, tries);
+//            per block a fixed-order shuffle + shared-memory reduction writes one
+//            partial, so the totals are deterministic for a given launch shape.
+//            Each point's draws depend only on (seed, event, attempt).
 // Both use a grid-stride loop over a grid sized in multiples of the SM count.
 #pragma once
 #include <cstdint>
@@ -84,28 +89,75 @@ __device__ __forceinline__ void block_reduce3(double a, double b, double c, doub
                                                      double* __restrict__ me2_out, double* __restrict__ mom_out,  \
                                                      double* __restrict__ wps_out, double* __restrict__ shat_out, \
                                                      int32_t* __restrict__ tries_out, int* status, int eval_me) { \
+    __shared__ double s_p[NEXT * 4][kThreads];                                                                    \
+    __shared__ double s_wps[kThreads], s_shat[kThreads];                                                          \
+    __shared__ int s_tries[kThreads];                                                                             \
+    __shared__ int s_q[2][kThreads];                                                                              \
+    __shared__ int s_qn[2];                                                                                       \
     double sw = 0.0, sw2 = 0.0, nt = 0.0;                                                                         \
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) { \
-      double pm[NEXT][4];                                                                                         \
-      double wps = 0.0, shat = 1.0;                                                                               \
-      int tries = 0;                                                                                              \
-      const bool ok = generate_point<NEXT>(kin, seed, offset + (uint64_t)i, pm, wps, shat, tries);                \
-      if (!ok) atomicOr(status, 1);                                                                               \
-      double m2 = 0.0;                                                                                            \
-      if (eval_me && ok) m2 = eval_event<R>(pm, prm);                                                             \
-      const double w = ok ? wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb : 0.0;                               \
-      sw += w;                                                                                                    \
-      sw2 += w * w;                                                                                               \
-      nt += (double)tries;                                                                                        \
-      if (me2_out) me2_out[i] = m2;                                                                               \
-      if (wps_out) wps_out[i] = wps;                                                                              \
-      if (shat_out) shat_out[i] = shat;                                                                           \
-      if (tries_out) tries_out[i] = tries;                                                                        \
-      if (mom_out) {                                                                                              \
+    const int64_t ntiles = (n + kThreads - 1) / kThreads;                                                         \
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {                                           \
+      const int64_t base = tile * kThreads;                                                                       \
+      const int cnt = (int)((n - base) < kThreads ? (n - base) : kThreads);                                       \
+      if (threadIdx.x == 0) { s_qn[0] = 0; s_qn[1] = 0; }                                                         \
+      if (threadIdx.x < cnt) { s_wps[threadIdx.x] = 0.0; s_tries[threadIdx.x] = kin.max_attempts; }               \
+      __syncthreads();                                                                                            \
+      int cur = 0;                                                                                                \
+      for (int att = 0;; ++att) {                                                                                 \
+        const int nitems = (att == 0) ? cnt : s_qn[cur];                                                          \
+        if (nitems == 0) break;                                                                                   \
+        if (att >= kin.max_attempts) {                                                                            \
+          if (threadIdx.x == 0) atomicOr(status, 1);                                                              \
+          break;                                                                                                  \
+        }                                                                                                         \
+        const int nxt = cur ^ 1;                                                                                  \
+        for (int j = threadIdx.x; j < nitems; j += kThreads) {                                                    \
+          const int ev = (att == 0) ? j : s_q[cur][j];                                                            \
+          double pm[NEXT][4];                                                                                     \
+          double wps = 0.0, shat = 1.0;                                                                           \
+          if (draw_point<NEXT>(kin, seed, offset + (uint64_t)(base + ev), att, pm, wps, shat)) {                  \
+            _Pragma("unroll") for (int k = 0; k < NEXT; ++k) {                                                    \
+              _Pragma("unroll") for (int m = 0; m < 4; ++m) s_p[k * 4 + m][ev] = pm[k][m];                        \
+            }                                                                                                     \
+            s_wps[ev] = wps;                                                                                      \
+            s_shat[ev] = shat;                                                                                    \
+            s_tries[ev] = att + 1;                                                                                \
+          } else {                                                                                                \
+            s_q[nxt][atomicAdd(&s_qn[nxt], 1)] = ev;                                                              \
+          }                                                                                                       \
+        }                                                                                                         \
+        __syncthreads();                                                                                          \
+        if (threadIdx.x == 0) s_qn[cur] = 0;                                                                      \
+        cur = nxt;                                                                                                \
+        __syncthreads();                                                                                          \
+      }                                                                                                           \
+      if (threadIdx.x < cnt) {                                                                                    \
+        const int ev = threadIdx.x;                                                                               \
+        const int64_t i = base + ev;                                                                              \
+        double pm[NEXT][4];                                                                                       \
         _Pragma("unroll") for (int k = 0; k < NEXT; ++k) {                                                        \
-          _Pragma("unroll") for (int m = 0; m < 4; ++m) mom_out[((int64_t)(k * 4 + m)) * n + i] = pm[k][m];       \
+          _Pragma("unroll") for (int m = 0; m < 4; ++m) pm[k][m] = s_p[k * 4 + m][ev];                            \
+        }                                                                                                         \
+        const double wps = s_wps[ev], shat = s_shat[ev];                                                          \
+        const int tries = s_tries[ev];                                                                            \
+        const bool ok = wps > 0.0;                                                                                \
+        double m2 = 0.0;                                                                                          \
+        if (eval_me && ok) m2 = eval_event<R>(pm, prm);                                                           \
+        const double w = ok ? wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb : 0.0;                             \
+        sw += w;                                                                                                  \
+        sw2 += w * w;                                                                                             \
+        nt += (double)tries;                                                                                      \
+        if (me2_out) me2_out[i] = m2;                                                                             \
+        if (wps_out) wps_out[i] = wps;                                                                            \
+        if (shat_out) shat_out[i] = shat;                                                                         \
+        if (tries_out) tries_out[i] = tries;                                                                      \
+        if (mom_out) {                                                                                            \
+          _Pragma("unroll") for (int k = 0; k < NEXT; ++k) {                                                      \
+            _Pragma("unroll") for (int m = 0; m < 4; ++m) mom_out[((int64_t)(k * 4 + m)) * n + i] = pm[k][m];     \
+          }                                                                                                       \
         }                                                                                                         \
       }                                                                                                           \
+      __syncthreads();                                                                                            \
     }                                                                                                             \
     if (partials) block_reduce3(sw, sw2, nt, partials);                                                           \
   }                                                                                                               \
