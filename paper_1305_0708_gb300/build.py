@@ -34,7 +34,7 @@ PROCESSES = [
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                     "-I", INCLUDE, "-I", CSRC]
+                     "-I", INCLUDE, "-I", CSRC, "-I", GEN]
 STATIC_SOURCES = ["me_runtime.cu"]
 
 
@@ -76,6 +76,13 @@ def generate_units():
                     flops_amp=info["flops_amp"], flops_fp64=info["flops_fp64"],
                     pdg=[PARTICLES[l.particle].pdg for l in prog.legs])
         units.append((tag, path, meta))
+    # double-float tables
+    from paper_1305_0708_gb300.compiler import dftables
+    tpath = os.path.join(GEN, "dfloat_tables.h")
+    tsrc = dftables.header()
+    if not os.path.exists(tpath) or open(tpath).read() != tsrc:
+        with open(tpath, "w") as f:
+            f.write(tsrc)
     # registry
     lines = ['#include "me_internal.h"', "namespace me {"]
     entries = []
@@ -115,7 +122,7 @@ def generate_units():
 
 def _headers_hash():
     parts = []
-    for d in (CSRC, INCLUDE):
+    for d in (CSRC, INCLUDE, GEN):
         for fn in sorted(os.listdir(d)):
             if fn.endswith((".cuh", ".h")):
                 parts.append(open(os.path.join(d, fn), "rb").read())

@@ -45,9 +45,10 @@ def _lit(x):
 
 
 class _Emitter:
-    def __init__(self, prog, tag):
+    def __init__(self, prog, tag, mode="fp64"):
         self.p = prog
         self.tag = tag
+        self.mode = mode          # "fp64": FP64 momenta and amplitudes; "mixed": double-float momenta, FP32
         self.lines = []
         self.flops32 = 0      # amplitude-precision flops per event
         self.flops64 = 0      # FP64 flops per event (momenta, invariants)
@@ -66,23 +67,27 @@ class _Emitter:
         n = p.n_ext
         E = self.emit
         nodes = p.nodes
-        E("  // momenta, FP64")
+        mixed = self.mode == "mixed"
+        E("  // momenta: " + ("double-float (hi, lo) pairs" if mixed else "FP64"))
         for k in range(n):
-            E(f"  const double* p{k} = pm[{k}];")
+            E(f"  const {'me::df' if mixed else 'double'}* p{k} = pm[{k}];")
         used_nodes = sorted(p.node_variants)
         E("  // external momenta in amplitude precision: r = physical, k = flowing into the vertex")
         for nid in used_nodes:
             nd = nodes[nid]
             if nd.external:
                 k = nd.leg
-                E(f"  const me::P4<R> r{nid} = me::p4<R>(p{k});")
+                E(f"  const me::P4<R> r{nid} = {'me::p4f' if mixed else 'me::p4<R>'}(p{k});")
                 if p.legs[k].incoming:
                     E(f"  const me::P4<R> k{nid} = r{nid};")
                 else:
                     E(f"  const me::P4<R> k{nid} = me::neg(r{nid});")
         E("  // internal lines: momentum (into the parent vertex) and reciprocal propagator denominator.")
-        E("  // Massive (resonant) lines form q^2 - m^2 in FP64 from the FP64 momenta; massless lines")
-        E("  // use the amplitude precision.")
+        if mixed:
+            E("  // Massive (resonant) lines form q^2 - m^2 in double-float arithmetic from the double-float")
+            E("  // momenta (no FP64 instructions); massless lines use FP32.")
+        else:
+            E("  // Massive (resonant) lines form q^2 - m^2 in FP64 from the FP64 momenta.")
         for nid in used_nodes:
             nd = nodes[nid]
             if nd.external:
@@ -111,12 +116,29 @@ class _Emitter:
                         else:
                             e += f" {sgn} p{l}[{mu}]"
                     comps.append(e)
-                E(f"  const double Q{nid}[4] = {{{', '.join(comps)}}};")
-                E(f"  const double q2_{nid} = Q{nid}[0] * Q{nid}[0] - Q{nid}[1] * Q{nid}[1] - Q{nid}[2] * Q{nid}[2] - "
-                  f"Q{nid}[3] * Q{nid}[3];")
                 wexpr = f"{m} * {w}" if w else "0.0"
-                E(f"  const me::cx<R> inv{nid} = inv_den<R>(q2_{nid} - {m} * {m}, {wexpr});")
-                self.flops64 += 4 * (len(legs) - 1) + 7 + 3
+                if mixed:
+                    dcomps = []
+                    for mu in range(4):
+                        e = ""
+                        for j, (sgn, l) in enumerate(terms):
+                            if j == 0:
+                                e += ("" if sgn == "+" else "-") + f"p{l}[{mu}]"
+                            else:
+                                e += f" {sgn} p{l}[{mu}]"
+                        dcomps.append(e)
+                    E(f"  const me::df Q{nid}[4] = {{{', '.join(dcomps)}}};")
+                    E(f"  const me::df q2_{nid} = ((me::sqr(Q{nid}[0]) - me::sqr(Q{nid}[1])) - me::sqr(Q{nid}[2])) - "
+                      f"me::sqr(Q{nid}[3]);")
+                    E(f"  const me::cx<R> inv{nid} = inv_den_f(me::to_float(q2_{nid} - me::from_double({m} * {m})), "
+                      f"(float)({wexpr}));")
+                    self.flops32 += 20 * (len(legs) - 1) * 4 + 4 * 8 + 3 * 20 + 20
+                else:
+                    E(f"  const double Q{nid}[4] = {{{', '.join(comps)}}};")
+                    E(f"  const double q2_{nid} = Q{nid}[0] * Q{nid}[0] - Q{nid}[1] * Q{nid}[1] - Q{nid}[2] * Q{nid}[2] - "
+                      f"Q{nid}[3] * Q{nid}[3];")
+                    E(f"  const me::cx<R> inv{nid} = inv_den<R>(q2_{nid} - {m} * {m}, {wexpr});")
+                    self.flops64 += 4 * (len(legs) - 1) + 7 + 3
         # root external node (last leg) appears only as an amplitude child
         E("  // wavefunctions and sub-currents, once per helicity variant")
         for nid in used_nodes:
@@ -341,20 +363,25 @@ def process_symbol(name):
 
 
 def generate_source(prog, tag):
-    """CUDA source for one process: evaluator template + the two launch wrappers."""
-    em = _Emitter(prog, tag)
-    em.generate()
-    body = "\n".join(em.lines)
-    cpl = sorted(em.cpl_names)
+    """CUDA source for one process: the FP64 and mixed evaluators in a traits struct."""
+    em64 = _Emitter(prog, tag, "fp64")
+    em64.generate()
+    emmx = _Emitter(prog, tag, "mixed")
+    emmx.generate()
+    cpl = sorted(em64.cpl_names | emmx.cpl_names)
     masses_for_mc2 = sorted({n for n in cpl if n.startswith("M")})
-    params = "\n".join(f"  double {_ident(n)};" for n in cpl) or "  double unused;"
-    unpack = "\n".join(f"  const double c_{_ident(n)} = prm.{_ident(n)};" for n in cpl)
+    params = "\n".join(f"    double {_ident(n)};" for n in cpl) or "    double unused;"
+    unpack = "\n".join(f"    const double c_{_ident(n)} = prm.{_ident(n)};" for n in cpl)
     mc2 = []
     for mname in masses_for_mc2:
         wname = "W" + mname[1:]
         if wname in cpl:
-            mc2.append(f"  const me::cx<R> inv_mc2_{mname} = inv_den<R>(c_{mname} * c_{mname}, -c_{mname} * c_{wname});")
+            mc2.append(f"    const me::cx<R> inv_mc2_{mname} = inv_den<R>(c_{mname} * c_{mname}, "
+                       f"-c_{mname} * c_{wname});")
     mc2 = "\n".join(mc2)
+    body64 = "\n".join("  " + ln for ln in em64.lines)
+    bodymx = "\n".join("  " + ln for ln in emmx.lines)
+    n = prog.n_ext
     src = f"""// Generated by paper_1305_0708_gb300.compiler for: {prog.name}
 // diagrams: {len(prog.amps)}, live helicities: {len(prog.live)} of {_ncomb(prog)}, colour basis: {prog.n_colour}
 #include "process_common.cuh"
@@ -362,23 +389,35 @@ def generate_source(prog, tag):
 namespace me {{
 namespace {tag} {{
 
-struct Params {{
+struct Traits {{
+  static constexpr int NEXT = {n};
+  struct Params {{
 {params}
-}};
+  }};
 
-template <class R>
-__host__ __device__ __forceinline__ double eval_event(const double (&pm)[{prog.n_ext}][4], const Params& prm) {{
+  // FP64 path: FP64 momenta, invariants and amplitudes
+  static __host__ __device__ __forceinline__ double eval64(const double (&pm)[{n}][4], const Params& prm) {{
+    using R = double;
 {unpack}
 {mc2}
-{body}
-}}
+{body64}
+  }}
+
+  // mixed path: double-float momenta and resonant invariants, FP32 amplitudes
+  static __host__ __device__ __forceinline__ double evalmx(const me::df (&pm)[{n}][4], const Params& prm) {{
+    using R = float;
+{unpack}
+{mc2}
+{bodymx}
+  }}
+}};
 
 }}  // namespace {tag}
 }}  // namespace me
 
-ME_DEFINE_PROCESS({tag}, {prog.n_ext}, {len(cpl) if cpl else 1})
+ME_DEFINE_PROCESS({tag}, {n}, {len(cpl) if cpl else 1})
 """
-    info = {"flops_amp": em.flops32, "flops_fp64": em.flops64, "params": cpl}
+    info = {"flops_amp": emmx.flops32, "flops_fp64": em64.flops64 + em64.flops32, "params": cpl}
     return src, info
 
 

@@ -21,6 +21,7 @@ struct KinDev {
   double sinh2_eta_max;  // sinh(eta_max)^2
   double cos_dr, cosh_dr, sinh_dr;
   double bw_mass[2], bw_width[2], bw_t0[2], bw_t1[2];  // top, W
+  int32_t massive;       // any final-state mass (RAMBO)
 };
 
 constexpr int kThreads = 128;

@@ -176,6 +176,7 @@ me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
     if (i >= 2 && i < next) msum += k.mass[i];
   }
   if (kin->kind == ME_PS_RAMBO && !(msum < kin->sqrt_s)) return fail(ME_ERR_ARG, "kin: masses exceed sqrt_s");
+  k.massive = msum > 0.0 ? 1 : 0;
   k.n_cut_legs = kin->n_cut_legs;
   for (int i = 0; i < 8; ++i) k.cut_legs[i] = kin->cut_legs[i];
   k.pt_min = kin->pt_min;

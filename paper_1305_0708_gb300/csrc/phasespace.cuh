@@ -17,6 +17,7 @@
 #pragma once
 #include <cstdint>
 
+#include "dfloat.cuh"
 #include "me_internal.h"
 
 namespace me {
@@ -350,6 +351,138 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
     ok = gen_ttbar<NEXT>(kin, u, p, wps, shat);
   }
   return ok && pass_cuts<NEXT>(kin, p);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision phase space: massless RAMBO in double-float arithmetic (FP32
+// pairs, ~2^-48 relative) on the FP32 pipe, the same formulas and draw order as
+// gen_rambo.  Other generators run in FP64 and are split into double-floats.
+// ---------------------------------------------------------------------------
+template <int NEXT>
+__host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
+                                         df (&p)[NEXT][4]) {
+  constexpr int NF = NEXT - 2;
+  const df w = from_double(kin.sqrt_s);
+  const df hw = df{w.hi * 0.5f, w.lo * 0.5f};
+  const df z = df{0.0f, 0.0f};
+  p[0][0] = hw; p[0][1] = z; p[0][2] = z; p[0][3] = hw;
+  p[1][0] = hw; p[1][1] = z; p[1][2] = z; p[1][3] = -hw;
+  df Q0 = z, Q1 = z, Q2 = z, Q3 = z;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    uint64_t o[4];
+    Philox::block(event, (uint64_t)att, (uint64_t)k, 0ull, seed, 0ull, o);
+    const df u0 = unit_df(o[0]), u1 = unit_df(o[1]), u2 = unit_df(o[2]), u3 = unit_df(o[3]);
+    const df c = df{u0.hi * 2.0f, u0.lo * 2.0f} + (-1.0f);
+    const df sn = df_sqrt((dfs(1.0f) - c) * (dfs(1.0f) + c));
+    df sp, cp;
+    df_sincospi(df{u1.hi * 2.0f, u1.lo * 2.0f}, sp, cp);
+    const df q0 = -df_log(u2 * u3);
+    const df qs = q0 * sn;
+    p[2 + k][0] = q0;
+    p[2 + k][1] = qs * cp;
+    p[2 + k][2] = qs * sp;
+    p[2 + k][3] = q0 * c;
+    Q0 = Q0 + p[2 + k][0]; Q1 = Q1 + p[2 + k][1]; Q2 = Q2 + p[2 + k][2]; Q3 = Q3 + p[2 + k][3];
+  }
+  const df M = df_sqrt(((sqr(Q0) - sqr(Q1)) - sqr(Q2)) - sqr(Q3));
+  const df iM = dfs(1.0f) / M;
+  const df b1 = -(Q1 * iM), b2 = -(Q2 * iM), b3 = -(Q3 * iM);
+  const df gam = Q0 * iM;
+  const df a = dfs(1.0f) / (gam + 1.0f);
+  const df x = w * iM;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    df* q = p[2 + k];
+    const df bq = (b1 * q[1] + b2 * q[2]) + b3 * q[3];
+    const df q0 = q[0];
+    const df c = q0 + a * bq;
+    q[0] = x * (gam * q0 + bq);
+    q[1] = x * (q[1] + b1 * c);
+    q[2] = x * (q[2] + b2 * c);
+    q[3] = x * (q[3] + b3 * c);
+  }
+}
+
+// cuts on double-float momenta: FP32 estimates decide outside a 1e-5 guard band;
+// a point with any undecided test is decided by the FP64 cuts on its momenta.
+template <int NEXT>
+__host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const df (&p)[NEXT][4]) {
+  const int nl = kin.n_cut_legs;
+  if (nl == 0) return true;
+  const float ptmin2 = (float)(kin.pt_min * kin.pt_min), sh2 = (float)kin.sinh2_eta_max;
+  const float cdr = (float)kin.cos_dr, chd = (float)kin.cosh_dr, shd = (float)kin.sinh_dr;
+  const float dr2 = (float)(kin.dr_min * kin.dr_min);
+  float ptf[8], af[8], rf[8];
+  bool undecided = false;
+  for (int i = 0; i < nl; ++i) {
+    const df* q = p[kin.cut_legs[i]];
+    const float x = q[1].hi, y = q[2].hi, zz = q[3].hi;
+    const float pt2 = x * x + y * y;
+    int c = fcmp(pt2, ptmin2, ptmin2);
+    if (c < 0) return false;
+    undecided |= (c == 0);
+    c = fcmp(zz * zz, sh2 * pt2, sh2 * pt2 + zz * zz);
+    if (c > 0) return false;
+    undecided |= (c == 0);
+    ptf[i] = sqrtf(pt2);
+    const float ip = 1.0f / ptf[i];
+    af[i] = zz * ip;
+    rf[i] = sqrtf(pt2 + zz * zz) * ip;
+  }
+  for (int i = 0; i < nl && !undecided; ++i) {
+    for (int j = i + 1; j < nl; ++j) {
+      const df* qi = p[kin.cut_legs[i]];
+      const df* qj = p[kin.cut_legs[j]];
+      const float dotf = qi[1].hi * qj[1].hi + qi[2].hi * qj[2].hi;
+      const float ptijf = ptf[i] * ptf[j];
+      int c = fcmp(dotf, cdr * ptijf, ptijf);
+      if (c < 0) continue;
+      if (c == 0) { undecided = true; break; }
+      const float sc = fabsf(af[i]) + fabsf(af[j]) + rf[i] + rf[j];
+      const int e1 = fcmp(af[i], af[j] * chd + rf[j] * shd, sc);
+      const int e2 = fcmp(af[j], af[i] * chd + rf[i] * shd, sc);
+      if (e1 > 0 || e2 > 0) continue;
+      if (e1 == 0 || e2 == 0) { undecided = true; break; }
+      const float deta = asinhf(af[i]) - asinhf(af[j]);
+      const float cross = qi[1].hi * qj[2].hi - qi[2].hi * qj[1].hi;
+      const float dphi = atan2f(fabsf(cross), dotf);
+      const int r = fcmp(deta * deta + dphi * dphi, dr2, dr2 + deta * deta + dphi * dphi);
+      if (r < 0) return false;
+      if (r == 0) { undecided = true; break; }
+    }
+  }
+  if (!undecided) return true;
+  double pd[NEXT][4];
+#pragma unroll
+  for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) pd[k][m] = to_double(p[k][m]);
+  }
+  return pass_cuts<NEXT>(kin, pd);
+}
+
+// one mixed-precision draw: double-float RAMBO for massless final states, else the
+// FP64 generator split into double-floats
+template <int NEXT>
+__host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
+                                              df (&p)[NEXT][4], double& wps, double& shat) {
+  if (kin.kind == ME_PS_RAMBO && !kin.massive) {
+    rambo_df<NEXT>(kin, seed, event, att, p);
+    wps = kin.rambo_volume;
+    shat = kin.sqrt_s * kin.sqrt_s;
+    return pass_cuts_df<NEXT>(kin, p);
+  }
+  double pd[NEXT][4];
+  const bool ok = draw_point<NEXT>(kin, seed, event, att, pd, wps, shat);
+  if (ok) {
+#pragma unroll
+    for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) p[k][m] = from_double(pd[k][m]);
+    }
+  }
+  return ok;
 }
 
 }  // namespace me

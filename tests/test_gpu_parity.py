@@ -102,14 +102,16 @@ def test_me_eval_parity(B, key):
     assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3, (np.median(rel), rel.max())
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("key", list(WORKLOADS))
-def test_generate_parity(B, key):
-    """On-device Philox + generator + cuts + redraws against the oracle's own generator."""
+def test_generate_parity(B, key, prec):
+    """On-device Philox + generator + cuts + redraws against the oracle's own generator
+    (FP64 generator for the FP64 path; double-float RAMBO for the mixed path)."""
     w = WORKLOADS[key]
     n_ext = len(opr_legs(w))
     n, off = 3000, 12345
     kin = B.make_kin(**kin_args(w))
-    h = B.me_create(w["process"], None, B.ME_FP64)
+    h = B.me_create(w["process"], None, prec)
     mom = torch.empty(n_ext * 4 * n, dtype=torch.float64, device="cuda")
     wt = torch.empty(n, dtype=torch.float64, device="cuda")
     sh = torch.empty(n, dtype=torch.float64, device="cuda")
