@@ -22,6 +22,7 @@ struct KinDev {
   double cos_dr, cosh_dr, sinh_dr;
   double bw_mass[2], bw_width[2], bw_t0[2], bw_t1[2];  // top, W
   int32_t massive;       // any final-state mass (RAMBO)
+  uint32_t cut_mask;     // bit k set: leg k is cut
 };
 
 constexpr int kThreads = 128;
@@ -41,6 +42,9 @@ struct ProcessDesc {
                              const double* params, double* partials, double* me2_out, double* mom_out,
                              double* wps_out, double* shat_out, int32_t* tries_out, int* status,
                              int eval_me, cudaStream_t s, int grid);
+  cudaError_t (*launch_step)(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t m,
+                             const double* params, void* ws, double* partials, double* me2_out, double* mom_out,
+                             int64_t out_stride, int* status, cudaStream_t s, int grid_ps, int grid_me);
 };
 
 }  // namespace me

@@ -113,6 +113,8 @@ struct me_handle_s {
   double* d_acc = nullptr;    // 3 doubles
   int* d_status = nullptr;
   double* h_acc = nullptr;    // pinned, 3 doubles + status
+  void* d_ws = nullptr;       // phase-space points of one chunk (k_ps -> k_me)
+  size_t ws_cap = 0;
   std::mutex mu;
 };
 
@@ -178,7 +180,9 @@ me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
   if (kin->kind == ME_PS_RAMBO && !(msum < kin->sqrt_s)) return fail(ME_ERR_ARG, "kin: masses exceed sqrt_s");
   k.massive = msum > 0.0 ? 1 : 0;
   k.n_cut_legs = kin->n_cut_legs;
+  k.cut_mask = 0;
   for (int i = 0; i < 8; ++i) k.cut_legs[i] = kin->cut_legs[i];
+  for (int i = 0; i < kin->n_cut_legs; ++i) k.cut_mask |= 1u << kin->cut_legs[i];
   k.pt_min = kin->pt_min;
   k.eta_max = kin->eta_max;
   k.dr_min = kin->dr_min;
@@ -224,6 +228,21 @@ me_status ensure_workspace(me_handle h, int nblocks) {
       return fail(ME_ERR_OOM, "workspace partials");
     h->partials_cap = nblocks;
   }
+  return ME_OK;
+}
+
+constexpr int64_t kChunk = 1 << 20;  // points per k_ps / k_me pair
+
+size_t ws_bytes(int n_ext, int64_t m) { return (size_t)m * (32 * (size_t)n_ext + 20); }
+
+me_status ensure_points_ws(me_handle h, int64_t m) {
+  const size_t need = ws_bytes(h->desc->n_ext, m);
+  if (need <= h->ws_cap) return ME_OK;
+  if (h->d_ws) cudaFree(h->d_ws);
+  h->d_ws = nullptr;
+  h->ws_cap = 0;
+  if (cudaMalloc(&h->d_ws, need) != cudaSuccess) return fail(ME_ERR_OOM, "workspace for phase-space points");
+  h->ws_cap = need;
   return ME_OK;
 }
 
@@ -351,13 +370,26 @@ me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t
   if ((st = make_kin(h, kin, k)) != ME_OK) return st;
   if (n_accept == 0) return ME_OK;
   std::lock_guard<std::mutex> lock(h->mu);
-  const int grid = grid_for(h, n_accept);
-  if ((st = ensure_workspace(h, grid)) != ME_OK) return st;
+  const int64_t m0 = std::min<int64_t>(n_accept, kChunk);
+  const int64_t nchunks = (n_accept + kChunk - 1) / kChunk;
+  const int grid_me = grid_for(h, m0);
+  // phase space: 4 resident blocks per SM, each with a contiguous range of points
+  const int grid_ps = (int)std::max<int64_t>(1, std::min<int64_t>((m0 + me::kThreads - 1) / me::kThreads,
+                                                                   (int64_t)h->n_sm * 4));
+  if ((st = ensure_workspace(h, (int)(grid_me * nchunks))) != ME_OK) return st;
+  if ((st = ensure_points_ws(h, m0)) != ME_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = h->desc->launch_xsec(h->prec, &k, seed, counter_offset, n_accept, h->cvals.data(), h->d_partials,
-                                       me2_out, momenta_out, nullptr, nullptr, nullptr, h->d_status, 1, s, grid);
-  if (e != cudaSuccess) return cuda_fail(e, "xsec_step launch");
-  k_reduce_partials<<<1, 256, 0, s>>>(h->d_partials, grid, h->d_acc);
+  cudaError_t e;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    const int64_t first = c * kChunk;
+    const int64_t m = std::min<int64_t>(kChunk, n_accept - first);
+    e = h->desc->launch_step(h->prec, &k, seed, counter_offset + (uint64_t)first, m, h->cvals.data(), h->d_ws,
+                             h->d_partials + 3 * (size_t)grid_me * c, me2_out ? me2_out + first : nullptr,
+                             momenta_out ? momenta_out + first : nullptr, n_accept, h->d_status, s, grid_ps,
+                             grid_me);
+    if (e != cudaSuccess) return cuda_fail(e, "xsec_step launch");
+  }
+  k_reduce_partials<<<1, 256, 0, s>>>(h->d_partials, (int)(grid_me * nchunks), h->d_acc);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "xsec_step reduce");
   if ((e = cudaMemcpyAsync(h->h_acc, h->d_acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(e, "xsec_step copy");
@@ -454,6 +486,7 @@ void me_destroy(me_handle h) {
   if (h->d_acc) cudaFree(h->d_acc);
   if (h->d_status) cudaFree(h->d_status);
   if (h->h_acc) cudaFreeHost(h->h_acc);
+  if (h->d_ws) cudaFree(h->d_ws);
   delete h;
 }
 

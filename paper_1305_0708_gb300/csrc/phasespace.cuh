@@ -279,12 +279,15 @@ __host__ __device__ __forceinline__ int fcmp(float x, float y, float scale) {
 
 template <int NEXT>
 __host__ __device__ __forceinline__ bool pass_cuts(const KinDev& kin, const double (&p)[NEXT][4]) {
-  const int nl = kin.n_cut_legs;
-  if (nl == 0) return true;
-  double pt2[8];
-  float ptf[8], af[8], rf[8];
-  for (int i = 0; i < nl; ++i) {
-    const double* q = p[kin.cut_legs[i]];
+  const uint32_t mask = kin.cut_mask;
+  if (mask == 0) return true;
+  // loops run over every leg with compile-time indices (registers, no local memory)
+  double pt2[NEXT];
+  float ptf[NEXT], af[NEXT], rf[NEXT];
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+    if (!((mask >> i) & 1u)) continue;
+    const double* q = p[i];
     pt2[i] = q[1] * q[1] + q[2] * q[2];
     if (!(pt2[i] > kin.pt_min * kin.pt_min)) return false;
     if (!(q[3] * q[3] < kin.sinh2_eta_max * pt2[i])) return false;
@@ -295,10 +298,13 @@ __host__ __device__ __forceinline__ bool pass_cuts(const KinDev& kin, const doub
     rf[i] = sqrtf(p2f + zf * zf) * ip;        // cosh(eta)
   }
   const float cdr = (float)kin.cos_dr, chd = (float)kin.cosh_dr, shd = (float)kin.sinh_dr;
-  for (int i = 0; i < nl; ++i) {
-    for (int j = i + 1; j < nl; ++j) {
-      const double* qi = p[kin.cut_legs[i]];
-      const double* qj = p[kin.cut_legs[j]];
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < NEXT; ++j) {
+      if (!((mask >> i) & 1u) || !((mask >> j) & 1u)) continue;
+      const double* qi = p[i];
+      const double* qj = p[j];
       // |d_phi| > dr_min  <=>  pT_i . pT_j < cos(dr_min) |pT_i| |pT_j|
       const float dotf = (float)qi[1] * (float)qj[1] + (float)qi[2] * (float)qj[2];
       const float ptijf = ptf[i] * ptf[j];
@@ -408,15 +414,17 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
 // a point with any undecided test is decided by the FP64 cuts on its momenta.
 template <int NEXT>
 __host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const df (&p)[NEXT][4]) {
-  const int nl = kin.n_cut_legs;
-  if (nl == 0) return true;
+  const uint32_t mask = kin.cut_mask;
+  if (mask == 0) return true;
   const float ptmin2 = (float)(kin.pt_min * kin.pt_min), sh2 = (float)kin.sinh2_eta_max;
   const float cdr = (float)kin.cos_dr, chd = (float)kin.cosh_dr, shd = (float)kin.sinh_dr;
   const float dr2 = (float)(kin.dr_min * kin.dr_min);
-  float ptf[8], af[8], rf[8];
+  float ptf[NEXT], af[NEXT], rf[NEXT];
   bool undecided = false;
-  for (int i = 0; i < nl; ++i) {
-    const df* q = p[kin.cut_legs[i]];
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+    if (!((mask >> i) & 1u)) continue;
+    const df* q = p[i];
     const float x = q[1].hi, y = q[2].hi, zz = q[3].hi;
     const float pt2 = x * x + y * y;
     int c = fcmp(pt2, ptmin2, ptmin2);
@@ -430,26 +438,30 @@ __host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const d
     af[i] = zz * ip;
     rf[i] = sqrtf(pt2 + zz * zz) * ip;
   }
-  for (int i = 0; i < nl && !undecided; ++i) {
-    for (int j = i + 1; j < nl; ++j) {
-      const df* qi = p[kin.cut_legs[i]];
-      const df* qj = p[kin.cut_legs[j]];
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < NEXT; ++j) {
+      if (undecided || !((mask >> i) & 1u) || !((mask >> j) & 1u)) continue;
+      const df* qi = p[i];
+      const df* qj = p[j];
       const float dotf = qi[1].hi * qj[1].hi + qi[2].hi * qj[2].hi;
       const float ptijf = ptf[i] * ptf[j];
-      int c = fcmp(dotf, cdr * ptijf, ptijf);
+      const int c = fcmp(dotf, cdr * ptijf, ptijf);
       if (c < 0) continue;
-      if (c == 0) { undecided = true; break; }
+      if (c == 0) { undecided = true; continue; }
       const float sc = fabsf(af[i]) + fabsf(af[j]) + rf[i] + rf[j];
       const int e1 = fcmp(af[i], af[j] * chd + rf[j] * shd, sc);
       const int e2 = fcmp(af[j], af[i] * chd + rf[i] * shd, sc);
       if (e1 > 0 || e2 > 0) continue;
-      if (e1 == 0 || e2 == 0) { undecided = true; break; }
+      if (e1 == 0 || e2 == 0) { undecided = true; continue; }
       const float deta = asinhf(af[i]) - asinhf(af[j]);
       const float cross = qi[1].hi * qj[2].hi - qi[2].hi * qj[1].hi;
       const float dphi = atan2f(fabsf(cross), dotf);
-      const int r = fcmp(deta * deta + dphi * dphi, dr2, dr2 + deta * deta + dphi * dphi);
+      const float r2 = deta * deta + dphi * dphi;
+      const int r = fcmp(r2, dr2, dr2 + r2);
       if (r < 0) return false;
-      if (r == 0) { undecided = true; break; }
+      if (r == 0) undecided = true;
     }
   }
   if (!undecided) return true;

@@ -222,6 +222,178 @@ __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, ui
   if (partials) block_reduce3(sw, sw2, nt, partials);
 }
 
+// ---------------------------------------------------------------------------
+// Two-kernel Monte Carlo step (xsec_step): k_ps draws the accepted points of a
+// chunk (the same work-queue redraws as k_xsec, without the amplitude code, so
+// it runs at high occupancy) into a workspace; k_me evaluates |M|^2, forms the
+// weights and writes one partial per block.  Workspace layout per chunk of m
+// points: momenta [NEXT*4][m] as FP64 (FP64 path) or as two FP32 arrays hi, lo
+// (mixed path), then wps [m], shat [m] (FP64) and tries [m] (int32).
+// ---------------------------------------------------------------------------
+// k_ps: each block owns a contiguous range of events and a circular queue of
+// redraws.  Every round takes up to kThreads items -- first the carried-over
+// redraws, then new events -- so rounds stay full until the range runs out; a
+// failed draw is appended with its next attempt number.  Accepted points are
+// written straight to their event's slot in the workspace.
+template <class P, bool MIXED>
+__global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, uint64_t seed, uint64_t offset, int64_t m,
+                                                    void* __restrict__ ws, int* status) {
+  constexpr int NEXT = P::NEXT;
+  constexpr int QCAP = 4 * kThreads;  // power of two; holds at most 2 kThreads items at any time
+  float* ph = reinterpret_cast<float*>(ws);
+  float* pl = ph + (int64_t)NEXT * 4 * m;
+  double* pd = reinterpret_cast<double*>(ws);
+  double* wps_a = reinterpret_cast<double*>(MIXED ? (void*)(pl + (int64_t)NEXT * 4 * m) : (void*)(pd + (int64_t)NEXT * 4 * m));
+  double* shat_a = wps_a + m;
+  int32_t* tries_a = reinterpret_cast<int32_t*>(shat_a + m);
+  __shared__ int64_t s_ev[QCAP];
+  __shared__ int s_att[QCAP];
+  __shared__ int s_head, s_tail;
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * per;
+  const int64_t b1 = b0 + per < m ? b0 + per : m;
+  if (threadIdx.x == 0) { s_head = 0; s_tail = 0; }
+  __syncthreads();
+  int64_t next_new = b0;
+  while (true) {
+    const int head = s_head, tail = s_tail;
+    const int carried = tail - head;
+    const int take_c = carried < kThreads ? carried : kThreads;
+    const int64_t left = b1 - next_new;
+    const int take_n = (int)((kThreads - take_c) < left ? (kThreads - take_c) : left);
+    if (take_c + take_n == 0) break;
+    int64_t ev = -1;
+    int att = 0;
+    if ((int)threadIdx.x < take_c) {
+      ev = s_ev[(head + threadIdx.x) & (QCAP - 1)];
+      att = s_att[(head + threadIdx.x) & (QCAP - 1)];
+    } else if ((int)threadIdx.x < take_c + take_n) {
+      ev = next_new + (threadIdx.x - take_c);
+    }
+    __syncthreads();  // every item read before the queue moves
+    if (threadIdx.x == 0) s_head = head + take_c;
+    next_new += take_n;
+    if (ev >= 0) {
+      double wps = 0.0, shat = 1.0;
+      bool ok;
+      if constexpr (MIXED) {
+        df q[NEXT][4];
+        ok = draw_point_df<NEXT>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat);
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+              ph[(int64_t)(k * 4 + mu) * m + ev] = q[k][mu].hi;
+              pl[(int64_t)(k * 4 + mu) * m + ev] = q[k][mu].lo;
+            }
+          }
+        }
+      } else {
+        double q[NEXT][4];
+        ok = draw_point<NEXT>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat);
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) pd[(int64_t)(k * 4 + mu) * m + ev] = q[k][mu];
+          }
+        }
+      }
+      if (ok) {
+        wps_a[ev] = wps;
+        shat_a[ev] = shat;
+        tries_a[ev] = att + 1;
+      } else if (att + 1 >= kin.max_attempts) {
+        wps_a[ev] = 0.0;
+        shat_a[ev] = 1.0;
+        tries_a[ev] = att + 1;
+        atomicOr(status, 1);
+      } else {
+        const int pos = atomicAdd(&s_tail, 1);
+        s_ev[pos & (QCAP - 1)] = ev;
+        s_att[pos & (QCAP - 1)] = att + 1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <class P, bool MIXED>
+__global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const void* __restrict__ ws,
+                                                 typename P::Params prm, double* __restrict__ partials,
+                                                 double* __restrict__ me2_out, double* __restrict__ mom_out,
+                                                 int64_t out_stride) {
+  constexpr int NEXT = P::NEXT;
+  const float* ph = reinterpret_cast<const float*>(ws);
+  const float* pl = ph + (int64_t)NEXT * 4 * m;
+  const double* pd = reinterpret_cast<const double*>(ws);
+  const double* wps_a = reinterpret_cast<const double*>(MIXED ? (const void*)(pl + (int64_t)NEXT * 4 * m)
+                                                              : (const void*)(pd + (int64_t)NEXT * 4 * m));
+  const double* shat_a = wps_a + m;
+  const int32_t* tries_a = reinterpret_cast<const int32_t*>(shat_a + m);
+  double sw = 0.0, sw2 = 0.0, nt = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wps = wps_a[i], shat = shat_a[i];
+    const bool ok = wps > 0.0;
+    double m2 = 0.0;
+    if constexpr (MIXED) {
+      df q[NEXT][4];
+#pragma unroll
+      for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+          q[k][mu] = df{__ldg(ph + (int64_t)(k * 4 + mu) * m + i), __ldg(pl + (int64_t)(k * 4 + mu) * m + i)};
+      }
+      if (ok) m2 = P::evalmx(q, prm);
+      if (mom_out) {
+#pragma unroll
+        for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+          for (int mu = 0; mu < 4; ++mu) mom_out[(int64_t)(k * 4 + mu) * out_stride + i] = to_double(q[k][mu]);
+        }
+      }
+    } else {
+      double q[NEXT][4];
+#pragma unroll
+      for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) q[k][mu] = __ldg(pd + (int64_t)(k * 4 + mu) * m + i);
+      }
+      if (ok) m2 = P::eval64(q, prm);
+      if (mom_out) {
+#pragma unroll
+        for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+          for (int mu = 0; mu < 4; ++mu) mom_out[(int64_t)(k * 4 + mu) * out_stride + i] = q[k][mu];
+        }
+      }
+    }
+    const double w = ok ? wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb : 0.0;
+    sw += w;
+    sw2 += w * w;
+    nt += (double)tries_a[i];
+    if (me2_out) me2_out[i] = m2;
+  }
+  block_reduce3(sw, sw2, nt, partials);
+}
+
+template <class P>
+cudaError_t launch_step(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t m, const double* params,
+                        void* ws, double* partials, double* me2_out, double* mom_out, int64_t out_stride,
+                        int* status, cudaStream_t s, int grid_ps, int grid_me) {
+  typename P::Params prm;
+  memcpy(&prm, params, sizeof(prm));
+  if (prec == ME_FP64) {
+    k_ps<P, false><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
+    k_me<P, false><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
+  } else {
+    k_ps<P, true><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
+    k_me<P, true><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
+  }
+  return cudaGetLastError();
+}
+
 template <class P>
 cudaError_t launch_eval(int prec, const double* mom, int64_t n, double* out, const double* params, cudaStream_t s,
                         int grid) {
@@ -254,4 +426,5 @@ cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t off
     d->n_ext = NEXT_;                                                               \
     d->launch_eval = me::launch_eval<me::TAG::Traits>;                              \
     d->launch_xsec = me::launch_xsec<me::TAG::Traits>;                              \
+    d->launch_step = me::launch_step<me::TAG::Traits>;                              \
   }
