@@ -27,6 +27,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# FP32 operations per phase-space draw of the mixed path (double-float RAMBO, counted from
+# the operation mix of dfloat.cuh: add 20, mul 7, sqrt 15, div 20, log 80, sin/cos 120 FP32
+# operations; 4 final-state particles plus the conformal transform and the FP32 cut tests)
+PS_FLOPS_PER_DRAW = {"rambo": 2700.0}
+
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -229,13 +234,30 @@ def main():
     step_ms = float(t_max.item())
     value = n * world / (step_ms * 1e-3)
 
-    # kernel-only duration of the fused kernel: me_eval-free k_xsec is the step minus the
-    # one-block reduction and the 32-byte read-back; time the reduction-free kernel via me_generate+eval
-    # is not separable here, so the step duration bounds the kernel duration from above.
-    kern_ms = step_ms
+    # per-kernel device time of the step (CUDA events recorded by the library on the launch
+    # stream around k_ps and k_me), taken on extra steps of the same work after the timed region
+    B.me_step_timing(h32, 1)
+    acc_t = B.me_xsec_acc()
+    n_kt = max(3, args.steps // 2)
+    for s_ in range(n_kt):
+        flush.zero_()
+        B.xsec_step(h32, w["seed"], offset0 + (args.warmup + args.steps + s_) * n, n, kin, stream, acc_t)
+    t_ps, t_me = B.me_step_timing(h32, 0)
+    ps_ms, me_ms = t_ps / n_kt, t_me / n_kt
+    tries_per_point = acc_t.n_try / acc_t.n_acc
     flops_event = info.flops_amp
-    achieved = flops_event * n / (kern_ms * 1e-3) / 1e12
     peak = fp32_alu_peak_tflops()
+    me_tflops = flops_event * n / (me_ms * 1e-3) / 1e12
+    ps_tflops = PS_FLOPS_PER_DRAW.get(w["kind"], 0.0) * tries_per_point * n / (ps_ms * 1e-3) / 1e12
+    kernels = {
+        "k_me": {"ms": me_ms, "achieved_tflops": me_tflops, "frac": me_tflops / peak,
+                 "flops_per_point": flops_event, "what": "|M|^2, weights, block sums (FP32 amplitudes)"},
+        "k_ps": {"ms": ps_ms, "achieved_tflops": ps_tflops, "frac": ps_tflops / peak,
+                 "flops_per_draw": PS_FLOPS_PER_DRAW.get(w["kind"], 0.0), "draws_per_point": tries_per_point,
+                 "what": "Philox + double-float RAMBO + cuts + redraw queue"},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    achieved = kernels[dom]["achieved_tflops"]
 
     # FP64 path for context
     fp64 = None
@@ -307,13 +329,12 @@ def main():
             "fp64_path": fp64,
             "me_eval_ms": me_eval_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_xsec<float> (fused phase space + |M|^2 + reduction), step duration",
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                         "flops_per_event": flops_event},
+                         "frac": achieved / peak, "traffic": None, "kernel": dom,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+            "kernels": kernels,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 3 * args.steps,
             "clocks": clk,
             "mc": {"sigma_pb": acc32.sum_w / acc32.n_try, "n_try": acc32.n_try, "n_acc": acc32.n_acc},
             "wall_s_timed": wall32,

@@ -165,6 +165,14 @@ me_status xsec_step_noalloc(me_handle h, uint64_t seed, uint64_t counter_offset,
                             const me_kin *kin, void *stream, me_xsec_acc *acc, double *me2_out,
                             double *momenta_out);
 
+/* Per-kernel device time of xsec_step, from CUDA events recorded on the call's
+ * stream around the phase-space kernel and the amplitude kernel of every chunk.
+ * Writes the sums (ms) accumulated since the previous call to *ms_ps and
+ * *ms_me (either may be NULL), resets them, and turns recording on (enable = 1)
+ * or off (0).  While on, xsec_step waits for each chunk's events.  (No
+ * counterpart in the paper; a measurement aid.) */
+me_status me_step_timing(me_handle h, int32_t enable, double *ms_ps, double *ms_me);
+
 /* sigma-hat = sum_w / n_try and its standard error (pb) from an accumulator. */
 me_status me_xsec_estimate(const me_xsec_acc *acc, double *sigma, double *error);
 

@@ -46,8 +46,8 @@ class me_info_t(ctypes.Structure):
 ME_FP64, ME_MIXED = 0, 1
 ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR = 0, 1, 2
 
-EXPORTS = ["me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_xsec_estimate", "me_info", "me_n_processes",
-           "me_process_name", "me_destroy", "me_last_error"]
+EXPORTS = ["me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
+           "me_xsec_estimate", "me_info", "me_n_processes", "me_process_name", "me_destroy", "me_last_error"]
 
 
 def lib_path():
@@ -70,6 +70,7 @@ def load(path=None):
     L.xsec_step.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc), vp, vp]
     L.xsec_step_noalloc.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc),
                                     vp, vp]
+    L.me_step_timing.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.me_xsec_estimate.argtypes = [ctypes.POINTER(me_xsec_acc), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]
     L.me_info.argtypes = [vp, ctypes.POINTER(me_info_t)]
@@ -79,8 +80,8 @@ def load(path=None):
     L.me_destroy.argtypes = [vp]
     L.me_destroy.restype = None
     L.me_last_error.restype = ctypes.c_char_p
-    for fn in ("me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_xsec_estimate",
-               "me_info"):
+    for fn in ("me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
+               "me_xsec_estimate", "me_info"):
         getattr(L, fn).restype = ctypes.c_int
     _LIB = L
     return L
@@ -162,6 +163,13 @@ def xsec_step_noalloc(h, seed, counter_offset, n_accept, kin, stream=None, acc=N
     _check(load().xsec_step_noalloc(h, seed, counter_offset, n_accept, ctypes.byref(kin), _stream(stream),
                                     ctypes.byref(acc), _ptr(me2_out), _ptr(momenta_out)))
     return acc
+
+
+def me_step_timing(h, enable):
+    """Returns (ms_ps, ms_me) accumulated since the previous call; enable turns recording on/off."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().me_step_timing(h, int(enable), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def me_xsec_estimate(acc):

@@ -22,7 +22,17 @@ kernel instead (colour_gemm.cuh).
 from fractions import Fraction
 
 from .model import PARTICLES, couplings
-from .program import _is_column, _PAIRINGS
+from .program import _ext_chirality, _is_column, _PAIRINGS
+
+_TAG = {frozenset("u"): "me::kUp", frozenset("l"): "me::kLo", frozenset("ul"): "me::kAll"}
+
+
+def _tag(h):
+    return _TAG[frozenset(h)]
+
+
+def _flip(h):
+    return frozenset({"u": "l", "l": "u"}[x] for x in h)
 
 
 def _hname(h):
@@ -53,6 +63,7 @@ class _Emitter:
         self.flops32 = 0      # amplitude-precision flops per event
         self.flops64 = 0      # FP64 flops per event (momenta, invariants)
         self.cpl_names = set()
+        self.half = {}            # spinor variable -> set of halves ("u", "l") that can be non-zero
 
     def emit(self, s):
         self.lines.append(s)
@@ -155,7 +166,7 @@ class _Emitter:
                 self.amp_code(aid, chvars, hi)
         # colour sum
         E("  // colour sum (J^T C J)/den per helicity, helicity sum, average")
-        E("  double tot = 0.0;")
+        E("  R tot = R(0);")
         C = p.cmat_num
         for hi in range(len(p.amp_terms)):
             E("  {")
@@ -168,9 +179,9 @@ class _Emitter:
                     if C[k][l]:
                         E(f"    s += {_lit(2 * C[k][l])} * (J{hi}_{k}.re * J{hi}_{l}.re + J{hi}_{k}.im * J{hi}_{l}.im);")
                         self.flops32 += 5
-            E("    tot += (double)s;")
+            E("    tot += s;")
             E("  }")
-        E(f"  return tot * {float(p.average / p.cmat_den)!r};")
+        E(f"  return (double)tot * {float(p.average / p.cmat_den)!r};")
 
     # ------------------------------------------------------------------
     def child_vars(self, nid, var, child):
@@ -191,10 +202,13 @@ class _Emitter:
         if part.is_fermion:
             if not part.massless:
                 raise NotImplementedError("massive external fermions")
+            chi = _ext_chirality(leg, h)
             if _is_column(nd.ptype):
                 self.emit(f"  const me::W4<R> {name} = me::ext_column_massless<R>(r{nid}, {h}, {inc});")
+                self.half[name] = frozenset("u" if chi == "L" else "l")
             else:
                 self.emit(f"  const me::W4<R> {name} = me::ext_row_massless<R>(r{nid}, {h}, {inc});")
+                self.half[name] = frozenset("l" if chi == "L" else "u")
             self.flops32 += 12
         elif part.is_vector:
             mass = "R(0)" if part.massless else f"(R){self.cpl(part.mass)}"
@@ -225,13 +239,27 @@ class _Emitter:
                 fk = [k for k in kids if k[1] in (0, 1)][0]
                 vk = [k for k in kids if k[1] == 2][0]
                 m = "R(0)" if part.massless else f"(R){self.cpl(part.mass)}"
+                hin = self.half[fk[2]]
                 if _is_column(nd.ptype):
-                    E(f"  const me::W4<R> {name} = me::prop_col<R>(me::ffv_col<R>({fk[2]}, {vk[2]}, {cargs}), "
-                      f"k{nid}, {m}, inv{nid});")
+                    hx = set()
+                    if "u" in hin and has_l:
+                        hx.add("l")
+                    if "l" in hin and has_r:
+                        hx.add("u")
+                    hx = frozenset(hx)
+                    E(f"  const me::W4<R> {name} = me::prop_col<R, {_tag(hx)}>(me::ffv_col<R, {_tag(hin)}>("
+                      f"{fk[2]}, {vk[2]}, {cargs}), k{nid}, {m}, inv{nid});")
                 else:
-                    E(f"  const me::W4<R> {name} = me::prop_row<R>(me::ffv_row<R>({fk[2]}, {vk[2]}, {cargs}), "
-                      f"me::neg(k{nid}), {m}, inv{nid});")
-                self.flops32 += 40 * nch + (64 if not part.massless else 48)
+                    hx = set()
+                    if "l" in hin and has_l:
+                        hx.add("u")
+                    if "u" in hin and has_r:
+                        hx.add("l")
+                    hx = frozenset(hx)
+                    E(f"  const me::W4<R> {name} = me::prop_row<R, {_tag(hx)}>(me::ffv_row<R, {_tag(hin)}>("
+                      f"{fk[2]}, {vk[2]}, {cargs}), me::neg(k{nid}), {m}, inv{nid});")
+                self.half[name] = _flip(hx) if part.massless else frozenset("ul")
+                self.flops32 += 20 * 2 * len(hx) + 24 * len(hx) + (32 if not part.massless else 0)
             else:
                 rk = [k for k in kids if k[1] == 0][0]
                 ck = [k for k in kids if k[1] == 1][0]
@@ -240,9 +268,11 @@ class _Emitter:
                 if massive:
                     self.cpl(part.mass)
                     self.cpl(part.width)
-                E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::ffv_current<R>({rk[2]}, {ck[2]}, {cargs}), "
-                  f"k{nid}, inv{nid}, {str(massive).lower()}, {mc2});")
-                self.flops32 += 48 * nch + (60 if massive else 24)
+                hr, hc = self.half[rk[2]], self.half[ck[2]]
+                E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::ffv_current<R, {_tag(hr)}, {_tag(hc)}>("
+                  f"{rk[2]}, {ck[2]}, {cargs}), k{nid}, inv{nid}, {str(massive).lower()}, {mc2});")
+                nterm = int(has_l and "l" in hr and "u" in hc) + int(has_r and "u" in hr and "l" in hc)
+                self.flops32 += 48 * nterm + (60 if massive else 24)
         elif v.kind == "VVV":
             g = self.cpl(v.couplings[0])
             a, b = kids
@@ -309,9 +339,11 @@ class _Emitter:
             has_l, has_r = gl != "ZERO", gr != "ZERO"
             gls = self.cpl(gl) if has_l else "0.0"
             grs = self.cpl(gr) if has_r else "0.0"
-            expr = (f"me::ffv_amp<R>({slot[0]}, {slot[1]}, {slot[2]}, (R){gls}, (R){grs}, "
+            hr, hc = self.half[slot[0]], self.half[slot[1]]
+            expr = (f"me::ffv_amp<R, {_tag(hr)}, {_tag(hc)}>({slot[0]}, {slot[1]}, {slot[2]}, (R){gls}, (R){grs}, "
                     f"{str(has_l).lower()}, {str(has_r).lower()})")
-            self.flops32 += 40 * (int(has_l) + int(has_r)) + 30
+            nterm = int(has_l and "u" in hc and "l" in hr) + int(has_r and "l" in hc and "u" in hr)
+            self.flops32 += 40 * nterm + 16 * nterm
         elif v.kind == "VVV":
             g = self.cpl(v.couplings[0])
             k0 = [c for c, s, _ in kids if s == 0][0]

@@ -127,15 +127,25 @@ DF_HD df from_double(double x) {
   return df{hi, lo};
 }
 
-// Uniform deviate ((x >> 11) + 1/2) 2^-53 as a double-float, from integer operations.
-// hi = k rounded to 24 bits; the exact integer remainder (plus 1/2) rounded to FP32
-// carries the next 24 bits, so the relative error is below 2^-48 for every k.
+// Exact FP32 value of a 23-bit unsigned integer without a conversion
+// instruction: 2^23 + c has the bit pattern 0x4B000000 | c.
+DF_HD float u23_to_float(uint32_t c) {
+  const uint32_t b = 0x4B000000u | c;
+  float f;
+  memcpy(&f, &b, 4);
+  return df_sub_rn(f, 8388608.0f);
+}
+
+// Uniform deviate ((x >> 11) + 1/2) 2^-53 as a double-float from integer and
+// FP32 operations only: k = x >> 11 (53 bits) = c2 2^46 + c1 2^23 + c0 with
+// 7-, 23- and 23-bit pieces, each converted exactly; relative error < 2^-48.
 DF_HD df unit_df(uint64_t x) {
-  const uint64_t k = x >> 11;                       // 53 bits
-  const float hi = (float)k;
-  const int64_t rem2 = 2 * ((int64_t)k - (int64_t)(uint64_t)hi) + 1;  // 2 (k - hi) + 1, exact
-  const df u = fast_two_sum(hi, (float)rem2 * 0.5f);
-  return df{u.hi * 0x1p-53f, u.lo * 0x1p-53f};
+  const uint64_t k = x >> 11;
+  const float c2 = u23_to_float((uint32_t)(k >> 46));
+  const float c1 = u23_to_float((uint32_t)(k >> 23) & 0x7fffffu);
+  const float c0 = u23_to_float((uint32_t)k & 0x7fffffu);
+  const df hi = two_sum(c2 * 0x1p-7f, c1 * 0x1p-30f);
+  return hi + (c0 + 0.5f) * 0x1p-53f;
 }
 
 // ---------------------------------------------------------------------------

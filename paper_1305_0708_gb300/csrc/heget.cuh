@@ -163,17 +163,26 @@ template <class R> ME_HD void vsigbar(const W4<R>& V, cx<R> m[4]) {
   m[3] = V.c[0] - V.c[3];
 }
 
+// Which halves of a four-spinor can be non-zero.  A massless line of definite
+// chirality keeps one half zero exactly: a left-chiral column spinor has only
+// its upper (P_L) half, its Dirac adjoint only the lower half.  The compiler
+// knows the half of every spinor and instantiates these functions so that the
+// zero half is neither read nor computed (IEEE arithmetic would not let the
+// compiler drop products with zeros on its own).
+enum : int { kUp = 0, kLo = 1, kAll = 2 };
+
 // Gamma psi for a column spinor: (gR (V.s) psi_lo, gL (V.sb) psi_up)
-template <class R> ME_HD W4<R> ffv_col(const W4<R>& psi, const W4<R>& V, R gl, R gr, bool has_l, bool has_r) {
+template <class R, int H = kAll>
+ME_HD W4<R> ffv_col(const W4<R>& psi, const W4<R>& V, R gl, R gr, bool has_l, bool has_r) {
   W4<R> o;
   const cx<R> z = mk(R(0), R(0));
-  if (has_r) {
+  if (H != kUp && has_r) {
     cx<R> m[4];
     vsig(V, m);
     o.c[0] = gr * (m[0] * psi.c[2] + m[1] * psi.c[3]);
     o.c[1] = gr * (m[2] * psi.c[2] + m[3] * psi.c[3]);
   } else { o.c[0] = z; o.c[1] = z; }
-  if (has_l) {
+  if (H != kLo && has_l) {
     cx<R> m[4];
     vsigbar(V, m);
     o.c[2] = gl * (m[0] * psi.c[0] + m[1] * psi.c[1]);
@@ -183,16 +192,17 @@ template <class R> ME_HD W4<R> ffv_col(const W4<R>& psi, const W4<R>& V, R gl, R
 }
 
 // row Gamma: (gL row_lo (V.sb), gR row_up (V.s))
-template <class R> ME_HD W4<R> ffv_row(const W4<R>& row, const W4<R>& V, R gl, R gr, bool has_l, bool has_r) {
+template <class R, int H = kAll>
+ME_HD W4<R> ffv_row(const W4<R>& row, const W4<R>& V, R gl, R gr, bool has_l, bool has_r) {
   W4<R> o;
   const cx<R> z = mk(R(0), R(0));
-  if (has_l) {
+  if (H != kUp && has_l) {
     cx<R> m[4];
     vsigbar(V, m);
     o.c[0] = gl * (row.c[2] * m[0] + row.c[3] * m[2]);
     o.c[1] = gl * (row.c[2] * m[1] + row.c[3] * m[3]);
   } else { o.c[0] = z; o.c[1] = z; }
-  if (has_r) {
+  if (H != kLo && has_r) {
     cx<R> m[4];
     vsig(V, m);
     o.c[2] = gr * (row.c[0] * m[0] + row.c[1] * m[2]);
@@ -201,19 +211,25 @@ template <class R> ME_HD W4<R> ffv_row(const W4<R>& row, const W4<R>& V, R gl, R
   return o;
 }
 
-// row Gamma column
-template <class R> ME_HD cx<R> ffv_amp(const W4<R>& row, const W4<R>& col, const W4<R>& V, R gl, R gr,
-                                       bool has_l, bool has_r) {
-  W4<R> g = ffv_col(col, V, gl, gr, has_l, has_r);
-  return row.c[0] * g.c[0] + row.c[1] * g.c[1] + row.c[2] * g.c[2] + row.c[3] * g.c[3];
+// row Gamma column; HR, HC: halves of the row and the column
+template <class R, int HR = kAll, int HC = kAll>
+ME_HD cx<R> ffv_amp(const W4<R>& row, const W4<R>& col, const W4<R>& V, R gl, R gr, bool has_l, bool has_r) {
+  const W4<R> g = ffv_col<R, HC>(col, V, gl, gr, has_l, has_r);
+  // g has the half opposite to HC; only the overlap with the row contributes
+  constexpr bool up = (HC != kUp) && (HR != kLo);   // g upper half (from psi_lo) meets row upper half
+  constexpr bool lo = (HC != kLo) && (HR != kUp);
+  cx<R> a = mk(R(0), R(0));
+  if (up) a = a + row.c[0] * g.c[0] + row.c[1] * g.c[1];
+  if (lo) a = a + row.c[2] * g.c[2] + row.c[3] * g.c[3];
+  return a;
 }
 
 // J^mu = row gamma^mu (gL P_L + gR P_R) col = gL row_lo sb^mu col_up + gR row_up s^mu col_lo
-template <class R> ME_HD W4<R> ffv_current(const W4<R>& row, const W4<R>& col, R gl, R gr, bool has_l,
-                                           bool has_r) {
+template <class R, int HR = kAll, int HC = kAll>
+ME_HD W4<R> ffv_current(const W4<R>& row, const W4<R>& col, R gl, R gr, bool has_l, bool has_r) {
   W4<R> J;
   cx<R> s0 = mk(R(0), R(0)), s1 = s0, s2 = s0, s3 = s0;
-  if (has_l) {  // a = row_lo, b = col_up, sigmabar: (1, -sigma)
+  if (has_l && HR != kUp && HC != kLo) {  // a = row_lo, b = col_up, sigmabar: (1, -sigma)
     const cx<R> a0 = row.c[2], a1 = row.c[3], b0 = col.c[0], b1 = col.c[1];
     const cx<R> t00 = a0 * b0, t11 = a1 * b1, t01 = a0 * b1, t10 = a1 * b0;
     s0 = s0 + gl * (t00 + t11);
@@ -221,7 +237,7 @@ template <class R> ME_HD W4<R> ffv_current(const W4<R>& row, const W4<R>& col, R
     s2 = s2 - gl * mul_i(t10 - t01);
     s3 = s3 - gl * (t00 - t11);
   }
-  if (has_r) {  // a = row_up, b = col_lo, sigma: (1, sigma)
+  if (has_r && HR != kLo && HC != kUp) {  // a = row_up, b = col_lo, sigma: (1, sigma)
     const cx<R> a0 = row.c[0], a1 = row.c[1], b0 = col.c[2], b1 = col.c[3];
     const cx<R> t00 = a0 * b0, t11 = a1 * b1, t01 = a0 * b1, t10 = a1 * b0;
     s0 = s0 + gr * (t00 + t11);
@@ -236,37 +252,47 @@ template <class R> ME_HD W4<R> ffv_current(const W4<R>& row, const W4<R>& col, R
 // ---------------------------------------------------------------------------
 // propagators (numerators times the reciprocal denominator inv = 1/(q^2 - m^2 + i m w))
 // ---------------------------------------------------------------------------
-// (qslash + m) x inv for a column;  q is the momentum along the fermion arrow
-template <class R> ME_HD W4<R> prop_col(const W4<R>& x, P4<R> q, R m, cx<R> inv) {
+// (qslash + m) x inv for a column with non-zero half HX;  q is the momentum along the fermion arrow
+template <class R, int HX = kAll>
+ME_HD W4<R> prop_col(const W4<R>& x, P4<R> q, R m, cx<R> inv) {
   // q.sigma = [[q0-q3, -q1+iq2], [-q1-iq2, q0+q3]],  q.sigmabar = [[q0+q3, q1-iq2], [q1+iq2, q0-q3]]
   const cx<R> s00 = mk(q.e - q.z, R(0)), s01 = mk(-q.x, q.y), s10 = mk(-q.x, -q.y), s11 = mk(q.e + q.z, R(0));
   const cx<R> b00 = mk(q.e + q.z, R(0)), b01 = mk(q.x, -q.y), b10 = mk(q.x, q.y), b11 = mk(q.e - q.z, R(0));
+  const cx<R> z = mk(R(0), R(0));
   W4<R> o;
-  o.c[0] = s00 * x.c[2] + s01 * x.c[3];
-  o.c[1] = s10 * x.c[2] + s11 * x.c[3];
-  o.c[2] = b00 * x.c[0] + b01 * x.c[1];
-  o.c[3] = b10 * x.c[0] + b11 * x.c[1];
+  if (HX != kUp) {
+    o.c[0] = (s00 * x.c[2] + s01 * x.c[3]) * inv;
+    o.c[1] = (s10 * x.c[2] + s11 * x.c[3]) * inv;
+  } else { o.c[0] = z; o.c[1] = z; }
+  if (HX != kLo) {
+    o.c[2] = (b00 * x.c[0] + b01 * x.c[1]) * inv;
+    o.c[3] = (b10 * x.c[0] + b11 * x.c[1]) * inv;
+  } else { o.c[2] = z; o.c[3] = z; }
   if (m != R(0)) {
-    for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] + m * x.c[k];
+    for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] + (m * x.c[k]) * inv;
   }
-  for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] * inv;
   return o;
 }
 
-// x (qslash + m) inv for a row
-template <class R> ME_HD W4<R> prop_row(const W4<R>& x, P4<R> q, R m, cx<R> inv) {
+// x (qslash + m) inv for a row with non-zero half HX
+template <class R, int HX = kAll>
+ME_HD W4<R> prop_row(const W4<R>& x, P4<R> q, R m, cx<R> inv) {
   const cx<R> s00 = mk(q.e - q.z, R(0)), s01 = mk(-q.x, q.y), s10 = mk(-q.x, -q.y), s11 = mk(q.e + q.z, R(0));
   const cx<R> b00 = mk(q.e + q.z, R(0)), b01 = mk(q.x, -q.y), b10 = mk(q.x, q.y), b11 = mk(q.e - q.z, R(0));
+  const cx<R> z = mk(R(0), R(0));
   W4<R> o;
   // (x_up, x_lo) [[0, q.s], [q.sb, 0]] = (x_lo q.sb, x_up q.s)
-  o.c[0] = x.c[2] * b00 + x.c[3] * b10;
-  o.c[1] = x.c[2] * b01 + x.c[3] * b11;
-  o.c[2] = x.c[0] * s00 + x.c[1] * s10;
-  o.c[3] = x.c[0] * s01 + x.c[1] * s11;
+  if (HX != kUp) {
+    o.c[0] = (x.c[2] * b00 + x.c[3] * b10) * inv;
+    o.c[1] = (x.c[2] * b01 + x.c[3] * b11) * inv;
+  } else { o.c[0] = z; o.c[1] = z; }
+  if (HX != kLo) {
+    o.c[2] = (x.c[0] * s00 + x.c[1] * s10) * inv;
+    o.c[3] = (x.c[0] * s01 + x.c[1] * s11) * inv;
+  } else { o.c[2] = z; o.c[3] = z; }
   if (m != R(0)) {
-    for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] + m * x.c[k];
+    for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] + (m * x.c[k]) * inv;
   }
-  for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] * inv;
   return o;
 }
 

@@ -23,6 +23,11 @@ struct KinDev {
   double bw_mass[2], bw_width[2], bw_t0[2], bw_t1[2];  // top, W
   int32_t massive;       // any final-state mass (RAMBO)
   uint32_t cut_mask;     // bit k set: leg k is cut
+  // FP32 / double-float copies formed on the host (no FP64 arithmetic per draw)
+  float sqrt_s_f[2];     // sqrt_s as (hi, lo)
+  double shat_fixed;     // sqrt_s^2
+  float f_ptmin2, f_sinh2, f_cdr, f_chd, f_shd, f_dr2;
+  double wfactor;        // constant weight factor W_PS s_ident pb / (2 s): fixed-energy generators, else 0
 };
 
 constexpr int kThreads = 128;
@@ -44,7 +49,8 @@ struct ProcessDesc {
                              int eval_me, cudaStream_t s, int grid);
   cudaError_t (*launch_step)(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t m,
                              const double* params, void* ws, double* partials, double* me2_out, double* mom_out,
-                             int64_t out_stride, int* status, cudaStream_t s, int grid_ps, int grid_me);
+                             int64_t out_stride, int* status, cudaStream_t s, int grid_ps, int grid_me,
+                             cudaEvent_t ev_mid);
 };
 
 }  // namespace me

@@ -115,6 +115,10 @@ struct me_handle_s {
   double* h_acc = nullptr;    // pinned, 3 doubles + status
   void* d_ws = nullptr;       // phase-space points of one chunk (k_ps -> k_me)
   size_t ws_cap = 0;
+  // optional per-kernel timing of xsec_step (CUDA events on the call's stream)
+  bool timing = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  double t_ps = 0.0, t_me = 0.0;
   std::mutex mu;
 };
 
@@ -210,6 +214,22 @@ me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
     k.bw_t1[r] = std::atan(x);
   }
   if (kin->kind == ME_PS_TTBAR && !(p.wt > 0 && p.wW > 0)) return fail(ME_ERR_ARG, "ttbar generator needs widths");
+  k.sqrt_s_f[0] = (float)kin->sqrt_s;
+  k.sqrt_s_f[1] = (float)(kin->sqrt_s - (double)k.sqrt_s_f[0]);
+  k.shat_fixed = kin->sqrt_s * kin->sqrt_s;
+  k.f_ptmin2 = (float)(k.pt_min * k.pt_min);
+  k.f_sinh2 = (float)k.sinh2_eta_max;
+  k.f_cdr = (float)k.cos_dr;
+  k.f_chd = (float)k.cosh_dr;
+  k.f_shd = (float)k.sinh_dr;
+  k.f_dr2 = (float)(k.dr_min * k.dr_min);
+  const double gev2pb = 0.3893793721e9;
+  if (kin->kind == ME_PS_TWO_BODY)
+    k.wfactor = (1.0 / (8.0 * kPi)) * k.s_ident * gev2pb / (2.0 * k.shat_fixed);
+  else if (kin->kind == ME_PS_RAMBO && !k.massive)
+    k.wfactor = k.rambo_volume * k.s_ident * gev2pb / (2.0 * k.shat_fixed);
+  else
+    k.wfactor = 0.0;
   return ME_OK;
 }
 
@@ -383,11 +403,21 @@ me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t
   for (int64_t c = 0; c < nchunks; ++c) {
     const int64_t first = c * kChunk;
     const int64_t m = std::min<int64_t>(kChunk, n_accept - first);
+    if (h->timing) cudaEventRecord(h->ev[0], s);
     e = h->desc->launch_step(h->prec, &k, seed, counter_offset + (uint64_t)first, m, h->cvals.data(), h->d_ws,
                              h->d_partials + 3 * (size_t)grid_me * c, me2_out ? me2_out + first : nullptr,
                              momenta_out ? momenta_out + first : nullptr, n_accept, h->d_status, s, grid_ps,
-                             grid_me);
+                             grid_me, h->timing ? h->ev[1] : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "xsec_step launch");
+    if (h->timing) {
+      cudaEventRecord(h->ev[2], s);
+      if ((e = cudaEventSynchronize(h->ev[2])) != cudaSuccess) return cuda_fail(e, "xsec_step timing");
+      float a = 0, b = 0;
+      cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+      cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+      h->t_ps += a;
+      h->t_me += b;
+    }
   }
   k_reduce_partials<<<1, 256, 0, s>>>(h->d_partials, (int)(grid_me * nchunks), h->d_acc);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "xsec_step reduce");
@@ -452,6 +482,23 @@ me_status xsec_step_noalloc(me_handle h, uint64_t seed, uint64_t counter_offset,
   return ME_OK;
 }
 
+me_status me_step_timing(me_handle h, int32_t enable, double* ms_ps, double* ms_me) {
+  me_status st = check_handle(h);
+  if (st != ME_OK) return st;
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (ms_ps) *ms_ps = h->t_ps;
+  if (ms_me) *ms_me = h->t_me;
+  h->t_ps = h->t_me = 0.0;
+  if (enable && !h->ev[0]) {
+    for (int i = 0; i < 3; ++i) {
+      cudaError_t e = cudaEventCreate(&h->ev[i]);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+  }
+  h->timing = enable != 0;
+  return ME_OK;
+}
+
 me_status me_xsec_estimate(const me_xsec_acc* acc, double* sigma, double* error) {
   if (!acc || !sigma || !error) return fail(ME_ERR_ARG, "me_xsec_estimate: null argument");
   if (acc->n_try <= 0) return fail(ME_ERR_STATE, "me_xsec_estimate: empty accumulator");
@@ -487,6 +534,8 @@ void me_destroy(me_handle h) {
   if (h->d_status) cudaFree(h->d_status);
   if (h->h_acc) cudaFreeHost(h->h_acc);
   if (h->d_ws) cudaFree(h->d_ws);
+  for (int i = 0; i < 3; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;
 }
 

@@ -35,7 +35,7 @@ struct Philox {
                                                         uint64_t k0, uint64_t k1, uint64_t out[4]) {
     const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
     const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < 10; ++r) {
       uint64_t h0, l0, h1, l1;
       mulhilo(M0, c0, h0, l0);
@@ -297,7 +297,7 @@ __host__ __device__ __forceinline__ bool pass_cuts(const KinDev& kin, const doub
     af[i] = zf * ip;                          // sinh(eta)
     rf[i] = sqrtf(p2f + zf * zf) * ip;        // cosh(eta)
   }
-  const float cdr = (float)kin.cos_dr, chd = (float)kin.cosh_dr, shd = (float)kin.sinh_dr;
+  const float cdr = kin.f_cdr, chd = kin.f_chd, shd = kin.f_shd;
 #pragma unroll
   for (int i = 2; i < NEXT; ++i) {
 #pragma unroll
@@ -368,7 +368,7 @@ template <int NEXT>
 __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
                                          df (&p)[NEXT][4]) {
   constexpr int NF = NEXT - 2;
-  const df w = from_double(kin.sqrt_s);
+  const df w = df{kin.sqrt_s_f[0], kin.sqrt_s_f[1]};
   const df hw = df{w.hi * 0.5f, w.lo * 0.5f};
   const df z = df{0.0f, 0.0f};
   p[0][0] = hw; p[0][1] = z; p[0][2] = z; p[0][3] = hw;
@@ -416,9 +416,9 @@ template <int NEXT>
 __host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const df (&p)[NEXT][4]) {
   const uint32_t mask = kin.cut_mask;
   if (mask == 0) return true;
-  const float ptmin2 = (float)(kin.pt_min * kin.pt_min), sh2 = (float)kin.sinh2_eta_max;
-  const float cdr = (float)kin.cos_dr, chd = (float)kin.cosh_dr, shd = (float)kin.sinh_dr;
-  const float dr2 = (float)(kin.dr_min * kin.dr_min);
+  const float ptmin2 = kin.f_ptmin2, sh2 = kin.f_sinh2;
+  const float cdr = kin.f_cdr, chd = kin.f_chd, shd = kin.f_shd;
+  const float dr2 = kin.f_dr2;
   float ptf[NEXT], af[NEXT], rf[NEXT];
   bool undecided = false;
 #pragma unroll
@@ -482,7 +482,7 @@ __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64
   if (kin.kind == ME_PS_RAMBO && !kin.massive) {
     rambo_df<NEXT>(kin, seed, event, att, p);
     wps = kin.rambo_volume;
-    shat = kin.sqrt_s * kin.sqrt_s;
+    shat = kin.shat_fixed;
     return pass_cuts_df<NEXT>(kin, p);
   }
   double pd[NEXT][4];

@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const vo
                                                               : (const void*)(pd + (int64_t)NEXT * 4 * m));
   const double* shat_a = wps_a + m;
   const int32_t* tries_a = reinterpret_cast<const int32_t*>(shat_a + m);
-  double sw = 0.0, sw2 = 0.0, nt = 0.0;
+  double sw = 0.0, sw2 = 0.0;
+  int64_t ntries = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     const double wps = wps_a[i], shat = shat_a[i];
     const bool ok = wps > 0.0;
@@ -369,28 +370,28 @@ __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const vo
         }
       }
     }
-    const double w = ok ? wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb : 0.0;
+    // constant weight factor for fixed-energy generators (one FP64 multiply per point)
+    const double w = !ok ? 0.0 : (kin.wfactor > 0.0 ? m2 * kin.wfactor
+                                                     : wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb);
     sw += w;
-    sw2 += w * w;
-    nt += (double)tries_a[i];
+    sw2 = fma(w, w, sw2);
+    ntries += tries_a[i];
     if (me2_out) me2_out[i] = m2;
   }
-  block_reduce3(sw, sw2, nt, partials);
+  block_reduce3(sw, sw2, (double)ntries, partials);
 }
 
 template <class P>
 cudaError_t launch_step(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t m, const double* params,
                         void* ws, double* partials, double* me2_out, double* mom_out, int64_t out_stride,
-                        int* status, cudaStream_t s, int grid_ps, int grid_me) {
+                        int* status, cudaStream_t s, int grid_ps, int grid_me, cudaEvent_t ev_mid) {
   typename P::Params prm;
   memcpy(&prm, params, sizeof(prm));
-  if (prec == ME_FP64) {
-    k_ps<P, false><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
-    k_me<P, false><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
-  } else {
-    k_ps<P, true><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
-    k_me<P, true><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
-  }
+  if (prec == ME_FP64) k_ps<P, false><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
+  else k_ps<P, true><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
+  if (ev_mid) cudaEventRecord(ev_mid, s);
+  if (prec == ME_FP64) k_me<P, false><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
+  else k_me<P, true><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
   return cudaGetLastError();
 }
 
