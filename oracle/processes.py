@@ -457,7 +457,7 @@ def gluon_partial_amplitudes(K, E, g):
     return orders, np.stack(A, axis=0)
 
 
-def gluons(P, n_in=2, par=SMParams(), per_helicity=False, eps_override=None, colour_matrix=None):
+def gluons(P, par=SMParams(), per_helicity=False, eps_override=None, colour_matrix=None, n_in=2):
     """g g > g ... g: sum over all helicities of sum_{sigma,tau} A_sigma C A_tau^*.
 
     Full amplitude: i M = sum_sigma Tr(T^{a1} T^{a_sigma2} ...) A(1, sigma),
