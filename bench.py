@@ -123,7 +123,7 @@ def oracle_step(w, events):
     from oracle.sm import SMParams
     fn = {"u u~ > e+ e-": opr.uux_epem, "u d~ > e+ ve g g": opr.udx_epvegg,
           "g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))": opr.gg_ttx_dilep,
-          "u s > d c h h": opr.us_dchh}[w["process"]]
+          "u s > d c h h": opr.us_dchh, "g g > g g g g": opr.gluons}[w["process"]]
     par = SMParams()
     P, W, S, T = oxs.generate(oracle_kin(w), par, w["seed"], events)
     return oxs.accumulate(fn(P, par), W, S, T, w["s_ident"])

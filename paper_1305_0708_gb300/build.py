@@ -32,6 +32,9 @@ PROCESSES = [
     ("g g > g g", []),
 ]
 
+# all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)
+GLUON_PROCESSES = [(5, "g g > g g g"), (6, "g g > g g g g")]
+
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", INCLUDE, "-I", CSRC, "-I", GEN]
@@ -76,6 +79,25 @@ def generate_units():
                     flops_amp=info["flops_amp"], flops_fp64=info["flops_fp64"],
                     pdg=[PARTICLES[l.particle].pdg for l in prog.legs])
         units.append((tag, path, meta))
+    # all-gluon units: recursion tables, colour matrix, registry entries
+    from paper_1305_0708_gb300.compiler import gluon as gl
+    from paper_1305_0708_gb300.compiler.diagrams import generate, parse
+    for ng, name in GLUON_PROCESSES:
+        hsrc, tab = gl.header(ng)
+        hpath = os.path.join(GEN, f"gluon_tables{ng}.h")
+        if not os.path.exists(hpath) or open(hpath).read() != hsrc:
+            with open(hpath, "w") as f:
+                f.write(hsrc)
+        f3, f4 = 158.0, 194.0
+        cur = sum(len(v3) * f3 + len(v4) * f4 + 8 for _, v3, v4 in tab["currents"][ng - 1:])
+        amp = sum(len(v3) * f3 + len(v4) * f4 + 28 for _, v3, v4 in tab["amps"])
+        colour_fl = 8.0 * len(tab["amps"]) ** 2
+        flops = (2 ** (ng - 1)) * (cur + amp + colour_fl)
+        _, amps = generate(parse(name))
+        meta = dict(name=name, aliases=[], tag=f"gluon{ng}", n_ext=ng, params=["GS"], n_hel=2 ** ng,
+                    n_hel_live=2 ** ng, n_colour=len(tab["amps"]), n_diagrams=len(amps), flops_amp=flops,
+                    flops_fp64=flops, pdg=[21] * ng, gluon=ng)
+        units.append((f"gluon{ng}", None, meta))
     # double-float tables
     from paper_1305_0708_gb300.compiler import dftables
     tpath = os.path.join(GEN, "dfloat_tables.h")
@@ -129,12 +151,12 @@ def _headers_hash():
     return _hash(*parts)
 
 
-def _compile(src, obj, hh, verbose):
+def _compile(src, obj, hh, verbose, extra=()):
     stamp = obj + ".hash"
-    h = _hash(open(src, "rb").read(), hh, " ".join(NVCC_FLAGS))
+    h = _hash(open(src, "rb").read(), hh, " ".join(NVCC_FLAGS), " ".join(extra))
     if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == h:
         return obj, False
-    cmd = [nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj]
+    cmd = [nvcc()] + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -150,13 +172,18 @@ def build(verbose=False, jobs=None):
     units, rpath = generate_units()
     os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
     hh = _headers_hash()
-    srcs = [os.path.join(CSRC, s) for s in STATIC_SOURCES] + [p for _, p, _ in units] + [rpath]
+    jobs_list = [(os.path.join(CSRC, s), os.path.basename(s) + ".o", ()) for s in STATIC_SOURCES]
+    for tag, path, m in units:
+        if m.get("gluon"):
+            jobs_list.append((os.path.join(CSRC, "gluon_process.cu"), f"{tag}.o", (f"-DNGLUON={m['gluon']}",)))
+        else:
+            jobs_list.append((path, os.path.basename(path) + ".o", ()))
+    jobs_list.append((rpath, "registry.cu.o", ()))
     objs = []
-    jobs = jobs or min(len(srcs), os.cpu_count() or 4)
+    jobs = jobs or min(len(jobs_list), os.cpu_count() or 4)
     changed = False
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        futs = [ex.submit(_compile, s, os.path.join(BUILD, "obj", os.path.basename(s) + ".o"), hh, verbose)
-                for s in srcs]
+        futs = [ex.submit(_compile, s, os.path.join(BUILD, "obj", o), hh, verbose, extra) for s, o, extra in jobs_list]
         for f in futs:
             o, ch = f.result()
             objs.append(o)

@@ -21,6 +21,11 @@ WORKLOADS = {
         n=1 << 20, seed=2, cuts=None, s_ident=1.0,
         describe="g g > t t~ > b e+ ve b~ e- ve~, sqrt(s) uniform in [400, 2000] GeV, Breit-Wigner t and W, "
                  "isotropic decays, 2^20 points, seed 2"),
+    "gg_gggg": dict(
+        process="g g > g g g g", kind="rambo", sqrt_s=1500.0, n=1 << 18, seed=3,
+        cuts=dict(legs=(2, 3, 4, 5), pt_min=30.0, eta_max=2.5, dr_min=0.4), s_ident=1.0 / 24.0,
+        describe="g g > g g g g (six gluons, 120 colour orderings), RAMBO at sqrt(s)=1.5 TeV, pT>30, |eta|<2.5, "
+                 "DeltaR>0.4 on the four final gluons, 2^18 accepted points, seed 3"),
     "us_dchh": dict(
         process="u s > d c h h", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 0, 0, 125.0, 125.0), n=1 << 18, seed=4,
         cuts=None, s_ident=0.5,

@@ -35,7 +35,7 @@ from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args  # noqa: E402
 
 PAR = SMParams()
 ORACLE = {"uux_epem": opr.uux_epem, "udx_epvegg": opr.udx_epvegg, "gg_ttx_dilep": opr.gg_ttx_dilep,
-          "us_dchh": opr.us_dchh}
+          "us_dchh": opr.us_dchh, "gg_gggg": opr.gluons}
 
 
 def oracle_kin(w):
@@ -90,7 +90,7 @@ def eval_gpu(B, process, P, prec):
 def test_me_eval_parity(B, key):
     """me_eval on oracle-generated points (several tiles and a ragged tail)."""
     w = WORKLOADS[key]
-    n = 1000 if key != "gg_ttx_dilep" else 400
+    n = {"gg_ttx_dilep": 400, "gg_gggg": 200}.get(key, 1000)
     P, _, _, _ = oxs.generate(oracle_kin(w), PAR, 99, np.arange(n))
     ref = ORACLE[key](P, PAR)
     g64 = eval_gpu(B, w["process"], P, B.ME_FP64)
@@ -146,6 +146,23 @@ def test_xsec_step_parity(B, key):
     s_gpu = B.me_xsec_estimate(acc)
     s_or = oxs.estimate(sw, sw2, ntry)
     assert s_gpu[0] == pytest.approx(s_or[0], rel=1e-11) and s_gpu[1] == pytest.approx(s_or[1], rel=1e-8)
+
+
+def test_five_gluons_parity(B):
+    """g g > g g g through the colour-ordered block kernel, both paths."""
+    from oracle import phasespace as ps
+    n = 300
+    u = ps.uniforms(11, np.arange(n), np.zeros(n), 3)
+    pf, _ = ps.rambo_massless(1000.0, 3, u)
+    P = np.zeros((n, 5, 4))
+    P[:, 0], P[:, 1] = ps.incoming(1000.0, n)
+    P[:, 2:] = pf
+    ref = opr.gluons(P, par=PAR)
+    g64 = eval_gpu(B, "g g > g g g", P, B.ME_FP64)
+    tol = fp64_tolerance(opr.gluons, P, ref)
+    assert np.all(np.abs(g64 - ref) <= tol)
+    rel = np.abs(eval_gpu(B, "g g > g g g", P, B.ME_MIXED) / ref - 1)
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
 
 
 def test_edge_cases(B):
