@@ -42,6 +42,15 @@ def fp32_alu_peak_tflops(mhz=SM_MAX_MHZ):
     return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
+def tensor_peak_tflops():
+    """Measured dense bf16 tensor peak of this GPU type (burst), else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -167,6 +176,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1000)
     ap.add_argument("--cpu-sample", type=int, default=1000)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--points", type=int, default=0,
+                    help="points per step instead of the workload's own count (small cases for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -193,7 +204,7 @@ def main():
     B.load()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = w["n"]
+    n = args.points if args.points > 0 else w["n"]
     kin = B.make_kin(**kin_args(w))
     stream = torch.cuda.current_stream(dev)
     offset0 = rank * (1 << 40)
@@ -251,11 +262,21 @@ def main():
     ps_tflops = PS_FLOPS_PER_DRAW.get(w["kind"], 0.0) * tries_per_point * n / (ps_ms * 1e-3) / 1e12
     kernels = {
         "k_me": {"ms": me_ms, "achieved_tflops": me_tflops, "frac": me_tflops / peak,
-                 "flops_per_point": flops_event, "what": "|M|^2, weights, block sums (FP32 amplitudes)"},
+                 "flops_per_point": flops_event,
+                 "what": "|M|^2, weights, block sums (FP32 amplitudes; CUDA-core flops)"},
         "k_ps": {"ms": ps_ms, "achieved_tflops": ps_tflops, "frac": ps_tflops / peak,
                  "flops_per_draw": PS_FLOPS_PER_DRAW.get(w["kind"], 0.0), "draws_per_point": tries_per_point,
                  "what": "Philox + double-float RAMBO + cuts + redraw queue"},
     }
+    if info.flops_colour > 0:
+        # colour quadratic form on the tensor cores (FP16 hi/lo operands, FP32 accumulation):
+        # algorithmic flops against the measured dense bf16 peak (FP16 runs at the same rate)
+        tpk = tensor_peak_tflops()
+        col_tflops = info.flops_colour * n / (me_ms * 1e-3) / 1e12
+        kernels["k_me"]["tensor"] = {"flops_per_point": info.flops_colour, "achieved_tflops": col_tflops,
+                                     "peak": tpk, "frac": col_tflops / tpk,
+                                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+                                     "what": "colour sum x.C.x, mma.sync m16n8k16 f16, hi/lo split"}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     achieved = kernels[dom]["achieved_tflops"]
 

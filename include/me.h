@@ -103,8 +103,11 @@ typedef struct {
   int32_t n_colour;        /* colour basis size K */
   int32_t n_diagrams;      /* Feynman-diagram amplitudes (a 4-gluon vertex counts 3) */
   int32_t pdg[16];         /* PDG code per leg */
-  double flops_amp;        /* amplitude-precision flops per event (compiler count) */
-  double flops_fp64;       /* FP64 flops per event in the amplitude kernel (momenta, invariants) */
+  double flops_amp;        /* mixed path: FP32 CUDA-core flops per event (compiler count) */
+  double flops_fp64;       /* FP64 path: flops per event (compiler count, colour sum included) */
+  double flops_colour;     /* mixed path: colour quadratic-form flops per event run on the tensor
+                              cores (algorithmic, 8 K^2 per helicity of the non-root legs);
+                              0 where the colour sum is part of flops_amp */
 } me_info_t;
 
 /* Create a handle for a compiled process, e.g. "u d~ > e+ ve g g".

@@ -40,7 +40,8 @@ class me_xsec_acc(ctypes.Structure):
 class me_info_t(ctypes.Structure):
     _fields_ = [("n_ext", ctypes.c_int32), ("n_hel", ctypes.c_int32), ("n_hel_live", ctypes.c_int32),
                 ("n_colour", ctypes.c_int32), ("n_diagrams", ctypes.c_int32), ("pdg", ctypes.c_int32 * 16),
-                ("flops_amp", ctypes.c_double), ("flops_fp64", ctypes.c_double)]
+                ("flops_amp", ctypes.c_double), ("flops_fp64", ctypes.c_double),
+                ("flops_colour", ctypes.c_double)]
 
 
 ME_FP64, ME_MIXED = 0, 1

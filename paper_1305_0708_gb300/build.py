@@ -76,7 +76,7 @@ def generate_units():
             ncomb *= len(l.hels)
         meta = dict(name=name, aliases=aliases, tag=tag, n_ext=prog.n_ext, params=info["params"],
                     n_hel=ncomb, n_hel_live=len(prog.live), n_colour=prog.n_colour, n_diagrams=len(prog.amps),
-                    flops_amp=info["flops_amp"], flops_fp64=info["flops_fp64"],
+                    flops_amp=info["flops_amp"], flops_fp64=info["flops_fp64"], flops_colour=0.0,
                     pdg=[PARTICLES[l.particle].pdg for l in prog.legs])
         units.append((tag, path, meta))
     # all-gluon units: recursion tables, colour matrix, registry entries
@@ -92,11 +92,11 @@ def generate_units():
         cur = sum(len(v3) * f3 + len(v4) * f4 + 8 for _, v3, v4 in tab["currents"][ng - 1:])
         amp = sum(len(v3) * f3 + len(v4) * f4 + 28 for _, v3, v4 in tab["amps"])
         colour_fl = 8.0 * len(tab["amps"]) ** 2
-        flops = (2 ** (ng - 1)) * (cur + amp + colour_fl)
+        nh = 2 ** (ng - 1)
         _, amps = generate(parse(name))
         meta = dict(name=name, aliases=[], tag=f"gluon{ng}", n_ext=ng, params=["GS"], n_hel=2 ** ng,
-                    n_hel_live=2 ** ng, n_colour=len(tab["amps"]), n_diagrams=len(amps), flops_amp=flops,
-                    flops_fp64=flops, pdg=[21] * ng, gluon=ng)
+                    n_hel_live=2 ** ng, n_colour=len(tab["amps"]), n_diagrams=len(amps), flops_amp=nh * (cur + amp),
+                    flops_fp64=nh * (cur + amp + colour_fl), flops_colour=nh * colour_fl, pdg=[21] * ng, gluon=ng)
         units.append((f"gluon{ng}", None, meta))
     # double-float tables
     from paper_1305_0708_gb300.compiler import dftables
@@ -125,6 +125,7 @@ def generate_units():
         lines.append(f"  table[{i}].n_hel = {m['n_hel']}; table[{i}].n_hel_live = {m['n_hel_live']}; "
                      f"table[{i}].n_colour = {m['n_colour']}; table[{i}].n_diagrams = {m['n_diagrams']};")
         lines.append(f"  table[{i}].flops_amp = {float(m['flops_amp'])!r}; table[{i}].flops_fp64 = {float(m['flops_fp64'])!r}; "
+                     f"table[{i}].flops_colour = {float(m['flops_colour'])!r}; "
                      f"table[{i}].pdg = pdg_{tag};")
         lines.append(f"  me_register_{tag}(&table[{i}]);")
     lines.append("  ready = true;")

@@ -108,7 +108,28 @@ def header(n):
 
     cm, ct = flat(cur)
     am, at = flat(amps)
+    # per tuple size S: the entries of that size (currents of one phase, or the amplitudes for
+    # S = n-1) all have S-1 three-vertex and (S-1)(S-2)/2 four-vertex terms; their child indices
+    # are stored slot-major, idx[slot * COUNT + entry], so that a warp reads consecutive entries
+    start, count, off, idx = [0] * n, [0] * n, [0] * n, []
+    by_size = {sz: (st, ct_) for sz, (st, ct_) in zip(range(2, n - 1), t["phases"])}
+    by_size[n - 1] = (0, len(amps))
+    for sz in range(2, n):
+        st, cnt = by_size[sz]
+        ents = amps if sz == n - 1 else cur[st:st + cnt]
+        nv3, nv4 = sz - 1, (sz - 1) * (sz - 2) // 2
+        slots = []
+        for tup, v3, v4 in ents:
+            assert len(tup) == sz and len(v3) == nv3 and len(v4) == nv4
+            slots.append([x for ab in v3 for x in ab] + [x for abc in v4 for x in abc])
+        start[sz], count[sz], off[sz] = st, cnt, len(idx)
+        for j in range(2 * nv3 + 3 * nv4):
+            idx += [row[j] for row in slots]
+    lines.append(f"  static constexpr int START[{n}] = {{{', '.join(map(str, start))}}};")
+    lines.append(f"  static constexpr int COUNT[{n}] = {{{', '.join(map(str, count))}}};")
+    lines.append(f"  static constexpr int IDX_OFF[{n}] = {{{', '.join(map(str, off))}}};")
     lines.append("};")
+    lines.append(f"__device__ const int16_t kIdx{n}[{len(idx)}] = {{" + ", ".join(map(str, idx)) + "};")
     lines.append(f"__device__ const int32_t kCurMeta{n}[{len(cm) * 4}] = {{" +
                  ", ".join(str(x) for m in cm for x in m) + "};")
     lines.append(f"__device__ const int16_t kCurTerms{n}[{max(len(ct), 1)}] = {{" +
@@ -119,9 +140,16 @@ def header(n):
     lines.append(f"__device__ const int32_t kPhase{n}[{max(2 * len(t['phases']), 2)}] = {{" +
                  (", ".join(str(x) for p in t["phases"] for x in p) or "0, 0") + "};")
     cn = t["cnum"]
+    diag = cn[0][0]
+    assert all(cn[i][i] == diag for i in range(len(cn))), "trace colour matrix has a constant diagonal"
+    assert all(cn[i][j] == cn[j][i] for i in range(len(cn)) for j in range(i)), "colour matrix is symmetric"
+    off = max(abs(cn[i][j]) for i in range(len(cn)) for j in range(len(cn)) if i != j)
+    lines.append(f"constexpr float kColourDiag{n} = {float(diag)!r}f;  // off-diagonal max |C| = {off}")
+    lines.append(f"constexpr bool kColourOffFitsHalf{n} = {'true' if off <= 2048 else 'false'};")
     lines.append(f"__device__ const float kColour{n}[{len(cn) * len(cn)}] = {{" +
                  ", ".join(f"{float(x)!r}f" for row in cn for x in row) + "};")
     # host copies for host-side checks
+    lines.append(f"static const int16_t kIdx{n}_h[{len(idx)}] = {{" + ", ".join(map(str, idx)) + "};")
     lines.append(f"static const int32_t kCurMeta{n}_h[{len(cm) * 4}] = {{" +
                  ", ".join(str(x) for m in cm for x in m) + "};")
     lines.append(f"static const int16_t kCurTerms{n}_h[{max(len(ct), 1)}] = {{" +

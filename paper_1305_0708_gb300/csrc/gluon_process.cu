@@ -1,9 +1,22 @@
 // Process unit for NGLUON gluons (compiled once per gluon count with -DNGLUON=n).
 // Kernels: k_eval_gluon (|M|^2 from momenta in HBM) and, for the Monte Carlo
 // step, the generic phase-space kernel k_ps followed by k_me_gluon.  One thread
-// block evaluates one event at a time (grid-stride over events).
+// block evaluates one event at a time (grid-stride over events, one resident
+// wave of blocks); its two halves run two helicities of the non-root legs side
+// by side, and after each such pair the block forms the colour sum of the
+// pair's 8 amplitude rows (2 helicities x 2 root helicities x re/im).
+//
+// Colour sum, Eq. 6 with the exact integer matrix C_num = den C:
+//   FP64 path:  y = C_num x on the FP64 CUDA cores, then x . y;
+//   mixed path: on the tensor cores.  Every row x of the pair is scaled by a
+//   power of two per helicity and split into FP16 hi + lo parts (22 bits); the
+//   off-diagonal part of C_num has integer entries below 2048 and is exact in
+//   FP16; D = C_off [x_hi x_lo]^T accumulates in FP32 (mma.sync m16n8k16);
+//   the constant diagonal of C_num (3641 for six gluons, not exact in FP16) is
+//   added on the CUDA cores in the epilogue, which also forms x . (D + c x).
 #include <cstdint>
 #include <cstring>
+#include <cuda_fp16.h>
 
 #include "gluon.cuh"
 #include "process_common.cuh"
@@ -26,6 +39,18 @@ namespace ME_CAT(g, NGLUON) {  // one namespace per gluon count: the units link 
 
 using T = ME_CAT(Tables, NGLUON);
 constexpr int NG = NGLUON;
+constexpr int HP = 2;                      // helicities evaluated side by side, one per half block
+constexpr int kThreadsG = HP * kThreads;   // threads per block
+constexpr int NHEL = 1 << (NG - 1);        // helicities of the non-root legs
+constexpr int NROW = 4 * HP;               // amplitude rows per pair: (helicity, root helicity, re/im)
+constexpr int MP = (T::NAMP + 15) / 16 * 16;  // colour rows padded to the MMA tile
+constexpr int KP = (T::NAMP + 31) / 32 * 32;  // colour columns padded to two MMA k-steps
+constexpr int XLD = KP + 4;                // FP32 row stride: epilogue reads hit 32 distinct banks
+constexpr int HLD = KP + 8;                // FP16 row stride (272 B for KP = 128): ldmatrix without conflicts
+constexpr float kDiag = ME_CAT(kColourDiag, NGLUON);
+static_assert(ME_CAT(kColourOffFitsHalf, NGLUON), "off-diagonal colour integers must be exact in FP16");
+static_assert(NROW == 8, "one n8 MMA tile per helicity pair");
+static_assert(T::NAMP % 2 == 0, "amplitude rows are converted in pairs");
 
 struct Traits {
   static constexpr int NEXT = NG;
@@ -35,91 +60,269 @@ struct Traits {
 };
 
 __host__ __device__ __forceinline__ const int32_t* cur_meta() { return ME_GTN(kCurMeta); }
-__host__ __device__ __forceinline__ const int16_t* cur_terms() { return ME_GTN(kCurTerms); }
-__host__ __device__ __forceinline__ const int32_t* amp_meta() { return ME_GTN(kAmpMeta); }
-__host__ __device__ __forceinline__ const int16_t* amp_terms() { return ME_GTN(kAmpTerms); }
-__host__ __device__ __forceinline__ const int32_t* phases() { return ME_GTN(kPhase); }
 __host__ __device__ __forceinline__ const float* colour() { return ME_GTN(kColour); }
+
+// Shared-memory storage of currents and momenta: 16-byte aligned with vector
+// loads and stores; the current stride is 48 B (FP32) / 80 B (FP64), not a
+// power of two, so gathers at data-dependent indices spread over the banks.
+template <class R>
+struct alignas(16) JS {
+  R v[sizeof(R) == 4 ? 12 : 10];
+};
+template <class R>
+struct alignas(16) KS {
+  R v[4];
+};
+
+__device__ __forceinline__ W4<float> ldj(const JS<float>& j) {
+  const float4 u = reinterpret_cast<const float4*>(j.v)[0], w = reinterpret_cast<const float4*>(j.v)[1];
+  return W4<float>{{{u.x, u.y}, {u.z, u.w}, {w.x, w.y}, {w.z, w.w}}};
+}
+__device__ __forceinline__ void stj(JS<float>& j, const W4<float>& a) {
+  reinterpret_cast<float4*>(j.v)[0] = make_float4(a.c[0].re, a.c[0].im, a.c[1].re, a.c[1].im);
+  reinterpret_cast<float4*>(j.v)[1] = make_float4(a.c[2].re, a.c[2].im, a.c[3].re, a.c[3].im);
+}
+__device__ __forceinline__ W4<double> ldj(const JS<double>& j) {
+  const double2* q = reinterpret_cast<const double2*>(j.v);
+  const double2 a = q[0], b = q[1], c = q[2], d = q[3];
+  return W4<double>{{{a.x, a.y}, {b.x, b.y}, {c.x, c.y}, {d.x, d.y}}};
+}
+__device__ __forceinline__ void stj(JS<double>& j, const W4<double>& a) {
+  double2* q = reinterpret_cast<double2*>(j.v);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) q[k] = make_double2(a.c[k].re, a.c[k].im);
+}
+__device__ __forceinline__ P4<float> ldk(const KS<float>& k) {
+  const float4 u = *reinterpret_cast<const float4*>(k.v);
+  return P4<float>{u.x, u.y, u.z, u.w};
+}
+__device__ __forceinline__ void stk(KS<float>& k, const P4<float>& p) {
+  *reinterpret_cast<float4*>(k.v) = make_float4(p.e, p.x, p.y, p.z);
+}
+__device__ __forceinline__ P4<double> ldk(const KS<double>& k) {
+  const double2* q = reinterpret_cast<const double2*>(k.v);
+  const double2 a = q[0], b = q[1];
+  return P4<double>{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void stk(KS<double>& k, const P4<double>& p) {
+  double2* q = reinterpret_cast<double2*>(k.v);
+  q[0] = make_double2(p.e, p.x);
+  q[1] = make_double2(p.y, p.z);
+}
 
 template <class R>
 struct Shared {
-  P4<R> K[T::NCUR];       // outgoing momenta of every current (externals first)
+  KS<R> K[T::NCUR];       // outgoing momenta of every current (externals first)
   R invp2[T::NCUR];
-  W4<R> J[T::NCUR];       // currents of the helicity being evaluated
+  JS<R> J[HP][T::NCUR];   // currents of the two helicities being evaluated
+  JS<R> ext[NG - 1][2];   // polarisation vectors of legs 1..NG-1, helicity -1 / +1
   W4<R> eps0[2];          // root polarisation, both helicities
-  cx<R> A[2][T::NAMP];    // amplitudes of both root helicities
-  R red[kThreads / 32];
+  R X[NROW][XLD];         // amplitudes of the pair, row 4 h + 2 r + (0: re, 1: im)
+  unsigned emax[HP];      // largest biased FP32 exponent in the rows of each helicity
+  R red[kThreadsG / 32];
 };
 
-// |M|^2 of one event, computed by the whole block.  p: physical momenta (leg-major).
-template <class R>
-__device__ double event_block(const R (&p)[NG][4], R gs, Shared<R>& sh, const float* sC) {
+// Tensor-core operands of the mixed path (dynamic shared memory after Shared<float>)
+struct TcShared {
+  __half Xh[NROW][HLD];   // scaled amplitude rows, high and low FP16 parts
+  __half Xl[NROW][HLD];
+  __half Ch[MP][HLD];     // C_num with zero diagonal, zero padded to MP x KP
+};
+
+// ---------------------------------------------------------------------------
+// tensor-core helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// scale 2^es with es = 141 - emax puts every value of the rows below 2^15
+__device__ __forceinline__ int scale_exp(unsigned emax) {
+  const int es = 141 - (int)emax;
+  return es > 126 ? 126 : es;
+}
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+__device__ __forceinline__ unsigned exp_bits(float x) { return (__float_as_uint(x) >> 23) & 0xffu; }
+
+// colour sum of the pair on the tensor cores; returns this thread's share of sum_rows x . C x
+__device__ float colour_pair(Shared<float>& sh, TcShared* tcp) {
+  TcShared& tc = *tcp;
   const int tid = threadIdx.x;
-  // (1) momenta of the currents: externals are legs 1..NG-1; incoming legs carry -p
+  // FP16 hi/lo split of the scaled rows (columns beyond NAMP are zero)
+  for (int i = tid; i < NROW * (KP / 2); i += blockDim.x) {
+    const int n = i / (KP / 2), k = 2 * (i % (KP / 2));
+    const float s = pow2f(scale_exp(sh.emax[n >> 2]));
+    float x0 = 0.0f, x1 = 0.0f;
+    if (k < T::NAMP) {
+      x0 = sh.X[n][k] * s;
+      x1 = sh.X[n][k + 1] * s;
+    }
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    *reinterpret_cast<__half2*>(&tc.Xh[n][k]) = h;
+    *reinterpret_cast<__half2*>(&tc.Xl[n][k]) = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+  }
+  __syncthreads();
+  float part = 0.0f;
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int mt = warp; mt < MP / 16; mt += blockDim.x / 32) {
+    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int kk = 0; kk < KP / 32; ++kk) {
+      uint32_t bh[4], bl[4];
+      // matrices j = 0..3: rows n = 0..7, columns 32 kk + 8 j .. + 7 (B fragments of two k-steps)
+      ldsm_x4(bh, &tc.Xh[lane & 7][32 * kk + 8 * (lane >> 3)]);
+      ldsm_x4(bl, &tc.Xl[lane & 7][32 * kk + 8 * (lane >> 3)]);
+#pragma unroll
+      for (int sub = 0; sub < 2; ++sub) {
+        uint32_t a[4];
+        ldsm_x4(a, &tc.Ch[16 * mt + (lane & 15)][32 * kk + 16 * sub + 8 * (lane >> 4)]);
+        mma_f16(d, a, bh[2 * sub], bh[2 * sub + 1]);
+        mma_f16(d, a, bl[2 * sub], bl[2 * sub + 1]);
+      }
+    }
+    // D[m][n] for m = 16 mt + lane/4 (+8), n = 2 (lane%4) (+1); both n in one helicity
+    const int m = 16 * mt + (lane >> 2), n = 2 * (lane & 3);
+    const float is = pow2f(-scale_exp(sh.emax[n >> 2]));
+    if (m < T::NAMP) {
+      const float x0 = sh.X[n][m], x1 = sh.X[n + 1][m];
+      part += x0 * fmaf(d[0], is, kDiag * x0) + x1 * fmaf(d[1], is, kDiag * x1);
+    }
+    if (m + 8 < T::NAMP) {
+      const float x0 = sh.X[n][m + 8], x1 = sh.X[n + 1][m + 8];
+      part += x0 * fmaf(d[2], is, kDiag * x0) + x1 * fmaf(d[3], is, kDiag * x1);
+    }
+  }
+  __syncthreads();
+  if (tid < HP) sh.emax[tid] = 0u;  // next use is behind at least one more barrier
+  return part;
+}
+
+// colour sum of the pair on the FP64 CUDA cores (C symmetric: column reads are row reads)
+__device__ double colour_pair(Shared<double>& sh, const float* sC) {
+  double part = 0.0;
+  for (int i = threadIdx.x; i < NROW * T::NAMP; i += blockDim.x) {
+    const int n = i / T::NAMP, m = i % T::NAMP;
+    double y = 0.0;
+    for (int l = 0; l < T::NAMP; ++l) y += (double)sC[l * T::NAMP + m] * sh.X[n][l];
+    part += sh.X[n][m] * y;
+  }
+  __syncthreads();
+  return part;
+}
+
+// Vertex sum of entry i of tuple size S (a current of one phase, or an amplitude
+// for S = NG-1), amputated: S-1 three-gluon and (S-1)(S-2)/2 four-gluon terms of
+// the consecutive splittings, child indices read slot-major (coalesced).
+template <int S, class R>
+__device__ __forceinline__ W4<R> vertex_sum(const JS<R>* J, const KS<R>* K, int i, R g, R g2) {
+  constexpr int NV3 = S - 1, NV4 = (S - 1) * (S - 2) / 2, CNT = T::COUNT[S], OFF = T::IDX_OFF[S];
+  const int16_t* ix = ME_GTN(kIdx) + OFF + i;
+  W4<R> s;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s.c[k] = mk(R(0), R(0));
+#pragma unroll
+  for (int t = 0; t < NV3; ++t) {
+    const int a = ix[(2 * t) * CNT], b = ix[(2 * t + 1) * CNT];
+    acc(s, v3(ldj(J[a]), ldk(K[a]), ldj(J[b]), ldk(K[b])), g);
+  }
+#pragma unroll
+  for (int u = 0; u < NV4; ++u) {
+    const int a = ix[(2 * NV3 + 3 * u) * CNT], b = ix[(2 * NV3 + 3 * u + 1) * CNT], c = ix[(2 * NV3 + 3 * u + 2) * CNT];
+    acc(s, v4(ldj(J[a]), ldj(J[b]), ldj(J[c])), g2);
+  }
+  return s;
+}
+
+// currents of tuple sizes S..NG-2, one phase per size, a barrier after each
+template <int S, class R>
+__device__ __forceinline__ void current_phases(Shared<R>& sh, JS<R>* J, int lt, R g, R g2) {
+  if constexpr (S <= NG - 2) {
+    constexpr int CNT = T::COUNT[S], ST = T::START[S];
+    for (int i = lt; i < CNT; i += kThreads) {
+      const int c = ST + i;
+      W4<R> s = vertex_sum<S, R>(J, sh.K, i, g, g2);
+      const R f = sh.invp2[c];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s.c[k] = f * s.c[k];
+      stj(J[c], s);
+    }
+    __syncthreads();
+    current_phases<S + 1, R>(sh, J, lt, g, g2);
+  }
+}
+
+// |M|^2 of one event, computed by the whole block.  p: physical momenta (leg-major).
+template <class R, class CS>
+__device__ double event_block(const R (&p)[NG][4], R gs, Shared<R>& sh, CS cs) {
+  const int tid = threadIdx.x, hs = tid / kThreads, lt = tid % kThreads;
+  // (1) momenta of the currents (externals are legs 1..NG-1; incoming legs carry -p),
+  // the polarisation vectors of every leg for both helicities
   if (tid < NG - 1) {
     const int leg = tid + 1;
     const R sg = leg < 2 ? R(-1) : R(1);
-    sh.K[tid] = P4<R>{sg * p[leg][0], sg * p[leg][1], sg * p[leg][2], sg * p[leg][3]};
+    stk(sh.K[tid], P4<R>{sg * p[leg][0], sg * p[leg][1], sg * p[leg][2], sg * p[leg][3]});
   }
-  if (tid < 2) {
+  if (tid >= 32 && tid < 32 + 2 * (NG - 1)) {
+    const int leg = (tid - 32) / 2 + 1, h = tid & 1;
+    const P4<R> k = {p[leg][0], p[leg][1], p[leg][2], p[leg][3]};
+    stj(sh.ext[leg - 1][h], ext_vector<R>(k, h ? 1 : -1, leg < 2, R(0)));
+  }
+  if (tid >= 64 && tid < 66) {
     const P4<R> k0 = {p[0][0], p[0][1], p[0][2], p[0][3]};
-    sh.eps0[tid] = ext_vector<R>(k0, tid ? 1 : -1, true, R(0));
+    sh.eps0[tid - 64] = ext_vector<R>(k0, (tid - 64) ? 1 : -1, true, R(0));
   }
   __syncthreads();
   for (int c = NG - 1 + tid; c < T::NCUR; c += blockDim.x) {
     const int mask = cur_meta()[4 * c];
     P4<R> k = {R(0), R(0), R(0), R(0)};
     for (int l = 1; l < NG; ++l)
-      if ((mask >> l) & 1) k = k + sh.K[l - 1];
-    sh.K[c] = k;
+      if ((mask >> l) & 1) k = k + ldk(sh.K[l - 1]);
+    stk(sh.K[c], k);
     sh.invp2[c] = R(1) / msq(k);
   }
-  __syncthreads();
   const R g = gs, g2 = gs * gs;
+  JS<R>* J = sh.J[hs];
+  // external currents of the first helicity (later ones are set during the colour step)
+  if (lt < NG - 1) J[lt] = sh.ext[lt][(hs >> lt) & 1];
+  __syncthreads();
   R part = R(0);
-  for (int hl = 0; hl < (1 << (NG - 1)); ++hl) {
-    // (2a) external polarisation vectors of legs 1..NG-1 for this helicity
-    if (tid < NG - 1) {
-      const int leg = tid + 1;
-      const int hel = ((hl >> tid) & 1) ? 1 : -1;
-      const P4<R> k = {p[leg][0], p[leg][1], p[leg][2], p[leg][3]};
-      sh.J[tid] = ext_vector<R>(k, hel, leg < 2, R(0));
+  for (int hp = 0; hp < NHEL / HP; ++hp) {
+    // (2a) currents, phase by phase
+    current_phases<2, R>(sh, J, lt, g, g2);
+    // (2b) amplitudes for both root helicities -> rows 4 hs .. 4 hs + 3
+    unsigned e = 0u;
+    for (int a = lt; a < T::NAMP; a += kThreads) {
+      const W4<R> s = vertex_sum<NG - 1, R>(J, sh.K, a, g, g2);
+      const cx<R> a0 = R(2) * mdot(sh.eps0[0], s), a1 = R(2) * mdot(sh.eps0[1], s);
+      sh.X[4 * hs + 0][a] = a0.re;
+      sh.X[4 * hs + 1][a] = a0.im;
+      sh.X[4 * hs + 2][a] = a1.re;
+      sh.X[4 * hs + 3][a] = a1.im;
+      if constexpr (sizeof(R) == 4)
+        e = max(max(max(e, exp_bits(a0.re)), max(exp_bits(a0.im), exp_bits(a1.re))), exp_bits(a1.im));
+    }
+    if constexpr (sizeof(R) == 4) {
+      e = __reduce_max_sync(0xffffffffu, e);
+      if ((lt & 31) == 0) atomicMax(&sh.emax[hs], e);
     }
     __syncthreads();
-    // (2b) currents, phase by phase
-    for (int ph = 0; ph < T::NPHASE; ++ph) {
-      const int start = phases()[2 * ph], count = phases()[2 * ph + 1];
-      for (int i = tid; i < count; i += blockDim.x) {
-        const int c = start + i;
-        W4<R> s = entry_sum<R>(cur_meta() + 4 * c, cur_terms(), sh.J, sh.K, g, g2);
-        const R f = sh.invp2[c];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) s.c[k] = f * s.c[k];
-        sh.J[c] = s;
-      }
-      __syncthreads();
-    }
-    // (2c) amplitudes for both root helicities
-    for (int a = tid; a < T::NAMP; a += blockDim.x) {
-      const W4<R> s = entry_sum<R>(amp_meta() + 4 * a, amp_terms(), sh.J, sh.K, g, g2);
-      sh.A[0][a] = R(2) * mdot(sh.eps0[0], s);
-      sh.A[1][a] = R(2) * mdot(sh.eps0[1], s);
-    }
-    __syncthreads();
-    // (2d) colour quadratic form: sum_kl C_kl Re(A_k^* A_l), row k per thread
-    for (int k = tid; k < T::NAMP; k += blockDim.x) {
-      R y0r = R(0), y0i = R(0), y1r = R(0), y1i = R(0);
-      const float* row = sC + k * T::NAMP;
-      for (int l = 0; l < T::NAMP; ++l) {
-        const R c = (R)row[l];
-        y0r += c * sh.A[0][l].re;
-        y0i += c * sh.A[0][l].im;
-        y1r += c * sh.A[1][l].re;
-        y1i += c * sh.A[1][l].im;
-      }
-      part += sh.A[0][k].re * y0r + sh.A[0][k].im * y0i + sh.A[1][k].re * y1r + sh.A[1][k].im * y1i;
-    }
-    __syncthreads();
+    // external currents of the next pair: J is not read again before the colour step's barriers
+    if (lt < NG - 1 && hp + 1 < NHEL / HP) J[lt] = sh.ext[lt][((HP * (hp + 1) + hs) >> lt) & 1];
+    // (2c) colour quadratic form of the pair's rows
+    part += colour_pair(sh, cs);
   }
   // (3) block sum
 #pragma unroll
@@ -134,37 +337,75 @@ __device__ double event_block(const R (&p)[NG][4], R gs, Shared<R>& sh, const fl
   return tot * (1.0 / (256.0 * (double)T::DEN));
 }
 
-__device__ __forceinline__ void load_colour(float* sC) {
-  for (int i = threadIdx.x; i < T::NAMP * T::NAMP; i += blockDim.x) sC[i] = colour()[i];
-  __syncthreads();
+// colour operand in shared memory: FP16 C_off for the tensor cores, FP32 C_num for FP64
+template <class R>
+struct ColourSmem;
+template <>
+struct ColourSmem<float> {
+  static constexpr size_t bytes = sizeof(TcShared);
+  static __device__ TcShared* load(unsigned char* p) {
+    TcShared& tc = *reinterpret_cast<TcShared*>(p);
+    for (int i = threadIdx.x; i < MP * KP; i += blockDim.x) {
+      const int m = i / KP, k = i % KP;
+      const float v = (m < T::NAMP && k < T::NAMP && m != k) ? colour()[m * T::NAMP + k] : 0.0f;
+      tc.Ch[m][k] = __float2half_rn(v);
+    }
+    return &tc;
+  }
+};
+template <>
+struct ColourSmem<double> {
+  static constexpr size_t bytes = sizeof(float) * T::NAMP * T::NAMP;
+  static __device__ const float* load(unsigned char* p) {
+    float* sC = reinterpret_cast<float*>(p);
+    for (int i = threadIdx.x; i < T::NAMP * T::NAMP; i += blockDim.x) sC[i] = colour()[i];
+    return sC;
+  }
+};
+
+template <class R>
+constexpr size_t shared_offset() {
+  return (sizeof(Shared<R>) + 127) / 128 * 128;
 }
 
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_eval_gluon(const double* __restrict__ mom, int64_t n,
-                                                         double* __restrict__ out, double gs) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ Shared<R>& setup(unsigned char* smem) {
   Shared<R>& sh = *reinterpret_cast<Shared<R>*>(smem);
-  float* sC = reinterpret_cast<float*>(smem + sizeof(Shared<R>));
-  load_colour(sC);
+  if (threadIdx.x < HP) sh.emax[threadIdx.x] = 0u;
+  return sh;
+}
+
+template <class R>
+constexpr int min_blocks() {
+  return sizeof(R) == 4 ? 3 : 2;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kThreadsG, min_blocks<R>())
+    k_eval_gluon(const double* __restrict__ mom, int64_t n, double* __restrict__ out, double gs) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  Shared<R>& sh = setup<R>(smem);
+  const auto cs = ColourSmem<R>::load(smem + shared_offset<R>());
   __shared__ R p[NG][4];
+  __syncthreads();
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     if (threadIdx.x < NG * 4) p[threadIdx.x / 4][threadIdx.x % 4] = (R)mom[(int64_t)threadIdx.x * n + i];
     __syncthreads();
-    const double m2 = event_block<R>(p, (R)gs, sh, sC);
+    const double m2 = event_block<R>(p, (R)gs, sh, cs);
     if (threadIdx.x == 0) out[i] = m2;
     __syncthreads();
   }
 }
 
 template <class R, bool MIXED>
-__global__ void __launch_bounds__(kThreads) k_me_gluon(KinDev kin, int64_t m, const void* __restrict__ ws, double gs,
-                                                       double* __restrict__ partials, double* __restrict__ me2_out,
-                                                       double* __restrict__ mom_out, int64_t out_stride) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Shared<R>& sh = *reinterpret_cast<Shared<R>*>(smem);
-  float* sC = reinterpret_cast<float*>(smem + sizeof(Shared<R>));
-  load_colour(sC);
+__global__ void __launch_bounds__(kThreadsG, min_blocks<R>())
+    k_me_gluon(KinDev kin, int64_t m, const void* __restrict__ ws, double gs, double* __restrict__ partials,
+               int nslots, double* __restrict__ me2_out, double* __restrict__ mom_out, int64_t out_stride) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  Shared<R>& sh = setup<R>(smem);
+  const auto cs = ColourSmem<R>::load(smem + shared_offset<R>());
   __shared__ R p[NG][4];
+  __syncthreads();
   const float* ph = reinterpret_cast<const float*>(ws);
   const float* pl = ph + (int64_t)NG * 4 * m;
   const double* pd = reinterpret_cast<const double*>(ws);
@@ -188,7 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_me_gluon(KinDev kin, int64_t m, co
     const double wps = wps_a[i], shat = shat_a[i];
     const bool ok = wps > 0.0;
     double m2 = 0.0;
-    if (ok) m2 = event_block<R>(p, (R)gs, sh, sC);
+    if (ok) m2 = event_block<R>(p, (R)gs, sh, cs);
     if (t == 0) {
       const double w = !ok ? 0.0 : (kin.wfactor > 0.0 ? m2 * kin.wfactor
                                                        : wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb);
@@ -200,31 +441,48 @@ __global__ void __launch_bounds__(kThreads) k_me_gluon(KinDev kin, int64_t m, co
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    partials[3 * blockIdx.x + 0] = sw;
-    partials[3 * blockIdx.x + 1] = sw2;
-    partials[3 * blockIdx.x + 2] = (double)ntries;
+    // this block's sums, and zeros in the slots of blocks the one-wave grid did not launch
+    for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
+      const bool own = b == (int)blockIdx.x;
+      partials[3 * b + 0] = own ? sw : 0.0;
+      partials[3 * b + 1] = own ? sw2 : 0.0;
+      partials[3 * b + 2] = own ? (double)ntries : 0.0;
+    }
   }
 }
 
 template <class R>
 size_t smem_bytes() {
-  return sizeof(Shared<R>) + sizeof(float) * T::NAMP * T::NAMP;
+  return shared_offset<R>() + ColourSmem<R>::bytes;
 }
 
+// dynamic shared memory opt-in, and the number of blocks of one resident wave (capped by `cap`)
 template <class R, class K>
-cudaError_t prepare(K kern) {
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<R>());
+cudaError_t prepare(K kern, int cap, int& grid) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<R>());
+  if (e != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+  int dev = 0, n_sm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsG, smem_bytes<R>())) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  grid = n_sm * per_sm < cap ? n_sm * per_sm : cap;
+  if (grid < 1) grid = 1;
+  return cudaSuccess;
 }
 
 cudaError_t launch_eval(int prec, const double* mom, int64_t n, double* out, const double* params, cudaStream_t s,
                         int grid) {
   cudaError_t e;
+  int g = 0;
   if (prec == ME_FP64) {
-    if ((e = prepare<double>(k_eval_gluon<double>)) != cudaSuccess) return e;
-    k_eval_gluon<double><<<grid, kThreads, smem_bytes<double>(), s>>>(mom, n, out, params[0]);
+    if ((e = prepare<double>(k_eval_gluon<double>, grid, g)) != cudaSuccess) return e;
+    k_eval_gluon<double><<<g, kThreadsG, smem_bytes<double>(), s>>>(mom, n, out, params[0]);
   } else {
-    if ((e = prepare<float>(k_eval_gluon<float>)) != cudaSuccess) return e;
-    k_eval_gluon<float><<<grid, kThreads, smem_bytes<float>(), s>>>(mom, n, out, params[0]);
+    if ((e = prepare<float>(k_eval_gluon<float>, grid, g)) != cudaSuccess) return e;
+    k_eval_gluon<float><<<g, kThreadsG, smem_bytes<float>(), s>>>(mom, n, out, params[0]);
   }
   return cudaGetLastError();
 }
@@ -233,17 +491,18 @@ cudaError_t launch_step(int prec, const KinDev* kin, uint64_t seed, uint64_t off
                         void* ws, double* partials, double* me2_out, double* mom_out, int64_t out_stride, int* status,
                         cudaStream_t s, int grid_ps, int grid_me, cudaEvent_t ev_mid) {
   cudaError_t e;
+  int g = 0;
   if (prec == ME_FP64) k_ps<Traits, false><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
   else k_ps<Traits, true><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
   if (ev_mid) cudaEventRecord(ev_mid, s);
   if (prec == ME_FP64) {
-    if ((e = prepare<double>(k_me_gluon<double, false>)) != cudaSuccess) return e;
-    k_me_gluon<double, false><<<grid_me, kThreads, smem_bytes<double>(), s>>>(*kin, m, ws, params[0], partials,
-                                                                              me2_out, mom_out, out_stride);
+    if ((e = prepare<double>(k_me_gluon<double, false>, grid_me, g)) != cudaSuccess) return e;
+    k_me_gluon<double, false><<<g, kThreadsG, smem_bytes<double>(), s>>>(*kin, m, ws, params[0], partials, grid_me,
+                                                                         me2_out, mom_out, out_stride);
   } else {
-    if ((e = prepare<float>(k_me_gluon<float, true>)) != cudaSuccess) return e;
-    k_me_gluon<float, true><<<grid_me, kThreads, smem_bytes<float>(), s>>>(*kin, m, ws, params[0], partials, me2_out,
-                                                                           mom_out, out_stride);
+    if ((e = prepare<float>(k_me_gluon<float, true>, grid_me, g)) != cudaSuccess) return e;
+    k_me_gluon<float, true><<<g, kThreadsG, smem_bytes<float>(), s>>>(*kin, m, ws, params[0], partials, grid_me,
+                                                                      me2_out, mom_out, out_stride);
   }
   return cudaGetLastError();
 }
@@ -280,6 +539,7 @@ cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t off
 
 extern "C" void ME_CAT(me_register_gluon, NGLUON)(me::ProcessDesc* d) {
   d->n_ext = NGLUON;
+  d->events_per_block = 1;
   d->launch_eval = me::gluon::ME_CAT(g, NGLUON)::launch_eval;
   d->launch_xsec = me::gluon::ME_CAT(g, NGLUON)::launch_xsec;
   d->launch_step = me::gluon::ME_CAT(g, NGLUON)::launch_step;

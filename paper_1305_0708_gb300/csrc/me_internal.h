@@ -39,8 +39,9 @@ struct ProcessDesc {
   int n_params;
   const char* const* param_names;
   int n_hel, n_hel_live, n_colour, n_diagrams;
-  double flops_amp, flops_fp64;
+  double flops_amp, flops_fp64, flops_colour;
   const int* pdg;
+  int events_per_block;  // events one block of the |M|^2 kernel takes at a time (0: kThreads)
   cudaError_t (*launch_eval)(int prec, const double* mom, int64_t n, double* out, const double* params,
                              cudaStream_t s, int grid);
   cudaError_t (*launch_xsec)(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t n,

@@ -153,7 +153,8 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int nbloc
 }
 
 int grid_for(me_handle h, int64_t n) {
-  const int64_t need = (n + me::kThreads - 1) / me::kThreads;
+  const int64_t per = h->desc->events_per_block > 0 ? h->desc->events_per_block : me::kThreads;
+  const int64_t need = (n + per - 1) / per;
   const int64_t cap = (int64_t)h->n_sm * 8;  // grid-stride beyond 8 blocks per SM
   return (int)std::max<int64_t>(1, std::min(need, cap));
 }
@@ -524,6 +525,7 @@ me_status me_info(me_handle h, me_info_t* info) {
   for (int i = 0; i < d->n_ext && i < 16; ++i) info->pdg[i] = d->pdg[i];
   info->flops_amp = d->flops_amp;
   info->flops_fp64 = d->flops_fp64;
+  info->flops_colour = d->flops_colour;
   return ME_OK;
 }
 
