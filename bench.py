@@ -166,6 +166,138 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
+    """Every workload: mixed and FP64 xsec_step rates on the full point count, the mixed
+    |M|^2 kernel's CUDA-core fraction, and the mixed path's relative error against the FP64
+    GPU path on the FP64 path's own momenta (median and max over the accepted points)."""
+    from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args
+    peak = fp32_alu_peak_tflops()
+    table = {}
+    for key, w in WORKLOADS.items():
+        n = w["n"]
+        kin = B.make_kin(**kin_args(w))
+        row = {"points": n}
+        for prec, name in ((B.ME_MIXED, "mixed"), (B.ME_FP64, "fp64")):
+            h = B.me_create(w["process"], None, prec)
+            slow = prec == B.ME_FP64 and key == "gg_gggg"
+            nw, ns = (1, 2) if slow else (warmup, steps)
+            acc = B.me_xsec_acc()
+            for s_ in range(nw):
+                B.xsec_step(h, w["seed"], offset0 + s_ * n, n, kin, stream, acc)
+            B.me_step_timing(h, 1)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ns)]
+            for s_ in range(ns):
+                flush.zero_()
+                ev[s_][0].record(stream)
+                B.xsec_step(h, w["seed"], offset0 + (nw + s_) * n, n, kin, stream, acc)
+                ev[s_][1].record(stream)
+            torch.cuda.synchronize(dev)
+            t_ps, t_me = B.me_step_timing(h, 0)
+            ms = sum(a.elapsed_time(b) for a, b in ev) / ns
+            info = B.me_info(h)
+            fl = info.flops_amp if prec == B.ME_MIXED else info.flops_fp64
+            row[name] = {"evals_per_s": n / (ms * 1e-3), "ms_per_step": ms, "k_me_ms": t_me / ns,
+                         "k_me_tflops": fl * n / (t_me / ns * 1e-3) / 1e12}
+            if prec == B.ME_MIXED:
+                row[name]["k_me_frac_fp32_peak"] = row[name]["k_me_tflops"] / peak
+            else:
+                # FP64 momenta and |M|^2 of one step, then the mixed me_eval on the same momenta
+                mom = torch.empty(info.n_ext * 4 * n, dtype=torch.float64, device=dev)
+                m64 = torch.empty(n, dtype=torch.float64, device=dev)
+                B.xsec_step(h, w["seed"], offset0, n, kin, stream, B.me_xsec_acc(), m64, mom)
+                hm = B.me_create(w["process"], None, B.ME_MIXED)
+                mmx = torch.empty(n, dtype=torch.float64, device=dev)
+                B.me_eval(hm, mom, n, mmx, stream)
+                torch.cuda.synchronize(dev)
+                B.me_destroy(hm)
+                ok = m64 > 0
+                rel = ((mmx[ok] - m64[ok]).abs() / m64[ok]).double()
+                row["mixed_rel_err"] = {"median": float(rel.median().item()), "max": float(rel.max().item()),
+                                        "points": int(ok.sum().item())}
+            B.me_destroy(h)
+        row["mixed_over_fp64"] = row["mixed"]["evals_per_s"] / row["fp64"]["evals_per_s"]
+        table[key] = row
+    return table
+
+
+def make_stream(rate, count, seed=4):
+    """Poisson request stream: arrival times (s), process keys, batch sizes, momentum seeds."""
+    import numpy as np
+    from paper_1305_0708_gb300.workloads import WORKLOADS
+    rng = np.random.default_rng([seed, int(rate)])
+    keys = list(WORKLOADS)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    procs = [keys[i] for i in rng.integers(0, len(keys), size=count)]
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=count)).astype(np.int64)
+    seeds = rng.integers(0, 2 ** 62, size=count)
+    return [(float(a), k, int(n), int(sd)) for a, k, n, sd in zip(t, procs, sizes, seeds)]
+
+
+def pct(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def serving_mix(B, rates=((10, 48), (100, 128), (1000, 256)), baseline_budget_s=30.0):
+    """Request server under Poisson streams (mixed precision, continuous batching) and, on the
+    10 req/s stream, the plain one-launch-per-request FP64 path (synchronous xsec_step per
+    request in arrival order, stopped after baseline_budget_s)."""
+    from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args
+    kins = {k: B.make_kin(**kin_args(w)) for k, w in WORKLOADS.items()}
+    srv = B.me_server_create()
+    chunks = {k: B.me_server_warm(srv, w["process"], B.ME_MIXED, kins[k]) for k, w in WORKLOADS.items()}
+    out = {"server": {"n_slots": 4, "mem_cap_gib": 40, "precision": "mixed", "chunk_autotuned": chunks},
+           "rates": {}}
+    try:
+        for rate, count in rates:
+            reqs = make_stream(rate, count)
+            t0 = time.perf_counter()
+            tickets = []
+            for arr, k, n, sd in reqs:
+                dt = t0 + arr - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append((B.me_server_submit(srv, WORKLOADS[k]["process"], B.ME_MIXED, sd, 0, n, kins[k]), n))
+            res = [B.me_server_wait(srv, t, 600.0) for t, _ in tickets]
+            lat = [r.t_done_ms - r.t_submit_ms for r in res]
+            span = (max(r.t_done_ms for r in res) - min(r.t_submit_ms for r in res)) * 1e-3
+            pts = sum(n for _, n in tickets)
+            out["rates"][str(rate)] = {
+                "requests": count, "points": pts, "offered_evals_per_s": pts / reqs[-1][0],
+                "evals_per_s": pts / span, "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat)},
+                "failed": sum(1 for r in res if r.status != 0)}
+        st = B.me_server_get_stats(srv)
+        out["server"]["bytes_peak"] = st.bytes_peak
+        out["server"]["launches"] = st.launches
+    finally:
+        B.me_server_destroy(srv)
+    # plain FP64 path, one synchronous launch sequence per request
+    reqs = make_stream(rates[0][0], rates[0][1])
+    hs = {k: B.me_create(w["process"], None, B.ME_FP64) for k, w in WORKLOADS.items()}
+    for k in hs:  # load kernels once, outside the clock
+        B.xsec_step(hs[k], 1, 0, 1000, kins[k])
+    lat, pts, done = [], 0, 0
+    t0 = time.perf_counter()
+    for arr, k, n, sd in reqs:
+        if time.perf_counter() - t0 > baseline_budget_s:
+            break
+        dt = t0 + arr - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        B.xsec_step(hs[k], sd, 0, n, kins[k])
+        lat.append((time.perf_counter() - t0 - arr) * 1e3)
+        pts += n
+        done += 1
+    wall = time.perf_counter() - t0
+    for h in hs.values():
+        B.me_destroy(h)
+    out["baseline_fp64_one_launch_per_request"] = {
+        "rate": rates[0][0], "requests": rates[0][1], "completed_within_budget": done, "budget_s": baseline_budget_s,
+        "evals_per_s": pts / wall, "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
+                                                  "max": max(lat) if lat else None}}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -176,6 +308,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1000)
     ap.add_argument("--cpu-sample", type=int, default=1000)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-table", action="store_true", help="skip the per-process table")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix leg")
     ap.add_argument("--points", type=int, default=0,
                     help="points per step instead of the workload's own count (small cases for profiling)")
     args = ap.parse_args()
@@ -327,6 +461,14 @@ def main():
     me_eval_ms = sorted(evals)[len(evals) // 2]
     B.me_destroy(h32)
 
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = serving_mix(B)
+
+    table = None
+    if not args.no_table:
+        table = per_process_table(B, torch, dev, stream, flush, offset0, 2, 3)
+
     cpu = None
     if rank == 0 and world == 1:
         events = np.arange(args.cpu_sample)
@@ -353,6 +495,8 @@ def main():
                          "frac": achieved / peak, "traffic": None, "kernel": dom,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
             "kernels": kernels,
+            "per_process": table,
+            "serving": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,

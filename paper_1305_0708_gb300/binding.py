@@ -1,4 +1,4 @@
-"""Thin ctypes binding of the C ABI (include/me.h): argument marshalling only.
+"""Thin ctypes binding of the C ABI (include/me.h, include/me_server.h): argument marshalling only.
 
 Every function has the name of the C entry point it calls.  Device buffers
 may be given as torch CUDA tensors (their data pointer is passed) or raw
@@ -44,11 +44,36 @@ class me_info_t(ctypes.Structure):
                 ("flops_colour", ctypes.c_double)]
 
 
+class me_server_config(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("n_slots", ctypes.c_int32), ("max_requests", ctypes.c_int32)]
+
+
+class me_request(ctypes.Structure):
+    _fields_ = [("process", ctypes.c_char_p), ("precision", ctypes.c_int32), ("want_me2", ctypes.c_int32),
+                ("want_momenta", ctypes.c_int32), ("pad_", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("counter_offset", ctypes.c_uint64), ("n", ctypes.c_int64), ("kin", me_kin)]
+
+
+class me_request_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("acc", me_xsec_acc),
+                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double), ("chunk", ctypes.c_int64)]
+
+
+class me_server_stats(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64),
+                ("bytes_peak", ctypes.c_uint64), ("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("waiting", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("points_done", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+
 ME_FP64, ME_MIXED = 0, 1
 ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR = 0, 1, 2
 
 EXPORTS = ["me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
-           "me_xsec_estimate", "me_info", "me_n_processes", "me_process_name", "me_destroy", "me_last_error"]
+           "me_xsec_estimate", "me_info", "me_n_processes", "me_process_name", "me_destroy", "me_last_error",
+           "me_server_create", "me_server_warm", "me_server_submit", "me_server_poll", "me_server_wait",
+           "me_server_get_stats", "me_server_destroy"]
 
 
 def lib_path():
@@ -81,8 +106,17 @@ def load(path=None):
     L.me_destroy.argtypes = [vp]
     L.me_destroy.restype = None
     L.me_last_error.restype = ctypes.c_char_p
+    L.me_server_create.argtypes = [ctypes.POINTER(me_server_config), ctypes.POINTER(vp)]
+    L.me_server_warm.argtypes = [vp, ctypes.c_char_p, i32, ctypes.POINTER(me_kin), ctypes.POINTER(i64)]
+    L.me_server_submit.argtypes = [vp, ctypes.POINTER(me_request), ctypes.POINTER(i64)]
+    L.me_server_poll.argtypes = [vp, i64, ctypes.POINTER(me_request_result)]
+    L.me_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(me_request_result), vp, vp]
+    L.me_server_get_stats.argtypes = [vp, ctypes.POINTER(me_server_stats)]
+    L.me_server_destroy.argtypes = [vp]
+    L.me_server_destroy.restype = None
     for fn in ("me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
-               "me_xsec_estimate", "me_info"):
+               "me_xsec_estimate", "me_info", "me_server_create", "me_server_warm", "me_server_submit",
+               "me_server_poll", "me_server_wait", "me_server_get_stats"):
         getattr(L, fn).restype = ctypes.c_int
     _LIB = L
     return L
@@ -200,3 +234,57 @@ def me_destroy(h):
 
 def me_last_error():
     return load().me_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# request server (include/me_server.h)
+# ---------------------------------------------------------------------------
+def me_server_create(mem_cap_bytes=0, n_slots=0, max_requests=0):
+    L = load()
+    cfg = me_server_config(mem_cap_bytes, n_slots, max_requests)
+    s = ctypes.c_void_p()
+    _check(L.me_server_create(ctypes.byref(cfg), ctypes.byref(s)))
+    return s.value
+
+
+def me_server_warm(s, process, precision, kin):
+    c = ctypes.c_int64()
+    _check(load().me_server_warm(s, process.encode(), precision, ctypes.byref(kin), ctypes.byref(c)))
+    return c.value
+
+
+def me_server_submit(s, process, precision, seed, counter_offset, n, kin, want_me2=False, want_momenta=False):
+    r = me_request(process.encode(), precision, int(want_me2), int(want_momenta), 0, seed, counter_offset, n, kin)
+    t = ctypes.c_int64()
+    _check(load().me_server_submit(s, ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def me_server_poll(s, ticket):
+    res = me_request_result()
+    _check(load().me_server_poll(s, ticket, ctypes.byref(res)))
+    return res
+
+
+def me_server_wait(s, ticket, timeout_s=-1.0, me2_host=None, momenta_host=None):
+    """Waits for a request; me2_host / momenta_host: host buffers (numpy arrays or addresses) or None."""
+    res = me_request_result()
+
+    def hp(a):
+        if a is None:
+            return None
+        return a if isinstance(a, int) else a.ctypes.data
+    st = load().me_server_wait(s, ticket, timeout_s, ctypes.byref(res), hp(me2_host), hp(momenta_host))
+    if st != 0:
+        raise MeError(st, _LIB.me_last_error().decode())
+    return res
+
+
+def me_server_get_stats(s):
+    st = me_server_stats()
+    _check(load().me_server_get_stats(s, ctypes.byref(st)))
+    return st
+
+
+def me_server_destroy(s):
+    load().me_server_destroy(s)

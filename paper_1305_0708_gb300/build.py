@@ -38,7 +38,7 @@ GLUON_PROCESSES = [(5, "g g > g g g"), (6, "g g > g g g g")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", INCLUDE, "-I", CSRC, "-I", GEN]
-STATIC_SOURCES = ["me_runtime.cu"]
+STATIC_SOURCES = ["me_runtime.cu", "me_server.cu"]
 
 
 def nvcc():
@@ -190,7 +190,7 @@ def build(verbose=False, jobs=None):
             objs.append(o)
             changed |= ch
     if changed or not os.path.exists(LIB):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcudart"]
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcudart", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")

@@ -7,8 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "me.h"
-#include "me_internal.h"
+#include "runtime_internal.h"
 
 namespace me {
 // generated registry (registry.cu)
@@ -16,7 +15,8 @@ int registry_size();
 ProcessDesc* registry_entry(int i);
 }  // namespace me
 
-namespace {
+namespace me {
+namespace rt {
 
 thread_local std::string g_err;
 
@@ -28,6 +28,13 @@ me_status fail(me_status st, const std::string& msg) {
 me_status cuda_fail(cudaError_t e, const char* where) {
   return fail(ME_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+}  // namespace rt
+}  // namespace me
+
+using namespace me::rt;
+
+namespace {
 
 const double kPi = 3.14159265358979323846;
 
@@ -100,27 +107,6 @@ std::string normalise(const char* s) {
 
 }  // namespace
 
-struct me_handle_s {
-  me::ProcessDesc* desc = nullptr;
-  me_params params;
-  int prec = ME_FP64;
-  std::vector<double> cvals;
-  int device = 0;
-  int n_sm = 0;
-  // workspace (lazy)
-  double* d_partials = nullptr;
-  int partials_cap = 0;
-  double* d_acc = nullptr;    // 3 doubles
-  int* d_status = nullptr;
-  double* h_acc = nullptr;    // pinned, 3 doubles + status
-  void* d_ws = nullptr;       // phase-space points of one chunk (k_ps -> k_me)
-  size_t ws_cap = 0;
-  // optional per-kernel timing of xsec_step (CUDA events on the call's stream)
-  bool timing = false;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-  double t_ps = 0.0, t_me = 0.0;
-  std::mutex mu;
-};
 
 namespace {
 
@@ -150,6 +136,16 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int nbloc
     acc[1] = sm[1][0];
     acc[2] = sm[2][0];
   }
+}
+
+}  // namespace
+
+namespace me {
+namespace rt {
+
+cudaError_t launch_reduce(const double* partials, int nblocks, double* acc, cudaStream_t s) {
+  k_reduce_partials<<<1, 256, 0, s>>>(partials, nblocks, acc);
+  return cudaGetLastError();
 }
 
 int grid_for(me_handle h, int64_t n) {
@@ -252,9 +248,17 @@ me_status ensure_workspace(me_handle h, int nblocks) {
   return ME_OK;
 }
 
-constexpr int64_t kChunk = 1 << 20;  // points per k_ps / k_me pair
-
 size_t ws_bytes(int n_ext, int64_t m) { return (size_t)m * (32 * (size_t)n_ext + 20); }
+
+int grid_ps_for(me_handle h, int64_t m) {
+  // phase space: 4 resident blocks per SM, each with a contiguous range of points
+  return (int)std::max<int64_t>(1, std::min<int64_t>((m + me::kThreads - 1) / me::kThreads, (int64_t)h->n_sm * 4));
+}
+
+}  // namespace rt
+}  // namespace me
+
+namespace {
 
 me_status ensure_points_ws(me_handle h, int64_t m) {
   const size_t need = ws_bytes(h->desc->n_ext, m);
@@ -394,9 +398,7 @@ me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t
   const int64_t m0 = std::min<int64_t>(n_accept, kChunk);
   const int64_t nchunks = (n_accept + kChunk - 1) / kChunk;
   const int grid_me = grid_for(h, m0);
-  // phase space: 4 resident blocks per SM, each with a contiguous range of points
-  const int grid_ps = (int)std::max<int64_t>(1, std::min<int64_t>((m0 + me::kThreads - 1) / me::kThreads,
-                                                                   (int64_t)h->n_sm * 4));
+  const int grid_ps = grid_ps_for(h, m0);
   if ((st = ensure_workspace(h, (int)(grid_me * nchunks))) != ME_OK) return st;
   if ((st = ensure_points_ws(h, m0)) != ME_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, uint64_t seed, u
   __shared__ int s_att[QCAP];
   __shared__ int s_head, s_tail;
   const int64_t per = (m + gridDim.x - 1) / gridDim.x;
-  const int64_t b0 = (int64_t)blockIdx.x * per;
+  const int64_t b0 = (int64_t)blockIdx.x * per < m ? (int64_t)blockIdx.x * per : m;  // empty range past m
   const int64_t b1 = b0 + per < m ? b0 + per : m;
   if (threadIdx.x == 0) { s_head = 0; s_tail = 0; }
   __syncthreads();

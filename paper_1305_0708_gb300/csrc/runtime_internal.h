@@ -1,0 +1,51 @@
+// Runtime internals shared by the C-ABI entry points (me_runtime.cu) and the
+// request server (me_server.cu): the handle, argument checks and launch sizing.
+#pragma once
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "me.h"
+#include "me_internal.h"
+
+struct me_handle_s {
+  me::ProcessDesc* desc = nullptr;
+  me_params params;
+  int prec = ME_FP64;
+  std::vector<double> cvals;
+  int device = 0;
+  int n_sm = 0;
+  // workspace (lazy)
+  double* d_partials = nullptr;
+  int partials_cap = 0;
+  double* d_acc = nullptr;    // 3 doubles
+  int* d_status = nullptr;
+  double* h_acc = nullptr;    // pinned, 3 doubles + status
+  void* d_ws = nullptr;       // phase-space points of one chunk (k_ps -> k_me)
+  size_t ws_cap = 0;
+  // optional per-kernel timing of xsec_step (CUDA events on the call's stream)
+  bool timing = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  double t_ps = 0.0, t_me = 0.0;
+  std::mutex mu;
+};
+
+namespace me {
+namespace rt {
+
+constexpr int64_t kChunk = 1 << 20;  // points per k_ps / k_me pair of xsec_step
+
+me_status fail(me_status st, const std::string& msg);
+me_status cuda_fail(cudaError_t e, const char* where);
+// device form of the generator and cut parameters; checks them against the process
+me_status make_kin(me_handle h, const me_kin* kin, KinDev& k);
+// blocks of the |M|^2 kernel and of the phase-space kernel for a chunk of m points
+int grid_for(me_handle h, int64_t n);
+int grid_ps_for(me_handle h, int64_t m);
+// bytes of the phase-space workspace between k_ps and k_me for m points
+size_t ws_bytes(int n_ext, int64_t m);
+// fixed-order sum of nblocks partials (3 doubles each) into acc[0..2]
+cudaError_t launch_reduce(const double* partials, int nblocks, double* acc, cudaStream_t s);
+
+}  // namespace rt
+}  // namespace me

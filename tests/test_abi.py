@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports every entry point of include/me.h (no GPU needed)."""
+"""The C-ABI library builds, loads and exports every entry point of include/*.h (no GPU needed)."""
 import ctypes
 import os
 import re
@@ -17,14 +17,20 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "me.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(?:me_status|void|int32_t|const char \*)\s*\*?\s*(\w+)\s*\(", src)))
+    names = set()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(?:me_status|void|int32_t|const char \*)\s*\*?\s*(\w+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
-    assert {"me_create", "me_eval", "xsec_step", "me_generate", "me_info", "me_destroy"} <= set(names)
+    assert {"me_create", "me_eval", "xsec_step", "me_generate", "me_info", "me_destroy", "me_server_create",
+            "me_server_submit", "me_server_wait"} <= set(names)
     for n in names:
         assert hasattr(lib, n), n
 
@@ -65,3 +71,35 @@ def test_xsec_estimate_arithmetic(lib):
     assert e == pytest.approx(((30.0 / 10 - 1.0) / 9) ** 0.5)
     with pytest.raises(binding.MeError):
         binding.me_xsec_estimate(binding.me_xsec_acc())
+
+
+def test_server_struct_layouts_match_the_header(lib, tmp_path):
+    """ctypes mirrors of the server structs have the C sizes (host compiler, no GPU)."""
+    import shutil
+    import subprocess
+    from paper_1305_0708_gb300 import binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "me_server.h"\nint main(void){printf("%zu %zu %zu %zu %zu",'
+                   'sizeof(me_kin), sizeof(me_request), sizeof(me_request_result), sizeof(me_server_stats),'
+                   'sizeof(me_server_config));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(t) for t in (B.me_kin, B.me_request, B.me_request_result, B.me_server_stats,
+                                       B.me_server_config)]
+    assert got == want
+
+
+def test_server_argument_errors_without_device_work(lib):
+    from paper_1305_0708_gb300 import binding as B
+    s = ctypes.c_void_p()
+    assert lib.me_server_create(None, None) == -1
+    cfg = B.me_server_config(0, 17, 0)
+    assert lib.me_server_create(ctypes.byref(cfg), ctypes.byref(s)) == -1
+    assert "n_slots" in B.me_last_error()
+    t = ctypes.c_int64()
+    assert lib.me_server_submit(None, None, ctypes.byref(t)) == -1
+    assert lib.me_server_wait(None, 1, 0.0, None, None, None) == -1
