@@ -213,6 +213,9 @@ def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
                 ok = m64 > 0
                 rel = ((mmx[ok] - m64[ok]).abs() / m64[ok]).double()
                 row["mixed_rel_err"] = {"median": float(rel.median().item()), "max": float(rel.max().item()),
+                                        "p99_99": float(torch.quantile(rel.float().cpu(), 0.9999).item()),
+                                        "frac_above_1e-3": float((rel > 1e-3).double().mean().item()),
+                                        "sum_me2": float(((mmx[ok].sum() - m64[ok].sum()) / m64[ok].sum()).abs()),
                                         "points": int(ok.sum().item())}
             B.me_destroy(h)
         row["mixed_over_fp64"] = row["mixed"]["evals_per_s"] / row["fp64"]["evals_per_s"]

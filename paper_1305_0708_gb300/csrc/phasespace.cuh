@@ -360,9 +360,9 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision phase space: massless RAMBO in double-float arithmetic (FP32
-// pairs, ~2^-48 relative) on the FP32 pipe, the same formulas and draw order as
-// gen_rambo.  Other generators run in FP64 and are split into double-floats.
+// Mixed-precision phase space: RAMBO in double-float arithmetic (FP32 pairs,
+// ~2^-48 relative) on the FP32 pipe, the same formulas and draw order as
+// gen_rambo.  The ttbar generator runs in FP64 and is split into double-floats.
 // ---------------------------------------------------------------------------
 template <int NEXT>
 __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
@@ -408,6 +408,70 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
     q[2] = x * (q[2] + b2 * c);
     q[3] = x * (q[3] + b3 * c);
   }
+}
+
+// Massive RAMBO rescaling in double-float: the massless momenta of rambo_df are
+// scaled so that every final particle gets its mass at fixed total energy w
+// (the same equation as gen_rambo: sum_k sqrt(m_k^2 + xi^2 E_k^2) = w).  xi is
+// found by Newton's method in FP32 from the same start, then refined by two
+// double-float Newton steps (quadratic convergence: FP32 accuracy squared is
+// below the double-float rounding).  Returns the factor of the weight,
+// xi^(2n-3) prod_k(|p_k|/E_k) w / sum_k(|p_k|^2/E_k).
+template <int NEXT>
+__host__ __device__ __forceinline__ df massive_rescale_df(const KinDev& kin, df (&p)[NEXT][4]) {
+  constexpr int NF = NEXT - 2;
+  const df w = df{kin.sqrt_s_f[0], kin.sqrt_s_f[1]};
+  df E0[NF], m2[NF];
+  float msum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    E0[k] = p[2 + k][0];
+    const df m = from_double(kin.mass[2 + k]);
+    m2[k] = sqr(m);
+    msum += m.hi;
+  }
+  const float r = msum / w.hi;
+  float xf = sqrtf(fmaxf(1.0f - r * r, 0.0f));
+  for (int it = 0; it < 12; ++it) {
+    float f = -w.hi, d = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const float e = E0[k].hi;
+      const float ek = sqrtf(m2[k].hi + xf * xf * e * e);
+      f += ek;
+      d += xf * e * e / ek;
+    }
+    xf -= f / d;
+  }
+  df X = dfs(xf);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    df f = -w, d = dfs(0.0f);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const df ak = X * E0[k];
+      const df ek = df_sqrt(m2[k] + sqr(ak));
+      f = f + ek;
+      d = d + (ak * E0[k]) / ek;
+    }
+    X = X - f / d;
+  }
+  df prod = dfs(1.0f), sum = dfs(0.0f);
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    const df ak = X * E0[k];
+    const df ek = df_sqrt(m2[k] + sqr(ak));
+    prod = prod * (ak / ek);
+    sum = sum + sqr(ak) / ek;
+    p[2 + k][0] = ek;
+    p[2 + k][1] = p[2 + k][1] * X;
+    p[2 + k][2] = p[2 + k][2] * X;
+    p[2 + k][3] = p[2 + k][3] * X;
+  }
+  df xp = dfs(1.0f);
+#pragma unroll
+  for (int i = 0; i < 2 * NF - 3; ++i) xp = xp * X;
+  return ((xp * prod) * w) / sum;
 }
 
 // cuts on double-float momenta: FP32 estimates decide outside a 1e-5 guard band;
@@ -474,14 +538,15 @@ __host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const d
   return pass_cuts<NEXT>(kin, pd);
 }
 
-// one mixed-precision draw: double-float RAMBO for massless final states, else the
-// FP64 generator split into double-floats
+// one mixed-precision draw: double-float RAMBO (massless, or with the massive
+// rescaling), else the FP64 generator split into double-floats
 template <int NEXT>
 __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
                                               df (&p)[NEXT][4], double& wps, double& shat) {
-  if (kin.kind == ME_PS_RAMBO && !kin.massive) {
+  if (kin.kind == ME_PS_RAMBO) {
     rambo_df<NEXT>(kin, seed, event, att, p);
     wps = kin.rambo_volume;
+    if (kin.massive) wps *= to_double(massive_rescale_df<NEXT>(kin, p));
     shat = kin.shat_fixed;
     return pass_cuts_df<NEXT>(kin, p);
   }
