@@ -32,6 +32,13 @@ sys.path.insert(0, ROOT)
 # operations; 4 final-state particles plus the conformal transform and the FP32 cut tests)
 PS_FLOPS_PER_DRAW = {"rambo": 2700.0}
 
+# DRAM bytes per point of the mixed-path kernels (dram__bytes_read.sum + dram__bytes_write.sum of one
+# ncu capture, divided by the points of that launch; profiles/ holds the captures).  A launch's
+# traffic is this times its points: the kernels stream their points, so traffic grows in proportion.
+TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): 326.337536e6 / 2 ** 20,
+                     ("udx_epvegg", "k_me"): 226.21568e6 / 2 ** 20,
+                     ("gg_gggg", "k_me"): 3.638784e6 / 16384}
+
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -416,6 +423,8 @@ def main():
                                      "what": "colour sum x.C.x, mma.sync m16n8k16 f16, hi/lo split"}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     achieved = kernels[dom]["achieved_tflops"]
+    tpp = TRAFFIC_PER_POINT.get((args.workload, dom))
+    traffic = tpp * n if tpp is not None else None
 
     # FP64 path for context
     fp64 = None
@@ -495,7 +504,7 @@ def main():
             "fp64_path": fp64,
             "me_eval_ms": me_eval_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": dom,
+                         "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
             "kernels": kernels,
             "per_process": table,
