@@ -37,7 +37,7 @@ PS_FLOPS_PER_DRAW = {"rambo": 2700.0}
 # traffic is this times its points: the kernels stream their points, so traffic grows in proportion.
 TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): 326.337536e6 / 2 ** 20,
                      ("udx_epvegg", "k_me"): 226.21568e6 / 2 ** 20,
-                     ("gg_gggg", "k_me"): 3.638784e6 / 16384}
+                     ("gg_gggg", "k_me"): 3.617792e6 / 16384}
 
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128

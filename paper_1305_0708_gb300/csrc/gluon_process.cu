@@ -39,10 +39,18 @@ namespace ME_CAT(g, NGLUON) {  // one namespace per gluon count: the units link 
 
 using T = ME_CAT(Tables, NGLUON);
 constexpr int NG = NGLUON;
-constexpr int HP = 2;                      // helicities evaluated side by side, one per half block
-constexpr int kThreadsG = HP * kThreads;   // threads per block
 constexpr int NHEL = 1 << (NG - 1);        // helicities of the non-root legs
-constexpr int NROW = 4 * HP;               // amplitude rows per pair: (helicity, root helicity, re/im)
+// Helicities evaluated side by side (one per kThreads-thread part of a block) and
+// the amplitude rows they produce (helicity, root helicity, re/im).  FP32: two, so
+// that the 8 rows of a pair fill one n8 tensor-core tile; FP64: one (its shared
+// memory allows two blocks per SM only at one helicity per block).
+template <class R>
+struct Cfg {
+  static constexpr int HP = sizeof(R) == 4 ? 2 : 1;
+  static constexpr int THREADS = HP * kThreads;
+  static constexpr int NROW = 4 * HP;
+};
+constexpr int NROW = Cfg<float>::NROW;     // rows of the tensor-core colour step
 constexpr int MP = (T::NAMP + 15) / 16 * 16;  // colour rows padded to the MMA tile
 constexpr int KP = (T::NAMP + 31) / 32 * 32;  // colour columns padded to two MMA k-steps
 constexpr int XLD = KP + 4;                // FP32 row stride: epilogue reads hit 32 distinct banks
@@ -63,11 +71,13 @@ __host__ __device__ __forceinline__ const int32_t* cur_meta() { return ME_GTN(kC
 __host__ __device__ __forceinline__ const float* colour() { return ME_GTN(kColour); }
 
 // Shared-memory storage of currents and momenta: 16-byte aligned with vector
-// loads and stores; the current stride is 48 B (FP32) / 80 B (FP64), not a
+// loads and stores.  A current slot holds the four complex components and the
+// two contractions e_r = eps0_r . J with the root polarisations (the amplitude
+// needs only these scalars, see amp_scalar); its stride is 48 B (FP32), not a
 // power of two, so gathers at data-dependent indices spread over the banks.
 template <class R>
 struct alignas(16) JS {
-  R v[sizeof(R) == 4 ? 12 : 10];
+  R v[12];
 };
 template <class R>
 struct alignas(16) KS {
@@ -92,6 +102,27 @@ __device__ __forceinline__ void stj(JS<double>& j, const W4<double>& a) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) q[k] = make_double2(a.c[k].re, a.c[k].im);
 }
+// e_r = eps0_r . J of a current slot, r = 0, 1
+__device__ __forceinline__ void lde(const JS<float>& j, cx<float>& e0, cx<float>& e1) {
+  const float4 u = reinterpret_cast<const float4*>(j.v)[2];
+  e0 = cx<float>{u.x, u.y};
+  e1 = cx<float>{u.z, u.w};
+}
+__device__ __forceinline__ void ste(JS<float>& j, cx<float> e0, cx<float> e1) {
+  reinterpret_cast<float4*>(j.v)[2] = make_float4(e0.re, e0.im, e1.re, e1.im);
+}
+__device__ __forceinline__ void lde(const JS<double>& j, cx<double>& e0, cx<double>& e1) {
+  const double2* q = reinterpret_cast<const double2*>(j.v);
+  const double2 a = q[4], b = q[5];
+  e0 = cx<double>{a.x, a.y};
+  e1 = cx<double>{b.x, b.y};
+}
+__device__ __forceinline__ void ste(JS<double>& j, cx<double> e0, cx<double> e1) {
+  double2* q = reinterpret_cast<double2*>(j.v);
+  q[4] = make_double2(e0.re, e0.im);
+  q[5] = make_double2(e1.re, e1.im);
+}
+
 __device__ __forceinline__ P4<float> ldk(const KS<float>& k) {
   const float4 u = *reinterpret_cast<const float4*>(k.v);
   return P4<float>{u.x, u.y, u.z, u.w};
@@ -113,13 +144,14 @@ __device__ __forceinline__ void stk(KS<double>& k, const P4<double>& p) {
 template <class R>
 struct Shared {
   KS<R> K[T::NCUR];       // outgoing momenta of every current (externals first)
+  KS<R> EK[T::NCUR];      // eps0_0 . K and eps0_1 . K (two complex numbers) of every current
   R invp2[T::NCUR];
-  JS<R> J[HP][T::NCUR];   // currents of the two helicities being evaluated
-  JS<R> ext[NG - 1][2];   // polarisation vectors of legs 1..NG-1, helicity -1 / +1
-  W4<R> eps0[2];          // root polarisation, both helicities
-  R X[NROW][XLD];         // amplitudes of the pair, row 4 h + 2 r + (0: re, 1: im)
-  unsigned emax[HP];      // largest biased FP32 exponent in the rows of each helicity
-  R red[kThreadsG / 32];
+  JS<R> J[Cfg<R>::HP][T::NCUR];  // currents of the helicities being evaluated
+  JS<R> ext[NG - 1][2];          // polarisation vectors of legs 1..NG-1, helicity -1 / +1
+  W4<R> eps0[2];                 // root polarisation, both helicities
+  R X[Cfg<R>::NROW][XLD];        // amplitude rows, row 4 h + 2 r + (0: re, 1: im)
+  unsigned emax[2];              // largest biased FP32 exponent in the rows of each helicity
+  R red[Cfg<R>::THREADS / 32];
 };
 
 // Tensor-core operands of the mixed path (dynamic shared memory after Shared<float>)
@@ -206,14 +238,14 @@ __device__ float colour_pair(Shared<float>& sh, TcShared* tcp) {
     }
   }
   __syncthreads();
-  if (tid < HP) sh.emax[tid] = 0u;  // next use is behind at least one more barrier
+  if (tid < 2) sh.emax[tid] = 0u;  // next use is behind at least one more barrier
   return part;
 }
 
 // colour sum of the pair on the FP64 CUDA cores (C symmetric: column reads are row reads)
 __device__ double colour_pair(Shared<double>& sh, const float* sC) {
   double part = 0.0;
-  for (int i = threadIdx.x; i < NROW * T::NAMP; i += blockDim.x) {
+  for (int i = threadIdx.x; i < Cfg<double>::NROW * T::NAMP; i += blockDim.x) {
     const int n = i / T::NAMP, m = i % T::NAMP;
     double y = 0.0;
     for (int l = 0; l < T::NAMP; ++l) y += (double)sC[l * T::NAMP + m] * sh.X[n][l];
@@ -258,15 +290,62 @@ __device__ __forceinline__ void current_phases(Shared<R>& sh, JS<R>* J, int lt, 
 #pragma unroll
       for (int k = 0; k < 4; ++k) s.c[k] = f * s.c[k];
       stj(J[c], s);
+      ste(J[c], mdot(sh.eps0[0], s), mdot(sh.eps0[1], s));
     }
     __syncthreads();
     current_phases<S + 1, R>(sh, J, lt, g, g2);
   }
 }
 
+// Amplitudes of ordering i for both root helicities, from scalars only.  The
+// amplitude is eps0_r . S with S the amputated vertex sum of the full tuple;
+// contracting each vertex term with eps0_r first gives, with e_r(J) = eps0_r . J
+// and E_r(k) = eps0_r . k (momenta outgoing, kx = -(k1 + k2)):
+//   three-gluon:  eps0.V3 = (E(k1) - E(k2)) (J1.J2) + e(J2) (k1 + 2 k2).J1 - e(J1) (2 k1 + k2).J2
+//   four-gluon:   eps0.V4 = 2 (J1.J3) e(J2) - (J1.J2) e(J3) - (J2.J3) e(J1)
+// (the vertices of v3 and v4 above), so that no four-vector sum is formed.
+template <class R>
+__device__ __forceinline__ void amp_scalar(const JS<R>* J, const KS<R>* K, const KS<R>* EK, int i, R g, R g2,
+                                           cx<R>& A0, cx<R>& A1) {
+  constexpr int S = NG - 1, NV3 = S - 1, NV4 = (S - 1) * (S - 2) / 2, CNT = T::COUNT[S], OFF = T::IDX_OFF[S];
+  const int16_t* ix = ME_GTN(kIdx) + OFF + i;
+  cx<R> s30 = mk(R(0), R(0)), s31 = s30, s40 = s30, s41 = s30;
+#pragma unroll
+  for (int t = 0; t < NV3; ++t) {
+    const int a = ix[(2 * t) * CNT], b = ix[(2 * t + 1) * CNT];
+    const W4<R> J1 = ldj(J[a]), J2 = ldj(J[b]);
+    const P4<R> k1 = ldk(K[a]), k2 = ldk(K[b]);
+    const P4<R> q1 = ldk(EK[a]), q2 = ldk(EK[b]);
+    cx<R> e10, e11, e20, e21;
+    lde(J[a], e10, e11);
+    lde(J[b], e20, e21);
+    const P4<R> d2x = {k1.e + R(2) * k2.e, k1.x + R(2) * k2.x, k1.y + R(2) * k2.y, k1.z + R(2) * k2.z};
+    const P4<R> dx1 = {-(R(2) * k1.e + k2.e), -(R(2) * k1.x + k2.x), -(R(2) * k1.y + k2.y), -(R(2) * k1.z + k2.z)};
+    const cx<R> j12 = mdot(J1, J2), av = mdot(d2x, J1), bv = mdot(dx1, J2);
+    s30 = s30 + mk(q1.e - q2.e, q1.x - q2.x) * j12 + e20 * av + e10 * bv;
+    s31 = s31 + mk(q1.y - q2.y, q1.z - q2.z) * j12 + e21 * av + e11 * bv;
+  }
+#pragma unroll
+  for (int u = 0; u < NV4; ++u) {
+    const int a = ix[(2 * NV3 + 3 * u) * CNT], b = ix[(2 * NV3 + 3 * u + 1) * CNT], c = ix[(2 * NV3 + 3 * u + 2) * CNT];
+    const W4<R> J1 = ldj(J[a]), J2 = ldj(J[b]), J3 = ldj(J[c]);
+    cx<R> e10, e11, e20, e21, e30, e31;
+    lde(J[a], e10, e11);
+    lde(J[b], e20, e21);
+    lde(J[c], e30, e31);
+    const cx<R> j13 = mdot(J1, J3), j12 = mdot(J1, J2), j23 = mdot(J2, J3);
+    const cx<R> t13 = j13 + j13;
+    s40 = s40 + t13 * e20 - j12 * e30 - j23 * e10;
+    s41 = s41 + t13 * e21 - j12 * e31 - j23 * e11;
+  }
+  A0 = R(2) * (g * s30 + g2 * s40);
+  A1 = R(2) * (g * s31 + g2 * s41);
+}
+
 // |M|^2 of one event, computed by the whole block.  p: physical momenta (leg-major).
 template <class R, class CS>
 __device__ double event_block(const R (&p)[NG][4], R gs, Shared<R>& sh, CS cs) {
+  constexpr int HP = Cfg<R>::HP;
   const int tid = threadIdx.x, hs = tid / kThreads, lt = tid % kThreads;
   // (1) momenta of the currents (externals are legs 1..NG-1; incoming legs carry -p),
   // the polarisation vectors of every leg for both helicities
@@ -285,16 +364,30 @@ __device__ double event_block(const R (&p)[NG][4], R gs, Shared<R>& sh, CS cs) {
     sh.eps0[tid - 64] = ext_vector<R>(k0, (tid - 64) ? 1 : -1, true, R(0));
   }
   __syncthreads();
-  for (int c = NG - 1 + tid; c < T::NCUR; c += blockDim.x) {
-    const int mask = cur_meta()[4 * c];
-    P4<R> k = {R(0), R(0), R(0), R(0)};
-    for (int l = 1; l < NG; ++l)
-      if ((mask >> l) & 1) k = k + ldk(sh.K[l - 1]);
-    stk(sh.K[c], k);
-    sh.invp2[c] = R(1) / msq(k);
+  // composite momenta, 1/P^2, and the root contractions of every momentum and external vector
+  for (int c = tid; c < T::NCUR; c += blockDim.x) {
+    P4<R> k;
+    if (c < NG - 1) {
+      k = ldk(sh.K[c]);
+    } else {
+      const int mask = cur_meta()[4 * c];
+      k = P4<R>{R(0), R(0), R(0), R(0)};
+      for (int l = 1; l < NG; ++l)
+        if ((mask >> l) & 1) k = k + ldk(sh.K[l - 1]);
+      stk(sh.K[c], k);
+      sh.invp2[c] = R(1) / msq(k);
+    }
+    const cx<R> q0 = mdot(k, sh.eps0[0]), q1 = mdot(k, sh.eps0[1]);
+    stk(sh.EK[c], P4<R>{q0.re, q0.im, q1.re, q1.im});
+  }
+  if (tid >= 64 && tid < 64 + 2 * (NG - 1)) {
+    JS<R>& x = sh.ext[(tid - 64) / 2][tid & 1];
+    const W4<R> v = ldj(x);
+    ste(x, mdot(sh.eps0[0], v), mdot(sh.eps0[1], v));
   }
   const R g = gs, g2 = gs * gs;
   JS<R>* J = sh.J[hs];
+  __syncthreads();
   // external currents of the first helicity (later ones are set during the colour step)
   if (lt < NG - 1) J[lt] = sh.ext[lt][(hs >> lt) & 1];
   __syncthreads();
@@ -305,8 +398,8 @@ __device__ double event_block(const R (&p)[NG][4], R gs, Shared<R>& sh, CS cs) {
     // (2b) amplitudes for both root helicities -> rows 4 hs .. 4 hs + 3
     unsigned e = 0u;
     for (int a = lt; a < T::NAMP; a += kThreads) {
-      const W4<R> s = vertex_sum<NG - 1, R>(J, sh.K, a, g, g2);
-      const cx<R> a0 = R(2) * mdot(sh.eps0[0], s), a1 = R(2) * mdot(sh.eps0[1], s);
+      cx<R> a0, a1;
+      amp_scalar<R>(J, sh.K, sh.EK, a, g, g2, a0, a1);
       sh.X[4 * hs + 0][a] = a0.re;
       sh.X[4 * hs + 1][a] = a0.im;
       sh.X[4 * hs + 2][a] = a1.re;
@@ -371,7 +464,7 @@ constexpr size_t shared_offset() {
 template <class R>
 __device__ __forceinline__ Shared<R>& setup(unsigned char* smem) {
   Shared<R>& sh = *reinterpret_cast<Shared<R>*>(smem);
-  if (threadIdx.x < HP) sh.emax[threadIdx.x] = 0u;
+  if (threadIdx.x < 2) sh.emax[threadIdx.x] = 0u;
   return sh;
 }
 
@@ -381,7 +474,7 @@ constexpr int min_blocks() {
 }
 
 template <class R>
-__global__ void __launch_bounds__(kThreadsG, min_blocks<R>())
+__global__ void __launch_bounds__(Cfg<R>::THREADS, min_blocks<R>())
     k_eval_gluon(const double* __restrict__ mom, int64_t n, double* __restrict__ out, double gs) {
   extern __shared__ __align__(128) unsigned char smem[];
   Shared<R>& sh = setup<R>(smem);
@@ -398,7 +491,7 @@ __global__ void __launch_bounds__(kThreadsG, min_blocks<R>())
 }
 
 template <class R, bool MIXED>
-__global__ void __launch_bounds__(kThreadsG, min_blocks<R>())
+__global__ void __launch_bounds__(Cfg<R>::THREADS, min_blocks<R>())
     k_me_gluon(KinDev kin, int64_t m, const void* __restrict__ ws, double gs, double* __restrict__ partials,
                int nslots, double* __restrict__ me2_out, double* __restrict__ mom_out, int64_t out_stride) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -465,7 +558,8 @@ cudaError_t prepare(K kern, int cap, int& grid) {
   int dev = 0, n_sm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsG, smem_bytes<R>())) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg<R>::THREADS, smem_bytes<R>())) !=
+      cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   grid = n_sm * per_sm < cap ? n_sm * per_sm : cap;
@@ -479,10 +573,10 @@ cudaError_t launch_eval(int prec, const double* mom, int64_t n, double* out, con
   int g = 0;
   if (prec == ME_FP64) {
     if ((e = prepare<double>(k_eval_gluon<double>, grid, g)) != cudaSuccess) return e;
-    k_eval_gluon<double><<<g, kThreadsG, smem_bytes<double>(), s>>>(mom, n, out, params[0]);
+    k_eval_gluon<double><<<g, Cfg<double>::THREADS, smem_bytes<double>(), s>>>(mom, n, out, params[0]);
   } else {
     if ((e = prepare<float>(k_eval_gluon<float>, grid, g)) != cudaSuccess) return e;
-    k_eval_gluon<float><<<g, kThreadsG, smem_bytes<float>(), s>>>(mom, n, out, params[0]);
+    k_eval_gluon<float><<<g, Cfg<float>::THREADS, smem_bytes<float>(), s>>>(mom, n, out, params[0]);
   }
   return cudaGetLastError();
 }
@@ -497,11 +591,11 @@ cudaError_t launch_step(int prec, const KinDev* kin, uint64_t seed, uint64_t off
   if (ev_mid) cudaEventRecord(ev_mid, s);
   if (prec == ME_FP64) {
     if ((e = prepare<double>(k_me_gluon<double, false>, grid_me, g)) != cudaSuccess) return e;
-    k_me_gluon<double, false><<<g, kThreadsG, smem_bytes<double>(), s>>>(*kin, m, ws, params[0], partials, grid_me,
+    k_me_gluon<double, false><<<g, Cfg<double>::THREADS, smem_bytes<double>(), s>>>(*kin, m, ws, params[0], partials, grid_me,
                                                                          me2_out, mom_out, out_stride);
   } else {
     if ((e = prepare<float>(k_me_gluon<float, true>, grid_me, g)) != cudaSuccess) return e;
-    k_me_gluon<float, true><<<g, kThreadsG, smem_bytes<float>(), s>>>(*kin, m, ws, params[0], partials, grid_me,
+    k_me_gluon<float, true><<<g, Cfg<float>::THREADS, smem_bytes<float>(), s>>>(*kin, m, ws, params[0], partials, grid_me,
                                                                       me2_out, mom_out, out_stride);
   }
   return cudaGetLastError();

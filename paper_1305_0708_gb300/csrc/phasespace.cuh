@@ -374,7 +374,7 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
   p[0][0] = hw; p[0][1] = z; p[0][2] = z; p[0][3] = hw;
   p[1][0] = hw; p[1][1] = z; p[1][2] = z; p[1][3] = -hw;
   df Q0 = z, Q1 = z, Q2 = z, Q3 = z;
-#pragma unroll
+#pragma unroll 1  // one copy of the per-particle code: the unrolled form overflows the instruction cache
   for (int k = 0; k < NF; ++k) {
     uint64_t o[4];
     Philox::block(event, (uint64_t)att, (uint64_t)k, 0ull, seed, 0ull, o);
@@ -397,7 +397,7 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
   const df gam = Q0 * iM;
   const df a = dfs(1.0f) / (gam + 1.0f);
   const df x = w * iM;
-#pragma unroll
+#pragma unroll 1
   for (int k = 0; k < NF; ++k) {
     df* q = p[2 + k];
     const df bq = (b1 * q[1] + b2 * q[2]) + b3 * q[3];
@@ -502,9 +502,9 @@ __host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const d
     af[i] = zz * ip;
     rf[i] = sqrtf(pt2 + zz * zz) * ip;
   }
-#pragma unroll
+#pragma unroll 1  // as in rambo_df: one copy of the pair test
   for (int i = 2; i < NEXT; ++i) {
-#pragma unroll
+#pragma unroll 1
     for (int j = i + 1; j < NEXT; ++j) {
       if (undecided || !((mask >> i) & 1u) || !((mask >> j) & 1u)) continue;
       const df* qi = p[i];
