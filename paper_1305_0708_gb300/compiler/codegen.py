@@ -181,7 +181,10 @@ class _Emitter:
                         self.flops32 += 5
             E("    tot += s;")
             E("  }")
-        E(f"  return (double)tot * {float(p.average / p.cmat_den)!r};")
+        if self.mode == "mixed":
+            E(f"  return tot * {float(p.average / p.cmat_den)!r}f;")
+        else:
+            E(f"  return (double)tot * {float(p.average / p.cmat_den)!r};")
 
     # ------------------------------------------------------------------
     def child_vars(self, nid, var, child):
@@ -435,8 +438,8 @@ struct Traits {{
 {body64}
   }}
 
-  // mixed path: double-float momenta and resonant invariants, FP32 amplitudes
-  static __host__ __device__ __forceinline__ double evalmx(const me::df (&pm)[{n}][4], const Params& prm) {{
+  // mixed path: double-float momenta and resonant invariants, FP32 amplitudes and result
+  static __host__ __device__ __forceinline__ float evalmx(const me::df (&pm)[{n}][4], const Params& prm) {{
     using R = float;
 {unpack}
 {mc2}

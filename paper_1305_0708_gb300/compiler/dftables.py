@@ -105,6 +105,9 @@ def header():
     ln2 = Decimal(2).ln()
     lines.append("constexpr float kLn2Hi = %s, kLn2Lo = %s;" % tuple(_f(x) for x in split(ln2)))
     lines.append("constexpr float kPiHi = %s, kPiLo = %s;" % tuple(_f(x) for x in split(PI)))
+    lines.append("constexpr float kInvPiHi = %s, kInvPiLo = %s;" % tuple(_f(x) for x in split(1 / PI)))
+    lines.append("constexpr float kInv2PiHi = %s, kInv2PiLo = %s;" % tuple(_f(x) for x in split(1 / (2 * PI))))
+    lines.append("constexpr float kInv4PiHi = %s, kInv4PiLo = %s;" % tuple(_f(x) for x in split(1 / (4 * PI))))
     lines.append("constexpr float kThirdHi = %s, kThirdLo = %s;" % tuple(_f(x) for x in split(Decimal(1) / 3)))
     lines.append("constexpr float kSixthHi = %s, kSixthLo = %s;" % tuple(_f(x) for x in split(Decimal(1) / 6)))
     lines.append("}  // namespace me")

@@ -519,13 +519,17 @@ __global__ void __launch_bounds__(Cfg<R>::THREADS, min_blocks<R>())
       if (mom_out) mom_out[(int64_t)t * out_stride + i] = v;
     }
     __syncthreads();
-    const double wps = wps_a[i], shat = shat_a[i];
-    const bool ok = wps > 0.0;
+    // mixed path: k_ps stored the weight factor as a double-float pair in the weight slot
+    const float2 wf = reinterpret_cast<const float2*>(wps_a)[i];
+    const double wps = MIXED ? 0.0 : wps_a[i], shat = shat_a[i];
+    const bool ok = MIXED ? wf.x > 0.0f : wps > 0.0;
     double m2 = 0.0;
     if (ok) m2 = event_block<R>(p, (R)gs, sh, cs);
     if (t == 0) {
-      const double w = !ok ? 0.0 : (kin.wfactor > 0.0 ? m2 * kin.wfactor
-                                                       : wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb);
+      const double w = !ok ? 0.0
+                           : MIXED ? m2 * ((double)wf.x + (double)wf.y)
+                                   : (kin.wfactor > 0.0 ? m2 * kin.wfactor
+                                                        : wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb);
       sw += w;
       sw2 = fma(w, w, sw2);
       ntries += tries_a[i];
@@ -609,7 +613,7 @@ struct NoME {
     double unused;
   };
   static __host__ __device__ double eval64(const double (&)[NG][4], const Params&) { return 0.0; }
-  static __host__ __device__ double evalmx(const df (&)[NG][4], const Params&) { return 0.0; }
+  static __host__ __device__ float evalmx(const df (&)[NG][4], const Params&) { return 0.0f; }
 };
 
 cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t n, const double* params,

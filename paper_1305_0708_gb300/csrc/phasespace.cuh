@@ -362,7 +362,7 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
 // ---------------------------------------------------------------------------
 // Mixed-precision phase space: RAMBO in double-float arithmetic (FP32 pairs,
 // ~2^-48 relative) on the FP32 pipe, the same formulas and draw order as
-// gen_rambo.  The ttbar generator runs in FP64 and is split into double-floats.
+// gen_rambo; the tt~ chain in double-float below.
 // ---------------------------------------------------------------------------
 template <int NEXT>
 __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
@@ -538,8 +538,143 @@ __host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const d
   return pass_cuts<NEXT>(kin, pd);
 }
 
+// ---------------------------------------------------------------------------
+// g g > t t~ > (b W+)(b~ W-) in double-float: the formulas and uniforms of
+// gen_ttbar (sqrt(s) uniform, Breit-Wigner t, t~, W+, W- virtualities from
+// s = m^2 + m G tan(theta), isotropic two-body decays boosted to the lab).  The
+// two-body momentum uses the factorised Kallen function
+// lambda(s, m1^2, m2^2) = (s - (m1 + m2)^2)(s - (m1 - m2)^2), with
+// s - (m1 +- m2)^2 = (rs - m1 -+ m2)(rs + m1 +- m2), which keeps its relative
+// accuracy near threshold; the Breit-Wigner Jacobian uses 1 + tan^2.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ void direction_df(df a, df b, df& nx, df& ny, df& nz) {
+  const df c = df{a.hi * 2.0f, a.lo * 2.0f} + (-1.0f);
+  const df sn = df_sqrt((dfs(1.0f) - c) * (dfs(1.0f) + c));
+  df sp, cp;
+  df_sincospi(df{b.hi * 2.0f, b.lo * 2.0f}, sp, cp);
+  nx = sn * cp;
+  ny = sn * sp;
+  nz = c;
+}
+
+__host__ __device__ __forceinline__ void boost_from_rest_df(df* p, const df* P, df M) {
+  const df pp = (P[1] * p[1] + P[2] * p[2]) + P[3] * p[3];
+  const df iM = dfs(1.0f) / M;
+  const df e = (P[0] * p[0] + pp) * iM;
+  const df f = (pp / (P[0] + M) + p[0]) * iM;
+  p[0] = e;
+  p[1] = p[1] + f * P[1];
+  p[2] = p[2] + f * P[2];
+  p[3] = p[3] + f * P[3];
+}
+
+// s = m^2 + m G tan(theta), theta = t0 + (t1 - t0) u in (-pi/2, pi/2); jac = (t1 - t0) m G (1 + tan^2) / (2 pi)
+__host__ __device__ __forceinline__ df bw_draw_df(double m, double g, double t0, double t1, df u, df& jac) {
+  const df T0 = from_double(t0), dT = from_double(t1) - T0;
+  const df th = T0 + dT * u;
+  df x = th * df{kInvPiHi, kInvPiLo};  // theta / pi in (-1/2, 1/2)
+  if (x.hi < 0.0f) x = x + 2.0f;        // sin and cos of pi x have period 2
+  df sn, cs;
+  df_sincospi(x, sn, cs);
+  const df t = sn / cs;
+  const df M = from_double(m), mg = M * from_double(g);
+  jac = (dT * mg) * (sqr(t) + 1.0f) * df{kInv2PiHi, kInv2PiLo};
+  return sqr(M) + mg * t;
+}
+
+__host__ __device__ __forceinline__ void set4_df(df* p, df e, df x, df y, df z) {
+  p[0] = e; p[1] = x; p[2] = y; p[3] = z;
+}
+
+// |p*| of the two-body decay of mass rs into masses m1, m2
+__host__ __device__ __forceinline__ df two_body_k(df rs, df m1, df m2) {
+  const df a = (rs - m1) - m2, b = (rs + m1) + m2, c = (rs - m1) + m2, d = (rs + m1) - m2;
+  return df_sqrt((a * b) * (c * d)) / df{rs.hi * 2.0f, rs.lo * 2.0f};
+}
+
+template <int NEXT>
+__host__ __device__ __forceinline__ bool ttbar_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
+                                                  df (&p)[NEXT][4], double& wps, double& shat) {
+  if constexpr (NEXT != 8) {
+    return false;
+  } else {
+    df u[16];
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      uint64_t o[4];
+      Philox::block(event, (uint64_t)att, (uint64_t)j, 0ull, seed, 0ull, o);
+      u[4 * j + 0] = unit_df(o[0]);
+      u[4 * j + 1] = unit_df(o[1]);
+      u[4 * j + 2] = unit_df(o[2]);
+      u[4 * j + 3] = unit_df(o[3]);
+    }
+    const df rmin = from_double(kin.sqrt_s_min);
+    const df rs = rmin + (from_double(kin.sqrt_s_max) - rmin) * u[0];
+    df jt, jtb, jwp, jwm;
+    const df st = bw_draw_df(kin.bw_mass[0], kin.bw_width[0], kin.bw_t0[0], kin.bw_t1[0], u[1], jt);
+    const df stb = bw_draw_df(kin.bw_mass[0], kin.bw_width[0], kin.bw_t0[0], kin.bw_t1[0], u[2], jtb);
+    const df swp = bw_draw_df(kin.bw_mass[1], kin.bw_width[1], kin.bw_t0[1], kin.bw_t1[1], u[3], jwp);
+    const df swm = bw_draw_df(kin.bw_mass[1], kin.bw_width[1], kin.bw_t0[1], kin.bw_t1[1], u[4], jwm);
+    if (!(st.hi > 0.0f && stb.hi > 0.0f && swp.hi > 0.0f && swm.hi > 0.0f)) return false;
+    const df mt = df_sqrt(st), mtb = df_sqrt(stb), mwp = df_sqrt(swp), mwm = df_sqrt(swm);
+    // kinematic limits, decided in FP64 on the double-float values (as gen_ttbar)
+    if (!(to_double(mwp) <= to_double(mt) && to_double(mwm) <= to_double(mtb) &&
+          to_double(mt) + to_double(mtb) <= to_double(rs)))
+      return false;
+    const df z = dfs(0.0f), hw = df{rs.hi * 0.5f, rs.lo * 0.5f};
+    set4_df(p[0], hw, z, z, hw);
+    set4_df(p[1], hw, z, z, -hw);
+    df nx, ny, nz;
+    // production in the CM frame
+    const df kp = two_body_k(rs, mt, mtb);
+    direction_df(u[5], u[6], nx, ny, nz);
+    df T[4], TB[4];
+    set4_df(T, df_sqrt(st + sqr(kp)), kp * nx, kp * ny, kp * nz);
+    set4_df(TB, df_sqrt(stb + sqr(kp)), -(kp * nx), -(kp * ny), -(kp * nz));
+    // t -> b W+
+    const df kt = (st - swp) / df{mt.hi * 2.0f, mt.lo * 2.0f};
+    direction_df(u[7], u[8], nx, ny, nz);
+    df WP[4];
+    set4_df(p[2], kt, kt * nx, kt * ny, kt * nz);
+    set4_df(WP, df_sqrt(swp + sqr(kt)), -(kt * nx), -(kt * ny), -(kt * nz));
+    boost_from_rest_df(p[2], T, mt);
+    boost_from_rest_df(WP, T, mt);
+    // W+ -> e+ ve
+    const df kw = df{mwp.hi * 0.5f, mwp.lo * 0.5f};
+    direction_df(u[9], u[10], nx, ny, nz);
+    set4_df(p[3], kw, kw * nx, kw * ny, kw * nz);
+    set4_df(p[4], kw, -(kw * nx), -(kw * ny), -(kw * nz));
+    boost_from_rest_df(p[3], WP, mwp);
+    boost_from_rest_df(p[4], WP, mwp);
+    // t~ -> b~ W-
+    const df ktb = (stb - swm) / df{mtb.hi * 2.0f, mtb.lo * 2.0f};
+    direction_df(u[11], u[12], nx, ny, nz);
+    df WM[4];
+    set4_df(p[5], ktb, ktb * nx, ktb * ny, ktb * nz);
+    set4_df(WM, df_sqrt(swm + sqr(ktb)), -(ktb * nx), -(ktb * ny), -(ktb * nz));
+    boost_from_rest_df(p[5], TB, mtb);
+    boost_from_rest_df(WM, TB, mtb);
+    // W- -> e- ve~
+    const df kw2 = df{mwm.hi * 0.5f, mwm.lo * 0.5f};
+    direction_df(u[13], u[14], nx, ny, nz);
+    set4_df(p[6], kw2, kw2 * nx, kw2 * ny, kw2 * nz);
+    set4_df(p[7], kw2, -(kw2 * nx), -(kw2 * ny), -(kw2 * nz));
+    boost_from_rest_df(p[6], WM, mwm);
+    boost_from_rest_df(p[7], WM, mwm);
+    // (kp / (4 pi rs)) (kt / (4 pi mt)) (kw / (4 pi mW+)) (ktb / (4 pi mt~)) (kw2 / (4 pi mW-)) x Jacobians
+    const df i4p = df{kInv4PiHi, kInv4PiLo};
+    const df w1 = (kp / rs) * (kt / mt), w2 = (kw / mwp) * (ktb / mtb), w3 = kw2 / mwm;
+    const df i4p2 = sqr(i4p);
+    const df jac = (jt * jtb) * (jwp * jwm);
+    const df wt = ((((w1 * w2) * w3) * jac) * (i4p2 * i4p2)) * i4p;
+    wps = to_double(wt);
+    shat = to_double(sqr(rs));
+    return true;
+  }
+}
+
 // one mixed-precision draw: double-float RAMBO (massless, or with the massive
-// rescaling), else the FP64 generator split into double-floats
+// rescaling) or tt~ chain; the two-body generator in FP64 split into double-floats
 template <int NEXT>
 __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
                                               df (&p)[NEXT][4], double& wps, double& shat) {
@@ -550,6 +685,7 @@ __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64
     shat = kin.shat_fixed;
     return pass_cuts_df<NEXT>(kin, p);
   }
+  if (kin.kind == ME_PS_TTBAR) return ttbar_df<NEXT>(kin, seed, event, att, p, wps, shat) && pass_cuts_df<NEXT>(kin, p);
   double pd[NEXT][4];
   const bool ok = draw_point<NEXT>(kin, seed, event, att, pd, wps, shat);
   if (ok) {

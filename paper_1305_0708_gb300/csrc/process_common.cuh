@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, ui
   __shared__ int s_q[2][kThreads];
   __shared__ int s_qn[2];
   double sw = 0.0, sw2 = 0.0, nt = 0.0;
+  df swf = dfs(0.0f), sw2f = dfs(0.0f);  // mixed path: weights formed and summed as in k_me
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t base = tile * kThreads;
@@ -184,13 +185,22 @@ __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, ui
 #pragma unroll
           for (int m = 0; m < 4; ++m) pm[k][m] = df{s_ph[k * 4 + m][ev], s_pl[k * 4 + m][ev]};
         }
-        if (eval_me && ok) m2 = P::evalmx(pm, prm);
+        const float m2f = (eval_me && ok) ? P::evalmx(pm, prm) : 0.0f;
+        m2 = (double)m2f;
         if (mom_out) {
 #pragma unroll
           for (int k = 0; k < NEXT; ++k) {
 #pragma unroll
             for (int m = 0; m < 4; ++m) mom_out[((int64_t)(k * 4 + m)) * n + i] = to_double(pm[k][m]);
           }
+        }
+        if (ok) {
+          const df wf = kin.wfactor > 0.0 ? from_double(kin.wfactor)
+                                          : (from_double(wps) * from_double(kin.s_ident * (0.5 * kGeV2pb))) /
+                                                from_double(shat);
+          const float w = m2f * wf.hi;
+          swf = swf + w;
+          sw2f = sw2f + two_prod(w, w);
         }
       } else {
         double pm[NEXT][4];
@@ -208,9 +218,11 @@ __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, ui
           }
         }
       }
-      const double w = ok ? wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb : 0.0;
-      sw += w;
-      sw2 += w * w;
+      if constexpr (!MIXED) {
+        const double w = ok ? wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb : 0.0;
+        sw += w;
+        sw2 += w * w;
+      }
       nt += (double)tries;
       if (me2_out) me2_out[i] = m2;
       if (wps_out) wps_out[i] = wps;
@@ -218,6 +230,10 @@ __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, ui
       if (tries_out) tries_out[i] = tries;
     }
     __syncthreads();
+  }
+  if constexpr (MIXED) {
+    sw = to_double(swf);
+    sw2 = to_double(sw2f);
   }
   if (partials) block_reduce3(sw, sw2, nt, partials);
 }
@@ -228,7 +244,10 @@ __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, ui
 // it runs at high occupancy) into a workspace; k_me evaluates |M|^2, forms the
 // weights and writes one partial per block.  Workspace layout per chunk of m
 // points: momenta [NEXT*4][m] as FP64 (FP64 path) or as two FP32 arrays hi, lo
-// (mixed path), then wps [m], shat [m] (FP64) and tries [m] (int32).
+// (mixed path), then wps [m] (FP64 path: FP64 phase-space weight; mixed path: the
+// whole weight factor w_PS s_ident / (2 s) in pb GeV^2 as an FP32 hi/lo pair), shat [m]
+// (FP64) and tries [m] (int32).  The mixed k_me thus forms each weight in FP32 and sums
+// a thread's weights as double-floats; the per-block and final sums are FP64.
 // ---------------------------------------------------------------------------
 // k_ps: each block owns a contiguous range of events and a circular queue of
 // redraws.  Every round takes up to kThreads items -- first the carried-over
@@ -301,7 +320,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, uint64_t seed, u
         }
       }
       if (ok) {
-        wps_a[ev] = wps;
+        if constexpr (MIXED) {
+          // weight factor w_PS s_ident / (2 s) GeV^2->pb as a double-float pair in the weight slot
+          const df wf = kin.wfactor > 0.0 ? from_double(kin.wfactor)
+                                          : (from_double(wps) * from_double(kin.s_ident * (0.5 * kGeV2pb))) /
+                                                from_double(shat);
+          float2* wf_a = reinterpret_cast<float2*>(wps_a);
+          wf_a[ev] = make_float2(wf.hi, wf.lo);
+        } else {
+          wps_a[ev] = wps;
+        }
         shat_a[ev] = shat;
         tries_a[ev] = att + 1;
       } else if (att + 1 >= kin.max_attempts) {
@@ -333,12 +361,14 @@ __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const vo
   const double* shat_a = wps_a + m;
   const int32_t* tries_a = reinterpret_cast<const int32_t*>(shat_a + m);
   double sw = 0.0, sw2 = 0.0;
+  df swf = dfs(0.0f), sw2f = dfs(0.0f);  // mixed path: per-thread sums as double-floats
   int64_t ntries = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const double wps = wps_a[i], shat = shat_a[i];
-    const bool ok = wps > 0.0;
     double m2 = 0.0;
     if constexpr (MIXED) {
+      // FP32 |M|^2 times the double-float weight factor written by k_ps; no FP64 per point
+      const float wf = reinterpret_cast<const float2*>(wps_a)[i].x;
+      const bool ok = wf > 0.0f;
       df q[NEXT][4];
 #pragma unroll
       for (int k = 0; k < NEXT; ++k) {
@@ -346,7 +376,7 @@ __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const vo
         for (int mu = 0; mu < 4; ++mu)
           q[k][mu] = df{__ldg(ph + (int64_t)(k * 4 + mu) * m + i), __ldg(pl + (int64_t)(k * 4 + mu) * m + i)};
       }
-      if (ok) m2 = P::evalmx(q, prm);
+      const float m2f = ok ? P::evalmx(q, prm) : 0.0f;
       if (mom_out) {
 #pragma unroll
         for (int k = 0; k < NEXT; ++k) {
@@ -354,7 +384,14 @@ __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const vo
           for (int mu = 0; mu < 4; ++mu) mom_out[(int64_t)(k * 4 + mu) * out_stride + i] = to_double(q[k][mu]);
         }
       }
+      const float w = m2f * wf;
+      swf = swf + w;
+      sw2f = sw2f + two_prod(w, w);
+      ntries += tries_a[i];
+      if (me2_out) me2_out[i] = (double)m2f;
     } else {
+      const double wps = wps_a[i], shat = shat_a[i];
+      const bool ok = wps > 0.0;
       double q[NEXT][4];
 #pragma unroll
       for (int k = 0; k < NEXT; ++k) {
@@ -369,14 +406,18 @@ __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const vo
           for (int mu = 0; mu < 4; ++mu) mom_out[(int64_t)(k * 4 + mu) * out_stride + i] = q[k][mu];
         }
       }
+      // constant weight factor for fixed-energy generators (one FP64 multiply per point)
+      const double w = !ok ? 0.0 : (kin.wfactor > 0.0 ? m2 * kin.wfactor
+                                                       : wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb);
+      sw += w;
+      sw2 = fma(w, w, sw2);
+      ntries += tries_a[i];
+      if (me2_out) me2_out[i] = m2;
     }
-    // constant weight factor for fixed-energy generators (one FP64 multiply per point)
-    const double w = !ok ? 0.0 : (kin.wfactor > 0.0 ? m2 * kin.wfactor
-                                                     : wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb);
-    sw += w;
-    sw2 = fma(w, w, sw2);
-    ntries += tries_a[i];
-    if (me2_out) me2_out[i] = m2;
+  }
+  if constexpr (MIXED) {
+    sw = to_double(swf);
+    sw2 = to_double(sw2f);
   }
   block_reduce3(sw, sw2, (double)ntries, partials);
 }
