@@ -67,6 +67,14 @@ DF_HD df operator+(df a, df b) {
   return fast_two_sum(v.hi, df_add_rn(t.lo, v.lo));
 }
 DF_HD df operator-(df a, df b) { return a + (-b); }
+// Sloppy sum (Dekker; SloppyDWPlusDW in Joldes, Muller, Popescu): one TwoSum, error
+// below 2^-47 (|a| + |b|) rather than 2^-47 |a + b|.  For sums whose accuracy is
+// needed relative to their operands' scale (momentum components against sqrt(s)).
+DF_HD df sadd(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, df_add_rn(s.lo, df_add_rn(a.lo, b.lo)));
+}
+DF_HD df ssub(df a, df b) { return sadd(a, df{-b.hi, -b.lo}); }
 DF_HD df operator*(df a, df b) {
   const df p = two_prod(a.hi, b.hi);
   const float t = df_fma(a.hi, b.lo, df_mul_rn(a.lo, b.hi));

@@ -389,9 +389,9 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
     p[2 + k][1] = qs * cp;
     p[2 + k][2] = qs * sp;
     p[2 + k][3] = q0 * c;
-    Q0 = Q0 + p[2 + k][0]; Q1 = Q1 + p[2 + k][1]; Q2 = Q2 + p[2 + k][2]; Q3 = Q3 + p[2 + k][3];
+    Q0 = sadd(Q0, p[2 + k][0]); Q1 = sadd(Q1, p[2 + k][1]); Q2 = sadd(Q2, p[2 + k][2]); Q3 = sadd(Q3, p[2 + k][3]);
   }
-  const df M = df_sqrt(((sqr(Q0) - sqr(Q1)) - sqr(Q2)) - sqr(Q3));
+  const df M = df_sqrt(ssub(ssub(ssub(sqr(Q0), sqr(Q1)), sqr(Q2)), sqr(Q3)));
   const df iM = dfs(1.0f) / M;
   const df b1 = -(Q1 * iM), b2 = -(Q2 * iM), b3 = -(Q3 * iM);
   const df gam = Q0 * iM;
@@ -400,13 +400,13 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
 #pragma unroll 1
   for (int k = 0; k < NF; ++k) {
     df* q = p[2 + k];
-    const df bq = (b1 * q[1] + b2 * q[2]) + b3 * q[3];
+    const df bq = sadd(sadd(b1 * q[1], b2 * q[2]), b3 * q[3]);
     const df q0 = q[0];
-    const df c = q0 + a * bq;
-    q[0] = x * (gam * q0 + bq);
-    q[1] = x * (q[1] + b1 * c);
-    q[2] = x * (q[2] + b2 * c);
-    q[3] = x * (q[3] + b3 * c);
+    const df c = sadd(q0, a * bq);
+    q[0] = x * sadd(gam * q0, bq);
+    q[1] = x * sadd(q[1], b1 * c);
+    q[2] = x * sadd(q[2], b2 * c);
+    q[3] = x * sadd(q[3], b3 * c);
   }
 }
 
