@@ -63,6 +63,7 @@ class _Emitter:
         self.flops32 = 0      # amplitude-precision flops per event
         self.flops64 = 0      # FP64 flops per event (momenta, invariants)
         self.cpl_names = set()
+        self.mx_masses = {}       # mixed path: mass parameter -> width parameter of its resonant lines
         self.half = {}            # spinor variable -> set of halves ("u", "l") that can be non-zero
 
     def emit(self, s):
@@ -141,8 +142,10 @@ class _Emitter:
                     E(f"  const me::df Q{nid}[4] = {{{', '.join(dcomps)}}};")
                     E(f"  const me::df q2_{nid} = ((me::sqr(Q{nid}[0]) - me::sqr(Q{nid}[1])) - me::sqr(Q{nid}[2])) - "
                       f"me::sqr(Q{nid}[3]);")
-                    E(f"  const me::cx<R> inv{nid} = inv_den_f(me::to_float(q2_{nid} - me::from_double({m} * {m})), "
-                      f"(float)({wexpr}));")
+                    # m^2 (double-float) and m Gamma (FP32) come converted from the host (ParamsMx)
+                    mname = _ident(part.mass)
+                    self.mx_masses[mname] = _ident(part.width) if w else None
+                    E(f"  const me::cx<R> inv{nid} = inv_den_f(me::to_float(q2_{nid} - prm.sq_{mname}), prm.mw_{mname});")
                     self.flops32 += 20 * (len(legs) - 1) * 4 + 4 * 8 + 3 * 20 + 20
                 else:
                     E(f"  const double Q{nid}[4] = {{{', '.join(comps)}}};")
@@ -414,6 +417,26 @@ def generate_source(prog, tag):
             mc2.append(f"    const me::cx<R> inv_mc2_{mname} = inv_den<R>(c_{mname} * c_{mname}, "
                        f"-c_{mname} * c_{wname});")
     mc2 = "\n".join(mc2)
+    # mixed path: every parameter as FP32, and per mass m^2 (double-float), m Gamma and
+    # 1/(m^2 - i m Gamma), converted once per launch on the host; in the kernel they are
+    # constant-bank operands (no conversion, no register held across the point loop)
+    mx_masses = sorted(set(masses_for_mc2) | set(emmx.mx_masses))
+    mx_fields = [f"    float {_ident(n)};" for n in cpl]
+    mx_init = [f"    q.{_ident(n)} = (float)p.{_ident(n)};" for n in cpl]
+    for mname in mx_masses:
+        wname = "W" + mname[1:]
+        wexpr = f"p.{mname} * p.{wname}" if wname in cpl else "0.0"
+        mx_fields += [f"    me::df sq_{mname};", f"    float mw_{mname};", f"    me::cx<float> imc2_{mname};"]
+        mx_init += [f"    q.sq_{mname} = me::from_double(p.{mname} * p.{mname});",
+                    f"    q.mw_{mname} = (float)({wexpr});",
+                    f"    q.imc2_{mname} = inv_den<float>(p.{mname} * p.{mname}, -({wexpr}));"]
+    if not mx_fields:
+        mx_fields = ["    float unused;"]
+    mx_fields = "\n".join(mx_fields)
+    mx_init = "\n".join(mx_init)
+    unpack_mx = "\n".join(f"    const float c_{_ident(n)} = prm.{_ident(n)};" for n in cpl)
+    mc2_mx = "\n".join(f"    const me::cx<R> inv_mc2_{m} = prm.imc2_{m};" for m in masses_for_mc2
+                        if ("W" + m[1:]) in cpl)
     body64 = "\n".join("  " + ln for ln in em64.lines)
     bodymx = "\n".join("  " + ln for ln in emmx.lines)
     n = prog.n_ext
@@ -429,6 +452,14 @@ struct Traits {{
   struct Params {{
 {params}
   }};
+  struct ParamsMx {{
+{mx_fields}
+  }};
+  static ParamsMx mixed_params(const Params& p) {{
+    ParamsMx q;
+{mx_init}
+    return q;
+  }}
 
   // FP64 path: FP64 momenta, invariants and amplitudes
   static __host__ __device__ __forceinline__ double eval64(const double (&pm)[{n}][4], const Params& prm) {{
@@ -439,10 +470,10 @@ struct Traits {{
   }}
 
   // mixed path: double-float momenta and resonant invariants, FP32 amplitudes and result
-  static __host__ __device__ __forceinline__ float evalmx(const me::df (&pm)[{n}][4], const Params& prm) {{
+  static __host__ __device__ __forceinline__ float evalmx(const me::df (&pm)[{n}][4], const ParamsMx& prm) {{
     using R = float;
-{unpack}
-{mc2}
+{unpack_mx}
+{mc2_mx}
 {bodymx}
   }}
 }};

@@ -612,8 +612,10 @@ struct NoME {
   struct Params {
     double unused;
   };
+  using ParamsMx = Params;
+  static ParamsMx mixed_params(const Params& p) { return p; }
   static __host__ __device__ double eval64(const double (&)[NG][4], const Params&) { return 0.0; }
-  static __host__ __device__ float evalmx(const df (&)[NG][4], const Params&) { return 0.0f; }
+  static __host__ __device__ float evalmx(const df (&)[NG][4], const ParamsMx&) { return 0.0f; }
 };
 
 cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t n, const double* params,

@@ -19,6 +19,7 @@
 // Both use a grid-stride loop over a grid sized in multiples of the SM count.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "dfloat.cuh"
@@ -49,6 +50,11 @@ __host__ __device__ __forceinline__ me::cx<float> inv_den_f(float a, float b) {
 namespace me {
 constexpr double kGeV2pb = 0.3893793721e9;
 
+// parameter block of a kernel: FP64 values (FP64 path) or the host-converted FP32 /
+// double-float values of the mixed path
+template <class P, bool MIXED>
+using PrmT = typename std::conditional<MIXED, typename P::ParamsMx, typename P::Params>::type;
+
 __host__ __device__ __forceinline__ P4<float> p4f(const df* p) {
   return P4<float>{to_float(p[0]), to_float(p[1]), to_float(p[2]), to_float(p[3])};
 }
@@ -76,7 +82,7 @@ __device__ __forceinline__ void block_reduce3(double a, double b, double c, doub
 
 template <class P, bool MIXED>
 __global__ void __launch_bounds__(kThreads) k_eval(const double* __restrict__ mom, int64_t n,
-                                                   double* __restrict__ out, typename P::Params prm) {
+                                                   double* __restrict__ out, PrmT<P, MIXED> prm) {
   constexpr int NEXT = P::NEXT;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if constexpr (MIXED) {
@@ -101,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_eval(const double* __restrict__ mo
 
 template <class P, bool MIXED>
 __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, uint64_t offset, int64_t n,
-                                                   typename P::Params prm, double* __restrict__ partials,
+                                                   PrmT<P, MIXED> prm, double* __restrict__ partials,
                                                    double* __restrict__ me2_out, double* __restrict__ mom_out,
                                                    double* __restrict__ wps_out, double* __restrict__ shat_out,
                                                    int32_t* __restrict__ tries_out, int* status, int eval_me) {
@@ -349,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, uint64_t seed, u
 
 template <class P, bool MIXED>
 __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const void* __restrict__ ws,
-                                                 typename P::Params prm, double* __restrict__ partials,
+                                                 PrmT<P, MIXED> prm, double* __restrict__ partials,
                                                  double* __restrict__ me2_out, double* __restrict__ mom_out,
                                                  int64_t out_stride) {
   constexpr int NEXT = P::NEXT;
@@ -432,7 +438,8 @@ cudaError_t launch_step(int prec, const KinDev* kin, uint64_t seed, uint64_t off
   else k_ps<P, true><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
   if (ev_mid) cudaEventRecord(ev_mid, s);
   if (prec == ME_FP64) k_me<P, false><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
-  else k_me<P, true><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
+  else k_me<P, true><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, P::mixed_params(prm), partials, me2_out, mom_out,
+                                                   out_stride);
   return cudaGetLastError();
 }
 
@@ -442,7 +449,7 @@ cudaError_t launch_eval(int prec, const double* mom, int64_t n, double* out, con
   typename P::Params prm;
   memcpy(&prm, params, sizeof(prm));
   if (prec == ME_FP64) k_eval<P, false><<<grid, kThreads, 0, s>>>(mom, n, out, prm);
-  else k_eval<P, true><<<grid, kThreads, 0, s>>>(mom, n, out, prm);
+  else k_eval<P, true><<<grid, kThreads, 0, s>>>(mom, n, out, P::mixed_params(prm));
   return cudaGetLastError();
 }
 
@@ -456,8 +463,8 @@ cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t off
     k_xsec<P, false><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, prm, partials, me2_out, mom_out, wps_out,
                                                shat_out, tries_out, status, eval_me);
   else
-    k_xsec<P, true><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, prm, partials, me2_out, mom_out, wps_out,
-                                              shat_out, tries_out, status, eval_me);
+    k_xsec<P, true><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, P::mixed_params(prm), partials, me2_out,
+                                              mom_out, wps_out, shat_out, tries_out, status, eval_me);
   return cudaGetLastError();
 }
 }  // namespace me
