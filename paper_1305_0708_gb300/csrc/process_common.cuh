@@ -428,6 +428,109 @@ __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const vo
   block_reduce3(sw, sw2, (double)ntries, partials);
 }
 
+// ---------------------------------------------------------------------------
+// k_me_mx: the mixed-path |M|^2 kernel with its inputs staged through shared
+// memory.  The helicity program holds ~255 registers, so only 8 warps fit on an
+// SM and the global loads of a point's 8*NEXT + 2 words stall them; here every
+// thread copies the next tile's words of its own point with cp.async (4-byte
+// copies: no alignment condition on the chunk size) while it evaluates the
+// current one.  A thread reads only the column it copied itself, so no block
+// barrier is needed between the stages.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+#ifdef __CUDA_ARCH__
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src));
+#endif
+}
+__device__ __forceinline__ void cp_async_commit() {
+#ifdef __CUDA_ARCH__
+  asm volatile("cp.async.commit_group;\n" ::);
+#endif
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+#ifdef __CUDA_ARCH__
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+#endif
+}
+
+template <class P>
+constexpr int me_mx_words() {
+  return 8 * P::NEXT + 2;  // momenta hi and lo, weight factor (hi), tries
+}
+template <class P>
+constexpr size_t me_mx_smem() {
+  return 2 * sizeof(float) * (size_t)me_mx_words<P>() * kThreads;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kThreads) k_me_mx(KinDev kin, int64_t m, const void* __restrict__ ws,
+                                                    PrmT<P, true> prm, double* __restrict__ partials,
+                                                    double* __restrict__ me2_out, double* __restrict__ mom_out,
+                                                    int64_t out_stride) {
+  constexpr int NEXT = P::NEXT, NW = me_mx_words<P>();
+  extern __shared__ __align__(16) float s_stage[];  // [2][NW][kThreads]
+  const float* ph = reinterpret_cast<const float*>(ws);
+  const float* pl = ph + (int64_t)NEXT * 4 * m;
+  const float2* wf_a = reinterpret_cast<const float2*>(pl + (int64_t)NEXT * 4 * m);
+  const int32_t* tries_a = reinterpret_cast<const int32_t*>(reinterpret_cast<const double*>(wf_a) + 2 * m);
+  const int64_t ntiles = (m + kThreads - 1) / kThreads;
+  const int tid = threadIdx.x;
+  auto stage = [&](int64_t tile, int b) {
+    const int64_t i = tile * kThreads + tid;
+    float* dst = s_stage + (size_t)b * NW * kThreads + tid;
+    if (i < m) {
+#pragma unroll
+      for (int c = 0; c < 4 * NEXT; ++c) {
+        cp_async4(dst + c * kThreads, ph + (int64_t)c * m + i);
+        cp_async4(dst + (4 * NEXT + c) * kThreads, pl + (int64_t)c * m + i);
+      }
+      cp_async4(dst + 8 * NEXT * kThreads, &wf_a[i].x);
+      cp_async4(dst + (8 * NEXT + 1) * kThreads, tries_a + i);
+    }
+    cp_async_commit();
+  };
+  df swf = dfs(0.0f), sw2f = dfs(0.0f);
+  int64_t ntries = 0;
+  int b = 0;
+  if ((int64_t)blockIdx.x < ntiles) stage(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (tile + gridDim.x < ntiles) stage(tile + gridDim.x, b ^ 1);
+    else cp_async_commit();  // an empty group keeps the wait count uniform
+    cp_async_wait<1>();      // this thread's copies of the current tile have landed
+    const int64_t i = tile * kThreads + tid;
+    if (i < m) {
+      const float* src = s_stage + (size_t)b * NW * kThreads + tid;
+      const float wf = src[8 * NEXT * kThreads];
+      const bool ok = wf > 0.0f;
+      df q[NEXT][4];
+#pragma unroll
+      for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+          q[k][mu] = df{src[(k * 4 + mu) * kThreads], src[(4 * NEXT + k * 4 + mu) * kThreads]};
+      }
+      const float m2f = ok ? P::evalmx(q, prm) : 0.0f;
+      if (mom_out) {
+#pragma unroll
+        for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+          for (int mu = 0; mu < 4; ++mu) mom_out[(int64_t)(k * 4 + mu) * out_stride + i] = to_double(q[k][mu]);
+        }
+      }
+      const float w = m2f * wf;
+      swf = swf + w;
+      sw2f = sw2f + two_prod(w, w);
+      ntries += __float_as_int(src[(8 * NEXT + 1) * kThreads]);
+      if (me2_out) me2_out[i] = (double)m2f;
+    }
+    b ^= 1;
+  }
+  cp_async_wait<0>();
+  block_reduce3(to_double(swf), to_double(sw2f), (double)ntries, partials);
+}
+
 template <class P>
 cudaError_t launch_step(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t m, const double* params,
                         void* ws, double* partials, double* me2_out, double* mom_out, int64_t out_stride,
@@ -437,9 +540,14 @@ cudaError_t launch_step(int prec, const KinDev* kin, uint64_t seed, uint64_t off
   if (prec == ME_FP64) k_ps<P, false><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
   else k_ps<P, true><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
   if (ev_mid) cudaEventRecord(ev_mid, s);
-  if (prec == ME_FP64) k_me<P, false><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
-  else k_me<P, true><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, P::mixed_params(prm), partials, me2_out, mom_out,
-                                                   out_stride);
+  if (prec == ME_FP64) {
+    k_me<P, false><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_me_mx<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)me_mx_smem<P>());
+    if (e != cudaSuccess) return e;
+    k_me_mx<P><<<grid_me, kThreads, me_mx_smem<P>(), s>>>(*kin, m, ws, P::mixed_params(prm), partials, me2_out,
+                                                           mom_out, out_stride);
+  }
   return cudaGetLastError();
 }
 
