@@ -108,28 +108,33 @@ def header(n):
 
     cm, ct = flat(cur)
     am, at = flat(amps)
-    # per tuple size S: the entries of that size (currents of one phase, or the amplitudes for
-    # S = n-1) all have S-1 three-vertex and (S-1)(S-2)/2 four-vertex terms; their child indices
-    # are stored slot-major, idx[slot * COUNT + entry], so that a warp reads consecutive entries
-    start, count, off, idx = [0] * n, [0] * n, [0] * n, []
+    # per tuple size S (currents of one phase, or the amplitudes for S = n-1): the distinct
+    # currents of the vertex terms of an entry s -- prefixes s[:t] and suffixes s[t:]
+    # (t = 1..S-1), then middles s[i:j] (1 <= i < j <= S-1); the three-gluon terms are
+    # (s[:t], s[t:]) and the four-gluon terms (s[:i], s[i:j], s[j:]).  Stored slot-major,
+    # pqm[slot * COUNT + entry], so that a warp reads consecutive entries.
+    start, count, off, pqm = [0] * n, [0] * n, [0] * n, []
     by_size = {sz: (st, ct_) for sz, (st, ct_) in zip(range(2, n - 1), t["phases"])}
     by_size[n - 1] = (0, len(amps))
+    index = t["index"]
     for sz in range(2, n):
         st, cnt = by_size[sz]
         ents = amps if sz == n - 1 else cur[st:st + cnt]
-        nv3, nv4 = sz - 1, (sz - 1) * (sz - 2) // 2
-        slots = []
+        npre = sz - 1
+        pairs = [(i, j) for i in range(1, npre + 1) for j in range(i + 1, npre + 1)]
+        rows = []
         for tup, v3, v4 in ents:
-            assert len(tup) == sz and len(v3) == nv3 and len(v4) == nv4
-            slots.append([x for ab in v3 for x in ab] + [x for abc in v4 for x in abc])
-        start[sz], count[sz], off[sz] = st, cnt, len(idx)
-        for j in range(2 * nv3 + 3 * nv4):
-            idx += [row[j] for row in slots]
+            assert len(tup) == sz and len(v3) == npre and len(v4) == len(pairs)
+            rows.append([index[tup[:k]] for k in range(1, npre + 1)] + [index[tup[k:]] for k in range(1, npre + 1)] +
+                        [index[tup[i:j]] for i, j in pairs])
+        start[sz], count[sz], off[sz] = st, cnt, len(pqm)
+        for j in range(len(rows[0])):
+            pqm += [r[j] for r in rows]
     lines.append(f"  static constexpr int START[{n}] = {{{', '.join(map(str, start))}}};")
     lines.append(f"  static constexpr int COUNT[{n}] = {{{', '.join(map(str, count))}}};")
-    lines.append(f"  static constexpr int IDX_OFF[{n}] = {{{', '.join(map(str, off))}}};")
+    lines.append(f"  static constexpr int PQM_OFF[{n}] = {{{', '.join(map(str, off))}}};")
     lines.append("};")
-    lines.append(f"__device__ const int16_t kIdx{n}[{len(idx)}] = {{" + ", ".join(map(str, idx)) + "};")
+    lines.append(f"__device__ const int16_t kPQM{n}[{len(pqm)}] = {{" + ", ".join(map(str, pqm)) + "};")
     lines.append(f"__device__ const int32_t kCurMeta{n}[{len(cm) * 4}] = {{" +
                  ", ".join(str(x) for m in cm for x in m) + "};")
     lines.append(f"__device__ const int16_t kCurTerms{n}[{max(len(ct), 1)}] = {{" +
@@ -149,7 +154,7 @@ def header(n):
     lines.append(f"__device__ const float kColour{n}[{len(cn) * len(cn)}] = {{" +
                  ", ".join(f"{float(x)!r}f" for row in cn for x in row) + "};")
     # host copies for host-side checks
-    lines.append(f"static const int16_t kIdx{n}_h[{len(idx)}] = {{" + ", ".join(map(str, idx)) + "};")
+    lines.append(f"static const int16_t kPQM{n}_h[{len(pqm)}] = {{" + ", ".join(map(str, pqm)) + "};")
     lines.append(f"static const int32_t kCurMeta{n}_h[{len(cm) * 4}] = {{" +
                  ", ".join(str(x) for m in cm for x in m) + "};")
     lines.append(f"static const int16_t kCurTerms{n}_h[{max(len(ct), 1)}] = {{" +

@@ -255,25 +255,43 @@ __device__ double colour_pair(Shared<double>& sh, const float* sC) {
   return part;
 }
 
-// Vertex sum of entry i of tuple size S (a current of one phase, or an amplitude
-// for S = NG-1), amputated: S-1 three-gluon and (S-1)(S-2)/2 four-gluon terms of
-// the consecutive splittings, child indices read slot-major (coalesced).
+// Vertex sum of current i of tuple size S, amputated: the three-gluon terms
+// V3(P_t, Q_t) and the four-gluon terms V4(P_i, M_ij, Q_j) of its prefixes
+// P_t = J(s[:t]), suffixes Q_t = J(s[t:]) and middles M_ij = J(s[i:j]) (table
+// kPQM, slot-major).  Each prefix is loaded once; with kc the current's own
+// outgoing momentum, k(Q_t) = kc - k(P_t), so the three-gluon vertex (legs P, Q, X
+// with kx = -kc) needs the prefix momentum only.
 template <int S, class R>
-__device__ __forceinline__ W4<R> vertex_sum(const JS<R>* J, const KS<R>* K, int i, R g, R g2) {
-  constexpr int NV3 = S - 1, NV4 = (S - 1) * (S - 2) / 2, CNT = T::COUNT[S], OFF = T::IDX_OFF[S];
-  const int16_t* ix = ME_GTN(kIdx) + OFF + i;
+__device__ __forceinline__ W4<R> vertex_sum(const JS<R>* J, const KS<R>* K, const P4<R>& kc, int i, R g, R g2) {
+  constexpr int NP = S - 1, CNT = T::COUNT[S], OFF = T::PQM_OFF[S];
+  const int16_t* ix = ME_GTN(kPQM) + OFF + i;
   W4<R> s;
 #pragma unroll
   for (int k = 0; k < 4; ++k) s.c[k] = mk(R(0), R(0));
 #pragma unroll
-  for (int t = 0; t < NV3; ++t) {
-    const int a = ix[(2 * t) * CNT], b = ix[(2 * t + 1) * CNT];
-    acc(s, v3(ldj(J[a]), ldk(K[a]), ldj(J[b]), ldk(K[b])), g);
-  }
+  for (int t = 1; t <= NP; ++t) {
+    const int pa = ix[(t - 1) * CNT];
+    const W4<R> Pj = ldj(J[pa]);
+    const P4<R> k1 = ldk(K[pa]);
+    {
+      const W4<R> Qj = ldj(J[ix[(NP + t - 1) * CNT]]);
+      // d12 = k1 - k2 = 2 k1 - kc, d2x = k2 - kx = 2 kc - k1, dx1 = kx - k1 = -(kc + k1)
+      const P4<R> d12 = {R(2) * k1.e - kc.e, R(2) * k1.x - kc.x, R(2) * k1.y - kc.y, R(2) * k1.z - kc.z};
+      const P4<R> d2x = {R(2) * kc.e - k1.e, R(2) * kc.x - k1.x, R(2) * kc.y - k1.y, R(2) * kc.z - k1.z};
+      const P4<R> dx1 = {-(kc.e + k1.e), -(kc.x + k1.x), -(kc.y + k1.y), -(kc.z + k1.z)};
+      const cx<R> j12 = mdot(Pj, Qj), av = mdot(d2x, Pj), bv = mdot(dx1, Qj);
+      W4<R> o;
+      o.c[0] = d12.e * j12 + Qj.c[0] * av + Pj.c[0] * bv;
+      o.c[1] = d12.x * j12 + Qj.c[1] * av + Pj.c[1] * bv;
+      o.c[2] = d12.y * j12 + Qj.c[2] * av + Pj.c[2] * bv;
+      o.c[3] = d12.z * j12 + Qj.c[3] * av + Pj.c[3] * bv;
+      acc(s, o, g);
+    }
 #pragma unroll
-  for (int u = 0; u < NV4; ++u) {
-    const int a = ix[(2 * NV3 + 3 * u) * CNT], b = ix[(2 * NV3 + 3 * u + 1) * CNT], c = ix[(2 * NV3 + 3 * u + 2) * CNT];
-    acc(s, v4(ldj(J[a]), ldj(J[b]), ldj(J[c])), g2);
+    for (int j = t + 1; j <= NP; ++j) {
+      const int ma = ix[(2 * NP + (t - 1) * (2 * NP - t) / 2 + (j - t - 1)) * CNT];
+      acc(s, v4(Pj, ldj(J[ma]), ldj(J[ix[(NP + j - 1) * CNT]])), g2);
+    }
   }
   return s;
 }
@@ -285,7 +303,7 @@ __device__ __forceinline__ void current_phases(Shared<R>& sh, JS<R>* J, int lt, 
     constexpr int CNT = T::COUNT[S], ST = T::START[S];
     for (int i = lt; i < CNT; i += kThreads) {
       const int c = ST + i;
-      W4<R> s = vertex_sum<S, R>(J, sh.K, i, g, g2);
+      W4<R> s = vertex_sum<S, R>(J, sh.K, ldk(sh.K[c]), i, g, g2);
       const R f = sh.invp2[c];
 #pragma unroll
       for (int k = 0; k < 4; ++k) s.c[k] = f * s.c[k];
@@ -297,46 +315,55 @@ __device__ __forceinline__ void current_phases(Shared<R>& sh, JS<R>* J, int lt, 
   }
 }
 
-// Amplitudes of ordering i for both root helicities, from scalars only.  The
-// amplitude is eps0_r . S with S the amputated vertex sum of the full tuple;
+// Amplitudes of ordering a for both root helicities, from scalars only.  The
+// amplitude is eps0_r . S with S the amputated vertex sum of the full tuple s;
 // contracting each vertex term with eps0_r first gives, with e_r(J) = eps0_r . J
 // and E_r(k) = eps0_r . k (momenta outgoing, kx = -(k1 + k2)):
-//   three-gluon:  eps0.V3 = (E(k1) - E(k2)) (J1.J2) + e(J2) (k1 + 2 k2).J1 - e(J1) (2 k1 + k2).J2
+//   three-gluon:  eps0.V3 = (E(k1) - E(k2)) (J1.J2) + e(J2) (k2 - kx).J1 + e(J1) (kx - k1).J2
 //   four-gluon:   eps0.V4 = 2 (J1.J3) e(J2) - (J1.J2) e(J3) - (J2.J3) e(J1)
-// (the vertices of v3 and v4 above), so that no four-vector sum is formed.
+// (the vertices of v3 and v4 above), so that no four-vector sum is formed.  The
+// terms use the prefixes P_t = J(s[:t]), suffixes Q_t = J(s[t:]) and middles
+// M_ij = J(s[i:j]) of s: V3(P_t, Q_t) and V4(P_i, M_ij, Q_j).  Each prefix is
+// loaded once; momentum conservation gives k(Q_t) = p0 - k(P_t), with p0 the root's
+// physical momentum, so kx = -p0, and transversality eps0 . p0 = 0 gives
+// E(k(Q_t)) = -E(k(P_t)).
 template <class R>
-__device__ __forceinline__ void amp_scalar(const JS<R>* J, const KS<R>* K, const KS<R>* EK, int i, R g, R g2,
-                                           cx<R>& A0, cx<R>& A1) {
-  constexpr int S = NG - 1, NV3 = S - 1, NV4 = (S - 1) * (S - 2) / 2, CNT = T::COUNT[S], OFF = T::IDX_OFF[S];
-  const int16_t* ix = ME_GTN(kIdx) + OFF + i;
+__device__ __forceinline__ void amp_scalar(const JS<R>* J, const KS<R>* K, const KS<R>* EK, const P4<R>& p0, int a,
+                                           R g, R g2, cx<R>& A0, cx<R>& A1) {
+  constexpr int NP = NG - 2, CNT = T::NAMP, OFF = T::PQM_OFF[NG - 1];
+  const int16_t* ix = ME_GTN(kPQM) + OFF + a;
   cx<R> s30 = mk(R(0), R(0)), s31 = s30, s40 = s30, s41 = s30;
 #pragma unroll
-  for (int t = 0; t < NV3; ++t) {
-    const int a = ix[(2 * t) * CNT], b = ix[(2 * t + 1) * CNT];
-    const W4<R> J1 = ldj(J[a]), J2 = ldj(J[b]);
-    const P4<R> k1 = ldk(K[a]), k2 = ldk(K[b]);
-    const P4<R> q1 = ldk(EK[a]), q2 = ldk(EK[b]);
-    cx<R> e10, e11, e20, e21;
-    lde(J[a], e10, e11);
-    lde(J[b], e20, e21);
-    const P4<R> d2x = {k1.e + R(2) * k2.e, k1.x + R(2) * k2.x, k1.y + R(2) * k2.y, k1.z + R(2) * k2.z};
-    const P4<R> dx1 = {-(R(2) * k1.e + k2.e), -(R(2) * k1.x + k2.x), -(R(2) * k1.y + k2.y), -(R(2) * k1.z + k2.z)};
-    const cx<R> j12 = mdot(J1, J2), av = mdot(d2x, J1), bv = mdot(dx1, J2);
-    s30 = s30 + mk(q1.e - q2.e, q1.x - q2.x) * j12 + e20 * av + e10 * bv;
-    s31 = s31 + mk(q1.y - q2.y, q1.z - q2.z) * j12 + e21 * av + e11 * bv;
-  }
+  for (int i = 1; i <= NP; ++i) {
+    const int pa = ix[(i - 1) * CNT];
+    const W4<R> Pj = ldj(J[pa]);
+    cx<R> ep0, ep1;
+    lde(J[pa], ep0, ep1);
+    const P4<R> k1 = ldk(K[pa]), q1 = ldk(EK[pa]);
+    {
+      const int qa = ix[(NP + i - 1) * CNT];
+      const W4<R> Qj = ldj(J[qa]);
+      cx<R> eq0, eq1;
+      lde(J[qa], eq0, eq1);
+      const P4<R> d2x = {R(2) * p0.e - k1.e, R(2) * p0.x - k1.x, R(2) * p0.y - k1.y, R(2) * p0.z - k1.z};
+      const P4<R> dx1 = {-(k1.e + p0.e), -(k1.x + p0.x), -(k1.y + p0.y), -(k1.z + p0.z)};
+      const cx<R> j12 = mdot(Pj, Qj), av = mdot(d2x, Pj), bv = mdot(dx1, Qj);
+      s30 = s30 + mk(R(2) * q1.e, R(2) * q1.x) * j12 + eq0 * av + ep0 * bv;
+      s31 = s31 + mk(R(2) * q1.y, R(2) * q1.z) * j12 + eq1 * av + ep1 * bv;
+    }
 #pragma unroll
-  for (int u = 0; u < NV4; ++u) {
-    const int a = ix[(2 * NV3 + 3 * u) * CNT], b = ix[(2 * NV3 + 3 * u + 1) * CNT], c = ix[(2 * NV3 + 3 * u + 2) * CNT];
-    const W4<R> J1 = ldj(J[a]), J2 = ldj(J[b]), J3 = ldj(J[c]);
-    cx<R> e10, e11, e20, e21, e30, e31;
-    lde(J[a], e10, e11);
-    lde(J[b], e20, e21);
-    lde(J[c], e30, e31);
-    const cx<R> j13 = mdot(J1, J3), j12 = mdot(J1, J2), j23 = mdot(J2, J3);
-    const cx<R> t13 = j13 + j13;
-    s40 = s40 + t13 * e20 - j12 * e30 - j23 * e10;
-    s41 = s41 + t13 * e21 - j12 * e31 - j23 * e11;
+    for (int j = i + 1; j <= NP; ++j) {
+      const int ma = ix[(2 * NP + (i - 1) * (2 * NP - i) / 2 + (j - i - 1)) * CNT];
+      const int qa = ix[(NP + j - 1) * CNT];
+      const W4<R> Mj = ldj(J[ma]), Qj = ldj(J[qa]);
+      cx<R> em0, em1, eq0, eq1;
+      lde(J[ma], em0, em1);
+      lde(J[qa], eq0, eq1);
+      const cx<R> j13 = mdot(Pj, Qj), j12 = mdot(Pj, Mj), j23 = mdot(Mj, Qj);
+      const cx<R> t13 = j13 + j13;
+      s40 = s40 + t13 * em0 - j12 * eq0 - j23 * ep0;
+      s41 = s41 + t13 * em1 - j12 * eq1 - j23 * ep1;
+    }
   }
   A0 = R(2) * (g * s30 + g2 * s40);
   A1 = R(2) * (g * s31 + g2 * s41);
@@ -397,9 +424,10 @@ __device__ double event_block(const R (&p)[NG][4], R gs, Shared<R>& sh, CS cs) {
     current_phases<2, R>(sh, J, lt, g, g2);
     // (2b) amplitudes for both root helicities -> rows 4 hs .. 4 hs + 3
     unsigned e = 0u;
+    const P4<R> p0 = {p[0][0], p[0][1], p[0][2], p[0][3]};
     for (int a = lt; a < T::NAMP; a += kThreads) {
       cx<R> a0, a1;
-      amp_scalar<R>(J, sh.K, sh.EK, a, g, g2, a0, a1);
+      amp_scalar<R>(J, sh.K, sh.EK, p0, a, g, g2, a0, a1);
       sh.X[4 * hs + 0][a] = a0.re;
       sh.X[4 * hs + 1][a] = a0.im;
       sh.X[4 * hs + 2][a] = a1.re;
