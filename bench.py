@@ -116,6 +116,35 @@ def dist_env():
     return rank, world, local
 
 
+# Philox counter ranges of the ranks: rank r draws its points from counters
+# [r * RANK_STRIDE, r * RANK_STRIDE + steps * points), disjoint for < 2^40 points per rank
+RANK_STRIDE = 1 << 40
+
+
+def rank_offset(rank):
+    return rank * RANK_STRIDE
+
+
+def job_rate(step_ms, points_per_rank, world, dist=None, device=None):
+    """Whole-job rate: every rank's points over the slowest rank's step time (max over ranks)."""
+    import torch
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return points_per_rank * world / (t_max * 1e-3), t_max
+
+
+def merge_acc(acc, world, dist=None, device=None):
+    """Monte Carlo sums of all ranks (each rank's xsec_step accumulator), summed."""
+    import torch
+    v = torch.tensor([acc.sum_w, acc.sum_w2, float(acc.n_acc), float(acc.n_try)], dtype=torch.float64,
+                     device=device)
+    if world > 1:
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return {"sum_w": float(v[0]), "sum_w2": float(v[1]), "n_acc": int(v[2]), "n_try": int(v[3])}
+
+
 def oracle_kin(w):
     from paper_1305_0708_gb300.compiler.diagrams import parse
     n_ext = len(parse(w["process"]).particles)
@@ -351,7 +380,7 @@ def main():
     n = args.points if args.points > 0 else w["n"]
     kin = B.make_kin(**kin_args(w))
     stream = torch.cuda.current_stream(dev)
-    offset0 = rank * (1 << 40)
+    offset0 = rank_offset(rank)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def barrier():
@@ -383,11 +412,8 @@ def main():
     ms32, wall32, acc32 = time_steps(h32, args.steps, args.warmup)
     clk = clocks.stop(local)
     step_ms = sum(ms32) / len(ms32)
-    t_max = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    step_ms = float(t_max.item())
-    value = n * world / (step_ms * 1e-3)
+    value, step_ms = job_rate(step_ms, n, world, dist, dev)
+    mc = merge_acc(acc32, world, dist, dev)
 
     # per-kernel device time of the step (CUDA events recorded by the library on the launch
     # stream around k_ps and k_me), taken on extra steps of the same work after the timed region
@@ -513,7 +539,8 @@ def main():
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
             "clocks": clk,
-            "mc": {"sigma_pb": acc32.sum_w / acc32.n_try, "n_try": acc32.n_try, "n_acc": acc32.n_acc},
+            "mc": {"sigma_pb": mc["sum_w"] / mc["n_try"], "n_try": mc["n_try"], "n_acc": mc["n_acc"],
+                   "ranks": world},
             "wall_s_timed": wall32,
         }
         print(json.dumps(line), flush=True)
