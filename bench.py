@@ -35,9 +35,9 @@ PS_FLOPS_PER_DRAW = {"rambo": 2700.0}
 # DRAM bytes per point of the mixed-path kernels (dram__bytes_read.sum + dram__bytes_write.sum of one
 # ncu capture, divided by the points of that launch; profiles/ holds the captures).  A launch's
 # traffic is this times its points: the kernels stream their points, so traffic grows in proportion.
-TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): 326.337536e6 / 2 ** 20,
-                     ("udx_epvegg", "k_me"): 226.21568e6 / 2 ** 20,
-                     ("gg_gggg", "k_me"): 3.617792e6 / 16384}
+TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (81.950976e6 + 290.4768e6) / 2 ** 20,
+                     ("udx_epvegg", "k_me"): (214.006016e6 + 3.48672e6) / 2 ** 20,
+                     ("gg_gggg", "k_me"): (3.478784e6 + 0.07552e6) / 16384}
 
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
