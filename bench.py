@@ -174,20 +174,56 @@ def oracle_step(w, events):
     return oxs.accumulate(fn(P, par), W, S, T, w["s_ident"])
 
 
+def _pool_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    import oracle.processes  # noqa: F401  (imports paid before the clock)
+
+
+def _pool_step(job):
+    w, events = job
+    return oracle_step(w, events)
+
+
+def oracle_pool(cores):
+    """Process pool for the oracle on the host cores, started with spawn (safe beside CUDA)."""
+    import multiprocessing
+    return multiprocessing.get_context("spawn").Pool(cores, initializer=_pool_init)
+
+
+def oracle_step_cores(pool, cores, w, events):
+    """The oracle's step on a sample split by points over the pool's processes; sums summed."""
+    import numpy as np
+    parts = [e for e in np.array_split(events, cores) if len(e)]
+    res = pool.map(_pool_step, [(w, e) for e in parts])
+    return tuple(sum(r[k] for r in res) for k in range(4))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def run_reference(args, w, rank, world):
     """FP64 CPU oracle on the host cores: bounded samples per step."""
     import numpy as np
     if rank != 0:
         return
-    sample = args.ref_sample
-    oracle_step(w, np.arange(64))  # warm caches and imports
+    cores = host_cores()
+    sample = args.ref_sample * cores
+    pool = oracle_pool(cores)
+    oracle_step_cores(pool, cores, w, np.arange(8 * cores))  # warm caches and imports
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle_step(w, np.arange(s * sample, (s + 1) * sample))
+        oracle_step_cores(pool, cores, w, np.arange(s * sample, (s + 1) * sample))
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
+    pool.close()
+    pool.join()
     per_step = sum(times) / len(times)
     value = sample / per_step
     line = {"metric": "|M|^2 evals/s", "value": value, "unit": "evals/s", "n_gpus": 0, "steps": args.steps,
@@ -195,9 +231,9 @@ def run_reference(args, w, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "describe": w["describe"], "points_per_step": sample,
                        "l2": "not applicable (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
                              "sample": f"{sample} accepted points per step of the same workload (numpy FP64, "
-                                       f"one thread)"},
+                                       f"split over {cores} single-threaded processes)"},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -509,14 +545,25 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1:
+        # one core, then every host core (the sample split by points over single-threaded processes)
         events = np.arange(args.cpu_sample)
         oracle_step(w, np.arange(32))
         t0 = time.perf_counter()
         oracle_step(w, events)
-        dt = time.perf_counter() - t0
-        cpu = {"value": args.cpu_sample / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_sample} accepted points of the same workload (generate, |M|^2, weights), "
-                         f"numpy FP64 on one host core"}
+        v1 = args.cpu_sample / (time.perf_counter() - t0)
+        cores = host_cores()
+        pool = oracle_pool(cores)
+        oracle_step_cores(pool, cores, w, np.arange(4 * cores))
+        n_all = args.cpu_sample * cores
+        t0 = time.perf_counter()
+        oracle_step_cores(pool, cores, w, np.arange(10 ** 7, 10 ** 7 + n_all))
+        vall = n_all / (time.perf_counter() - t0)
+        pool.close()
+        pool.join()
+        cpu = {"value": vall, "unit": "evals/s", "cores": cores, "kind": "oracle", "value_1core": v1,
+               "sample": f"{n_all} accepted points of the same workload (generate, |M|^2, weights), numpy FP64 "
+                         f"split over {cores} single-threaded processes; value_1core: {args.cpu_sample} points "
+                         f"on one core"}
 
     if rank == 0:
         line = {
