@@ -344,6 +344,7 @@ def serving_mix(B, rates=((10, 48), (100, 128), (1000, 256)), baseline_budget_s=
         st = B.me_server_get_stats(srv)
         out["server"]["bytes_peak"] = st.bytes_peak
         out["server"]["launches"] = st.launches
+        out["server"]["graph_launches"] = st.graph_launches
     finally:
         B.me_server_destroy(srv)
     # plain FP64 path, one synchronous launch sequence per request

@@ -9,6 +9,10 @@
  *   - admits requests first-in first-out while the device memory they need
  *     (|M|^2 and momentum arrays, per-chunk partial sums) fits in the budget
  *     beside the slot workspaces; a request bigger than the budget is refused;
+ *   - launches a chunk as one CUDA graph per slot and process (the phase-space
+ *     and |M|^2 kernels, captured at the first use and instantiated once; a
+ *     chunk rewrites the kernels' per-chunk arguments in the executable graph),
+ *     falling back to direct launches if a graph cannot be made;
  *   - splits every admitted request into chunks of a per-process size chosen
  *     by a timing autotuner (the smallest chunk whose time per point is within
  *     15 % of the best one), and keeps n_slots CUDA streams busy with chunks
@@ -72,6 +76,7 @@ typedef struct {
   int64_t submitted, admitted, completed, waiting, active;
   int64_t points_done;     /* accepted points of completed requests */
   int64_t launches;        /* chunk launches (each: phase-space and |M|^2 kernels) */
+  int64_t graph_launches;  /* of those, launched as the slot's instantiated CUDA graph of the step */
 } me_server_stats;
 
 /* Start a server on the caller's current CUDA device.  cfg may be NULL (defaults). */

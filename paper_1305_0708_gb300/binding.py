@@ -64,7 +64,7 @@ class me_server_stats(ctypes.Structure):
     _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64),
                 ("bytes_peak", ctypes.c_uint64), ("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
                 ("completed", ctypes.c_int64), ("waiting", ctypes.c_int64), ("active", ctypes.c_int64),
-                ("points_done", ctypes.c_int64), ("launches", ctypes.c_int64)]
+                ("points_done", ctypes.c_int64), ("launches", ctypes.c_int64), ("graph_launches", ctypes.c_int64)]
 
 
 ME_FP64, ME_MIXED = 0, 1

@@ -520,8 +520,13 @@ __global__ void __launch_bounds__(Cfg<R>::THREADS, min_blocks<R>())
 
 template <class R, bool MIXED>
 __global__ void __launch_bounds__(Cfg<R>::THREADS, min_blocks<R>())
-    k_me_gluon(KinDev kin, int64_t m, const void* __restrict__ ws, double gs, double* __restrict__ partials,
-               int nslots, double* __restrict__ me2_out, double* __restrict__ mom_out, int64_t out_stride) {
+    k_me_gluon(KinDev kin, StepArgs a, double gs) {
+  const int64_t m = a.m, out_stride = a.out_stride;
+  const void* __restrict__ ws = a.ws;
+  double* __restrict__ partials = a.partials;
+  double* __restrict__ me2_out = a.me2_out;
+  double* __restrict__ mom_out = a.mom_out;
+  const int nslots = a.nslots;
   extern __shared__ __align__(128) unsigned char smem[];
   Shared<R>& sh = setup<R>(smem);
   const auto cs = ColourSmem<R>::load(smem + shared_offset<R>());
@@ -613,22 +618,19 @@ cudaError_t launch_eval(int prec, const double* mom, int64_t n, double* out, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_step(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t m, const double* params,
-                        void* ws, double* partials, double* me2_out, double* mom_out, int64_t out_stride, int* status,
-                        cudaStream_t s, int grid_ps, int grid_me, cudaEvent_t ev_mid) {
+cudaError_t launch_step(int prec, const KinDev* kin, const StepArgs* a, const double* params, cudaStream_t s,
+                        int grid_ps, int grid_me, cudaEvent_t ev_mid) {
   cudaError_t e;
   int g = 0;
-  if (prec == ME_FP64) k_ps<Traits, false><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
-  else k_ps<Traits, true><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
+  if (prec == ME_FP64) k_ps<Traits, false><<<grid_ps, kThreads, 0, s>>>(*kin, *a);
+  else k_ps<Traits, true><<<grid_ps, kThreads, 0, s>>>(*kin, *a);
   if (ev_mid) cudaEventRecord(ev_mid, s);
   if (prec == ME_FP64) {
     if ((e = prepare<double>(k_me_gluon<double, false>, grid_me, g)) != cudaSuccess) return e;
-    k_me_gluon<double, false><<<g, Cfg<double>::THREADS, smem_bytes<double>(), s>>>(*kin, m, ws, params[0], partials, grid_me,
-                                                                         me2_out, mom_out, out_stride);
+    k_me_gluon<double, false><<<g, Cfg<double>::THREADS, smem_bytes<double>(), s>>>(*kin, *a, params[0]);
   } else {
     if ((e = prepare<float>(k_me_gluon<float, true>, grid_me, g)) != cudaSuccess) return e;
-    k_me_gluon<float, true><<<g, Cfg<float>::THREADS, smem_bytes<float>(), s>>>(*kin, m, ws, params[0], partials, grid_me,
-                                                                      me2_out, mom_out, out_stride);
+    k_me_gluon<float, true><<<g, Cfg<float>::THREADS, smem_bytes<float>(), s>>>(*kin, *a, params[0]);
   }
   return cudaGetLastError();
 }

@@ -33,6 +33,21 @@ struct KinDev {
 constexpr int kThreads = 128;
 
 // Entry points of one compiled process.
+// Per-chunk arguments of the Monte Carlo step kernels, in one struct so that a
+// captured CUDA graph of a step can be pointed at the next chunk by rewriting
+// one kernel argument.
+struct StepArgs {
+  uint64_t seed, offset;  // Philox key and the counter of the chunk's first point
+  int64_t m;              // points of the chunk
+  void* ws;               // phase-space workspace of the chunk (k_ps -> |M|^2 kernel)
+  int* status;            // set to 1 if a point exhausts its redraws
+  double* partials;       // 3 doubles (sum w, sum w^2, tries) per block of the |M|^2 kernel
+  int nslots;             // partial slots reserved for the chunk (>= blocks launched)
+  double* me2_out;        // optional |M|^2 per point
+  double* mom_out;        // optional momenta, SoA [n_ext][4] with stride out_stride
+  int64_t out_stride;
+};
+
 struct ProcessDesc {
   const char* name;
   int n_ext;
@@ -48,10 +63,8 @@ struct ProcessDesc {
                              const double* params, double* partials, double* me2_out, double* mom_out,
                              double* wps_out, double* shat_out, int32_t* tries_out, int* status,
                              int eval_me, cudaStream_t s, int grid);
-  cudaError_t (*launch_step)(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t m,
-                             const double* params, void* ws, double* partials, double* me2_out, double* mom_out,
-                             int64_t out_stride, int* status, cudaStream_t s, int grid_ps, int grid_me,
-                             cudaEvent_t ev_mid);
+  cudaError_t (*launch_step)(int prec, const KinDev* kin, const StepArgs* a, const double* params, cudaStream_t s,
+                             int grid_ps, int grid_me, cudaEvent_t ev_mid);
 };
 
 }  // namespace me

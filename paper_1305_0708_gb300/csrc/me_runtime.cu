@@ -407,10 +407,10 @@ me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t
     const int64_t first = c * kChunk;
     const int64_t m = std::min<int64_t>(kChunk, n_accept - first);
     if (h->timing) cudaEventRecord(h->ev[0], s);
-    e = h->desc->launch_step(h->prec, &k, seed, counter_offset + (uint64_t)first, m, h->cvals.data(), h->d_ws,
-                             h->d_partials + 3 * (size_t)grid_me * c, me2_out ? me2_out + first : nullptr,
-                             momenta_out ? momenta_out + first : nullptr, n_accept, h->d_status, s, grid_ps,
-                             grid_me, h->timing ? h->ev[1] : nullptr);
+    me::StepArgs a{seed, counter_offset + (uint64_t)first, m, h->d_ws, h->d_status,
+                   h->d_partials + 3 * (size_t)grid_me * c, grid_me, me2_out ? me2_out + first : nullptr,
+                   momenta_out ? momenta_out + first : nullptr, n_accept};
+    e = h->desc->launch_step(h->prec, &k, &a, h->cvals.data(), s, grid_ps, grid_me, h->timing ? h->ev[1] : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "xsec_step launch");
     if (h->timing) {
       cudaEventRecord(h->ev[2], s);

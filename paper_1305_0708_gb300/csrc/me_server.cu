@@ -22,6 +22,7 @@
 #include <memory>
 #include <thread>
 #include <utility>
+#include <vector>
 
 #include "me_server.h"
 #include "runtime_internal.h"
@@ -69,6 +70,17 @@ struct Request {
   me_request_result res{};
 };
 
+// The step of one process on one slot as an instantiated CUDA graph (the
+// phase-space and |M|^2 kernels, captured once); a chunk rewrites the two
+// kernels' (KinDev, StepArgs) arguments in the executable graph and launches it.
+struct SlotGraph {
+  bool ok = false;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t node_ps = nullptr, node_me = nullptr;
+  cudaKernelNodeParams p_ps{}, p_me{};  // as captured; p_me.kernelParams[2] is the parameter block
+};
+
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
@@ -76,6 +88,7 @@ struct Slot {
   size_t ws_cap = 0;
   Request* req = nullptr;  // request whose chunk (or final reduction) is in flight
   bool final = false;
+  std::map<const Proc*, SlotGraph> graphs;
 };
 
 }  // namespace
@@ -108,6 +121,7 @@ struct me_server_s {
   bool admit(Request* q);
   bool launch_chunk(Slot& sl, Request* q);
   bool grow_workspaces(size_t need);
+  SlotGraph& graph_for(Slot& sl, Request* q, const me::StepArgs& sa);
   void finish(Request* q, me_status status);
   void release(Request* q);
 };
@@ -141,9 +155,10 @@ me_status tune_chunk(me_handle h, const me::KinDev& kin, cudaStream_t s, int64_t
     float best = 0.0f;
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {  // first repetition warms up
       e = cudaEventRecord(e0, s);
-      if (e == cudaSuccess)
-        e = h->desc->launch_step(h->prec, &kin, 12345u, (uint64_t)rep * (uint64_t)m, m, h->cvals.data(), ws, part,
-                                 nullptr, nullptr, m, status, s, gp, gm, nullptr);
+      if (e == cudaSuccess) {
+        const me::StepArgs sa{12345u, (uint64_t)rep * (uint64_t)m, m, ws, status, part, gm, nullptr, nullptr, m};
+        e = h->desc->launch_step(h->prec, &kin, &sa, h->cvals.data(), s, gp, gm, nullptr);
+      }
       if (e == cudaSuccess) e = cudaEventRecord(e1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.0f;
@@ -252,17 +267,77 @@ bool me_server_s::grow_workspaces(size_t need) {
   return true;
 }
 
+// Capture the step of q's process on this slot (first use only).  Its two kernel
+// nodes are told apart by their dependencies (the phase-space kernel has none).
+SlotGraph& me_server_s::graph_for(Slot& sl, Request* q, const me::StepArgs& sa) {
+  auto it = sl.graphs.find(q->proc);
+  if (it != sl.graphs.end()) return it->second;
+  SlotGraph& sg = sl.graphs[q->proc];
+  me_handle h = q->proc->h;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return sg;
+  const cudaError_t el = h->desc->launch_step(h->prec, &q->kin, &sa, h->cvals.data(), sl.stream, q->grid_ps,
+                                              q->grid_me, nullptr);
+  e = cudaStreamEndCapture(sl.stream, &g);
+  if (el != cudaSuccess || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return sg;
+  }
+  size_t n = 0;
+  cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) cudaGraphGetNodes(g, nodes.data(), &n);
+  int nk = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    ++nk;
+    size_t ndep = 0;
+    cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &ndep);
+    if (ndep == 0) sg.node_ps = nd;
+    else sg.node_me = nd;
+  }
+  if (nk != 2 || !sg.node_ps || !sg.node_me || cudaGraphKernelNodeGetParams(sg.node_ps, &sg.p_ps) != cudaSuccess ||
+      cudaGraphKernelNodeGetParams(sg.node_me, &sg.p_me) != cudaSuccess ||
+      cudaGraphInstantiate(&sg.exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    sg = SlotGraph{};
+    return sg;
+  }
+  sg.g = g;
+  sg.ok = true;
+  return sg;
+}
+
 bool me_server_s::launch_chunk(Slot& sl, Request* q) {
   const int64_t c = q->next_chunk++;
   const int64_t first = c * q->chunk;
   const int64_t m = std::min<int64_t>(q->chunk, q->r.n - first);
   me_handle h = q->proc->h;
   cudaError_t e = cudaStreamWaitEvent(sl.stream, q->ready, 0);
-  if (e == cudaSuccess)
-    e = h->desc->launch_step(h->prec, &q->kin, q->r.seed, q->r.counter_offset + (uint64_t)first, m, h->cvals.data(),
-                             sl.ws, q->d_partials + 3 * (size_t)q->grid_me * (size_t)c,
-                             q->d_me2 ? q->d_me2 + first : nullptr, q->d_mom ? q->d_mom + first : nullptr, q->r.n,
-                             q->d_status, sl.stream, q->grid_ps, q->grid_me, nullptr);
+  const me::StepArgs sa{q->r.seed, q->r.counter_offset + (uint64_t)first, m, sl.ws, q->d_status,
+                        q->d_partials + 3 * (size_t)q->grid_me * (size_t)c, q->grid_me,
+                        q->d_me2 ? q->d_me2 + first : nullptr, q->d_mom ? q->d_mom + first : nullptr, q->r.n};
+  SlotGraph& sg = graph_for(sl, q, sa);
+  if (e == cudaSuccess && sg.ok) {
+    // the chunk's arguments into the executable graph, then one launch
+    me::KinDev kin = q->kin;
+    me::StepArgs args = sa;
+    void* a_ps[2] = {&kin, &args};
+    void* a_me[3] = {&kin, &args, sg.p_me.kernelParams[2]};
+    cudaKernelNodeParams pp = sg.p_ps, pm = sg.p_me;
+    pp.kernelParams = a_ps;
+    pm.kernelParams = a_me;
+    e = cudaGraphExecKernelNodeSetParams(sg.exec, sg.node_ps, &pp);
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(sg.exec, sg.node_me, &pm);
+    if (e == cudaSuccess) e = cudaGraphLaunch(sg.exec, sl.stream);
+    if (e == cudaSuccess) ++st.graph_launches;
+  } else if (e == cudaSuccess) {
+    e = h->desc->launch_step(h->prec, &q->kin, &sa, h->cvals.data(), sl.stream, q->grid_ps, q->grid_me, nullptr);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
   if (c == 0) q->res.t_start_ms = now_ms(t0);
   ++st.launches;
@@ -331,8 +406,10 @@ void me_server_s::run() {
       me::rt::make_kin(p->h, &q->r.kin, q->kin);  // checked at submit
       q->chunk = std::min<int64_t>(p->chunk, q->r.n);
       q->nchunks = (q->r.n + q->chunk - 1) / q->chunk;
-      q->grid_me = me::rt::grid_for(p->h, q->chunk);
-      q->grid_ps = me::rt::grid_ps_for(p->h, q->chunk);
+      // one launch shape per process (its autotuned chunk), so that its captured graph serves
+      // every request; a shorter chunk leaves blocks without points
+      q->grid_me = me::rt::grid_for(p->h, p->chunk);
+      q->grid_ps = me::rt::grid_ps_for(p->h, p->chunk);
       q->res.chunk = q->chunk;
       const int n_ext = p->h->desc->n_ext;
       q->ws_need = me::rt::ws_bytes(n_ext, q->chunk);
@@ -592,6 +669,11 @@ void me_server_destroy(me_server s) {
   cudaSetDevice(s->device);
   for (auto& kv : s->all) s->release(kv.second.get());
   for (Slot& sl : s->slots) {
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    for (auto& kv : sl.graphs) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      if (kv.second.g) cudaGraphDestroy(kv.second.g);
+    }
     if (sl.ws) cudaFreeAsync(sl.ws, sl.stream);
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     if (sl.ev) cudaEventDestroy(sl.ev);

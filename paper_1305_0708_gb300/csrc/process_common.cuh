@@ -261,8 +261,11 @@ __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, ui
 // failed draw is appended with its next attempt number.  Accepted points are
 // written straight to their event's slot in the workspace.
 template <class P, bool MIXED>
-__global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, uint64_t seed, uint64_t offset, int64_t m,
-                                                    void* __restrict__ ws, int* status) {
+__global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
+  const uint64_t seed = a.seed, offset = a.offset;
+  const int64_t m = a.m;
+  void* __restrict__ ws = a.ws;
+  int* status = a.status;
   constexpr int NEXT = P::NEXT;
   constexpr int QCAP = 4 * kThreads;  // power of two; holds at most 2 kThreads items at any time
   float* ph = reinterpret_cast<float*>(ws);
@@ -354,10 +357,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, uint64_t seed, u
 }
 
 template <class P, bool MIXED>
-__global__ void __launch_bounds__(kThreads) k_me(KinDev kin, int64_t m, const void* __restrict__ ws,
-                                                 PrmT<P, MIXED> prm, double* __restrict__ partials,
-                                                 double* __restrict__ me2_out, double* __restrict__ mom_out,
-                                                 int64_t out_stride) {
+__global__ void __launch_bounds__(kThreads) k_me(KinDev kin, StepArgs a, PrmT<P, MIXED> prm) {
+  const int64_t m = a.m, out_stride = a.out_stride;
+  const void* __restrict__ ws = a.ws;
+  double* __restrict__ partials = a.partials;
+  double* __restrict__ me2_out = a.me2_out;
+  double* __restrict__ mom_out = a.mom_out;
   constexpr int NEXT = P::NEXT;
   const float* ph = reinterpret_cast<const float*>(ws);
   const float* pl = ph + (int64_t)NEXT * 4 * m;
@@ -465,10 +470,12 @@ constexpr size_t me_mx_smem() {
 }
 
 template <class P>
-__global__ void __launch_bounds__(kThreads) k_me_mx(KinDev kin, int64_t m, const void* __restrict__ ws,
-                                                    PrmT<P, true> prm, double* __restrict__ partials,
-                                                    double* __restrict__ me2_out, double* __restrict__ mom_out,
-                                                    int64_t out_stride) {
+__global__ void __launch_bounds__(kThreads) k_me_mx(KinDev kin, StepArgs a, PrmT<P, true> prm) {
+  const int64_t m = a.m, out_stride = a.out_stride;
+  const void* __restrict__ ws = a.ws;
+  double* __restrict__ partials = a.partials;
+  double* __restrict__ me2_out = a.me2_out;
+  double* __restrict__ mom_out = a.mom_out;
   constexpr int NEXT = P::NEXT, NW = me_mx_words<P>();
   extern __shared__ __align__(16) float s_stage[];  // [2][NW][kThreads]
   const float* ph = reinterpret_cast<const float*>(ws);
@@ -532,21 +539,19 @@ __global__ void __launch_bounds__(kThreads) k_me_mx(KinDev kin, int64_t m, const
 }
 
 template <class P>
-cudaError_t launch_step(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t m, const double* params,
-                        void* ws, double* partials, double* me2_out, double* mom_out, int64_t out_stride,
-                        int* status, cudaStream_t s, int grid_ps, int grid_me, cudaEvent_t ev_mid) {
+cudaError_t launch_step(int prec, const KinDev* kin, const StepArgs* a, const double* params, cudaStream_t s,
+                        int grid_ps, int grid_me, cudaEvent_t ev_mid) {
   typename P::Params prm;
   memcpy(&prm, params, sizeof(prm));
-  if (prec == ME_FP64) k_ps<P, false><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
-  else k_ps<P, true><<<grid_ps, kThreads, 0, s>>>(*kin, seed, offset, m, ws, status);
+  if (prec == ME_FP64) k_ps<P, false><<<grid_ps, kThreads, 0, s>>>(*kin, *a);
+  else k_ps<P, true><<<grid_ps, kThreads, 0, s>>>(*kin, *a);
   if (ev_mid) cudaEventRecord(ev_mid, s);
   if (prec == ME_FP64) {
-    k_me<P, false><<<grid_me, kThreads, 0, s>>>(*kin, m, ws, prm, partials, me2_out, mom_out, out_stride);
+    k_me<P, false><<<grid_me, kThreads, 0, s>>>(*kin, *a, prm);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_me_mx<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)me_mx_smem<P>());
     if (e != cudaSuccess) return e;
-    k_me_mx<P><<<grid_me, kThreads, me_mx_smem<P>(), s>>>(*kin, m, ws, P::mixed_params(prm), partials, me2_out,
-                                                           mom_out, out_stride);
+    k_me_mx<P><<<grid_me, kThreads, me_mx_smem<P>(), s>>>(*kin, *a, P::mixed_params(prm));
   }
   return cudaGetLastError();
 }

@@ -88,6 +88,7 @@ def test_alone_and_in_a_mix_are_identical(B):
                 (r0.acc.sum_w, r0.acc.sum_w2, r0.acc.n_acc, r0.acc.n_try), p
         st = B.me_server_get_stats(s)
         assert st.completed == st.submitted and st.waiting == 0 and st.active == 0
+        assert st.graph_launches == st.launches > 0  # every chunk ran as the slot's instantiated graph
     finally:
         B.me_server_destroy(s)
 
