@@ -20,6 +20,8 @@ colour-ordered Berends-Giele recursion for the partial amplitudes and a
 colour matrix summed by brute force over explicit generators.  Phase space:
 Philox4x64-10 (Salmon et al., SC'11), RAMBO (Kleiss, Stirling, Ellis 1986),
 two-body decay chains with the Breit-Wigner mapping of Eq. 16 / App. A.2.
+Adaptive integration: VEGAS (Lepage 1978) grids over the generators' uniform
+variables (vegas.py), the role of the BASES / gBASES integrator of Sect. 6.
 
 Parity status per function is given in each module header.
 """

@@ -52,12 +52,33 @@ def nblocks(kin):
     return 4
 
 
+def grid_dims(kin):
+    """Uniform variables a draw uses: the dimensions of an adaptive grid (oracle.vegas)."""
+    if kin["kind"] == "2to2":
+        return 2
+    if kin["kind"] == "rambo":
+        return 4 * kin["n_final"]
+    return 15
+
+
 def generate(kin, par, seed, events, max_attempts=10000):
     """Accepted points for the given event indices, redrawing failed ones.
 
     Returns (P [N, n, 4], W_PS [N], s-hat [N], tries [N]) where tries is the
     number of draws the event used (accepted attempt index + 1).
     """
+    return _generate(kin, par, seed, events, max_attempts, None)[:4]
+
+
+def generate_grid(kin, par, seed, events, grid, max_attempts=10000):
+    """generate() with the uniforms of every draw mapped through an adaptive grid
+    (oracle.vegas.vegas_map on the first grid_dims(kin) uniforms): the weight
+    carries the map's Jacobian.  Returns (P, W, s-hat, tries, bins [N, D])."""
+    return _generate(kin, par, seed, events, max_attempts, np.asarray(grid, dtype=np.float64))
+
+
+def _generate(kin, par, seed, events, max_attempts, grid):
+    from . import vegas
     events = np.asarray(events, dtype=np.uint64)
     N = events.shape[0]
     attempt = np.zeros(N, dtype=np.uint64)
@@ -67,10 +88,21 @@ def generate(kin, par, seed, events, max_attempts=10000):
     S = np.zeros(N)
     nb = nblocks(kin)
     cut = kin.get("cuts")
+    bins = None
+    if grid is not None:
+        assert grid.shape[0] == grid_dims(kin)
+        bins = np.zeros((N, grid.shape[0]), dtype=np.int64)
     while pending.any():
         idx = np.nonzero(pending)[0]
         u = ps.uniforms(seed, events[idx], attempt[idx], nb)
+        if grid is not None:
+            D = grid.shape[0]
+            x, jac, b = vegas.vegas_map(grid, u[:, :D])
+            u = u.copy()
+            u[:, :D] = x
         Pn, Wn, ok, Sn = draw(kin, par, u)
+        if grid is not None:
+            Wn = Wn * jac
         if cut is not None:
             ok = ok & ps.pass_cuts(Pn, cut["legs"], cut["pt_min"], cut["eta_max"], cut["dr_min"])
         if P is None:
@@ -79,11 +111,13 @@ def generate(kin, par, seed, events, max_attempts=10000):
         P[acc] = Pn[ok]
         W[acc] = Wn[ok]
         S[acc] = Sn[ok]
+        if grid is not None:
+            bins[acc] = b[ok]
         pending[acc] = False
         attempt[idx[~ok]] += np.uint64(1)
         if int(attempt.max()) >= max_attempts:
             raise RuntimeError("phase-space resampling did not converge")
-    return P, W, S, attempt.astype(np.int64) + 1
+    return P, W, S, attempt.astype(np.int64) + 1, bins
 
 
 def accumulate(me2, W, S, tries, s_ident):
