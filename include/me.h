@@ -176,6 +176,49 @@ me_status xsec_step_noalloc(me_handle h, uint64_t seed, uint64_t counter_offset,
  * counterpart in the paper; a measurement aid.) */
 me_status me_step_timing(me_handle h, int32_t enable, double *ms_ps, double *ms_me);
 
+/* ---------------------------------------------------------------------------
+ * Adaptive integration: VEGAS grids (G. P. Lepage, J. Comput. Phys. 27 (1978)
+ * 192), the role of the BASES / gBASES integrator the paper uses for its cross
+ * sections (Sect. 6).  A grid holds, for each uniform variable the phase-space
+ * generator draws (2 for the two-body generator, 4 per final-state particle for
+ * RAMBO, 15 for the tt~ chain), n_bins bin edges 0 = e_0 < ... < e_N = 1,
+ * stored [dimension][N + 1].  A uniform y in bin i = floor(N y) maps to
+ * e_i + (N y - i)(e_{i+1} - e_i) and the weight is multiplied by the map's
+ * Jacobian prod_d N (e_{d,i+1} - e_{d,i}).  Host-side object; device buffers
+ * are owned by the grid.
+ * ------------------------------------------------------------------------- */
+typedef struct me_grid_s *me_grid;
+
+/* Equal bins for the generator and cuts of kin on handle h's process.
+ * n_bins: 1..256, with dimensions * n_bins <= 6144. */
+me_status me_grid_create(me_handle h, const me_kin *kin, int32_t n_bins, me_grid *out);
+me_status me_grid_info(me_grid g, int32_t *n_dims, int32_t *n_bins);
+/* Host copies of the edges, [n_dims][n_bins + 1]; set checks 0 .. 1 and increase. */
+me_status me_grid_get_edges(me_grid g, double *edges);
+me_status me_grid_set_edges(me_grid g, const double *edges);
+/* Histogram of the refinement, [n_dims][n_bins]: sum of w^2 over the accepted
+ * points of the grid steps since the last refine or clear whose uniform of that
+ * dimension fell in that bin.  Summed with atomics: equal to rounding, not
+ * bitwise, between runs. */
+me_status me_grid_get_hist(me_grid g, double *hist);
+me_status me_grid_clear_hist(me_grid g);
+/* New edges from the histogram (per dimension: neighbour smoothing of the bin
+ * sums, normalisation r_i, damping ((1 - r_i) / ln(1 / r_i))^alpha, equal shares
+ * of the damped weights per new bin; a dimension with no weight keeps its
+ * edges), then clears the histogram.  alpha > 0 (1.5 is customary). */
+me_status me_grid_refine(me_grid g, double alpha);
+/* The same refinement on host arrays, no device involved: edges and out
+ * [n_dims][n_bins + 1], hist [n_dims][n_bins]. */
+me_status me_vegas_refine_edges(const double *edges, const double *hist, int32_t n_dims, int32_t n_bins, double alpha,
+                                double *out);
+/* xsec_step with every uniform mapped through the grid and the weights
+ * carrying its Jacobian; adds the points' squared weights to the grid's
+ * histogram.  The grid must come from the same process and generator kind.
+ * One step at a time per grid (its per-chunk buffers are shared). */
+me_status xsec_step_grid(me_handle h, me_grid g, uint64_t seed, uint64_t counter_offset, int64_t n_accept,
+                         const me_kin *kin, void *stream, me_xsec_acc *acc, double *me2_out, double *momenta_out);
+void me_grid_destroy(me_grid g);
+
 /* sigma-hat = sum_w / n_try and its standard error (pb) from an accumulator. */
 me_status me_xsec_estimate(const me_xsec_acc *acc, double *sigma, double *error);
 

@@ -73,7 +73,9 @@ ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR = 0, 1, 2
 EXPORTS = ["me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
            "me_xsec_estimate", "me_info", "me_n_processes", "me_process_name", "me_destroy", "me_last_error",
            "me_server_create", "me_server_warm", "me_server_submit", "me_server_poll", "me_server_wait",
-           "me_server_get_stats", "me_server_destroy"]
+           "me_server_get_stats", "me_server_destroy", "me_grid_create", "me_grid_info", "me_grid_get_edges",
+           "me_grid_set_edges", "me_grid_get_hist", "me_grid_clear_hist", "me_grid_refine", "xsec_step_grid",
+           "me_grid_destroy", "me_vegas_refine_edges"]
 
 
 def lib_path():
@@ -114,9 +116,24 @@ def load(path=None):
     L.me_server_get_stats.argtypes = [vp, ctypes.POINTER(me_server_stats)]
     L.me_server_destroy.argtypes = [vp]
     L.me_server_destroy.restype = None
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.me_grid_create.argtypes = [vp, ctypes.POINTER(me_kin), i32, ctypes.POINTER(vp)]
+    L.me_grid_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.me_grid_get_edges.argtypes = [vp, vp]
+    L.me_grid_set_edges.argtypes = [vp, vp]
+    L.me_grid_get_hist.argtypes = [vp, vp]
+    L.me_grid_clear_hist.argtypes = [vp]
+    L.me_grid_refine.argtypes = [vp, ctypes.c_double]
+    L.xsec_step_grid.argtypes = [vp, vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc),
+                                 vp, vp]
+    L.me_grid_destroy.argtypes = [vp]
+    L.me_grid_destroy.restype = None
+    L.me_vegas_refine_edges.argtypes = [vp, vp, i32, i32, ctypes.c_double, vp]
     for fn in ("me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
                "me_xsec_estimate", "me_info", "me_server_create", "me_server_warm", "me_server_submit",
-               "me_server_poll", "me_server_wait", "me_server_get_stats"):
+               "me_server_poll", "me_server_wait", "me_server_get_stats", "me_grid_create", "me_grid_info",
+               "me_grid_get_edges", "me_grid_set_edges", "me_grid_get_hist", "me_grid_clear_hist",
+               "me_grid_refine", "xsec_step_grid", "me_vegas_refine_edges"):
         getattr(L, fn).restype = ctypes.c_int
     _LIB = L
     return L
@@ -288,3 +305,71 @@ def me_server_get_stats(s):
 
 def me_server_destroy(s):
     load().me_server_destroy(s)
+
+
+# ---------------------------------------------------------------------------
+# adaptive grids (include/me.h, me_grid_*)
+# ---------------------------------------------------------------------------
+def me_grid_create(h, kin, n_bins):
+    g = ctypes.c_void_p()
+    _check(load().me_grid_create(h, ctypes.byref(kin), n_bins, ctypes.byref(g)))
+    return g.value
+
+
+def me_grid_info(g):
+    d, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().me_grid_info(g, ctypes.byref(d), ctypes.byref(b)))
+    return d.value, b.value
+
+
+def me_grid_get_edges(g):
+    import numpy as np
+    d, b = me_grid_info(g)
+    out = np.empty((d, b + 1))
+    _check(load().me_grid_get_edges(g, out.ctypes.data))
+    return out
+
+
+def me_grid_set_edges(g, edges):
+    import numpy as np
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    _check(load().me_grid_set_edges(g, e.ctypes.data))
+
+
+def me_grid_get_hist(g):
+    import numpy as np
+    d, b = me_grid_info(g)
+    out = np.empty((d, b))
+    _check(load().me_grid_get_hist(g, out.ctypes.data))
+    return out
+
+
+def me_grid_clear_hist(g):
+    _check(load().me_grid_clear_hist(g))
+
+
+def me_grid_refine(g, alpha=1.5):
+    _check(load().me_grid_refine(g, alpha))
+
+
+def xsec_step_grid(h, g, seed, counter_offset, n_accept, kin, stream=None, acc=None, me2_out=None,
+                   momenta_out=None):
+    acc = acc if acc is not None else me_xsec_acc()
+    _check(load().xsec_step_grid(h, g, seed, counter_offset, n_accept, ctypes.byref(kin), _stream(stream),
+                                 ctypes.byref(acc), _ptr(me2_out), _ptr(momenta_out)))
+    return acc
+
+
+def me_grid_destroy(g):
+    load().me_grid_destroy(g)
+
+
+def me_vegas_refine_edges(edges, hist, alpha=1.5):
+    """Host-only refinement of edges [D, N+1] from hist [D, N] (no device)."""
+    import numpy as np
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    h = np.ascontiguousarray(hist, dtype=np.float64)
+    out = np.empty_like(e)
+    _check(load().me_vegas_refine_edges(e.ctypes.data, h.ctypes.data, e.shape[0], e.shape[1] - 1, alpha,
+                                        out.ctypes.data))
+    return out

@@ -38,7 +38,7 @@ GLUON_PROCESSES = [(5, "g g > g g g"), (6, "g g > g g g g")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", INCLUDE, "-I", CSRC, "-I", GEN]
-STATIC_SOURCES = ["me_runtime.cu", "me_server.cu"]
+STATIC_SOURCES = ["me_runtime.cu", "me_server.cu", "me_grid.cu"]
 
 
 def nvcc():

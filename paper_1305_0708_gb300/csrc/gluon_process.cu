@@ -567,6 +567,7 @@ __global__ void __launch_bounds__(Cfg<R>::THREADS, min_blocks<R>())
       sw2 = fma(w, w, sw2);
       ntries += tries_a[i];
       if (me2_out) me2_out[i] = m2;
+      if (a.vg_w) a.vg_w[i] = w;
     }
     __syncthreads();
   }

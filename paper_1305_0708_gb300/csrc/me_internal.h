@@ -28,7 +28,12 @@ struct KinDev {
   double shat_fixed;     // sqrt_s^2
   float f_ptmin2, f_sinh2, f_cdr, f_chd, f_shd, f_dr2;
   double wfactor;        // constant weight factor W_PS s_ident pb / (2 s): fixed-energy generators, else 0
+  // adaptive grid over the generator's uniforms (VEGAS); vg_bins == 0: none
+  int32_t vg_dims, vg_bins;
+  const double* vg_edges;  // device [vg_dims][vg_bins + 1]
 };
+
+constexpr int kGridMaxDims = 32, kGridMaxBins = 256;
 
 constexpr int kThreads = 128;
 
@@ -46,6 +51,8 @@ struct StepArgs {
   double* me2_out;        // optional |M|^2 per point
   double* mom_out;        // optional momenta, SoA [n_ext][4] with stride out_stride
   int64_t out_stride;
+  uint8_t* vg_idx;        // grid steps: [vg_dims][m] bin of every uniform of each accepted point
+  double* vg_w;           // grid steps: [m] weight of each point
 };
 
 struct ProcessDesc {

@@ -317,6 +317,69 @@ me_status noalloc_scratch(int device, NoAllocScratch** out) {
 
 }  // namespace
 
+namespace me {
+namespace rt {
+
+me_status run_step(me_handle h, KinDev& k, uint64_t seed, uint64_t counter_offset, int64_t n_accept, void* stream,
+                   me_xsec_acc* acc, double* me2_out, double* momenta_out, GridHook* grid) {
+  me_status st;
+  if (n_accept == 0) return ME_OK;
+  std::lock_guard<std::mutex> lock(h->mu);
+  const int64_t m0 = std::min<int64_t>(n_accept, kChunk);
+  const int64_t nchunks = (n_accept + kChunk - 1) / kChunk;
+  const int grid_me = grid_for(h, m0);
+  const int grid_ps = grid_ps_for(h, m0);
+  if ((st = ensure_workspace(h, (int)(grid_me * nchunks))) != ME_OK) return st;
+  if ((st = ensure_points_ws(h, m0)) != ME_OK) return st;
+  if (grid && (st = grid->ensure(m0)) != ME_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    const int64_t first = c * kChunk;
+    const int64_t m = std::min<int64_t>(kChunk, n_accept - first);
+    if (h->timing) cudaEventRecord(h->ev[0], s);
+    me::StepArgs a{seed, counter_offset + (uint64_t)first, m, h->d_ws, h->d_status,
+                   h->d_partials + 3 * (size_t)grid_me * c, grid_me, me2_out ? me2_out + first : nullptr,
+                   momenta_out ? momenta_out + first : nullptr, n_accept,
+                   grid ? grid->idx : nullptr, grid ? grid->w : nullptr};
+    e = h->desc->launch_step(h->prec, &k, &a, h->cvals.data(), s, grid_ps, grid_me, h->timing ? h->ev[1] : nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "xsec_step launch");
+    if (grid && (e = launch_vg_hist(m, grid->dims, grid->bins, grid->idx, grid->w, grid->hist, s)) != cudaSuccess)
+      return cuda_fail(e, "grid histogram");
+    if (h->timing) {
+      cudaEventRecord(h->ev[2], s);
+      if ((e = cudaEventSynchronize(h->ev[2])) != cudaSuccess) return cuda_fail(e, "xsec_step timing");
+      float a = 0, b = 0;
+      cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+      cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+      h->t_ps += a;
+      h->t_me += b;
+    }
+  }
+  k_reduce_partials<<<1, 256, 0, s>>>(h->d_partials, (int)(grid_me * nchunks), h->d_acc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "xsec_step reduce");
+  if ((e = cudaMemcpyAsync(h->h_acc, h->d_acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "xsec_step copy");
+  int status = 0;
+  if ((e = cudaMemcpyAsync(&h->h_acc[3], h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "xsec_step copy");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "xsec_step sync");
+  std::memcpy(&status, &h->h_acc[3], sizeof(int));
+  if (status) {
+    cudaMemsetAsync(h->d_status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return fail(ME_ERR_TIMEOUT, "xsec_step: a point exhausted its phase-space redraws");
+  }
+  acc->sum_w += h->h_acc[0];
+  acc->sum_w2 += h->h_acc[1];
+  acc->n_acc += n_accept;
+  acc->n_try += (int64_t)llround(h->h_acc[2]);
+  return ME_OK;
+}
+
+}  // namespace rt
+}  // namespace me
+
 extern "C" {
 
 int32_t me_n_processes(void) { return me::registry_size(); }
@@ -393,54 +456,7 @@ me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t
   if (n_accept < 0) return fail(ME_ERR_ARG, "xsec_step: n_accept < 0");
   me::KinDev k;
   if ((st = make_kin(h, kin, k)) != ME_OK) return st;
-  if (n_accept == 0) return ME_OK;
-  std::lock_guard<std::mutex> lock(h->mu);
-  const int64_t m0 = std::min<int64_t>(n_accept, kChunk);
-  const int64_t nchunks = (n_accept + kChunk - 1) / kChunk;
-  const int grid_me = grid_for(h, m0);
-  const int grid_ps = grid_ps_for(h, m0);
-  if ((st = ensure_workspace(h, (int)(grid_me * nchunks))) != ME_OK) return st;
-  if ((st = ensure_points_ws(h, m0)) != ME_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e;
-  for (int64_t c = 0; c < nchunks; ++c) {
-    const int64_t first = c * kChunk;
-    const int64_t m = std::min<int64_t>(kChunk, n_accept - first);
-    if (h->timing) cudaEventRecord(h->ev[0], s);
-    me::StepArgs a{seed, counter_offset + (uint64_t)first, m, h->d_ws, h->d_status,
-                   h->d_partials + 3 * (size_t)grid_me * c, grid_me, me2_out ? me2_out + first : nullptr,
-                   momenta_out ? momenta_out + first : nullptr, n_accept};
-    e = h->desc->launch_step(h->prec, &k, &a, h->cvals.data(), s, grid_ps, grid_me, h->timing ? h->ev[1] : nullptr);
-    if (e != cudaSuccess) return cuda_fail(e, "xsec_step launch");
-    if (h->timing) {
-      cudaEventRecord(h->ev[2], s);
-      if ((e = cudaEventSynchronize(h->ev[2])) != cudaSuccess) return cuda_fail(e, "xsec_step timing");
-      float a = 0, b = 0;
-      cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
-      cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
-      h->t_ps += a;
-      h->t_me += b;
-    }
-  }
-  k_reduce_partials<<<1, 256, 0, s>>>(h->d_partials, (int)(grid_me * nchunks), h->d_acc);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "xsec_step reduce");
-  if ((e = cudaMemcpyAsync(h->h_acc, h->d_acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return cuda_fail(e, "xsec_step copy");
-  int status = 0;
-  if ((e = cudaMemcpyAsync(&h->h_acc[3], h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return cuda_fail(e, "xsec_step copy");
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "xsec_step sync");
-  std::memcpy(&status, &h->h_acc[3], sizeof(int));
-  if (status) {
-    cudaMemsetAsync(h->d_status, 0, sizeof(int), s);
-    cudaStreamSynchronize(s);
-    return fail(ME_ERR_TIMEOUT, "xsec_step: a point exhausted its phase-space redraws");
-  }
-  acc->sum_w += h->h_acc[0];
-  acc->sum_w2 += h->h_acc[1];
-  acc->n_acc += n_accept;
-  acc->n_try += (int64_t)llround(h->h_acc[2]);
-  return ME_OK;
+  return me::rt::run_step(h, k, seed, counter_offset, n_accept, stream, acc, me2_out, momenta_out, nullptr);
 }
 
 me_status xsec_step_noalloc(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept,

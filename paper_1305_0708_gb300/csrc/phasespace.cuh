@@ -52,6 +52,37 @@ __host__ __device__ __forceinline__ double to_unit(uint64_t x) {
   return ((double)(x >> 11) + 0.5) * 0x1p-53;
 }
 
+// ---------------------------------------------------------------------------
+// Adaptive grid (VEGAS, Lepage 1978) over the generator's uniforms: in
+// dimension d a uniform y lies in bin i = floor(N y) and maps to
+// x = e_i + (N y - i)(e_{i+1} - e_i); the Jacobian N (e_{i+1} - e_i) multiplies
+// the weight and the bin is recorded for the histogram of the refinement.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double vg_map(const KinDev& kin, int d, double y, double& jac, uint8_t* bins) {
+  const int N = kin.vg_bins;
+  const double t = y * N;
+  int i = (int)t;
+  i = i < N - 1 ? i : N - 1;
+  const double* e = kin.vg_edges + (size_t)d * (N + 1);
+  const double lo = e[i], w = e[i + 1] - lo;
+  jac *= N * w;
+  if (bins) bins[d] = (uint8_t)i;
+  return lo + (t - i) * w;
+}
+
+__host__ __device__ __forceinline__ df vg_map_df(const KinDev& kin, int d, df y, df& jac, uint8_t* bins) {
+  const int N = kin.vg_bins;
+  const df t = y * (float)N;  // N <= 256: exact in FP32
+  int i = (int)floorf(t.hi);
+  if ((float)i == t.hi && t.lo < 0.0f) --i;
+  i = i < 0 ? 0 : (i < N - 1 ? i : N - 1);
+  const double* e = kin.vg_edges + (size_t)d * (N + 1);
+  const df lo = from_double(e[i]), w = from_double(e[i + 1]) - lo;
+  jac = jac * (w * (float)N);
+  if (bins) bins[d] = (uint8_t)i;
+  return lo + (t + (float)(-i)) * w;
+}
+
 // uniforms u[4*nb] for (event, attempt)
 template <int NB>
 __host__ __device__ __forceinline__ void draw_uniforms(uint64_t seed, uint64_t event, uint64_t attempt, double (&u)[4 * NB]) {
@@ -341,21 +372,33 @@ __host__ __device__ __forceinline__ bool pass_cuts(const KinDev& kin, const doub
 // one draw (attempt `att`) for `event`: false if outside the kinematic limits or the cuts
 template <int NEXT>
 __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t seed, uint64_t event, int att,
-                                                    double (&p)[NEXT][4], double& wps, double& shat) {
+                                                    double (&p)[NEXT][4], double& wps, double& shat,
+                                                    uint8_t* bins = nullptr) {
   bool ok;
+  double jac = 1.0;
   if (kin.kind == ME_PS_TWO_BODY) {
     double u[4];
     draw_uniforms<1>(seed, event, (uint64_t)att, u);
+#pragma unroll
+    for (int d = 0; d < 4; ++d)  // compile-time indices keep u in registers
+      if (d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
     ok = gen_two_body<NEXT>(kin, u, p, wps, shat);
   } else if (kin.kind == ME_PS_RAMBO) {
     double u[4 * (NEXT - 2)];
     draw_uniforms<NEXT - 2>(seed, event, (uint64_t)att, u);
+#pragma unroll
+    for (int d = 0; d < 4 * (NEXT - 2); ++d)
+      if (d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
     ok = gen_rambo<NEXT>(kin, u, p, wps, shat);
   } else {
     double u[16];
     draw_uniforms<4>(seed, event, (uint64_t)att, u);
+#pragma unroll
+    for (int d = 0; d < 16; ++d)
+      if (d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
     ok = gen_ttbar<NEXT>(kin, u, p, wps, shat);
   }
+  wps *= jac;
   return ok && pass_cuts<NEXT>(kin, p);
 }
 
@@ -366,7 +409,7 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
 // ---------------------------------------------------------------------------
 template <int NEXT>
 __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
-                                         df (&p)[NEXT][4]) {
+                                         df (&p)[NEXT][4], df& jac, uint8_t* bins = nullptr) {
   constexpr int NF = NEXT - 2;
   const df w = df{kin.sqrt_s_f[0], kin.sqrt_s_f[1]};
   const df hw = df{w.hi * 0.5f, w.lo * 0.5f};
@@ -378,7 +421,13 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
   for (int k = 0; k < NF; ++k) {
     uint64_t o[4];
     Philox::block(event, (uint64_t)att, (uint64_t)k, 0ull, seed, 0ull, o);
-    const df u0 = unit_df(o[0]), u1 = unit_df(o[1]), u2 = unit_df(o[2]), u3 = unit_df(o[3]);
+    df u0 = unit_df(o[0]), u1 = unit_df(o[1]), u2 = unit_df(o[2]), u3 = unit_df(o[3]);
+    if (kin.vg_bins) {
+      u0 = vg_map_df(kin, 4 * k + 0, u0, jac, bins);
+      u1 = vg_map_df(kin, 4 * k + 1, u1, jac, bins);
+      u2 = vg_map_df(kin, 4 * k + 2, u2, jac, bins);
+      u3 = vg_map_df(kin, 4 * k + 3, u3, jac, bins);
+    }
     const df c = df{u0.hi * 2.0f, u0.lo * 2.0f} + (-1.0f);
     const df sn = df_sqrt((dfs(1.0f) - c) * (dfs(1.0f) + c));
     df sp, cp;
@@ -594,7 +643,8 @@ __host__ __device__ __forceinline__ df two_body_k(df rs, df m1, df m2) {
 
 template <int NEXT>
 __host__ __device__ __forceinline__ bool ttbar_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
-                                                  df (&p)[NEXT][4], double& wps, double& shat) {
+                                                  df (&p)[NEXT][4], double& wps, double& shat, df& jac,
+                                                  uint8_t* bins = nullptr) {
   if constexpr (NEXT != 8) {
     return false;
   } else {
@@ -608,6 +658,9 @@ __host__ __device__ __forceinline__ bool ttbar_df(const KinDev& kin, uint64_t se
       u[4 * j + 2] = unit_df(o[2]);
       u[4 * j + 3] = unit_df(o[3]);
     }
+#pragma unroll
+    for (int d = 0; d < 16; ++d)
+      if (d < kin.vg_dims) u[d] = vg_map_df(kin, d, u[d], jac, bins);
     const df rmin = from_double(kin.sqrt_s_min);
     const df rs = rmin + (from_double(kin.sqrt_s_max) - rmin) * u[0];
     df jt, jtb, jwp, jwm;
@@ -677,17 +730,24 @@ __host__ __device__ __forceinline__ bool ttbar_df(const KinDev& kin, uint64_t se
 // rescaling) or tt~ chain; the two-body generator in FP64 split into double-floats
 template <int NEXT>
 __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
-                                              df (&p)[NEXT][4], double& wps, double& shat) {
+                                              df (&p)[NEXT][4], double& wps, double& shat,
+                                              uint8_t* bins = nullptr) {
+  df jac = dfs(1.0f);
   if (kin.kind == ME_PS_RAMBO) {
-    rambo_df<NEXT>(kin, seed, event, att, p);
+    rambo_df<NEXT>(kin, seed, event, att, p, jac, bins);
     wps = kin.rambo_volume;
     if (kin.massive) wps *= to_double(massive_rescale_df<NEXT>(kin, p));
+    if (kin.vg_bins) wps *= to_double(jac);
     shat = kin.shat_fixed;
     return pass_cuts_df<NEXT>(kin, p);
   }
-  if (kin.kind == ME_PS_TTBAR) return ttbar_df<NEXT>(kin, seed, event, att, p, wps, shat) && pass_cuts_df<NEXT>(kin, p);
+  if (kin.kind == ME_PS_TTBAR) {
+    const bool ok = ttbar_df<NEXT>(kin, seed, event, att, p, wps, shat, jac, bins);
+    if (kin.vg_bins) wps *= to_double(jac);
+    return ok && pass_cuts_df<NEXT>(kin, p);
+  }
   double pd[NEXT][4];
-  const bool ok = draw_point<NEXT>(kin, seed, event, att, pd, wps, shat);
+  const bool ok = draw_point<NEXT>(kin, seed, event, att, pd, wps, shat, bins);
   if (ok) {
 #pragma unroll
     for (int k = 0; k < NEXT; ++k) {

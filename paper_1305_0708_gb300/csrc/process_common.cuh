@@ -304,9 +304,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
     if (ev >= 0) {
       double wps = 0.0, shat = 1.0;
       bool ok;
+      uint8_t vbins[kGridMaxDims];  // grid steps: bin of every mapped uniform
+      uint8_t* vb = kin.vg_bins ? vbins : nullptr;
       if constexpr (MIXED) {
         df q[NEXT][4];
-        ok = draw_point_df<NEXT>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat);
+        ok = draw_point_df<NEXT>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat, vb);
         if (ok) {
 #pragma unroll
           for (int k = 0; k < NEXT; ++k) {
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
         }
       } else {
         double q[NEXT][4];
-        ok = draw_point<NEXT>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat);
+        ok = draw_point<NEXT>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat, vb);
         if (ok) {
 #pragma unroll
           for (int k = 0; k < NEXT; ++k) {
@@ -328,6 +330,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
           }
         }
       }
+      if (a.vg_idx && (ok || att + 1 >= kin.max_attempts))
+        for (int d = 0; d < kin.vg_dims; ++d) a.vg_idx[(int64_t)d * m + ev] = ok ? vbins[d] : (uint8_t)0;
       if (ok) {
         if constexpr (MIXED) {
           // weight factor w_PS s_ident / (2 s) GeV^2->pb as a double-float pair in the weight slot
@@ -400,6 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, StepArgs a, PrmT<P,
       sw2f = sw2f + two_prod(w, w);
       ntries += tries_a[i];
       if (me2_out) me2_out[i] = (double)m2f;
+      if (a.vg_w) a.vg_w[i] = (double)w;
     } else {
       const double wps = wps_a[i], shat = shat_a[i];
       const bool ok = wps > 0.0;
@@ -424,6 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_me(KinDev kin, StepArgs a, PrmT<P,
       sw2 = fma(w, w, sw2);
       ntries += tries_a[i];
       if (me2_out) me2_out[i] = m2;
+      if (a.vg_w) a.vg_w[i] = w;
     }
   }
   if constexpr (MIXED) {
@@ -531,6 +537,7 @@ __global__ void __launch_bounds__(kThreads) k_me_mx(KinDev kin, StepArgs a, PrmT
       sw2f = sw2f + two_prod(w, w);
       ntries += __float_as_int(src[(8 * NEXT + 1) * kThreads]);
       if (me2_out) me2_out[i] = (double)m2f;
+      if (a.vg_w) a.vg_w[i] = (double)w;
     }
     b ^= 1;
   }

@@ -47,5 +47,21 @@ size_t ws_bytes(int n_ext, int64_t m);
 // fixed-order sum of nblocks partials (3 doubles each) into acc[0..2]
 cudaError_t launch_reduce(const double* partials, int nblocks, double* acc, cudaStream_t s);
 
+// the adaptive-grid part of a Monte Carlo step: per-chunk bins and weights, the histogram
+struct GridHook {
+  int dims = 0, bins = 0;
+  uint8_t* idx = nullptr;  // [dims][chunk]
+  double* w = nullptr;     // [chunk]
+  double* hist = nullptr;  // [dims][bins]
+  virtual me_status ensure(int64_t chunk) = 0;  // buffers for chunks of up to `chunk` points
+  virtual ~GridHook() = default;
+};
+// adds sum of w^2 per (dimension, bin) of m points to hist (me_grid.cu)
+cudaError_t launch_vg_hist(int64_t m, int dims, int bins, const uint8_t* idx, const double* w, double* hist,
+                           cudaStream_t s);
+// one Monte Carlo step of n_accept points in chunks (xsec_step, and with a grid xsec_step_grid)
+me_status run_step(me_handle h, KinDev& k, uint64_t seed, uint64_t counter_offset, int64_t n_accept, void* stream,
+                   me_xsec_acc* acc, double* me2_out, double* momenta_out, GridHook* grid);
+
 }  // namespace rt
 }  // namespace me

@@ -103,3 +103,24 @@ def test_server_argument_errors_without_device_work(lib):
     t = ctypes.c_int64()
     assert lib.me_server_submit(None, None, ctypes.byref(t)) == -1
     assert lib.me_server_wait(None, 1, 0.0, None, None, None) == -1
+
+
+def test_library_vegas_refinement_matches_the_oracle(lib):
+    """The library's host refinement of an adaptive grid against oracle.vegas.refine (no GPU)."""
+    import numpy as np
+    from oracle import vegas
+    from paper_1305_0708_gb300 import binding as B
+    rng = np.random.default_rng(11)
+    for D, N, alpha in ((1, 8, 1.0), (3, 16, 1.5), (15, 50, 0.7)):
+        w = rng.uniform(0.2, 1.0, size=(D, N))
+        e = np.concatenate([np.zeros((D, 1)), np.cumsum(w, axis=1)], axis=1)
+        e /= e[:, -1:]
+        h = rng.random((D, N)) ** 3
+        h[0, : N // 3] = 0.0
+        if D > 2:
+            h[2] = 0.0
+        got = B.me_vegas_refine_edges(e, h, alpha)
+        ref = vegas.refine(e, h, alpha)
+        assert np.abs(got - ref).max() < 1e-13
+    with pytest.raises(B.MeError):
+        B.me_vegas_refine_edges(e, h, -1.0)
