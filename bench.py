@@ -374,6 +374,43 @@ def serving_mix(B, rates=((10, 48), (100, 128), (1000, 256)), baseline_budget_s=
     return out
 
 
+def vegas_leg(B, torch, dev, stream, keys=("uux_epem", "gg_ttx_dilep", "udx_epvegg"), rounds=5, n_round=1 << 18, n_final=1 << 20):
+    """Adaptive grids: `rounds` refinements of n_round-point grid steps, then sigma-hat on n_final
+    points with the adapted grid against uniform sampling on the same points (mixed precision)."""
+    from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args
+    out = {}
+    for key in keys:
+        w = WORKLOADS[key]
+        kin = B.make_kin(**kin_args(w))
+        h = B.me_create(w["process"], None, B.ME_MIXED)
+        g = B.me_grid_create(h, kin, 64)
+        t0 = time.perf_counter()
+        for r in range(rounds):
+            B.xsec_step_grid(h, g, w["seed"], r * n_round, n_round, kin, stream)
+            B.me_grid_refine(g, 1.5)
+        t_adapt = time.perf_counter() - t0
+        off = 1 << 36
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        acc = B.xsec_step_grid(h, g, w["seed"], off, n_final, kin, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_g = ev0.elapsed_time(ev1)
+        ev0.record(stream)
+        acc0 = B.xsec_step(h, w["seed"], off, n_final, kin, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_0 = ev0.elapsed_time(ev1)
+        (s_g, e_g), (s_0, e_0) = B.me_xsec_estimate(acc), B.me_xsec_estimate(acc0)
+        out[key] = {"sigma_pb_adapted": s_g, "error_pb_adapted": e_g, "sigma_pb_uniform": s_0,
+                    "error_pb_uniform": e_0, "error_ratio": e_g / e_0, "points": n_final,
+                    "rounds": rounds, "points_per_round": n_round, "bins": 64, "adapt_s": t_adapt,
+                    "step_ms_adapted": ms_g, "step_ms_uniform": ms_0}
+        B.me_grid_destroy(g)
+        B.me_destroy(h)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,6 +423,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-table", action="store_true", help="skip the per-process table")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix leg")
+    ap.add_argument("--no-vegas", action="store_true", help="skip the adaptive-grid leg")
     ap.add_argument("--points", type=int, default=0,
                     help="points per step instead of the workload's own count (small cases for profiling)")
     args = ap.parse_args()
@@ -540,6 +578,10 @@ def main():
     if not args.no_serving and world == 1:
         serving = serving_mix(B)
 
+    vegas = None
+    if not args.no_vegas and world == 1:
+        vegas = vegas_leg(B, torch, dev, stream)
+
     table = None
     if not args.no_table:
         table = per_process_table(B, torch, dev, stream, flush, offset0, 2, 3)
@@ -583,6 +625,7 @@ def main():
             "kernels": kernels,
             "per_process": table,
             "serving": serving,
+            "vegas": vegas,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
