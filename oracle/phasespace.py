@@ -178,6 +178,52 @@ def rambo_massive(w, masses, u, iterations=40):
     return out, wt
 
 
+def rambo_massive_events(w, masses, u, iterations=40):
+    """rambo_massive with per-event masses [N, n] (same Newton solve and weight, row by row)."""
+    m = np.asarray(masses, dtype=float)
+    N, n = m.shape
+    p, wt0 = rambo_massless(w, n, u)
+    E0 = p[:, :, 0]
+    xi = np.sqrt(np.maximum(1.0 - (m.sum(axis=1) / w) ** 2, 0.0))
+    for _ in range(iterations):
+        Ek = np.sqrt(m ** 2 + (xi[:, None] * E0) ** 2)
+        f = Ek.sum(axis=1) - w
+        df = (xi[:, None] * E0 ** 2 / Ek).sum(axis=1)
+        xi = xi - f / df
+    Ek = np.sqrt(m ** 2 + (xi[:, None] * E0) ** 2)
+    out = np.empty_like(p)
+    out[:, :, 0] = Ek
+    out[:, :, 1:] = xi[:, None, None] * p[:, :, 1:]
+    absk = xi[:, None] * E0
+    wt = wt0 * xi ** (2 * n - 3) * np.prod(absk / Ek, axis=1) * w / (absk ** 2 / Ek).sum(axis=1)
+    return out, wt
+
+
+def rambo_resonance(w, nf, m, width, u):
+    """nf massless final particles, the first two the decay products of a resonance of mass m and
+    width `width` (App. A.2): dPhi_nf = dPhi_{nf-1}(R, 3..nf) ds/(2 pi) dPhi_2(R -> 1 2), with
+    s = p_R^2 Breit-Wigner mapped (Eq. 16 range, bw_sample) and an isotropic decay at rest.
+    u [N, 4 nf]: 4 RAMBO uniforms per particle of (R, 3, ..., nf), then theta, then the decay
+    direction (cos = 2u - 1, phi = 2 pi u) of particle 1.
+    Returns (pf [N, nf, 4] in the order 1, 2, 3, ..., nf; weight [N]; ok [N])."""
+    N = u.shape[0]
+    k = 4 * (nf - 1)
+    s, jac = bw_sample(m, width, u[:, k])
+    M = np.sqrt(np.maximum(s, 0.0))
+    ok = (s > 0) & (M < w)
+    Mr = np.where(ok, M, 0.5 * w)  # rejected rows get a harmless mass; their weight is unused
+    masses = np.zeros((N, nf - 1))
+    masses[:, 0] = Mr
+    q, wt = rambo_massive_events(w, masses, u[:, :k])
+    p1s, p2s, pabs = _iso_pair(Mr, np.zeros(N), np.zeros(N), 2.0 * u[:, k + 1] - 1.0, 2.0 * math.pi * u[:, k + 2])
+    pf = np.empty((N, nf, 4))
+    pf[:, 0] = _boost_from_rest(p1s, q[:, 0], Mr)
+    pf[:, 1] = _boost_from_rest(p2s, q[:, 0], Mr)
+    pf[:, 2:] = q[:, 1:]
+    wt = wt * jac * pabs / (4.0 * math.pi * Mr)
+    return pf, wt, ok
+
+
 def _lam(a, b, c):
     return a * a + b * b + c * c - 2 * a * b - 2 * b * c - 2 * c * a
 

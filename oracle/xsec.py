@@ -41,13 +41,21 @@ def draw(kin, par, u):
         return P, wt, np.ones(N, dtype=bool), np.full(N, w * w)
     if kind == "ttbar":
         return ps.ttbar_dilepton(u, par, kin["sqrt_s_range"])
+    if kind == "rambo_bw":
+        w = kin["sqrt_s"]
+        nf = kin["n_final"]
+        pf, wt, ok = ps.rambo_resonance(w, nf, kin["res_mass"], kin["res_width"], u)
+        P = np.zeros((N, nf + 2, 4))
+        P[:, 0], P[:, 1] = ps.incoming(w, N)
+        P[:, 2:] = pf
+        return P, wt, ok, np.full(N, w * w)
     raise ValueError(kind)
 
 
 def nblocks(kin):
     if kin["kind"] == "2to2":
         return 1
-    if kin["kind"] == "rambo":
+    if kin["kind"] in ("rambo", "rambo_bw"):
         return kin["n_final"]
     return 4
 
@@ -58,6 +66,8 @@ def grid_dims(kin):
         return 2
     if kin["kind"] == "rambo":
         return 4 * kin["n_final"]
+    if kin["kind"] == "rambo_bw":
+        return 4 * kin["n_final"] - 1
     return 15
 
 
