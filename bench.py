@@ -374,13 +374,13 @@ def serving_mix(B, rates=((10, 48), (100, 128), (1000, 256)), baseline_budget_s=
     return out
 
 
-def vegas_leg(B, torch, dev, stream, keys=("uux_epem", "gg_ttx_dilep", "udx_epvegg"), rounds=5, n_round=1 << 18, n_final=1 << 20):
+def vegas_leg(B, torch, dev, stream, keys=("uux_epem", "gg_ttx_dilep", "udx_epvegg", "udx_epvegg_bw"), rounds=5, n_round=1 << 18, n_final=1 << 20):
     """Adaptive grids: `rounds` refinements of n_round-point grid steps, then sigma-hat on n_final
     points with the adapted grid against uniform sampling on the same points (mixed precision)."""
-    from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args
+    from paper_1305_0708_gb300.workloads import VARIANTS, WORKLOADS, kin_args
     out = {}
     for key in keys:
-        w = WORKLOADS[key]
+        w = WORKLOADS[key] if key in WORKLOADS else VARIANTS[key]
         kin = B.make_kin(**kin_args(w))
         h = B.me_create(w["process"], None, B.ME_MIXED)
         g = B.me_grid_create(h, kin, 64)

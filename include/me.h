@@ -69,9 +69,13 @@ typedef struct {
 typedef enum {
   ME_PS_TWO_BODY = 0,  /* 2 -> 2 at fixed sqrt_s, cos(theta) and phi uniform (massless) */
   ME_PS_RAMBO = 1,     /* flat n-body (RAMBO) at fixed sqrt_s; mass[] per leg, 0 = massless */
-  ME_PS_TTBAR = 2      /* g g > t t~ > (b e+ ve)(b~ e- ve~): sqrt_s uniform in [sqrt_s_min,
+  ME_PS_TTBAR = 2,     /* g g > t t~ > (b e+ ve)(b~ e- ve~): sqrt_s uniform in [sqrt_s_min,
                           sqrt_s_max], Breit-Wigner t, t~, W+, W- (Eq. 16, App. A.2), isotropic
                           two-body decays in every rest frame */
+  ME_PS_RAMBO_BW = 3   /* massless final state at fixed sqrt_s whose legs 2 and 3 come from a
+                          resonance (res_mass, res_width): dPhi_n = dPhi_{n-1} ds/(2 pi) dPhi_2
+                          (App. A.2), s Breit-Wigner mapped over the Eq. 16 range, RAMBO for the
+                          resonance and legs 4.., isotropic decay at rest */
 } me_ps_kind;
 
 typedef struct {
@@ -86,6 +90,7 @@ typedef struct {
   double eta_max;          /* |eta| < eta_max (pseudorapidity) */
   double dr_min;           /* Delta R > dr_min for every pair of cut legs */
   double s_ident;          /* identical-particle factor 1/k! applied to the weights */
+  double res_mass, res_width;  /* resonance of ME_PS_RAMBO_BW (GeV) */
 } me_kin;
 
 /* Monte Carlo accumulator (host).  xsec_step adds to it. */

@@ -29,7 +29,8 @@ class me_kin(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("max_attempts", ctypes.c_int32), ("sqrt_s", ctypes.c_double),
                 ("sqrt_s_min", ctypes.c_double), ("sqrt_s_max", ctypes.c_double), ("mass", ctypes.c_double * 16),
                 ("n_cut_legs", ctypes.c_int32), ("cut_legs", ctypes.c_int32 * 8), ("pt_min", ctypes.c_double),
-                ("eta_max", ctypes.c_double), ("dr_min", ctypes.c_double), ("s_ident", ctypes.c_double)]
+                ("eta_max", ctypes.c_double), ("dr_min", ctypes.c_double), ("s_ident", ctypes.c_double),
+                ("res_mass", ctypes.c_double), ("res_width", ctypes.c_double)]
 
 
 class me_xsec_acc(ctypes.Structure):
@@ -68,7 +69,7 @@ class me_server_stats(ctypes.Structure):
 
 
 ME_FP64, ME_MIXED = 0, 1
-ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR = 0, 1, 2
+ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR, ME_PS_RAMBO_BW = 0, 1, 2, 3
 
 EXPORTS = ["me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
            "me_xsec_estimate", "me_info", "me_n_processes", "me_process_name", "me_destroy", "me_last_error",
@@ -169,7 +170,7 @@ def make_params(**kw):
 
 
 def make_kin(kind, sqrt_s=0.0, sqrt_s_range=(0.0, 0.0), masses=(), cut_legs=(), pt_min=0.0, eta_max=0.0,
-             dr_min=0.0, s_ident=1.0, max_attempts=0):
+             dr_min=0.0, s_ident=1.0, max_attempts=0, res_mass=0.0, res_width=0.0):
     k = me_kin()
     k.kind = kind
     k.max_attempts = max_attempts
@@ -181,6 +182,7 @@ def make_kin(kind, sqrt_s=0.0, sqrt_s_range=(0.0, 0.0), masses=(), cut_legs=(), 
     for i, l in enumerate(cut_legs):
         k.cut_legs[i] = l
     k.pt_min, k.eta_max, k.dr_min, k.s_ident = pt_min, eta_max, dr_min, s_ident
+    k.res_mass, k.res_width = res_mass, res_width
     return k
 
 

@@ -26,6 +26,7 @@ namespace {
 int grid_dims_for(int kind, int n_ext) {
   if (kind == ME_PS_TWO_BODY) return 2;
   if (kind == ME_PS_RAMBO) return 4 * (n_ext - 2);
+  if (kind == ME_PS_RAMBO_BW) return 4 * (n_ext - 2) - 1;
   return 15;
 }
 

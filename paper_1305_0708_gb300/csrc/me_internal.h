@@ -20,7 +20,7 @@ struct KinDev {
   double rambo_volume;   // massless n-body volume with the (2 pi) factors of Eq. 5
   double sinh2_eta_max;  // sinh(eta_max)^2
   double cos_dr, cosh_dr, sinh_dr;
-  double bw_mass[2], bw_width[2], bw_t0[2], bw_t1[2];  // top, W
+  double bw_mass[2], bw_width[2], bw_t0[2], bw_t1[2];  // top, W (ttbar); [0] the resonance of RAMBO_BW
   int32_t massive;       // any final-state mass (RAMBO)
   uint32_t cut_mask;     // bit k set: leg k is cut
   // FP32 / double-float copies formed on the host (no FP64 arithmetic per draw)

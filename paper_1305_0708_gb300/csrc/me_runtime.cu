@@ -156,11 +156,15 @@ int grid_for(me_handle h, int64_t n) {
 }
 
 me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
-  if (kin->kind < ME_PS_TWO_BODY || kin->kind > ME_PS_TTBAR) return fail(ME_ERR_ARG, "kin->kind: unknown generator");
+  if (kin->kind < ME_PS_TWO_BODY || kin->kind > ME_PS_RAMBO_BW) return fail(ME_ERR_ARG, "kin->kind: unknown generator");
   const int next = h->desc->n_ext;
   if (kin->kind == ME_PS_TWO_BODY && next != 4) return fail(ME_ERR_ARG, "two-body generator needs 4 legs");
   if (kin->kind == ME_PS_TTBAR && next != 8) return fail(ME_ERR_ARG, "ttbar generator needs 8 legs");
   if (kin->kind == ME_PS_RAMBO && (next < 4 || next > 10)) return fail(ME_ERR_ARG, "RAMBO supports 2 to 8 final legs");
+  if (kin->kind == ME_PS_RAMBO_BW && (next < 5 || next > 10))
+    return fail(ME_ERR_ARG, "resonance RAMBO supports 3 to 8 final legs");
+  if (kin->kind == ME_PS_RAMBO_BW && !(kin->res_mass > 0 && kin->res_width > 0 && kin->res_mass < kin->sqrt_s))
+    return fail(ME_ERR_ARG, "kin: resonance mass and width must be positive, mass below sqrt_s");
   if (kin->n_cut_legs < 0 || kin->n_cut_legs > 8) return fail(ME_ERR_ARG, "kin->n_cut_legs out of range");
   for (int i = 0; i < kin->n_cut_legs; ++i)
     if (kin->cut_legs[i] < 2 || kin->cut_legs[i] >= next) return fail(ME_ERR_ARG, "kin->cut_legs: not a final-state leg");
@@ -188,7 +192,8 @@ me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
   k.eta_max = kin->eta_max;
   k.dr_min = kin->dr_min;
   k.s_ident = kin->s_ident > 0 ? kin->s_ident : 1.0;
-  const int nf = next - 2;
+  // RAMBO volume of the particles RAMBO draws (the resonance counts as one for RAMBO_BW)
+  const int nf = kin->kind == ME_PS_RAMBO_BW ? next - 3 : next - 2;
   double fact = 1;
   for (int i = 2; i <= nf - 1; ++i) fact *= i;  // (n-1)!
   double fact2 = 1;
@@ -205,6 +210,10 @@ me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
   k.bw_width[0] = p.wt;
   k.bw_mass[1] = p.mW;
   k.bw_width[1] = p.wW;
+  if (kin->kind == ME_PS_RAMBO_BW) {
+    k.bw_mass[0] = kin->res_mass;
+    k.bw_width[0] = kin->res_width;
+  }
   for (int r = 0; r < 2; ++r) {
     const double x = std::min(20.0, k.bw_mass[r] / k.bw_width[r]);
     k.bw_t0[r] = -std::atan(x);

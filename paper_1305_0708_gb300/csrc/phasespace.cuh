@@ -151,21 +151,18 @@ __host__ __device__ __forceinline__ bool gen_two_body(const KinDev& kin, const d
   return true;
 }
 
-// RAMBO: massless momenta, then (if any mass) the Kleiss-Stirling-Ellis rescaling
-template <int NEXT>
-__host__ __device__ __forceinline__ bool gen_rambo(const KinDev& kin, const double* u, double (&p)[NEXT][4],
-                                                   double& wps, double& shat) {
-  constexpr int NF = NEXT - 2;
-  const double w = kin.sqrt_s;
-  beams<NEXT>(p, w);
+// RAMBO (Kleiss, Stirling, Ellis 1986): NF massless momenta at total energy w
+// from 4 NF uniforms, in q[0..NF-1]
+template <int NF>
+__host__ __device__ __forceinline__ void rambo_massless_core(double w, const double* u, double (*q)[4]) {
   double Q0 = 0, Q1 = 0, Q2 = 0, Q3 = 0;
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     double nx, ny, nz;
     direction(u[4 * k + 0], u[4 * k + 1], nx, ny, nz);
     const double q0 = -log(u[4 * k + 2] * u[4 * k + 3]);
-    set4(p[2 + k], q0, q0 * nx, q0 * ny, q0 * nz);
-    Q0 += q0; Q1 += p[2 + k][1]; Q2 += p[2 + k][2]; Q3 += p[2 + k][3];
+    set4(q[k], q0, q0 * nx, q0 * ny, q0 * nz);
+    Q0 += q0; Q1 += q[k][1]; Q2 += q[k][2]; Q3 += q[k][3];
   }
   const double M = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
   const double iM = 1.0 / M;
@@ -173,51 +170,62 @@ __host__ __device__ __forceinline__ bool gen_rambo(const KinDev& kin, const doub
   const double gam = Q0 * iM, a = 1.0 / (1.0 + gam), x = w * iM;
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
-    double* q = p[2 + k];
-    const double bq = b1 * q[1] + b2 * q[2] + b3 * q[3];
-    const double q0 = q[0];
+    double* r = q[k];
+    const double bq = b1 * r[1] + b2 * r[2] + b3 * r[3];
+    const double q0 = r[0];
     const double c = q0 + a * bq;
-    q[0] = x * (gam * q0 + bq);
-    q[1] = x * (q[1] + b1 * c);
-    q[2] = x * (q[2] + b2 * c);
-    q[3] = x * (q[3] + b3 * c);
+    r[0] = x * (gam * q0 + bq);
+    r[1] = x * (r[1] + b1 * c);
+    r[2] = x * (r[2] + b2 * c);
+    r[3] = x * (r[3] + b3 * c);
   }
+}
+
+// massive rescaling of NF massless momenta q at total energy w to masses m[]:
+// sum_k sqrt(m_k^2 + xi^2 E_k^2) = w by Newton's method; returns the weight factor
+// xi^(2 NF - 3) prod_k(|p_k| / E_k) w / sum_k(|p_k|^2 / E_k)
+template <int NF>
+__host__ __device__ __forceinline__ double rambo_massive_rescale(double w, const double* m, double (*q)[4]) {
+  double E0[NF];
+  double msum = 0;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) { E0[k] = q[k][0]; msum += m[k]; }
+  double xi = sqrt(fmax(1.0 - (msum / w) * (msum / w), 0.0));
+  for (int it = 0; it < 40; ++it) {
+    double f = -w, df = 0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const double Ek = sqrt(m[k] * m[k] + xi * xi * E0[k] * E0[k]);
+      f += Ek;
+      df += xi * E0[k] * E0[k] / Ek;
+    }
+    xi -= f / df;
+  }
+  double prod = 1.0, sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    const double ak = xi * E0[k];
+    const double Ek = sqrt(m[k] * m[k] + ak * ak);
+    prod *= ak / Ek;
+    sum += ak * ak / Ek;
+    q[k][0] = Ek;
+    q[k][1] *= xi; q[k][2] *= xi; q[k][3] *= xi;
+  }
+  return pow(xi, 2 * NF - 3) * prod * w / sum;
+}
+
+// RAMBO: massless momenta, then (if any mass) the Kleiss-Stirling-Ellis rescaling
+template <int NEXT>
+__host__ __device__ __forceinline__ bool gen_rambo(const KinDev& kin, const double* u, double (&p)[NEXT][4],
+                                                   double& wps, double& shat) {
+  constexpr int NF = NEXT - 2;
+  const double w = kin.sqrt_s;
+  beams<NEXT>(p, w);
+  rambo_massless_core<NF>(w, u, p + 2);
   // massless volume (2pi)^(4-3n) (pi/2)^(n-1) w^(2n-4) / ((n-1)! (n-2)!)
   wps = kin.rambo_volume;
   shat = w * w;
-  bool massive = false;
-#pragma unroll
-  for (int k = 0; k < NF; ++k) massive |= kin.mass[2 + k] > 0.0;
-  if (massive) {
-    double E0[NF];
-    double msum = 0;
-#pragma unroll
-    for (int k = 0; k < NF; ++k) { E0[k] = p[2 + k][0]; msum += kin.mass[2 + k]; }
-    double xi = sqrt(fmax(1.0 - (msum / w) * (msum / w), 0.0));
-    for (int it = 0; it < 40; ++it) {
-      double f = -w, df = 0;
-#pragma unroll
-      for (int k = 0; k < NF; ++k) {
-        const double m = kin.mass[2 + k];
-        const double Ek = sqrt(m * m + xi * xi * E0[k] * E0[k]);
-        f += Ek;
-        df += xi * E0[k] * E0[k] / Ek;
-      }
-      xi -= f / df;
-    }
-    double prod = 1.0, sum = 0.0;
-#pragma unroll
-    for (int k = 0; k < NF; ++k) {
-      const double m = kin.mass[2 + k];
-      const double ak = xi * E0[k];
-      const double Ek = sqrt(m * m + ak * ak);
-      prod *= ak / Ek;
-      sum += ak * ak / Ek;
-      p[2 + k][0] = Ek;
-      p[2 + k][1] *= xi; p[2 + k][2] *= xi; p[2 + k][3] *= xi;
-    }
-    wps *= pow(xi, 2 * NF - 3) * prod * w / sum;
-  }
+  if (kin.massive) wps *= rambo_massive_rescale<NF>(w, kin.mass + 2, p + 2);
   return true;
 }
 
@@ -227,6 +235,42 @@ __host__ __device__ __forceinline__ double bw_draw(double m, double g, double t0
   const double d = s - m * m;
   jac = (t1 - t0) * (d * d + m * m * g * g) / (m * g) * (1.0 / (2.0 * 3.14159265358979323846));
   return s;
+}
+
+// Resonance-mapped RAMBO (App. A.2): legs 2 and 3 are the decay products of a
+// resonance R (kin.bw_mass[0], kin.bw_width[0]); dPhi_n = dPhi_{n-1}(R, 4..) ds/(2 pi)
+// dPhi_2(R -> 2 3), s Breit-Wigner mapped (Eq. 16 range), RAMBO with the resonance
+// mass for (R, legs 4..), isotropic decay at rest.  Uniforms: 4 per RAMBO particle
+// of (R, 4, ...), then theta, then the decay direction of leg 2.
+template <int NEXT>
+__host__ __device__ __forceinline__ bool gen_rambo_bw(const KinDev& kin, const double* u, double (&p)[NEXT][4],
+                                                      double& wps, double& shat) {
+  constexpr int NR = NEXT - 3;  // RAMBO particles: the resonance and legs 4..NEXT-1
+  const double w = kin.sqrt_s;
+  double jac;
+  const double s = bw_draw(kin.bw_mass[0], kin.bw_width[0], kin.bw_t0[0], kin.bw_t1[0], u[4 * NR], jac);
+  if (!(s > 0.0)) return false;
+  const double M = sqrt(s);
+  if (!(M < w)) return false;
+  beams<NEXT>(p, w);
+  double q[NR][4];
+  rambo_massless_core<NR>(w, u, q);
+  double m[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) m[k] = k == 0 ? M : 0.0;
+  const double fac = rambo_massive_rescale<NR>(w, m, q);
+  double nx, ny, nz;
+  direction(u[4 * NR + 1], u[4 * NR + 2], nx, ny, nz);
+  const double kd = 0.5 * M;
+  set4(p[2], kd, kd * nx, kd * ny, kd * nz);
+  set4(p[3], kd, -kd * nx, -kd * ny, -kd * nz);
+  boost_from_rest(p[2], q[0], M);
+  boost_from_rest(p[3], q[0], M);
+#pragma unroll
+  for (int k = 1; k < NR; ++k) set4(p[3 + k], q[k][0], q[k][1], q[k][2], q[k][3]);
+  wps = kin.rambo_volume * fac * jac * kd / (4.0 * 3.14159265358979323846 * M);
+  shat = w * w;
+  return true;
 }
 
 // g g > t t~ > (b (e+ ve)) (b~ (e- ve~)); legs g g b e+ ve b~ e- ve~
@@ -383,13 +427,15 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
     for (int d = 0; d < 4; ++d)  // compile-time indices keep u in registers
       if (d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
     ok = gen_two_body<NEXT>(kin, u, p, wps, shat);
-  } else if (kin.kind == ME_PS_RAMBO) {
+  } else if (kin.kind == ME_PS_RAMBO || kin.kind == ME_PS_RAMBO_BW) {
     double u[4 * (NEXT - 2)];
     draw_uniforms<NEXT - 2>(seed, event, (uint64_t)att, u);
 #pragma unroll
     for (int d = 0; d < 4 * (NEXT - 2); ++d)
       if (d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
-    ok = gen_rambo<NEXT>(kin, u, p, wps, shat);
+    if (kin.kind == ME_PS_RAMBO) ok = gen_rambo<NEXT>(kin, u, p, wps, shat);
+    else if constexpr (NEXT >= 5) ok = gen_rambo_bw<NEXT>(kin, u, p, wps, shat);
+    else ok = false;
   } else {
     double u[16];
     draw_uniforms<4>(seed, event, (uint64_t)att, u);
@@ -467,7 +513,8 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
 // below the double-float rounding).  Returns the factor of the weight,
 // xi^(2n-3) prod_k(|p_k|/E_k) w / sum_k(|p_k|^2/E_k).
 template <int NEXT>
-__host__ __device__ __forceinline__ df massive_rescale_df(const KinDev& kin, df (&p)[NEXT][4]) {
+__host__ __device__ __forceinline__ df massive_rescale_df(const KinDev& kin, df (&p)[NEXT][4],
+                                                         const df* mass = nullptr) {
   constexpr int NF = NEXT - 2;
   const df w = df{kin.sqrt_s_f[0], kin.sqrt_s_f[1]};
   df E0[NF], m2[NF];
@@ -475,7 +522,7 @@ __host__ __device__ __forceinline__ df massive_rescale_df(const KinDev& kin, df 
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     E0[k] = p[2 + k][0];
-    const df m = from_double(kin.mass[2 + k]);
+    const df m = mass ? mass[k] : from_double(kin.mass[2 + k]);
     m2[k] = sqr(m);
     msum += m.hi;
   }
@@ -726,8 +773,54 @@ __host__ __device__ __forceinline__ bool ttbar_df(const KinDev& kin, uint64_t se
   }
 }
 
-// one mixed-precision draw: double-float RAMBO (massless, or with the massive
-// rescaling) or tt~ chain; the two-body generator in FP64 split into double-floats
+// resonance-mapped RAMBO in double-float (gen_rambo_bw's formulas and uniforms)
+template <int NEXT>
+__host__ __device__ __forceinline__ bool rambo_bw_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
+                                                     df (&p)[NEXT][4], double& wps, df& jac, uint8_t* bins) {
+  constexpr int NR = NEXT - 3;
+  uint64_t o[4];
+  Philox::block(event, (uint64_t)att, (uint64_t)NR, 0ull, seed, 0ull, o);
+  df ub = unit_df(o[0]), ud0 = unit_df(o[1]), ud1 = unit_df(o[2]);
+  if (kin.vg_bins) {
+    ub = vg_map_df(kin, 4 * NR, ub, jac, bins);
+    ud0 = vg_map_df(kin, 4 * NR + 1, ud0, jac, bins);
+    ud1 = vg_map_df(kin, 4 * NR + 2, ud1, jac, bins);
+  }
+  df jbw;
+  const df s = bw_draw_df(kin.bw_mass[0], kin.bw_width[0], kin.bw_t0[0], kin.bw_t1[0], ub, jbw);
+  if (!(s.hi > 0.0f)) return false;
+  const df M = df_sqrt(s);
+  if (!(to_double(M) < kin.sqrt_s)) return false;
+  df q[NR + 2][4];
+  rambo_df<NR + 2>(kin, seed, event, att, q, jac, bins);
+  df masses[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) masses[k] = k == 0 ? M : dfs(0.0f);
+  const df fac = massive_rescale_df<NR + 2>(kin, q, masses);
+  df nx, ny, nz;
+  direction_df(ud0, ud1, nx, ny, nz);
+  const df kd = df{M.hi * 0.5f, M.lo * 0.5f};
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    p[0][mu] = q[0][mu];
+    p[1][mu] = q[1][mu];
+  }
+  set4_df(p[2], kd, kd * nx, kd * ny, kd * nz);
+  set4_df(p[3], kd, -(kd * nx), -(kd * ny), -(kd * nz));
+  boost_from_rest_df(p[2], q[2], M);
+  boost_from_rest_df(p[3], q[2], M);
+#pragma unroll
+  for (int k = 1; k < NR; ++k) {
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) p[3 + k][mu] = q[2 + k][mu];
+  }
+  wps = kin.rambo_volume * to_double(((fac * jbw) * (kd / M)) * df{kInv4PiHi, kInv4PiLo});
+  return true;
+}
+
+// one mixed-precision draw: double-float RAMBO (massless, with the massive
+// rescaling, or resonance-mapped) or tt~ chain; the two-body generator in FP64
+// split into double-floats
 template <int NEXT>
 __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
                                               df (&p)[NEXT][4], double& wps, double& shat,
@@ -740,6 +833,16 @@ __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64
     if (kin.vg_bins) wps *= to_double(jac);
     shat = kin.shat_fixed;
     return pass_cuts_df<NEXT>(kin, p);
+  }
+  if (kin.kind == ME_PS_RAMBO_BW) {
+    if constexpr (NEXT >= 5) {
+      const bool ok = rambo_bw_df<NEXT>(kin, seed, event, att, p, wps, jac, bins);
+      if (kin.vg_bins) wps *= to_double(jac);
+      shat = kin.shat_fixed;
+      return ok && pass_cuts_df<NEXT>(kin, p);
+    } else {
+      return false;
+    }
   }
   if (kin.kind == ME_PS_TTBAR) {
     const bool ok = ttbar_df<NEXT>(kin, seed, event, att, p, wps, shat, jac, bins);

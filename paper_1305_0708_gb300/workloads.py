@@ -32,7 +32,16 @@ WORKLOADS = {
         describe="u s > d c h h (W+ W- fusion), massive RAMBO at sqrt(s)=1 TeV, 2^18 points, seed 4"),
 }
 
-KIND = {"two_body": 0, "rambo": 1, "ttbar": 2}
+# The same processes with another generator (not part of the benchmark workload list)
+VARIANTS = {
+    "udx_epvegg_bw": dict(
+        process="u d~ > e+ ve g g", kind="rambo_bw", sqrt_s=1000.0, res_mass=80.4, res_width=2.085, n=1 << 20,
+        seed=1, cuts=dict(legs=(2, 4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,
+        describe="u d~ > e+ ve g g with the W+ -> e+ ve pair generated Breit-Wigner mapped (App. A.2) and "
+                 "RAMBO for (W*, g, g) at sqrt(s)=1 TeV, same cuts, 2^20 points, seed 1"),
+}
+
+KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3}
 
 
 def kin_args(w):
@@ -40,4 +49,5 @@ def kin_args(w):
     cut = w.get("cuts") or {}
     return dict(kind=KIND[w["kind"]], sqrt_s=w.get("sqrt_s", 0.0), sqrt_s_range=w.get("sqrt_s_range", (0.0, 0.0)),
                 masses=w.get("masses", ()), cut_legs=cut.get("legs", ()), pt_min=cut.get("pt_min", 0.0),
-                eta_max=cut.get("eta_max", 0.0), dr_min=cut.get("dr_min", 0.0), s_ident=w["s_ident"])
+                eta_max=cut.get("eta_max", 0.0), dr_min=cut.get("dr_min", 0.0), s_ident=w["s_ident"],
+                res_mass=w.get("res_mass", 0.0), res_width=w.get("res_width", 0.0))

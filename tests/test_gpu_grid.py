@@ -11,7 +11,7 @@ import pytest
 
 from oracle import processes as opr, vegas, xsec as oxs
 from oracle.sm import SMParams
-from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args
+from paper_1305_0708_gb300.workloads import VARIANTS, WORKLOADS, kin_args
 from test_gpu_parity import ORACLE, from_soa, oracle_kin
 
 pytestmark = pytest.mark.gpu
@@ -40,10 +40,10 @@ def random_grid(rng, D, N):
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("key,n", [("uux_epem", 3000), ("udx_epvegg", 1000), ("gg_ttx_dilep", 300),
-                                   ("us_dchh", 500)])
+                                   ("us_dchh", 500), ("udx_epvegg_bw", 1000)])
 def test_grid_step_matches_oracle(B, key, n, prec):
     import torch
-    w = WORKLOADS[key]
+    w = WORKLOADS[key] if key in WORKLOADS else VARIANTS[key]
     kin = B.make_kin(**kin_args(w))
     h = B.me_create(w["process"], None, prec)
     n_ext = B.me_info(h).n_ext
@@ -63,7 +63,7 @@ def test_grid_step_matches_oracle(B, key, n, prec):
         scale = w.get("sqrt_s") or w["sqrt_s_range"][1]
         assert np.abs(from_soa(mom, n_ext, n) - P).max() <= 4e-12 * scale
         assert acc.n_acc == n and acc.n_try == int(T.sum())
-        ref = ORACLE[key](P, PAR)
+        ref = ORACLE[key if key in ORACLE else "udx_epvegg"](P, PAR)
         rel = np.abs(me2.cpu().numpy() / ref - 1)
         wor = W * ref * w["s_ident"] / (2.0 * S) * 0.3893793721e9
         h_or = vegas.histogram(D, N, bins, wor)

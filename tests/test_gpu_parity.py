@@ -46,6 +46,9 @@ def oracle_kin(w):
         k = {"kind": "rambo", "sqrt_s": w["sqrt_s"], "n_final": nf}
         if "masses" in w:
             k["masses"] = list(w["masses"][2:])
+    elif w["kind"] == "rambo_bw":
+        k = {"kind": "rambo_bw", "sqrt_s": w["sqrt_s"], "n_final": len(opr_legs(w)) - 2,
+             "res_mass": w["res_mass"], "res_width": w["res_width"]}
     else:
         k = {"kind": "ttbar", "sqrt_s_range": w["sqrt_s_range"]}
     if w.get("cuts"):
@@ -210,3 +213,38 @@ def test_full_size_sampled(B):
     # total number of draws over all 2^20 points: oracle generator alone (no |M|^2)
     _, _, _, Tall = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(n))
     assert acc.n_try == int(Tall.sum())
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_resonance_generator_parity(B, prec):
+    """The resonance-mapped generator (App. A.2) on the device against the oracle's: draws, momenta
+    and weights; the FP64 path's Monte Carlo sums against the oracle's.  Mixed-path weights: the
+    double-float massive rescaling divides by the resonance's massless RAMBO energy, which carries
+    2^-48 of sqrt(s) (FP64: 2^-53), hence 5e-11 instead of 1e-12."""
+    from paper_1305_0708_gb300.workloads import VARIANTS
+    w = VARIANTS["udx_epvegg_bw"]
+    n, off = 3000, 777
+    kin = B.make_kin(**kin_args(w))
+    h = B.me_create(w["process"], None, prec)
+    mom = torch.empty(24 * n, dtype=torch.float64, device="cuda")
+    wt = torch.empty(n, dtype=torch.float64, device="cuda")
+    sh = torch.empty(n, dtype=torch.float64, device="cuda")
+    tries = torch.empty(n, dtype=torch.int32, device="cuda")
+    B.me_generate(h, w["seed"], off, n, kin, mom, wt, sh, tries)
+    me2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    acc = B.xsec_step(h, w["seed"], off, n, kin, None, None, me2)
+    torch.cuda.synchronize()
+    B.me_destroy(h)
+    P, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(off, off + n))
+    assert np.array_equal(tries.cpu().numpy(), T)
+    assert np.abs(from_soa(mom, 6, n) - P).max() <= 4e-12 * w["sqrt_s"]
+    assert np.allclose(wt.cpu().numpy(), W, rtol=1e-12 if prec == 0 else 5e-11, atol=0)
+    ref = ORACLE["udx_epvegg"](P, PAR)
+    sw, sw2, nacc, ntry = oxs.accumulate(ref, W, S, T, w["s_ident"])
+    assert acc.n_try == ntry
+    if prec == 0:
+        assert acc.sum_w == pytest.approx(sw, rel=1e-11) and acc.sum_w2 == pytest.approx(sw2, rel=1e-11)
+    else:
+        rel = np.abs(me2.cpu().numpy() / ref - 1)
+        assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
+        assert acc.sum_w == pytest.approx(sw, rel=1e-5)
