@@ -623,8 +623,7 @@ cudaError_t launch_step(int prec, const KinDev* kin, const StepArgs* a, const do
                         int grid_ps, int grid_me, cudaEvent_t ev_mid) {
   cudaError_t e;
   int g = 0;
-  if (prec == ME_FP64) k_ps<Traits, false><<<grid_ps, kThreads, 0, s>>>(*kin, *a);
-  else k_ps<Traits, true><<<grid_ps, kThreads, 0, s>>>(*kin, *a);
+  if ((e = launch_ps<Traits>(prec, kin, a, grid_ps, s)) != cudaSuccess) return e;
   if (ev_mid) cudaEventRecord(ev_mid, s);
   if (prec == ME_FP64) {
     if ((e = prepare<double>(k_me_gluon<double, false>, grid_me, g)) != cudaSuccess) return e;

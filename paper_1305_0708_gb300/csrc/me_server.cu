@@ -70,9 +70,10 @@ struct Request {
   me_request_result res{};
 };
 
-// The step of one process on one slot as an instantiated CUDA graph (the
-// phase-space and |M|^2 kernels, captured once); a chunk rewrites the two
-// kernels' (KinDev, StepArgs) arguments in the executable graph and launches it.
+// The step of one process and generator kind on one slot as an instantiated CUDA
+// graph (the phase-space kernel compiled for that generator and the |M|^2 kernel,
+// captured once); a chunk rewrites the two kernels' (KinDev, StepArgs) arguments
+// in the executable graph and launches it.
 struct SlotGraph {
   bool ok = false;
   cudaGraph_t g = nullptr;
@@ -88,7 +89,7 @@ struct Slot {
   size_t ws_cap = 0;
   Request* req = nullptr;  // request whose chunk (or final reduction) is in flight
   bool final = false;
-  std::map<const Proc*, SlotGraph> graphs;
+  std::map<std::pair<const Proc*, int>, SlotGraph> graphs;  // by (process, generator kind)
 };
 
 }  // namespace
@@ -270,9 +271,10 @@ bool me_server_s::grow_workspaces(size_t need) {
 // Capture the step of q's process on this slot (first use only).  Its two kernel
 // nodes are told apart by their dependencies (the phase-space kernel has none).
 SlotGraph& me_server_s::graph_for(Slot& sl, Request* q, const me::StepArgs& sa) {
-  auto it = sl.graphs.find(q->proc);
+  const std::pair<const Proc*, int> key(q->proc, q->kin.kind);
+  auto it = sl.graphs.find(key);
   if (it != sl.graphs.end()) return it->second;
-  SlotGraph& sg = sl.graphs[q->proc];
+  SlotGraph& sg = sl.graphs[key];
   me_handle h = q->proc->h;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);

@@ -25,17 +25,35 @@ namespace me {
 struct Philox {
   static __host__ __device__ __forceinline__ void mulhilo(uint64_t a, uint64_t b, uint64_t& hi, uint64_t& lo) {
 #ifdef __CUDA_ARCH__
-    hi = __umul64hi(a, b);
+    // the 128-bit product from four 32 x 32-bit partial products with one carry chain
+    // (the lower and upper halves share their partial products)
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint32_t r0, r1, r2, r3;
+    asm("{\n\t"
+        "mul.lo.u32 %0, %4, %6;\n\t"
+        "mul.hi.u32 %1, %4, %6;\n\t"
+        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.hi.u32 %2, %4, %7, 0;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "madc.hi.u32 %3, %5, %7, 0;\n\t"
+        "mad.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "}"
+        : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    lo = ((uint64_t)r1 << 32) | r0;
+    hi = ((uint64_t)r3 << 32) | r2;
 #else
     hi = (uint64_t)(((unsigned __int128)a * b) >> 64);
-#endif
     lo = a * b;
+#endif
   }
   static __host__ __device__ __forceinline__ void block(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
                                                         uint64_t k0, uint64_t k1, uint64_t out[4]) {
     const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
     const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll 1
+#pragma unroll  // unrolled: the Weyl key increments fold into constants
     for (int r = 0; r < 10; ++r) {
       uint64_t h0, l0, h1, l1;
       mulhilo(M0, c0, h0, l0);
@@ -413,27 +431,36 @@ __host__ __device__ __forceinline__ bool pass_cuts(const KinDev& kin, const doub
   return true;
 }
 
+// Generator kind as a template argument: kKindAny reads kin.kind at run time;
+// a fixed kind compiles only that generator (smaller code, fewer registers).
+// kKindRamboMassive is RAMBO with the massive rescaling; ME_PS_RAMBO as a fixed
+// kind on the mixed path is massless RAMBO.  The grid map runs where `bins` is
+// not null (the caller passes null unless kin carries a grid).
+constexpr int kKindAny = -1;
+constexpr int kKindRamboMassive = 100 + ME_PS_RAMBO;
+
 // one draw (attempt `att`) for `event`: false if outside the kinematic limits or the cuts
-template <int NEXT>
+template <int NEXT, int KIND = kKindAny>
 __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t seed, uint64_t event, int att,
                                                     double (&p)[NEXT][4], double& wps, double& shat,
                                                     uint8_t* bins = nullptr) {
   bool ok;
   double jac = 1.0;
-  if (kin.kind == ME_PS_TWO_BODY) {
+  const int kind = KIND == kKindAny ? kin.kind : KIND == kKindRamboMassive ? ME_PS_RAMBO : KIND;
+  if (kind == ME_PS_TWO_BODY) {
     double u[4];
     draw_uniforms<1>(seed, event, (uint64_t)att, u);
 #pragma unroll
     for (int d = 0; d < 4; ++d)  // compile-time indices keep u in registers
-      if (d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
+      if (bins && d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
     ok = gen_two_body<NEXT>(kin, u, p, wps, shat);
-  } else if (kin.kind == ME_PS_RAMBO || kin.kind == ME_PS_RAMBO_BW) {
+  } else if (kind == ME_PS_RAMBO || kind == ME_PS_RAMBO_BW) {
     double u[4 * (NEXT - 2)];
     draw_uniforms<NEXT - 2>(seed, event, (uint64_t)att, u);
 #pragma unroll
     for (int d = 0; d < 4 * (NEXT - 2); ++d)
-      if (d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
-    if (kin.kind == ME_PS_RAMBO) ok = gen_rambo<NEXT>(kin, u, p, wps, shat);
+      if (bins && d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
+    if (kind == ME_PS_RAMBO) ok = gen_rambo<NEXT>(kin, u, p, wps, shat);
     else if constexpr (NEXT >= 5) ok = gen_rambo_bw<NEXT>(kin, u, p, wps, shat);
     else ok = false;
   } else {
@@ -441,7 +468,7 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
     draw_uniforms<4>(seed, event, (uint64_t)att, u);
 #pragma unroll
     for (int d = 0; d < 16; ++d)
-      if (d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
+      if (bins && d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
     ok = gen_ttbar<NEXT>(kin, u, p, wps, shat);
   }
   wps *= jac;
@@ -468,7 +495,7 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
     uint64_t o[4];
     Philox::block(event, (uint64_t)att, (uint64_t)k, 0ull, seed, 0ull, o);
     df u0 = unit_df(o[0]), u1 = unit_df(o[1]), u2 = unit_df(o[2]), u3 = unit_df(o[3]);
-    if (kin.vg_bins) {
+    if (bins) {
       u0 = vg_map_df(kin, 4 * k + 0, u0, jac, bins);
       u1 = vg_map_df(kin, 4 * k + 1, u1, jac, bins);
       u2 = vg_map_df(kin, 4 * k + 2, u2, jac, bins);
@@ -570,59 +597,29 @@ __host__ __device__ __forceinline__ df massive_rescale_df(const KinDev& kin, df 
   return ((xp * prod) * w) / sum;
 }
 
-// cuts on double-float momenta: FP32 estimates decide outside a 1e-5 guard band;
-// a point with any undecided test is decided by the FP64 cuts on its momenta.
+// Delta R test of the pairs in `close` (bit k NF + l: legs k + 2 and l + 2, not
+// certainly separated by their azimuth or pseudorapidity distance alone) in FP32
+// with the guard band, then the FP64 cuts for any undecided point.  Kept out of line: a few lanes of most
+// warps take it, and inlined its code and registers slow the common path.
+// Returns the decision.
 template <int NEXT>
-__host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const df (&p)[NEXT][4]) {
-  const uint32_t mask = kin.cut_mask;
-  if (mask == 0) return true;
-  const float ptmin2 = kin.f_ptmin2, sh2 = kin.f_sinh2;
-  const float cdr = kin.f_cdr, chd = kin.f_chd, shd = kin.f_shd;
+__device__ __noinline__ bool cuts_close_pairs(const KinDev& kin, const df (&p)[NEXT][4], uint64_t close,
+                                              bool undecided) {
+  constexpr int NF = NEXT - 2;
   const float dr2 = kin.f_dr2;
-  float ptf[NEXT], af[NEXT], rf[NEXT];
-  bool undecided = false;
-#pragma unroll
-  for (int i = 2; i < NEXT; ++i) {
-    if (!((mask >> i) & 1u)) continue;
-    const df* q = p[i];
-    const float x = q[1].hi, y = q[2].hi, zz = q[3].hi;
-    const float pt2 = x * x + y * y;
-    int c = fcmp(pt2, ptmin2, ptmin2);
-    if (c < 0) return false;
-    undecided |= (c == 0);
-    c = fcmp(zz * zz, sh2 * pt2, sh2 * pt2 + zz * zz);
-    if (c > 0) return false;
-    undecided |= (c == 0);
-    ptf[i] = sqrtf(pt2);
-    const float ip = 1.0f / ptf[i];
-    af[i] = zz * ip;
-    rf[i] = sqrtf(pt2 + zz * zz) * ip;
-  }
-#pragma unroll 1  // as in rambo_df: one copy of the pair test
-  for (int i = 2; i < NEXT; ++i) {
-#pragma unroll 1
-    for (int j = i + 1; j < NEXT; ++j) {
-      if (undecided || !((mask >> i) & 1u) || !((mask >> j) & 1u)) continue;
-      const df* qi = p[i];
-      const df* qj = p[j];
-      const float dotf = qi[1].hi * qj[1].hi + qi[2].hi * qj[2].hi;
-      const float ptijf = ptf[i] * ptf[j];
-      const int c = fcmp(dotf, cdr * ptijf, ptijf);
-      if (c < 0) continue;
-      if (c == 0) { undecided = true; continue; }
-      const float sc = fabsf(af[i]) + fabsf(af[j]) + rf[i] + rf[j];
-      const int e1 = fcmp(af[i], af[j] * chd + rf[j] * shd, sc);
-      const int e2 = fcmp(af[j], af[i] * chd + rf[i] * shd, sc);
-      if (e1 > 0 || e2 > 0) continue;
-      if (e1 == 0 || e2 == 0) { undecided = true; continue; }
-      const float deta = asinhf(af[i]) - asinhf(af[j]);
-      const float cross = qi[1].hi * qj[2].hi - qi[2].hi * qj[1].hi;
-      const float dphi = atan2f(fabsf(cross), dotf);
-      const float r2 = deta * deta + dphi * dphi;
-      const int r = fcmp(r2, dr2, dr2 + r2);
-      if (r < 0) return false;
-      if (r == 0) undecided = true;
-    }
+  while (close && !undecided) {
+    const int b = __ffsll((long long)close) - 1;
+    close &= close - 1;
+    const int k = b / NF, l = b - (b / NF) * NF;
+    const df* qi = p[k + 2];
+    const df* qj = p[l + 2];
+    const float xi = qi[1].hi, yi = qi[2].hi, xj = qj[1].hi, yj = qj[2].hi;
+    const float deta = asinhf(qi[3].hi / sqrtf(xi * xi + yi * yi)) - asinhf(qj[3].hi / sqrtf(xj * xj + yj * yj));
+    const float dphi = atan2f(fabsf(xi * yj - yi * xj), xi * xj + yi * yj);
+    const float r2 = deta * deta + dphi * dphi;
+    const int r = fcmp(r2, dr2, dr2 + r2);
+    if (r < 0) return false;
+    undecided |= (r == 0);
   }
   if (!undecided) return true;
   double pd[NEXT][4];
@@ -632,6 +629,68 @@ __host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const d
     for (int m = 0; m < 4; ++m) pd[k][m] = to_double(p[k][m]);
   }
   return pass_cuts<NEXT>(kin, pd);
+}
+
+// cuts on double-float momenta: FP32 estimates decide outside a 1e-5 guard band;
+// a point with any undecided test is decided by the FP64 cuts on its momenta.
+// The per-leg quantities and the pair pre-tests (azimuth, then pseudorapidity
+// through sinh/cosh) stay in registers; pairs not certainly separated by one of them
+// go to cuts_close_pairs.
+template <int NEXT>
+__host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const df (&p)[NEXT][4]) {
+  const uint32_t mask = kin.cut_mask;
+  if (mask == 0) return true;
+  constexpr int NF = NEXT - 2;
+  const float ptmin2 = kin.f_ptmin2, sh2 = kin.f_sinh2;
+  const float cdr = kin.f_cdr, chd = kin.f_chd, shd = kin.f_shd;
+  float px[NF], py[NF], pt[NF], a[NF], r[NF];  // a = sinh(eta), r = cosh(eta)
+  bool undecided = false;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    px[k] = p[k + 2][1].hi;
+    py[k] = p[k + 2][2].hi;
+    pt[k] = 1.0f; a[k] = 0.0f; r[k] = 1.0f;
+    if (!((mask >> (k + 2)) & 1u)) continue;
+    const float z = p[k + 2][3].hi;
+    const float pt2 = px[k] * px[k] + py[k] * py[k];
+    int c = fcmp(pt2, ptmin2, ptmin2);
+    if (c < 0) return false;
+    undecided |= (c == 0);
+    c = fcmp(z * z, sh2 * pt2, sh2 * pt2 + z * z);
+    if (c > 0) return false;
+    undecided |= (c == 0);
+    pt[k] = sqrtf(pt2);
+    const float ip = 1.0f / pt[k];
+    a[k] = z * ip;
+    r[k] = sqrtf(pt2 + z * z) * ip;
+  }
+  uint64_t close = 0;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+#pragma unroll
+    for (int l = k + 1; l < NF; ++l) {
+      if (!((mask >> (k + 2)) & 1u) || !((mask >> (l + 2)) & 1u)) continue;
+      // |d_phi| > dr_min  <=>  pT_k . pT_l < cos(dr_min) |pT_k| |pT_l|
+      const float ptkl = pt[k] * pt[l];
+      const int c = fcmp(px[k] * px[l] + py[k] * py[l], cdr * ptkl, ptkl);
+      if (c < 0) continue;
+      // eta_k - eta_l > dr_min  <=>  sinh(eta_k) > sinh(eta_l) cosh(dr) + cosh(eta_l) sinh(dr), and k <-> l
+      const float sc = fabsf(a[k]) + fabsf(a[l]) + r[k] + r[l];
+      const int e1 = fcmp(a[k], a[l] * chd + r[l] * shd, sc);
+      const int e2 = fcmp(a[l], a[k] * chd + r[k] * shd, sc);
+      if (e1 > 0 || e2 > 0) continue;
+      close |= 1ull << (k * NF + l);  // Delta R decides (also where a pre-test was in its band)
+    }
+  }
+  if (!undecided && !close) return true;
+#ifdef __CUDA_ARCH__
+  return cuts_close_pairs<NEXT>(kin, p, close, undecided);
+#else
+  double pd[NEXT][4];
+  for (int k = 0; k < NEXT; ++k)
+    for (int m = 0; m < 4; ++m) pd[k][m] = to_double(p[k][m]);
+  return pass_cuts<NEXT>(kin, pd);
+#endif
 }
 
 // ---------------------------------------------------------------------------
@@ -707,7 +766,7 @@ __host__ __device__ __forceinline__ bool ttbar_df(const KinDev& kin, uint64_t se
     }
 #pragma unroll
     for (int d = 0; d < 16; ++d)
-      if (d < kin.vg_dims) u[d] = vg_map_df(kin, d, u[d], jac, bins);
+      if (bins && d < kin.vg_dims) u[d] = vg_map_df(kin, d, u[d], jac, bins);
     const df rmin = from_double(kin.sqrt_s_min);
     const df rs = rmin + (from_double(kin.sqrt_s_max) - rmin) * u[0];
     df jt, jtb, jwp, jwm;
@@ -781,7 +840,7 @@ __host__ __device__ __forceinline__ bool rambo_bw_df(const KinDev& kin, uint64_t
   uint64_t o[4];
   Philox::block(event, (uint64_t)att, (uint64_t)NR, 0ull, seed, 0ull, o);
   df ub = unit_df(o[0]), ud0 = unit_df(o[1]), ud1 = unit_df(o[2]);
-  if (kin.vg_bins) {
+  if (bins) {
     ub = vg_map_df(kin, 4 * NR, ub, jac, bins);
     ud0 = vg_map_df(kin, 4 * NR + 1, ud0, jac, bins);
     ud1 = vg_map_df(kin, 4 * NR + 2, ud1, jac, bins);
@@ -821,36 +880,38 @@ __host__ __device__ __forceinline__ bool rambo_bw_df(const KinDev& kin, uint64_t
 // one mixed-precision draw: double-float RAMBO (massless, with the massive
 // rescaling, or resonance-mapped) or tt~ chain; the two-body generator in FP64
 // split into double-floats
-template <int NEXT>
+template <int NEXT, int KIND = kKindAny>
 __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
                                               df (&p)[NEXT][4], double& wps, double& shat,
                                               uint8_t* bins = nullptr) {
   df jac = dfs(1.0f);
-  if (kin.kind == ME_PS_RAMBO) {
+  const int kind = KIND == kKindAny ? kin.kind : KIND == kKindRamboMassive ? ME_PS_RAMBO : KIND;
+  const bool massive = KIND == kKindAny ? kin.massive != 0 : KIND == kKindRamboMassive;
+  if (kind == ME_PS_RAMBO) {
     rambo_df<NEXT>(kin, seed, event, att, p, jac, bins);
     wps = kin.rambo_volume;
-    if (kin.massive) wps *= to_double(massive_rescale_df<NEXT>(kin, p));
-    if (kin.vg_bins) wps *= to_double(jac);
+    if (massive) wps *= to_double(massive_rescale_df<NEXT>(kin, p));
+    if (bins) wps *= to_double(jac);
     shat = kin.shat_fixed;
     return pass_cuts_df<NEXT>(kin, p);
   }
-  if (kin.kind == ME_PS_RAMBO_BW) {
+  if (kind == ME_PS_RAMBO_BW) {
     if constexpr (NEXT >= 5) {
       const bool ok = rambo_bw_df<NEXT>(kin, seed, event, att, p, wps, jac, bins);
-      if (kin.vg_bins) wps *= to_double(jac);
+      if (bins) wps *= to_double(jac);
       shat = kin.shat_fixed;
       return ok && pass_cuts_df<NEXT>(kin, p);
     } else {
       return false;
     }
   }
-  if (kin.kind == ME_PS_TTBAR) {
+  if (kind == ME_PS_TTBAR) {
     const bool ok = ttbar_df<NEXT>(kin, seed, event, att, p, wps, shat, jac, bins);
-    if (kin.vg_bins) wps *= to_double(jac);
+    if (bins) wps *= to_double(jac);
     return ok && pass_cuts_df<NEXT>(kin, p);
   }
   double pd[NEXT][4];
-  const bool ok = draw_point<NEXT>(kin, seed, event, att, pd, wps, shat, bins);
+  const bool ok = draw_point<NEXT, KIND>(kin, seed, event, att, pd, wps, shat, bins);
   if (ok) {
 #pragma unroll
     for (int k = 0; k < NEXT; ++k) {

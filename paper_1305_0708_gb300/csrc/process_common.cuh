@@ -260,7 +260,10 @@ __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, ui
 // redraws, then new events -- so rounds stay full until the range runs out; a
 // failed draw is appended with its next attempt number.  Accepted points are
 // written straight to their event's slot in the workspace.
-template <class P, bool MIXED>
+// KIND fixes the generator at compile time and GRID whether the adaptive-grid
+// code is compiled in (used where kin carries a grid); launch_ps picks the
+// instantiation.
+template <class P, bool MIXED, int KIND, bool GRID>
 __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
   const uint64_t seed = a.seed, offset = a.offset;
   const int64_t m = a.m;
@@ -304,11 +307,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
     if (ev >= 0) {
       double wps = 0.0, shat = 1.0;
       bool ok;
-      uint8_t vbins[kGridMaxDims];  // grid steps: bin of every mapped uniform
-      uint8_t* vb = kin.vg_bins ? vbins : nullptr;
+      uint8_t vbins[GRID ? kGridMaxDims : 1];  // grid steps: bin of every mapped uniform
+      uint8_t* vb = GRID && kin.vg_bins ? vbins : nullptr;
       if constexpr (MIXED) {
         df q[NEXT][4];
-        ok = draw_point_df<NEXT>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat, vb);
+        ok = draw_point_df<NEXT, KIND>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat, vb);
         if (ok) {
 #pragma unroll
           for (int k = 0; k < NEXT; ++k) {
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
         }
       } else {
         double q[NEXT][4];
-        ok = draw_point<NEXT>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat, vb);
+        ok = draw_point<NEXT, KIND>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat, vb);
         if (ok) {
 #pragma unroll
           for (int k = 0; k < NEXT; ++k) {
@@ -330,12 +333,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
           }
         }
       }
-      if (a.vg_idx && (ok || att + 1 >= kin.max_attempts))
+      if (GRID && a.vg_idx && (ok || att + 1 >= kin.max_attempts))
         for (int d = 0; d < kin.vg_dims; ++d) a.vg_idx[(int64_t)d * m + ev] = ok ? vbins[d] : (uint8_t)0;
       if (ok) {
         if constexpr (MIXED) {
           // weight factor w_PS s_ident / (2 s) GeV^2->pb as a double-float pair in the weight slot
-          const df wf = kin.wfactor > 0.0 ? from_double(kin.wfactor)
+          // fixed-energy generators without a grid have a constant factor
+          constexpr bool kConstW = !GRID && (KIND == ME_PS_RAMBO || KIND == ME_PS_TWO_BODY);
+          const df wf = kConstW || kin.wfactor > 0.0 ? from_double(kin.wfactor)
                                           : (from_double(wps) * from_double(kin.s_ident * (0.5 * kGeV2pb))) /
                                                 from_double(shat);
           float2* wf_a = reinterpret_cast<float2*>(wps_a);
@@ -545,13 +550,59 @@ __global__ void __launch_bounds__(kThreads) k_me_mx(KinDev kin, StepArgs a, PrmT
   block_reduce3(to_double(swf), to_double(sw2f), (double)ntries, partials);
 }
 
+// k_ps for the generator of kin (the kinds the host accepts for NEXT legs).  The
+// mixed path has one kernel per generator, massless and massive RAMBO apart, with
+// and without the grid code; the FP64 path one per generator with the grid code.
+template <class P, bool MIXED, bool GRID>
+cudaError_t launch_ps_kind(const KinDev* kin, const StepArgs* a, int grid, cudaStream_t s) {
+  constexpr int N = P::NEXT;
+  switch (kin->kind) {
+    case ME_PS_TWO_BODY:
+      if constexpr (N == 4) {
+        k_ps<P, MIXED, ME_PS_TWO_BODY, GRID><<<grid, kThreads, 0, s>>>(*kin, *a);
+        return cudaSuccess;
+      }
+      break;
+    case ME_PS_RAMBO:
+      if constexpr (MIXED) {
+        if (kin->massive) {
+          k_ps<P, MIXED, kKindRamboMassive, GRID><<<grid, kThreads, 0, s>>>(*kin, *a);
+          return cudaSuccess;
+        }
+      }
+      k_ps<P, MIXED, ME_PS_RAMBO, GRID><<<grid, kThreads, 0, s>>>(*kin, *a);
+      return cudaSuccess;
+    case ME_PS_RAMBO_BW:
+      if constexpr (N >= 5) {
+        k_ps<P, MIXED, ME_PS_RAMBO_BW, GRID><<<grid, kThreads, 0, s>>>(*kin, *a);
+        return cudaSuccess;
+      }
+      break;
+    case ME_PS_TTBAR:
+      if constexpr (N == 8) {
+        k_ps<P, MIXED, ME_PS_TTBAR, GRID><<<grid, kThreads, 0, s>>>(*kin, *a);
+        return cudaSuccess;
+      }
+      break;
+    default:
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class P>
+cudaError_t launch_ps(int prec, const KinDev* kin, const StepArgs* a, int grid, cudaStream_t s) {
+  if (prec == ME_FP64) return launch_ps_kind<P, false, true>(kin, a, grid, s);
+  return kin->vg_bins ? launch_ps_kind<P, true, true>(kin, a, grid, s) : launch_ps_kind<P, true, false>(kin, a, grid, s);
+}
+
 template <class P>
 cudaError_t launch_step(int prec, const KinDev* kin, const StepArgs* a, const double* params, cudaStream_t s,
                         int grid_ps, int grid_me, cudaEvent_t ev_mid) {
   typename P::Params prm;
   memcpy(&prm, params, sizeof(prm));
-  if (prec == ME_FP64) k_ps<P, false><<<grid_ps, kThreads, 0, s>>>(*kin, *a);
-  else k_ps<P, true><<<grid_ps, kThreads, 0, s>>>(*kin, *a);
+  cudaError_t e0 = launch_ps<P>(prec, kin, a, grid_ps, s);
+  if (e0 != cudaSuccess) return e0;
   if (ev_mid) cudaEventRecord(ev_mid, s);
   if (prec == ME_FP64) {
     k_me<P, false><<<grid_me, kThreads, 0, s>>>(*kin, *a, prm);
