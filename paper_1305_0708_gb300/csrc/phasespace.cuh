@@ -358,8 +358,9 @@ __host__ __device__ __forceinline__ bool gen_ttbar(const KinDev& kin, const doub
 // pT and |eta| (as |pz| < sinh(eta_max) pT) are exact FP64 comparisons.  A pair
 // is separated when its azimuthal or its pseudorapidity distance alone exceeds
 // dr_min; both tests run first in FP32 and decide only outside a 1e-5 relative
-// guard band around the boundary (FP32 rounding here is below 1e-6), else the
-// same test runs in FP64.  Only pairs close in both evaluate Delta R with asinh
+// guard band around the boundary (FP32 rounding and the approximate reciprocal
+// square roots of the mixed path stay below 1e-6 here), else the same test runs
+// in FP64.  Only pairs close in both evaluate Delta R with asinh
 // and atan2 in FP64.  The decision therefore equals the FP64 one.
 // ---------------------------------------------------------------------------
 // returns +1 (certainly x > y), -1 (certainly x < y) or 0 (undecided) for float estimates
@@ -614,7 +615,7 @@ __device__ __noinline__ bool cuts_close_pairs(const KinDev& kin, const df (&p)[N
     const df* qi = p[k + 2];
     const df* qj = p[l + 2];
     const float xi = qi[1].hi, yi = qi[2].hi, xj = qj[1].hi, yj = qj[2].hi;
-    const float deta = asinhf(qi[3].hi / sqrtf(xi * xi + yi * yi)) - asinhf(qj[3].hi / sqrtf(xj * xj + yj * yj));
+    const float deta = asinhf(qi[3].hi * rsqrtf(xi * xi + yi * yi)) - asinhf(qj[3].hi * rsqrtf(xj * xj + yj * yj));
     const float dphi = atan2f(fabsf(xi * yj - yi * xj), xi * xj + yi * yj);
     const float r2 = deta * deta + dphi * dphi;
     const int r = fcmp(r2, dr2, dr2 + r2);
@@ -659,10 +660,12 @@ __host__ __device__ __forceinline__ bool pass_cuts_df(const KinDev& kin, const d
     c = fcmp(z * z, sh2 * pt2, sh2 * pt2 + z * z);
     if (c > 0) return false;
     undecided |= (c == 0);
-    pt[k] = sqrtf(pt2);
-    const float ip = 1.0f / pt[k];
+    // approximate reciprocal square roots (relative error below 3e-7, inside the band)
+    const float ip = rsqrtf(pt2);
+    const float p2 = pt2 + z * z;
+    pt[k] = pt2 * ip;
     a[k] = z * ip;
-    r[k] = sqrtf(pt2 + z * z) * ip;
+    r[k] = p2 * rsqrtf(p2) * ip;
   }
   uint64_t close = 0;
 #pragma unroll
