@@ -109,7 +109,7 @@ class _Emitter:
             self.flops32 += 4 * (len(kids) - 1)
             part = PARTICLES[nd.ptype]
             if part.massless:
-                E(f"  const me::cx<R> inv{nid} = me::mk(R(1) / me::msq(k{nid}), R(0));")
+                E(f"  const R inv{nid} = R(1) / me::msq(k{nid});  // real: massless line")
                 self.flops32 += 8
             else:
                 m = self.cpl(part.mass)
@@ -265,7 +265,9 @@ class _Emitter:
                     E(f"  const me::W4<R> {name} = me::prop_row<R, {_tag(hx)}>(me::ffv_row<R, {_tag(hin)}>("
                       f"{fk[2]}, {vk[2]}, {cargs}), me::neg(k{nid}), {m}, inv{nid});")
                 self.half[name] = _flip(hx) if part.massless else frozenset("ul")
-                self.flops32 += 20 * 2 * len(hx) + 24 * len(hx) + (32 if not part.massless else 0)
+                # per non-zero half: vertex 40 (sigma matrix 8, two components of 16); propagator
+                # 24 with the real reciprocal of a massless line, 32 with a complex one, plus the mass term
+                self.flops32 += (40 + (24 if part.massless else 32)) * len(hx) + 2 + (32 if not part.massless else 0)
             else:
                 rk = [k for k in kids if k[1] == 0][0]
                 ck = [k for k in kids if k[1] == 1][0]
@@ -278,13 +280,13 @@ class _Emitter:
                 E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::ffv_current<R, {_tag(hr)}, {_tag(hc)}>("
                   f"{rk[2]}, {ck[2]}, {cargs}), k{nid}, inv{nid}, {str(massive).lower()}, {mc2});")
                 nterm = int(has_l and "l" in hr and "u" in hc) + int(has_r and "u" in hr and "l" in hc)
-                self.flops32 += 48 * nterm + (60 if massive else 24)
+                self.flops32 += 48 * nterm + (60 if massive else 8)
         elif v.kind == "VVV":
             g = self.cpl(v.couplings[0])
             a, b = kids
             E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::vvv_current<R>({a[2]}, k{a[0]}, {b[2]}, k{b[0]}, "
               f"(R){g}), k{nid}, inv{nid}, false, me::mk(R(0), R(0)));")
-            self.flops32 += 150 + 24
+            self.flops32 += 150 + 8
         elif v.kind == "VVVV":
             g = self.cpl(v.couplings[0])
             slot = {s: nm for _, s, nm in kids}
@@ -295,7 +297,7 @@ class _Emitter:
             t2 = self._v4_term(o, [(x, w), (y, z)], slot)
             E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::w4_sub<R>({t1}, {t2}, (R){g}), k{nid}, inv{nid}, "
               f"false, me::mk(R(0), R(0)));")
-            self.flops32 += 2 * 54 + 16 + 24
+            self.flops32 += 2 * 54 + 16 + 8
         elif v.kind in ("VVS", "VVSS"):
             g = self.cpl(v.couplings[0])
             vs = [k for k in kids if PARTICLES[v.fields[k[1]]].is_vector]
@@ -310,7 +312,7 @@ class _Emitter:
                     self.cpl(part.width)
                 E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::w4_scale<R>({vs[0][2]}, {s_expr}), k{nid}, "
                   f"inv{nid}, {str(massive).lower()}, {mc2});")
-                self.flops32 += 24 + 60 + 6 * len(ss)
+                self.flops32 += 24 + (60 if massive else 8) + 6 * len(ss)
             else:
                 d = f"me::mdot<R>({vs[0][2]}, {vs[1][2]})"
                 extra = f" * {sprod}" if sprod else ""

@@ -251,22 +251,26 @@ ME_HD W4<R> ffv_current(const W4<R>& row, const W4<R>& col, R gl, R gr, bool has
 
 // ---------------------------------------------------------------------------
 // propagators (numerators times the reciprocal denominator inv = 1/(q^2 - m^2 + i m w))
+// INV is cx<R> for a line with a width and R for a massless line (a real
+// reciprocal: IEEE arithmetic would not let the compiler drop the products with
+// its zero imaginary part).  The real diagonal entries of q.sigma, q.sigmabar
+// multiply as reals for the same reason.
 // ---------------------------------------------------------------------------
 // (qslash + m) x inv for a column with non-zero half HX;  q is the momentum along the fermion arrow
-template <class R, int HX = kAll>
-ME_HD W4<R> prop_col(const W4<R>& x, P4<R> q, R m, cx<R> inv) {
+template <class R, int HX = kAll, class INV>
+ME_HD W4<R> prop_col(const W4<R>& x, P4<R> q, R m, INV inv) {
   // q.sigma = [[q0-q3, -q1+iq2], [-q1-iq2, q0+q3]],  q.sigmabar = [[q0+q3, q1-iq2], [q1+iq2, q0-q3]]
-  const cx<R> s00 = mk(q.e - q.z, R(0)), s01 = mk(-q.x, q.y), s10 = mk(-q.x, -q.y), s11 = mk(q.e + q.z, R(0));
-  const cx<R> b00 = mk(q.e + q.z, R(0)), b01 = mk(q.x, -q.y), b10 = mk(q.x, q.y), b11 = mk(q.e - q.z, R(0));
+  const R qm = q.e - q.z, qp = q.e + q.z;
+  const cx<R> s01 = mk(-q.x, q.y), s10 = mk(-q.x, -q.y), b01 = mk(q.x, -q.y), b10 = mk(q.x, q.y);
   const cx<R> z = mk(R(0), R(0));
   W4<R> o;
   if (HX != kUp) {
-    o.c[0] = (s00 * x.c[2] + s01 * x.c[3]) * inv;
-    o.c[1] = (s10 * x.c[2] + s11 * x.c[3]) * inv;
+    o.c[0] = (qm * x.c[2] + s01 * x.c[3]) * inv;
+    o.c[1] = (s10 * x.c[2] + qp * x.c[3]) * inv;
   } else { o.c[0] = z; o.c[1] = z; }
   if (HX != kLo) {
-    o.c[2] = (b00 * x.c[0] + b01 * x.c[1]) * inv;
-    o.c[3] = (b10 * x.c[0] + b11 * x.c[1]) * inv;
+    o.c[2] = (qp * x.c[0] + b01 * x.c[1]) * inv;
+    o.c[3] = (b10 * x.c[0] + qm * x.c[1]) * inv;
   } else { o.c[2] = z; o.c[3] = z; }
   if (m != R(0)) {
     for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] + (m * x.c[k]) * inv;
@@ -275,20 +279,20 @@ ME_HD W4<R> prop_col(const W4<R>& x, P4<R> q, R m, cx<R> inv) {
 }
 
 // x (qslash + m) inv for a row with non-zero half HX
-template <class R, int HX = kAll>
-ME_HD W4<R> prop_row(const W4<R>& x, P4<R> q, R m, cx<R> inv) {
-  const cx<R> s00 = mk(q.e - q.z, R(0)), s01 = mk(-q.x, q.y), s10 = mk(-q.x, -q.y), s11 = mk(q.e + q.z, R(0));
-  const cx<R> b00 = mk(q.e + q.z, R(0)), b01 = mk(q.x, -q.y), b10 = mk(q.x, q.y), b11 = mk(q.e - q.z, R(0));
+template <class R, int HX = kAll, class INV>
+ME_HD W4<R> prop_row(const W4<R>& x, P4<R> q, R m, INV inv) {
+  const R qm = q.e - q.z, qp = q.e + q.z;
+  const cx<R> s01 = mk(-q.x, q.y), s10 = mk(-q.x, -q.y), b01 = mk(q.x, -q.y), b10 = mk(q.x, q.y);
   const cx<R> z = mk(R(0), R(0));
   W4<R> o;
   // (x_up, x_lo) [[0, q.s], [q.sb, 0]] = (x_lo q.sb, x_up q.s)
   if (HX != kUp) {
-    o.c[0] = (x.c[2] * b00 + x.c[3] * b10) * inv;
-    o.c[1] = (x.c[2] * b01 + x.c[3] * b11) * inv;
+    o.c[0] = (x.c[2] * qp + x.c[3] * b10) * inv;
+    o.c[1] = (x.c[2] * b01 + x.c[3] * qm) * inv;
   } else { o.c[0] = z; o.c[1] = z; }
   if (HX != kLo) {
-    o.c[2] = (x.c[0] * s00 + x.c[1] * s10) * inv;
-    o.c[3] = (x.c[0] * s01 + x.c[1] * s11) * inv;
+    o.c[2] = (x.c[0] * qm + x.c[1] * s10) * inv;
+    o.c[3] = (x.c[0] * s01 + x.c[1] * qp) * inv;
   } else { o.c[2] = z; o.c[3] = z; }
   if (m != R(0)) {
     for (int k = 0; k < 4; ++k) o.c[k] = o.c[k] + (m * x.c[k]) * inv;
@@ -304,7 +308,8 @@ template <class R> ME_HD cx<R> mdot(P4<R> q, const W4<R>& b) {
 }
 
 // vector propagator numerator g^{mu nu} - q^mu q^nu / mc2 applied to X, times inv
-template <class R> ME_HD W4<R> prop_vec(const W4<R>& X, P4<R> q, cx<R> inv, bool massive, cx<R> inv_mc2) {
+template <class R, class INV>
+ME_HD W4<R> prop_vec(const W4<R>& X, P4<R> q, INV inv, bool massive, cx<R> inv_mc2) {
   W4<R> o;
   if (massive) {
     const cx<R> f = mdot(q, X) * inv_mc2;
