@@ -128,6 +128,17 @@ me_status me_create(const char *process, const me_params *params, int32_t prec, 
  * doubles.  Asynchronous on stream; n = 0 is a no-op. */
 me_status me_eval(me_handle h, const double *momenta, int64_t n, double *out, void *stream);
 
+/* me_eval for host buffers: momenta (n_ext * 4 * n doubles, layout above) and
+ * out (n doubles) in host memory, caller-owned.  Page-locked memory that the
+ * device maps (cudaHostAlloc / cudaMallocHost, or registered) is read and
+ * written by the kernel directly over the CPU-GPU link; other host memory goes
+ * through two device buffers in chunks of 2^17 points, copies overlapping the
+ * evaluation (buffers kept by the handle until me_destroy).  Synchronous:
+ * returns once out holds |M|^2.  Runs on stream (and, for staged memory, a
+ * second stream of the handle that follows it).  Errors: ME_ERR_ARG for n < 0,
+ * a null pointer or a device pointer; ME_ERR_CUDA. */
+me_status me_eval_host(me_handle h, const double *momenta, int64_t n, double *out, void *stream);
+
 /* Phase-space points only: for events counter_offset .. counter_offset+n-1,
  * draw with Philox4x64-10 (counter = (event, attempt, block, 0), key =
  * (seed, 0)) until the cuts pass.  Outputs (device, any may be NULL):

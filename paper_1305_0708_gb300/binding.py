@@ -71,7 +71,7 @@ class me_server_stats(ctypes.Structure):
 ME_FP64, ME_MIXED = 0, 1
 ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR, ME_PS_RAMBO_BW = 0, 1, 2, 3
 
-EXPORTS = ["me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
+EXPORTS = ["me_create", "me_eval", "me_eval_host", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
            "me_xsec_estimate", "me_info", "me_n_processes", "me_process_name", "me_destroy", "me_last_error",
            "me_server_create", "me_server_warm", "me_server_submit", "me_server_poll", "me_server_wait",
            "me_server_get_stats", "me_server_destroy", "me_grid_create", "me_grid_info", "me_grid_get_edges",
@@ -95,6 +95,7 @@ def load(path=None):
     vp, i64, u64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32
     L.me_create.argtypes = [ctypes.c_char_p, ctypes.POINTER(me_params), i32, ctypes.POINTER(vp)]
     L.me_eval.argtypes = [vp, vp, i64, vp, vp]
+    L.me_eval_host.argtypes = [vp, vp, i64, vp, vp]
     L.me_generate.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, vp, vp, vp, vp]
     L.xsec_step.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc), vp, vp]
     L.xsec_step_noalloc.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc),
@@ -130,7 +131,7 @@ def load(path=None):
     L.me_grid_destroy.argtypes = [vp]
     L.me_grid_destroy.restype = None
     L.me_vegas_refine_edges.argtypes = [vp, vp, i32, i32, ctypes.c_double, vp]
-    for fn in ("me_create", "me_eval", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
+    for fn in ("me_create", "me_eval", "me_eval_host", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
                "me_xsec_estimate", "me_info", "me_server_create", "me_server_warm", "me_server_submit",
                "me_server_poll", "me_server_wait", "me_server_get_stats", "me_grid_create", "me_grid_info",
                "me_grid_get_edges", "me_grid_set_edges", "me_grid_get_hist", "me_grid_clear_hist",
@@ -196,6 +197,11 @@ def me_create(process, params=None, prec=ME_FP64):
 
 def me_eval(h, momenta, n, out, stream=None):
     _check(load().me_eval(h, _ptr(momenta), n, _ptr(out), _stream(stream)))
+
+
+def me_eval_host(h, momenta, n, out, stream=None):
+    """|M|^2 for host buffers (CPU tensors or addresses); returns when out is filled."""
+    _check(load().me_eval_host(h, _ptr(momenta), n, _ptr(out), _stream(stream)))
 
 
 def me_generate(h, seed, counter_offset, n, kin, momenta=None, weight=None, shat=None, tries=None, stream=None):

@@ -439,6 +439,67 @@ me_status me_eval(me_handle h, const double* momenta, int64_t n, double* out, vo
   return ME_OK;
 }
 
+me_status me_eval_host(me_handle h, const double* momenta, int64_t n, double* out, void* stream) {
+  me_status st = check_handle(h);
+  if (st != ME_OK) return st;
+  if (n < 0) return fail(ME_ERR_ARG, "me_eval_host: n < 0");
+  if (n == 0) return ME_OK;
+  if (!momenta || !out) return fail(ME_ERR_ARG, "me_eval_host: null buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaPointerAttributes am{}, ao{};
+  cudaError_t e = cudaPointerGetAttributes(&am, momenta);
+  if (e == cudaSuccess) e = cudaPointerGetAttributes(&ao, out);
+  if (e != cudaSuccess) return cuda_fail(e, "me_eval_host: cudaPointerGetAttributes");
+  if (am.type == cudaMemoryTypeDevice || ao.type == cudaMemoryTypeDevice)
+    return fail(ME_ERR_ARG, "me_eval_host: device buffer (use me_eval)");
+  std::lock_guard<std::mutex> lock(h->mu);
+  const bool mapped = am.type == cudaMemoryTypeHost && am.devicePointer && ao.type == cudaMemoryTypeHost &&
+                      ao.devicePointer;
+  if (mapped) {
+    // page-locked, mapped host memory: the kernel reads the momenta and writes |M|^2 over the
+    // CPU-GPU link itself, no staging copy
+    e = h->desc->launch_eval(h->prec, (const double*)am.devicePointer, n, (double*)ao.devicePointer,
+                             h->cvals.data(), s, grid_for(h, n));
+    if (e != cudaSuccess) return cuda_fail(e, "me_eval_host launch");
+    e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_eval_host");
+  }
+  // other host memory: chunks of kHostChunk points through two device buffers, alternating
+  // between the caller's stream and a second one, so that one chunk's copies overlap the
+  // other's evaluation
+  const int rows = h->desc->n_ext * 4;
+  const int64_t cm = std::min<int64_t>(n, kHostChunk);
+  if (!h->s_aux) {
+    for (int b = 0; b < 2; ++b) {
+      if ((e = cudaMalloc(&h->d_stage[b], sizeof(double) * rows * kHostChunk)) != cudaSuccess ||
+          (e = cudaMalloc(&h->d_stage_out[b], sizeof(double) * kHostChunk)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&h->ev_aux[b], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "me_eval_host: staging");
+    }
+    if ((e = cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "me_eval_host: stream");
+  }
+  // the second stream starts after the work already queued on the caller's stream
+  if ((e = cudaEventRecord(h->ev_aux[0], s)) != cudaSuccess || (e = cudaStreamWaitEvent(h->s_aux, h->ev_aux[0], 0)))
+    return cuda_fail(e, "me_eval_host: order");
+  const int64_t nchunk = (n + cm - 1) / cm;
+  for (int64_t c = 0; c < nchunk && e == cudaSuccess; ++c) {
+    const int b = (int)(c & 1);
+    cudaStream_t sc = b ? h->s_aux : s;
+    const int64_t first = c * cm, m = std::min<int64_t>(cm, n - first);
+    e = cudaMemcpy2DAsync(h->d_stage[b], sizeof(double) * m, momenta + first, sizeof(double) * n, sizeof(double) * m,
+                          rows, cudaMemcpyHostToDevice, sc);
+    if (e == cudaSuccess)
+      e = h->desc->launch_eval(h->prec, h->d_stage[b], m, h->d_stage_out[b], h->cvals.data(), sc, grid_for(h, m));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out + first, h->d_stage_out[b], sizeof(double) * m, cudaMemcpyDeviceToHost, sc);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(h->s_aux);
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+  return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_eval_host");
+}
+
 me_status me_generate(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n, const me_kin* kin,
                       double* momenta, double* weight, double* shat, int32_t* tries, void* stream) {
   me_status st = check_handle(h);
@@ -563,6 +624,12 @@ void me_destroy(me_handle h) {
   if (h->d_status) cudaFree(h->d_status);
   if (h->h_acc) cudaFreeHost(h->h_acc);
   if (h->d_ws) cudaFree(h->d_ws);
+  for (int b = 0; b < 2; ++b) {
+    if (h->d_stage[b]) cudaFree(h->d_stage[b]);
+    if (h->d_stage_out[b]) cudaFree(h->d_stage_out[b]);
+    if (h->ev_aux[b]) cudaEventDestroy(h->ev_aux[b]);
+  }
+  if (h->s_aux) cudaStreamDestroy(h->s_aux);
   for (int i = 0; i < 3; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;

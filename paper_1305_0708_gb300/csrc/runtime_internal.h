@@ -23,6 +23,12 @@ struct me_handle_s {
   double* h_acc = nullptr;    // pinned, 3 doubles + status
   void* d_ws = nullptr;       // phase-space points of one chunk (k_ps -> k_me)
   size_t ws_cap = 0;
+  // me_eval_host staging for host memory the device cannot address (lazy): two
+  // momentum buffers [n_ext*4][kHostChunk], two |M|^2 buffers, a second stream
+  double* d_stage[2] = {nullptr, nullptr};
+  double* d_stage_out[2] = {nullptr, nullptr};
+  cudaStream_t s_aux = nullptr;
+  cudaEvent_t ev_aux[2] = {nullptr, nullptr};
   // optional per-kernel timing of xsec_step (CUDA events on the call's stream)
   bool timing = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -33,7 +39,8 @@ struct me_handle_s {
 namespace me {
 namespace rt {
 
-constexpr int64_t kChunk = 1 << 20;  // points per k_ps / k_me pair of xsec_step
+constexpr int64_t kChunk = 1 << 20;      // points per k_ps / k_me pair of xsec_step
+constexpr int64_t kHostChunk = 1 << 17;  // points per staged chunk of me_eval_host
 
 me_status fail(me_status st, const std::string& msg);
 me_status cuda_fail(cudaError_t e, const char* where);

@@ -60,6 +60,7 @@ def test_argument_errors_before_device_work(lib):
     assert lib.me_create(b"u u~ > z z z z z", None, 0, ctypes.byref(h)) == -2
     assert "not compiled" in binding.me_last_error()
     assert lib.me_eval(None, None, 4, None, None) == -1
+    assert lib.me_eval_host(None, None, 4, None, None) == -1
     assert lib.me_info(None, None) == -1
 
 
