@@ -7,7 +7,10 @@ from its published definition: ten rounds of
     (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
 with the key bumped by the Weyl constants between rounds.  Event i, attempt
 a, block j uses counter (i, a, j, 0) and key (seed, 0); each block gives four
-64-bit words, mapped to doubles in (0, 1) as ((x >> 11) + 1/2) 2^-53.
+64-bit words, each word two 32-bit deviates (low half first) mapped to doubles
+in (0, 1) as (w + 1/2) 2^-32 -- 32-bit deviates like those of the paper's
+generator (App. B).  Uniform i of a draw is half i % 2 of word (i % 8) // 2 of
+block i // 8.
 
 Generators (the paper's own parametrisation, App. A, is replaced by the
 workload's stated generators; the Breit-Wigner mapping is the paper's Eq. 16):
@@ -68,21 +71,25 @@ def philox4x64_10(ctr, key):
         return np.stack(c, axis=1)
 
 
-def to_unit(x):
-    """uint64 -> double in (0, 1): ((x >> 11) + 0.5) * 2^-53."""
-    return ((x >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
+def to_unit32(w):
+    """uint32 values (held in uint64) -> doubles in (0, 1): (w + 0.5) * 2^-32."""
+    return (w.astype(np.float64) + 0.5) * (2.0 ** -32)
 
 
-def uniforms(seed, event, attempt, nblocks):
-    """[N, 4 * nblocks] doubles for events `event` at attempts `attempt`."""
+def uniforms(seed, event, attempt, n):
+    """[N, n] doubles for events `event` at attempts `attempt` (uniform i: block i // 8,
+    word (i % 8) // 2, its low 32 bits for even i, its high 32 bits for odd i)."""
     event = np.asarray(event, dtype=np.uint64)
     attempt = np.asarray(attempt, dtype=np.uint64)
     N = event.shape[0]
-    out = np.empty((N, 4 * nblocks))
-    for j in range(nblocks):
+    nb = (n + 7) // 8
+    out = np.empty((N, 8 * nb))
+    for j in range(nb):
         ctr = np.stack([event, attempt, np.full(N, j, dtype=np.uint64), np.zeros(N, dtype=np.uint64)], axis=1)
-        out[:, 4 * j:4 * j + 4] = to_unit(philox4x64_10(ctr, np.array([seed, 0], dtype=np.uint64)))
-    return out
+        o = philox4x64_10(ctr, np.array([seed, 0], dtype=np.uint64))
+        halves = np.stack([o & np.uint64(0xFFFFFFFF), o >> np.uint64(32)], axis=2).reshape(N, 8)
+        out[:, 8 * j:8 * j + 8] = to_unit32(halves)
+    return out[:, :n]
 
 
 # ---------------------------------------------------------------------------

@@ -52,16 +52,8 @@ def draw(kin, par, u):
     raise ValueError(kind)
 
 
-def nblocks(kin):
-    if kin["kind"] == "2to2":
-        return 1
-    if kin["kind"] in ("rambo", "rambo_bw"):
-        return kin["n_final"]
-    return 4
-
-
 def grid_dims(kin):
-    """Uniform variables a draw uses: the dimensions of an adaptive grid (oracle.vegas)."""
+    """Uniform variables a draw uses (also the dimensions of an adaptive grid, oracle.vegas)."""
     if kin["kind"] == "2to2":
         return 2
     if kin["kind"] == "rambo":
@@ -96,7 +88,7 @@ def _generate(kin, par, seed, events, max_attempts, grid):
     P = None
     W = np.zeros(N)
     S = np.zeros(N)
-    nb = nblocks(kin)
+    nu = grid_dims(kin)
     cut = kin.get("cuts")
     bins = None
     if grid is not None:
@@ -104,7 +96,7 @@ def _generate(kin, par, seed, events, max_attempts, grid):
         bins = np.zeros((N, grid.shape[0]), dtype=np.int64)
     while pending.any():
         idx = np.nonzero(pending)[0]
-        u = ps.uniforms(seed, events[idx], attempt[idx], nb)
+        u = ps.uniforms(seed, events[idx], attempt[idx], nu)
         if grid is not None:
             D = grid.shape[0]
             x, jac, b = vegas.vegas_map(grid, u[:, :D])

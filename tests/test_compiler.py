@@ -73,15 +73,15 @@ def test_pruned_helicities_are_exact_zeros(name, fn):
     live = set(prog.live)
     n = prog.n_ext
     if n == 4:
-        P, _ = ps.two_to_two_massless(500.0, ps.uniforms(0, np.arange(8), np.zeros(8), 1))
+        P, _ = ps.two_to_two_massless(500.0, ps.uniforms(0, np.arange(8), np.zeros(8), 4))
     elif n == 6:
-        pf, _ = ps.rambo_massless(1000.0, 4, ps.uniforms(0, np.arange(8), np.zeros(8), 4))
+        pf, _ = ps.rambo_massless(1000.0, 4, ps.uniforms(0, np.arange(8), np.zeros(8), 16))
         P = np.zeros((8, 6, 4))
         P[:, 0], P[:, 1] = ps.incoming(1000.0, 8)
         P[:, 2:] = pf
     else:
         from oracle.sm import SMParams
-        Q, _, ok, _ = ps.ttbar_dilepton(ps.uniforms(0, np.arange(32), np.zeros(32), 4), SMParams(), (400, 2000))
+        Q, _, ok, _ = ps.ttbar_dilepton(ps.uniforms(0, np.arange(32), np.zeros(32), 16), SMParams(), (400, 2000))
         P = Q[ok][:8]
     _, ph = fn(P, per_helicity=True)
     tot = sum(ph.values())

@@ -155,7 +155,7 @@ def test_five_gluons_parity(B):
     """g g > g g g through the colour-ordered block kernel, both paths."""
     from oracle import phasespace as ps
     n = 300
-    u = ps.uniforms(11, np.arange(n), np.zeros(n), 3)
+    u = ps.uniforms(11, np.arange(n), np.zeros(n), 12)
     pf, _ = ps.rambo_massless(1000.0, 3, u)
     P = np.zeros((n, 5, 4))
     P[:, 0], P[:, 1] = ps.incoming(1000.0, n)

@@ -27,20 +27,33 @@ def test_philox_matches_numpy_library():
         assert np.array_equal(mine.ravel(), lib)
 
 
+def test_uniforms_are_halves_of_the_library_words():
+    """Uniform i of a draw is the low (even i) or high (odd i) 32 bits w of word (i % 8) // 2 of
+    Philox block i // 8, as (w + 1/2) 2^-32; the words from numpy's library Philox4x64-10."""
+    seed, ev, att = 987654321, 4242, 5
+    u = ps.uniforms(seed, np.array([ev]), np.array([att]), 21)[0]
+    key = np.array([seed, 0], dtype=np.uint64)
+    for i in range(21):
+        ctr = np.array([ev - 1, att, i // 8, 0], dtype=np.uint64)  # the library steps the counter first
+        word = int(np.random.Philox(counter=ctr, key=key).random_raw(4)[(i % 8) // 2])
+        w = (word >> 32) if i % 2 else (word & 0xFFFFFFFF)
+        assert u[i] == (w + 0.5) / 2.0 ** 32
+
+
 def test_uniforms_range_and_moments():
-    u = ps.uniforms(7, np.arange(20000), np.zeros(20000), 2)
+    u = ps.uniforms(7, np.arange(20000), np.zeros(20000), 8)
     assert u.min() > 0 and u.max() < 1
     assert abs(u.mean() - 0.5) < 0.005
     assert abs((u * u).mean() - 1 / 3) < 0.005
     # distinct attempts give distinct streams
-    u1 = ps.uniforms(7, np.arange(100), np.ones(100), 2)
+    u1 = ps.uniforms(7, np.arange(100), np.ones(100), 8)
     assert not np.allclose(u[:100], u1)
 
 
 @pytest.mark.parametrize("n", [2, 3, 4, 6])
 def test_rambo_massless(n):
     w = 1000.0
-    u = ps.uniforms(1, np.arange(500), np.zeros(500), n)
+    u = ps.uniforms(1, np.arange(500), np.zeros(500), 4 * n)
     p, wt = ps.rambo_massless(w, n, u)
     tot = p.sum(axis=1)
     assert np.allclose(tot, [w, 0, 0, 0], atol=1e-9 * w)
@@ -56,11 +69,11 @@ def test_rambo_massless(n):
 def test_rambo_flat_distributions():
     """n=2: isotropic; n=3: flat Dalitz plot, <x_i> = 2/3, <x_i^2> = 1/2 (x = 2E/w)."""
     N = 40000
-    u = ps.uniforms(2, np.arange(N), np.zeros(N), 2)
+    u = ps.uniforms(2, np.arange(N), np.zeros(N), 8)
     p, _ = ps.rambo_massless(500.0, 2, u)
     c = p[:, 0, 3] / p[:, 0, 0]
     assert abs(c.mean()) < 0.02 and abs((c * c).mean() - 1 / 3) < 0.01
-    u = ps.uniforms(3, np.arange(N), np.zeros(N), 3)
+    u = ps.uniforms(3, np.arange(N), np.zeros(N), 12)
     p, _ = ps.rambo_massless(500.0, 3, u)
     x = 2 * p[:, :, 0] / 500.0
     assert np.allclose(x.mean(axis=0), 2 / 3, atol=0.01)
@@ -69,7 +82,7 @@ def test_rambo_flat_distributions():
 
 def test_rambo_massive():
     w = 1000.0
-    u = ps.uniforms(4, np.arange(200), np.zeros(200), 2)
+    u = ps.uniforms(4, np.arange(200), np.zeros(200), 8)
     m1, m2 = 125.0, 300.0
     p, wt = ps.rambo_massive(w, [m1, m2], u)
     assert np.allclose(p.sum(axis=1), [w, 0, 0, 0], atol=1e-9 * w)
@@ -79,7 +92,7 @@ def test_rambo_massive():
     assert np.allclose(wt, k / (4 * math.pi * w), rtol=1e-12)
     # three massive bodies: volume against direct two-step integration
     N = 200000
-    u = ps.uniforms(5, np.arange(N), np.zeros(N), 3)
+    u = ps.uniforms(5, np.arange(N), np.zeros(N), 12)
     ms = [125.0, 125.0, 0.0]
     p, wt = ps.rambo_massive(w, ms, u)
     vol_mc = wt.mean()
@@ -107,7 +120,7 @@ def test_breit_wigner_jacobian():
 
 def test_ttbar_chain_kinematics():
     N = 2000
-    u = ps.uniforms(2, np.arange(N), np.zeros(N), 4)
+    u = ps.uniforms(2, np.arange(N), np.zeros(N), 16)
     P, wt, ok, shat = ps.ttbar_dilepton(u, PAR, (400.0, 2000.0))
     P, wt, shat = P[ok], wt[ok], shat[ok]
     assert ok.mean() > 0.5
@@ -166,7 +179,7 @@ def test_mc_estimate_two_body_closed_form():
 
 
 def test_per_event_massive_rambo_matches_rambo_massive():
-    u = ps.uniforms(5, np.arange(500), np.zeros(500), 3)
+    u = ps.uniforms(5, np.arange(500), np.zeros(500), 12)
     masses = [125.0, 0.0, 30.0]
     p1, w1 = ps.rambo_massive(1000.0, masses, u)
     p2, w2 = ps.rambo_massive_events(1000.0, np.tile(masses, (500, 1)), u)
@@ -177,7 +190,7 @@ def test_resonance_generator_kinematics():
     """App. A.2 resonance mapping: momentum conservation, massless particles, the pair mass in the
     Breit-Wigner window of Eq. 16."""
     m, g = 80.4, 2.085
-    u = ps.uniforms(6, np.arange(4000), np.zeros(4000), 4)
+    u = ps.uniforms(6, np.arange(4000), np.zeros(4000), 16)
     pf, wt, ok = ps.rambo_resonance(1000.0, 4, m, g, u)
     assert ok.all() and np.all(wt > 0)
     tot = pf.sum(axis=1)
@@ -204,10 +217,10 @@ def test_resonance_generator_factorises_phase_space(shape):
         f = (m * g) ** 2 / ((s - m * m) ** 2 + (m * g) ** 2) if shape == "breit-wigner" else np.ones_like(s)
         return np.where(inside, f, 0.0)
 
-    u = ps.uniforms(7, np.arange(n), np.zeros(n), nf)
+    u = ps.uniforms(7, np.arange(n), np.zeros(n), 4 * nf)
     pf, wt, ok = ps.rambo_resonance(w, nf, m, g, u)
     a = np.where(ok, wt, 0.0) * integrand(pf)
-    u2 = ps.uniforms(8, np.arange(n), np.zeros(n), nf)
+    u2 = ps.uniforms(8, np.arange(n), np.zeros(n), 4 * nf)
     p2, w2 = ps.rambo_massless(w, nf, u2)
     b = w2 * integrand(p2)
     ma, ea = a.mean(), a.std() / math.sqrt(n)
