@@ -141,7 +141,9 @@ me_status me_eval_host(me_handle h, const double *momenta, int64_t n, double *ou
 
 /* Phase-space points only: for events counter_offset .. counter_offset+n-1,
  * draw with Philox4x64-10 (counter = (event, attempt, block, 0), key =
- * (seed, 0)) until the cuts pass.  Outputs (device, any may be NULL):
+ * (seed, 0); each 64-bit word gives two uniforms (w + 1/2) 2^-32 of its 32-bit
+ * halves, low half first: uniform i of a draw is half i % 2 of word
+ * (i % 8) / 2 of block i / 8) until the cuts pass.  Outputs (device, any may be NULL):
  * momenta (n_ext * 4 * n, layout above), weight (n: phase-space weight),
  * shat (n), tries (n: draws used).  Asynchronous on stream.  A point that
  * exhausts kin->max_attempts is reported by the next synchronising call on

@@ -135,51 +135,13 @@ DF_HD df from_double(double x) {
   return df{hi, lo};
 }
 
-// Exact FP32 value of a 23-bit unsigned integer without a conversion
-// instruction: 2^23 + c has the bit pattern 0x4B000000 | c.
-DF_HD float u23_to_float(uint32_t c) {
-  const uint32_t b = 0x4B000000u | c;
-  float f;
-  memcpy(&f, &b, 4);
-  return df_sub_rn(f, 8388608.0f);
-}
-
-// Uniform deviate ((x >> 11) + 1/2) 2^-53 as a double-float from integer and
-// FP32 operations only: k = x >> 11 (53 bits) = c2 2^46 + c1 2^23 + c0 with
-// 7-, 23- and 23-bit pieces, each converted exactly; relative error < 2^-48.
-DF_HD df unit_df_pieces(uint64_t x) {
-  const uint64_t k = x >> 11;
-  const float c2 = u23_to_float((uint32_t)(k >> 46));
-  const float c1 = u23_to_float((uint32_t)(k >> 23) & 0x7fffffu);
-  const float c0 = u23_to_float((uint32_t)k & 0x7fffffu);
-  const df hi = two_sum(c2 * 0x1p-7f, c1 * 0x1p-30f);
-  return hi + (c0 + 0.5f) * 0x1p-53f;
-}
-
-// The same deviate with fewer operations: u = y 2^-64 exactly, y = x with its
-// bits 10..0 replaced by 10000000000b.  With the leading one of y moved to bit 63
-// (count of leading zeros lz), hi is the leading 24 bits with its exponent
-// 2^(-1-lz) set directly, lo the remaining bits (at most 30 significant, all in
-// bits 39..8) converted with one rounding and scaled by 2^(-56-lz); FastTwoSum
-// renormalises the pair (hi is truncated, so 0 <= lo < ulp(hi)).  Relative error
-// < 2^-48.  The high word of y is zero with probability 2^-32: unit_df_pieces.
-DF_HD df unit_df(uint64_t x) {
-#ifdef __CUDA_ARCH__
-  const uint64_t y = (x & ~0x7ffull) | 0x400ull;
-  const uint32_t yh = (uint32_t)(y >> 32);
-  if (yh == 0u) return unit_df_pieces(x);
-  const int lz = __clz((int)yh);
-  const uint64_t nrm = y << lz;
-  const uint32_t hb = ((uint32_t)(126 - lz) << 23) | ((uint32_t)(nrm >> 40) & 0x7fffffu);
-  const uint32_t sb = (uint32_t)(71 - lz) << 23;  // 2^(-56-lz)
-  float hi, sc;
-  memcpy(&hi, &hb, 4);
-  memcpy(&sc, &sb, 4);
-  const float lo = df_mul_rn(__uint2float_rn((uint32_t)(nrm >> 8)), sc);
+// Uniform deviate (w + 1/2) 2^-32 of a 32-bit word as an exact double-float: hi
+// = the top 24 bits (w with its low 8 bits cleared, exact in FP32), lo = the low
+// 8 bits plus 1/2; FastTwoSum normalises the pair (|hi| >= |lo| or hi = 0).
+DF_HD df unit_df32(uint32_t w) {
+  const float hi = (float)(w & 0xffffff00u) * 0x1p-32f;
+  const float lo = ((float)(w & 0xffu) + 0.5f) * 0x1p-32f;
   return fast_two_sum(hi, lo);
-#else
-  return unit_df_pieces(x);
-#endif
 }
 
 // ---------------------------------------------------------------------------

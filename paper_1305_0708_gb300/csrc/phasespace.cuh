@@ -2,8 +2,10 @@
 //
 // Random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), one
 // counter per (event, attempt, block): counter = (event, attempt, block, 0),
-// key = (seed, 0), ten rounds with the Weyl key schedule; a 64-bit word x
-// maps to ((x >> 11) + 1/2) 2^-53 in (0, 1).
+// key = (seed, 0), ten rounds with the Weyl key schedule.  Each 64-bit word
+// gives two 32-bit deviates w (low half first), mapped to (w + 1/2) 2^-32 in
+// (0, 1), as the paper's generator delivers 32-bit deviates (App. B): uniform i
+// of a draw is half i % 2 of word (i % 8) / 2 of block i / 8.
 //
 // Generators: two-body at fixed sqrt(s) with cos(theta), phi uniform;
 // massless RAMBO (Kleiss, Stirling, Ellis 1986) with the massive rescaling;
@@ -66,9 +68,8 @@ struct Philox {
   }
 };
 
-__host__ __device__ __forceinline__ double to_unit(uint64_t x) {
-  return ((double)(x >> 11) + 0.5) * 0x1p-53;
-}
+__host__ __device__ __forceinline__ double unit32(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+__host__ __device__ __forceinline__ uint32_t half32(uint64_t x, int h) { return (uint32_t)(h ? x >> 32 : x); }
 
 // ---------------------------------------------------------------------------
 // Adaptive grid (VEGAS, Lepage 1978) over the generator's uniforms: in
@@ -101,17 +102,16 @@ __host__ __device__ __forceinline__ df vg_map_df(const KinDev& kin, int d, df y,
   return lo + (t + (float)(-i)) * w;
 }
 
-// uniforms u[4*nb] for (event, attempt)
-template <int NB>
-__host__ __device__ __forceinline__ void draw_uniforms(uint64_t seed, uint64_t event, uint64_t attempt, double (&u)[4 * NB]) {
+// uniforms u[NU] for (event, attempt)
+template <int NU>
+__host__ __device__ __forceinline__ void draw_uniforms(uint64_t seed, uint64_t event, uint64_t attempt, double (&u)[NU]) {
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
+  for (int j = 0; j < (NU + 7) / 8; ++j) {
     uint64_t o[4];
     Philox::block(event, attempt, (uint64_t)j, 0ull, seed, 0ull, o);
-    u[4 * j + 0] = to_unit(o[0]);
-    u[4 * j + 1] = to_unit(o[1]);
-    u[4 * j + 2] = to_unit(o[2]);
-    u[4 * j + 3] = to_unit(o[3]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (8 * j + q < NU) u[8 * j + q] = unit32(half32(o[q / 2], q & 1));
   }
 }
 
@@ -449,15 +449,15 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
   double jac = 1.0;
   const int kind = KIND == kKindAny ? kin.kind : KIND == kKindRamboMassive ? ME_PS_RAMBO : KIND;
   if (kind == ME_PS_TWO_BODY) {
-    double u[4];
-    draw_uniforms<1>(seed, event, (uint64_t)att, u);
+    double u[2];
+    draw_uniforms<2>(seed, event, (uint64_t)att, u);
 #pragma unroll
-    for (int d = 0; d < 4; ++d)  // compile-time indices keep u in registers
+    for (int d = 0; d < 2; ++d)  // compile-time indices keep u in registers
       if (bins && d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
     ok = gen_two_body<NEXT>(kin, u, p, wps, shat);
   } else if (kind == ME_PS_RAMBO || kind == ME_PS_RAMBO_BW) {
     double u[4 * (NEXT - 2)];
-    draw_uniforms<NEXT - 2>(seed, event, (uint64_t)att, u);
+    draw_uniforms<4 * (NEXT - 2)>(seed, event, (uint64_t)att, u);
 #pragma unroll
     for (int d = 0; d < 4 * (NEXT - 2); ++d)
       if (bins && d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
@@ -466,7 +466,7 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
     else ok = false;
   } else {
     double u[16];
-    draw_uniforms<4>(seed, event, (uint64_t)att, u);
+    draw_uniforms<16>(seed, event, (uint64_t)att, u);
 #pragma unroll
     for (int d = 0; d < 16; ++d)
       if (bins && d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
@@ -491,11 +491,13 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
   p[0][0] = hw; p[0][1] = z; p[0][2] = z; p[0][3] = hw;
   p[1][0] = hw; p[1][1] = z; p[1][2] = z; p[1][3] = -hw;
   df Q0 = z, Q1 = z, Q2 = z, Q3 = z;
+  uint64_t o[4];  // Philox block k / 2: uniforms 4k .. 4k+3 are words 2 (k % 2) and 2 (k % 2) + 1
 #pragma unroll 1  // one copy of the per-particle code: the unrolled form overflows the instruction cache
   for (int k = 0; k < NF; ++k) {
-    uint64_t o[4];
-    Philox::block(event, (uint64_t)att, (uint64_t)k, 0ull, seed, 0ull, o);
-    df u0 = unit_df(o[0]), u1 = unit_df(o[1]), u2 = unit_df(o[2]), u3 = unit_df(o[3]);
+    if ((k & 1) == 0) Philox::block(event, (uint64_t)att, (uint64_t)(k >> 1), 0ull, seed, 0ull, o);
+    const uint64_t wa = (k & 1) ? o[2] : o[0], wb = (k & 1) ? o[3] : o[1];
+    df u0 = unit_df32((uint32_t)wa), u1 = unit_df32((uint32_t)(wa >> 32));
+    df u2 = unit_df32((uint32_t)wb), u3 = unit_df32((uint32_t)(wb >> 32));
     if (bins) {
       u0 = vg_map_df(kin, 4 * k + 0, u0, jac, bins);
       u1 = vg_map_df(kin, 4 * k + 1, u1, jac, bins);
@@ -758,14 +760,12 @@ __host__ __device__ __forceinline__ bool ttbar_df(const KinDev& kin, uint64_t se
     return false;
   } else {
     df u[16];
-#pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
       uint64_t o[4];
       Philox::block(event, (uint64_t)att, (uint64_t)j, 0ull, seed, 0ull, o);
-      u[4 * j + 0] = unit_df(o[0]);
-      u[4 * j + 1] = unit_df(o[1]);
-      u[4 * j + 2] = unit_df(o[2]);
-      u[4 * j + 3] = unit_df(o[3]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) u[8 * j + q] = unit_df32(half32(o[q / 2], q & 1));
     }
 #pragma unroll
     for (int d = 0; d < 16; ++d)
@@ -841,8 +841,10 @@ __host__ __device__ __forceinline__ bool rambo_bw_df(const KinDev& kin, uint64_t
                                                      df (&p)[NEXT][4], double& wps, df& jac, uint8_t* bins) {
   constexpr int NR = NEXT - 3;
   uint64_t o[4];
-  Philox::block(event, (uint64_t)att, (uint64_t)NR, 0ull, seed, 0ull, o);
-  df ub = unit_df(o[0]), ud0 = unit_df(o[1]), ud1 = unit_df(o[2]);
+  // uniforms 4 NR, 4 NR + 1, 4 NR + 2: block NR / 2, words 2 (NR % 2) and 2 (NR % 2) + 1
+  Philox::block(event, (uint64_t)att, (uint64_t)(NR / 2), 0ull, seed, 0ull, o);
+  constexpr int WB = 2 * (NR % 2);
+  df ub = unit_df32((uint32_t)o[WB]), ud0 = unit_df32((uint32_t)(o[WB] >> 32)), ud1 = unit_df32((uint32_t)o[WB + 1]);
   if (bins) {
     ub = vg_map_df(kin, 4 * NR, ub, jac, bins);
     ud0 = vg_map_df(kin, 4 * NR + 1, ud0, jac, bins);
