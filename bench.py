@@ -289,6 +289,19 @@ def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
                                         "frac_above_1e-3": float((rel > 1e-3).double().mean().item()),
                                         "sum_me2": float(((mmx[ok].sum() - m64[ok].sum()) / m64[ok].sum()).abs()),
                                         "points": int(ok.sum().item())}
+                # conditioning of the points above 1e-3: how far the FP64 program itself moves when
+                # its input momenta are rounded to FP32 (what any FP32-wavefunction evaluation sees)
+                bad = torch.nonzero(ok & ((mmx - m64).abs() > 1e-3 * m64.abs())).flatten()[:64]
+                if bad.numel():
+                    nb = int(bad.numel())
+                    mb = mom.view(info.n_ext * 4, n)[:, bad].float().double().contiguous()
+                    o64 = torch.empty(nb, dtype=torch.float64, device=dev)
+                    B.me_eval(h, mb, nb, o64, stream)
+                    torch.cuda.synchronize(dev)
+                    shift = ((o64 - m64[bad]).abs() / m64[bad]).cpu().tolist()
+                    err = ((mmx[bad] - m64[bad]).abs() / m64[bad]).cpu().tolist()
+                    row["mixed_rel_err"]["above_1e-3"] = [{"mixed_err": e_, "fp64_shift_at_fp32_inputs": s_}
+                                                         for e_, s_ in zip(err, shift)]
             B.me_destroy(h)
         row["mixed_over_fp64"] = row["mixed"]["evals_per_s"] / row["fp64"]["evals_per_s"]
         table[key] = row
