@@ -477,20 +477,27 @@ def main():
         torch.cuda.synchronize(dev)
 
     def time_steps(h, steps, warmup):
-        acc = B.me_xsec_acc()
+        """Steps queued back to back with xsec_step_async (sums accumulated on the device, read
+        once at the end); each step bracketed by CUDA events on the launch stream, the L2 flush
+        between steps outside the brackets."""
+        acc_dev = torch.zeros(4, dtype=torch.float64, device=dev)
         for s in range(warmup):
-            B.xsec_step(h, w["seed"], offset0 + s * n, n, kin, stream, acc)
+            B.xsec_step_async(h, w["seed"], offset0 + s * n, n, kin, acc_dev, stream)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
         t0 = time.perf_counter()
         for s in range(steps):
             flush.zero_()
             ev[s][0].record(stream)
-            B.xsec_step(h, w["seed"], offset0 + (warmup + s) * n, n, kin, stream, acc)
+            B.xsec_step_async(h, w["seed"], offset0 + (warmup + s) * n, n, kin, acc_dev, stream)
             ev[s][1].record(stream)
         barrier()
         wall = time.perf_counter() - t0
         ms = [a.elapsed_time(b) for a, b in ev]
+        a = acc_dev.cpu().tolist()
+        if a[3] != 0:
+            raise RuntimeError("a point exhausted its phase-space redraws")
+        acc = B.me_xsec_acc(sum_w=a[0], sum_w2=a[1], n_acc=(warmup + steps) * n, n_try=int(round(a[2])))
         return ms, wall, acc
 
     clocks = Clocks()

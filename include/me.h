@@ -161,6 +161,19 @@ me_status me_generate(me_handle h, uint64_t seed, uint64_t counter_offset, int64
 me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept, const me_kin *kin,
                     void *stream, me_xsec_acc *acc, double *me2_out, double *momenta_out);
 
+/* xsec_step without a host synchronisation, for back-to-back steps: the
+ * step's sums are added on the device, after its kernels and in the same fixed
+ * order as xsec_step, to acc_dev[0..3] = (sum of weights in pb, sum of squared
+ * weights, draws, number of steps in which a point exhausted its redraws).
+ * acc_dev: device memory, 4 doubles, caller-owned and initialised (zeros for a
+ * new estimate); n_acc is the sum of the steps' n_accept.  Returns once the
+ * work is queued on stream; argument errors return synchronously, a device
+ * error at the next synchronising call.  Steps on one handle share its
+ * workspace and must be queued on one stream (or otherwise ordered).  The
+ * per-kernel timing of me_step_timing does not apply. */
+me_status xsec_step_async(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept,
+                          const me_kin *kin, void *stream, double *acc_dev);
+
 /* xsec_step for callers that cannot allocate device memory: the same
  * computation and arguments, but the step's scratch (per-block partial sums,
  * totals, status flag) lives in a fixed array compiled into the library

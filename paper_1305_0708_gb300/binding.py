@@ -71,7 +71,7 @@ class me_server_stats(ctypes.Structure):
 ME_FP64, ME_MIXED = 0, 1
 ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR, ME_PS_RAMBO_BW = 0, 1, 2, 3
 
-EXPORTS = ["me_create", "me_eval", "me_eval_host", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
+EXPORTS = ["me_create", "me_eval", "me_eval_host", "me_generate", "xsec_step", "xsec_step_async", "xsec_step_noalloc", "me_step_timing",
            "me_xsec_estimate", "me_info", "me_n_processes", "me_process_name", "me_destroy", "me_last_error",
            "me_server_create", "me_server_warm", "me_server_submit", "me_server_poll", "me_server_wait",
            "me_server_get_stats", "me_server_destroy", "me_grid_create", "me_grid_info", "me_grid_get_edges",
@@ -98,6 +98,7 @@ def load(path=None):
     L.me_eval_host.argtypes = [vp, vp, i64, vp, vp]
     L.me_generate.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, vp, vp, vp, vp]
     L.xsec_step.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc), vp, vp]
+    L.xsec_step_async.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, vp]
     L.xsec_step_noalloc.argtypes = [vp, u64, u64, i64, ctypes.POINTER(me_kin), vp, ctypes.POINTER(me_xsec_acc),
                                     vp, vp]
     L.me_step_timing.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -131,7 +132,7 @@ def load(path=None):
     L.me_grid_destroy.argtypes = [vp]
     L.me_grid_destroy.restype = None
     L.me_vegas_refine_edges.argtypes = [vp, vp, i32, i32, ctypes.c_double, vp]
-    for fn in ("me_create", "me_eval", "me_eval_host", "me_generate", "xsec_step", "xsec_step_noalloc", "me_step_timing",
+    for fn in ("me_create", "me_eval", "me_eval_host", "me_generate", "xsec_step", "xsec_step_async", "xsec_step_noalloc", "me_step_timing",
                "me_xsec_estimate", "me_info", "me_server_create", "me_server_warm", "me_server_submit",
                "me_server_poll", "me_server_wait", "me_server_get_stats", "me_grid_create", "me_grid_info",
                "me_grid_get_edges", "me_grid_set_edges", "me_grid_get_hist", "me_grid_clear_hist",
@@ -214,6 +215,12 @@ def xsec_step(h, seed, counter_offset, n_accept, kin, stream=None, acc=None, me2
     _check(load().xsec_step(h, seed, counter_offset, n_accept, ctypes.byref(kin), _stream(stream),
                             ctypes.byref(acc), _ptr(me2_out), _ptr(momenta_out)))
     return acc
+
+
+def xsec_step_async(h, seed, counter_offset, n_accept, kin, acc_dev, stream=None):
+    """xsec_step adding its sums to acc_dev (device, 4 doubles) without a host synchronisation."""
+    _check(load().xsec_step_async(h, seed, counter_offset, n_accept, ctypes.byref(kin), _stream(stream),
+                                  _ptr(acc_dev)))
 
 
 def xsec_step_noalloc(h, seed, counter_offset, n_accept, kin, stream=None, acc=None, me2_out=None,

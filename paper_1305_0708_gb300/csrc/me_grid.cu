@@ -238,7 +238,7 @@ me_status xsec_step_grid(me_handle h, me_grid g, uint64_t seed, uint64_t counter
   k.vg_bins = g->bins;
   k.vg_edges = g->d_edges;
   k.wfactor = 0.0;  // the Jacobian makes every weight differ
-  return me::rt::run_step(h, k, seed, counter_offset, n_accept, stream, acc, me2_out, momenta_out, g);
+  return me::rt::run_step(h, k, seed, counter_offset, n_accept, stream, acc, me2_out, momenta_out, g, nullptr);
 }
 
 me_status me_vegas_refine_edges(const double* edges, const double* hist, int32_t n_dims, int32_t n_bins, double alpha,

@@ -143,6 +143,40 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int nbloc
 namespace me {
 namespace rt {
 
+// Asynchronous steps: the same fixed-order reduction, added to a caller's device accumulator
+// (sum w, sum w^2, tries, steps with an exhausted point); the status word is consumed.
+__global__ void k_reduce_partials_add(const double* __restrict__ partials, int nblocks, double* __restrict__ acc,
+                                      int* __restrict__ status) {
+  __shared__ double sm[3][256];
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    s0 += partials[3 * b + 0];
+    s1 += partials[3 * b + 1];
+    s2 += partials[3 * b + 2];
+  }
+  sm[0][threadIdx.x] = s0;
+  sm[1][threadIdx.x] = s1;
+  sm[2][threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sm[0][threadIdx.x] += sm[0][threadIdx.x + o];
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + o];
+      sm[2][threadIdx.x] += sm[2][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    acc[0] += sm[0][0];
+    acc[1] += sm[1][0];
+    acc[2] += sm[2][0];
+    if (*status) {
+      acc[3] += 1.0;
+      *status = 0;
+    }
+  }
+}
+
 cudaError_t launch_reduce(const double* partials, int nblocks, double* acc, cudaStream_t s) {
   k_reduce_partials<<<1, 256, 0, s>>>(partials, nblocks, acc);
   return cudaGetLastError();
@@ -330,7 +364,7 @@ namespace me {
 namespace rt {
 
 me_status run_step(me_handle h, KinDev& k, uint64_t seed, uint64_t counter_offset, int64_t n_accept, void* stream,
-                   me_xsec_acc* acc, double* me2_out, double* momenta_out, GridHook* grid) {
+                   me_xsec_acc* acc, double* me2_out, double* momenta_out, GridHook* grid, double* acc_dev) {
   me_status st;
   if (n_accept == 0) return ME_OK;
   std::lock_guard<std::mutex> lock(h->mu);
@@ -346,16 +380,17 @@ me_status run_step(me_handle h, KinDev& k, uint64_t seed, uint64_t counter_offse
   for (int64_t c = 0; c < nchunks; ++c) {
     const int64_t first = c * kChunk;
     const int64_t m = std::min<int64_t>(kChunk, n_accept - first);
-    if (h->timing) cudaEventRecord(h->ev[0], s);
+    if (h->timing && !acc_dev) cudaEventRecord(h->ev[0], s);
     me::StepArgs a{seed, counter_offset + (uint64_t)first, m, h->d_ws, h->d_status,
                    h->d_partials + 3 * (size_t)grid_me * c, grid_me, me2_out ? me2_out + first : nullptr,
                    momenta_out ? momenta_out + first : nullptr, n_accept,
                    grid ? grid->idx : nullptr, grid ? grid->w : nullptr};
-    e = h->desc->launch_step(h->prec, &k, &a, h->cvals.data(), s, grid_ps, grid_me, h->timing ? h->ev[1] : nullptr);
+    e = h->desc->launch_step(h->prec, &k, &a, h->cvals.data(), s, grid_ps, grid_me,
+                             h->timing && !acc_dev ? h->ev[1] : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "xsec_step launch");
     if (grid && (e = launch_vg_hist(m, grid->dims, grid->bins, grid->idx, grid->w, grid->hist, s)) != cudaSuccess)
       return cuda_fail(e, "grid histogram");
-    if (h->timing) {
+    if (h->timing && !acc_dev) {
       cudaEventRecord(h->ev[2], s);
       if ((e = cudaEventSynchronize(h->ev[2])) != cudaSuccess) return cuda_fail(e, "xsec_step timing");
       float a = 0, b = 0;
@@ -364,6 +399,11 @@ me_status run_step(me_handle h, KinDev& k, uint64_t seed, uint64_t counter_offse
       h->t_ps += a;
       h->t_me += b;
     }
+  }
+  if (acc_dev) {  // asynchronous: the sums stay on the device
+    k_reduce_partials_add<<<1, 256, 0, s>>>(h->d_partials, (int)(grid_me * nchunks), acc_dev, h->d_status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "xsec_step_async reduce");
+    return ME_OK;
   }
   k_reduce_partials<<<1, 256, 0, s>>>(h->d_partials, (int)(grid_me * nchunks), h->d_acc);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "xsec_step reduce");
@@ -526,7 +566,23 @@ me_status xsec_step(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t
   if (n_accept < 0) return fail(ME_ERR_ARG, "xsec_step: n_accept < 0");
   me::KinDev k;
   if ((st = make_kin(h, kin, k)) != ME_OK) return st;
-  return me::rt::run_step(h, k, seed, counter_offset, n_accept, stream, acc, me2_out, momenta_out, nullptr);
+  return me::rt::run_step(h, k, seed, counter_offset, n_accept, stream, acc, me2_out, momenta_out, nullptr, nullptr);
+}
+
+me_status xsec_step_async(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept, const me_kin* kin,
+                          void* stream, double* acc_dev) {
+  me_status st = check_handle(h);
+  if (st != ME_OK) return st;
+  if (!kin || !acc_dev) return fail(ME_ERR_ARG, "xsec_step_async: null argument");
+  if (n_accept < 0) return fail(ME_ERR_ARG, "xsec_step_async: n_accept < 0");
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, acc_dev);
+  if (e != cudaSuccess) return cuda_fail(e, "xsec_step_async: cudaPointerGetAttributes");
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(ME_ERR_ARG, "xsec_step_async: acc_dev is not device memory");
+  me::KinDev k;
+  if ((st = make_kin(h, kin, k)) != ME_OK) return st;
+  return me::rt::run_step(h, k, seed, counter_offset, n_accept, stream, nullptr, nullptr, nullptr, nullptr, acc_dev);
 }
 
 me_status xsec_step_noalloc(me_handle h, uint64_t seed, uint64_t counter_offset, int64_t n_accept,

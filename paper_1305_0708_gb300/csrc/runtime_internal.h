@@ -67,8 +67,9 @@ struct GridHook {
 cudaError_t launch_vg_hist(int64_t m, int dims, int bins, const uint8_t* idx, const double* w, double* hist,
                            cudaStream_t s);
 // one Monte Carlo step of n_accept points in chunks (xsec_step, and with a grid xsec_step_grid)
+// acc_dev != nullptr: asynchronous step, sums added on the device to acc_dev (no host sync)
 me_status run_step(me_handle h, KinDev& k, uint64_t seed, uint64_t counter_offset, int64_t n_accept, void* stream,
-                   me_xsec_acc* acc, double* me2_out, double* momenta_out, GridHook* grid);
+                   me_xsec_acc* acc, double* me2_out, double* momenta_out, GridHook* grid, double* acc_dev);
 
 }  // namespace rt
 }  // namespace me

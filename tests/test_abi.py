@@ -61,6 +61,7 @@ def test_argument_errors_before_device_work(lib):
     assert "not compiled" in binding.me_last_error()
     assert lib.me_eval(None, None, 4, None, None) == -1
     assert lib.me_eval_host(None, None, 4, None, None) == -1
+    assert lib.xsec_step_async(None, 0, 0, 1, None, None, None) == -1
     assert lib.me_info(None, None) == -1
 
 

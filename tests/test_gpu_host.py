@@ -79,3 +79,27 @@ def test_host_entry_argument_errors(B):
         B.me_eval_host(h, np.zeros(16).ctypes.data, 0, np.zeros(1).ctypes.data)  # n = 0: no-op
     finally:
         B.me_destroy(h)
+
+
+@pytest.mark.parametrize("key,n,steps", [("udx_epvegg", 50000, 3), ("gg_ttx_dilep", (1 << 20) + 4097, 1)])
+def test_async_steps_equal_synchronous_steps(B, key, n, steps):
+    """xsec_step_async adds each step's fixed-order sums on the device: after the same steps the
+    device accumulator equals the host accumulator of xsec_step exactly."""
+    from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args
+    w = WORKLOADS[key]
+    kin = B.make_kin(**kin_args(w))
+    h = B.me_create(w["process"], None, B.ME_MIXED)
+    try:
+        acc = B.me_xsec_acc()
+        for s in range(steps):
+            B.xsec_step(h, w["seed"], s * n, n, kin, None, acc)
+        acc_dev = torch.zeros(4, dtype=torch.float64, device="cuda")
+        for s in range(steps):
+            B.xsec_step_async(h, w["seed"], s * n, n, kin, acc_dev)
+        torch.cuda.synchronize()
+        a = acc_dev.cpu().numpy()
+        assert a[0] == acc.sum_w and a[1] == acc.sum_w2 and a[2] == acc.n_try and a[3] == 0.0
+        with pytest.raises(B.MeError):
+            B.xsec_step_async(h, w["seed"], 0, 10, kin, np.zeros(4).ctypes.data)  # host accumulator
+    finally:
+        B.me_destroy(h)
