@@ -35,8 +35,8 @@ PS_FLOPS_PER_DRAW = {"rambo": 2700.0}
 # DRAM bytes per point of the mixed-path kernels (dram__bytes_read.sum + dram__bytes_write.sum of one
 # ncu capture, divided by the points of that launch; profiles/ holds the captures).  A launch's
 # traffic is this times its points: the kernels stream their points, so traffic grows in proportion.
-TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (85.252352e6 + 282.218496e6) / 2 ** 20,
-                     ("udx_epvegg", "k_me"): (214.010368e6 + 3.701248e6) / 2 ** 20,
+TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (85.422592e6 + 282.576896e6) / 2 ** 20,
+                     ("udx_epvegg", "k_me"): (214.007552e6 + 3.591424e6) / 2 ** 20,
                      ("gg_gggg", "k_me"): (3.478784e6 + 0.07552e6) / 16384}
 
 SM_COUNT = 152
