@@ -65,6 +65,7 @@ class _Emitter:
         self.cpl_names = set()
         self.mx_masses = {}       # mixed path: mass parameter -> width parameter of its resonant lines
         self.half = {}            # spinor variable -> set of halves ("u", "l") that can be non-zero
+        self.pv = set()           # massless external vectors carried as me::PV (zero time, real z component)
 
     def emit(self, s):
         self.lines.append(s)
@@ -216,9 +217,12 @@ class _Emitter:
                 self.emit(f"  const me::W4<R> {name} = me::ext_row_massless<R>(r{nid}, {h}, {inc});")
                 self.half[name] = frozenset("l" if chi == "L" else "u")
             self.flops32 += 12
+        elif part.is_vector and part.massless:
+            self.emit(f"  const me::PV<R> {name} = me::ext_pol<R>(r{nid}, {h}, {inc});")
+            self.pv.add(name)
+            self.flops32 += 25
         elif part.is_vector:
-            mass = "R(0)" if part.massless else f"(R){self.cpl(part.mass)}"
-            self.emit(f"  const me::W4<R> {name} = me::ext_vector<R>(r{nid}, {h}, {inc}, {mass});")
+            self.emit(f"  const me::W4<R> {name} = me::ext_vector<R>(r{nid}, {h}, {inc}, (R){self.cpl(part.mass)});")
             self.flops32 += 25
         else:
             self.emit(f"  const me::cx<R> {name} = me::mk(R(1), R(0));")
@@ -265,9 +269,11 @@ class _Emitter:
                     E(f"  const me::W4<R> {name} = me::prop_row<R, {_tag(hx)}>(me::ffv_row<R, {_tag(hin)}>("
                       f"{fk[2]}, {vk[2]}, {cargs}), me::neg(k{nid}), {m}, inv{nid});")
                 self.half[name] = _flip(hx) if part.massless else frozenset("ul")
-                # per non-zero half: vertex 40 (sigma matrix 8, two components of 16); propagator
-                # 24 with the real reciprocal of a massless line, 32 with a complex one, plus the mass term
-                self.flops32 += (40 + (24 if part.massless else 32)) * len(hx) + 2 + (32 if not part.massless else 0)
+                # per non-zero half: vertex 40 (sigma matrix 8, two components of 16; 28 with a PV
+                # vector); propagator 24 with the real reciprocal of a massless line, 32 with a complex
+                # one, plus the mass term
+                vtx = 28 if vk[2] in self.pv else 40
+                self.flops32 += (vtx + (24 if part.massless else 32)) * len(hx) + 2 + (32 if not part.massless else 0)
             else:
                 rk = [k for k in kids if k[1] == 0][0]
                 ck = [k for k in kids if k[1] == 1][0]
@@ -286,7 +292,7 @@ class _Emitter:
             a, b = kids
             E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::vvv_current<R>({a[2]}, k{a[0]}, {b[2]}, k{b[0]}, "
               f"(R){g}), k{nid}, inv{nid}, false, me::mk(R(0), R(0)));")
-            self.flops32 += 150 + 8
+            self.flops32 += self._vvv_current_flops(a[2], b[2]) + 8
         elif v.kind == "VVVV":
             g = self.cpl(v.couplings[0])
             slot = {s: nm for _, s, nm in kids}
@@ -326,6 +332,12 @@ class _Emitter:
         else:
             raise NotImplementedError(v.kind)
 
+    def _vvv_current_flops(self, v1, v2):
+        """vvv_current: 154 flops for two W4 vectors; a PV operand saves 30 (its zero time and real z
+        components in V1.V2, in its momentum contraction and in the output combination), two save 51."""
+        npv = int(v1 in self.pv) + int(v2 in self.pv)
+        return 150 - (0, 30, 51)[npv]
+
     def _v4_term(self, o, pairs, slot):
         """Current of sum over pairs structure g_{ab} g_{cd} with slot o open."""
         (a, b), (c, d) = pairs
@@ -351,13 +363,13 @@ class _Emitter:
             expr = (f"me::ffv_amp<R, {_tag(hr)}, {_tag(hc)}>({slot[0]}, {slot[1]}, {slot[2]}, (R){gls}, (R){grs}, "
                     f"{str(has_l).lower()}, {str(has_r).lower()})")
             nterm = int(has_l and "u" in hc and "l" in hr) + int(has_r and "l" in hc and "u" in hr)
-            self.flops32 += 40 * nterm + 16 * nterm
+            self.flops32 += (28 if slot[2] in self.pv else 40) * nterm + 16 * nterm
         elif v.kind == "VVV":
             g = self.cpl(v.couplings[0])
             k0 = [c for c, s, _ in kids if s == 0][0]
             k1 = [c for c, s, _ in kids if s == 1][0]
             expr = f"me::vvv_amp<R>({slot[0]}, k{k0}, {slot[1]}, k{k1}, {slot[2]}, (R){g})"
-            self.flops32 += 150 + 30
+            self.flops32 += self._vvv_current_flops(slot[0], slot[1]) + (18 if slot[2] in self.pv else 30)
         elif v.kind == "VVVV":
             g = self.cpl(v.couplings[0])
             (x, y), (z, w) = _PAIRINGS[a.struct]

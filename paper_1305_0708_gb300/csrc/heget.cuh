@@ -146,6 +146,37 @@ template <class R> ME_HD W4<R> ext_vector(P4<R> k, int hel, bool incoming, R mas
   return w;
 }
 
+// Transverse polarisation of a massless external vector in the helicity basis:
+// eps(+-1) above has a zero time component and a real z component.  It is
+// carried as PV (two complex and one real number), and the vertex functions
+// below take it beside W4 and skip its zero and real parts (IEEE arithmetic
+// would not let the compiler drop products with the literal zeros of a W4).
+template <class R>
+struct PV {
+  cx<R> c1, c2;
+  R c3;
+};
+
+template <class R> ME_HD PV<R> ext_pol(P4<R> k, int hel, bool incoming) {
+  const R pt2 = k.x * k.x + k.y * k.y;
+  const R pt = sqrt(pt2);
+  const R ak = sqrt(pt2 + k.z * k.z);
+  R cth, sth, cph, sph;
+  if (pt > R(0)) {
+    cth = k.z / ak; sth = pt / ak; cph = k.x / pt; sph = k.y / pt;
+  } else {
+    cth = k.z >= R(0) ? R(1) : R(-1); sth = R(0); cph = R(1); sph = R(0);
+  }
+  const R r = R(0.70710678118654752440);
+  const R l = (R)hel;
+  const R sgn = incoming ? R(1) : R(-1);
+  PV<R> w;
+  w.c1 = mk(-l * cth * cph * r, sgn * sph * r);
+  w.c2 = mk(-l * cth * sph * r, -sgn * cph * r);
+  w.c3 = l * sth * r;
+  return w;
+}
+
 // ---------------------------------------------------------------------------
 // FFV: Gamma = Vslash (gL P_L + gR P_R)
 // ---------------------------------------------------------------------------
@@ -211,9 +242,45 @@ ME_HD W4<R> ffv_row(const W4<R>& row, const W4<R>& V, R gl, R gr, bool has_l, bo
   return o;
 }
 
+// ffv_col with a PV: V.s = [[-V3, -V1+iV2], [-V1-iV2, V3]], V.sb = [[V3, V1-iV2], [V1+iV2, -V3]]
+template <class R, int H = kAll>
+ME_HD W4<R> ffv_col(const W4<R>& psi, const PV<R>& V, R gl, R gr, bool has_l, bool has_r) {
+  W4<R> o;
+  const cx<R> z = mk(R(0), R(0));
+  if (H != kUp && has_r) {
+    const cx<R> m1 = -V.c1 + mul_i(V.c2), m2 = -V.c1 - mul_i(V.c2);
+    o.c[0] = gr * ((-V.c3) * psi.c[2] + m1 * psi.c[3]);
+    o.c[1] = gr * (m2 * psi.c[2] + V.c3 * psi.c[3]);
+  } else { o.c[0] = z; o.c[1] = z; }
+  if (H != kLo && has_l) {
+    const cx<R> m1 = V.c1 - mul_i(V.c2), m2 = V.c1 + mul_i(V.c2);
+    o.c[2] = gl * (V.c3 * psi.c[0] + m1 * psi.c[1]);
+    o.c[3] = gl * (m2 * psi.c[0] + (-V.c3) * psi.c[1]);
+  } else { o.c[2] = z; o.c[3] = z; }
+  return o;
+}
+
+// ffv_row with a PV
+template <class R, int H = kAll>
+ME_HD W4<R> ffv_row(const W4<R>& row, const PV<R>& V, R gl, R gr, bool has_l, bool has_r) {
+  W4<R> o;
+  const cx<R> z = mk(R(0), R(0));
+  if (H != kUp && has_l) {
+    const cx<R> m1 = V.c1 - mul_i(V.c2), m2 = V.c1 + mul_i(V.c2);
+    o.c[0] = gl * (row.c[2] * V.c3 + row.c[3] * m2);
+    o.c[1] = gl * (row.c[2] * m1 + row.c[3] * (-V.c3));
+  } else { o.c[0] = z; o.c[1] = z; }
+  if (H != kLo && has_r) {
+    const cx<R> m1 = -V.c1 + mul_i(V.c2), m2 = -V.c1 - mul_i(V.c2);
+    o.c[2] = gr * (row.c[0] * (-V.c3) + row.c[1] * m2);
+    o.c[3] = gr * (row.c[0] * m1 + row.c[1] * V.c3);
+  } else { o.c[2] = z; o.c[3] = z; }
+  return o;
+}
+
 // row Gamma column; HR, HC: halves of the row and the column
-template <class R, int HR = kAll, int HC = kAll>
-ME_HD cx<R> ffv_amp(const W4<R>& row, const W4<R>& col, const W4<R>& V, R gl, R gr, bool has_l, bool has_r) {
+template <class R, int HR = kAll, int HC = kAll, class VV>
+ME_HD cx<R> ffv_amp(const W4<R>& row, const W4<R>& col, const VV& V, R gl, R gr, bool has_l, bool has_r) {
   const W4<R> g = ffv_col<R, HC>(col, V, gl, gr, has_l, has_r);
   // g has the half opposite to HC; only the overlap with the row contributes
   constexpr bool up = (HC != kUp) && (HR != kLo);   // g upper half (from psi_lo) meets row upper half
@@ -306,6 +373,28 @@ template <class R> ME_HD cx<R> mdot(const W4<R>& a, const W4<R>& b) {
 template <class R> ME_HD cx<R> mdot(P4<R> q, const W4<R>& b) {
   return q.e * b.c[0] - q.x * b.c[1] - q.y * b.c[2] - q.z * b.c[3];
 }
+// with a PV (time component zero, z component real)
+template <class R> ME_HD cx<R> mdot(const W4<R>& a, const PV<R>& b) {
+  return -(a.c[1] * b.c1 + a.c[2] * b.c2 + a.c[3] * b.c3);
+}
+template <class R> ME_HD cx<R> mdot(const PV<R>& a, const W4<R>& b) { return mdot(b, a); }
+template <class R> ME_HD cx<R> mdot(const PV<R>& a, const PV<R>& b) {
+  const cx<R> t = a.c1 * b.c1 + a.c2 * b.c2;
+  return mk(-(t.re + a.c3 * b.c3), -t.im);
+}
+template <class R> ME_HD cx<R> mdot(P4<R> q, const PV<R>& b) {
+  const cx<R> t = q.x * b.c1 + q.y * b.c2;
+  return mk(-(t.re + q.z * b.c3), -t.im);
+}
+
+// acc + v_mu s for component MU of a W4 or a PV (nothing for the zero time component of a PV)
+template <int MU, class R> ME_HD cx<R> add_comp(cx<R> acc, const W4<R>& v, cx<R> s) { return acc + v.c[MU] * s; }
+template <int MU, class R> ME_HD cx<R> add_comp(cx<R> acc, const PV<R>& v, cx<R> s) {
+  if constexpr (MU == 0) return acc;
+  else if constexpr (MU == 1) return acc + v.c1 * s;
+  else if constexpr (MU == 2) return acc + v.c2 * s;
+  else return acc + v.c3 * s;
+}
 
 // vector propagator numerator g^{mu nu} - q^mu q^nu / mc2 applied to X, times inv
 template <class R, class INV>
@@ -326,31 +415,42 @@ ME_HD W4<R> prop_vec(const W4<R>& X, P4<R> q, INV inv, bool massive, cx<R> inv_m
 // ---------------------------------------------------------------------------
 // VVV (all momenta incoming):  g [ g^{12}(k1-k2)^3 + g^{23}(k2-k3)^1 + g^{31}(k3-k1)^2 ]
 // ---------------------------------------------------------------------------
-template <class R> ME_HD W4<R> vvv_current(const W4<R>& V1, P4<R> k1, const W4<R>& V2, P4<R> k2, R g) {
+template <class R, class VA, class VB>
+ME_HD W4<R> vvv_current(const VA& V1, P4<R> k1, const VB& V2, P4<R> k2, R g) {
   const P4<R> k3 = {-(k1.e + k2.e), -(k1.x + k2.x), -(k1.y + k2.y), -(k1.z + k2.z)};
   const P4<R> d12 = {k1.e - k2.e, k1.x - k2.x, k1.y - k2.y, k1.z - k2.z};
   const P4<R> d23 = {k2.e - k3.e, k2.x - k3.x, k2.y - k3.y, k2.z - k3.z};
   const P4<R> d31 = {k3.e - k1.e, k3.x - k1.x, k3.y - k1.y, k3.z - k1.z};
   const cx<R> v12 = mdot(V1, V2), a = mdot(d23, V1), b = mdot(d31, V2);
   W4<R> o;
-  o.c[0] = g * (d12.e * v12 + V2.c[0] * a + V1.c[0] * b);
-  o.c[1] = g * (d12.x * v12 + V2.c[1] * a + V1.c[1] * b);
-  o.c[2] = g * (d12.y * v12 + V2.c[2] * a + V1.c[2] * b);
-  o.c[3] = g * (d12.z * v12 + V2.c[3] * a + V1.c[3] * b);
+  o.c[0] = g * add_comp<0>(add_comp<0>(d12.e * v12, V2, a), V1, b);
+  o.c[1] = g * add_comp<1>(add_comp<1>(d12.x * v12, V2, a), V1, b);
+  o.c[2] = g * add_comp<2>(add_comp<2>(d12.y * v12, V2, a), V1, b);
+  o.c[3] = g * add_comp<3>(add_comp<3>(d12.z * v12, V2, a), V1, b);
   return o;
 }
 
-template <class R> ME_HD cx<R> vvv_amp(const W4<R>& V1, P4<R> k1, const W4<R>& V2, P4<R> k2, const W4<R>& V3,
-                                       R g) {
-  return mdot(vvv_current(V1, k1, V2, k2, g), V3);
+template <class R, class VA, class VB, class VC>
+ME_HD cx<R> vvv_amp(const VA& V1, P4<R> k1, const VB& V2, P4<R> k2, const VC& V3, R g) {
+  return mdot(vvv_current<R>(V1, k1, V2, k2, g), V3);
 }
 
 // VVVV pairing current: V_p (V_a . V_b)
-template <class R> ME_HD W4<R> v4_term(const W4<R>& Vp, const W4<R>& Va, const W4<R>& Vb) {
-  const cx<R> d = mdot(Va, Vb);
+template <class R> ME_HD W4<R> vec_times(const W4<R>& v, cx<R> d) {
   W4<R> o;
-  for (int k = 0; k < 4; ++k) o.c[k] = Vp.c[k] * d;
+  for (int k = 0; k < 4; ++k) o.c[k] = v.c[k] * d;
   return o;
+}
+template <class R> ME_HD W4<R> vec_times(const PV<R>& v, cx<R> d) {
+  W4<R> o;
+  o.c[0] = mk(R(0), R(0));
+  o.c[1] = v.c1 * d;
+  o.c[2] = v.c2 * d;
+  o.c[3] = v.c3 * d;
+  return o;
+}
+template <class R, class VP, class VA, class VB> ME_HD W4<R> v4_term(const VP& Vp, const VA& Va, const VB& Vb) {
+  return vec_times<R>(Vp, mdot(Va, Vb));
 }
 
 template <class R> ME_HD W4<R> w4_sub(const W4<R>& a, const W4<R>& b, R g) {
