@@ -154,25 +154,35 @@ class _Emitter:
                       f"Q{nid}[3] * Q{nid}[3];")
                     E(f"  const me::cx<R> inv{nid} = inv_den<R>(q2_{nid} - {m} * {m}, {wexpr});")
                     self.flops64 += 4 * (len(legs) - 1) + 7 + 3
-        # root external node (last leg) appears only as an amplitude child
-        E("  // wavefunctions and sub-currents, once per helicity variant")
-        for nid in used_nodes:
+        # Wavefunctions and sub-currents are emitted on demand, helicity by helicity: each
+        # helicity's amplitudes are preceded by the variants they use that are not emitted yet,
+        # and followed by its colour sum, so a variant lives only from its first to its last use
+        # (shorter live ranges, fewer registers held across the program).
+        emitted = set()
+
+        def need(nid, var):
+            if (nid, var) in emitted:
+                return
             nd = nodes[nid]
-            for var in p.node_variants[nid]:
-                self.node_code(nid, var)
-        # amplitudes
+            if not nd.external:
+                for c in nd.children:
+                    need(c, self.child_vars(nid, var, c))
+            self.node_code(nid, var)
+            emitted.add((nid, var))
+
         K = p.n_colour
-        E("  // diagram amplitudes into colour components")
+        C = p.cmat_num
+        E("  // per helicity: the wavefunctions and sub-currents it needs first, its diagram amplitudes")
+        E("  // into colour components, then its colour sum (J^T C J)/den; helicity sum, average")
+        E("  R tot = R(0);")
         for hi, terms in enumerate(p.amp_terms):
+            for aid, chvars in terms:
+                for c, cv in zip(p.amps[aid].children, chvars):
+                    need(c, cv)
             for k in range(K):
                 E(f"  me::cx<R> J{hi}_{k} = me::mk(R(0), R(0));")
             for aid, chvars in terms:
                 self.amp_code(aid, chvars, hi)
-        # colour sum
-        E("  // colour sum (J^T C J)/den per helicity, helicity sum, average")
-        E("  R tot = R(0);")
-        C = p.cmat_num
-        for hi in range(len(p.amp_terms)):
             E("  {")
             E("    R s = R(0);")
             for k in range(K):
