@@ -535,12 +535,28 @@ __host__ __device__ __forceinline__ void rambo_df(const KinDev& kin, uint64_t se
   }
 }
 
+// approximate 1/sqrt(x) and x/y (the device's fast forms; plain IEEE on the host)
+__host__ __device__ __forceinline__ float approx_rsqrt(float x) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(x);
+#else
+  return 1.0f / sqrtf(x);
+#endif
+}
+__host__ __device__ __forceinline__ float approx_div(float x, float y) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(x, y);
+#else
+  return x / y;
+#endif
+}
+
 // Massive RAMBO rescaling in double-float: the massless momenta of rambo_df are
 // scaled so that every final particle gets its mass at fixed total energy w
 // (the same equation as gen_rambo: sum_k sqrt(m_k^2 + xi^2 E_k^2) = w).  xi is
 // found by Newton's method in FP32 from the same start, then refined by two
 // double-float Newton steps (quadratic convergence: FP32 accuracy squared is
-// below the double-float rounding).  Returns the factor of the weight,
+// below the double-float rounding).  Massless particles take e_k = xi E_k exactly.  Returns the factor of the weight,
 // xi^(2n-3) prod_k(|p_k|/E_k) w / sum_k(|p_k|^2/E_k).
 template <int NEXT>
 __host__ __device__ __forceinline__ df massive_rescale_df(const KinDev& kin, df (&p)[NEXT][4],
@@ -558,16 +574,27 @@ __host__ __device__ __forceinline__ df massive_rescale_df(const KinDev& kin, df 
   }
   const float r = msum / w.hi;
   float xf = sqrtf(fmaxf(1.0f - r * r, 0.0f));
+  // FP32 stage with approximate square roots and quotients, until the step falls below 2^-22 x
+  // (at most 12 iterations): it only starts the double-float steps, which square its error.
+  // Massless particles (m = 0, the same in every thread) contribute x E exactly.
   for (int it = 0; it < 12; ++it) {
     float f = -w.hi, d = 0.0f;
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
       const float e = E0[k].hi;
-      const float ek = sqrtf(m2[k].hi + xf * xf * e * e);
-      f += ek;
-      d += xf * e * e / ek;
+      if (m2[k].hi == 0.0f) {
+        f += xf * e;
+        d += e;
+      } else {
+        const float q = m2[k].hi + xf * xf * e * e;
+        const float rq = approx_rsqrt(q);
+        f += q * rq;
+        d += xf * e * e * rq;
+      }
     }
-    xf -= f / d;
+    const float dx = approx_div(f, d);
+    xf -= dx;
+    if (fabsf(dx) <= 0x1p-22f * xf) break;
   }
   df X = dfs(xf);
 #pragma unroll
@@ -576,9 +603,14 @@ __host__ __device__ __forceinline__ df massive_rescale_df(const KinDev& kin, df 
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
       const df ak = X * E0[k];
-      const df ek = df_sqrt(m2[k] + sqr(ak));
-      f = f + ek;
-      d = d + (ak * E0[k]) / ek;
+      if (m2[k].hi == 0.0f) {  // e_k = x E_k
+        f = f + ak;
+        d = d + E0[k];
+      } else {
+        const df ek = df_sqrt(m2[k] + sqr(ak));
+        f = f + ek;
+        d = d + (ak * E0[k]) / ek;
+      }
     }
     X = X - f / d;
   }
@@ -586,10 +618,15 @@ __host__ __device__ __forceinline__ df massive_rescale_df(const KinDev& kin, df 
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     const df ak = X * E0[k];
-    const df ek = df_sqrt(m2[k] + sqr(ak));
-    prod = prod * (ak / ek);
-    sum = sum + sqr(ak) / ek;
-    p[2 + k][0] = ek;
+    if (m2[k].hi == 0.0f) {  // |p_k| / e_k = 1, |p_k|^2 / e_k = |p_k|
+      sum = sum + ak;
+      p[2 + k][0] = ak;
+    } else {
+      const df ek = df_sqrt(m2[k] + sqr(ak));
+      prod = prod * (ak / ek);
+      sum = sum + sqr(ak) / ek;
+      p[2 + k][0] = ek;
+    }
     p[2 + k][1] = p[2 + k][1] * X;
     p[2 + k][2] = p[2 + k][2] * X;
     p[2 + k][3] = p[2 + k][3] * X;
