@@ -92,11 +92,24 @@ DF_HD df sqr(df a) {
   const df p = two_prod(a.hi, a.hi);
   return fast_two_sum(p.hi, df_fma(df_add_rn(a.hi, a.hi), a.lo, p.lo));
 }
-// a / b: one FP32 quotient corrected by the double-float residual
+// 1/x to about one ulp: on the device the fast reciprocal and one Newton step
+// (FMA form), on the host IEEE division.  Normal, finite x.
+DF_HD float df_recip(float x) {
+#ifdef __CUDA_ARCH__
+  const float r = __fdividef(1.0f, x);
+  return df_fma(r, df_fma(-x, r, 1.0f), r);
+#else
+  return 1.0f / x;
+#endif
+}
+// a / b: an FP32 quotient corrected by the double-float residual, both from one
+// reciprocal of b.hi (the residual a - b q1 is formed exactly, so q1 need not be
+// correctly rounded; q2 carries an error of about one ulp of itself, 2^-47 of a / b)
 DF_HD df operator/(df a, df b) {
-  const float q1 = a.hi / b.hi;
+  const float rb = df_recip(b.hi);
+  const float q1 = df_mul_rn(a.hi, rb);
   const df r = a - b * q1;
-  const float q2 = r.hi / b.hi;
+  const float q2 = df_mul_rn(r.hi, rb);
   return fast_two_sum(q1, q2);
 }
 DF_HD df df_sqrt(df a) {
