@@ -27,10 +27,24 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP32 operations per phase-space draw of the mixed path (double-float RAMBO, counted from
-# the operation mix of dfloat.cuh: add 20, mul 7, sqrt 15, div 20, log 80, sin/cos 120 FP32
-# operations; 4 final-state particles plus the conformal transform and the FP32 cut tests)
-PS_FLOPS_PER_DRAW = {"rambo": 2700.0}
+# FP32 operations per accepted point of the mixed-path kernels as executed: FADD + FMUL + 2 FFMA
+# thread instructions of one ncu capture per workload, divided by the points of that launch
+# (profiles/ holds the captures; k_ps includes every draw of a point).  The code generator's own
+# count of the |M|^2 program (me_info flops_amp) counts the program as written, before the compiler
+# removes the repeated subexpressions of the helicity variants; it is the fallback where no
+# capture exists.
+EXECUTED_FLOPS_PER_POINT = {
+    ("udx_epvegg", "k_ps"): 3912.1,
+    ("udx_epvegg", "k_me"): 3121.0,
+    ("gg_ttx_dilep", "k_ps"): 7003.3,
+    ("gg_ttx_dilep", "k_me"): 6758.0,
+    ("us_dchh", "k_ps"): 5216.0,
+    ("us_dchh", "k_me"): 1793.8,
+    ("uux_epem", "k_ps"): 18.0,
+    ("uux_epem", "k_me"): 1091.0,
+    ("gg_gggg", "k_ps"): 4249.2,
+    ("gg_gggg", "k_me"): 10968317.3,
+}
 
 # DRAM bytes per point of the mixed-path kernels (dram__bytes_read.sum + dram__bytes_write.sum of one
 # ncu capture, divided by the points of that launch; profiles/ holds the captures).  A launch's
@@ -273,7 +287,8 @@ def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
             t_ps, t_me = B.me_step_timing(h, 0)
             ns_t = nt
             info = B.me_info(h)
-            fl = info.flops_amp if prec == B.ME_MIXED else info.flops_fp64
+            fl = (EXECUTED_FLOPS_PER_POINT.get((key, "k_me"), info.flops_amp) if prec == B.ME_MIXED
+                  else info.flops_fp64)
             row[name] = {"evals_per_s": n / (ms * 1e-3), "ms_per_step": ms, "k_me_ms": t_me / ns_t,
                          "k_me_tflops": fl * n / (t_me / ns_t * 1e-3) / 1e12}
             if prec == B.ME_MIXED:
@@ -527,16 +542,20 @@ def main():
     t_ps, t_me = B.me_step_timing(h32, 0)
     ps_ms, me_ms = t_ps / n_kt, t_me / n_kt
     tries_per_point = acc_t.n_try / acc_t.n_acc
-    flops_event = info.flops_amp
+    me_flops = EXECUTED_FLOPS_PER_POINT.get((args.workload, "k_me"))
+    ps_flops = EXECUTED_FLOPS_PER_POINT.get((args.workload, "k_ps"))
+    flops_event = me_flops if me_flops is not None else info.flops_amp
     peak = fp32_alu_peak_tflops()
     me_tflops = flops_event * n / (me_ms * 1e-3) / 1e12
-    ps_tflops = PS_FLOPS_PER_DRAW.get(w["kind"], 0.0) * tries_per_point * n / (ps_ms * 1e-3) / 1e12
+    ps_tflops = (ps_flops or 0.0) * n / (ps_ms * 1e-3) / 1e12
     kernels = {
         "k_me": {"ms": me_ms, "achieved_tflops": me_tflops, "frac": me_tflops / peak,
-                 "flops_per_point": flops_event,
+                 "flops_per_point": flops_event, "flops_model": info.flops_amp,
+                 "flops_source": "executed (ncu FP32 op counters)" if me_flops is not None else "code generator count",
                  "what": "|M|^2, weights, block sums (FP32 amplitudes; CUDA-core flops)"},
         "k_ps": {"ms": ps_ms, "achieved_tflops": ps_tflops, "frac": ps_tflops / peak,
-                 "flops_per_draw": PS_FLOPS_PER_DRAW.get(w["kind"], 0.0), "draws_per_point": tries_per_point,
+                 "flops_per_point": ps_flops, "draws_per_point": tries_per_point,
+                 "flops_source": "executed (ncu FP32 op counters)" if ps_flops is not None else "none",
                  "what": "Philox + double-float RAMBO + cuts + redraw queue"},
     }
     if info.flops_colour > 0:
@@ -636,7 +655,7 @@ def main():
         line = {
             "metric": "|M|^2 evals/s", "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 amplitudes, f64 momenta/resonant invariants/accumulation",
+            "vs_baseline": None, "dtype": "f32 (amplitudes; momenta, resonant invariants and per-thread sums as f32 pairs; f64 block sums)",
             "data": "synthetic (on-device Philox phase space)",
             "config": {"workload": args.workload, "describe": w["describe"], "points_per_step_per_gpu": n,
                        "precision": "mixed", "l2": "flushed (256 MB write) between timed steps",
@@ -645,6 +664,8 @@ def main():
             "me_eval_ms": me_eval_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                         "flops_per_point": kernels[dom]["flops_per_point"],
+                         "flops_source": kernels[dom]["flops_source"],
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
             "kernels": kernels,
             "per_process": table,
