@@ -21,6 +21,9 @@ Functions and their pins (tests/test_oracle_processes.py):
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
   gg_ttx_dilep    g g > t t~ > b e+ ve b~ e- ve~ (doubly resonant diagrams):
                    Ward identity (zero widths), Bose symmetry, boosts
+  uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
+                   (each diagram grows like s/mW^2, the sum stays finite), the W
+                   polarisation sum against the tensor form -g + k k/mW^2, boosts
   us_dchh         u s > d c h h  (WW fusion): Higgs-exchange symmetry, boosts;
                    its W current is pinned by u d~ > e+ ve, its WWH/WWHH/HHH
                    couplings and diagram set by the gauge cancellation of the
@@ -386,6 +389,47 @@ def wpwm_hh_amplitudes(P, hel, par=SMParams()):
 
 
 # --------------------------------------------------------------------------
+# u u~ > W+ W-  (t-channel d exchange, s-channel photon and Z through the WWV vertex)
+# --------------------------------------------------------------------------
+HEL_W = (-1, 0, 1)
+
+
+def uux_wpwm_amplitudes(P, hel, par=SMParams()):
+    """The three diagrams of u(p0) u~(p1) > W+(p2) W-(p3) for fixed helicities (t-channel d quark,
+    s-channel photon, s-channel Z), returned separately as M values.
+
+    WWV vertex (the VVV function of Sect. 4.2 with (V1, V2, V3) = (W-, W+, V) and coupling
+    g_WWA = e, g_WWZ = g cos(theta_W)): with every momentum incoming and the outgoing W- and W+
+    entering as V1 and V2, its factor in i M is -i g_V [g^{12}(k1 - k2)^3 + g^{23}(k2 - k3)^1 +
+    g^{31}(k3 - k1)^2].  The phase and orientation are those under which the longitudinal
+    amplitude stays finite at high energy (tests/test_oracle_processes.py)."""
+    p = [P[:, k] for k in range(4)]
+    gw = par.g / np.sqrt(2.0)
+    u = u_spinor(p[0], hel[0])
+    vb = bar(v_spinor(p[1], hel[1]))
+    ep = polarisation(p[2], hel[2], mass=par.mW).conj()
+    em = polarisation(p[3], hel[3], mass=par.mW).conj()
+    out = [fermion_line(vb, u, p[0], [(vector_insertion(ep, gw, 0.0), p[2]),
+                                      (vector_insertion(em, gw, 0.0), p[3])])]
+    q = p[0] + p[1]
+    X = vvv_out(em, -p[3], ep, -p[2], q, 1.0)
+    ga = _a_coupling("u", par)
+    for gv, (gl, gr), mV, wV in ((par.e, (ga, ga), 0.0, 0.0),
+                                 (par.g * par.cw, _z_couplings("u", par), par.mZ, par.wZ)):
+        V = vector_prop(q, ffv_current(vb, u, gl, gr), mV, wV)
+        out.append(-1j * gv * mdot(X, V))
+    return [x / 1j for x in out]
+
+
+def uux_wpwm(P, par=SMParams()):
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_W):
+        M = sum(uux_wpwm_amplitudes(P, h, par))
+        tot = tot + colour.colour_sum([M], [_DELTA3])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
 # n gluons: colour-ordered Berends-Giele recursion + brute-force colour matrix
 # --------------------------------------------------------------------------
 _SQ2 = np.sqrt(2.0)
@@ -499,6 +543,7 @@ PROCESSES = {
     "g g > t t~": gg_ttx,
     "g g > t t~ > b e+ ve b~ e- ve~": gg_ttx_dilep,
     "u s > d c h h": us_dchh,
+    "u u~ > w+ w-": uux_wpwm,
     "g g > g g": gluons,
     "g g > g g g": gluons,
     "g g > g g g g": gluons,

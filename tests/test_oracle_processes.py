@@ -308,3 +308,84 @@ def test_ww_hh_gauge_cancellation():
         vals.append(tot)
     assert abs(vals[-1] / vals[-2] - 1) < 0.01
     assert abs(vals[-1]) < 10.0
+
+
+def _ww_point(sqrt_s, cth, par=PAR):
+    """u u~ > W+ W- at fixed sqrt(s) and cos(theta) of the W+ (one point)."""
+    E = 0.5 * sqrt_s
+    k = math.sqrt(E * E - par.mW ** 2)
+    st = math.sqrt(1 - cth * cth)
+    P = np.zeros((1, 4, 4))
+    P[0, 0] = [E, 0, 0, E]
+    P[0, 1] = [E, 0, 0, -E]
+    P[0, 2] = [E, k * st, 0, k * cth]
+    P[0, 3] = [E, -k * st, 0, -k * cth]
+    return P
+
+
+def test_uux_wpwm_gauge_cancellation():
+    """Longitudinal W+ W- from u u~: the t-channel quark-exchange diagram grows like s/mW^2, and only
+    with the WWA and WWZ couplings e and g cos(theta_W), the -i phase and the (W-, W+, V)
+    orientation of the WWV vertex relative to the fermion couplings do the photon and Z diagrams
+    cancel that growth: the summed |M|^2 tends to a constant while the t-channel amplitude alone
+    rises a hundredfold per decade of sqrt(s).  Zero widths (a fixed Z width leaves a remainder
+    growing like s)."""
+    par0 = PAR.with_(wZ=0.0, wW=0.0)
+    vals, tch = [], []
+    for rs in (5e3, 5e4, 5e5):
+        P = _ww_point(rs, 0.3, par0)
+        m2 = 0.0
+        for hf in itertools.product((-1, 1), (-1, 1)):
+            a = pr.uux_wpwm_amplitudes(P, hf + (0, 0), par0)
+            m2 += abs(sum(a)[0]) ** 2
+        vals.append(m2)
+        tch.append(abs(pr.uux_wpwm_amplitudes(P, (-1, 1, 0, 0), par0)[0][0]))
+    assert tch[1] / tch[0] > 90 and tch[2] / tch[1] > 90
+    assert abs(vals[2] / vals[1] - 1) < 1e-3 and abs(vals[1] / vals[0] - 1) < 0.05
+    # the opposite phase of the WWV vertex (equivalently the opposite orientation) does not cancel
+    P = _ww_point(5e4, 0.3, par0)
+    a = pr.uux_wpwm_amplitudes(P, (-1, 1, 0, 0), par0)
+    flipped = abs((a[0] - a[1] - a[2])[0]) ** 2
+    assert flipped > 1e3 * vals[1]
+
+
+def test_uux_wpwm_polarisation_sum_and_boosts():
+    """The helicity sum over the three W polarisations equals the contraction of the amplitude
+    tensor with -g^{mu nu} + k^mu k^nu / mW^2 for each W, and the summed |M|^2 is invariant under
+    random Lorentz transformations."""
+    P = two_to_two(800.0, 50, PAR.mW, PAR.mW, seed=5)
+    ref = pr.uux_wpwm(P, PAR)
+    # tensor form: amplitude as a function of the W polarisation vectors (basis vectors e_mu)
+    from oracle.lorentz import bar, u_spinor, v_spinor
+    from oracle.feynman import fermion_line, vector_insertion, vector_prop, vvv_out, ffv_current
+    g = np.diag([1.0, -1.0, -1.0, -1.0])
+    p = [P[:, k] for k in range(4)]
+    gw = PAR.g / np.sqrt(2.0)
+    q = p[0] + p[1]
+    tot = 0.0
+    for hf in itertools.product((-1, 1), (-1, 1)):
+        u = u_spinor(p[0], hf[0])
+        vb = bar(v_spinor(p[1], hf[1]))
+        T = np.zeros((P.shape[0], 4, 4), dtype=complex)
+        for mu in range(4):
+            for nu in range(4):
+                ep = np.zeros((P.shape[0], 4), dtype=complex)
+                em = np.zeros((P.shape[0], 4), dtype=complex)
+                ep[:, mu] = 1.0
+                em[:, nu] = 1.0
+                a = fermion_line(vb, u, p[0], [(vector_insertion(ep, gw, 0.0), p[2]),
+                                               (vector_insertion(em, gw, 0.0), p[3])])
+                X = vvv_out(em, -p[3], ep, -p[2], q, 1.0)
+                ga = PAR.e * CHARGE["u"]
+                gl, gr = PAR.gz * (T3["u"] - CHARGE["u"] * PAR.sw2), PAR.gz * (-CHARGE["u"] * PAR.sw2)
+                a = a - 1j * PAR.e * mdot(X, vector_prop(q, ffv_current(vb, u, ga, ga)))
+                a = a - 1j * PAR.g * PAR.cw * mdot(X, vector_prop(q, ffv_current(vb, u, gl, gr), PAR.mZ, PAR.wZ))
+                T[:, mu, nu] = a / 1j
+        # M = sum_ab eps+*^a eps-*^b T_ab; sum over polarisations of eps*^a eps^c = -g^{ac} + k^a k^c / m^2
+        Pp = -g[None] + np.einsum("ni,nj->nij", p[2], p[2]) / PAR.mW ** 2
+        Pm = -g[None] + np.einsum("ni,nj->nij", p[3], p[3]) / PAR.mW ** 2
+        tot = tot + np.einsum("nab,ncd,nac,nbd->n", T, T.conj(), Pp, Pm).real
+    tens = 3.0 * tot / 36.0
+    assert np.allclose(tens, ref, rtol=1e-11)
+    Q = random_lorentz(P, seed=6)
+    assert np.allclose(pr.uux_wpwm(Q, PAR), ref, rtol=1e-10)
