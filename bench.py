@@ -253,13 +253,13 @@ def run_reference(args, w, rank, world):
 
 
 def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
-    """Every workload: mixed and FP64 xsec_step rates on the full point count, the mixed
+    """Every workload and variant: mixed and FP64 xsec_step rates on the full point count, the mixed
     |M|^2 kernel's CUDA-core fraction, and the mixed path's relative error against the FP64
     GPU path on the FP64 path's own momenta (median and max over the accepted points)."""
-    from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args
+    from paper_1305_0708_gb300.workloads import VARIANTS, WORKLOADS, kin_args
     peak = fp32_alu_peak_tflops()
     table = {}
-    for key, w in WORKLOADS.items():
+    for key, w in list(WORKLOADS.items()) + list(VARIANTS.items()):
         n = w["n"]
         kin = B.make_kin(**kin_args(w))
         row = {"points": n}

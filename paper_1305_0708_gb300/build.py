@@ -30,6 +30,7 @@ PROCESSES = [
     ("u d~ > e+ ve", []),
     ("u u~ > g g", []),
     ("g g > g g", []),
+    ("u u~ > w+ w-", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

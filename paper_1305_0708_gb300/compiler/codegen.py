@@ -299,7 +299,11 @@ class _Emitter:
                 self.flops32 += 48 * nterm + (60 if massive else 8)
         elif v.kind == "VVV":
             g = self.cpl(v.couplings[0])
-            a, b = kids
+            # inputs in cyclic order after the output slot: the antisymmetric Lorentz structure
+            # then equals the vertex's (slot 0, 1, 2) form
+            by_slot = {k[1]: k for k in kids}
+            o = nd.out_slot
+            a, b = by_slot[(o + 1) % 3], by_slot[(o + 2) % 3]
             E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::vvv_current<R>({a[2]}, k{a[0]}, {b[2]}, k{b[0]}, "
               f"(R){g}), k{nid}, inv{nid}, false, me::mk(R(0), R(0)));")
             self.flops32 += self._vvv_current_flops(a[2], b[2]) + 8

@@ -13,6 +13,7 @@ of |M|^2):
                                                  W: gL = g / sqrt2, gR = 0
                                                  gluon: gL = gR = g_s, colour t^a
   g g g     g_s f^{abc} [g^{mn}(k1-k2)^r + cyclic]   (all momenta incoming)
+  W+ W- V   -i g_V [g^{mn}(k1-k2)^r + cyclic] for incoming (W+, W-, V), g_A = e, g_Z = g cw
   g g g g   -i g_s^2 f^{XYe} f^{ZWe} (g_XZ g_YW - g_XW g_YZ) for the three pairings
   W+ W- h   i g mW g^{mn}        Z Z h  i gZ mZ g^{mn}
   W+ W- h h i g^2/2 g^{mn}       Z Z h h i gZ^2/2 g^{mn}
@@ -90,6 +91,7 @@ class Vertex:
     kind: str
     couplings: tuple
     colour: str = "none"
+    phase: int = -1   # power of i of the vertex factor; -1: the default of its kind
 
 
 def _ffv_vertices():
@@ -115,6 +117,10 @@ def _ffv_vertices():
 VERTICES = _ffv_vertices() + [
     Vertex(("g", "g", "g"), "VVV", ("GS",), "f"),
     Vertex(("g", "g", "g", "g"), "VVVV", ("GS2",), "ff"),
+    # W W gamma and W W Z (Sect. 4.2 VVV with (V1, V2, V3) = (W-, W+, V) named by their outgoing
+    # quantum numbers, i.e. incoming W+, W-, V here): -i g_V times the Lorentz structure
+    Vertex(("w+", "w-", "a"), "VVV", ("GWWA",), "none", phase=3),
+    Vertex(("w+", "w-", "z"), "VVV", ("GWWZ",), "none", phase=3),
     Vertex(("w+", "w-", "h"), "VVS", ("GWWH",)),
     Vertex(("z", "z", "h"), "VVS", ("GZZH",)),
     Vertex(("w+", "w-", "h", "h"), "VVSS", ("GWWHH",)),
@@ -139,6 +145,7 @@ def couplings(par):
     v = 2 * par["mW"] / g
     c = {"ZERO": 0.0, "GS": gs, "GS2": gs * gs, "GW": g / math.sqrt(2),
          "GWWH": g * par["mW"], "GZZH": gz * par["mZ"], "GWWHH": g * g / 2, "GZZHH": gz * gz / 2,
+         "GWWA": e, "GWWZ": g * cw,
          "GHHH": -3 * par["mH"] ** 2 / v,
          "MT": par["mt"], "WT": par["wt"], "MZ": par["mZ"], "WZ": par["wZ"], "MW": par["mW"], "WW": par["wW"],
          "MH": par["mH"], "WH": par["wH"], "0": 0.0}

@@ -278,6 +278,10 @@ def _fermion_sign(nodes, a):
     return -1 if inv % 2 else 1
 
 
+def _vphase(v):
+    return v.phase if v.phase >= 0 else _VERTEX_PHASE[v.kind]
+
+
 def _phase(nodes, nid, cache):
     if nid in cache:
         return cache[nid]
@@ -285,7 +289,7 @@ def _phase(nodes, nid, cache):
     if nd.external:
         ph = 0
     else:
-        ph = _VERTEX_PHASE[nd.vertex.kind] + _PROP_PHASE[_kind_of(nd.ptype)]
+        ph = _vphase(nd.vertex) + _PROP_PHASE[_kind_of(nd.ptype)]
         ph += sum(_phase(nodes, c, cache) for c in nd.children)
     cache[nid] = ph % 4
     return cache[nid]
@@ -347,7 +351,7 @@ def compile_process(name):
     basis_set = {}
     for a in amps:
         expr = _amp_colour(nodes, legs, a, cache, internal)
-        ph = (_VERTEX_PHASE[a.vertex.kind] + sum(_phase(nodes, c, pcache) for c in a.children) + 3) % 4
+        ph = (_vphase(a.vertex) + sum(_phase(nodes, c, pcache) for c in a.children) + 3) % 4
         sgn = _fermion_sign(nodes, a)
         fac = _IPOW[ph] * sgn
         expr = {k: v * fac for k, v in expr.items()}

@@ -69,6 +69,8 @@ bool coupling_value(const std::string& n, const me_params& p, double& v) {
   if (n == "GS2") { v = gs * gs; return true; }
   if (n == "GW") { v = g / std::sqrt(2.0); return true; }
   if (n == "GWWH") { v = g * p.mW; return true; }
+  if (n == "GWWA") { v = e; return true; }
+  if (n == "GWWZ") { v = g * cw; return true; }
   if (n == "GZZH") { v = gz * p.mZ; return true; }
   if (n == "GWWHH") { v = g * g / 2; return true; }
   if (n == "GZZHH") { v = gz * gz / 2; return true; }

@@ -39,6 +39,11 @@ VARIANTS = {
         seed=1, cuts=dict(legs=(2, 4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,
         describe="u d~ > e+ ve g g with the W+ -> e+ ve pair generated Breit-Wigner mapped (App. A.2) and "
                  "RAMBO for (W*, g, g) at sqrt(s)=1 TeV, same cuts, 2^20 points, seed 1"),
+    "uux_wpwm": dict(
+        process="u u~ > w+ w-", kind="rambo", sqrt_s=500.0, masses=(0, 0, 80.4, 80.4), n=1 << 20, seed=5,
+        cuts=None, s_ident=1.0,
+        describe="u u~ > W+ W- (t-channel d, s-channel photon and Z through the WWV vertex), massive RAMBO "
+                 "at sqrt(s)=500 GeV, 2^20 points, seed 5"),
 }
 
 KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3}

@@ -248,3 +248,28 @@ def test_resonance_generator_parity(B, prec):
         rel = np.abs(me2.cpu().numpy() / ref - 1)
         assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
         assert acc.sum_w == pytest.approx(sw, rel=1e-5)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ww_production_parity(B, prec):
+    """u u~ > W+ W- (electroweak triple-gauge vertices): me_eval on the oracle's massive-RAMBO points
+    and the Monte Carlo sums of xsec_step against the oracle's generate and accumulate."""
+    from paper_1305_0708_gb300.workloads import VARIANTS
+    w = VARIANTS["uux_wpwm"]
+    n = 1500
+    P, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(n))
+    ref = opr.uux_wpwm(P, PAR)
+    got = eval_gpu(B, w["process"], P, prec)
+    if prec == 0:
+        assert np.all(np.abs(got - ref) <= fp64_tolerance(opr.uux_wpwm, P, ref))
+    else:
+        rel = np.abs(got / ref - 1)
+        assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
+    kin = B.make_kin(**kin_args(w))
+    h = B.me_create(w["process"], None, prec)
+    acc = B.xsec_step(h, w["seed"], 0, n, kin)
+    B.me_destroy(h)
+    sw, sw2, nacc, ntry = oxs.accumulate(ref, W, S, T, w["s_ident"])
+    assert acc.n_acc == nacc == n and acc.n_try == ntry
+    tol = 1e-11 if prec == 0 else 1e-5
+    assert acc.sum_w == pytest.approx(sw, rel=tol) and acc.sum_w2 == pytest.approx(sw2, rel=2 * tol)
