@@ -168,6 +168,9 @@ def oracle_kin(w):
         k = {"kind": "rambo", "sqrt_s": w["sqrt_s"], "n_final": n_ext - 2}
         if "masses" in w:
             k["masses"] = list(w["masses"][2:])
+    elif w["kind"] == "rambo_bw":
+        k = {"kind": "rambo_bw", "sqrt_s": w["sqrt_s"], "n_final": n_ext - 2, "res_mass": w["res_mass"],
+             "res_width": w["res_width"]}
     else:
         k = {"kind": "ttbar", "sqrt_s_range": w["sqrt_s_range"]}
     if w.get("cuts"):
@@ -182,7 +185,7 @@ def oracle_step(w, events):
     from oracle.sm import SMParams
     fn = {"u u~ > e+ e-": opr.uux_epem, "u d~ > e+ ve g g": opr.udx_epvegg,
           "g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))": opr.gg_ttx_dilep,
-          "u s > d c h h": opr.us_dchh, "g g > g g g g": opr.gluons}[w["process"]]
+          "u s > d c h h": opr.us_dchh, "g g > g g g g": opr.gluons, "u u~ > w+ w-": opr.uux_wpwm}[w["process"]]
     par = SMParams()
     P, W, S, T = oxs.generate(oracle_kin(w), par, w["seed"], events)
     return oxs.accumulate(fn(P, par), W, S, T, w["s_ident"])
@@ -465,8 +468,8 @@ def main():
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
 
-    from paper_1305_0708_gb300.workloads import WORKLOADS, kin_args
-    w = WORKLOADS[args.workload]
+    from paper_1305_0708_gb300.workloads import VARIANTS, WORKLOADS, kin_args
+    w = WORKLOADS[args.workload] if args.workload in WORKLOADS else VARIANTS[args.workload]
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, w, rank, world)
