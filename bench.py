@@ -44,13 +44,17 @@ EXECUTED_FLOPS_PER_POINT = {
     ("uux_epem", "k_me"): 1091.0,
     ("gg_gggg", "k_ps"): 4249.2,
     ("gg_gggg", "k_me"): 10968317.3,
+    ("uux_wpwm", "k_ps"): 3200.0,
+    ("uux_wpwm", "k_me"): 3691.7,
+    ("udx_epvegg_bw", "k_ps"): 6256.0,
+    ("udx_epvegg_bw", "k_me"): 3121.0,
 }
 
 # DRAM bytes per point of the mixed-path kernels (dram__bytes_read.sum + dram__bytes_write.sum of one
 # ncu capture, divided by the points of that launch; profiles/ holds the captures).  A launch's
 # traffic is this times its points: the kernels stream their points, so traffic grows in proportion.
-TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (85.422592e6 + 282.576896e6) / 2 ** 20,
-                     ("udx_epvegg", "k_me"): (214.007552e6 + 3.591424e6) / 2 ** 20,
+TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (85.43872e6 + 282.851328e6) / 2 ** 20,
+                     ("udx_epvegg", "k_me"): (214.006016e6 + 3.588608e6) / 2 ** 20,
                      ("gg_gggg", "k_me"): (3.478784e6 + 0.07552e6) / 16384}
 
 SM_COUNT = 152
