@@ -607,8 +607,20 @@ def main():
         torch.cuda.synchronize(dev)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_step = sorted(e2e_ms)[len(e2e_ms) // 2]
+    # the CPU-GPU link alone: the same momenta as one page-locked copy-engine transfer
+    lk = []
+    for _ in range(5):
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        mom_dev.copy_(mom_host, non_blocking=True)
+        l1.record(stream)
+        torch.cuda.synchronize(dev)
+        lk.append(l0.elapsed_time(l1))
+    link_gbs = mom_host.numel() * 8 / (sorted(lk)[len(lk) // 2] * 1e-3) / 1e9
+    e2e_gbs = mom_host.numel() * 8 / (e2e_step * 1e-3) / 1e9
     e2e = {"value": n * world / (e2e_step * 1e-3), "unit": "evals/s",
            "h2d_bytes_per_step": int(mom_host.numel() * 8), "d2h_bytes_per_step": int(n * 8),
+           "h2d_gbs": e2e_gbs, "link_copy_gbs": link_gbs, "frac_of_link": e2e_gbs / link_gbs,
            "path": "me_eval_host on page-locked host momenta and |M|^2 (the kernel reads and writes the mapped "
                    "host memory over the CPU-GPU link)"}
     # kernel-only me_eval time (momenta resident)
