@@ -24,6 +24,8 @@ Functions and their pins (tests/test_oracle_processes.py):
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
+  udx_wpz         u d~ > w+ z    : gauge cancellation of the longitudinal amplitude
+                   (the WWZ vertex with an incoming W), boosts
   us_dchh         u s > d c h h  (WW fusion): Higgs-exchange symmetry, boosts;
                    its W current is pinned by u d~ > e+ ve, its WWH/WWHH/HHH
                    couplings and diagram set by the gauge cancellation of the
@@ -430,6 +432,37 @@ def uux_wpwm(P, par=SMParams()):
 
 
 # --------------------------------------------------------------------------
+# u d~ > W+ Z  (u and d exchange, s-channel W through the WWZ vertex)
+# --------------------------------------------------------------------------
+def udx_wpz_amplitudes(P, hel, par=SMParams()):
+    """The three diagrams of u(p0) d~(p1) > W+(p2) Z(p3) for fixed helicities (Z from the u line, Z
+    from the d line, s-channel W), returned separately as M values.  The WWZ vertex is the one of
+    uux_wpwm_amplitudes: -i g_WWZ times the Lorentz structure, with the s-channel W+ entering as the
+    incoming W+ (V1), the outgoing W+ as the incoming W- (V2) and the Z as V3."""
+    p = [P[:, k] for k in range(4)]
+    gw = par.g / np.sqrt(2.0)
+    u = u_spinor(p[0], hel[0])
+    vb = bar(v_spinor(p[1], hel[1]))
+    ew = polarisation(p[2], hel[2], mass=par.mW).conj()
+    ez = polarisation(p[3], hel[3], mass=par.mZ).conj()
+    zu, zd = _z_couplings("u", par), _z_couplings("d", par)
+    out = [fermion_line(vb, u, p[0], [(vector_insertion(ez, *zu), p[3]), (vector_insertion(ew, gw, 0.0), p[2])]),
+           fermion_line(vb, u, p[0], [(vector_insertion(ew, gw, 0.0), p[2]), (vector_insertion(ez, *zd), p[3])])]
+    q = p[0] + p[1]
+    W = vector_prop(q, ffv_current(vb, u, gw, 0.0), par.mW, par.wW)
+    out.append(-1j * par.g * par.cw * mdot(vvv_out(W, q, ew, -p[2], -p[3], 1.0), ez))
+    return [x / 1j for x in out]
+
+
+def udx_wpz(P, par=SMParams()):
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_W):
+        M = sum(udx_wpz_amplitudes(P, h, par))
+        tot = tot + colour.colour_sum([M], [_DELTA3])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
 # n gluons: colour-ordered Berends-Giele recursion + brute-force colour matrix
 # --------------------------------------------------------------------------
 _SQ2 = np.sqrt(2.0)
@@ -544,6 +577,7 @@ PROCESSES = {
     "g g > t t~ > b e+ ve b~ e- ve~": gg_ttx_dilep,
     "u s > d c h h": us_dchh,
     "u u~ > w+ w-": uux_wpwm,
+    "u d~ > w+ z": udx_wpz,
     "g g > g g": gluons,
     "g g > g g g": gluons,
     "g g > g g g g": gluons,

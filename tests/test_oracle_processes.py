@@ -389,3 +389,33 @@ def test_uux_wpwm_polarisation_sum_and_boosts():
     assert np.allclose(tens, ref, rtol=1e-11)
     Q = random_lorentz(P, seed=6)
     assert np.allclose(pr.uux_wpwm(Q, PAR), ref, rtol=1e-10)
+
+
+def test_udx_wpz_gauge_cancellation_and_boosts():
+    """u d~ > W+ Z, longitudinal W and Z: the Z-from-u, Z-from-d and s-channel-W diagrams each grow like
+    s/mW^2, and their sum stays finite only with the Z couplings of the two quark lines, the W
+    propagator and the WWZ vertex of uux_wpwm_amplitudes (incoming W+ as V1) mutually consistent;
+    the opposite WWZ phase grows like s^2 in |M|^2.  Zero widths.  The helicity sum is Lorentz
+    invariant."""
+    par0 = PAR.with_(wZ=0.0, wW=0.0)
+    vals = []
+    for rs in (5e3, 5e4, 5e5):
+        mW, mZ = par0.mW, par0.mZ
+        E3 = (rs * rs + mW * mW - mZ * mZ) / (2 * rs)
+        k = math.sqrt(E3 * E3 - mW * mW)
+        P = np.zeros((1, 4, 4))
+        P[0, 0] = [rs / 2, 0, 0, rs / 2]
+        P[0, 1] = [rs / 2, 0, 0, -rs / 2]
+        P[0, 2] = [E3, k * math.sqrt(1 - 0.09), 0, k * 0.3]
+        P[0, 3] = [rs - E3, -k * math.sqrt(1 - 0.09), 0, -k * 0.3]
+        m2 = 0.0
+        for hf in itertools.product((-1, 1), (-1, 1)):
+            m2 += abs(sum(pr.udx_wpz_amplitudes(P, hf + (0, 0), par0))[0]) ** 2
+        a = pr.udx_wpz_amplitudes(P, (-1, 1, 0, 0), par0)
+        assert min(abs(x[0]) for x in a) > 1e3 * math.sqrt(m2) or rs == 5e3
+        vals.append((m2, abs((a[0] + a[1] - a[2])[0]) ** 2))
+    assert abs(vals[2][0] / vals[1][0] - 1) < 1e-3 and abs(vals[1][0] / vals[0][0] - 1) < 0.01
+    assert vals[1][1] > 1e6 * vals[1][0]
+    P = two_to_two(700.0, 40, PAR.mW, PAR.mZ, seed=8)
+    ref = pr.udx_wpz(P, PAR)
+    assert np.allclose(pr.udx_wpz(random_lorentz(P, seed=9), PAR), ref, rtol=1e-10)
