@@ -48,6 +48,8 @@ EXECUTED_FLOPS_PER_POINT = {
     ("uux_wpwm", "k_me"): 3691.7,
     ("udx_epvegg_bw", "k_ps"): 6256.0,
     ("udx_epvegg_bw", "k_me"): 3121.0,
+    ("udx_wpz", "k_ps"): 3224.0,
+    ("udx_wpz", "k_me"): 2346.6,
 }
 
 # DRAM bytes per point of the mixed-path kernels (dram__bytes_read.sum + dram__bytes_write.sum of one
@@ -189,7 +191,8 @@ def oracle_step(w, events):
     from oracle.sm import SMParams
     fn = {"u u~ > e+ e-": opr.uux_epem, "u d~ > e+ ve g g": opr.udx_epvegg,
           "g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))": opr.gg_ttx_dilep,
-          "u s > d c h h": opr.us_dchh, "g g > g g g g": opr.gluons, "u u~ > w+ w-": opr.uux_wpwm}[w["process"]]
+          "u s > d c h h": opr.us_dchh, "g g > g g g g": opr.gluons, "u u~ > w+ w-": opr.uux_wpwm,
+          "u d~ > w+ z": opr.udx_wpz}[w["process"]]
     par = SMParams()
     P, W, S, T = oxs.generate(oracle_kin(w), par, w["seed"], events)
     return oxs.accumulate(fn(P, par), W, S, T, w["s_ident"])

@@ -31,6 +31,7 @@ PROCESSES = [
     ("u u~ > g g", []),
     ("g g > g g", []),
     ("u u~ > w+ w-", []),
+    ("u d~ > w+ z", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -44,6 +44,11 @@ VARIANTS = {
         cuts=None, s_ident=1.0,
         describe="u u~ > W+ W- (t-channel d, s-channel photon and Z through the WWV vertex), massive RAMBO "
                  "at sqrt(s)=500 GeV, 2^20 points, seed 5"),
+    "udx_wpz": dict(
+        process="u d~ > w+ z", kind="rambo", sqrt_s=500.0, masses=(0, 0, 80.4, 91.1876), n=1 << 20, seed=6,
+        cuts=None, s_ident=1.0,
+        describe="u d~ > W+ Z (u and d exchange, s-channel W through the WWZ vertex), massive RAMBO at "
+                 "sqrt(s)=500 GeV, 2^20 points, seed 6"),
 }
 
 KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3}
