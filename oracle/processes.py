@@ -21,6 +21,7 @@ Functions and their pins (tests/test_oracle_processes.py):
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
   gg_ttx_dilep    g g > t t~ > b e+ ve b~ e- ve~ (doubly resonant diagrams):
                    Ward identity (zero widths), Bose symmetry, boosts
+  uu_uu           u u > u u      : textbook closed form for identical quarks, exact per point
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
@@ -391,6 +392,27 @@ def wpwm_hh_amplitudes(P, hel, par=SMParams()):
 
 
 # --------------------------------------------------------------------------
+# u u > u u  (identical quarks: t- and u-channel gluon exchange with a relative minus sign)
+# --------------------------------------------------------------------------
+def uu_uu(P, par=SMParams()):
+    """Gluon exchange between the two quark lines, u(p0) > u(p2) with u(p1) > u(p3) (t channel) and
+    u(p0) > u(p3) with u(p1) > u(p2) (u channel); exchanging the two identical outgoing quarks
+    gives the relative minus sign.  Colour t^a_{i2 i0} t^a_{i3 i1} and t^a_{i3 i0} t^a_{i2 i1}."""
+    p = [P[:, k] for k in range(4)]
+    gs = par.gs
+    Ct = np.einsum("aji,alk->ikjl", _T, _T)   # [i0, i1, i2, i3]: t^a_{i2 i0} t^a_{i3 i1}
+    Cu = np.einsum("adi,ack->ikcd", _T, _T)   # t^a_{i3 i0} t^a_{i2 i1}
+    tot = 0.0
+    for h in itertools.product(HEL_F, repeat=4):
+        u0, u1 = u_spinor(p[0], h[0]), u_spinor(p[1], h[1])
+        ub2, ub3 = bar(u_spinor(p[2], h[2])), bar(u_spinor(p[3], h[3]))
+        Mt = mdot(vector_prop(p[0] - p[2], ffv_current(ub2, u0, gs, gs)), ffv_current(ub3, u1, gs, gs)) / 1j
+        Mu = mdot(vector_prop(p[0] - p[3], ffv_current(ub3, u0, gs, gs)), ffv_current(ub2, u1, gs, gs)) / 1j
+        tot = tot + colour.colour_sum([Mt, -Mu], [Ct, Cu])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
 # u u~ > W+ W-  (t-channel d exchange, s-channel photon and Z through the WWV vertex)
 # --------------------------------------------------------------------------
 HEL_W = (-1, 0, 1)
@@ -576,6 +598,7 @@ PROCESSES = {
     "g g > t t~": gg_ttx,
     "g g > t t~ > b e+ ve b~ e- ve~": gg_ttx_dilep,
     "u s > d c h h": us_dchh,
+    "u u > u u": uu_uu,
     "u u~ > w+ w-": uux_wpwm,
     "u d~ > w+ z": udx_wpz,
     "g g > g g": gluons,

@@ -419,3 +419,17 @@ def test_udx_wpz_gauge_cancellation_and_boosts():
     P = two_to_two(700.0, 40, PAR.mW, PAR.mZ, seed=8)
     ref = pr.udx_wpz(P, PAR)
     assert np.allclose(pr.udx_wpz(random_lorentz(P, seed=9), PAR), ref, rtol=1e-10)
+
+
+def test_uu_uu_closed_form():
+    """u u > u u (identical quarks): the spin- and colour-averaged |M|^2 of t- and u-channel gluon
+    exchange, g_s^4 [4/9 ((s^2 + u^2)/t^2 + (s^2 + t^2)/u^2) - 8/27 s^2/(u t)]; the interference term
+    carries the relative minus sign of the exchanged identical fermions and the colour factor
+    Tr(t^a t^b t^a t^b)."""
+    P = two_to_two(400.0, 200, seed=4)
+    ref = pr.uu_uu(P, PAR)
+    s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
+    t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
+    u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    cf = PAR.gs ** 4 * (4 / 9 * ((s * s + u * u) / t ** 2 + (s * s + t * t) / u ** 2) - 8 / 27 * s * s / (u * t))
+    assert np.allclose(ref, cf, rtol=1e-12, atol=0)
