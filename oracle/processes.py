@@ -21,7 +21,8 @@ Functions and their pins (tests/test_oracle_processes.py):
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
   gg_ttx_dilep    g g > t t~ > b e+ ve b~ e- ve~ (doubly resonant diagrams):
                    Ward identity (zero widths), Bose symmetry, boosts
-  uu_uu           u u > u u      : textbook closed form for identical quarks, exact per point
+  uu_uu           u u > u u      : gluon, photon and Z exchange; textbook closed forms for
+                   the gluon part and the photon part, exact per point; boosts
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
@@ -394,21 +395,32 @@ def wpwm_hh_amplitudes(P, hel, par=SMParams()):
 # --------------------------------------------------------------------------
 # u u > u u  (identical quarks: t- and u-channel gluon exchange with a relative minus sign)
 # --------------------------------------------------------------------------
-def uu_uu(P, par=SMParams()):
-    """Gluon exchange between the two quark lines, u(p0) > u(p2) with u(p1) > u(p3) (t channel) and
-    u(p0) > u(p3) with u(p1) > u(p2) (u channel); exchanging the two identical outgoing quarks
-    gives the relative minus sign.  Colour t^a_{i2 i0} t^a_{i3 i1} and t^a_{i3 i0} t^a_{i2 i1}."""
+def uu_uu(P, par=SMParams(), bosons=("g", "a", "z")):
+    """Gauge-boson exchange between the two quark lines, u(p0) > u(p2) with u(p1) > u(p3) (t channel)
+    and u(p0) > u(p3) with u(p1) > u(p2) (u channel), for the gluon, the photon and the Z (the
+    diagrams of the Standard Model at tree level); exchanging the two identical outgoing quarks gives
+    the u-channel diagrams their relative minus sign.  Colour: t^a_{i2 i0} t^a_{i3 i1} and
+    t^a_{i3 i0} t^a_{i2 i1} for the gluon, the deltas of the same lines for the photon and the Z.
+    `bosons` selects the exchanged bosons (the pins take them one at a time)."""
     p = [P[:, k] for k in range(4)]
-    gs = par.gs
-    Ct = np.einsum("aji,alk->ikjl", _T, _T)   # [i0, i1, i2, i3]: t^a_{i2 i0} t^a_{i3 i1}
-    Cu = np.einsum("adi,ack->ikcd", _T, _T)   # t^a_{i3 i0} t^a_{i2 i1}
+    d = np.eye(3, dtype=complex)
+    col = {"g": (np.einsum("aji,alk->ikjl", _T, _T), np.einsum("adi,ack->ikcd", _T, _T)),
+           "ew": (np.einsum("ji,lk->ikjl", d, d), np.einsum("di,ck->ikcd", d, d))}
+    ga = _a_coupling("u", par)
+    cpl = {"g": ((par.gs, par.gs), 0.0, 0.0, "g"), "a": ((ga, ga), 0.0, 0.0, "ew"),
+           "z": (_z_couplings("u", par), par.mZ, par.wZ, "ew")}
     tot = 0.0
     for h in itertools.product(HEL_F, repeat=4):
         u0, u1 = u_spinor(p[0], h[0]), u_spinor(p[1], h[1])
         ub2, ub3 = bar(u_spinor(p[2], h[2])), bar(u_spinor(p[3], h[3]))
-        Mt = mdot(vector_prop(p[0] - p[2], ffv_current(ub2, u0, gs, gs)), ffv_current(ub3, u1, gs, gs)) / 1j
-        Mu = mdot(vector_prop(p[0] - p[3], ffv_current(ub3, u0, gs, gs)), ffv_current(ub2, u1, gs, gs)) / 1j
-        tot = tot + colour.colour_sum([Mt, -Mu], [Ct, Cu])
+        amps, tens = [], []
+        for b in bosons:
+            (gl, gr), m, w, c = cpl[b]
+            Mt = mdot(vector_prop(p[0] - p[2], ffv_current(ub2, u0, gl, gr), m, w), ffv_current(ub3, u1, gl, gr)) / 1j
+            Mu = mdot(vector_prop(p[0] - p[3], ffv_current(ub3, u0, gl, gr), m, w), ffv_current(ub2, u1, gl, gr)) / 1j
+            amps += [Mt, -Mu]
+            tens += list(col[c])
+        tot = tot + colour.colour_sum(amps, tens)
     return tot / 36.0
 
 

@@ -423,13 +423,23 @@ def test_udx_wpz_gauge_cancellation_and_boosts():
 
 def test_uu_uu_closed_form():
     """u u > u u (identical quarks): the spin- and colour-averaged |M|^2 of t- and u-channel gluon
-    exchange, g_s^4 [4/9 ((s^2 + u^2)/t^2 + (s^2 + t^2)/u^2) - 8/27 s^2/(u t)]; the interference term
-    carries the relative minus sign of the exchanged identical fermions and the colour factor
-    Tr(t^a t^b t^a t^b)."""
+    exchange alone, g_s^4 [4/9 ((s^2 + u^2)/t^2 + (s^2 + t^2)/u^2) - 8/27 s^2/(u t)], whose
+    interference term carries the relative minus sign of the exchanged identical fermions and the
+    colour factor Tr(t^a t^b t^a t^b); photon exchange alone, the Moller form times the colour
+    factors 1 and 1/3; the full gluon + photon + Z result is Lorentz invariant."""
     P = two_to_two(400.0, 200, seed=4)
-    ref = pr.uu_uu(P, PAR)
     s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
     t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
     u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    ref = pr.uu_uu(P, PAR, bosons=("g",))
     cf = PAR.gs ** 4 * (4 / 9 * ((s * s + u * u) / t ** 2 + (s * s + t * t) / u ** 2) - 8 / 27 * s * s / (u * t))
     assert np.allclose(ref, cf, rtol=1e-12, atol=0)
+    # photon alone: the Moller form with colour factors 1 (direct) and 1/3 (interference)
+    eq4 = (PAR.e * CHARGE["u"]) ** 4
+    ref = pr.uu_uu(P, PAR, bosons=("a",))
+    cf = eq4 * (2 * ((s * s + u * u) / t ** 2 + (s * s + t * t) / u ** 2) + 4 / 3 * s * s / (u * t))
+    assert np.allclose(ref, cf, rtol=1e-12, atol=0)
+    # all bosons: Lorentz invariant, and different from the pure-QCD value by the electroweak terms
+    full = pr.uu_uu(P, PAR)
+    assert np.allclose(pr.uu_uu(random_lorentz(P, seed=10), PAR), full, rtol=1e-10)
+    assert not np.allclose(full, pr.uu_uu(P, PAR, bosons=("g",)), rtol=1e-3)
