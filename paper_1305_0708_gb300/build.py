@@ -32,6 +32,7 @@ PROCESSES = [
     ("g g > g g", []),
     ("u u~ > w+ w-", []),
     ("u d~ > w+ z", []),
+    ("u u > u u", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -287,3 +287,20 @@ def test_ew_boson_pair_parity(B, key, prec):
     assert acc.n_acc == nacc == n and acc.n_try == ntry
     tol = 1e-11 if prec == 0 else 1e-5
     assert acc.sum_w == pytest.approx(sw, rel=tol) and acc.sum_w2 == pytest.approx(sw2, rel=2 * tol)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_identical_quarks_parity(B, prec):
+    """u u > u u: gluon, photon and Z exchange in the t and u channels, whose relative minus sign the
+    compiler's fermion-permutation sign must supply; me_eval on the oracle's two-body points at
+    |cos theta| < 0.95 (away from the forward poles)."""
+    n = 2000
+    P, _, _, _ = oxs.generate({"kind": "2to2", "sqrt_s": 400.0}, PAR, 21, np.arange(n))
+    P = P[np.abs(P[:, 2, 3] / P[:, 2, 0]) < 0.95]
+    ref = opr.uu_uu(P, PAR)
+    got = eval_gpu(B, "u u > u u", P, prec)
+    if prec == 0:
+        assert np.all(np.abs(got - ref) <= fp64_tolerance(opr.uu_uu, P, ref))
+    else:
+        rel = np.abs(got / ref - 1)
+        assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
