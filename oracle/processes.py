@@ -23,6 +23,7 @@ Functions and their pins (tests/test_oracle_processes.py):
                    Ward identity (zero widths), Bose symmetry, boosts
   uu_uu           u u > u u      : gluon, photon and Z exchange; textbook closed forms for
                    the gluon part and the photon part, exact per point; boosts
+  uux_zz          u u~ > z z     : closed form, exact per point; Bose symmetry
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
@@ -425,6 +426,27 @@ def uu_uu(P, par=SMParams(), bosons=("g", "a", "z")):
 
 
 # --------------------------------------------------------------------------
+# u u~ > Z Z  (t- and u-channel u exchange; no triple-gauge vertex)
+# --------------------------------------------------------------------------
+def uux_zz(P, par=SMParams()):
+    """The two diagrams of u(p0) u~(p1) > Z(p2) Z(p3): both orders of the two Z emissions along the
+    quark line."""
+    p = [P[:, k] for k in range(4)]
+    zl, zr = _z_couplings("u", par)
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_W):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        e2 = polarisation(p[2], h[2], mass=par.mZ).conj()
+        e3 = polarisation(p[3], h[3], mass=par.mZ).conj()
+        G2 = (vector_insertion(e2, zl, zr), p[2])
+        G3 = (vector_insertion(e3, zl, zr), p[3])
+        M = (fermion_line(vb, u, p[0], [G2, G3]) + fermion_line(vb, u, p[0], [G3, G2])) / 1j
+        tot = tot + colour.colour_sum([M], [_DELTA3])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
 # u u~ > W+ W-  (t-channel d exchange, s-channel photon and Z through the WWV vertex)
 # --------------------------------------------------------------------------
 HEL_W = (-1, 0, 1)
@@ -611,6 +633,7 @@ PROCESSES = {
     "g g > t t~ > b e+ ve b~ e- ve~": gg_ttx_dilep,
     "u s > d c h h": us_dchh,
     "u u > u u": uu_uu,
+    "u u~ > z z": uux_zz,
     "u u~ > w+ w-": uux_wpwm,
     "u d~ > w+ z": udx_wpz,
     "g g > g g": gluons,

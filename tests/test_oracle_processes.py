@@ -443,3 +443,19 @@ def test_uu_uu_closed_form():
     full = pr.uu_uu(P, PAR)
     assert np.allclose(pr.uu_uu(random_lorentz(P, seed=10), PAR), full, rtol=1e-10)
     assert not np.allclose(full, pr.uu_uu(P, PAR, bosons=("g",)), rtol=1e-3)
+
+
+def test_uux_zz_closed_form():
+    """u u~ > Z Z: per point, (gL^4 + gR^4)/3 [t/u + u/t + 4 mZ^2 s/(t u) - mZ^4 (1/t^2 + 1/u^2)] (spin
+    sum 4, colour sum 3, average 1/36), and symmetric under the exchange of the two Z bosons."""
+    P = two_to_two(500.0, 100, PAR.mZ, PAR.mZ, seed=4)
+    ref = pr.uux_zz(P, PAR)
+    s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
+    t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
+    u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    m2 = PAR.mZ ** 2
+    gl = PAR.gz * (T3["u"] - CHARGE["u"] * PAR.sw2)
+    gr = PAR.gz * (-CHARGE["u"] * PAR.sw2)
+    cf = (gl ** 4 + gr ** 4) / 3.0 * (t / u + u / t + 4 * m2 * s / (t * u) - m2 * m2 * (1 / t ** 2 + 1 / u ** 2))
+    assert np.allclose(ref, cf, rtol=1e-12, atol=0)
+    assert np.allclose(pr.uux_zz(P[:, [0, 1, 3, 2]], PAR), ref, rtol=1e-12)
