@@ -24,6 +24,7 @@ Functions and their pins (tests/test_oracle_processes.py):
   uu_uu           u u > u u      : gluon, photon and Z exchange; textbook closed forms for
                    the gluon part and the photon part, exact per point; boosts
   uux_zz          u u~ > z z     : closed form, exact per point; Bose symmetry
+  uux_zh          u u~ > z h     : closed form from the trace, exact per point
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
@@ -447,6 +448,26 @@ def uux_zz(P, par=SMParams()):
 
 
 # --------------------------------------------------------------------------
+# u u~ > Z H  (s-channel Z through the ZZH vertex)
+# --------------------------------------------------------------------------
+def uux_zh(P, par=SMParams()):
+    """u(p0) u~(p1) > Z(p2) H(p3): the quark current into the Z propagator and the ZZH vertex
+    i g_ZZH g^{mu nu}, g_ZZH = gZ mZ (Sect. 4.2 VVS)."""
+    p = [P[:, k] for k in range(4)]
+    zl, zr = _z_couplings("u", par)
+    gzzh = par.gz * par.mZ
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ez = polarisation(p[2], h[2], mass=par.mZ).conj()
+        Z = vector_prop(p[0] + p[1], ffv_current(vb, u, zl, zr), par.mZ, par.wZ)
+        M = 1j * gzzh * mdot(Z, ez) / 1j
+        tot = tot + colour.colour_sum([M], [_DELTA3])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
 # u u~ > W+ W-  (t-channel d exchange, s-channel photon and Z through the WWV vertex)
 # --------------------------------------------------------------------------
 HEL_W = (-1, 0, 1)
@@ -634,6 +655,7 @@ PROCESSES = {
     "u s > d c h h": us_dchh,
     "u u > u u": uu_uu,
     "u u~ > z z": uux_zz,
+    "u u~ > z h": uux_zh,
     "u u~ > w+ w-": uux_wpwm,
     "u d~ > w+ z": udx_wpz,
     "g g > g g": gluons,

@@ -459,3 +459,19 @@ def test_uux_zz_closed_form():
     cf = (gl ** 4 + gr ** 4) / 3.0 * (t / u + u / t + 4 * m2 * s / (t * u) - m2 * m2 * (1 / t ** 2 + 1 / u ** 2))
     assert np.allclose(ref, cf, rtol=1e-12, atol=0)
     assert np.allclose(pr.uux_zz(P[:, [0, 1, 3, 2]], PAR), ref, rtol=1e-12)
+
+
+def test_uux_zh_closed_form():
+    """u u~ > Z H through the s-channel Z: the spin trace with the Z polarisation sum gives, per point,
+    g_ZZH^2 (gL^2 + gR^2) [s/2 + 2 (p1.k)(p2.k)/mZ^2] / (6 ((s - mZ^2)^2 + mZ^2 wZ^2)) (colour sum 3,
+    average 1/36; the q q/mZ^2 part of the propagator vanishes on the massless current)."""
+    P = two_to_two(600.0, 100, PAR.mZ, PAR.mH, seed=11)
+    ref = pr.uux_zh(P, PAR)
+    s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
+    k = P[:, 2]
+    gl = PAR.gz * (T3["u"] - CHARGE["u"] * PAR.sw2)
+    gr = PAR.gz * (-CHARGE["u"] * PAR.sw2)
+    m2 = PAR.mZ ** 2
+    cf = ((PAR.gz * PAR.mZ) ** 2 * (gl ** 2 + gr ** 2) * (s / 2 + 2 * mdot(P[:, 0], k) * mdot(P[:, 1], k) / m2)
+          / (6.0 * ((s - m2) ** 2 + m2 * PAR.wZ ** 2)))
+    assert np.allclose(ref, cf, rtol=1e-12, atol=0)
