@@ -192,7 +192,8 @@ def oracle_step(w, events):
     fn = {"u u~ > e+ e-": opr.uux_epem, "u d~ > e+ ve g g": opr.udx_epvegg,
           "g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))": opr.gg_ttx_dilep,
           "u s > d c h h": opr.us_dchh, "g g > g g g g": opr.gluons, "u u~ > w+ w-": opr.uux_wpwm,
-          "u d~ > w+ z": opr.udx_wpz}[w["process"]]
+          "u d~ > w+ z": opr.udx_wpz, "u u~ > z z": opr.uux_zz,
+          "u u~ > z h": opr.uux_zh}[w["process"]]
     par = SMParams()
     P, W, S, T = oxs.generate(oracle_kin(w), par, w["seed"], events)
     return oxs.accumulate(fn(P, par), W, S, T, w["s_ident"])

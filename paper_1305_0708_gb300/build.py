@@ -33,6 +33,8 @@ PROCESSES = [
     ("u u~ > w+ w-", []),
     ("u d~ > w+ z", []),
     ("u u > u u", []),
+    ("u u~ > z z", []),
+    ("u u~ > z h", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -49,6 +49,15 @@ VARIANTS = {
         cuts=None, s_ident=1.0,
         describe="u d~ > W+ Z (u and d exchange, s-channel W through the WWZ vertex), massive RAMBO at "
                  "sqrt(s)=500 GeV, 2^20 points, seed 6"),
+    "uux_zz": dict(
+        process="u u~ > z z", kind="rambo", sqrt_s=500.0, masses=(0, 0, 91.1876, 91.1876), n=1 << 20, seed=7,
+        cuts=None, s_ident=0.5,
+        describe="u u~ > Z Z (t- and u-channel u exchange, identical Z bosons), massive RAMBO at "
+                 "sqrt(s)=500 GeV, 2^20 points, seed 7"),
+    "uux_zh": dict(
+        process="u u~ > z h", kind="rambo", sqrt_s=500.0, masses=(0, 0, 91.1876, 125.0), n=1 << 20, seed=8,
+        cuts=None, s_ident=1.0,
+        describe="u u~ > Z H (s-channel Z, ZZH vertex), massive RAMBO at sqrt(s)=500 GeV, 2^20 points, seed 8"),
 }
 
 KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3}

@@ -304,3 +304,31 @@ def test_identical_quarks_parity(B, prec):
     else:
         rel = np.abs(got / ref - 1)
         assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("key", ["uux_zz", "uux_zh"])
+def test_zz_zh_production_parity(B, key, prec):
+    """u u~ > Z Z (identical massive vectors, identical-particle factor 1/2) and u u~ > Z H (ZZH vertex,
+    external scalar): me_eval on the oracle's massive-RAMBO points and the Monte Carlo sums against the
+    oracle."""
+    from paper_1305_0708_gb300.workloads import VARIANTS
+    w = VARIANTS[key]
+    fn = {"uux_zz": opr.uux_zz, "uux_zh": opr.uux_zh}[key]
+    n = 1500
+    P, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(n))
+    ref = fn(P, PAR)
+    got = eval_gpu(B, w["process"], P, prec)
+    if prec == 0:
+        assert np.all(np.abs(got - ref) <= fp64_tolerance(fn, P, ref))
+    else:
+        rel = np.abs(got / ref - 1)
+        assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
+    kin = B.make_kin(**kin_args(w))
+    h = B.me_create(w["process"], None, prec)
+    acc = B.xsec_step(h, w["seed"], 0, n, kin)
+    B.me_destroy(h)
+    sw, sw2, nacc, ntry = oxs.accumulate(ref, W, S, T, w["s_ident"])
+    assert acc.n_acc == nacc == n and acc.n_try == ntry
+    tol = 1e-11 if prec == 0 else 1e-5
+    assert acc.sum_w == pytest.approx(sw, rel=tol) and acc.sum_w2 == pytest.approx(sw2, rel=2 * tol)
