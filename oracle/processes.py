@@ -25,11 +25,15 @@ Functions and their pins (tests/test_oracle_processes.py):
                    the gluon part and the photon part, exact per point; boosts
   uux_zz          u u~ > z z     : closed form, exact per point; Bose symmetry
   uux_zh          u u~ > z h     : closed form from the trace, exact per point
+  udx_wph         u d~ > w+ h    : closed form from the trace, exact per point
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
   udx_wpz         u d~ > w+ z    : gauge cancellation of the longitudinal amplitude
                    (the WWZ vertex with an incoming W), boosts
+  uux_wpwma       u u~ > w+ w- a : the photon's Ward identity with zero W and Z widths (the
+                   fifteen diagrams cancel only with the quartic WWAA and WWAZ vertices),
+                   the soft-photon limit against the eikonal factor times u u~ > w+ w-, boosts
   us_dchh         u s > d c h h  (WW fusion): Higgs-exchange symmetry, boosts;
                    its W current is pinned by u d~ > e+ ve, its WWH/WWHH/HHH
                    couplings and diagram set by the gauge cancellation of the
@@ -468,6 +472,26 @@ def uux_zh(P, par=SMParams()):
 
 
 # --------------------------------------------------------------------------
+# u d~ > W+ H  (s-channel W through the WWH vertex)
+# --------------------------------------------------------------------------
+def udx_wph(P, par=SMParams()):
+    """u(p0) d~(p1) > W+(p2) H(p3): the quark current into the W propagator and the WWH vertex
+    i g_WWH g^{mu nu}, g_WWH = g mW (Sect. 4.2 VVS)."""
+    p = [P[:, k] for k in range(4)]
+    gw = par.g / np.sqrt(2.0)
+    gwwh = par.g * par.mW
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ew = polarisation(p[2], h[2], mass=par.mW).conj()
+        W = vector_prop(p[0] + p[1], ffv_current(vb, u, gw, 0.0), par.mW, par.wW)
+        M = 1j * gwwh * mdot(W, ew) / 1j
+        tot = tot + colour.colour_sum([M], [_DELTA3])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
 # u u~ > W+ W-  (t-channel d exchange, s-channel photon and Z through the WWV vertex)
 # --------------------------------------------------------------------------
 HEL_W = (-1, 0, 1)
@@ -535,6 +559,87 @@ def udx_wpz(P, par=SMParams()):
     tot = 0.0
     for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_W):
         M = sum(udx_wpz_amplitudes(P, h, par))
+        tot = tot + colour.colour_sum([M], [_DELTA3])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
+# u u~ > W+ W- gamma  (quark-line emissions, W-line emissions, the WWAA and WWAZ quartic vertices)
+# --------------------------------------------------------------------------
+def vvvv(gg, V1, V2, V3, V4):
+    """The four-vector function of Sect. 4.2 (VVVV): gg [(V1.V4)(V2.V3) - (V1.V3)(V2.V4)], the
+    Lagrangian of four distinct vectors evaluated on the four wavefunctions."""
+    return gg * (mdot(V1, V4) * mdot(V2, V3) - mdot(V1, V3) * mdot(V2, V4))
+
+
+def ww33(gg, Wm, V2, Wp, V4):
+    """The electroweak quartic W- W3 W+ W3 vertex as the sum of its two channels (Sect. 4.2 VVVV,
+    the W W W3 W3 identification): Gamma(gg; W-, V2, W+, V4) + Gamma(gg; W-, V4, W+, V2), with the
+    vectors named by their outgoing quantum numbers and gg = g^2 times the W3 projections of the two
+    neutral bosons (sw^2 for two photons, sw cw for a photon and a Z, cw^2 for two Z).  Its factor
+    in i M is i times this value."""
+    return vvvv(gg, Wm, V2, Wp, V4) + vvvv(gg, Wm, V4, Wp, V2)
+
+
+def uux_wpwma_amplitudes(P, hel, par=SMParams(), eps_override=None, widths=True):
+    """The fifteen diagrams of u(p0) u~(p1) > W+(p2) W-(p3) gamma(p4) for fixed helicities, returned
+    as M values in five groups:
+      line   the photon on the u, d or u segment of the t-channel quark line (3),
+      wline  the photon from the W+ or the W- of the t-channel graph (2),
+      isr    the photon from the quark line before or after the s-channel photon or Z that turns
+             into W+ W- (4),
+      wv     the s-channel photon or Z into W+* W- or W+ W-* with the photon from the W (4),
+      quart  the s-channel photon or Z into W+ W- gamma through the quartic vertex (2).
+    The WWV vertex is the one of uux_wpwm_amplitudes; the quartic one is ww33.  eps_override
+    replaces the photon's polarisation vector (the Ward identity); widths=False sets the W and Z
+    widths to zero."""
+    p = [P[:, k] for k in range(5)]
+    gw = par.g / np.sqrt(2.0)
+    wW = par.wW if widths else 0.0
+    wZ = par.wZ if widths else 0.0
+    u = u_spinor(p[0], hel[0])
+    vb = bar(v_spinor(p[1], hel[1]))
+    ep = polarisation(p[2], hel[2], mass=par.mW).conj()
+    em = polarisation(p[3], hel[3], mass=par.mW).conj()
+    ea = polarisation(p[4], hel[4]).conj() if eps_override is None else eps_override
+    Wp_ins = vector_insertion(ep, gw, 0.0)
+    Wm_ins = vector_insertion(em, gw, 0.0)
+    Au = vector_insertion(ea, *(2 * (_a_coupling("u", par),)))
+    Ad = vector_insertion(ea, *(2 * (_a_coupling("d", par),)))
+    out = {}
+    out["line"] = [fermion_line(vb, u, p[0], [(Au, p[4]), (Wp_ins, p[2]), (Wm_ins, p[3])]),
+                   fermion_line(vb, u, p[0], [(Wp_ins, p[2]), (Ad, p[4]), (Wm_ins, p[3])]),
+                   fermion_line(vb, u, p[0], [(Wp_ins, p[2]), (Wm_ins, p[3]), (Au, p[4])])]
+    # off-shell W+* -> W+ gamma and W-* -> W- gamma, propagated (the WWA vertex, coupling e)
+    Pp = p[2] + p[4]
+    Pm = p[3] + p[4]
+    Wps = vector_prop(Pp, -1j * par.e * vvv_out(ep, -p[2], ea, -p[4], Pp, 1.0), par.mW, wW)
+    Wms = vector_prop(Pm, -1j * par.e * vvv_out(ea, -p[4], em, -p[3], Pm, 1.0), par.mW, wW)
+    out["wline"] = [fermion_line(vb, u, p[0], [(vector_insertion(Wps, gw, 0.0), Pp), (Wm_ins, p[3])]),
+                    fermion_line(vb, u, p[0], [(Wp_ins, p[2]), (vector_insertion(Wms, gw, 0.0), Pm)])]
+    q = p[0] + p[1]
+    Q = p[2] + p[3]
+    ga = _a_coupling("u", par)
+    out["isr"], out["wv"], out["quart"] = [], [], []
+    for gv, (gl, gr), mV, wV, g4 in ((par.e, (ga, ga), 0.0, 0.0, par.g ** 2 * par.sw2),
+                                     (par.g * par.cw, _z_couplings("u", par), par.mZ, wZ,
+                                      par.g ** 2 * par.sw * par.cw)):
+        # photon from the quark line, then V* (momentum p2 + p3) into W+ W-
+        X = -1j * gv * vvv_out(em, -p[3], ep, -p[2], Q, 1.0)
+        Vins = vector_insertion(vector_prop(Q, X, mV, wV), gl, gr)
+        out["isr"] += [fermion_line(vb, u, p[0], [(Au, p[4]), (Vins, Q)]),
+                       fermion_line(vb, u, p[0], [(Vins, Q), (Au, p[4])])]
+        V = vector_prop(q, ffv_current(vb, u, gl, gr), mV, wV)
+        out["wv"] += [-1j * gv * mdot(vvv_out(em, -p[3], Wps, -Pp, q, 1.0), V),
+                      -1j * gv * mdot(vvv_out(Wms, -Pm, ep, -p[2], q, 1.0), V)]
+        out["quart"] += [1j * ww33(g4, em, ea, ep, V)]
+    return {k: [x / 1j for x in v] for k, v in out.items()}
+
+
+def uux_wpwma(P, par=SMParams()):
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_W, HEL_V):
+        M = sum(sum(v) for v in uux_wpwma_amplitudes(P, h, par).values())
         tot = tot + colour.colour_sum([M], [_DELTA3])
     return tot / 36.0
 
@@ -656,6 +761,8 @@ PROCESSES = {
     "u u > u u": uu_uu,
     "u u~ > z z": uux_zz,
     "u u~ > z h": uux_zh,
+    "u d~ > w+ h": udx_wph,
+    "u u~ > w+ w- a": uux_wpwma,
     "u u~ > w+ w-": uux_wpwm,
     "u d~ > w+ z": udx_wpz,
     "g g > g g": gluons,

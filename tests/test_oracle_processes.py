@@ -475,3 +475,89 @@ def test_uux_zh_closed_form():
     cf = ((PAR.gz * PAR.mZ) ** 2 * (gl ** 2 + gr ** 2) * (s / 2 + 2 * mdot(P[:, 0], k) * mdot(P[:, 1], k) / m2)
           / (6.0 * ((s - m2) ** 2 + m2 * PAR.wZ ** 2)))
     assert np.allclose(ref, cf, rtol=1e-12, atol=0)
+
+
+def test_udx_wph_closed_form():
+    """u d~ > W+ H through the s-channel W: the trace of the purely left-handed current with the W
+    polarisation sum gives, per point, g_WWH^2 gW^2 [s/2 + 2 (p1.k)(p2.k)/mW^2] / (6 ((s - mW^2)^2 +
+    mW^2 wW^2)), gW = g/sqrt2 (the ZH form with gL = gW, gR = 0)."""
+    P = two_to_two(600.0, 100, PAR.mW, PAR.mH, seed=12)
+    ref = pr.udx_wph(P, PAR)
+    s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
+    k = P[:, 2]
+    m2 = PAR.mW ** 2
+    cf = ((PAR.g * PAR.mW) ** 2 * (PAR.g ** 2 / 2) * (s / 2 + 2 * mdot(P[:, 0], k) * mdot(P[:, 1], k) / m2)
+          / (6.0 * ((s - m2) ** 2 + m2 * PAR.wW ** 2)))
+    assert np.allclose(ref, cf, rtol=1e-12, atol=0)
+
+
+def _wwa_points(sqrt_s, n, seed, par=PAR):
+    """u u~ > W+ W- gamma points from the oracle's massive RAMBO (masses mW, mW, 0)."""
+    u = np.random.default_rng(seed).uniform(0.01, 0.99, (n, 12))
+    pf, _ = ps.rambo_massive(sqrt_s, [par.mW, par.mW, 0.0], u)
+    P = np.zeros((n, 5, 4))
+    P[:, 0], P[:, 1] = ps.incoming(sqrt_s, n)
+    P[:, 2:] = pf
+    return P
+
+
+def test_uux_wpwma_ward_identity():
+    """The photon's polarisation replaced by its momentum: with zero W and Z widths the fifteen
+    diagrams of u u~ > W+ W- gamma sum to zero for every helicity of the quarks and W bosons, to
+    rounding of the individual diagrams; without the two quartic diagrams, or with the quartic
+    vertex's sign flipped, the sum is of the order of the diagrams."""
+    P = _wwa_points(700.0, 40, seed=21)
+    k = P[:, 4].astype(complex)
+    for h in itertools.product((-1, 1), (-1, 1), (-1, 0, 1), (-1, 0, 1)):
+        a = pr.uux_wpwma_amplitudes(P, h + (1,), PAR, eps_override=k, widths=False)
+        allv = [x for v in a.values() for x in v]
+        scale = sum(abs(x) for x in allv)
+        tot = sum(allv)
+        assert np.all(abs(tot) <= 1e-12 * scale)
+        if h[2] == 0 and h[3] == 0 and h[0] != h[1]:
+            noq = sum(x for key, v in a.items() if key != "quart" for x in v)
+            assert np.all(abs(noq) > 1e-6 * scale)
+            flip = noq - sum(a["quart"])
+            assert np.all(abs(flip) > 1e-6 * scale)
+
+
+def test_uux_wpwma_soft_photon_limit():
+    """As the photon's energy w goes to zero, |M|^2(u u~ > W+ W- gamma) summed over the photon's
+    helicities tends to -J.J |M|^2(u u~ > W+ W-) with the eikonal current J = e sum_i eta_i Q_i p_i /
+    (p_i.k) over the four charged legs (eta = -1 incoming, +1 outgoing), the deviation falling in
+    proportion to w.  Zero W width: a fixed width regulates the W propagator next to the emitted soft
+    photon (1 / (2 p.k + i mW wW)) and removes the W terms of the eikonal limit."""
+    par = PAR.with_(wW=0.0)
+    base = two_to_two(500.0, 8, par.mW, par.mW, seed=22)
+    m2 = pr.uux_wpwm(base, par)
+    nhat = np.array([0.48, -0.6, 0.64])
+    devs = []
+    for w in (1e-1, 1e-2):
+        P = np.zeros((8, 5, 4))
+        P[:, :2] = base[:, :2]
+        kph = np.concatenate([[w], w * nhat])
+        Qv = base[:, 0] + base[:, 1] - kph
+        Q2 = mdot(Qv, Qv)
+        pst = np.sqrt(Q2 / 4 - par.mW ** 2)
+        d = base[:, 2, 1:] / np.linalg.norm(base[:, 2, 1:], axis=1)[:, None]
+        rest = np.zeros((8, 2, 4))
+        rest[:, 0, 0] = rest[:, 1, 0] = np.sqrt(Q2) / 2
+        rest[:, 0, 1:] = pst[:, None] * d
+        rest[:, 1, 1:] = -pst[:, None] * d
+        for i in range(8):
+            beta = Qv[i, 1:] / Qv[i, 0]
+            P[i, 2:4] = boost(rest[i], beta)
+        P[:, 4] = kph
+        assert np.allclose(P[:, 0] + P[:, 1], P[:, 2:].sum(axis=1), atol=1e-9)
+        m3 = pr.uux_wpwma(P, par)
+        qs = [(-1, CHARGE["u"], P[:, 0]), (-1, -CHARGE["u"], P[:, 1]), (1, 1.0, P[:, 2]), (1, -1.0, P[:, 3])]
+        J = sum(eta * qc * p / mdot(p, P[:, 4])[:, None] for eta, qc, p in qs) * par.e
+        soft = -mdot(J, J) * m2
+        devs.append(np.max(np.abs(m3 / soft - 1)))
+    assert devs[1] < 2e-3 and devs[1] < devs[0] / 5
+
+
+def test_uux_wpwma_boosts():
+    """|M|^2 of u u~ > W+ W- gamma is invariant under random Lorentz transformations."""
+    P = _wwa_points(600.0, 12, seed=23)
+    assert np.allclose(pr.uux_wpwma(random_lorentz(P, seed=24), PAR), pr.uux_wpwma(P, PAR), rtol=1e-10)
