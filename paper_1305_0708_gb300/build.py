@@ -35,6 +35,8 @@ PROCESSES = [
     ("u u > u u", []),
     ("u u~ > z z", []),
     ("u u~ > z h", []),
+    ("u d~ > w+ h", []),
+    ("u u~ > w+ w- a", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -304,9 +304,30 @@ class _Emitter:
             by_slot = {k[1]: k for k in kids}
             o = nd.out_slot
             a, b = by_slot[(o + 1) % 3], by_slot[(o + 2) % 3]
+            # a massive line keeps the k k / m^2 term unless its current is conserved
+            massive = not part.massless and nid not in p.conserved
+            mc2 = f"inv_mc2_{part.mass}" if massive else "me::mk(R(0), R(0))"
+            if massive:
+                self.cpl(part.mass)
+                self.cpl(part.width)
             E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::vvv_current<R>({a[2]}, k{a[0]}, {b[2]}, k{b[0]}, "
-              f"(R){g}), k{nid}, inv{nid}, false, me::mk(R(0), R(0)));")
-            self.flops32 += self._vvv_current_flops(a[2], b[2]) + 8
+              f"(R){g}), k{nid}, inv{nid}, {str(massive).lower()}, {mc2});")
+            self.flops32 += self._vvv_current_flops(a[2], b[2]) + (60 if massive else 8)
+        elif v.kind == "VVVV" and v.colour != "ff":
+            # electroweak quartic: C [T_a + T_b - 2 T_pair], T_j the current of pairing j
+            g = self.cpl(v.couplings[0])
+            slot = {s: nm for _, s, nm in kids}
+            o = nd.out_slot
+            t = [self._v4_term(o, list(_PAIRINGS[j]), slot) for j in range(3)]
+            ta, tb = [t[j] for j in range(3) if j != v.pair]
+            massive = not part.massless and nid not in p.conserved
+            mc2 = f"inv_mc2_{part.mass}" if massive else "me::mk(R(0), R(0))"
+            if massive:
+                self.cpl(part.mass)
+                self.cpl(part.width)
+            E(f"  const me::W4<R> {name} = me::prop_vec<R>(me::w4_quartic<R>({ta}, {tb}, {t[v.pair]}, (R){g}), "
+              f"k{nid}, inv{nid}, {str(massive).lower()}, {mc2});")
+            self.flops32 += 3 * 54 + 40 + (60 if massive else 8)
         elif v.kind == "VVVV":
             g = self.cpl(v.couplings[0])
             slot = {s: nm for _, s, nm in kids}
@@ -384,6 +405,13 @@ class _Emitter:
             k1 = [c for c, s, _ in kids if s == 1][0]
             expr = f"me::vvv_amp<R>({slot[0]}, k{k0}, {slot[1]}, k{k1}, {slot[2]}, (R){g})"
             self.flops32 += self._vvv_current_flops(slot[0], slot[1]) + (18 if slot[2] in self.pv else 30)
+        elif v.kind == "VVVV" and v.colour != "ff":
+            g = self.cpl(v.couplings[0])
+            prods = [f"me::mdot<R>({slot[x]}, {slot[y]}) * me::mdot<R>({slot[z]}, {slot[w]})"
+                     for (x, y), (z, w) in _PAIRINGS]
+            pa, pb = [prods[j] for j in range(3) if j != v.pair]
+            expr = f"(R){g} * ({pa} + {pb} - R(2) * ({prods[v.pair]}))"
+            self.flops32 += 6 * 30 + 3 * 6 + 12
         elif v.kind == "VVVV":
             g = self.cpl(v.couplings[0])
             (x, y), (z, w) = _PAIRINGS[a.struct]

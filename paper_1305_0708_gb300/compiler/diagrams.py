@@ -162,7 +162,7 @@ def generate(proc):
                             continue
                         out = rest[0]
                         ptype = PARTICLES[v.fields[out]].anti
-                        structs = [0, 1, 2] if v.kind == "VVVV" else [-1]
+                        structs = [0, 1, 2] if v.colour == "ff" else [-1]
                         for st in structs:
                             nd = Node(len(nodes), frozenset().union(*[nodes[c].legs for c in combo]), ptype,
                                       vertex=v, slots=tuple(perm), children=tuple(combo), out_slot=out, struct=st)
@@ -180,7 +180,7 @@ def generate(proc):
                 for v, perm, rest in _vertex_matches(types):
                     if rest:
                         continue
-                    structs = [0, 1, 2] if v.kind == "VVVV" else [-1]
+                    structs = [0, 1, 2] if v.colour == "ff" else [-1]
                     for st in structs:
                         amps.append(Amplitude(len(amps), v, tuple(perm), combo, st))
     nodes, amps = _prune(nodes, amps, proc)

@@ -86,12 +86,15 @@ class Vertex:
     kind: "FFV" (fields f~, f, V), "VVV", "VVVV", "VVS", "VVSS", "SSS".
     couplings: names resolved by couplings() at me_create time; for FFV
     (gL, gR).  colour: "delta" (f~ f), "T" (f~ f g), "f" (ggg), "ff" (gggg).
+    pair: for a colourless VVVV vertex, the slot pairing (0: (01)(23), 1: (02)(13), 2: (03)(12))
+    whose metric product enters with -2 while the other two enter with +1.
     """
     fields: tuple
     kind: str
     couplings: tuple
     colour: str = "none"
     phase: int = -1   # power of i of the vertex factor; -1: the default of its kind
+    pair: int = -1
 
 
 def _ffv_vertices():
@@ -121,6 +124,14 @@ VERTICES = _ffv_vertices() + [
     # quantum numbers, i.e. incoming W+, W-, V here): -i g_V times the Lorentz structure
     Vertex(("w+", "w-", "a"), "VVV", ("GWWA",), "none", phase=3),
     Vertex(("w+", "w-", "z"), "VVV", ("GWWZ",), "none", phase=3),
+    # electroweak quartic vertices (Sect. 4.2 VVVV, the W W W W and W W W3 W3 terms with each
+    # vertex's two channels summed): i C [g^{ab} g^{cd} summed over the two pairings other than
+    # `pair`, minus twice the metric product of `pair`]; C = -g^2 for W+ W- W+ W- (pair: the two
+    # like-charged bosons) and g^2 times the W3 projections for W+ W- V V' (pair: W W and V V')
+    Vertex(("w+", "w-", "w+", "w-"), "VVVV", ("GWWWW",), "none", phase=1, pair=1),
+    Vertex(("w+", "w-", "a", "a"), "VVVV", ("GWWAA",), "none", phase=1, pair=0),
+    Vertex(("w+", "w-", "a", "z"), "VVVV", ("GWWAZ",), "none", phase=1, pair=0),
+    Vertex(("w+", "w-", "z", "z"), "VVVV", ("GWWZZ",), "none", phase=1, pair=0),
     Vertex(("w+", "w-", "h"), "VVS", ("GWWH",)),
     Vertex(("z", "z", "h"), "VVS", ("GZZH",)),
     Vertex(("w+", "w-", "h", "h"), "VVSS", ("GWWHH",)),
@@ -146,6 +157,7 @@ def couplings(par):
     c = {"ZERO": 0.0, "GS": gs, "GS2": gs * gs, "GW": g / math.sqrt(2),
          "GWWH": g * par["mW"], "GZZH": gz * par["mZ"], "GWWHH": g * g / 2, "GZZHH": gz * gz / 2,
          "GWWA": e, "GWWZ": g * cw,
+         "GWWWW": -g * g, "GWWAA": g * g * sw * sw, "GWWAZ": g * g * sw * cw, "GWWZZ": g * g * cw * cw,
          "GHHH": -3 * par["mH"] ** 2 / v,
          "MT": par["mt"], "WT": par["wt"], "MZ": par["mZ"], "WZ": par["wZ"], "MW": par["mW"], "WW": par["wW"],
          "MH": par["mH"], "WH": par["wH"], "0": 0.0}

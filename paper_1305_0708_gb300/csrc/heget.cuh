@@ -459,6 +459,13 @@ template <class R> ME_HD W4<R> w4_sub(const W4<R>& a, const W4<R>& b, R g) {
   return o;
 }
 
+// electroweak quartic current: g (a + b - 2 p), with a, b, p the currents of the three metric pairings
+template <class R> ME_HD W4<R> w4_quartic(const W4<R>& a, const W4<R>& b, const W4<R>& p, R g) {
+  W4<R> o;
+  for (int k = 0; k < 4; ++k) o.c[k] = g * (a.c[k] + b.c[k] - R(2) * p.c[k]);
+  return o;
+}
+
 template <class R> ME_HD W4<R> w4_scale(const W4<R>& a, cx<R> s) {
   W4<R> o;
   for (int k = 0; k < 4; ++k) o.c[k] = a.c[k] * s;

@@ -71,6 +71,10 @@ bool coupling_value(const std::string& n, const me_params& p, double& v) {
   if (n == "GWWH") { v = g * p.mW; return true; }
   if (n == "GWWA") { v = e; return true; }
   if (n == "GWWZ") { v = g * cw; return true; }
+  if (n == "GWWWW") { v = -g * g; return true; }
+  if (n == "GWWAA") { v = g * g * sw * sw; return true; }
+  if (n == "GWWAZ") { v = g * g * sw * cw; return true; }
+  if (n == "GWWZZ") { v = g * g * cw * cw; return true; }
   if (n == "GZZH") { v = gz * p.mZ; return true; }
   if (n == "GWWHH") { v = g * g / 2; return true; }
   if (n == "GZZHH") { v = gz * gz / 2; return true; }

@@ -58,6 +58,16 @@ VARIANTS = {
         process="u u~ > z h", kind="rambo", sqrt_s=500.0, masses=(0, 0, 91.1876, 125.0), n=1 << 20, seed=8,
         cuts=None, s_ident=1.0,
         describe="u u~ > Z H (s-channel Z, ZZH vertex), massive RAMBO at sqrt(s)=500 GeV, 2^20 points, seed 8"),
+    "udx_wph": dict(
+        process="u d~ > w+ h", kind="rambo", sqrt_s=500.0, masses=(0, 0, 80.4, 125.0), n=1 << 20, seed=9,
+        cuts=None, s_ident=1.0,
+        describe="u d~ > W+ H (s-channel W, WWH vertex), massive RAMBO at sqrt(s)=500 GeV, 2^20 points, seed 9"),
+    "uux_wpwma": dict(
+        process="u u~ > w+ w- a", kind="rambo", sqrt_s=500.0, masses=(0, 0, 80.4, 80.4, 0), n=1 << 20, seed=10,
+        cuts=dict(legs=(4,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="u u~ > W+ W- gamma (fifteen diagrams: the photon from the quark line and the W bosons, the "
+                 "WWAA and WWAZ quartic vertices), massive RAMBO at sqrt(s)=500 GeV, photon pT>20, |eta|<2.5, "
+                 "2^20 accepted points, seed 10"),
 }
 
 KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3}

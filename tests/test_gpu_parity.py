@@ -307,14 +307,15 @@ def test_identical_quarks_parity(B, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("key", ["uux_zz", "uux_zh"])
-def test_zz_zh_production_parity(B, key, prec):
-    """u u~ > Z Z (identical massive vectors, identical-particle factor 1/2) and u u~ > Z H (ZZH vertex,
-    external scalar): me_eval on the oracle's massive-RAMBO points and the Monte Carlo sums against the
+@pytest.mark.parametrize("key", ["uux_zz", "uux_zh", "udx_wph", "uux_wpwma"])
+def test_boson_production_parity(B, key, prec):
+    """u u~ > Z Z (identical massive vectors, identical-particle factor 1/2), u u~ > Z H (ZZH vertex,
+    external scalar), u d~ > W+ H (WWH vertex) and u u~ > W+ W- gamma (the electroweak quartic
+    vertices, VVV currents into massive W lines, photon pT and rapidity cuts): me_eval on the oracle's massive-RAMBO points and the Monte Carlo sums against the
     oracle."""
     from paper_1305_0708_gb300.workloads import VARIANTS
     w = VARIANTS[key]
-    fn = {"uux_zz": opr.uux_zz, "uux_zh": opr.uux_zh}[key]
+    fn = {"uux_zz": opr.uux_zz, "uux_zh": opr.uux_zh, "udx_wph": opr.udx_wph, "uux_wpwma": opr.uux_wpwma}[key]
     n = 1500
     P, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(n))
     ref = fn(P, PAR)
