@@ -19,6 +19,8 @@ Functions and their pins (tests/test_oracle_processes.py):
                    built from blocks pinned by the two cases above and q q~ > g g
   uux_gg          u u~ > g g     : textbook closed form, exact per point
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
+  gg_ttxh         g g > t t~ h   : Ward identity for each gluon (zero top width), the soft-Higgs
+                   limit against the eikonal factor times g g > t t~, Bose symmetry, boosts
   gg_ttx_dilep    g g > t t~ > b e+ ve b~ e- ve~ (doubly resonant diagrams):
                    Ward identity (zero widths), Bose symmetry, boosts
   uu_uu           u u > u u      : gluon, photon and Z exchange; textbook closed forms for
@@ -247,6 +249,59 @@ def gg_ttx(P, par=SMParams()):
         Gint = vector_prop(p[0] + p[1], X)
         AG = fermion_line(ubt, vt, -p[3], [(vector_insertion(Gint, gs, gs), -(p[0] + p[1]))], mt)
         tot = tot + colour.colour_sum([A01 / 1j, A10 / 1j, AG / 1j], [cAB, cBA, cG])
+    return tot / (4.0 * 64.0)
+
+
+# --------------------------------------------------------------------------
+# g g > t t~ H (the Higgs from every top line of g g > t t~: eight diagrams)
+# --------------------------------------------------------------------------
+def gg_ttxh(P, par=SMParams(), per_helicity=False, eps_override=None, widths=True):
+    """g(0) g(1) > t(2) t~(3) H(4).  The top line runs from the t~ spinor v(p3) to ubar(p2); the two
+    gluons and the Higgs are inserted in every order along it (six diagrams, colour t^a t^b or t^b t^a
+    by the order of the gluons), and the s-channel gluon of g g > t t~ is inserted with the Higgs before
+    or after it (two diagrams, colour f^{abc} t^c).  The Higgs vertex is the FFS one of Sect. 4.2 with
+    the Yukawa coupling of L = -(mt/v) t~ t H: a factor -i mt/v in i M.  Internal tops carry the width
+    wt unless widths=False.  eps_override = (leg, vector) replaces that gluon's polarisation vector."""
+    p = [P[:, k] for k in range(5)]
+    n = P.shape[0]
+    gs, mt = par.gs, par.mt
+    wt = par.wt if widths else 0.0
+    yt = -mt / par.vev
+    cAB = _colour_string([0, 1], 2)
+    cBA = _colour_string([1, 0], 2)
+    cG = _colour_string(["G"], 2, with_f=(0, 1))
+    Hins = (np.broadcast_to(1j * yt * np.eye(4, dtype=complex), (n, 4, 4)), p[4])
+    tot = 0.0
+    ph = {}
+    for h in itertools.product(HEL_V, HEL_V, HEL_F, HEL_F):
+        e0 = polarisation(p[0], h[0])
+        e1 = polarisation(p[1], h[1])
+        if eps_override is not None:
+            if eps_override[0] == 0:
+                e0 = eps_override[1]
+            else:
+                e1 = eps_override[1]
+        ubt = bar(u_spinor(p[2], h[2]))
+        vt = v_spinor(p[3], h[3])
+        G0 = (vector_insertion(e0, gs, gs), -p[0])
+        G1 = (vector_insertion(e1, gs, gs), -p[1])
+        AB, BA = 0.0, 0.0
+        for order in itertools.permutations(["G0", "G1", "H"]):
+            ins = [{"G0": G0, "G1": G1, "H": Hins}[x] for x in order]
+            a = fermion_line(ubt, vt, -p[3], ins, mt, wt)
+            if order.index("G0") < order.index("G1"):
+                AB = AB + a
+            else:
+                BA = BA + a
+        X = vvv_out(e0, p[0], e1, p[1], -(p[0] + p[1]), gs)
+        Gs = (vector_insertion(vector_prop(p[0] + p[1], X), gs, gs), -(p[0] + p[1]))
+        AG = fermion_line(ubt, vt, -p[3], [Gs, Hins], mt, wt) + fermion_line(ubt, vt, -p[3], [Hins, Gs], mt, wt)
+        val = colour.colour_sum([AB / 1j, BA / 1j, AG / 1j], [cAB, cBA, cG])
+        if per_helicity:
+            ph[h] = val
+        tot = tot + val
+    if per_helicity:
+        return ph
     return tot / (4.0 * 64.0)
 
 
@@ -763,6 +818,8 @@ PROCESSES = {
     "u u~ > z h": uux_zh,
     "u d~ > w+ h": udx_wph,
     "u u~ > w+ w- a": uux_wpwma,
+    "g g > t t~": gg_ttx,
+    "g g > t t~ h": gg_ttxh,
     "u u~ > w+ w-": uux_wpwm,
     "u d~ > w+ z": udx_wpz,
     "g g > g g": gluons,

@@ -561,3 +561,61 @@ def test_uux_wpwma_boosts():
     """|M|^2 of u u~ > W+ W- gamma is invariant under random Lorentz transformations."""
     P = _wwa_points(600.0, 12, seed=23)
     assert np.allclose(pr.uux_wpwma(random_lorentz(P, seed=24), PAR), pr.uux_wpwma(P, PAR), rtol=1e-10)
+
+
+def _ttxh_points(sqrt_s, n, seed, mh=PAR.mH):
+    u = np.random.default_rng(seed).uniform(0.01, 0.99, (n, 12))
+    pf, _ = ps.rambo_massive(sqrt_s, [PAR.mt, PAR.mt, mh], u)
+    P = np.zeros((n, 5, 4))
+    P[:, 0], P[:, 1] = ps.incoming(sqrt_s, n)
+    P[:, 2:] = pf
+    return P
+
+
+def test_gg_ttxh_ward_identity():
+    """Either gluon's polarisation replaced by its momentum: with zero top width the eight diagrams of
+    g g > t t~ H sum to zero for every helicity of the other gluon and the tops."""
+    P = _ttxh_points(1000.0, 20, seed=31)
+    ref = pr.gg_ttxh(P, PAR, per_helicity=True, widths=False)
+    for leg in (0, 1):
+        ward = pr.gg_ttxh(P, PAR, per_helicity=True, widths=False, eps_override=(leg, P[:, leg].astype(complex)))
+        for h, v in ward.items():
+            assert np.all(np.abs(v) <= 1e-20 * np.abs(ref[h]) + 1e-24 * max(abs(x).max() for x in ref.values()))
+
+
+def test_gg_ttxh_soft_higgs_limit():
+    """A soft massless scalar emitted from the external top lines: as its energy w goes to zero, |M|^2
+    of g g > t t~ H tends to (mt/v)^2 mt^2 [1/(p_t.k) + 1/(p_t~.k)]^2 |M|^2(g g > t t~), the deviation
+    falling in proportion to w (the Higgs mass enters the amplitude only through its momentum)."""
+    par = PAR
+    base = two_to_two(800.0, 6, par.mt, par.mt, seed=32)
+    m2 = pr.gg_ttx(base, par)
+    nhat = np.array([0.36, 0.48, -0.8])
+    devs = []
+    for w in (1e-1, 1e-2):
+        P = np.zeros((6, 5, 4))
+        P[:, :2] = base[:, :2]
+        k = np.concatenate([[w], w * nhat])
+        Qv = base[:, 0] + base[:, 1] - k
+        Q2 = mdot(Qv, Qv)
+        pst = np.sqrt(Q2 / 4 - par.mt ** 2)
+        d = base[:, 2, 1:] / np.linalg.norm(base[:, 2, 1:], axis=1)[:, None]
+        rest = np.zeros((6, 2, 4))
+        rest[:, 0, 0] = rest[:, 1, 0] = np.sqrt(Q2) / 2
+        rest[:, 0, 1:] = pst[:, None] * d
+        rest[:, 1, 1:] = -pst[:, None] * d
+        for i in range(6):
+            P[i, 2:4] = boost(rest[i], Qv[i, 1:] / Qv[i, 0])
+        P[:, 4] = k
+        m3 = pr.gg_ttxh(P, par, widths=False)
+        eik = (par.mt / par.vev) * par.mt * (1 / mdot(P[:, 2], k) + 1 / mdot(P[:, 3], k))
+        devs.append(np.max(np.abs(m3 / (eik ** 2 * m2) - 1)))
+    assert devs[1] < 2e-3 and devs[1] < devs[0] / 5
+
+
+def test_gg_ttxh_bose_and_boosts():
+    """Swapping the two gluons leaves |M|^2 unchanged; so do random Lorentz transformations."""
+    P = _ttxh_points(900.0, 10, seed=33)
+    ref = pr.gg_ttxh(P, PAR)
+    assert np.allclose(pr.gg_ttxh(P[:, [1, 0, 2, 3, 4]], PAR), ref, rtol=1e-11)
+    assert np.allclose(pr.gg_ttxh(random_lorentz(P, seed=34), PAR), ref, rtol=1e-10)
