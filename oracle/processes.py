@@ -229,9 +229,12 @@ def udx_epvegg(P, par=SMParams(), per_helicity=False, eps_override=None):
 # --------------------------------------------------------------------------
 # g g > t t~ (on-shell tops; textbook closed-form pin of the massive line)
 # --------------------------------------------------------------------------
-def gg_ttx(P, par=SMParams()):
+def gg_ttx(P, par=SMParams(), widths=True):
+    """g(0) g(1) > t(2) t~(3) with on-shell tops: t- and u-channel top exchange and the s-channel gluon.
+    The internal top carries the width wt (as every internal massive line does) unless widths=False."""
     p = [P[:, k] for k in range(4)]
     gs, mt = par.gs, par.mt
+    wt = par.wt if widths else 0.0
     cAB = _colour_string([0, 1], 2)  # arrow starts at the t~ spinor: gluon 0 nearest t~
     cBA = _colour_string([1, 0], 2)
     cG = _colour_string(["G"], 2, with_f=(0, 1))
@@ -243,11 +246,11 @@ def gg_ttx(P, par=SMParams()):
         vt = v_spinor(p[3], h[3])
         G0 = (vector_insertion(e0, gs, gs), -p[0])
         G1 = (vector_insertion(e1, gs, gs), -p[1])
-        A01 = fermion_line(ubt, vt, -p[3], [G0, G1], mt)
-        A10 = fermion_line(ubt, vt, -p[3], [G1, G0], mt)
+        A01 = fermion_line(ubt, vt, -p[3], [G0, G1], mt, wt)
+        A10 = fermion_line(ubt, vt, -p[3], [G1, G0], mt, wt)
         X = vvv_out(e0, p[0], e1, p[1], -(p[0] + p[1]), gs)
         Gint = vector_prop(p[0] + p[1], X)
-        AG = fermion_line(ubt, vt, -p[3], [(vector_insertion(Gint, gs, gs), -(p[0] + p[1]))], mt)
+        AG = fermion_line(ubt, vt, -p[3], [(vector_insertion(Gint, gs, gs), -(p[0] + p[1]))], mt, wt)
         tot = tot + colour.colour_sum([A01 / 1j, A10 / 1j, AG / 1j], [cAB, cBA, cG])
     return tot / (4.0 * 64.0)
 

@@ -100,7 +100,7 @@ def test_gg_ttx_closed_form():
     t2 = 2 * mdot(P[:, 1], P[:, 2]) / s
     rho = 4 * mt * mt / s
     want = PAR.gs ** 4 * (1 / (6 * t1 * t2) - 3 / 8) * (t1 ** 2 + t2 ** 2 + rho - rho ** 2 / (4 * t1 * t2))
-    assert np.allclose(pr.gg_ttx(P), want, rtol=1e-12)
+    assert np.allclose(pr.gg_ttx(P, widths=False), want, rtol=1e-12)
 
 
 def test_gg_gg_closed_form():
@@ -589,7 +589,7 @@ def test_gg_ttxh_soft_higgs_limit():
     falling in proportion to w (the Higgs mass enters the amplitude only through its momentum)."""
     par = PAR
     base = two_to_two(800.0, 6, par.mt, par.mt, seed=32)
-    m2 = pr.gg_ttx(base, par)
+    m2 = pr.gg_ttx(base, par, widths=False)
     nhat = np.array([0.36, 0.48, -0.8])
     devs = []
     for w in (1e-1, 1e-2):
