@@ -37,6 +37,8 @@ PROCESSES = [
     ("u u~ > z h", []),
     ("u d~ > w+ h", []),
     ("u u~ > w+ w- a", []),
+    ("g g > t t~", []),
+    ("g g > t t~ h", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -216,9 +216,13 @@ class _Emitter:
         h = var[0]
         name = _vname(nid, var)
         inc = "true" if leg.incoming else "false"
-        if part.is_fermion:
-            if not part.massless:
-                raise NotImplementedError("massive external fermions")
+        if part.is_fermion and not part.massless:
+            m = self.cpl(part.mass)
+            fn = "ext_column_massive" if _is_column(nd.ptype) else "ext_row_massive"
+            self.emit(f"  const me::W4<R> {name} = me::{fn}<R>(r{nid}, {h}, {inc}, (R){m});")
+            self.half[name] = frozenset("ul")
+            self.flops32 += 40
+        elif part.is_fermion:
             chi = _ext_chirality(leg, h)
             if _is_column(nd.ptype):
                 self.emit(f"  const me::W4<R> {name} = me::ext_column_massless<R>(r{nid}, {h}, {inc});")
@@ -297,6 +301,38 @@ class _Emitter:
                   f"{rk[2]}, {ck[2]}, {cargs}), k{nid}, inv{nid}, {str(massive).lower()}, {mc2});")
                 nterm = int(has_l and "l" in hr and "u" in hc) + int(has_r and "u" in hr and "l" in hc)
                 self.flops32 += 48 * nterm + (60 if massive else 8)
+        elif v.kind == "FFS":
+            gl, gr = v.couplings
+            has_l, has_r = gl != "ZERO", gr != "ZERO"
+            cargs = (f"(R){self.cpl(gl) if has_l else '0.0'}, (R){self.cpl(gr) if has_r else '0.0'}, "
+                     f"{str(has_l).lower()}, {str(has_r).lower()}")
+            if part.is_fermion:
+                fk = [k for k in kids if k[1] in (0, 1)][0]
+                sk = [k for k in kids if k[1] == 2][0]
+                m = "R(0)" if part.massless else f"(R){self.cpl(part.mass)}"
+                hin = self.half[fk[2]]
+                # S (gL P_L + gR P_R) keeps the halves: gL acts on the upper, gR on the lower one
+                hx = set()
+                if "u" in hin and has_l:
+                    hx.add("u")
+                if "l" in hin and has_r:
+                    hx.add("l")
+                hx = frozenset(hx)
+                if _is_column(nd.ptype):
+                    E(f"  const me::W4<R> {name} = me::prop_col<R, {_tag(hx)}>(me::ffs_col<R, {_tag(hin)}>("
+                      f"{fk[2]}, {sk[2]}, {cargs}), k{nid}, {m}, inv{nid});")
+                else:
+                    E(f"  const me::W4<R> {name} = me::prop_row<R, {_tag(hx)}>(me::ffs_row<R, {_tag(hin)}>("
+                      f"{fk[2]}, {sk[2]}, {cargs}), me::neg(k{nid}), {m}, inv{nid});")
+                self.half[name] = _flip(hx) if part.massless else frozenset("ul")
+                self.flops32 += (14 + 24 + (32 if not part.massless else 0)) * len(hx) + 2
+            else:
+                rk = [k for k in kids if k[1] == 0][0]
+                ck = [k for k in kids if k[1] == 1][0]
+                hr, hc = self.half[rk[2]], self.half[ck[2]]
+                E(f"  const me::cx<R> {name} = me::ffs_scalar<R, {_tag(hr)}, {_tag(hc)}>({rk[2]}, {ck[2]}, "
+                  f"{cargs}) * inv{nid};")
+                self.flops32 += 34
         elif v.kind == "VVV":
             g = self.cpl(v.couplings[0])
             # inputs in cyclic order after the output slot: the antisymmetric Lorentz structure
@@ -399,6 +435,14 @@ class _Emitter:
                     f"{str(has_l).lower()}, {str(has_r).lower()})")
             nterm = int(has_l and "u" in hc and "l" in hr) + int(has_r and "l" in hc and "u" in hr)
             self.flops32 += (28 if slot[2] in self.pv else 40) * nterm + 16 * nterm
+        elif v.kind == "FFS":
+            gl, gr = v.couplings
+            has_l, has_r = gl != "ZERO", gr != "ZERO"
+            hr, hc = self.half[slot[0]], self.half[slot[1]]
+            expr = (f"(me::ffs_scalar<R, {_tag(hr)}, {_tag(hc)}>({slot[0]}, {slot[1]}, "
+                    f"(R){self.cpl(gl) if has_l else '0.0'}, (R){self.cpl(gr) if has_r else '0.0'}, "
+                    f"{str(has_l).lower()}, {str(has_r).lower()}) * {slot[2]})")
+            self.flops32 += 34 + 6
         elif v.kind == "VVV":
             g = self.cpl(v.couplings[0])
             k0 = [c for c, s, _ in kids if s == 0][0]

@@ -83,7 +83,7 @@ WEAK_DOUBLETS = [("u", "d"), ("c", "s"), ("t", "b"), ("ve", "e-"), ("vm", "mu-")
 class Vertex:
     """A Feynman rule: incoming fields, Lorentz kind and coupling names.
 
-    kind: "FFV" (fields f~, f, V), "VVV", "VVVV", "VVS", "VVSS", "SSS".
+    kind: "FFV" (fields f~, f, V), "FFS" (f~, f, S), "VVV", "VVVV", "VVS", "VVSS", "SSS".
     couplings: names resolved by couplings() at me_create time; for FFV
     (gL, gR).  colour: "delta" (f~ f), "T" (f~ f g), "f" (ggg), "ff" (gggg).
     pair: for a colourless VVVV vertex, the slot pairing (0: (01)(23), 1: (02)(13), 2: (03)(12))
@@ -133,6 +133,8 @@ VERTICES = _ffv_vertices() + [
     Vertex(("w+", "w-", "a", "z"), "VVVV", ("GWWAZ",), "none", phase=1, pair=0),
     Vertex(("w+", "w-", "z", "z"), "VVVV", ("GWWZZ",), "none", phase=1, pair=0),
     Vertex(("w+", "w-", "h"), "VVS", ("GWWH",)),
+    # top Yukawa (Sect. 4.2 FFS): L = -(mt/v) t~ t H, i (gL P_L + gR P_R) with gL = gR = -mt/v
+    Vertex(("t~", "t", "h"), "FFS", ("GHTT", "GHTT"), "delta"),
     Vertex(("z", "z", "h"), "VVS", ("GZZH",)),
     Vertex(("w+", "w-", "h", "h"), "VVSS", ("GWWHH",)),
     Vertex(("z", "z", "h", "h"), "VVSS", ("GZZHH",)),
@@ -158,7 +160,7 @@ def couplings(par):
          "GWWH": g * par["mW"], "GZZH": gz * par["mZ"], "GWWHH": g * g / 2, "GZZHH": gz * gz / 2,
          "GWWA": e, "GWWZ": g * cw,
          "GWWWW": -g * g, "GWWAA": g * g * sw * sw, "GWWAZ": g * g * sw * cw, "GWWZZ": g * g * cw * cw,
-         "GHHH": -3 * par["mH"] ** 2 / v,
+         "GHHH": -3 * par["mH"] ** 2 / v, "GHTT": -par["mt"] / v,
          "MT": par["mt"], "WT": par["wt"], "MZ": par["mZ"], "WZ": par["wZ"], "MW": par["mW"], "WW": par["wW"],
          "MH": par["mH"], "WH": par["wH"], "0": 0.0}
     for f, q in CHARGE.items():

@@ -30,7 +30,7 @@ from .model import PARTICLES
 
 # own phase (power of i) of a current: vertex factor + propagator
 _PROP_PHASE = {"F": 1, "V": 3, "S": 1}
-_VERTEX_PHASE = {"FFV": 1, "VVV": 0, "VVVV": 3, "VVS": 1, "VVSS": 1, "SSS": 1}
+_VERTEX_PHASE = {"FFV": 1, "FFS": 1, "VVV": 0, "VVVV": 3, "VVS": 1, "VVSS": 1, "SSS": 1}
 
 
 def _kind_of(ptype):
@@ -140,6 +140,9 @@ class _Analysis:
             ch = [self.node_state(c, hmap) for c in nd.children]
             if any(c is None for c in ch):
                 res = None
+            elif nd.vertex.kind == "FFS":
+                # a scalar vertex flips chirality; no pruning through it (both chiralities kept)
+                res = "M" if PARTICLES[nd.ptype].is_fermion else True
             elif nd.vertex.kind == "FFV":
                 allowed = _ffv_allowed(nd.vertex, self.coup_zero)
                 ferm = [c for c, s in zip(ch, nd.slots) if s in (0, 1)]
@@ -260,7 +263,7 @@ def _fermion_sign(nodes, a):
         nd = nodes[nid]
         if nd.external:
             return
-        if nd.vertex.kind == "FFV" and not PARTICLES[nd.ptype].is_fermion:
+        if nd.vertex.kind in ("FFV", "FFS") and not PARTICLES[nd.ptype].is_fermion:
             row = [c for c, s in zip(nd.children, nd.slots) if s == 0][0]
             colm = [c for c, s in zip(nd.children, nd.slots) if s == 1][0]
             pairs.append((_fermion_leaf(nodes, row), _fermion_leaf(nodes, colm)))
@@ -269,7 +272,7 @@ def _fermion_sign(nodes, a):
 
     for c in a.children:
         visit(c)
-    if a.vertex.kind == "FFV":
+    if a.vertex.kind in ("FFV", "FFS"):
         row = [c for c, s in zip(a.children, a.slots) if s == 0][0]
         colm = [c for c, s in zip(a.children, a.slots) if s == 1][0]
         pairs.append((_fermion_leaf(nodes, row), _fermion_leaf(nodes, colm)))

@@ -114,6 +114,60 @@ template <class R> ME_HD W4<R> ext_row_massless(P4<R> p, int hel, bool incoming)
   return w;
 }
 
+// Two-component helicity eigenstates xi_+-(p) of p^.sigma, with the phases of the massless forms
+// above: xi_+ = (cos th/2, e^{i ph} sin th/2), xi_- = (-e^{-i ph} sin th/2, cos th/2); along -z
+// xi_+ = (0, 1), xi_- = (-1, 0); at rest the spin states along +z.
+template <class R> ME_HD void helicity_xi(P4<R> p, R r, cx<R> xp[2], cx<R> xm[2]) {
+  const R rp = p.z >= R(0) ? r + p.z : (p.x * p.x + p.y * p.y) / (r - p.z);
+  if (r > R(0) && rp > R(0)) {
+    const R n = R(1) / sqrt(R(2) * r * rp);
+    xp[0] = mk(rp * n, R(0));
+    xp[1] = mk(p.x * n, p.y * n);
+    xm[0] = mk(-p.x * n, p.y * n);
+    xm[1] = mk(rp * n, R(0));
+  } else if (r > R(0)) {
+    xp[0] = mk(R(0), R(0)); xp[1] = mk(R(1), R(0));
+    xm[0] = mk(R(-1), R(0)); xm[1] = mk(R(0), R(0));
+  } else {
+    xp[0] = mk(R(1), R(0)); xp[1] = mk(R(0), R(0));
+    xm[0] = mk(R(0), R(0)); xm[1] = mk(R(1), R(0));
+  }
+}
+
+// Column spinor of a massive fermion line entering its vertex, helicity basis:
+//   incoming fermion     u(p, l) = (sqrt(E - l|p|) xi_l, sqrt(E + l|p|) xi_l)
+//   outgoing antifermion v(p, l) = (-l sqrt(E + l|p|) xi_-l, l sqrt(E - l|p|) xi_-l)
+// E - |p| is formed as m^2 / (E + |p|) (no cancellation at high energy).
+template <class R> ME_HD W4<R> ext_column_massive(P4<R> p, int hel, bool incoming, R mass) {
+  const R r = sqrt(p.x * p.x + p.y * p.y + p.z * p.z);
+  const R wp = sqrt(p.e + r), wm = mass / wp;  // sqrt(E + |p|), sqrt(E - |p|)
+  cx<R> xp[2], xm[2];
+  helicity_xi(p, r, xp, xm);
+  const R l = (R)hel;
+  W4<R> w;
+  if (incoming) {
+    const cx<R>* x = hel > 0 ? xp : xm;
+    const R a = hel > 0 ? wm : wp, b = hel > 0 ? wp : wm;
+    w.c[0] = a * x[0]; w.c[1] = a * x[1]; w.c[2] = b * x[0]; w.c[3] = b * x[1];
+  } else {
+    const cx<R>* x = hel > 0 ? xm : xp;
+    const R a = hel > 0 ? wp : wm, b = hel > 0 ? wm : wp;
+    w.c[0] = (-l * a) * x[0]; w.c[1] = (-l * a) * x[1]; w.c[2] = (l * b) * x[0]; w.c[3] = (l * b) * x[1];
+  }
+  return w;
+}
+
+// Row spinor of a massive fermion line leaving its vertex (ubar outgoing, vbar incoming)
+template <class R> ME_HD W4<R> ext_row_massive(P4<R> p, int hel, bool incoming, R mass) {
+  W4<R> col = ext_column_massive(p, hel, !incoming, mass);
+  W4<R> w;
+  w.c[0] = conj(col.c[2]);
+  w.c[1] = conj(col.c[3]);
+  w.c[2] = conj(col.c[0]);
+  w.c[3] = conj(col.c[1]);
+  return w;
+}
+
 // Polarisation vector eps(k, hel) (incoming) or eps^*(k, hel) (outgoing).
 // eps(+-1) = (0, -+ e_theta - i e_phi)/sqrt2, eps(0) = (|k|, E k^)/m.
 template <class R> ME_HD W4<R> ext_vector(P4<R> k, int hel, bool incoming, R mass) {
@@ -288,6 +342,35 @@ ME_HD cx<R> ffv_amp(const W4<R>& row, const W4<R>& col, const VV& V, R gl, R gr,
   cx<R> a = mk(R(0), R(0));
   if (up) a = a + row.c[0] * g.c[0] + row.c[1] * g.c[1];
   if (lo) a = a + row.c[2] * g.c[2] + row.c[3] * g.c[3];
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// FFS: Gamma = S (gL P_L + gR P_R)   (P_L: the upper half)
+// ---------------------------------------------------------------------------
+template <class R, int H = kAll>
+ME_HD W4<R> ffs_col(const W4<R>& psi, cx<R> S, R gl, R gr, bool has_l, bool has_r) {
+  W4<R> o;
+  const cx<R> z = mk(R(0), R(0));
+  if (H != kLo && has_l) { const cx<R> f = gl * S; o.c[0] = f * psi.c[0]; o.c[1] = f * psi.c[1]; }
+  else { o.c[0] = z; o.c[1] = z; }
+  if (H != kUp && has_r) { const cx<R> f = gr * S; o.c[2] = f * psi.c[2]; o.c[3] = f * psi.c[3]; }
+  else { o.c[2] = z; o.c[3] = z; }
+  return o;
+}
+
+// row (gL P_L + gR P_R) S: (gL S row_up, gR S row_lo)
+template <class R, int H = kAll>
+ME_HD W4<R> ffs_row(const W4<R>& row, cx<R> S, R gl, R gr, bool has_l, bool has_r) {
+  return ffs_col<R, H>(row, S, gl, gr, has_l, has_r);
+}
+
+// row (gL P_L + gR P_R) col
+template <class R, int HR = kAll, int HC = kAll>
+ME_HD cx<R> ffs_scalar(const W4<R>& row, const W4<R>& col, R gl, R gr, bool has_l, bool has_r) {
+  cx<R> a = mk(R(0), R(0));
+  if (has_l && HR != kLo && HC != kLo) a = a + gl * (row.c[0] * col.c[0] + row.c[1] * col.c[1]);
+  if (has_r && HR != kUp && HC != kUp) a = a + gr * (row.c[2] * col.c[2] + row.c[3] * col.c[3]);
   return a;
 }
 

@@ -68,6 +68,16 @@ VARIANTS = {
         describe="u u~ > W+ W- gamma (fifteen diagrams: the photon from the quark line and the W bosons, the "
                  "WWAA and WWAZ quartic vertices), massive RAMBO at sqrt(s)=500 GeV, photon pT>20, |eta|<2.5, "
                  "2^20 accepted points, seed 10"),
+    "gg_ttx": dict(
+        process="g g > t t~", kind="rambo", sqrt_s=800.0, masses=(0, 0, 175.0, 175.0), n=1 << 20, seed=11,
+        cuts=None, s_ident=1.0,
+        describe="g g > t t~ with on-shell tops (massive external spinors; t- and u-channel top exchange, "
+                 "s-channel gluon), massive RAMBO at sqrt(s)=800 GeV, 2^20 points, seed 11"),
+    "gg_ttxh": dict(
+        process="g g > t t~ h", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 175.0, 175.0, 125.0), n=1 << 20,
+        seed=12, cuts=None, s_ident=1.0,
+        describe="g g > t t~ H (eight diagrams: the Higgs from every top line through the FFS Yukawa vertex), "
+                 "massive RAMBO at sqrt(s)=1 TeV, 2^20 points, seed 12"),
 }
 
 KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3}
