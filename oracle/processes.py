@@ -19,6 +19,7 @@ Functions and their pins (tests/test_oracle_processes.py):
                    built from blocks pinned by the two cases above and q q~ > g g
   uux_gg          u u~ > g g     : textbook closed form, exact per point
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
+  hh_hh           h h > h h      : closed form from the Higgs potential, exact per point
   gg_ttxh         g g > t t~ h   : Ward identity for each gluon (zero top width), the soft-Higgs
                    limit against the eikonal factor times g g > t t~, Bose symmetry, boosts
   gg_ttx_dilep    g g > t t~ > b e+ ve b~ e- ve~ (doubly resonant diagrams):
@@ -622,6 +623,23 @@ def udx_wpz(P, par=SMParams()):
 
 
 # --------------------------------------------------------------------------
+# h h > h h  (the SSSS contact vertex and the s-, t- and u-channel Higgs exchange)
+# --------------------------------------------------------------------------
+def hh_hh(P, par=SMParams()):
+    """h(0) h(1) > h(2) h(3) from the Feynman rules of Sect. 4.2 (SSS and SSSS): the contact vertex
+    -i 3 mH^2/v^2 and the three exchange diagrams, each (-i 3 mH^2/v)^2 times the scalar propagator
+    i/(q^2 - mH^2 + i mH wH).  No spins or colours to sum."""
+    p = [P[:, k] for k in range(4)]
+    v = par.vev
+    g3 = -3.0 * par.mH ** 2 / v
+    g4 = -3.0 * par.mH ** 2 / v ** 2
+    iM = 1j * g4 + 0.0 * p[0][:, 0]
+    for q in (p[0] + p[1], p[0] - p[2], p[0] - p[3]):
+        iM = iM + (1j * g3) * scalar_prop(q, par.mH, par.wH) * (1j * g3)
+    return np.abs(iM / 1j) ** 2
+
+
+# --------------------------------------------------------------------------
 # u u~ > W+ W- gamma  (quark-line emissions, W-line emissions, the WWAA and WWAZ quartic vertices)
 # --------------------------------------------------------------------------
 def vvvv(gg, V1, V2, V3, V4):
@@ -823,6 +841,7 @@ PROCESSES = {
     "u u~ > w+ w- a": uux_wpwma,
     "g g > t t~": gg_ttx,
     "g g > t t~ h": gg_ttxh,
+    "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,
     "u d~ > w+ z": udx_wpz,
     "g g > g g": gluons,

@@ -619,3 +619,30 @@ def test_gg_ttxh_bose_and_boosts():
     ref = pr.gg_ttxh(P, PAR)
     assert np.allclose(pr.gg_ttxh(P[:, [1, 0, 2, 3, 4]], PAR), ref, rtol=1e-11)
     assert np.allclose(pr.gg_ttxh(random_lorentz(P, seed=34), PAR), ref, rtol=1e-10)
+
+
+def test_hh_hh_closed_form():
+    """h h > h h from the potential lambda (H^dag H - v^2/2)^2 with mH^2 = 2 lambda v^2: the h^3 and
+    h^4 terms lambda v h^3 + lambda/4 h^4 give M = -6 lambda - (6 lambda v)^2 sum_{x=s,t,u} 1/(x - mH^2)
+    at zero Higgs width.  Per point at 1e-12, and the high-energy limit (the contact term alone)."""
+    par = PAR.with_(wH=0.0)
+    P = np.zeros((40, 4, 4))
+    rs = np.linspace(300.0, 3000.0, 40)
+    rng = np.random.default_rng(41)
+    for i, w in enumerate(rs):
+        P[i] = two_to_two(w, 1, par.mH, par.mH, seed=int(rng.integers(1 << 30)))[0]
+        pin = math.sqrt(w * w / 4 - par.mH ** 2)
+        P[i, 0] = [w / 2, 0, 0, pin]
+        P[i, 1] = [w / 2, 0, 0, -pin]
+    lam = par.mH ** 2 / (2 * par.vev ** 2)
+    s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
+    t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
+    u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    m2 = par.mH ** 2
+    M = -6 * lam - (6 * lam * par.vev) ** 2 * (1 / (s - m2) + 1 / (t - m2) + 1 / (u - m2))
+    assert np.allclose(pr.hh_hh(P, par), M ** 2, rtol=1e-12, atol=0)
+    Q = two_to_two(1e6, 4, par.mH, par.mH, seed=42)
+    pin = math.sqrt(1e12 / 4 - par.mH ** 2)
+    Q[:, 0] = [5e5, 0, 0, pin]
+    Q[:, 1] = [5e5, 0, 0, -pin]
+    assert np.allclose(pr.hh_hh(Q, par), 36 * lam ** 2, rtol=1e-3)
