@@ -39,6 +39,7 @@ PROCESSES = [
     ("u u~ > w+ w- a", []),
     ("g g > t t~", []),
     ("g g > t t~ h", []),
+    ("h h > h h", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -395,11 +395,11 @@ class _Emitter:
                 extra = f" * {sprod}" if sprod else ""
                 E(f"  const me::cx<R> {name} = ((R){g} * {d}){extra} * inv{nid};")
                 self.flops32 += 30 + 12 + 6 * len(ss)
-        elif v.kind == "SSS":
+        elif v.kind in ("SSS", "SSSS"):
             g = self.cpl(v.couplings[0])
-            a, b = kids
-            E(f"  const me::cx<R> {name} = ((R){g} * ({a[2]} * {b[2]})) * inv{nid};")
-            self.flops32 += 14
+            prod = " * ".join(k[2] for k in kids)
+            E(f"  const me::cx<R> {name} = ((R){g} * ({prod})) * inv{nid};")
+            self.flops32 += 8 + 6 * len(kids)
         else:
             raise NotImplementedError(v.kind)
 
@@ -468,10 +468,11 @@ class _Emitter:
             ss = [nm for _, s, nm in kids if PARTICLES[v.fields[s]].is_scalar]
             expr = f"((R){g} * me::mdot<R>({vs[0]}, {vs[1]}))" + "".join(f" * {s}" for s in ss)
             self.flops32 += 32 + 6 * len(ss)
-        elif v.kind == "SSS":
+        elif v.kind in ("SSS", "SSSS"):
             g = self.cpl(v.couplings[0])
-            expr = f"((R){g} * ({slot[0]} * {slot[1]} * {slot[2]}))"
-            self.flops32 += 14
+            prod = " * ".join(slot[s] for s in range(len(v.fields)))
+            expr = f"((R){g} * ({prod}))"
+            self.flops32 += 2 + 6 * len(v.fields)
         else:
             raise NotImplementedError(v.kind)
         E(f"  {{ const me::cx<R> a = {expr};")

@@ -1,8 +1,7 @@
 """Standard Model particle and vertex table for the process compiler.
 
 The vertex set is the one the paper's HEGET functions cover (Sect. 4.2,
-Table 2): FFV, VVV, VVVV, VVS, VVSS, SSS (FFS is not needed for massless
-light quarks and is left out).  Conventions: every vertex lists the fields
+Table 2): FFV, FFS, VVV, VVVV, VVS, VVSS, SSS, SSSS.  Conventions: every vertex lists the fields
 it annihilates, i.e. all particles incoming.  Couplings follow the textbook
 Lagrangian with D_mu = d_mu - i g_s t^a G^a_mu - i g W^a T^a - i g' Y B_mu
 (the paper's Eqs. 22-40 up to the sign convention of g_s, which drops out
@@ -17,7 +16,8 @@ of |M|^2):
   g g g g   -i g_s^2 f^{XYe} f^{ZWe} (g_XZ g_YW - g_XW g_YZ) for the three pairings
   W+ W- h   i g mW g^{mn}        Z Z h  i gZ mZ g^{mn}
   W+ W- h h i g^2/2 g^{mn}       Z Z h h i gZ^2/2 g^{mn}
-  h h h     -i 3 mH^2 / v
+  h h h     -i 3 mH^2 / v          h h h h  -i 3 mH^2 / v^2
+  t~ t h    -i mt / v
 """
 import math
 from dataclasses import dataclass, field
@@ -83,7 +83,7 @@ WEAK_DOUBLETS = [("u", "d"), ("c", "s"), ("t", "b"), ("ve", "e-"), ("vm", "mu-")
 class Vertex:
     """A Feynman rule: incoming fields, Lorentz kind and coupling names.
 
-    kind: "FFV" (fields f~, f, V), "FFS" (f~, f, S), "VVV", "VVVV", "VVS", "VVSS", "SSS".
+    kind: "FFV" (fields f~, f, V), "FFS" (f~, f, S), "VVV", "VVVV", "VVS", "VVSS", "SSS", "SSSS".
     couplings: names resolved by couplings() at me_create time; for FFV
     (gL, gR).  colour: "delta" (f~ f), "T" (f~ f g), "f" (ggg), "ff" (gggg).
     pair: for a colourless VVVV vertex, the slot pairing (0: (01)(23), 1: (02)(13), 2: (03)(12))
@@ -139,6 +139,7 @@ VERTICES = _ffv_vertices() + [
     Vertex(("w+", "w-", "h", "h"), "VVSS", ("GWWHH",)),
     Vertex(("z", "z", "h", "h"), "VVSS", ("GZZHH",)),
     Vertex(("h", "h", "h"), "SSS", ("GHHH",)),
+    Vertex(("h", "h", "h", "h"), "SSSS", ("GHHHH",)),
 ]
 
 
@@ -161,6 +162,7 @@ def couplings(par):
          "GWWA": e, "GWWZ": g * cw,
          "GWWWW": -g * g, "GWWAA": g * g * sw * sw, "GWWAZ": g * g * sw * cw, "GWWZZ": g * g * cw * cw,
          "GHHH": -3 * par["mH"] ** 2 / v, "GHTT": -par["mt"] / v,
+         "GHHHH": -3 * par["mH"] ** 2 / v ** 2,
          "MT": par["mt"], "WT": par["wt"], "MZ": par["mZ"], "WZ": par["wZ"], "MW": par["mW"], "WW": par["wW"],
          "MH": par["mH"], "WH": par["wH"], "0": 0.0}
     for f, q in CHARGE.items():

@@ -30,7 +30,7 @@ from .model import PARTICLES
 
 # own phase (power of i) of a current: vertex factor + propagator
 _PROP_PHASE = {"F": 1, "V": 3, "S": 1}
-_VERTEX_PHASE = {"FFV": 1, "FFS": 1, "VVV": 0, "VVVV": 3, "VVS": 1, "VVSS": 1, "SSS": 1}
+_VERTEX_PHASE = {"FFV": 1, "FFS": 1, "VVV": 0, "VVVV": 3, "VVS": 1, "VVSS": 1, "SSS": 1, "SSSS": 1}
 
 
 def _kind_of(ptype):

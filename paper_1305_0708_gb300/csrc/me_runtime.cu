@@ -80,6 +80,7 @@ bool coupling_value(const std::string& n, const me_params& p, double& v) {
   if (n == "GZZHH") { v = gz * gz / 2; return true; }
   if (n == "GHHH") { v = -3 * p.mH * p.mH / vev; return true; }
   if (n == "GHTT") { v = -p.mt / vev; return true; }
+  if (n == "GHHHH") { v = -3 * p.mH * p.mH / (vev * vev); return true; }
   if (n == "MT") { v = p.mt; return true; }
   if (n == "WT") { v = p.wt; return true; }
   if (n == "MZ") { v = p.mZ; return true; }

@@ -347,3 +347,34 @@ def test_massive_final_state_parity(B, key, prec):
     assert acc.n_acc == nacc == n and acc.n_try == ntry
     tol = 1e-11 if prec == 0 else 1e-5
     assert acc.sum_w == pytest.approx(sw, rel=tol) and acc.sum_w2 == pytest.approx(sw2, rel=2 * tol)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_scalar_quartic_parity(B, prec):
+    """h h > h h (the SSSS contact vertex beside s-, t- and u-channel Higgs exchange through SSS):
+    me_eval on massive incoming and outgoing Higgs bosons from threshold to 3 TeV, against the
+    oracle (no generator takes massive beams, so there is no Monte Carlo leg)."""
+    import math
+    n = 700
+    rng = np.random.default_rng(51)
+    rs = rng.uniform(255.0, 3000.0, n)
+    c = rng.uniform(-1.0, 1.0, n)
+    phi = rng.uniform(0.0, 2 * np.pi, n)
+    m = PAR.mH
+    P = np.zeros((n, 4, 4))
+    pin = np.sqrt(rs * rs / 4 - m * m)
+    P[:, 0] = np.stack([rs / 2, 0 * rs, 0 * rs, pin], axis=1)
+    P[:, 1] = np.stack([rs / 2, 0 * rs, 0 * rs, -pin], axis=1)
+    nv = np.stack([np.sqrt(1 - c * c) * np.cos(phi), np.sqrt(1 - c * c) * np.sin(phi), c], axis=1)
+    P[:, 2, 0] = P[:, 3, 0] = rs / 2
+    P[:, 2, 1:] = pin[:, None] * nv
+    P[:, 3, 1:] = -pin[:, None] * nv
+    ref = opr.hh_hh(P, PAR)
+    got = eval_gpu(B, "h h > h h", P, prec)
+    if prec == 0:
+        assert np.all(np.abs(got - ref) <= fp64_tolerance(opr.hh_hh, P, ref, masses=[m] * 4))
+        assert np.median(np.abs(got / ref - 1)) <= 1e-12
+    else:
+        rel = np.abs(got / ref - 1)
+        assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
+    assert math.isfinite(float(got.sum()))
