@@ -29,6 +29,7 @@ Functions and their pins (tests/test_oracle_processes.py):
   uux_zz          u u~ > z z     : closed form, exact per point; Bose symmetry
   uux_zh          u u~ > z h     : closed form from the trace, exact per point
   udx_wph         u d~ > w+ h    : closed form from the trace, exact per point
+  udx_wpg, uux_zg q q~ > V g     : textbook closed form (t^2 + u^2 + 2 s mV^2)/(t u), exact per point
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
@@ -531,6 +532,39 @@ def uux_zh(P, par=SMParams()):
 
 
 # --------------------------------------------------------------------------
+# q q~' > V g  (vector boson plus one jet: the gluon from either quark)
+# --------------------------------------------------------------------------
+def _qqx_vg(P, par, gl, gr, mV):
+    """q(p0) q~'(p1) > V(p2) g(p3) with V coupling i gamma^mu (gl P_L + gr P_R): the two orderings of
+    the gluon and V insertions along the quark line, colour t^a."""
+    p = [P[:, k] for k in range(4)]
+    gs = par.gs
+    cT = _colour_string([0], 1)
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ev = polarisation(p[2], h[2], mass=mV).conj()
+        eg = polarisation(p[3], h[3]).conj()
+        G = (vector_insertion(eg, gs, gs), p[3])
+        V = (vector_insertion(ev, gl, gr), p[2])
+        A = fermion_line(vb, u, p[0], [G, V]) + fermion_line(vb, u, p[0], [V, G])
+        tot = tot + colour.colour_sum([A / 1j], [cT])
+    return tot / 36.0
+
+
+def udx_wpg(P, par=SMParams()):
+    """u d~ > W+ g."""
+    return _qqx_vg(P, par, par.g / np.sqrt(2.0), 0.0, par.mW)
+
+
+def uux_zg(P, par=SMParams()):
+    """u u~ > Z g."""
+    gl, gr = _z_couplings("u", par)
+    return _qqx_vg(P, par, gl, gr, par.mZ)
+
+
+# --------------------------------------------------------------------------
 # u d~ > W+ H  (s-channel W through the WWH vertex)
 # --------------------------------------------------------------------------
 def udx_wph(P, par=SMParams()):
@@ -838,6 +872,8 @@ PROCESSES = {
     "u u~ > z z": uux_zz,
     "u u~ > z h": uux_zh,
     "u d~ > w+ h": udx_wph,
+    "u d~ > w+ g": udx_wpg,
+    "u u~ > z g": uux_zg,
     "u u~ > w+ w- a": uux_wpwma,
     "g g > t t~": gg_ttx,
     "g g > t t~ h": gg_ttxh,

@@ -646,3 +646,22 @@ def test_hh_hh_closed_form():
     Q[:, 0] = [5e5, 0, 0, pin]
     Q[:, 1] = [5e5, 0, 0, -pin]
     assert np.allclose(pr.hh_hh(Q, par), 36 * lam ** 2, rtol=1e-3)
+
+
+@pytest.mark.parametrize("which", ["w", "z"])
+def test_qqx_vg_closed_form(which):
+    """q q~' > V g with an on-shell massive V: the spin- and colour-averaged |M|^2 is
+    (4/9) (gL^2 + gR^2) gs^2 (t^2 + u^2 + 2 s mV^2) / (t u), the massive-V form of the textbook
+    q q~ > gamma g result (8/9) e^2 eq^2 gs^2 (t/u + u/t); t = (p_q - p_V)^2, u = (p_q - p_g)^2."""
+    if which == "w":
+        mV, gl, gr, fn = PAR.mW, PAR.g / math.sqrt(2.0), 0.0, pr.udx_wpg
+    else:
+        mV, fn = PAR.mZ, pr.uux_zg
+        gl = PAR.gz * (T3["u"] - CHARGE["u"] * PAR.sw2)
+        gr = PAR.gz * (-CHARGE["u"] * PAR.sw2)
+    P = two_to_two(400.0, 64, mV, 0.0, seed=61)
+    s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
+    t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
+    u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    want = (4.0 / 9.0) * (gl ** 2 + gr ** 2) * PAR.gs ** 2 * (t * t + u * u + 2 * s * mV ** 2) / (t * u)
+    assert np.allclose(fn(P, PAR), want, rtol=1e-12, atol=0)
