@@ -40,6 +40,8 @@ PROCESSES = [
     ("g g > t t~", []),
     ("g g > t t~ h", []),
     ("h h > h h", []),
+    ("u d~ > w+ g", []),
+    ("u u~ > z g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -68,6 +68,16 @@ VARIANTS = {
         describe="u u~ > W+ W- gamma (fifteen diagrams: the photon from the quark line and the W bosons, the "
                  "WWAA and WWAZ quartic vertices), massive RAMBO at sqrt(s)=500 GeV, photon pT>20, |eta|<2.5, "
                  "2^20 accepted points, seed 10"),
+    "udx_wpg": dict(
+        process="u d~ > w+ g", kind="rambo", sqrt_s=500.0, masses=(0, 0, 80.4, 0), n=1 << 20, seed=13,
+        cuts=dict(legs=(3,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="u d~ > W+ g (W plus one jet), massive RAMBO at sqrt(s)=500 GeV, gluon pT>20, |eta|<2.5, "
+                 "2^20 accepted points, seed 13"),
+    "uux_zg": dict(
+        process="u u~ > z g", kind="rambo", sqrt_s=500.0, masses=(0, 0, 91.1876, 0), n=1 << 20, seed=14,
+        cuts=dict(legs=(3,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="u u~ > Z g (Z plus one jet), massive RAMBO at sqrt(s)=500 GeV, gluon pT>20, |eta|<2.5, "
+                 "2^20 accepted points, seed 14"),
     "gg_ttx": dict(
         process="g g > t t~", kind="rambo", sqrt_s=800.0, masses=(0, 0, 175.0, 175.0), n=1 << 20, seed=11,
         cuts=None, s_ident=1.0,

@@ -76,15 +76,15 @@ def fp64_tolerance(fn, P, ref, masses=None):
     for _ in range(4):
         Q = P * (1 + 2.0 ** -52 * rng.standard_normal(P.shape))
         spread = np.maximum(spread, np.abs(fn(Q, PAR) - ref))
-    if masses is not None and any(m > 0 for m in masses):
+    if masses is not None:
         # RAMBO's boosts leave a few points off shell by up to ~1e-11 relative (the massless momenta
-        # lose digits when the boost nearly cancels a particle's energy).  A massive spinor or
-        # polarisation then depends on whether it reads the mass from the momentum or from the
-        # parameter card; the spread between the two readings bounds the agreement.
+        # lose digits when the boost nearly cancels a particle's energy).  A wavefunction then depends
+        # on whether it reads the mass (or masslessness) from the energy or from the parameter card, and
+        # on which components it reads; the spread between the momenta as given and the same momenta
+        # with on-shell energies bounds the agreement.
         Q = P.copy()
         for k, m in enumerate(masses):
-            if m > 0:
-                Q[:, k, 0] = np.sqrt(m * m + np.sum(P[:, k, 1:] ** 2, axis=1))
+            Q[:, k, 0] = np.sqrt(m * m + np.sum(P[:, k, 1:] ** 2, axis=1))
         spread = np.maximum(spread, np.abs(fn(Q, PAR) - ref))
     return 1e-12 * np.abs(ref) + 32 * spread
 
@@ -317,17 +317,19 @@ def test_identical_quarks_parity(B, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("key", ["uux_zz", "uux_zh", "udx_wph", "uux_wpwma", "gg_ttx", "gg_ttxh"])
+@pytest.mark.parametrize("key", ["uux_zz", "uux_zh", "udx_wph", "uux_wpwma", "gg_ttx", "gg_ttxh", "udx_wpg",
+                                 "uux_zg"])
 def test_massive_final_state_parity(B, key, prec):
     """u u~ > Z Z (identical massive vectors, identical-particle factor 1/2), u u~ > Z H (ZZH vertex,
     external scalar), u d~ > W+ H (WWH vertex), u u~ > W+ W- gamma (the electroweak quartic
     vertices, VVV currents into massive W lines, photon pT and rapidity cuts), g g > t t~ (massive
-    external spinors) and g g > t t~ H (the FFS Yukawa vertex): me_eval on the oracle's massive-RAMBO
-    points and the Monte Carlo sums against the oracle."""
+    external spinors), g g > t t~ H (the FFS Yukawa vertex), u d~ > W+ g and u u~ > Z g (vector boson
+    plus one jet, gluon cuts): me_eval on the oracle's massive-RAMBO points and the Monte Carlo sums
+    against the oracle."""
     from paper_1305_0708_gb300.workloads import VARIANTS
     w = VARIANTS[key]
     fn = {"uux_zz": opr.uux_zz, "uux_zh": opr.uux_zh, "udx_wph": opr.udx_wph, "uux_wpwma": opr.uux_wpwma,
-          "gg_ttx": opr.gg_ttx, "gg_ttxh": opr.gg_ttxh}[key]
+          "gg_ttx": opr.gg_ttx, "gg_ttxh": opr.gg_ttxh, "udx_wpg": opr.udx_wpg, "uux_zg": opr.uux_zg}[key]
     n = 1500
     P, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(n))
     ref = fn(P, PAR)
