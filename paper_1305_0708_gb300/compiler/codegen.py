@@ -54,66 +54,6 @@ def _lit(x):
     return f"R({v!r})"
 
 
-def _peak_live(p, order):
-    """Estimated peak number of live registers (32-bit words) of the wavefunctions and sub-currents
-    when the helicities are emitted in `order` (indices into p.amp_terms), each variant living from its
-    emission to its last use: 8 words for a four-vector or spinor, 2 for a scalar."""
-    nodes = p.nodes
-    first, last = {}, {}
-    t = 0
-
-    def size(nid):
-        return 2 if PARTICLES[nodes[nid].ptype].is_scalar else 8
-
-    def child_vars(nid, var, child):
-        hmap = dict(zip(sorted(nodes[nid].legs), var))
-        return tuple(hmap[l] for l in sorted(nodes[child].legs))
-
-    def need(nid, var):
-        nonlocal t
-        key = (nid, var)
-        if key in first:
-            last[key] = t
-            return
-        nd = nodes[nid]
-        if not nd.external:
-            for c in nd.children:
-                need(c, child_vars(nid, var, c))
-        t += 1
-        first[key] = last[key] = t
-
-    for hi in order:
-        for aid, chvars in p.amp_terms[hi]:
-            for c, cv in zip(p.amps[aid].children, chvars):
-                need(c, cv)
-        t += 1
-    delta = [0] * (t + 2)
-    for key, a in first.items():
-        delta[a] += size(key[0])
-        delta[last[key] + 1] -= size(key[0])
-    peak = cur = 0
-    for d in delta:
-        cur += d
-        peak = max(peak, cur)
-    return peak
-
-
-def _helicity_order(p):
-    """Emission order of the live helicities: lexicographic over the legs taken in the order (slowest
-    leg first) that minimises the estimated peak of live registers.  A sub-current lives from the
-    first to the last helicity that uses it; it dies early when the legs it depends on vary slowly."""
-    import itertools
-    n = len(p.legs)
-    best = None
-    perms = itertools.permutations(range(n)) if n <= 7 else [tuple(range(n))]
-    for perm in perms:
-        order = sorted(range(len(p.live)), key=lambda i: tuple(p.live[i][l] for l in perm))
-        pk = _peak_live(p, order)
-        if best is None or pk < best[0]:
-            best = (pk, order)
-    return best[1]
-
-
 class _Emitter:
     def __init__(self, prog, tag, mode="fp64"):
         self.p = prog
@@ -235,8 +175,7 @@ class _Emitter:
         E("  // per helicity: the wavefunctions and sub-currents it needs first, its diagram amplitudes")
         E("  // into colour components, then its colour sum (J^T C J)/den; helicity sum, average")
         E("  R tot = R(0);")
-        for hi in _helicity_order(p):
-            terms = p.amp_terms[hi]
+        for hi, terms in enumerate(p.amp_terms):
             for aid, chvars in terms:
                 for c, cv in zip(p.amps[aid].children, chvars):
                     need(c, cv)
