@@ -30,6 +30,9 @@ Functions and their pins (tests/test_oracle_processes.py):
   uux_zh          u u~ > z h     : closed form from the trace, exact per point
   udx_wph         u d~ > w+ h    : closed form from the trace, exact per point
   udx_wpg, uux_zg q q~ > V g     : textbook closed form (t^2 + u^2 + 2 s mV^2)/(t u), exact per point
+  ug_wpd          u g > w+ d     : the same closed form crossed (s <-> u, one fermion: sign -1), exact
+  uux_zzg         u u~ > z z g   : Ward identity for the gluon, the soft-gluon limit against C_F times
+                   the eikonal factor times u u~ > z z, boosts
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
@@ -512,6 +515,52 @@ def uux_zz(P, par=SMParams()):
 
 
 # --------------------------------------------------------------------------
+# u u~ > Z Z g  (Z pair plus one jet: the gluon and the two Z in every order along the quark line)
+# --------------------------------------------------------------------------
+def uux_zzg(P, par=SMParams(), eps_override=None):
+    """u(p0) u~(p1) > Z(p2) Z(p3) g(p4): the six orderings of the gluon and the two Z emissions along
+    the quark line, colour t^a.  eps_override replaces the gluon's polarisation vector."""
+    p = [P[:, k] for k in range(5)]
+    zl, zr = _z_couplings("u", par)
+    cT = _colour_string([0], 1)
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_W, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        e2 = polarisation(p[2], h[2], mass=par.mZ).conj()
+        e3 = polarisation(p[3], h[3], mass=par.mZ).conj()
+        eg = polarisation(p[4], h[4]).conj() if eps_override is None else eps_override
+        ins = {"Z2": (vector_insertion(e2, zl, zr), p[2]), "Z3": (vector_insertion(e3, zl, zr), p[3]),
+               "G": (vector_insertion(eg, par.gs, par.gs), p[4])}
+        A = sum(fermion_line(vb, u, p[0], [ins[x] for x in order])
+                for order in itertools.permutations(["Z2", "Z3", "G"]))
+        tot = tot + colour.colour_sum([A / 1j], [cT])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
+# u g > W+ d  (the crossing of u d~ > W+ g: the incoming gluon on either side of the W emission)
+# --------------------------------------------------------------------------
+def ug_wpd(P, par=SMParams()):
+    """u(p0) g(p1) > W+(p2) d(p3): the quark line from u(p0) to ubar_d(p3) with the gluon absorbed
+    before or after the W emission, colour t^a; averaged over 2 x 2 spins and 3 x 8 colours."""
+    p = [P[:, k] for k in range(4)]
+    gw = par.g / np.sqrt(2.0)
+    cT = _colour_string([0], 1)
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_V, HEL_W, HEL_F):
+        u = u_spinor(p[0], h[0])
+        eg = polarisation(p[1], h[1])
+        ew = polarisation(p[2], h[2], mass=par.mW).conj()
+        ubd = bar(u_spinor(p[3], h[3]))
+        G = (vector_insertion(eg, par.gs, par.gs), -p[1])
+        W = (vector_insertion(ew, gw, 0.0), p[2])
+        A = fermion_line(ubd, u, p[0], [G, W]) + fermion_line(ubd, u, p[0], [W, G])
+        tot = tot + colour.colour_sum([A / 1j], [cT])
+    return tot / 96.0
+
+
+# --------------------------------------------------------------------------
 # u u~ > Z H  (s-channel Z through the ZZH vertex)
 # --------------------------------------------------------------------------
 def uux_zh(P, par=SMParams()):
@@ -874,6 +923,8 @@ PROCESSES = {
     "u d~ > w+ h": udx_wph,
     "u d~ > w+ g": udx_wpg,
     "u u~ > z g": uux_zg,
+    "u g > w+ d": ug_wpd,
+    "u u~ > z z g": uux_zzg,
     "u u~ > w+ w- a": uux_wpwma,
     "g g > t t~": gg_ttx,
     "g g > t t~ h": gg_ttxh,

@@ -665,3 +665,59 @@ def test_qqx_vg_closed_form(which):
     u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
     want = (4.0 / 9.0) * (gl ** 2 + gr ** 2) * PAR.gs ** 2 * (t * t + u * u + 2 * s * mV ** 2) / (t * u)
     assert np.allclose(fn(P, PAR), want, rtol=1e-12, atol=0)
+
+
+def test_ug_wpd_crossed_closed_form():
+    """u g > W+ d is u d~ > W+ g crossed (the d~ and the gluon exchanged, one fermion crossed: sign -1).
+    The q q~ invariants map as s -> u, t -> t, u -> s, so summed over spins and colours it is
+    -(4/9)(36)(gL^2)(gs^2)(s^2 + t^2 + 2 u mW^2)/(s t), averaged over 4 spins and 24 colours, with
+    s = (p_u + p_g)^2, t = (p_u - p_W)^2, u = (p_u - p_d)^2."""
+    mW, gl = PAR.mW, PAR.g / math.sqrt(2.0)
+    P = two_to_two(400.0, 64, mW, 0.0, seed=71)
+    s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
+    t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
+    u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    summed = -(4.0 / 9.0) * 36.0 * gl ** 2 * PAR.gs ** 2 * (s * s + t * t + 2 * u * mW ** 2) / (s * t)
+    assert np.allclose(pr.ug_wpd(P, PAR), summed / 96.0, rtol=1e-12, atol=0)
+
+
+def _zzg_points(sqrt_s, n, seed):
+    u = np.random.default_rng(seed).uniform(0.01, 0.99, (n, 12))
+    pf, _ = ps.rambo_massive(sqrt_s, [PAR.mZ, PAR.mZ, 0.0], u)
+    P = np.zeros((n, 5, 4))
+    P[:, 0], P[:, 1] = ps.incoming(sqrt_s, n)
+    P[:, 2:] = pf
+    return P
+
+
+def test_uux_zzg_ward_soft_and_boosts():
+    """u u~ > Z Z g: the gluon's polarisation replaced by its momentum gives zero; as the gluon's energy
+    w goes to zero |M|^2 tends to gs^2 C_F 2 (p_u.p_u~) / ((p_u.k)(p_u~.k)) |M|^2(u u~ > Z Z), the
+    deviation falling in proportion to w; and |M|^2 is Lorentz invariant."""
+    P = _zzg_points(600.0, 20, seed=72)
+    ref = pr.uux_zzg(P, PAR)
+    ward = pr.uux_zzg(P, PAR, eps_override=P[:, 4].astype(complex))
+    assert np.all(np.abs(ward) <= 1e-24 * ref)
+    assert np.allclose(pr.uux_zzg(random_lorentz(P, seed=73), PAR), ref, rtol=1e-10)
+    base = two_to_two(500.0, 6, PAR.mZ, PAR.mZ, seed=74)
+    m2 = pr.uux_zz(base, PAR)
+    nhat = np.array([0.6, 0.0, 0.8])
+    devs = []
+    for w in (1e-1, 1e-2):
+        Q = np.zeros((6, 5, 4))
+        Q[:, :2] = base[:, :2]
+        k = np.concatenate([[w], w * nhat])
+        Qv = base[:, 0] + base[:, 1] - k
+        Q2 = mdot(Qv, Qv)
+        pst = np.sqrt(Q2 / 4 - PAR.mZ ** 2)
+        d = base[:, 2, 1:] / np.linalg.norm(base[:, 2, 1:], axis=1)[:, None]
+        rest = np.zeros((6, 2, 4))
+        rest[:, 0, 0] = rest[:, 1, 0] = np.sqrt(Q2) / 2
+        rest[:, 0, 1:] = pst[:, None] * d
+        rest[:, 1, 1:] = -pst[:, None] * d
+        for i in range(6):
+            Q[i, 2:4] = boost(rest[i], Qv[i, 1:] / Qv[i, 0])
+        Q[:, 4] = k
+        eik = PAR.gs ** 2 * (4.0 / 3.0) * 2 * mdot(Q[:, 0], Q[:, 1]) / (mdot(Q[:, 0], k) * mdot(Q[:, 1], k))
+        devs.append(np.max(np.abs(pr.uux_zzg(Q, PAR) / (eik * m2) - 1)))
+    assert devs[1] < 2e-3 and devs[1] < devs[0] / 5
