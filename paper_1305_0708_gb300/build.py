@@ -42,6 +42,8 @@ PROCESSES = [
     ("h h > h h", []),
     ("u d~ > w+ g", []),
     ("u u~ > z g", []),
+    ("u g > w+ d", []),
+    ("u u~ > z z g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -78,6 +78,16 @@ VARIANTS = {
         cuts=dict(legs=(3,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
         describe="u u~ > Z g (Z plus one jet), massive RAMBO at sqrt(s)=500 GeV, gluon pT>20, |eta|<2.5, "
                  "2^20 accepted points, seed 14"),
+    "ug_wpd": dict(
+        process="u g > w+ d", kind="rambo", sqrt_s=500.0, masses=(0, 0, 80.4, 0), n=1 << 20, seed=15,
+        cuts=dict(legs=(3,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="u g > W+ d (quark-gluon initial state), massive RAMBO at sqrt(s)=500 GeV, d-jet pT>20, "
+                 "|eta|<2.5, 2^20 accepted points, seed 15"),
+    "uux_zzg": dict(
+        process="u u~ > z z g", kind="rambo", sqrt_s=500.0, masses=(0, 0, 91.1876, 91.1876, 0), n=1 << 20,
+        seed=16, cuts=dict(legs=(4,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=0.5,
+        describe="u u~ > Z Z g (Z pair plus one jet, six diagrams), massive RAMBO at sqrt(s)=500 GeV, gluon "
+                 "pT>20, |eta|<2.5, 2^20 accepted points, seed 16"),
     "gg_ttx": dict(
         process="g g > t t~", kind="rambo", sqrt_s=800.0, masses=(0, 0, 175.0, 175.0), n=1 << 20, seed=11,
         cuts=None, s_ident=1.0,
