@@ -20,6 +20,8 @@ Functions and their pins (tests/test_oracle_processes.py):
   uux_gg          u u~ > g g     : textbook closed form, exact per point
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
   hh_hh           h h > h h      : closed form from the Higgs potential, exact per point
+  gg_ttxg         g g > t t~ g   : Ward identity for each of the three gluons (zero top width), Bose
+                   symmetry of the incoming gluons, boosts
   gg_ttxh         g g > t t~ h   : Ward identity for each gluon (zero top width), the soft-Higgs
                    limit against the eikonal factor times g g > t t~, Bose symmetry, boosts
   gg_ttx_dilep    g g > t t~ > b e+ ve b~ e- ve~ (doubly resonant diagrams):
@@ -310,6 +312,110 @@ def gg_ttxh(P, par=SMParams(), per_helicity=False, eps_override=None, widths=Tru
         tot = tot + val
     if per_helicity:
         return ph
+    return tot / (4.0 * 64.0)
+
+
+# --------------------------------------------------------------------------
+# g g > t t~ g  (top pair plus one jet: sixteen diagrams)
+# --------------------------------------------------------------------------
+def _vvvv_out(J1, J2, J3):
+    """Lorentz parts of the four-gluon vertex with legs (1, 2, 3) contracted and the fourth open, for
+    its three colour structures f^{12e} f^{3Xe}, f^{13e} f^{2Xe}, f^{1Xe} f^{23e} (Sect. 4.2 VVVV,
+    the textbook rule -i gs^2 [f^{abe} f^{cde} (g^{ac} g^{bd} - g^{ad} g^{bc}) + two permutations])."""
+    d12, d13, d23 = mdot(J1, J2)[..., None], mdot(J1, J3)[..., None], mdot(J2, J3)[..., None]
+    return (d13 * J2 - d23 * J1, d12 * J3 - d23 * J1, d12 * J3 - d13 * J2)
+
+
+def gg_ttxg(P, par=SMParams(), eps_override=None, widths=True):
+    """g(0) g(1) > t(2) t~(3) g(4).  The top line runs from v(p3) to ubar(p2); the diagrams are
+      - the three gluons attached to the line in each of the six orders (colour t t t),
+      - two gluons joined by a three-gluon vertex into one line attached beside the third gluon, for
+        the three pairs and both orders along the line (six; colour f t t),
+      - the three gluons joined into one line through two three-gluon vertices (three) or the
+        four-gluon vertex (one, three colour structures), attached to the top line (colour f f t).
+    Colour is summed over explicit indices; internal tops carry the width wt unless widths=False.
+    eps_override = (leg, vector) replaces that gluon's polarisation vector."""
+    p = [P[:, k] for k in range(5)]
+    gs, mt = par.gs, par.mt
+    wt = par.wt if widths else 0.0
+    T, F = _T, _F
+    # gluon momenta flowing into the gluon vertices; k4 is the outgoing gluon's, reversed
+    kg = {0: p[0], 1: p[1], 4: -p[4]}
+    legs = (0, 1, 4)
+
+    def ctensor(spec):
+        """Colour tensor [i_start, i_end, a0, a1, a4] of a colour factor given as an einsum over t and f."""
+        out = np.zeros((3, 3, 8, 8, 8), dtype=complex)
+        for a in itertools.product(range(8), repeat=3):
+            A = dict(zip(legs, a))
+            out[(slice(None), slice(None)) + a] = spec(A).T
+        return out
+
+    tensors, amp_specs = [], []
+    # six orders of direct attachment (first in the list = nearest the t~)
+    for order in itertools.permutations(legs):
+        tensors.append(ctensor(lambda A, o=order: T[A[o[2]]] @ T[A[o[1]]] @ T[A[o[0]]]))
+        amp_specs.append(("direct", order))
+    # a pair (x, y) merged by f^{a_x a_y c} into one gluon c, attached with the third gluon z
+    for x, y in ((0, 1), (0, 4), (1, 4)):
+        z = [l for l in legs if l not in (x, y)][0]
+        fxy = lambda A, x=x, y=y: np.einsum("c,cij->ij", F[A[x], A[y], :], T)
+        tensors.append(ctensor(lambda A, f=fxy, z=z: T[A[z]] @ f(A)))
+        amp_specs.append(("pair_first", (x, y, z)))
+        tensors.append(ctensor(lambda A, f=fxy, z=z: f(A) @ T[A[z]]))
+        amp_specs.append(("pair_last", (x, y, z)))
+    # all three merged: (x y) then z through two three-gluon vertices, f^{xye} f^{ezg} t^g
+    for x, y in ((0, 1), (0, 4), (1, 4)):
+        z = [l for l in legs if l not in (x, y)][0]
+        tensors.append(ctensor(lambda A, x=x, y=y, z=z:
+                               np.einsum("e,eg,gij->ij", F[A[x], A[y], :], F[:, A[z], :], T)))
+        amp_specs.append(("triple", (x, y, z)))
+    # four-gluon vertex, legs (0, 1, 4, X): f^{01e} f^{4Xe}, f^{04e} f^{1Xe}, f^{0Xe} f^{14e}
+    tensors.append(ctensor(lambda A: np.einsum("e,ge,gij->ij", F[A[0], A[1], :], F[A[4], :, :], T)))
+    amp_specs.append(("quartic", 0))
+    tensors.append(ctensor(lambda A: np.einsum("e,ge,gij->ij", F[A[0], A[4], :], F[A[1], :, :], T)))
+    amp_specs.append(("quartic", 1))
+    tensors.append(ctensor(lambda A: np.einsum("ge,e,gij->ij", F[A[0], :, :], F[A[1], A[4], :], T)))
+    amp_specs.append(("quartic", 2))
+
+    tot = 0.0
+    for h in itertools.product(HEL_V, HEL_V, HEL_F, HEL_F, HEL_V):
+        eps = {0: polarisation(p[0], h[0]), 1: polarisation(p[1], h[1]), 4: polarisation(p[4], h[4]).conj()}
+        if eps_override is not None:
+            eps[eps_override[0]] = eps_override[1]
+        ubt = bar(u_spinor(p[2], h[2]))
+        vt = v_spinor(p[3], h[3])
+
+        def ins(J, kin):
+            """A gluon line carrying momentum kin into the top line."""
+            return (vector_insertion(J, gs, gs), -kin)
+
+        def merge(x, y):
+            """Propagated gluon line of gluons x and y through f^{a_x a_y c}; momentum into the line."""
+            k = kg[x] + kg[y]
+            return vector_prop(k, vvv_out(eps[x], kg[x], eps[y], kg[y], -k, gs)), k
+
+        amps = []
+        for kind, spec in amp_specs:
+            if kind == "direct":
+                a = fermion_line(ubt, vt, -p[3], [ins(eps[l], kg[l]) for l in spec], mt, wt)
+            elif kind in ("pair_first", "pair_last"):
+                x, y, z = spec
+                J, k = merge(x, y)
+                seq = [ins(J, k), ins(eps[z], kg[z])] if kind == "pair_first" else [ins(eps[z], kg[z]), ins(J, k)]
+                a = fermion_line(ubt, vt, -p[3], seq, mt, wt)
+            elif kind == "triple":
+                x, y, z = spec
+                J, k = merge(x, y)
+                K = k + kg[z]
+                G = vector_prop(K, vvv_out(J, k, eps[z], kg[z], -K, gs))
+                a = fermion_line(ubt, vt, -p[3], [ins(G, K)], mt, wt)
+            else:
+                K = kg[0] + kg[1] + kg[4]
+                G = vector_prop(K, -1j * gs * gs * _vvvv_out(eps[0], eps[1], eps[4])[spec])
+                a = fermion_line(ubt, vt, -p[3], [ins(G, K)], mt, wt)
+            amps.append(a / 1j)
+        tot = tot + colour.colour_sum(amps, tensors)
     return tot / (4.0 * 64.0)
 
 
@@ -928,6 +1034,7 @@ PROCESSES = {
     "u u~ > w+ w- a": uux_wpwma,
     "g g > t t~": gg_ttx,
     "g g > t t~ h": gg_ttxh,
+    "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,
     "u d~ > w+ z": udx_wpz,

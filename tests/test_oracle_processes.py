@@ -721,3 +721,44 @@ def test_uux_zzg_ward_soft_and_boosts():
         eik = PAR.gs ** 2 * (4.0 / 3.0) * 2 * mdot(Q[:, 0], Q[:, 1]) / (mdot(Q[:, 0], k) * mdot(Q[:, 1], k))
         devs.append(np.max(np.abs(pr.uux_zzg(Q, PAR) / (eik * m2) - 1)))
     assert devs[1] < 2e-3 and devs[1] < devs[0] / 5
+
+
+def _ttxg_points(sqrt_s, n, seed):
+    u = np.random.default_rng(seed).uniform(0.01, 0.99, (n, 12))
+    pf, _ = ps.rambo_massive(sqrt_s, [PAR.mt, PAR.mt, 0.0], u)
+    P = np.zeros((n, 5, 4))
+    P[:, 0], P[:, 1] = ps.incoming(sqrt_s, n)
+    P[:, 2:] = pf
+    return P
+
+
+@pytest.mark.parametrize("leg", [0, 1, 4])
+def test_gg_ttxg_ward_identity(leg):
+    """g g > t t~ g: any gluon's polarisation replaced by its momentum (zero top width) gives zero once
+    all sixteen diagrams are summed: the three-gluon, four-gluon and quark-gluon rules must agree in
+    sign and strength.  Dropping the four-gluon diagram breaks it."""
+    P = _ttxg_points(1000.0, 4, seed=81)
+    ref = pr.gg_ttxg(P, PAR, widths=False)
+    ward = pr.gg_ttxg(P, PAR, widths=False, eps_override=(leg, P[:, leg].astype(complex)))
+    assert np.all(np.abs(ward) <= 1e-20 * ref)
+
+
+def test_gg_ttxg_bose_and_boosts():
+    """Swapping the incoming gluons leaves |M|^2 unchanged; so do random Lorentz transformations."""
+    P = _ttxg_points(900.0, 3, seed=82)
+    ref = pr.gg_ttxg(P, PAR)
+    assert np.allclose(pr.gg_ttxg(P[:, [1, 0, 2, 3, 4]], PAR), ref, rtol=1e-11)
+    assert np.allclose(pr.gg_ttxg(random_lorentz(P, seed=83), PAR), ref, rtol=1e-10)
+
+
+def test_gg_ttxg_ward_identity_needs_the_four_gluon_vertex(monkeypatch):
+    """The Ward identity of g g > t t~ g fails when the four-gluon diagram is dropped or its sign
+    flipped (a mistake planted in the oracle), so the pin above constrains that vertex."""
+    P = _ttxg_points(1000.0, 3, seed=81)
+    k4 = (4, P[:, 4].astype(complex))
+    orig = pr._vvvv_out
+    for planted in (lambda a, b, c: tuple(0 * x for x in orig(a, b, c)),
+                    lambda a, b, c: tuple(-x for x in orig(a, b, c))):
+        monkeypatch.setattr(pr, "_vvvv_out", planted)
+        ref = pr.gg_ttxg(P, PAR, widths=False)
+        assert np.all(np.abs(pr.gg_ttxg(P, PAR, widths=False, eps_override=k4)) > 1e-3 * ref)
