@@ -44,6 +44,7 @@ PROCESSES = [
     ("u u~ > z g", []),
     ("u g > w+ d", []),
     ("u u~ > z z g", []),
+    ("g g > t t~ g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)
