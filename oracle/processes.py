@@ -1032,7 +1032,6 @@ PROCESSES = {
     "u g > w+ d": ug_wpd,
     "u u~ > z z g": uux_zzg,
     "u u~ > w+ w- a": uux_wpwma,
-    "g g > t t~": gg_ttx,
     "g g > t t~ h": gg_ttxh,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,

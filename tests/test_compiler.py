@@ -14,6 +14,23 @@ CASES = {
     "u s > d c h h": (4, 1, 1),
     "u u~ > g g": (3, 8, 2),
     "g g > g g": (6, 16, 6),
+    # diagram terms (the four-gluon vertex counts once per colour structure), live helicities, colour
+    # dimension, each counted by hand from the Feynman rules
+    "u u~ > w+ w-": (3, 18, 1),          # t-channel d; s-channel photon and Z
+    "u d~ > w+ z": (3, 9, 1),            # Z from u, Z from d; s-channel W
+    "u u~ > z z": (2, 18, 1),
+    "u u~ > z h": (1, 6, 1),
+    "u d~ > w+ h": (1, 3, 1),
+    "u d~ > w+ g": (2, 6, 1),
+    "u g > w+ d": (2, 6, 1),
+    "u u~ > z g": (2, 12, 1),
+    "u u~ > z z g": (6, 36, 1),          # 3! orders of Z, Z, g along the quark line
+    "u u~ > w+ w- a": (15, 36, 1),       # 3 + 2 + 4 + 4 + 2 (line, W lines, ISR, W emission, quartic)
+    "g g > t t~": (3, 16, 2),
+    "g g > t t~ h": (8, 16, 2),          # the Higgs on every top line of the three g g > t t~ graphs
+    "g g > t t~ g": (18, 32, 6),         # 6 + 6 + 3 + one four-gluon graph with three colour structures
+    "u u > u u": (6, 6, 2),              # g, photon, Z in the t and u channels; chirality-conserving helicities
+    "h h > h h": (4, 1, 1),              # contact plus s, t, u exchange
 }
 
 
@@ -89,3 +106,20 @@ def test_pruned_helicities_are_exact_zeros(name, fn):
         if h not in live:
             assert np.all(v <= 1e-13 * tot), h
     assert sum(1 for h in ph if h in live and np.any(ph[h] > 1e-12 * tot)) > 0
+
+
+def test_every_compiled_process_has_a_pinned_oracle_and_a_parity_workload():
+    """Each process string compiled into the library has an oracle function, and each workload or
+    variant that the GPU parity tests and the bench run names a compiled process with an oracle."""
+    from paper_1305_0708_gb300 import build
+    from paper_1305_0708_gb300.workloads import VARIANTS, WORKLOADS
+    compiled = set()
+    for name, aliases in build.PROCESSES:
+        compiled.add(name)
+        compiled.update(aliases)
+        assert name in opr.PROCESSES or any(a in opr.PROCESSES for a in aliases), name
+    for n, _ in build.GLUON_PROCESSES:
+        assert "g g > " + " ".join(["g"] * (n - 2)) in opr.PROCESSES
+    for key, w in {**WORKLOADS, **VARIANTS}.items():
+        proc = w["process"]
+        assert proc in compiled or proc.startswith("g g > g g g"), key
