@@ -762,3 +762,39 @@ def test_gg_ttxg_ward_identity_needs_the_four_gluon_vertex(monkeypatch):
         monkeypatch.setattr(pr, "_vvvv_out", planted)
         ref = pr.gg_ttxg(P, PAR, widths=False)
         assert np.all(np.abs(pr.gg_ttxg(P, PAR, widths=False, eps_override=k4)) > 1e-3 * ref)
+
+
+def test_ttbar_chain_narrow_width_factorisation():
+    """Integrated over the full six-body phase space at fixed sqrt(s) = 1 TeV, g g > t t~ > b e+ ve
+    b~ e- ve~ factorises into the on-shell g g > t t~ phase-space integral times the square of the
+    branching ratio B = [Gamma(t > b W) / wt] [Gamma(W > e ve) / wW], computed from the same couplings
+    (Gamma(t > b W) = g^2 mt^3 (1 - r)^2 (1 + 2r) / (64 pi mW^2), r = mW^2/mt^2; Gamma(W > e ve) =
+    g^2 mW / (48 pi)), times the fraction (2/pi) atan(20) of each Breit-Wigner inside the generator's
+    window of 20 widths.  This pins the decay chain's normalisation (couplings, propagators, phase-space
+    weights) against the closed-form-pinned g g > t t~.  The finite widths (wt/mt ~ 1 %, wW/mW ~ 3 %)
+    and the Monte Carlo error (~2 % at 6,000 points) bound the agreement; 8 % is allowed."""
+    par = PAR
+    rs = 1000.0
+    n = 6000
+    u = np.random.default_rng(5).uniform(0.0, 1.0, (n, 16))
+    P, wt, ok, _ = ps.ttbar_dilepton(u, par, (rs, rs))
+    f = np.zeros(n)
+    f[ok] = pr.gg_ttx_dilep(P[ok], par) * wt[ok]
+    i6 = f.mean()
+    x, wq = np.polynomial.legendre.leggauss(64)
+    beta = math.sqrt(1 - 4 * par.mt ** 2 / rs ** 2)
+    Q = np.zeros((64, 4, 4))
+    Q[:, 0] = [rs / 2, 0, 0, rs / 2]
+    Q[:, 1] = [rs / 2, 0, 0, -rs / 2]
+    Q[:, 2, 0] = Q[:, 3, 0] = rs / 2
+    Q[:, 2, 1] = beta * rs / 2 * np.sqrt(1 - x * x)
+    Q[:, 2, 3] = beta * rs / 2 * x
+    Q[:, 3, 1:] = -Q[:, 2, 1:]
+    i2 = beta / (8 * math.pi) * 0.5 * np.sum(wq * pr.gg_ttx(Q, par, widths=False))
+    g2 = par.g ** 2
+    r = par.mW ** 2 / par.mt ** 2
+    gamma_tbw = g2 * par.mt ** 3 * (1 - r) ** 2 * (1 + 2 * r) / (64 * math.pi * par.mW ** 2)
+    gamma_wen = g2 * par.mW / (48 * math.pi)
+    B = gamma_tbw / par.wt * gamma_wen / par.wW
+    window = (2 / math.pi) * math.atan(20.0)
+    assert abs(i6 / (i2 * B ** 2 * window ** 4) - 1) < 0.08
