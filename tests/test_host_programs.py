@@ -1,0 +1,133 @@
+"""The generated helicity programs, compiled for the host CPU, against the oracle.
+
+The code generator's FP64 and mixed-precision evaluators are host-and-device functions.  Compiled
+into a small host program (tests/host/host_eval.cu) they run here without a GPU, so the process
+compiler, the HEGET-style device functions and the double-float arithmetic are checked on the
+CPU.  The same tolerances as the GPU parity tests apply: FP64 within 1e-12 relative plus the
+oracle's own conditioning spread, mixed median <= 1e-5 and max <= 1e-3.  Needs nvcc.
+"""
+import math
+import os
+import re
+import shutil
+import struct
+import subprocess
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+from oracle import phasespace as ps, processes as opr
+from oracle.sm import SMParams
+
+PAR = SMParams()
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1305_0708_gb300", "csrc")
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="needs nvcc")
+
+# process -> (oracle, sqrt(s), final-state masses, legs with pT > 20 and |eta| < 2.5)
+CASES = {
+    "u u~ > w+ w- a": (opr.uux_wpwma, 500.0, (80.4, 80.4, 0.0), (4,)),
+    "g g > t t~ h": (opr.gg_ttxh, 1000.0, (175.0, 175.0, 125.0), ()),
+    "g g > t t~ g": (opr.gg_ttxg, 1000.0, (175.0, 175.0, 0.0), (4,)),
+    "u u~ > z z g": (opr.uux_zzg, 500.0, (91.1876, 91.1876, 0.0), (4,)),
+    "u s > d c h h": (opr.us_dchh, 1000.0, (0.0, 0.0, 125.0, 125.0), ()),
+    "u g > w+ d": (opr.ug_wpd, 500.0, (80.4, 0.0), (3,)),
+}
+
+
+def _nvcc():
+    return shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+
+
+def _points(sqrt_s, masses, cut_legs, n, seed):
+    u = ps.uniforms(seed, np.arange(n), np.zeros(n), 4 * len(masses))
+    pf, _ = ps.rambo_massive(sqrt_s, list(masses), u)
+    P = np.zeros((n, len(masses) + 2, 4))
+    P[:, 0], P[:, 1] = ps.incoming(sqrt_s, n)
+    P[:, 2:] = pf
+    keep = np.ones(n, dtype=bool)
+    for leg in cut_legs:
+        pt = np.hypot(P[:, leg, 1], P[:, leg, 2])
+        eta = np.arcsinh(P[:, leg, 3] / np.maximum(pt, 1e-300))
+        keep &= (pt > 20.0) & (np.abs(eta) < 2.5)
+    return P[keep]
+
+
+def _tolerance(fn, P, ref, masses):
+    """1e-12 relative plus 32 times the oracle's spread under 2^-52 input perturbations and under
+    recomputing the energies on shell (RAMBO leaves a few points off shell at ~1e-11)."""
+    rng = np.random.default_rng(123)
+    spread = np.zeros_like(ref)
+    for _ in range(3):
+        Q = P * (1 + 2.0 ** -52 * rng.standard_normal(P.shape))
+        spread = np.maximum(spread, np.abs(fn(Q, PAR) - ref))
+    Q = P.copy()
+    for k, m in enumerate(masses):
+        Q[:, k, 0] = np.sqrt(m * m + np.sum(P[:, k, 1:] ** 2, axis=1))
+    spread = np.maximum(spread, np.abs(fn(Q, PAR) - ref))
+    return 1e-12 * np.abs(ref) + 32 * spread
+
+
+def _build(name, workdir):
+    from paper_1305_0708_gb300.compiler.codegen import generate_source, process_symbol
+    from paper_1305_0708_gb300.compiler.model import DEFAULT_PARAMS, couplings
+    from paper_1305_0708_gb300.compiler.program import compile_process
+    tag = process_symbol(name)
+    src, _ = generate_source(compile_process(name), tag)
+    cut = src.rindex("ME_DEFINE_PROCESS(")           # kernels and registration stay out of the host build
+    unit = os.path.join(workdir, tag + ".cuh")
+    with open(unit, "w") as f:
+        f.write(src[:cut] + src[src.index("\n", cut):])
+    fields = re.findall(r"double (\w+);", src[src.index("struct Params {"):src.index("struct ParamsMx")])
+    c = couplings(DEFAULT_PARAMS)
+    params = [c[x] for x in fields]
+    exe = os.path.join(workdir, tag)
+    n_ext = int(re.search(r"static constexpr int NEXT = (\d+);", src).group(1))
+    cmd = [_nvcc(), "-O1", "-std=c++17", "--expt-relaxed-constexpr", "-gencode", "arch=compute_103a,code=sm_103a",
+           "-I", CSRC, "-I", workdir, "-I", os.path.join(ROOT, "include"), f'-DGEN_UNIT="{unit}"', f"-DTAG={tag}",
+           f"-DNEXT_H={n_ext}", os.path.join(HERE, "host", "host_eval.cu"), "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-4000:]
+    return exe, params
+
+
+@pytest.fixture(scope="module")
+def programs():
+    from paper_1305_0708_gb300.compiler import dftables
+    with tempfile.TemporaryDirectory() as d:
+        with open(os.path.join(d, "dfloat_tables.h"), "w") as f:
+            f.write(dftables.header())
+        with ThreadPoolExecutor(max_workers=min(6, os.cpu_count() or 1)) as ex:
+            built = dict(zip(CASES, ex.map(lambda n: _build(n, d), CASES)))
+        yield d, built
+
+
+def _run(exe, params, P, workdir):
+    inp = os.path.join(workdir, os.path.basename(exe) + ".in")
+    out = os.path.join(workdir, os.path.basename(exe) + ".out")
+    with open(inp, "wb") as f:
+        f.write(struct.pack("ii", P.shape[0], len(params)))
+        f.write(np.asarray(params, dtype=np.float64).tobytes())
+        f.write(np.ascontiguousarray(P, dtype=np.float64).tobytes())
+    subprocess.run([exe, inp, out], check=True)
+    return np.fromfile(out).reshape(-1, 2)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_host_program_matches_oracle(programs, name):
+    d, built = programs
+    fn, rs, masses, cut_legs = CASES[name]
+    P = _points(rs, masses, cut_legs, 300, seed=7)
+    assert P.shape[0] > 200
+    exe, params = built[name]
+    got = _run(exe, params, P, d)
+    ref = fn(P, PAR)
+    assert np.all(np.abs(got[:, 0] - ref) <= _tolerance(fn, P, ref, (0.0, 0.0) + tuple(masses)))
+    rel = np.abs(got[:, 1] / ref - 1)
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3, (np.median(rel), rel.max())
+    assert math.isfinite(float(got.sum()))
