@@ -35,6 +35,8 @@ Functions and their pins (tests/test_oracle_processes.py):
   ug_wpd          u g > w+ d     : the same closed form crossed (s <-> u, one fermion: sign -1), exact
   uux_zzg         u u~ > z z g   : Ward identity for the gluon, the soft-gluon limit against C_F times
                    the eikonal factor times u u~ > z z, boosts
+  uux_zhg, udx_wpzg  u u~ > z h g, u d~ > w+ z g : the same three pins against u u~ > z h and
+                   u d~ > w+ z
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
@@ -645,6 +647,69 @@ def uux_zzg(P, par=SMParams(), eps_override=None):
 
 
 # --------------------------------------------------------------------------
+# vector-boson pairs and HV plus one jet: the gluon at every place along the quark line
+# --------------------------------------------------------------------------
+def _with_gluon(lines, eg, kg, gs):
+    """Sum over the places of one gluon emission (vector eg, outgoing momentum kg) along each quark
+    line of `lines`: (row, col, p_start, inserts) with the insertions of the process without the
+    gluon; the gluon goes before, between or after them."""
+    G = (vector_insertion(eg, gs, gs), kg)
+    tot = 0.0
+    for row, col, p0, ins in lines:
+        for k in range(len(ins) + 1):
+            tot = tot + fermion_line(row, col, p0, ins[:k] + [G] + ins[k:])
+    return tot
+
+
+def uux_zhg(P, par=SMParams(), eps_override=None):
+    """u(p0) u~(p1) > Z(p2) H(p3) g(p4): the s-channel Z of u u~ > Z H (ZZH vertex) with the gluon
+    from the quark line before or after it (two diagrams, colour t^a)."""
+    p = [P[:, k] for k in range(5)]
+    zl, zr = _z_couplings("u", par)
+    gzzh = par.gz * par.mZ
+    cT = _colour_string([0], 1)
+    Q = p[2] + p[3]
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ez = polarisation(p[2], h[2], mass=par.mZ).conj()
+        eg = polarisation(p[4], h[3]).conj() if eps_override is None else eps_override
+        Y = vector_prop(Q, 1j * gzzh * ez, par.mZ, par.wZ)
+        A = _with_gluon([(vb, u, p[0], [(vector_insertion(Y, zl, zr), Q)])], eg, p[4], par.gs)
+        tot = tot + colour.colour_sum([A / 1j], [cT])
+    return tot / 36.0
+
+
+def udx_wpzg(P, par=SMParams(), eps_override=None):
+    """u(p0) d~(p1) > W+(p2) Z(p3) g(p4): the three graphs of u d~ > W+ Z (Z from the u line, Z from
+    the d line, s-channel W into the WWZ vertex) with the gluon at every place along the quark line
+    (3 + 3 + 2 diagrams, colour t^a)."""
+    p = [P[:, k] for k in range(5)]
+    gw = par.g / np.sqrt(2.0)
+    zu, zd = _z_couplings("u", par), _z_couplings("d", par)
+    cT = _colour_string([0], 1)
+    Q = p[2] + p[3]
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_W, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ew = polarisation(p[2], h[2], mass=par.mW).conj()
+        ez = polarisation(p[3], h[3], mass=par.mZ).conj()
+        eg = polarisation(p[4], h[4]).conj() if eps_override is None else eps_override
+        W = (vector_insertion(ew, gw, 0.0), p[2])
+        # the s-channel W: the WWZ vertex with the W+* on its first leg, contracted with the outgoing
+        # W+ and Z, propagated back to the quark line (the vertex of udx_wpz_amplitudes, leg order cycled)
+        Y = vector_prop(Q, -1j * par.g * par.cw * vvv_out(ew, -p[2], ez, -p[3], Q, 1.0), par.mW, par.wW)
+        lines = [(vb, u, p[0], [(vector_insertion(ez, *zu), p[3]), W]),
+                 (vb, u, p[0], [W, (vector_insertion(ez, *zd), p[3])]),
+                 (vb, u, p[0], [(vector_insertion(Y, gw, 0.0), Q)])]
+        A = _with_gluon(lines, eg, p[4], par.gs)
+        tot = tot + colour.colour_sum([A / 1j], [cT])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
 # u g > W+ d  (the crossing of u d~ > W+ g: the incoming gluon on either side of the W emission)
 # --------------------------------------------------------------------------
 def ug_wpd(P, par=SMParams()):
@@ -1031,6 +1096,8 @@ PROCESSES = {
     "u u~ > z g": uux_zg,
     "u g > w+ d": ug_wpd,
     "u u~ > z z g": uux_zzg,
+    "u u~ > z h g": uux_zhg,
+    "u d~ > w+ z g": udx_wpzg,
     "u u~ > w+ w- a": uux_wpwma,
     "g g > t t~ h": gg_ttxh,
     "g g > t t~ g": gg_ttxg,

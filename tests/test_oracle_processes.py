@@ -798,3 +798,54 @@ def test_ttbar_chain_narrow_width_factorisation():
     B = gamma_tbw / par.wt * gamma_wen / par.wW
     window = (2 / math.pi) * math.atan(20.0)
     assert abs(i6 / (i2 * B ** 2 * window ** 4) - 1) < 0.08
+
+
+def _soft_emission_points(base, w, nhat, m2, m3):
+    """2 -> 3 points from 2 -> 2 points: a massless emission of energy w along nhat, the two final
+    particles (masses m2, m3) recoiling in their rest frame along the original direction."""
+    n = base.shape[0]
+    P = np.zeros((n, 5, 4))
+    P[:, :2] = base[:, :2]
+    k = np.concatenate([[w], w * np.asarray(nhat)])
+    Qv = base[:, 0] + base[:, 1] - k
+    Q2 = mdot(Qv, Qv)
+    rq = np.sqrt(Q2)
+    pst = np.sqrt((Q2 - (m2 + m3) ** 2) * (Q2 - (m2 - m3) ** 2)) / (2 * rq)
+    d = base[:, 2, 1:] / np.linalg.norm(base[:, 2, 1:], axis=1)[:, None]
+    rest = np.zeros((n, 2, 4))
+    rest[:, 0, 0] = np.sqrt(m2 * m2 + pst * pst)
+    rest[:, 1, 0] = np.sqrt(m3 * m3 + pst * pst)
+    rest[:, 0, 1:] = pst[:, None] * d
+    rest[:, 1, 1:] = -pst[:, None] * d
+    for i in range(n):
+        P[i, 2:4] = boost(rest[i], Qv[i, 1:] / Qv[i, 0])
+    P[:, 4] = k
+    return P
+
+
+@pytest.mark.parametrize("which", ["zh", "wz"])
+def test_v_pair_plus_gluon_ward_soft_and_boosts(which):
+    """u u~ > Z H g and u d~ > W+ Z g: the gluon's Ward identity; as the gluon's energy w goes to zero
+    |M|^2 tends to gs^2 C_F 2 (p_q.p_q~) / ((p_q.k)(p_q~.k)) times |M|^2 without the gluon, the
+    deviation falling in proportion to w; Lorentz invariance."""
+    if which == "zh":
+        fn, base_fn, m2, m3 = pr.uux_zhg, pr.uux_zh, PAR.mZ, PAR.mH
+    else:
+        fn, base_fn, m2, m3 = pr.udx_wpzg, pr.udx_wpz, PAR.mW, PAR.mZ
+    u = np.random.default_rng(91).uniform(0.01, 0.99, (12, 12))
+    pf, _ = ps.rambo_massive(600.0, [m2, m3, 0.0], u)
+    P = np.zeros((12, 5, 4))
+    P[:, 0], P[:, 1] = ps.incoming(600.0, 12)
+    P[:, 2:] = pf
+    ref = fn(P, PAR)
+    assert np.all(np.abs(fn(P, PAR, eps_override=P[:, 4].astype(complex))) <= 1e-20 * ref)
+    assert np.allclose(fn(random_lorentz(P, seed=92), PAR), ref, rtol=1e-10)
+    base = two_to_two(500.0, 6, m2, m3, seed=93)
+    mb = base_fn(base, PAR)
+    devs = []
+    for w in (1e-1, 1e-2):
+        Q = _soft_emission_points(base, w, [0.0, 0.6, 0.8], m2, m3)
+        k = Q[:, 4]
+        eik = PAR.gs ** 2 * (4.0 / 3.0) * 2 * mdot(Q[:, 0], Q[:, 1]) / (mdot(Q[:, 0], k) * mdot(Q[:, 1], k))
+        devs.append(np.max(np.abs(fn(Q, PAR) / (eik * mb) - 1)))
+    assert devs[1] < 2e-3 and devs[1] < devs[0] / 5
