@@ -45,6 +45,8 @@ PROCESSES = [
     ("u g > w+ d", []),
     ("u u~ > z z g", []),
     ("g g > t t~ g", []),
+    ("u u~ > z h g", []),
+    ("u d~ > w+ z g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

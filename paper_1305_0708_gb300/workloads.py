@@ -88,6 +88,16 @@ VARIANTS = {
         seed=16, cuts=dict(legs=(4,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=0.5,
         describe="u u~ > Z Z g (Z pair plus one jet, six diagrams), massive RAMBO at sqrt(s)=500 GeV, gluon "
                  "pT>20, |eta|<2.5, 2^20 accepted points, seed 16"),
+    "uux_zhg": dict(
+        process="u u~ > z h g", kind="rambo", sqrt_s=600.0, masses=(0, 0, 91.1876, 125.0, 0), n=1 << 20, seed=18,
+        cuts=dict(legs=(4,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="u u~ > Z H g (Higgs-strahlung plus one jet), massive RAMBO at sqrt(s)=600 GeV, gluon pT>20, "
+                 "|eta|<2.5, 2^20 accepted points, seed 18"),
+    "udx_wpzg": dict(
+        process="u d~ > w+ z g", kind="rambo", sqrt_s=600.0, masses=(0, 0, 80.4, 91.1876, 0), n=1 << 20, seed=19,
+        cuts=dict(legs=(4,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="u d~ > W+ Z g (W Z plus one jet, eight diagrams), massive RAMBO at sqrt(s)=600 GeV, gluon "
+                 "pT>20, |eta|<2.5, 2^20 accepted points, seed 19"),
     "gg_ttx": dict(
         process="g g > t t~", kind="rambo", sqrt_s=800.0, masses=(0, 0, 175.0, 175.0), n=1 << 20, seed=11,
         cuts=None, s_ident=1.0,

@@ -25,6 +25,8 @@ CASES = {
     "u g > w+ d": (2, 6, 1),
     "u u~ > z g": (2, 12, 1),
     "u u~ > z z g": (6, 36, 1),          # 3! orders of Z, Z, g along the quark line
+    "u u~ > z h g": (2, 12, 1),          # the gluon before or after the s-channel Z
+    "u d~ > w+ z g": (8, 18, 1),         # 3 + 3 along the two t-channel lines, 2 beside the s-channel W
     "u u~ > w+ w- a": (15, 36, 1),       # 3 + 2 + 4 + 4 + 2 (line, W lines, ISR, W emission, quartic)
     "g g > t t~": (3, 16, 2),
     "g g > t t~ h": (8, 16, 2),          # the Higgs on every top line of the three g g > t t~ graphs
