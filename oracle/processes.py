@@ -35,8 +35,8 @@ Functions and their pins (tests/test_oracle_processes.py):
   ug_wpd          u g > w+ d     : the same closed form crossed (s <-> u, one fermion: sign -1), exact
   uux_zzg         u u~ > z z g   : Ward identity for the gluon, the soft-gluon limit against C_F times
                    the eikonal factor times u u~ > z z, boosts
-  uux_zhg, udx_wpzg  u u~ > z h g, u d~ > w+ z g : the same three pins against u u~ > z h and
-                   u d~ > w+ z
+  uux_zhg, udx_wpzg, uux_wpwmg  u u~ > z h g, u d~ > w+ z g, u u~ > w+ w- g : the same three pins
+                   against u u~ > z h, u d~ > w+ z and u u~ > w+ w-
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
@@ -709,6 +709,33 @@ def udx_wpzg(P, par=SMParams(), eps_override=None):
     return tot / 36.0
 
 
+def uux_wpwmg(P, par=SMParams(), eps_override=None):
+    """u(p0) u~(p1) > W+(p2) W-(p3) g(p4): the graphs of u u~ > W+ W- (t-channel d, s-channel photon
+    and Z into the WWV vertex) with the gluon at every place along the quark line (3 + 2 + 2
+    diagrams, colour t^a)."""
+    p = [P[:, k] for k in range(5)]
+    gw = par.g / np.sqrt(2.0)
+    cT = _colour_string([0], 1)
+    Q = p[2] + p[3]
+    ga = _a_coupling("u", par)
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_W, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ep = polarisation(p[2], h[2], mass=par.mW).conj()
+        em = polarisation(p[3], h[3], mass=par.mW).conj()
+        eg = polarisation(p[4], h[4]).conj() if eps_override is None else eps_override
+        lines = [(vb, u, p[0], [(vector_insertion(ep, gw, 0.0), p[2]), (vector_insertion(em, gw, 0.0), p[3])])]
+        X = vvv_out(em, -p[3], ep, -p[2], Q, 1.0)
+        for gv, (gl, gr), mV, wV in ((par.e, (ga, ga), 0.0, 0.0),
+                                     (par.g * par.cw, _z_couplings("u", par), par.mZ, par.wZ)):
+            Y = vector_prop(Q, -1j * gv * X, mV, wV)
+            lines.append((vb, u, p[0], [(vector_insertion(Y, gl, gr), Q)]))
+        A = _with_gluon(lines, eg, p[4], par.gs)
+        tot = tot + colour.colour_sum([A / 1j], [cT])
+    return tot / 36.0
+
+
 # --------------------------------------------------------------------------
 # u g > W+ d  (the crossing of u d~ > W+ g: the incoming gluon on either side of the W emission)
 # --------------------------------------------------------------------------
@@ -1098,6 +1125,7 @@ PROCESSES = {
     "u u~ > z z g": uux_zzg,
     "u u~ > z h g": uux_zhg,
     "u d~ > w+ z g": udx_wpzg,
+    "u u~ > w+ w- g": uux_wpwmg,
     "u u~ > w+ w- a": uux_wpwma,
     "g g > t t~ h": gg_ttxh,
     "g g > t t~ g": gg_ttxg,
