@@ -47,6 +47,7 @@ PROCESSES = [
     ("g g > t t~ g", []),
     ("u u~ > z h g", []),
     ("u d~ > w+ z g", []),
+    ("u u~ > w+ w- g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

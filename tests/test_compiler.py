@@ -27,6 +27,7 @@ CASES = {
     "u u~ > z z g": (6, 36, 1),          # 3! orders of Z, Z, g along the quark line
     "u u~ > z h g": (2, 12, 1),          # the gluon before or after the s-channel Z
     "u d~ > w+ z g": (8, 18, 1),         # 3 + 3 along the two t-channel lines, 2 beside the s-channel W
+    "u u~ > w+ w- g": (7, 36, 1),        # 3 along the t-channel line, 2 beside each s-channel photon and Z
     "u u~ > w+ w- a": (15, 36, 1),       # 3 + 2 + 4 + 4 + 2 (line, W lines, ISR, W emission, quartic)
     "g g > t t~": (3, 16, 2),
     "g g > t t~ h": (8, 16, 2),          # the Higgs on every top line of the three g g > t t~ graphs
