@@ -48,6 +48,7 @@ PROCESSES = [
     ("u u~ > z h g", []),
     ("u d~ > w+ z g", []),
     ("u u~ > w+ w- g", []),
+    ("g g > w+ d u~", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)
