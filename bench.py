@@ -59,9 +59,32 @@ TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (85.43872e6 + 282.851328e6) / 2 ** 
                      ("udx_epvegg", "k_me"): (214.006016e6 + 3.588608e6) / 2 ** 20,
                      ("gg_gggg", "k_me"): (3.478784e6 + 0.07552e6) / 16384}
 
+# Warp instructions issued per accepted point (smsp__inst_executed.sum of the same ncu captures,
+# divided by the points of the launch).  The phase-space kernel mixes integer (Philox), FP32 and
+# control instructions and is bound by instruction issue, so its roofline is also stated against
+# the issue rate.
+WARP_INSTRUCTIONS_PER_POINT = {("udx_epvegg", "k_ps"): 175110311.0 / 2 ** 20,
+                               ("udx_epvegg", "k_me"): 97712128.0 / 2 ** 20}
+
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+SCHEDULERS_PER_SM = 4
 SM_MAX_MHZ = 2070.0
+
+
+def issue_roofline(workload, kernel, ms, points, mhz=SM_MAX_MHZ):
+    """Issue-rate view of a kernel's roofline: warp instructions per second against the SMs' issue
+    ceiling (152 SMs x 4 schedulers x one warp instruction per cycle x clock), or None without a
+    capture for this workload and kernel."""
+    per_point = WARP_INSTRUCTIONS_PER_POINT.get((workload, kernel))
+    if per_point is None or ms <= 0:
+        return None
+    achieved = per_point * points / (ms * 1e-3) / 1e9
+    peak = SM_COUNT * SCHEDULERS_PER_SM * mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G warp instructions/s", "frac": achieved / peak,
+            "instructions_per_point": per_point,
+            "source": "smsp__inst_executed.sum of the ncu capture; peak 152 SMs x 4 schedulers x 1 per cycle "
+                      "x 2070 MHz"}
 
 
 def fp32_alu_peak_tflops(mhz=SM_MAX_MHZ):
@@ -694,7 +717,8 @@ def main():
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                          "flops_per_point": kernels[dom]["flops_per_point"],
                          "flops_source": kernels[dom]["flops_source"],
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                         "issue": issue_roofline(args.workload, dom, kernels[dom]["ms"], n)},
             "kernels": kernels,
             "per_process": table,
             "serving": serving,

@@ -54,3 +54,13 @@ def test_two_gloo_ranks():
     assert t_max == 3.0                              # the slowest rank
     assert value == pytest.approx(2 * (1 << 20) / 3.0e-3)
     assert mc == {"sum_w": 4.5, "sum_w2": 0.75, "n_acc": 2 << 20, "n_try": (2 << 20) + 10}
+
+
+def test_issue_roofline_arithmetic():
+    """The issue-rate roofline: instructions per point x points / time against 152 x 4 x clock."""
+    import bench
+    r = bench.issue_roofline("udx_epvegg", "k_ps", 0.222, 2 ** 20)
+    assert r["peak"] == pytest.approx(152 * 4 * 2.07)
+    assert r["achieved"] == pytest.approx(175110311.0 / 0.222e-3 / 1e9)
+    assert 0.5 < r["frac"] < 0.8
+    assert bench.issue_roofline("uux_epem", "k_ps", 0.1, 65536) is None
