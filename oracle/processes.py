@@ -32,7 +32,7 @@ Functions and their pins (tests/test_oracle_processes.py):
   uux_zh          u u~ > z h     : closed form from the trace, exact per point
   udx_wph         u d~ > w+ h    : closed form from the trace, exact per point
   udx_wpg, uux_zg q q~ > V g     : textbook closed form (t^2 + u^2 + 2 s mV^2)/(t u), exact per point
-  gg_wpdux        g g > w+ d u~  : Ward identity for each gluon, Bose symmetry, boosts
+  gg_wpdux, gg_zuux  g g > w+ d u~, g g > z u u~ : Ward identity for each gluon, Bose symmetry, boosts
   ug_wpd          u g > w+ d     : the same closed form crossed (s <-> u, one fermion: sign -1), exact
   uux_zzg         u u~ > z z g   : Ward identity for the gluon, the soft-gluon limit against C_F times
                    the eikonal factor times u u~ > z z, boosts
@@ -321,14 +321,13 @@ def gg_ttxh(P, par=SMParams(), per_helicity=False, eps_override=None, widths=Tru
 # --------------------------------------------------------------------------
 # g g > W+ d u~  (W plus two jets from two gluons: eight diagrams)
 # --------------------------------------------------------------------------
-def gg_wpdux(P, par=SMParams(), eps_override=None):
-    """g(0) g(1) > W+(2) d(3) u~(4).  The quark line runs from v(p4) (the u~) to ubar(p3) (the d): the
-    two gluons and the W in every order along it (six diagrams, colour t^a t^b or t^b t^a by the order
-    of the gluons), and the s-channel gluon of the two gluons beside the W (two, colour f^{abc} t^c).
-    eps_override = (leg, vector) replaces that gluon's polarisation vector."""
+def _gg_vqqx(P, par, gl, gr, mV, eps_override):
+    """g(0) g(1) > V(2) q(3) q~'(4).  The quark line runs from v(p4) to ubar(p3): the two gluons and
+    the V (coupling i gamma^mu (gl P_L + gr P_R)) in every order along it (six diagrams, colour
+    t^a t^b or t^b t^a by the order of the gluons), and the s-channel gluon of the two gluons beside
+    the V (two, colour f^{abc} t^c).  eps_override = (leg, vector) replaces that gluon's vector."""
     p = [P[:, k] for k in range(5)]
     gs = par.gs
-    gw = par.g / np.sqrt(2.0)
     cAB = _colour_string([0, 1], 2)
     cBA = _colour_string([1, 0], 2)
     cG = _colour_string(["G"], 2, with_f=(0, 1))
@@ -338,11 +337,11 @@ def gg_wpdux(P, par=SMParams(), eps_override=None):
         e1 = polarisation(p[1], h[1])
         if eps_override is not None:
             e0, e1 = (eps_override[1], e1) if eps_override[0] == 0 else (e0, eps_override[1])
-        ew = polarisation(p[2], h[2], mass=par.mW).conj()
+        ev = polarisation(p[2], h[2], mass=mV).conj()
         ubd = bar(u_spinor(p[3], h[3]))
         vu = v_spinor(p[4], h[4])
         ins = {"G0": (vector_insertion(e0, gs, gs), -p[0]), "G1": (vector_insertion(e1, gs, gs), -p[1]),
-               "W": (vector_insertion(ew, gw, 0.0), p[2])}
+               "W": (vector_insertion(ev, gl, gr), p[2])}
         AB, BA = 0.0, 0.0
         for order in itertools.permutations(["G0", "G1", "W"]):
             a = fermion_line(ubd, vu, -p[4], [ins[x] for x in order])
@@ -355,6 +354,17 @@ def gg_wpdux(P, par=SMParams(), eps_override=None):
         AG = fermion_line(ubd, vu, -p[4], [Gs, ins["W"]]) + fermion_line(ubd, vu, -p[4], [ins["W"], Gs])
         tot = tot + colour.colour_sum([AB / 1j, BA / 1j, AG / 1j], [cAB, cBA, cG])
     return tot / (4.0 * 64.0)
+
+
+def gg_wpdux(P, par=SMParams(), eps_override=None):
+    """g g > W+ d u~ (the quark line from the u~ to the d emits the W+)."""
+    return _gg_vqqx(P, par, par.g / np.sqrt(2.0), 0.0, par.mW, eps_override)
+
+
+def gg_zuux(P, par=SMParams(), eps_override=None):
+    """g g > Z u u~."""
+    gl, gr = _z_couplings("u", par)
+    return _gg_vqqx(P, par, gl, gr, par.mZ, eps_override)
 
 
 # --------------------------------------------------------------------------
@@ -1167,6 +1177,7 @@ PROCESSES = {
     "u d~ > w+ z g": udx_wpzg,
     "u u~ > w+ w- g": uux_wpwmg,
     "g g > w+ d u~": gg_wpdux,
+    "g g > z u u~": gg_zuux,
     "u u~ > w+ w- a": uux_wpwma,
     "g g > t t~ h": gg_ttxh,
     "g g > t t~ g": gg_ttxg,

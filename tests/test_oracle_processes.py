@@ -853,21 +853,23 @@ def test_v_pair_plus_gluon_ward_soft_and_boosts(which):
     assert devs[1] < 2e-3 and devs[1] < devs[0] / 5
 
 
-def test_gg_wpdux_ward_bose_and_boosts():
-    """g g > W+ d u~: either gluon's polarisation replaced by its momentum gives zero once the six
+@pytest.mark.parametrize("which", ["w", "z"])
+def test_gg_vqqx_ward_bose_and_boosts(which):
+    """g g > W+ d u~ and g g > Z u u~: either gluon's polarisation replaced by its momentum gives zero once the six
     quark-line orderings and the two s-channel-gluon diagrams are summed; the gluons are
     interchangeable; |M|^2 is Lorentz invariant.  The external quarks are put exactly on shell
     (E = |p|): an external massless spinor of a momentum with p^2 = eps E^2 breaks the identity at
     sqrt(eps), and RAMBO's rescaling leaves eps ~ 1e-15."""
+    fn, mV = (pr.gg_wpdux, PAR.mW) if which == "w" else (pr.gg_zuux, PAR.mZ)
     u = np.random.default_rng(101).uniform(0.01, 0.99, (10, 12))
-    pf, _ = ps.rambo_massive(700.0, [PAR.mW, 0.0, 0.0], u)
+    pf, _ = ps.rambo_massive(700.0, [mV, 0.0, 0.0], u)
     P = np.zeros((10, 5, 4))
     P[:, 0], P[:, 1] = ps.incoming(700.0, 10)
     P[:, 2:] = pf
     for k in (3, 4):
         P[:, k, 0] = np.linalg.norm(P[:, k, 1:], axis=1)
-    ref = pr.gg_wpdux(P, PAR)
+    ref = fn(P, PAR)
     for leg in (0, 1):
-        assert np.all(np.abs(pr.gg_wpdux(P, PAR, eps_override=(leg, P[:, leg].astype(complex)))) <= 1e-20 * ref)
-    assert np.allclose(pr.gg_wpdux(P[:, [1, 0, 2, 3, 4]], PAR), ref, rtol=1e-11)
-    assert np.allclose(pr.gg_wpdux(random_lorentz(P, seed=102), PAR), ref, rtol=1e-10)
+        assert np.all(np.abs(fn(P, PAR, eps_override=(leg, P[:, leg].astype(complex)))) <= 1e-20 * ref)
+    assert np.allclose(fn(P[:, [1, 0, 2, 3, 4]], PAR), ref, rtol=1e-11)
+    assert np.allclose(fn(random_lorentz(P, seed=102), PAR), ref, rtol=1e-10)
