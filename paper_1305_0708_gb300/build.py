@@ -49,6 +49,7 @@ PROCESSES = [
     ("u d~ > w+ z g", []),
     ("u u~ > w+ w- g", []),
     ("g g > w+ d u~", []),
+    ("g g > z u u~", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

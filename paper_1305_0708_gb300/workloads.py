@@ -108,6 +108,11 @@ VARIANTS = {
         cuts=dict(legs=(3, 4), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=1.0,
         describe="g g > W+ d u~ (W plus two jets from two gluons, eight diagrams), massive RAMBO at sqrt(s)=600 "
                  "GeV, pT>20, |eta|<2.5, DeltaR>0.4 on the two quarks, 2^20 accepted points, seed 21"),
+    "gg_zuux": dict(
+        process="g g > z u u~", kind="rambo", sqrt_s=600.0, masses=(0, 0, 91.1876, 0, 0), n=1 << 20, seed=22,
+        cuts=dict(legs=(3, 4), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=1.0,
+        describe="g g > Z u u~ (Z plus two jets from two gluons, eight diagrams), massive RAMBO at sqrt(s)=600 "
+                 "GeV, pT>20, |eta|<2.5, DeltaR>0.4 on the two quarks, 2^20 accepted points, seed 22"),
     "gg_ttx": dict(
         process="g g > t t~", kind="rambo", sqrt_s=800.0, masses=(0, 0, 175.0, 175.0), n=1 << 20, seed=11,
         cuts=None, s_ident=1.0,

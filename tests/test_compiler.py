@@ -29,6 +29,7 @@ CASES = {
     "u d~ > w+ z g": (8, 18, 1),         # 3 + 3 along the two t-channel lines, 2 beside the s-channel W
     "u u~ > w+ w- g": (7, 36, 1),        # 3 along the t-channel line, 2 beside each s-channel photon and Z
     "g g > w+ d u~": (8, 12, 2),         # 3! orders of g, g, W along the quark line, 2 with the s-channel gluon
+    "g g > z u u~": (8, 24, 2),          # the same graphs; both quark chiralities couple to the Z
     "u u~ > w+ w- a": (15, 36, 1),       # 3 + 2 + 4 + 4 + 2 (line, W lines, ISR, W emission, quartic)
     "g g > t t~": (3, 16, 2),
     "g g > t t~ h": (8, 16, 2),          # the Higgs on every top line of the three g g > t t~ graphs

@@ -41,6 +41,7 @@ CASES = {
     "u d~ > w+ z g": (opr.udx_wpzg, 600.0, (80.4, 91.1876, 0.0), (4,)),
     "u u~ > w+ w- g": (opr.uux_wpwmg, 600.0, (80.4, 80.4, 0.0), (4,)),
     "g g > w+ d u~": (opr.gg_wpdux, 600.0, (80.4, 0.0, 0.0), (3, 4)),
+    "g g > z u u~": (opr.gg_zuux, 600.0, (91.1876, 0.0, 0.0), (3, 4)),
 }
 
 
