@@ -58,7 +58,7 @@ template <class R> ME_HD P4<R> neg(P4<R> k) { return P4<R>{-k.e, -k.x, -k.y, -k.
 template <class R> ME_HD R msq(P4<R> k) { return k.e * k.e - k.x * k.x - k.y * k.y - k.z * k.z; }
 
 // ---------------------------------------------------------------------------
-// external wavefunctions (massless fermions, massless/massive vectors, scalars)
+// external wavefunctions (massless and massive fermions, massless/massive vectors, scalars)
 // ---------------------------------------------------------------------------
 // sqrt(E + pz) computed without cancellation for pz < 0; zero only for p along -z.
 template <class R> ME_HD R kplus(P4<R> p) {
