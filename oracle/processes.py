@@ -36,8 +36,8 @@ Functions and their pins (tests/test_oracle_processes.py):
   ug_wpd          u g > w+ d     : the same closed form crossed (s <-> u, one fermion: sign -1), exact
   uux_zzg         u u~ > z z g   : Ward identity for the gluon, the soft-gluon limit against C_F times
                    the eikonal factor times u u~ > z z, boosts
-  uux_zhg, udx_wpzg, uux_wpwmg  u u~ > z h g, u d~ > w+ z g, u u~ > w+ w- g : the same three pins
-                   against u u~ > z h, u d~ > w+ z and u u~ > w+ w-
+  uux_zhg, udx_wphg, udx_wpzg, uux_wpwmg  u u~ > z h g, u d~ > w+ h g, u d~ > w+ z g,
+                   u u~ > w+ w- g : the same three pins against the processes without the gluon
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
@@ -731,6 +731,26 @@ def uux_zhg(P, par=SMParams(), eps_override=None):
     return tot / 36.0
 
 
+def udx_wphg(P, par=SMParams(), eps_override=None):
+    """u(p0) d~(p1) > W+(p2) H(p3) g(p4): the s-channel W of u d~ > W+ H (WWH vertex) with the gluon
+    from the quark line before or after it (two diagrams, colour t^a)."""
+    p = [P[:, k] for k in range(5)]
+    gw = par.g / np.sqrt(2.0)
+    gwwh = par.g * par.mW
+    cT = _colour_string([0], 1)
+    Q = p[2] + p[3]
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ew = polarisation(p[2], h[2], mass=par.mW).conj()
+        eg = polarisation(p[4], h[3]).conj() if eps_override is None else eps_override
+        Y = vector_prop(Q, 1j * gwwh * ew, par.mW, par.wW)
+        A = _with_gluon([(vb, u, p[0], [(vector_insertion(Y, gw, 0.0), Q)])], eg, p[4], par.gs)
+        tot = tot + colour.colour_sum([A / 1j], [cT])
+    return tot / 36.0
+
+
 def udx_wpzg(P, par=SMParams(), eps_override=None):
     """u(p0) d~(p1) > W+(p2) Z(p3) g(p4): the three graphs of u d~ > W+ Z (Z from the u line, Z from
     the d line, s-channel W into the WWZ vertex) with the gluon at every place along the quark line
@@ -1174,6 +1194,7 @@ PROCESSES = {
     "u g > w+ d": ug_wpd,
     "u u~ > z z g": uux_zzg,
     "u u~ > z h g": uux_zhg,
+    "u d~ > w+ h g": udx_wphg,
     "u d~ > w+ z g": udx_wpzg,
     "u u~ > w+ w- g": uux_wpwmg,
     "g g > w+ d u~": gg_wpdux,

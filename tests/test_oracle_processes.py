@@ -823,13 +823,15 @@ def _soft_emission_points(base, w, nhat, m2, m3):
     return P
 
 
-@pytest.mark.parametrize("which", ["zh", "wz", "ww"])
+@pytest.mark.parametrize("which", ["zh", "wh", "wz", "ww"])
 def test_v_pair_plus_gluon_ward_soft_and_boosts(which):
-    """u u~ > Z H g, u d~ > W+ Z g and u u~ > W+ W- g: the gluon's Ward identity; as the gluon's energy w goes to zero
+    """u u~ > Z H g, u d~ > W+ H g, u d~ > W+ Z g and u u~ > W+ W- g: the gluon's Ward identity; as the gluon's energy w goes to zero
     |M|^2 tends to gs^2 C_F 2 (p_q.p_q~) / ((p_q.k)(p_q~.k)) times |M|^2 without the gluon, the
     deviation falling in proportion to w; Lorentz invariance."""
     if which == "zh":
         fn, base_fn, m2, m3 = pr.uux_zhg, pr.uux_zh, PAR.mZ, PAR.mH
+    elif which == "wh":
+        fn, base_fn, m2, m3 = pr.udx_wphg, pr.udx_wph, PAR.mW, PAR.mH
     elif which == "wz":
         fn, base_fn, m2, m3 = pr.udx_wpzg, pr.udx_wpz, PAR.mW, PAR.mZ
     else:
