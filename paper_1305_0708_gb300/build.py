@@ -46,6 +46,7 @@ PROCESSES = [
     ("u u~ > z z g", []),
     ("g g > t t~ g", []),
     ("u u~ > z h g", []),
+    ("u d~ > w+ h g", []),
     ("u d~ > w+ z g", []),
     ("u u~ > w+ w- g", []),
     ("g g > w+ d u~", []),

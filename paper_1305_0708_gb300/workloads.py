@@ -93,6 +93,11 @@ VARIANTS = {
         cuts=dict(legs=(4,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
         describe="u u~ > Z H g (Higgs-strahlung plus one jet), massive RAMBO at sqrt(s)=600 GeV, gluon pT>20, "
                  "|eta|<2.5, 2^20 accepted points, seed 18"),
+    "udx_wphg": dict(
+        process="u d~ > w+ h g", kind="rambo", sqrt_s=600.0, masses=(0, 0, 80.4, 125.0, 0), n=1 << 20, seed=23,
+        cuts=dict(legs=(4,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="u d~ > W+ H g (W Higgs-strahlung plus one jet), massive RAMBO at sqrt(s)=600 GeV, gluon pT>20, "
+                 "|eta|<2.5, 2^20 accepted points, seed 23"),
     "udx_wpzg": dict(
         process="u d~ > w+ z g", kind="rambo", sqrt_s=600.0, masses=(0, 0, 80.4, 91.1876, 0), n=1 << 20, seed=19,
         cuts=dict(legs=(4,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,

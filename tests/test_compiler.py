@@ -26,6 +26,7 @@ CASES = {
     "u u~ > z g": (2, 12, 1),
     "u u~ > z z g": (6, 36, 1),          # 3! orders of Z, Z, g along the quark line
     "u u~ > z h g": (2, 12, 1),          # the gluon before or after the s-channel Z
+    "u d~ > w+ h g": (2, 6, 1),          # the gluon before or after the s-channel W
     "u d~ > w+ z g": (8, 18, 1),         # 3 + 3 along the two t-channel lines, 2 beside the s-channel W
     "u u~ > w+ w- g": (7, 36, 1),        # 3 along the t-channel line, 2 beside each s-channel photon and Z
     "g g > w+ d u~": (8, 12, 2),         # 3! orders of g, g, W along the quark line, 2 with the s-channel gluon

@@ -38,6 +38,7 @@ CASES = {
     "u s > d c h h": (opr.us_dchh, 1000.0, (0.0, 0.0, 125.0, 125.0), ()),
     "u g > w+ d": (opr.ug_wpd, 500.0, (80.4, 0.0), (3,)),
     "u u~ > z h g": (opr.uux_zhg, 600.0, (91.1876, 125.0, 0.0), (4,)),
+    "u d~ > w+ h g": (opr.udx_wphg, 600.0, (80.4, 125.0, 0.0), (4,)),
     "u d~ > w+ z g": (opr.udx_wpzg, 600.0, (80.4, 91.1876, 0.0), (4,)),
     "u u~ > w+ w- g": (opr.uux_wpwmg, 600.0, (80.4, 80.4, 0.0), (4,)),
     "g g > w+ d u~": (opr.gg_wpdux, 600.0, (80.4, 0.0, 0.0), (3, 4)),
