@@ -19,6 +19,8 @@ Functions and their pins (tests/test_oracle_processes.py):
                    built from blocks pinned by the two cases above and q q~ > g g
   uux_gg          u u~ > g g     : textbook closed form, exact per point
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
+  uux_ttx         u u~ > t t~    : textbook closed forms of the gluon and the photon exchange (massive
+                   final quarks), exact per point; no gluon-electroweak interference; boosts
   hh_hh           h h > h h      : closed form from the Higgs potential, exact per point
   gg_ttxg         g g > t t~ g   : Ward identity for each of the three gluons (zero top width), Bose
                    symmetry of the incoming gluons, boosts
@@ -365,6 +367,36 @@ def gg_zuux(P, par=SMParams(), eps_override=None):
     """g g > Z u u~."""
     gl, gr = _z_couplings("u", par)
     return _gg_vqqx(P, par, gl, gr, par.mZ, eps_override)
+
+
+# --------------------------------------------------------------------------
+# u u~ > t t~  (s-channel gluon, photon and Z)
+# --------------------------------------------------------------------------
+def uux_ttx(P, par=SMParams(), bosons=("g", "a", "z")):
+    """u(p0) u~(p1) > t(p2) t~(p3) through an s-channel gluon, photon or Z between the light-quark
+    current and the top current.  Colour: t^a_{i1 i0} t^a_{i2 i3} for the gluon, delta_{i1 i0}
+    delta_{i2 i3} for the photon and the Z (axes i0 u, i1 u~, i2 t, i3 t~).  `bosons` selects the
+    exchanged bosons (the pins take them one at a time)."""
+    p = [P[:, k] for k in range(4)]
+    d = np.eye(3, dtype=complex)
+    tens = {"g": np.einsum("aji,akl->ijkl", _T, _T), "ew": np.einsum("ji,kl->ijkl", d, d)}
+    q = p[0] + p[1]
+    spec = {"g": ((par.gs, par.gs), (par.gs, par.gs), 0.0, 0.0, "g"),
+            "a": ((_a_coupling("u", par),) * 2, (_a_coupling("t", par),) * 2, 0.0, 0.0, "ew"),
+            "z": (_z_couplings("u", par), _z_couplings("t", par), par.mZ, par.wZ, "ew")}
+    tot = 0.0
+    for h in itertools.product(HEL_F, repeat=4):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ubt = bar(u_spinor(p[2], h[2]))
+        vt = v_spinor(p[3], h[3])
+        amps, cols = [], []
+        for b in bosons:
+            cq, ct, m, w, c = spec[b]
+            amps.append(mdot(vector_prop(q, ffv_current(vb, u, *cq), m, w), ffv_current(ubt, vt, *ct)) / 1j)
+            cols.append(tens[c])
+        tot = tot + colour.colour_sum(amps, cols)
+    return tot / 36.0
 
 
 # --------------------------------------------------------------------------
@@ -1201,6 +1233,7 @@ PROCESSES = {
     "g g > z u u~": gg_zuux,
     "u u~ > w+ w- a": uux_wpwma,
     "g g > t t~ h": gg_ttxh,
+    "u u~ > t t~": uux_ttx,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,

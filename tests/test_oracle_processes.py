@@ -875,3 +875,22 @@ def test_gg_vqqx_ward_bose_and_boosts(which):
         assert np.all(np.abs(fn(P, PAR, eps_override=(leg, P[:, leg].astype(complex)))) <= 1e-20 * ref)
     assert np.allclose(fn(P[:, [1, 0, 2, 3, 4]], PAR), ref, rtol=1e-11)
     assert np.allclose(fn(random_lorentz(P, seed=102), PAR), ref, rtol=1e-10)
+
+
+def test_uux_ttx_closed_forms():
+    """u u~ > t t~: with F = (mt^2 - t)^2 + (mt^2 - u)^2 + 2 mt^2 s, the gluon exchange alone gives
+    (4/9) gs^4 F / s^2 and the photon exchange alone 2 e^4 Qu^2 Qt^2 F / s^2 (colour factors 2 and
+    9 over 36, the massive-final-state QED trace); the gluon does not interfere with the photon or
+    the Z (colour orthogonality); |M|^2 is Lorentz invariant."""
+    mt = PAR.mt
+    P = two_to_two(900.0, 40, mt, mt, seed=111)
+    s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
+    t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
+    u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    F = (mt * mt - t) ** 2 + (mt * mt - u) ** 2 + 2 * mt * mt * s
+    assert np.allclose(pr.uux_ttx(P, PAR, bosons=("g",)), (4.0 / 9.0) * PAR.gs ** 4 * F / s ** 2, rtol=1e-12)
+    qa = PAR.e ** 2 * CHARGE["u"] * CHARGE["t"]
+    assert np.allclose(pr.uux_ttx(P, PAR, bosons=("a",)), 2 * qa ** 2 * F / s ** 2, rtol=1e-12)
+    full = pr.uux_ttx(P, PAR)
+    assert np.allclose(full, pr.uux_ttx(P, PAR, bosons=("g",)) + pr.uux_ttx(P, PAR, bosons=("a", "z")), rtol=1e-12)
+    assert np.allclose(pr.uux_ttx(random_lorentz(P, seed=112), PAR), full, rtol=1e-10)
