@@ -38,6 +38,7 @@ PROCESSES = [
     ("u d~ > w+ h", []),
     ("u u~ > w+ w- a", []),
     ("g g > t t~", []),
+    ("u u~ > t t~", []),
     ("g g > t t~ h", []),
     ("h h > h h", []),
     ("u d~ > w+ g", []),

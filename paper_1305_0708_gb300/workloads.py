@@ -129,6 +129,11 @@ VARIANTS = {
         describe="g g > t t~ g (top pair plus one jet: sixteen diagrams with the three- and four-gluon "
                  "vertices), massive RAMBO at sqrt(s)=1 TeV, gluon pT>20, |eta|<2.5, 2^20 accepted points, "
                  "seed 17"),
+    "uux_ttx": dict(
+        process="u u~ > t t~", kind="rambo", sqrt_s=800.0, masses=(0, 0, 175.0, 175.0), n=1 << 20, seed=24,
+        cuts=None, s_ident=1.0,
+        describe="u u~ > t t~ with on-shell tops (s-channel gluon, photon and Z), massive RAMBO at sqrt(s)=800 "
+                 "GeV, 2^20 points, seed 24"),
     "gg_ttxh": dict(
         process="g g > t t~ h", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 175.0, 175.0, 125.0), n=1 << 20,
         seed=12, cuts=None, s_ident=1.0,

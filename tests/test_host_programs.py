@@ -43,6 +43,7 @@ CASES = {
     "u u~ > w+ w- g": (opr.uux_wpwmg, 600.0, (80.4, 80.4, 0.0), (4,)),
     "g g > w+ d u~": (opr.gg_wpdux, 600.0, (80.4, 0.0, 0.0), (3, 4)),
     "g g > z u u~": (opr.gg_zuux, 600.0, (91.1876, 0.0, 0.0), (3, 4)),
+    "u u~ > t t~": (opr.uux_ttx, 800.0, (175.0, 175.0), ()),
 }
 
 
