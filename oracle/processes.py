@@ -21,6 +21,7 @@ Functions and their pins (tests/test_oracle_processes.py):
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
   uux_ttx         u u~ > t t~    : textbook closed forms of the gluon and the photon exchange (massive
                    final quarks), exact per point; no gluon-electroweak interference; boosts
+  uux_ttxg        u u~ > t t~ g  : Ward identity for the gluon (zero top width), boosts
   hh_hh           h h > h h      : closed form from the Higgs potential, exact per point
   gg_ttxg         g g > t t~ g   : Ward identity for each of the three gluons (zero top width), Bose
                    symmetry of the incoming gluons, boosts
@@ -395,6 +396,65 @@ def uux_ttx(P, par=SMParams(), bosons=("g", "a", "z")):
             cq, ct, m, w, c = spec[b]
             amps.append(mdot(vector_prop(q, ffv_current(vb, u, *cq), m, w), ffv_current(ubt, vt, *ct)) / 1j)
             cols.append(tens[c])
+        tot = tot + colour.colour_sum(amps, cols)
+    return tot / 36.0
+
+
+def uux_ttxg(P, par=SMParams(), eps_override=None, widths=True):
+    """u(p0) u~(p1) > t(p2) t~(p3) g(p4): the s-channel gluon, photon or Z of u u~ > t t~ with the
+    gluon emitted from the light-quark line (two places) or from the top line (two places), and the
+    s-channel gluon's three-gluon vertex with the emitted gluon (13 diagrams).  Colour tensors over
+    (i0 u, i1 u~, i2 t, i3 t~, a): along the light line the product of generators runs from u to u~,
+    along the top line from t~ to t.  Internal tops carry the width wt unless widths=False."""
+    p = [P[:, k] for k in range(5)]
+    gs, mt = par.gs, par.mt
+    wt = par.wt if widths else 0.0
+    T, F = _T, _F
+    d = np.eye(3, dtype=complex)
+    cpl = {"g": ((gs, gs), (gs, gs), 0.0, 0.0), "a": ((_a_coupling("u", par),) * 2, (_a_coupling("t", par),) * 2, 0.0, 0.0),
+           "z": (_z_couplings("u", par), _z_couplings("t", par), par.mZ, par.wZ)}
+    # colour tensors
+    c_light = {"GV": np.einsum("cjk,aki,clm->ijlma", T, T, T),    # (t^c t^a)_{i1 i0} t^c_{i2 i3}
+               "VG": np.einsum("ajk,cki,clm->ijlma", T, T, T)}    # (t^a t^c)_{i1 i0} t^c_{i2 i3}
+    c_top = {"GV": np.einsum("cji,clk,akm->ijlma", T, T, T),      # t^c_{i1 i0} (t^c t^a)_{i2 i3}
+             "VG": np.einsum("cji,alk,ckm->ijlma", T, T, T)}      # t^c_{i1 i0} (t^a t^c)_{i2 i3}
+    c_ew_light = np.einsum("aji,lm->ijlma", T, d)                 # t^a_{i1 i0} delta_{i2 i3}
+    c_ew_top = np.einsum("ji,alm->ijlma", d, T)                   # delta_{i1 i0} t^a_{i2 i3}
+    c_ggg = np.einsum("cji,cae,elm->ijlma", T, F, T)              # t^c_{i1 i0} f^{c a e} t^e_{i2 i3}
+    q = p[0] + p[1]
+    Q = p[2] + p[3]
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_F, HEL_F, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ubt = bar(u_spinor(p[2], h[2]))
+        vt = v_spinor(p[3], h[3])
+        eg = polarisation(p[4], h[4]).conj() if eps_override is None else eps_override
+        amps, cols = [], []
+        for b in ("g", "a", "z"):
+            cu, ct, m, w = cpl[b]
+            # gluon from the light line: the boson carries Q into the top current
+            Yt = vector_prop(Q, ffv_current(ubt, vt, *ct), m, w)
+            Vu = (vector_insertion(Yt, *cu), Q)
+            Gu = (vector_insertion(eg, gs, gs), p[4])
+            a_gv = fermion_line(vb, u, p[0], [Gu, Vu]) / 1j
+            a_vg = fermion_line(vb, u, p[0], [Vu, Gu]) / 1j
+            # gluon from the top line: the boson carries q out of the light current into the top line
+            Yu = vector_prop(q, ffv_current(vb, u, *cu), m, w)
+            Vt = (vector_insertion(Yu, *ct), -q)
+            a_tgv = fermion_line(ubt, vt, -p[3], [Gu, Vt], mt, wt) / 1j
+            a_tvg = fermion_line(ubt, vt, -p[3], [Vt, Gu], mt, wt) / 1j
+            if b == "g":
+                amps += [a_gv, a_vg, a_tgv, a_tvg]
+                cols += [c_light["GV"], c_light["VG"], c_top["GV"], c_top["VG"]]
+            else:
+                amps += [a_gv + a_vg, a_tgv + a_tvg]
+                cols += [c_ew_light, c_ew_top]
+        # the s-channel gluon emits the gluon through the three-gluon vertex
+        Ju = vector_prop(q, ffv_current(vb, u, gs, gs))
+        X = vvv_out(Ju, q, eg, -p[4], -Q, gs)
+        amps.append(fermion_line(ubt, vt, -p[3], [(vector_insertion(vector_prop(Q, X), gs, gs), -Q)], mt, wt) / 1j)
+        cols.append(c_ggg)
         tot = tot + colour.colour_sum(amps, cols)
     return tot / 36.0
 
@@ -1234,6 +1294,7 @@ PROCESSES = {
     "u u~ > w+ w- a": uux_wpwma,
     "g g > t t~ h": gg_ttxh,
     "u u~ > t t~": uux_ttx,
+    "u u~ > t t~ g": uux_ttxg,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,

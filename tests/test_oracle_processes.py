@@ -894,3 +894,19 @@ def test_uux_ttx_closed_forms():
     full = pr.uux_ttx(P, PAR)
     assert np.allclose(full, pr.uux_ttx(P, PAR, bosons=("g",)) + pr.uux_ttx(P, PAR, bosons=("a", "z")), rtol=1e-12)
     assert np.allclose(pr.uux_ttx(random_lorentz(P, seed=112), PAR), full, rtol=1e-10)
+
+
+def test_uux_ttxg_ward_and_boosts():
+    """u u~ > t t~ g: the gluon's polarisation replaced by its momentum gives zero (zero top width)
+    once the thirteen diagrams are summed; |M|^2 is Lorentz invariant."""
+    u = np.random.default_rng(121).uniform(0.01, 0.99, (8, 12))
+    pf, _ = ps.rambo_massive(1000.0, [PAR.mt, PAR.mt, 0.0], u)
+    P = np.zeros((8, 5, 4))
+    P[:, 0], P[:, 1] = ps.incoming(1000.0, 8)
+    P[:, 2:] = pf
+    P[:, 4, 0] = np.linalg.norm(P[:, 4, 1:], axis=1)
+    ref = pr.uux_ttxg(P, PAR, widths=False)
+    ward = pr.uux_ttxg(P, PAR, widths=False, eps_override=P[:, 4].astype(complex))
+    assert np.all(np.abs(ward) <= 1e-20 * ref)
+    full = pr.uux_ttxg(P, PAR)
+    assert np.allclose(pr.uux_ttxg(random_lorentz(P, seed=122), PAR), full, rtol=1e-10)
