@@ -39,6 +39,7 @@ PROCESSES = [
     ("u u~ > w+ w- a", []),
     ("g g > t t~", []),
     ("u u~ > t t~", []),
+    ("u u~ > t t~ g", []),
     ("g g > t t~ h", []),
     ("h h > h h", []),
     ("u d~ > w+ g", []),

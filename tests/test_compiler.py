@@ -34,6 +34,7 @@ CASES = {
     "u u~ > w+ w- a": (15, 36, 1),       # 3 + 2 + 4 + 4 + 2 (line, W lines, ISR, W emission, quartic)
     "g g > t t~": (3, 16, 2),
     "u u~ > t t~": (3, 8, 2),            # s-channel g, photon, Z; opposite light-quark helicities
+    "u u~ > t t~ g": (13, 16, 4),        # (2 + 2) emissions x (g, photon, Z) + the three-gluon vertex
     "g g > t t~ h": (8, 16, 2),          # the Higgs on every top line of the three g g > t t~ graphs
     "g g > t t~ g": (18, 32, 6),         # 6 + 6 + 3 + one four-gluon graph with three colour structures
     "u u > u u": (6, 6, 2),              # g, photon, Z in the t and u channels; chirality-conserving helicities

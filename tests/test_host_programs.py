@@ -44,6 +44,7 @@ CASES = {
     "g g > w+ d u~": (opr.gg_wpdux, 600.0, (80.4, 0.0, 0.0), (3, 4)),
     "g g > z u u~": (opr.gg_zuux, 600.0, (91.1876, 0.0, 0.0), (3, 4)),
     "u u~ > t t~": (opr.uux_ttx, 800.0, (175.0, 175.0), ()),
+    "u u~ > t t~ g": (opr.uux_ttxg, 1000.0, (175.0, 175.0, 0.0), (4,)),
 }
 
 
