@@ -49,6 +49,7 @@ Functions and their pins (tests/test_oracle_processes.py):
   uux_wpwma       u u~ > w+ w- a : the photon's Ward identity with zero W and Z widths (the
                    fifteen diagrams cancel only with the quartic WWAA and WWAZ vertices),
                    the soft-photon limit against the eikonal factor times u u~ > w+ w-, boosts
+  us_dch          u s > d c h    (WW fusion): closed form from the V-A traces, exact per point
   us_dchh         u s > d c h h  (WW fusion): Higgs-exchange symmetry, boosts;
                    its W current is pinned by u d~ > e+ ve, its WWH/WWHH/HHH
                    couplings and diagram set by the gauge cancellation of the
@@ -689,6 +690,23 @@ def us_dchh(P, par=SMParams(), per_helicity=False):
     return (avg, ph) if per_helicity else avg
 
 
+def us_dch(P, par=SMParams()):
+    """u(p0) s(p1) > d(p2) c(p3) H(p4) by W+ W- fusion: the two quark currents, each into its t-channel
+    W propagator, meet at the WWH vertex (one diagram; no Z fusion for these flavours)."""
+    p = [P[:, k] for k in range(5)]
+    gw = par.g / np.sqrt(2.0)
+    gwwh = par.g * par.mW
+    q1 = p[0] - p[2]
+    q2 = p[1] - p[3]
+    tot = 0.0
+    for h in itertools.product(HEL_F, repeat=4):
+        J1 = ffv_current(bar(u_spinor(p[2], h[2])), u_spinor(p[0], h[0]), gw, 0.0)
+        J2 = ffv_current(bar(u_spinor(p[3], h[3])), u_spinor(p[1], h[1]), gw, 0.0)
+        M = (1j * gwwh * mdot(vector_prop(q1, J1, par.mW, par.wW), vector_prop(q2, J2, par.mW, par.wW))) / 1j
+        tot = tot + 9.0 * np.abs(M) ** 2
+    return tot / 36.0
+
+
 # --------------------------------------------------------------------------
 # W+ W- > h h with on-shell external W bosons (gauge-cancellation pin of the
 # WWH / WWHH / HHH couplings used by u s > d c h h)
@@ -1295,6 +1313,7 @@ PROCESSES = {
     "g g > t t~ h": gg_ttxh,
     "u u~ > t t~": uux_ttx,
     "u u~ > t t~ g": uux_ttxg,
+    "u s > d c h": us_dch,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,

@@ -910,3 +910,25 @@ def test_uux_ttxg_ward_and_boosts():
     assert np.all(np.abs(ward) <= 1e-20 * ref)
     full = pr.uux_ttxg(P, PAR)
     assert np.allclose(pr.uux_ttxg(random_lorentz(P, seed=122), PAR), full, rtol=1e-10)
+
+
+def test_us_dch_closed_form():
+    """u s > d c H through W+ W- fusion: the two left-handed currents give
+    sum_spins |[d gamma^mu P_L u][c gamma_mu P_L s]|^2 = 16 (p_u.p_s)(p_d.p_c) (the V-A trace of muon
+    decay with P_L = (1 - gamma5)/2), so |M|^2 = (9/36) gWWH^2 gW^4 16 (p_u.p_s)(p_d.p_c) /
+    (|q1^2 - mW^2 + i mW wW|^2 |q2^2 - mW^2 + i mW wW|^2), q1 = p_u - p_d, q2 = p_s - p_c (the
+    propagators' q q / mW^2 terms vanish on the conserved massless currents)."""
+    u = np.random.default_rng(131).uniform(0.01, 0.99, (30, 12))
+    pf, _ = ps.rambo_massive(1000.0, [0.0, 0.0, PAR.mH], u)
+    P = np.zeros((30, 5, 4))
+    P[:, 0], P[:, 1] = ps.incoming(1000.0, 30)
+    P[:, 2:] = pf
+    for k in (2, 3):
+        P[:, k, 0] = np.linalg.norm(P[:, k, 1:], axis=1)
+    gw2 = PAR.g ** 2 / 2
+    q1 = P[:, 0] - P[:, 2]
+    q2 = P[:, 1] - P[:, 3]
+    den = lambda q: (mdot(q, q) - PAR.mW ** 2) ** 2 + (PAR.mW * PAR.wW) ** 2
+    want = (9.0 / 36.0) * (PAR.g * PAR.mW) ** 2 * gw2 ** 2 * 16 * mdot(P[:, 0], P[:, 1]) * mdot(P[:, 2], P[:, 3]) \
+        / (den(q1) * den(q2))
+    assert np.allclose(pr.us_dch(P, PAR), want, rtol=1e-10)
