@@ -221,7 +221,8 @@ def oracle_step(w, events):
           "g g > t t~ h": opr.gg_ttxh, "u d~ > w+ g": opr.udx_wpg, "u u~ > z g": opr.uux_zg,
           "u g > w+ d": opr.ug_wpd, "u u~ > z z g": opr.uux_zzg, "g g > t t~ g": opr.gg_ttxg,
           "u u~ > z h g": opr.uux_zhg, "u d~ > w+ z g": opr.udx_wpzg, "u d~ > w+ h g": opr.udx_wphg,
-          "u u~ > w+ w- g": opr.uux_wpwmg, "u u~ > t t~": opr.uux_ttx, "u u~ > t t~ g": opr.uux_ttxg, "g g > w+ d u~": opr.gg_wpdux,
+          "u u~ > w+ w- g": opr.uux_wpwmg, "u u~ > t t~": opr.uux_ttx, "u u~ > t t~ g": opr.uux_ttxg,
+          "u s > d c h": opr.us_dch, "g g > w+ d u~": opr.gg_wpdux,
           "g g > z u u~": opr.gg_zuux}[w["process"]]
     par = SMParams()
     P, W, S, T = oxs.generate(oracle_kin(w), par, w["seed"], events)

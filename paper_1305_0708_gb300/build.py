@@ -27,6 +27,7 @@ PROCESSES = [
     ("u d~ > e+ ve g g", []),
     ("g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))", ["g g > t t~ > b e+ ve b~ e- ve~"]),
     ("u s > d c h h", []),
+    ("u s > d c h", []),
     ("u d~ > e+ ve", []),
     ("u u~ > g g", []),
     ("g g > g g", []),

@@ -139,6 +139,10 @@ VARIANTS = {
         cuts=dict(legs=(4,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
         describe="u u~ > t t~ g (top pair plus one jet from q q~: thirteen diagrams with gluon, photon and Z "
                  "exchange), massive RAMBO at sqrt(s)=1 TeV, gluon pT>20, |eta|<2.5, 2^20 accepted points, seed 25"),
+    "us_dch": dict(
+        process="u s > d c h", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 0, 0, 125.0), n=1 << 20, seed=26,
+        cuts=None, s_ident=1.0,
+        describe="u s > d c H (W+ W- fusion, one diagram), massive RAMBO at sqrt(s)=1 TeV, 2^20 points, seed 26"),
     "gg_ttxh": dict(
         process="g g > t t~ h", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 175.0, 175.0, 125.0), n=1 << 20,
         seed=12, cuts=None, s_ident=1.0,

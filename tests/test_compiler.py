@@ -39,6 +39,7 @@ CASES = {
     "g g > t t~ g": (18, 32, 6),         # 6 + 6 + 3 + one four-gluon graph with three colour structures
     "u u > u u": (6, 6, 2),              # g, photon, Z in the t and u channels; chirality-conserving helicities
     "h h > h h": (4, 1, 1),              # contact plus s, t, u exchange
+    "u s > d c h": (1, 1, 1),            # W+ W- fusion; all four quarks left-handed
 }
 
 

@@ -36,6 +36,7 @@ CASES = {
     "g g > t t~ g": (opr.gg_ttxg, 1000.0, (175.0, 175.0, 0.0), (4,)),
     "u u~ > z z g": (opr.uux_zzg, 500.0, (91.1876, 91.1876, 0.0), (4,)),
     "u s > d c h h": (opr.us_dchh, 1000.0, (0.0, 0.0, 125.0, 125.0), ()),
+    "u s > d c h": (opr.us_dch, 1000.0, (0.0, 0.0, 125.0), ()),
     "u g > w+ d": (opr.ug_wpd, 500.0, (80.4, 0.0), (3,)),
     "u u~ > z h g": (opr.uux_zhg, 600.0, (91.1876, 125.0, 0.0), (4,)),
     "u d~ > w+ h g": (opr.udx_wphg, 600.0, (80.4, 125.0, 0.0), (4,)),
