@@ -301,72 +301,75 @@ def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
     peak = fp32_alu_peak_tflops()
     table = {}
     for key, w in list(WORKLOADS.items()) + list(VARIANTS.items()):
-        n = w["n"]
-        kin = B.make_kin(**kin_args(w))
-        row = {"points": n}
-        for prec, name in ((B.ME_MIXED, "mixed"), (B.ME_FP64, "fp64")):
-            h = B.me_create(w["process"], None, prec)
-            slow = prec == B.ME_FP64 and key == "gg_gggg"
-            nw, ns = (1, 2) if slow else (warmup, steps)
-            acc_dev = torch.zeros(4, dtype=torch.float64, device=dev)
-            for s_ in range(nw):
-                B.xsec_step_async(h, w["seed"], offset0 + s_ * n, n, kin, acc_dev, stream)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ns)]
-            for s_ in range(ns):
-                flush.zero_()
-                ev[s_][0].record(stream)
-                B.xsec_step_async(h, w["seed"], offset0 + (nw + s_) * n, n, kin, acc_dev, stream)
-                ev[s_][1].record(stream)
-            torch.cuda.synchronize(dev)
-            ms = sum(a.elapsed_time(b) for a, b in ev) / ns
-            # per-kernel device time on further steps of the same work
-            nt = 1 if slow else ns
-            B.me_step_timing(h, 1)
-            for s_ in range(nt):
-                flush.zero_()
-                B.xsec_step(h, w["seed"], offset0 + (nw + ns + s_) * n, n, kin, stream, B.me_xsec_acc())
-            t_ps, t_me = B.me_step_timing(h, 0)
-            ns_t = nt
-            info = B.me_info(h)
-            fl = (EXECUTED_FLOPS_PER_POINT.get((key, "k_me"), info.flops_amp) if prec == B.ME_MIXED
-                  else info.flops_fp64)
-            row[name] = {"evals_per_s": n / (ms * 1e-3), "ms_per_step": ms, "k_me_ms": t_me / ns_t,
-                         "k_me_tflops": fl * n / (t_me / ns_t * 1e-3) / 1e12}
-            if prec == B.ME_MIXED:
-                row[name]["k_me_frac_fp32_peak"] = row[name]["k_me_tflops"] / peak
-            else:
-                # FP64 momenta and |M|^2 of one step, then the mixed me_eval on the same momenta
-                mom = torch.empty(info.n_ext * 4 * n, dtype=torch.float64, device=dev)
-                m64 = torch.empty(n, dtype=torch.float64, device=dev)
-                B.xsec_step(h, w["seed"], offset0, n, kin, stream, B.me_xsec_acc(), m64, mom)
-                hm = B.me_create(w["process"], None, B.ME_MIXED)
-                mmx = torch.empty(n, dtype=torch.float64, device=dev)
-                B.me_eval(hm, mom, n, mmx, stream)
+        try:
+            n = w["n"]
+            kin = B.make_kin(**kin_args(w))
+            row = {"points": n}
+            for prec, name in ((B.ME_MIXED, "mixed"), (B.ME_FP64, "fp64")):
+                h = B.me_create(w["process"], None, prec)
+                slow = prec == B.ME_FP64 and key == "gg_gggg"
+                nw, ns = (1, 2) if slow else (warmup, steps)
+                acc_dev = torch.zeros(4, dtype=torch.float64, device=dev)
+                for s_ in range(nw):
+                    B.xsec_step_async(h, w["seed"], offset0 + s_ * n, n, kin, acc_dev, stream)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ns)]
+                for s_ in range(ns):
+                    flush.zero_()
+                    ev[s_][0].record(stream)
+                    B.xsec_step_async(h, w["seed"], offset0 + (nw + s_) * n, n, kin, acc_dev, stream)
+                    ev[s_][1].record(stream)
                 torch.cuda.synchronize(dev)
-                B.me_destroy(hm)
-                ok = m64 > 0
-                rel = ((mmx[ok] - m64[ok]).abs() / m64[ok]).double()
-                row["mixed_rel_err"] = {"median": float(rel.median().item()), "max": float(rel.max().item()),
-                                        "p99_99": float(torch.quantile(rel.float().cpu(), 0.9999).item()),
-                                        "frac_above_1e-3": float((rel > 1e-3).double().mean().item()),
-                                        "sum_me2": float(((mmx[ok].sum() - m64[ok].sum()) / m64[ok].sum()).abs()),
-                                        "points": int(ok.sum().item())}
-                # conditioning of the points above 1e-3: how far the FP64 program itself moves when
-                # its input momenta are rounded to FP32 (what any FP32-wavefunction evaluation sees)
-                bad = torch.nonzero(ok & ((mmx - m64).abs() > 1e-3 * m64.abs())).flatten()[:64]
-                if bad.numel():
-                    nb = int(bad.numel())
-                    mb = mom.view(info.n_ext * 4, n)[:, bad].float().double().contiguous()
-                    o64 = torch.empty(nb, dtype=torch.float64, device=dev)
-                    B.me_eval(h, mb, nb, o64, stream)
+                ms = sum(a.elapsed_time(b) for a, b in ev) / ns
+                # per-kernel device time on further steps of the same work
+                nt = 1 if slow else ns
+                B.me_step_timing(h, 1)
+                for s_ in range(nt):
+                    flush.zero_()
+                    B.xsec_step(h, w["seed"], offset0 + (nw + ns + s_) * n, n, kin, stream, B.me_xsec_acc())
+                t_ps, t_me = B.me_step_timing(h, 0)
+                ns_t = nt
+                info = B.me_info(h)
+                fl = (EXECUTED_FLOPS_PER_POINT.get((key, "k_me"), info.flops_amp) if prec == B.ME_MIXED
+                      else info.flops_fp64)
+                row[name] = {"evals_per_s": n / (ms * 1e-3), "ms_per_step": ms, "k_me_ms": t_me / ns_t,
+                             "k_me_tflops": fl * n / (t_me / ns_t * 1e-3) / 1e12}
+                if prec == B.ME_MIXED:
+                    row[name]["k_me_frac_fp32_peak"] = row[name]["k_me_tflops"] / peak
+                else:
+                    # FP64 momenta and |M|^2 of one step, then the mixed me_eval on the same momenta
+                    mom = torch.empty(info.n_ext * 4 * n, dtype=torch.float64, device=dev)
+                    m64 = torch.empty(n, dtype=torch.float64, device=dev)
+                    B.xsec_step(h, w["seed"], offset0, n, kin, stream, B.me_xsec_acc(), m64, mom)
+                    hm = B.me_create(w["process"], None, B.ME_MIXED)
+                    mmx = torch.empty(n, dtype=torch.float64, device=dev)
+                    B.me_eval(hm, mom, n, mmx, stream)
                     torch.cuda.synchronize(dev)
-                    shift = ((o64 - m64[bad]).abs() / m64[bad]).cpu().tolist()
-                    err = ((mmx[bad] - m64[bad]).abs() / m64[bad]).cpu().tolist()
-                    row["mixed_rel_err"]["above_1e-3"] = [{"mixed_err": e_, "fp64_shift_at_fp32_inputs": s_}
-                                                         for e_, s_ in zip(err, shift)]
-            B.me_destroy(h)
-        row["mixed_over_fp64"] = row["mixed"]["evals_per_s"] / row["fp64"]["evals_per_s"]
-        table[key] = row
+                    B.me_destroy(hm)
+                    ok = m64 > 0
+                    rel = ((mmx[ok] - m64[ok]).abs() / m64[ok]).double()
+                    row["mixed_rel_err"] = {"median": float(rel.median().item()), "max": float(rel.max().item()),
+                                            "p99_99": float(torch.quantile(rel.float().cpu(), 0.9999).item()),
+                                            "frac_above_1e-3": float((rel > 1e-3).double().mean().item()),
+                                            "sum_me2": float(((mmx[ok].sum() - m64[ok].sum()) / m64[ok].sum()).abs()),
+                                            "points": int(ok.sum().item())}
+                    # conditioning of the points above 1e-3: how far the FP64 program itself moves when
+                    # its input momenta are rounded to FP32 (what any FP32-wavefunction evaluation sees)
+                    bad = torch.nonzero(ok & ((mmx - m64).abs() > 1e-3 * m64.abs())).flatten()[:64]
+                    if bad.numel():
+                        nb = int(bad.numel())
+                        mb = mom.view(info.n_ext * 4, n)[:, bad].float().double().contiguous()
+                        o64 = torch.empty(nb, dtype=torch.float64, device=dev)
+                        B.me_eval(h, mb, nb, o64, stream)
+                        torch.cuda.synchronize(dev)
+                        shift = ((o64 - m64[bad]).abs() / m64[bad]).cpu().tolist()
+                        err = ((mmx[bad] - m64[bad]).abs() / m64[bad]).cpu().tolist()
+                        row["mixed_rel_err"]["above_1e-3"] = [{"mixed_err": e_, "fp64_shift_at_fp32_inputs": s_}
+                                                             for e_, s_ in zip(err, shift)]
+                B.me_destroy(h)
+            row["mixed_over_fp64"] = row["mixed"]["evals_per_s"] / row["fp64"]["evals_per_s"]
+            table[key] = row
+        except Exception as exc:  # an auxiliary row that fails is recorded, not fatal to the headline line
+            table[key] = {"points": w["n"], "error": f"{type(exc).__name__}: {exc}"[:300]}
     return table
 
 
