@@ -37,6 +37,15 @@ CASES = {
     "u u~ > z z g": (opr.uux_zzg, 500.0, (91.1876, 91.1876, 0.0), (4,)),
     "u s > d c h h": (opr.us_dchh, 1000.0, (0.0, 0.0, 125.0, 125.0), ()),
     "u s > d c h": (opr.us_dch, 1000.0, (0.0, 0.0, 125.0), ()),
+    "u u~ > w+ w-": (opr.uux_wpwm, 500.0, (80.4, 80.4), ()),
+    "u d~ > w+ z": (opr.udx_wpz, 500.0, (80.4, 91.1876), ()),
+    "u u~ > z z": (opr.uux_zz, 500.0, (91.1876, 91.1876), ()),
+    "u u~ > z h": (opr.uux_zh, 500.0, (91.1876, 125.0), ()),
+    "u d~ > w+ h": (opr.udx_wph, 500.0, (80.4, 125.0), ()),
+    "u d~ > w+ g": (opr.udx_wpg, 500.0, (80.4, 0.0), (3,)),
+    "u u~ > z g": (opr.uux_zg, 500.0, (91.1876, 0.0), (3,)),
+    "g g > t t~": (opr.gg_ttx, 800.0, (175.0, 175.0), ()),
+    "u u > u u": (opr.uu_uu, 500.0, (0.0, 0.0), (2, 3)),
     "u g > w+ d": (opr.ug_wpd, 500.0, (80.4, 0.0), (3,)),
     "u u~ > z h g": (opr.uux_zhg, 600.0, (91.1876, 125.0, 0.0), (4,)),
     "u d~ > w+ h g": (opr.udx_wphg, 600.0, (80.4, 125.0, 0.0), (4,)),
