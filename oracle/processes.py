@@ -44,6 +44,7 @@ Functions and their pins (tests/test_oracle_processes.py):
   uux_wpwm        u u~ > w+ w-   : gauge cancellation of the longitudinal amplitude
                    (each diagram grows like s/mW^2, the sum stays finite), the W
                    polarisation sum against the tensor form -g + k k/mW^2, boosts
+  udx_wpa         u d~ > w+ a    : the radiation amplitude zero at cos(u, photon) = -1/3
   udx_wpz         u d~ > w+ z    : gauge cancellation of the longitudinal amplitude
                    (the WWZ vertex with an incoming W), boosts
   uux_wpwma       u u~ > w+ w- a : the photon's Ward identity with zero W and Z widths (the
@@ -861,6 +862,29 @@ def udx_wphg(P, par=SMParams(), eps_override=None):
     return tot / 36.0
 
 
+def udx_wpa(P, par=SMParams(), widths=True):
+    """u(p0) d~(p1) > W+(p2) gamma(p3): the photon from the u line, from the d line, and from the
+    s-channel W through the WWA vertex (the vertex of udx_wpz_amplitudes with the photon in place of
+    the Z).  The s-channel W carries the width wW unless widths=False."""
+    p = [P[:, k] for k in range(4)]
+    gw = par.g / np.sqrt(2.0)
+    wW = par.wW if widths else 0.0
+    q = p[0] + p[1]
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ew = polarisation(p[2], h[2], mass=par.mW).conj()
+        ea = polarisation(p[3], h[3]).conj()
+        W = (vector_insertion(ew, gw, 0.0), p[2])
+        A = (fermion_line(vb, u, p[0], [(vector_insertion(ea, *(2 * (_a_coupling("u", par),))), p[3]), W])
+             + fermion_line(vb, u, p[0], [W, (vector_insertion(ea, *(2 * (_a_coupling("d", par),))), p[3])]))
+        Ws = vector_prop(q, ffv_current(vb, u, gw, 0.0), par.mW, wW)
+        A = A - 1j * par.e * mdot(vvv_out(Ws, q, ew, -p[2], -p[3], 1.0), ea)
+        tot = tot + colour.colour_sum([A / 1j], [_DELTA3])
+    return tot / 36.0
+
+
 def udx_wpzg(P, par=SMParams(), eps_override=None):
     """u(p0) d~(p1) > W+(p2) Z(p3) g(p4): the three graphs of u d~ > W+ Z (Z from the u line, Z from
     the d line, s-channel W into the WWZ vertex) with the gluon at every place along the quark line
@@ -1305,6 +1329,7 @@ PROCESSES = {
     "u u~ > z z g": uux_zzg,
     "u u~ > z h g": uux_zhg,
     "u d~ > w+ h g": udx_wphg,
+    "u d~ > w+ a": udx_wpa,
     "u d~ > w+ z g": udx_wpzg,
     "u u~ > w+ w- g": uux_wpwmg,
     "g g > w+ d u~": gg_wpdux,

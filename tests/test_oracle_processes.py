@@ -932,3 +932,31 @@ def test_us_dch_closed_form():
     want = (9.0 / 36.0) * (PAR.g * PAR.mW) ** 2 * gw2 ** 2 * 16 * mdot(P[:, 0], P[:, 1]) * mdot(P[:, 2], P[:, 3]) \
         / (den(q1) * den(q2))
     assert np.allclose(pr.us_dch(P, PAR), want, rtol=1e-10)
+
+
+def _wa_points(rs, cos_uph, phi):
+    """u d~ > W+ gamma in the CM frame with the photon at angle theta to the u (cos theta = cos_uph)."""
+    n = len(cos_uph)
+    pabs = (rs ** 2 - PAR.mW ** 2) / (2 * rs)
+    P = np.zeros((n, 4, 4))
+    P[:, 0] = [rs / 2, 0, 0, rs / 2]
+    P[:, 1] = [rs / 2, 0, 0, -rs / 2]
+    s_ = np.sqrt(1 - cos_uph ** 2)
+    P[:, 3] = np.stack([np.full(n, pabs), pabs * s_ * np.cos(phi), pabs * s_ * np.sin(phi), pabs * cos_uph], axis=1)
+    P[:, 2, 0] = math.sqrt(PAR.mW ** 2 + pabs ** 2)
+    P[:, 2, 1:] = -P[:, 3, 1:]
+    return P
+
+
+def test_udx_wpa_radiation_zero():
+    """u d~ > W+ gamma has the radiation amplitude zero: at zero W width every helicity amplitude
+    vanishes when the photon leaves at cos theta = -1/3 to the u direction (the point where the photon
+    couplings of the u, the d~ and the W, weighted by their eikonal factors, cancel; Mikaelian, Samuel
+    and Sahdev 1979).  It needs the WWA vertex with the quark couplings' sign and strength."""
+    rng = np.random.default_rng(141)
+    for rs in (300.0, 600.0, 2000.0):
+        phi = rng.uniform(0, 2 * np.pi, 5)
+        at_zero = pr.udx_wpa(_wa_points(rs, np.full(5, -1.0 / 3.0), phi), PAR, widths=False)
+        away = pr.udx_wpa(_wa_points(rs, np.full(5, 0.5), phi), PAR, widths=False)
+        assert np.all(at_zero <= 1e-20 * away)
+        assert np.all(pr.udx_wpa(_wa_points(rs, np.full(5, -0.2), phi), PAR, widths=False) > 1e-3 * away)
