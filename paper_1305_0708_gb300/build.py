@@ -33,6 +33,7 @@ PROCESSES = [
     ("g g > g g", []),
     ("u u~ > w+ w-", []),
     ("u d~ > w+ z", []),
+    ("u d~ > w+ a", []),
     ("u u > u u", []),
     ("u u~ > z z", []),
     ("u u~ > z h", []),

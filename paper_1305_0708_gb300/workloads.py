@@ -49,6 +49,11 @@ VARIANTS = {
         cuts=None, s_ident=1.0,
         describe="u d~ > W+ Z (u and d exchange, s-channel W through the WWZ vertex), massive RAMBO at "
                  "sqrt(s)=500 GeV, 2^20 points, seed 6"),
+    "udx_wpa": dict(
+        process="u d~ > w+ a", kind="rambo", sqrt_s=500.0, masses=(0, 0, 80.4, 0), n=1 << 20, seed=27,
+        cuts=dict(legs=(3,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="u d~ > W+ gamma (photon from either quark and from the s-channel W through the WWA vertex), "
+                 "massive RAMBO at sqrt(s)=500 GeV, photon pT>20, |eta|<2.5, 2^20 accepted points, seed 27"),
     "uux_zz": dict(
         process="u u~ > z z", kind="rambo", sqrt_s=500.0, masses=(0, 0, 91.1876, 91.1876), n=1 << 20, seed=7,
         cuts=None, s_ident=0.5,
