@@ -35,6 +35,7 @@ Functions and their pins (tests/test_oracle_processes.py):
   uux_zh          u u~ > z h     : closed form from the trace, exact per point
   udx_wph         u d~ > w+ h    : closed form from the trace, exact per point
   udx_wpg, uux_zg q q~ > V g     : textbook closed form (t^2 + u^2 + 2 s mV^2)/(t u), exact per point
+  uux_za, uux_aa  u u~ > z a, a a: the same form with the photon (colour N_c in place of C_F N_c)
   gg_wpdux, gg_zuux  g g > w+ d u~, g g > z u u~ : Ward identity for each gluon, Bose symmetry, boosts
   ug_wpd          u g > w+ d     : the same closed form crossed (s <-> u, one fermion: sign -1), exact
   uux_zzg         u u~ > z z g   : Ward identity for the gluon, the soft-gluon limit against C_F times
@@ -1004,6 +1005,35 @@ def _qqx_vg(P, par, gl, gr, mV):
     return tot / 36.0
 
 
+def _uux_va(P, par, gl, gr, mV):
+    """u(p0) u~(p1) > V(p2) gamma(p3): both orders of the V (coupling gl, gr; mass mV, 0 for a photon)
+    and the photon along the quark line, colour delta."""
+    p = [P[:, k] for k in range(4)]
+    qa = _a_coupling("u", par)
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W if mV > 0 else HEL_V, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ev = polarisation(p[2], h[2], mass=mV).conj()
+        ea = polarisation(p[3], h[3]).conj()
+        V = (vector_insertion(ev, gl, gr), p[2])
+        A = (vector_insertion(ea, qa, qa), p[3])
+        M = (fermion_line(vb, u, p[0], [A, V]) + fermion_line(vb, u, p[0], [V, A])) / 1j
+        tot = tot + colour.colour_sum([M], [_DELTA3])
+    return tot / 36.0
+
+
+def uux_za(P, par=SMParams()):
+    """u u~ > Z gamma."""
+    return _uux_va(P, par, *_z_couplings("u", par), par.mZ)
+
+
+def uux_aa(P, par=SMParams()):
+    """u u~ > gamma gamma (identical photons; no symmetry factor here)."""
+    qa = _a_coupling("u", par)
+    return _uux_va(P, par, qa, qa, 0.0)
+
+
 def udx_wpg(P, par=SMParams()):
     """u d~ > W+ g."""
     return _qqx_vg(P, par, par.g / np.sqrt(2.0), 0.0, par.mW)
@@ -1325,6 +1355,8 @@ PROCESSES = {
     "u d~ > w+ h": udx_wph,
     "u d~ > w+ g": udx_wpg,
     "u u~ > z g": uux_zg,
+    "u u~ > z a": uux_za,
+    "u u~ > a a": uux_aa,
     "u g > w+ d": ug_wpd,
     "u u~ > z z g": uux_zzg,
     "u u~ > z h g": uux_zhg,

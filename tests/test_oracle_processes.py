@@ -960,3 +960,25 @@ def test_udx_wpa_radiation_zero():
         away = pr.udx_wpa(_wa_points(rs, np.full(5, 0.5), phi), PAR, widths=False)
         assert np.all(at_zero <= 1e-20 * away)
         assert np.all(pr.udx_wpa(_wa_points(rs, np.full(5, -0.2), phi), PAR, widths=False) > 1e-3 * away)
+
+
+@pytest.mark.parametrize("which", ["za", "aa"])
+def test_uux_va_closed_form(which):
+    """u u~ > Z gamma and u u~ > gamma gamma: the q q~ > V g form with the gluon replaced by a photon,
+    the colour factor C_F N_c = 4 by N_c = 3: (1/3)(gL^2 + gR^2) e^2 Qu^2 (t^2 + u^2 + 2 s mV^2)/(t u);
+    for two photons (2/3) e^4 Qu^4 (t/u + u/t), the textbook q q~ > gamma gamma result."""
+    qa = PAR.e * CHARGE["u"]
+    if which == "za":
+        mV, fn = PAR.mZ, pr.uux_za
+        gl = PAR.gz * (T3["u"] - CHARGE["u"] * PAR.sw2)
+        gr = PAR.gz * (-CHARGE["u"] * PAR.sw2)
+    else:
+        mV, fn, gl, gr = 0.0, pr.uux_aa, qa, qa
+    P = two_to_two(400.0, 64, mV, 0.0, seed=151)
+    s = mdot(P[:, 0] + P[:, 1], P[:, 0] + P[:, 1])
+    t = mdot(P[:, 0] - P[:, 2], P[:, 0] - P[:, 2])
+    u = mdot(P[:, 0] - P[:, 3], P[:, 0] - P[:, 3])
+    want = (1.0 / 3.0) * (gl ** 2 + gr ** 2) * qa ** 2 * (t * t + u * u + 2 * s * mV ** 2) / (t * u)
+    assert np.allclose(fn(P, PAR), want, rtol=1e-12, atol=0)
+    if which == "aa":
+        assert np.allclose(want, (2.0 / 3.0) * qa ** 4 * (t / u + u / t), rtol=1e-12)
