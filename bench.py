@@ -215,7 +215,8 @@ def oracle_step(w, events):
     fn = {"u u~ > e+ e-": opr.uux_epem, "u d~ > e+ ve g g": opr.udx_epvegg,
           "g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))": opr.gg_ttx_dilep,
           "u s > d c h h": opr.us_dchh, "g g > g g g g": opr.gluons, "u u~ > w+ w-": opr.uux_wpwm,
-          "u d~ > w+ z": opr.udx_wpz, "u d~ > w+ a": opr.udx_wpa, "u u~ > z z": opr.uux_zz,
+          "u d~ > w+ z": opr.udx_wpz, "u d~ > w+ a": opr.udx_wpa, "u u~ > z a": opr.uux_za,
+          "u u~ > a a": opr.uux_aa, "u u~ > z z": opr.uux_zz,
           "u u~ > z h": opr.uux_zh, "u d~ > w+ h": opr.udx_wph,
           "u u~ > w+ w- a": opr.uux_wpwma, "g g > t t~": opr.gg_ttx,
           "g g > t t~ h": opr.gg_ttxh, "u d~ > w+ g": opr.udx_wpg, "u u~ > z g": opr.uux_zg,

@@ -34,6 +34,8 @@ PROCESSES = [
     ("u u~ > w+ w-", []),
     ("u d~ > w+ z", []),
     ("u d~ > w+ a", []),
+    ("u u~ > z a", []),
+    ("u u~ > a a", []),
     ("u u > u u", []),
     ("u u~ > z z", []),
     ("u u~ > z h", []),

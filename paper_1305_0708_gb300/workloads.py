@@ -54,6 +54,16 @@ VARIANTS = {
         cuts=dict(legs=(3,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
         describe="u d~ > W+ gamma (photon from either quark and from the s-channel W through the WWA vertex), "
                  "massive RAMBO at sqrt(s)=500 GeV, photon pT>20, |eta|<2.5, 2^20 accepted points, seed 27"),
+    "uux_za": dict(
+        process="u u~ > z a", kind="rambo", sqrt_s=500.0, masses=(0, 0, 91.1876, 0), n=1 << 20, seed=28,
+        cuts=dict(legs=(3,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="u u~ > Z gamma, massive RAMBO at sqrt(s)=500 GeV, photon pT>20, |eta|<2.5, 2^20 accepted "
+                 "points, seed 28"),
+    "uux_aa": dict(
+        process="u u~ > a a", kind="rambo", sqrt_s=500.0, n=1 << 20, seed=29,
+        cuts=dict(legs=(2, 3), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,
+        describe="u u~ > gamma gamma (identical photons), RAMBO at sqrt(s)=500 GeV, pT>20, |eta|<2.5, "
+                 "DeltaR>0.4 on the photons, 2^20 accepted points, seed 29"),
     "uux_zz": dict(
         process="u u~ > z z", kind="rambo", sqrt_s=500.0, masses=(0, 0, 91.1876, 91.1876), n=1 << 20, seed=7,
         cuts=None, s_ident=0.5,

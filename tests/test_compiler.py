@@ -19,6 +19,8 @@ CASES = {
     "u u~ > w+ w-": (3, 18, 1),          # t-channel d; s-channel photon and Z
     "u d~ > w+ z": (3, 9, 1),            # Z from u, Z from d; s-channel W
     "u d~ > w+ a": (3, 6, 1),            # photon from u, from d~, from the s-channel W
+    "u u~ > z a": (2, 12, 1),
+    "u u~ > a a": (2, 8, 1),
     "u u~ > z z": (2, 18, 1),
     "u u~ > z h": (1, 6, 1),
     "u d~ > w+ h": (1, 3, 1),

@@ -320,14 +320,15 @@ def test_identical_quarks_parity(B, prec):
 @pytest.mark.parametrize("key", ["uux_zz", "uux_zh", "udx_wph", "uux_wpwma", "gg_ttx", "gg_ttxh", "udx_wpg",
                                  "uux_zg", "ug_wpd", "uux_zzg", "gg_ttxg", "uux_zhg", "udx_wpzg",
                                  "uux_wpwmg", "gg_wpdux", "gg_zuux", "udx_wphg",
-                                 "uux_ttx", "uux_ttxg", "us_dch", "udx_wpa"])
+                                 "uux_ttx", "uux_ttxg", "us_dch", "udx_wpa",
+                                 "uux_za", "uux_aa"])
 def test_massive_final_state_parity(B, key, prec):
     """u u~ > Z Z (identical massive vectors, identical-particle factor 1/2), u u~ > Z H (ZZH vertex,
     external scalar), u d~ > W+ H (WWH vertex), u u~ > W+ W- gamma (the electroweak quartic
     vertices, VVV currents into massive W lines, photon pT and rapidity cuts), g g > t t~ (massive
     external spinors), u u~ > t t~ and u u~ > t t~ g (gluon, photon and Z exchange), g g > t t~ H (the FFS Yukawa vertex), u d~ > W+ g, u u~ > Z g, u g > W+ d and
     u u~ > Z Z g, u u~ > Z H g, u d~ > W+ H g, u d~ > W+ Z g, u u~ > W+ W- g (bosons plus one jet, jet cuts), g g > W+ d u~
-    and g g > Z u u~ (V plus two jets from two gluons), u s > d c H (W+ W- fusion), u d~ > W+ gamma and g g > t t~ g (the
+    and g g > Z u u~ (V plus two jets from two gluons), u s > d c H (W+ W- fusion), u d~ > W+ gamma, u u~ > Z gamma, u u~ > gamma gamma and g g > t t~ g (the
     four-gluon vertex beside a top line): me_eval on the oracle's massive-RAMBO points and the Monte Carlo sums
     against the oracle."""
     from paper_1305_0708_gb300.workloads import VARIANTS
@@ -337,13 +338,14 @@ def test_massive_final_state_parity(B, key, prec):
           "ug_wpd": opr.ug_wpd, "uux_zzg": opr.uux_zzg, "gg_ttxg": opr.gg_ttxg, "uux_zhg": opr.uux_zhg,
           "udx_wpzg": opr.udx_wpzg, "uux_wpwmg": opr.uux_wpwmg, "gg_wpdux": opr.gg_wpdux,
           "gg_zuux": opr.gg_zuux, "udx_wphg": opr.udx_wphg,
-          "uux_ttx": opr.uux_ttx, "uux_ttxg": opr.uux_ttxg, "us_dch": opr.us_dch, "udx_wpa": opr.udx_wpa}[key]
+          "uux_ttx": opr.uux_ttx, "uux_ttxg": opr.uux_ttxg, "us_dch": opr.us_dch, "udx_wpa": opr.udx_wpa,
+          "uux_za": opr.uux_za, "uux_aa": opr.uux_aa}[key]
     n = 1500
     P, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(n))
     ref = fn(P, PAR)
     got = eval_gpu(B, w["process"], P, prec)
     if prec == 0:
-        tol = fp64_tolerance(fn, P, ref, masses=w["masses"])
+        tol = fp64_tolerance(fn, P, ref, masses=w.get("masses", (0.0,) * P.shape[1]))
         assert np.all(np.abs(got - ref) <= tol)
         assert np.median(np.abs(got / ref - 1)) <= 1e-12
     else:

@@ -40,6 +40,8 @@ CASES = {
     "u u~ > w+ w-": (opr.uux_wpwm, 500.0, (80.4, 80.4), ()),
     "u d~ > w+ z": (opr.udx_wpz, 500.0, (80.4, 91.1876), ()),
     "u d~ > w+ a": (opr.udx_wpa, 500.0, (80.4, 0.0), (3,)),
+    "u u~ > z a": (opr.uux_za, 500.0, (91.1876, 0.0), (3,)),
+    "u u~ > a a": (opr.uux_aa, 500.0, (0.0, 0.0), (2, 3)),
     "u u~ > z z": (opr.uux_zz, 500.0, (91.1876, 91.1876), ()),
     "u u~ > z h": (opr.uux_zh, 500.0, (91.1876, 125.0), ()),
     "u d~ > w+ h": (opr.udx_wph, 500.0, (80.4, 125.0), ()),
