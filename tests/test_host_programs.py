@@ -80,8 +80,9 @@ def _points(sqrt_s, masses, cut_legs, n, seed):
 
 
 def _tolerance(fn, P, ref, masses):
-    """1e-12 relative plus 32 times the oracle's spread under 2^-52 input perturbations and under
-    recomputing the energies on shell (RAMBO leaves a few points off shell at ~1e-11)."""
+    """1e-12 relative plus 32 times the oracle's spread under 2^-52 input perturbations, under
+    recomputing the energies on shell and under restoring momentum conservation (RAMBO's boosts leave a
+    few points off shell at ~1e-11 and unbalanced by up to ~1e-9 GeV)."""
     rng = np.random.default_rng(123)
     spread = np.zeros_like(ref)
     for _ in range(3):
@@ -90,6 +91,9 @@ def _tolerance(fn, P, ref, masses):
     Q = P.copy()
     for k, m in enumerate(masses):
         Q[:, k, 0] = np.sqrt(m * m + np.sum(P[:, k, 1:] ** 2, axis=1))
+    spread = np.maximum(spread, np.abs(fn(Q, PAR) - ref))
+    Q = P.copy()                                     # momentum conservation restored on the last leg
+    Q[:, -1] = P[:, 0] + P[:, 1] - P[:, 2:-1].sum(axis=1)
     spread = np.maximum(spread, np.abs(fn(Q, PAR) - ref))
     return 1e-12 * np.abs(ref) + 32 * spread
 
