@@ -15,8 +15,9 @@ pz), incoming legs first, in the order of the process string.
 Functions and their pins (tests/test_oracle_processes.py):
   uux_epem        u u~ > e+ e-   : closed-form dsigma/dcos(theta), exact per point
   udx_epve        u d~ > e+ ve   : closed form (V-A), exact per point
-  udx_epvegg      u d~ > e+ ve g g : Ward identity, Bose symmetry, boosts,
-                   built from blocks pinned by the two cases above and q q~ > g g
+  udx_epvegg      u d~ > e+ ve g g : Ward identity, Bose symmetry, boosts; its
+                   normalisation by the soft limit of either gluon against the
+                   colour-correlated eikonal factor of q, q~, g times u d~ > e+ ve g
   uux_gg          u u~ > g g     : textbook closed form, exact per point
   gg_ttx          g g > t t~     : textbook closed form (massive), exact per point
   uux_ttx         u u~ > t t~    : textbook closed forms of the gluon and the photon exchange (massive
@@ -52,10 +53,15 @@ Functions and their pins (tests/test_oracle_processes.py):
                    fifteen diagrams cancel only with the quartic WWAA and WWAZ vertices),
                    the soft-photon limit against the eikonal factor times u u~ > w+ w-, boosts
   us_dch          u s > d c h    (WW fusion): closed form from the V-A traces, exact per point
-  us_dchh         u s > d c h h  (WW fusion): Higgs-exchange symmetry, boosts;
-                   its W current is pinned by u d~ > e+ ve, its WWH/WWHH/HHH
-                   couplings and diagram set by the gauge cancellation of the
-                   longitudinal W+ W- > h h amplitude (wpwm_hh_amplitudes)
+  us_dchh         u s > d c h h  (WW fusion): its W W > h h core (_ww_hh, the code
+                   it runs) pinned by the gauge cancellation of the longitudinal
+                   on-shell W+ W- > h h amplitude (wpwm_hh_amplitudes calls the same
+                   core); the whole process by the fixed-angle high-energy limit
+                   (zero W width: s^2 |M|^2 tends to a constant, a wrong relative
+                   sign or coupling of the four diagrams grows like s^2); its W
+                   currents by u s > d c h; Higgs-exchange symmetry, boosts
+  udx_epveg       u d~ > e+ ve g : Ward identity; soft-gluon limit against C_F times
+                   the eikonal factor times u d~ > e+ ve (closed form); boosts
   gluons          g g > g...g    : Berends-Giele, pinned by the gg > gg closed
                    form, Parke-Taylor MHV amplitudes, Ward, Bose, boosts
 """
@@ -135,6 +141,30 @@ def udx_epve(P, par=SMParams()):
         Jq = ffv_current(vb, u, gw, 0.0)
         M = mdot(Jq, W) / 1j
         tot = tot + colour.colour_sum([M], [_DELTA3])
+    return tot / 36.0
+
+
+# --------------------------------------------------------------------------
+# u d~ > e+ ve g  (W+ -> e+ ve plus one gluon: the link of the soft-gluon chain
+# u d~ > e+ ve  <-  u d~ > e+ ve g  <-  u d~ > e+ ve g g)
+# --------------------------------------------------------------------------
+def udx_epveg(P, par=SMParams(), eps_override=None):
+    """Two diagrams: the gluon before or after the W along the quark line.
+    eps_override: optional vector[N,4] replacing the gluon polarisation (Ward identity)."""
+    p = [P[:, k] for k in range(5)]
+    gs, gw = par.gs, par.g / np.sqrt(2.0)
+    cg = _colour_string([0], 1)
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_F, HEL_F, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        L = ffv_current(bar(u_spinor(p[3], h[3])), v_spinor(p[2], h[2]), gw, 0.0)
+        qW = p[2] + p[3]
+        W = (vector_insertion(vector_prop(qW, L, par.mW, par.wW), gw, 0.0), qW)
+        eg = polarisation(p[4], h[4]).conj() if eps_override is None else eps_override.astype(complex)
+        G = (vector_insertion(eg, gs, gs), p[4])
+        amps = [fermion_line(vb, u, p[0], [W, G]) / 1j, fermion_line(vb, u, p[0], [G, W]) / 1j]
+        tot = tot + colour.colour_sum(amps, [cg, cg])
     return tot / 36.0
 
 
@@ -659,15 +689,27 @@ def _line_with_flavours(row, col, p_start, inserts, seq, mt, wt):
 # --------------------------------------------------------------------------
 # u s > d c h h  (W+ W- fusion into a Higgs pair)
 # --------------------------------------------------------------------------
-def us_dchh(P, par=SMParams(), per_helicity=False):
-    """Four diagrams: WWHH contact, s-channel H with HHH, and t/u-channel W
-    exchange with two WWH vertices.  H wavefunctions are 1."""
-    p = [P[:, k] for k in range(6)]
+def _ww_hh(W1, q1, W2, q2, pA, pB, par):
+    """The four W+ W- > h h diagrams as i M pieces (contact WWHH, s-channel H through HHH, and W
+    exchange with the Higgs bosons pA or pB leaving the W1 end), for vector wavefunctions W1 (a W+
+    flowing in with momentum q1) and W2 (a W- flowing in with momentum q2), off shell or on shell.
+    H wavefunctions are 1; couplings g mW (WWH), g^2/2 (WWHH) and -3 mH^2/v (HHH)."""
     g, mW, wW, mH, wH, v = par.g, par.mW, par.wW, par.mH, par.wH, par.vev
-    gw = g / np.sqrt(2.0)
-    gwwh = g * mW
-    gwwhh = g * g / 2.0
-    ghhh = -3.0 * mH * mH / v
+    gwwh, gwwhh, ghhh = g * mW, g * g / 2.0, -3.0 * mH * mH / v
+    w12 = mdot(W1, W2)
+    out = [1j * gwwhh * w12, (1j * gwwh * w12) * scalar_prop(q1 + q2, mH, wH) * (1j * ghhh)]
+    for ph in (pA, pB):
+        Wst = vector_prop(q1 - ph, 1j * gwwh * W1, mW, wW)
+        out.append(1j * gwwh * mdot(Wst, W2))
+    return out
+
+
+def us_dchh(P, par=SMParams(), per_helicity=False):
+    """Four diagrams: the two quark currents, each into its t-channel W propagator, feed the
+    W+ W- > h h core (_ww_hh): WWHH contact, s-channel H with HHH, and t/u-channel W exchange
+    with two WWH vertices."""
+    p = [P[:, k] for k in range(6)]
+    gw = par.g / np.sqrt(2.0)
     q1 = p[0] - p[2]
     q2 = p[1] - p[3]
     tot = 0.0
@@ -675,16 +717,9 @@ def us_dchh(P, par=SMParams(), per_helicity=False):
     for h in itertools.product(HEL_F, repeat=4):
         J1 = ffv_current(bar(u_spinor(p[2], h[2])), u_spinor(p[0], h[0]), gw, 0.0)
         J2 = ffv_current(bar(u_spinor(p[3], h[3])), u_spinor(p[1], h[1]), gw, 0.0)
-        W1 = vector_prop(q1, J1, mW, wW)
-        W2 = vector_prop(q2, J2, mW, wW)
-        w12 = mdot(W1, W2)
-        iM = 1j * gwwhh * w12
-        iM = iM + (1j * gwwh * w12) * scalar_prop(q1 + q2, mH, wH) * (1j * ghhh)
-        for hA in (4, 5):
-            k = q1 - p[hA]
-            Wst = vector_prop(k, 1j * gwwh * W1, mW, wW)
-            iM = iM + 1j * gwwh * mdot(Wst, W2)
-        M = iM / 1j
+        W1 = vector_prop(q1, J1, par.mW, par.wW)
+        W2 = vector_prop(q2, J2, par.mW, par.wW)
+        M = sum(_ww_hh(W1, q1, W2, q2, p[4], p[5], par)) / 1j
         m2 = 9.0 * np.abs(M) ** 2
         ph[h + (0, 0)] = m2
         tot = tot + m2
@@ -715,20 +750,12 @@ def us_dch(P, par=SMParams()):
 # --------------------------------------------------------------------------
 def wpwm_hh_amplitudes(P, hel, par=SMParams()):
     """The four diagrams of W+(p0) W-(p1) > h(p2) h(p3) for fixed W helicities,
-    returned separately (contact, s-channel H, t- and u-channel W) as M values."""
+    returned separately (contact, s-channel H, t- and u-channel W) as M values:
+    the core of u s > d c h h (_ww_hh) fed with on-shell polarisation vectors."""
     p = [P[:, k] for k in range(4)]
-    g, mW, wW, mH, wH, v = par.g, par.mW, par.wW, par.mH, par.wH, par.vev
-    gwwh, gwwhh, ghhh = g * mW, g * g / 2.0, -3.0 * mH * mH / v
-    e0 = polarisation(p[0], hel[0], mass=mW)
-    e1 = polarisation(p[1], hel[1], mass=mW)
-    e01 = mdot(e0, e1)
-    out = [gwwhh * e01 * 1j,
-           (1j * gwwh * e01) * scalar_prop(p[0] + p[1], mH, wH) * (1j * ghhh)]
-    for hA in (2, 3):
-        k = p[0] - p[hA]
-        Wst = vector_prop(k, 1j * gwwh * e0, mW, wW)
-        out.append(1j * gwwh * mdot(Wst, e1))
-    return [x / 1j for x in out]
+    e0 = polarisation(p[0], hel[0], mass=par.mW)
+    e1 = polarisation(p[1], hel[1], mass=par.mW)
+    return [x / 1j for x in _ww_hh(e0, p[0], e1, p[1], p[2], p[3], par)]
 
 
 # --------------------------------------------------------------------------
@@ -1344,6 +1371,7 @@ def gluons(P, par=SMParams(), per_helicity=False, eps_override=None, colour_matr
 PROCESSES = {
     "u u~ > e+ e-": uux_epem,
     "u d~ > e+ ve": udx_epve,
+    "u d~ > e+ ve g": udx_epveg,
     "u u~ > g g": uux_gg,
     "u d~ > e+ ve g g": udx_epvegg,
     "g g > t t~": gg_ttx,
