@@ -188,7 +188,11 @@ me_status xsec_step_async(me_handle h, uint64_t seed, uint64_t counter_offset, i
  *    ME_ERR_ARG.  The array occupies about 100 KB on every GPU that loads the
  *    library, until the process exits.
  *  - The first call on a device looks up the array's device address (with that
- *    device current); make that first call before any stream capture.
+ *    device current), and so does the first call after the device's context
+ *    was made anew (cudaDeviceReset); make those calls before any stream
+ *    capture.
+ *  - Processes whose |M|^2 kernel takes one event per block (the all-gluon
+ *    processes) have no fused step: ME_ERR_ARG, before any device work.
  *  - Every call shares the one array: calls whose work overlaps on the GPU (on
  *    different streams, or from several threads) race and corrupt each other's
  *    sums.  Serialise them.  The array keeps the previous call's contents; the

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "runtime_internal.h"
 
 namespace me {
@@ -348,21 +350,57 @@ __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-NoAllocScratch* g_noalloc_ptr[kMaxDevices] = {};
+struct NoAllocSlot {
+  unsigned long long ctx_id;  // context the address belongs to (0: not looked up yet)
+  NoAllocScratch* ptr;
+};
+NoAllocSlot g_noalloc_slot[kMaxDevices] = {};
+
+// Unique id of the calling thread's current context (driver entry points taken through the runtime,
+// so the library needs no link dependency on the driver library).  0 if it cannot be had.
+unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrent)(CUcontext*);
+  typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 // Device address of the scratch array for the current device.  Host code may
 // not use &g_noalloc_scratch (that is a host-side stand-in); the address is
-// looked up once per device, with that device current.
+// looked up with the device current, once per device and context: a context
+// made anew (after cudaDeviceReset, say) reloads the module, so the address is
+// looked up again.  Call after a CUDA call has made the device's context
+// current (the runtime does that on first use).
 me_status noalloc_scratch(int device, NoAllocScratch** out) {
   if (device < 0 || device >= kMaxDevices) return fail(ME_ERR_ARG, "xsec_step_noalloc: device index out of range");
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[device]) {
+  NoAllocSlot& slot = g_noalloc_slot[device];
+  if (!slot.ptr || ctx == 0 || slot.ctx_id != ctx) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-    g_noalloc_ptr[device] = static_cast<NoAllocScratch*>(ptr);
+    slot.ptr = static_cast<NoAllocScratch*>(ptr);
+    slot.ctx_id = ctx;
   }
-  *out = g_noalloc_ptr[device];
+  *out = slot.ptr;
   return ME_OK;
 }
 
@@ -600,6 +638,9 @@ me_status xsec_step_noalloc(me_handle h, uint64_t seed, uint64_t counter_offset,
   if (st != ME_OK) return st;
   if (!kin || !acc) return fail(ME_ERR_ARG, "xsec_step_noalloc: null argument");
   if (n_accept < 0) return fail(ME_ERR_ARG, "xsec_step_noalloc: n_accept < 0");
+  if (h->desc->events_per_block == 1)
+    return fail(ME_ERR_ARG, std::string("xsec_step_noalloc: not available for ") + h->desc->name +
+                                " (its |M|^2 kernel takes one event per block and has no fused step)");
   me::KinDev k;
   if ((st = make_kin(h, kin, k)) != ME_OK) return st;
   if (n_accept == 0) return ME_OK;
