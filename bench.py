@@ -11,6 +11,11 @@ beside it for context.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload KEY]
 
+Output: the last line of stdout is one compact JSON record (rate, FP64 rate, the relative error
+of both paths against the FP64 CPU oracle on points sampled over one full-size step, roofline,
+CPU baseline, end-to-end rate, clocks); the full record (per-kernel figures, every process's
+rates and errors, the serving mix, the adaptive grids) goes to --detail (bench_detail.json).
+
 With N > 1 (torchrun, one process per GPU) each rank runs its own 2^20 points
 (disjoint Philox counters): weak scaling, no data-path collective.
 --impl reference times the FP64 CPU oracle on the host cores instead.
@@ -208,23 +213,19 @@ def oracle_kin(w):
     return k
 
 
+def oracle_me_fn(process):
+    """The oracle's |M|^2 function of a compiled process string (the decay-chain tt~ process under
+    either of its names)."""
+    from oracle import processes as opr
+    alias = {"g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))": "g g > t t~ > b e+ ve b~ e- ve~"}
+    return opr.PROCESSES[alias.get(process, process)]
+
+
 def oracle_step(w, events):
     """The oracle's whole step on a sample of events: generate, |M|^2, accumulate."""
-    from oracle import processes as opr, xsec as oxs
+    from oracle import xsec as oxs
     from oracle.sm import SMParams
-    fn = {"u u~ > e+ e-": opr.uux_epem, "u d~ > e+ ve g g": opr.udx_epvegg,
-          "g g > (t > b (w+ > e+ ve)) (t~ > b~ (w- > e- ve~))": opr.gg_ttx_dilep,
-          "u s > d c h h": opr.us_dchh, "g g > g g g g": opr.gluons, "u u~ > w+ w-": opr.uux_wpwm,
-          "u d~ > w+ z": opr.udx_wpz, "u d~ > w+ a": opr.udx_wpa, "u u~ > z a": opr.uux_za,
-          "u u~ > a a": opr.uux_aa, "u u~ > z z": opr.uux_zz,
-          "u u~ > z h": opr.uux_zh, "u d~ > w+ h": opr.udx_wph,
-          "u u~ > w+ w- a": opr.uux_wpwma, "g g > t t~": opr.gg_ttx,
-          "g g > t t~ h": opr.gg_ttxh, "u d~ > w+ g": opr.udx_wpg, "u u~ > z g": opr.uux_zg,
-          "u g > w+ d": opr.ug_wpd, "u u~ > z z g": opr.uux_zzg, "g g > t t~ g": opr.gg_ttxg,
-          "u u~ > z h g": opr.uux_zhg, "u d~ > w+ z g": opr.udx_wpzg, "u d~ > w+ h g": opr.udx_wphg,
-          "u u~ > w+ w- g": opr.uux_wpwmg, "u u~ > t t~": opr.uux_ttx, "u u~ > t t~ g": opr.uux_ttxg,
-          "u s > d c h": opr.us_dch, "g g > w+ d u~": opr.gg_wpdux,
-          "g g > z u u~": opr.gg_zuux}[w["process"]]
+    fn = oracle_me_fn(w["process"])
     par = SMParams()
     P, W, S, T = oxs.generate(oracle_kin(w), par, w["seed"], events)
     return oxs.accumulate(fn(P, par), W, S, T, w["s_ident"])
@@ -503,6 +504,10 @@ def main():
     ap.add_argument("--no-table", action="store_true", help="skip the per-process table")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix leg")
     ap.add_argument("--no-vegas", action="store_true", help="skip the adaptive-grid leg")
+    ap.add_argument("--par-sample", type=int, default=512,
+                    help="points of one full-size step compared with the oracle (0: skip)")
+    ap.add_argument("--detail", default="bench_detail.json",
+                    help="file for the full record (per-kernel figures, per-process table, serving, grids)")
     ap.add_argument("--points", type=int, default=0,
                     help="points per step instead of the workload's own count (small cases for profiling)")
     args = ap.parse_args()
@@ -686,8 +691,36 @@ def main():
     if not args.no_table:
         table = per_process_table(B, torch, dev, stream, flush, offset0, 2, 3)
 
+    # sampled points of one full-size step in the timed launch shape, both precisions, for the
+    # oracle comparison in the cpu_baseline leg: |M|^2 and the momenta of n_par points spread
+    # over the whole launch (first and last point included)
+    samples = {}
+    if rank == 0 and world == 1 and args.par_sample > 0:
+        idx = torch.from_numpy(np.unique(np.linspace(0, n - 1, args.par_sample).astype(np.int64))).to(dev)
+        for prec, name in ((B.ME_MIXED, "mixed"), (B.ME_FP64, "fp64")):
+            hp = B.me_create(w["process"], None, prec)
+            mom_s = torch.empty(info.n_ext * 4 * n, dtype=torch.float64, device=dev)
+            me2_s = torch.empty(n, dtype=torch.float64, device=dev)
+            B.xsec_step(hp, w["seed"], offset0 + (1 << 32), n, kin, stream, B.me_xsec_acc(), me2_s, mom_s)
+            torch.cuda.synchronize(dev)
+            P = mom_s.view(info.n_ext, 4, n)[:, :, idx].permute(2, 0, 1).contiguous().cpu().numpy()
+            samples[name] = (me2_s[idx].cpu().numpy(), P)
+            B.me_destroy(hp)
+            del mom_s, me2_s
+
     cpu = None
+    parity = None
     if rank == 0 and world == 1:
+        # the oracle on the sampled points of both paths: relative error of |M|^2 per point
+        if samples:
+            from oracle.sm import SMParams
+            fn = oracle_me_fn(w["process"])
+            parity = {"points": int(len(samples["fp64"][0])), "spread_over": n}
+            for name, (got, P) in samples.items():
+                ref = fn(np.ascontiguousarray(P), SMParams())
+                ok = ref > 0
+                rel = np.abs(got[ok] / ref[ok] - 1.0)
+                parity[name] = {"median": float(np.median(rel)), "max": float(rel.max())}
         # one core, then every host core (the sample split by points over single-threaded processes)
         events = np.arange(args.cpu_sample)
         oracle_step(w, np.arange(32))
@@ -709,35 +742,37 @@ def main():
                          f"on one core"}
 
     if rank == 0:
+        # the full record (per-kernel figures, the per-process table, the serving mix, the adaptive
+        # grids) goes to a side file; stdout ends with one compact headline line
+        detail = {"kernels": kernels, "me_eval_ms": me_eval_ms, "per_process": table, "serving": serving,
+                  "vegas": vegas, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "wall_s_timed": wall32,
+                  "mc": {"sigma_pb": mc["sum_w"] / mc["n_try"], "n_try": mc["n_try"], "n_acc": mc["n_acc"],
+                         "ranks": world}}
+        if args.detail:
+            d = os.path.dirname(os.path.abspath(args.detail))
+            os.makedirs(d, exist_ok=True)
+            with open(args.detail, "w") as f:
+                json.dump(detail, f, indent=1)
+        iss = issue_roofline(args.workload, dom, kernels[dom]["ms"], n)
         line = {
             "metric": "|M|^2 evals/s", "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (amplitudes; momenta, resonant invariants and per-thread sums as f32 pairs; f64 block sums)",
-            "data": "synthetic (on-device Philox phase space)",
-            "config": {"workload": args.workload, "describe": w["describe"], "points_per_step_per_gpu": n,
-                       "precision": "mixed", "l2": "flushed (256 MB write) between timed steps",
-                       "parallelism": f"replicas x{world}"},
-            "fp64_path": fp64,
-            "me_eval_ms": me_eval_ms,
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (on-device Philox phase space)",
+            "config": {"workload": args.workload, "points_per_step_per_gpu": n, "precision": "mixed",
+                       "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
+            "fp64_path": None if fp64 is None else {"value": fp64["value"], "ms_per_step": fp64["ms_per_step"]},
+            "rel_err_vs_oracle": parity,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
-                         "flops_per_point": kernels[dom]["flops_per_point"],
-                         "flops_source": kernels[dom]["flops_source"],
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                         "issue": issue_roofline(args.workload, dom, kernels[dom]["ms"], n)},
-            "kernels": kernels,
-            "per_process": table,
-            "serving": serving,
-            "vegas": vegas,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
+                         "issue_frac": None if iss is None else iss["frac"]},
+            "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
             "gpu_launches": 3 * args.steps,
-            "clocks": clk,
-            "mc": {"sigma_pb": mc["sum_w"] / mc["n_try"], "n_try": mc["n_try"], "n_acc": mc["n_acc"],
-                   "ranks": world},
-            "wall_s_timed": wall32,
+            "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "detail_file": args.detail or None,
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
