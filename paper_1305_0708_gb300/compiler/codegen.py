@@ -106,9 +106,10 @@ class _Emitter:
             if nd.external:
                 continue
             kids = nd.children
-            E(f"  const me::P4<R> k{nid} = " + " + ".join(f"k{c}" for c in kids) + ";")
-            self.flops32 += 4 * (len(kids) - 1)
             part = PARTICLES[nd.ptype]
+            if not (mixed and not part.massless):
+                E(f"  const me::P4<R> k{nid} = " + " + ".join(f"k{c}" for c in kids) + ";")
+                self.flops32 += 4 * (len(kids) - 1)
             if part.massless:
                 E(f"  const R inv{nid} = R(1) / me::msq(k{nid});  // real: massless line")
                 self.flops32 += 8
@@ -141,6 +142,11 @@ class _Emitter:
                                 e += f" {sgn} p{l}[{mu}]"
                         dcomps.append(e)
                     E(f"  const me::df Q{nid}[4] = {{{', '.join(dcomps)}}};")
+                    # the line's FP32 momentum is the rounding of its double-float sum: FP32 sums of the
+                    # rounded external momenta lose the digits that cancel between incoming and outgoing
+                    # legs, and near-collinear decay products turn that loss into errors of 1e-3 in |M|^2
+                    E(f"  const me::P4<R> k{nid} = me::p4f(Q{nid});")
+                    self.flops32 += 4
                     E(f"  const me::df q2_{nid} = ((me::sqr(Q{nid}[0]) - me::sqr(Q{nid}[1])) - me::sqr(Q{nid}[2])) - "
                       f"me::sqr(Q{nid}[3]);")
                     # m^2 (double-float) and m Gamma (FP32) come converted from the host (ParamsMx)

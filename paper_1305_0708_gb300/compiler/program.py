@@ -76,7 +76,7 @@ class Program:
     cmat_den: int
     average: Fraction               # 1/(spin states x colour states) of the initial legs
     phases: dict = field(default_factory=dict)
-    conserved: set = field(default_factory=set)   # nodes whose vector current is conserved
+    conserved: set = field(default_factory=set)   # vector lines whose k k / m^2 term vanishes
     flops: dict = field(default_factory=dict)
 
     @property
@@ -383,11 +383,29 @@ def compile_process(name):
         if l.incoming:
             avg /= len(l.hels)
             avg /= abs(l.colour)
+    # vector lines whose k^mu k^nu / m^2 propagator term gives exactly zero: the current they carry, or
+    # the current they are contracted with at every place they are used, comes from two external
+    # massless fermions (k.J = 0 by the Dirac equation).  Computing such a term anyway adds only
+    # rounding, amplified in FP32 by the size of k.J of the other end.
+    def _massless_pair(vertex_kind, children):
+        return vertex_kind == "FFV" and all(nodes[c].external and PARTICLES[nodes[c].ptype].massless
+                                            for c in children if PARTICLES[nodes[c].ptype].is_fermion)
+    uses = {}
+    for nd in nodes:
+        if not nd.external:
+            for c in nd.children:
+                uses.setdefault(c, []).append((nd.vertex.kind, [x for x in nd.children if x != c]))
+    for a in amps:
+        for c in a.children:
+            uses.setdefault(c, []).append((a.vertex.kind, [x for x in a.children if x != c], "amp"))
     conserved = set()
     for nd in nodes:
-        if (not nd.external and nd.vertex.kind == "FFV" and not PARTICLES[nd.ptype].is_fermion
-                and all(nodes[c].external and PARTICLES[nodes[c].ptype].massless for c in nd.children
-                        if PARTICLES[nodes[c].ptype].is_fermion)):
+        if nd.external or PARTICLES[nd.ptype].is_fermion:
+            continue
+        if _massless_pair(nd.vertex.kind, nd.children):
+            conserved.add(nd.id)
+        elif PARTICLES[nd.ptype].is_vector and nd.id in uses and all(
+                len(u) == 3 and _massless_pair(u[0], u[1]) for u in uses[nd.id]):
             conserved.add(nd.id)
     prog = Program(name, legs, nodes, amps, live, node_variants, amp_terms, coeffs, basis, cnum, den, avg,
                    phases={nid: _phase(nodes, nid, pcache) for nid in range(len(nodes))}, conserved=conserved)
