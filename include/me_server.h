@@ -22,6 +22,19 @@
  *   - sums each request's per-block partials in a fixed order, so a request's
  *     results do not depend on what else runs: alone or in a mix, |M|^2 and
  *     the sums are bit-identical.
+ * Persistent mode (config.persistent = 1).  Instead of one graph launch per chunk,
+ * each slot becomes a lane that runs one persistent kernel for one process at a
+ * time (launched as a captured CUDA graph: claim-counter reset and kernel).  The
+ * kernel's blocks claim items -- tiles of admitted requests -- from a queue in
+ * page-locked host memory that the scheduler keeps filling while the kernel runs:
+ * requests of that process that arrive meanwhile join the running kernel, their
+ * tiles interleaved round-robin with the others' a little ahead of the blocks'
+ * claims.  The block finishing a request's last tile sums its tile partials in tile
+ * order and publishes the sums; the scheduler closes the queue when it has nothing
+ * left to publish and the kernel ends.  A lane's kernel takes the SMs' resident
+ * blocks divided by the number of lanes running.  The tile size (points per item)
+ * and the resident blocks per SM come from an autotuner per process.  A block that
+ * waits spin_limit_us for an item fails the lane (ME_ERR_TIMEOUT) rather than hang.
  * One scheduler thread owns all device work; the entry points may be called
  * from any host thread.  Latencies are host-clock times in ms since
  * me_server_create.  The paper has no serving layer: this interface is the
@@ -43,6 +56,14 @@ typedef struct {
                              requests' buffers (0: 40 GiB) */
   int32_t n_slots;        /* CUDA streams with a chunk in flight at once, 1..16 (0: 4) */
   int32_t max_requests;   /* requests admitted at once, 1..65536 (0: 4096) */
+  int32_t persistent;     /* 1: persistent lanes (below) for every process that has a persistent
+                             kernel; the others (all-gluon processes) keep the chunk launches */
+  int32_t spin_limit_us;  /* persistent lanes: longest a block of the kernel waits for its next
+                             item (about 1 us per poll) before it gives up, 1..10^7 (0: 500000);
+                             requests it leaves unfinished fail with ME_ERR_TIMEOUT */
+  int32_t inject_feeder_stall; /* failure injection for tests: 1 = the scheduler never publishes
+                             items to a running lane nor closes it, so its kernel's waits run out */
+  int32_t pad_;
 } me_server_config;
 
 typedef struct {
@@ -77,6 +98,9 @@ typedef struct {
   int64_t points_done;     /* accepted points of completed requests */
   int64_t launches;        /* chunk launches (each: phase-space and |M|^2 kernels) */
   int64_t graph_launches;  /* of those, launched as the slot's instantiated CUDA graph of the step */
+  int64_t lane_launches;   /* persistent mode: persistent kernels started (each a graph launch) */
+  int64_t lane_items;      /* persistent mode: tiles published to running kernels */
+  int64_t lane_timeouts;   /* persistent mode: kernels that ended because a wait ran out */
 } me_server_stats;
 
 /* Start a server on the caller's current CUDA device.  cfg may be NULL (defaults). */
@@ -84,7 +108,8 @@ me_status me_server_create(const me_server_config* cfg, me_server* out);
 
 /* Create the process (if new) and run the chunk autotuner for it now, on the
  * calling thread, so that the first request does not pay for it.  kin: the
- * generator and cuts to tune with.  *chunk (may be NULL) receives the choice. */
+ * generator and cuts to tune with.  *chunk (may be NULL) receives the choice:
+ * points per launch (chunk mode), or points per tile (persistent mode). */
 me_status me_server_warm(me_server s, const char* process, int32_t precision, const me_kin* kin, int64_t* chunk);
 
 /* Queue a request; returns at once with a ticket.  Argument errors (unknown

@@ -46,7 +46,9 @@ class me_info_t(ctypes.Structure):
 
 
 class me_server_config(ctypes.Structure):
-    _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("n_slots", ctypes.c_int32), ("max_requests", ctypes.c_int32)]
+    _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("n_slots", ctypes.c_int32), ("max_requests", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("spin_limit_us", ctypes.c_int32),
+                ("inject_feeder_stall", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class me_request(ctypes.Structure):
@@ -65,7 +67,8 @@ class me_server_stats(ctypes.Structure):
     _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64),
                 ("bytes_peak", ctypes.c_uint64), ("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
                 ("completed", ctypes.c_int64), ("waiting", ctypes.c_int64), ("active", ctypes.c_int64),
-                ("points_done", ctypes.c_int64), ("launches", ctypes.c_int64), ("graph_launches", ctypes.c_int64)]
+                ("points_done", ctypes.c_int64), ("launches", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+                ("lane_launches", ctypes.c_int64), ("lane_items", ctypes.c_int64), ("lane_timeouts", ctypes.c_int64)]
 
 
 ME_FP64, ME_MIXED = 0, 1
@@ -271,9 +274,10 @@ def me_last_error():
 # ---------------------------------------------------------------------------
 # request server (include/me_server.h)
 # ---------------------------------------------------------------------------
-def me_server_create(mem_cap_bytes=0, n_slots=0, max_requests=0):
+def me_server_create(mem_cap_bytes=0, n_slots=0, max_requests=0, persistent=0, spin_limit_us=0,
+                     inject_feeder_stall=0):
     L = load()
-    cfg = me_server_config(mem_cap_bytes, n_slots, max_requests)
+    cfg = me_server_config(mem_cap_bytes, n_slots, max_requests, persistent, spin_limit_us, inject_feeder_stall, 0)
     s = ctypes.c_void_p()
     _check(L.me_server_create(ctypes.byref(cfg), ctypes.byref(s)))
     return s.value

@@ -55,6 +55,47 @@ struct StepArgs {
   double* vg_w;           // grid steps: [m] weight of each point
 };
 
+// Persistent serving (request server, persistent mode).  A lane's kernel claims
+// items (tiles of requests) one at a time from a queue that the host fills while the
+// kernel runs.  Items, the per-request records, the kinematics table and the control
+// words live in page-locked host memory mapped into the device; the host writes an
+// item and its request record before it publishes the item by raising `published`
+// (release), and the kernel reads `published` with acquire semantics.
+struct ServeItem {
+  uint64_t seed, offset;  // request key; counter of the request's first point
+  int64_t n;              // points of the request (stride of its momentum output)
+  int64_t first;          // index of the tile's first point within the request
+  int32_t count;          // points of the tile
+  int32_t req;            // request record
+  int32_t tile;           // partial slot of the tile within the request
+  int32_t kin;            // index into the kinematics table
+};
+
+struct ServeReq {
+  double* partials;        // device, 3 doubles per tile
+  double* me2;             // device [n] or null
+  double* mom;             // device [n_ext * 4][n] or null
+  int* status;             // device: set to 1 if a point exhausts its redraws
+  uint32_t* tiles_done;    // device counter, zero between requests
+  int32_t tiles;           // tiles of the request
+  int32_t pad_;
+  double* totals;          // mapped host [4]: sum w, sum w^2, draws, redraw status
+  uint32_t* done;          // mapped host: set to 1 (release) once totals hold the request's sums
+};
+
+struct ServeCtl {
+  const ServeItem* items;      // mapped host
+  const uint32_t* published;   // mapped host: items [0, published) are complete
+  const uint32_t* closed;      // mapped host: nonzero once no further item will be published
+  uint32_t* claim;             // device: next item index to hand out
+  const ServeReq* reqs;        // mapped host
+  const KinDev* kins;          // mapped host
+  uint32_t* timed_out;         // mapped host: set to 1 by a block whose wait ran out
+  uint32_t* claimed;           // mapped host: a recent claim index + 1 (how far the blocks have got)
+  uint64_t spin_limit;         // waits of about 1 us a block may spend on one claim
+  int32_t tile_points;         // points per item (a multiple of kThreads)
+};
+
 struct ProcessDesc {
   const char* name;
   int n_ext;
@@ -72,6 +113,9 @@ struct ProcessDesc {
                              int eval_me, cudaStream_t s, int grid);
   cudaError_t (*launch_step)(int prec, const KinDev* kin, const StepArgs* a, const double* params, cudaStream_t s,
                              int grid_ps, int grid_me, cudaEvent_t ev_mid);
+  // persistent serving kernel (null for processes without one); blocks_per_sm: resident blocks of it
+  cudaError_t (*launch_serve)(int prec, const ServeCtl* ctl, const double* params, cudaStream_t s, int grid);
+  int (*serve_blocks_per_sm)(int prec);
 };
 
 }  // namespace me

@@ -43,7 +43,17 @@ double now_ms(std::chrono::steady_clock::time_point t0) {
 struct Proc {
   me_handle h = nullptr;
   int64_t chunk = 0;  // 0: not tuned yet
+  // persistent mode: the process has a persistent kernel; its autotuned tile (points per
+  // queue item) and resident blocks per SM
+  bool serve = false;
+  int64_t tile = 0;
+  int bps = 0;
 };
+
+// lane capacities (page-locked host memory of every lane)
+constexpr uint32_t kLaneItems = 1u << 18;
+constexpr int kLaneReqs = 1024;
+constexpr int kLaneKins = 32;
 
 enum class RState { Waiting, Active, Final, Done };
 
@@ -68,6 +78,34 @@ struct Request {
   int stage = -1;  // pinned staging slot index
   cudaEvent_t ready = nullptr;
   me_request_result res{};
+  // persistent mode
+  struct Lane* lane = nullptr;
+  int lane_slot = -1, lane_kin = -1;
+  int64_t tiles = 0, tiles_published = 0;
+};
+
+// A persistent lane: one slot's persistent kernel for one process at a time, fed through a
+// queue in page-locked host memory mapped into the device (layout: me_internal.h).
+struct Lane {
+  me::ServeItem* items = nullptr;  // [kLaneItems]
+  me::ServeReq* reqs = nullptr;    // [kLaneReqs]
+  me::KinDev* kins = nullptr;      // [kLaneKins]
+  uint32_t* ctl = nullptr;         // [0] published, [1] closed, [2] timed_out, [3] claim hint
+  double* totals = nullptr;        // [kLaneReqs][4]
+  uint32_t* done = nullptr;        // [kLaneReqs]
+  me::ServeCtl dctl{};             // device view (pointers as the kernel sees them)
+  uint32_t* d_claim = nullptr;
+  uint32_t* d_tiles_done = nullptr;
+  const Proc* proc = nullptr;
+  int grid = 0;
+  bool running = false, closed = false;
+  uint32_t n_items = 0;
+  int n_kins = 0;
+  size_t rr = 0;
+  std::vector<int> free_req;
+  std::vector<Request*> in;        // requests with a record in this lane
+  cudaEvent_t ev_end = nullptr;
+  std::map<std::pair<const Proc*, int>, cudaGraphExec_t> graphs;  // by (process, grid)
 };
 
 // The step of one process and generator kind on one slot as an instantiated CUDA
@@ -90,7 +128,153 @@ struct Slot {
   Request* req = nullptr;  // request whose chunk (or final reduction) is in flight
   bool final = false;
   std::map<std::pair<const Proc*, int>, SlotGraph> graphs;  // by (process, generator kind)
+  std::unique_ptr<Lane> lane;  // persistent mode
 };
+
+// host stores and loads that order the mapped queue against the device's acquire/release
+inline void store_release(uint32_t* p, uint32_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+inline uint32_t load_acquire(const uint32_t* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+
+template <class T>
+cudaError_t mapped_alloc(T** host, size_t count) {
+  cudaError_t e = cudaHostAlloc((void**)host, sizeof(T) * count, cudaHostAllocMapped | cudaHostAllocPortable);
+  if (e == cudaSuccess) std::memset((void*)*host, 0, sizeof(T) * count);
+  return e;
+}
+template <class T>
+T* dev_view(T* host) {
+  void* d = nullptr;
+  return cudaHostGetDevicePointer(&d, (void*)host, 0) == cudaSuccess ? static_cast<T*>(d) : nullptr;
+}
+
+cudaError_t lane_init(Lane& L, uint64_t spin_limit) {
+  cudaError_t e = mapped_alloc(&L.items, kLaneItems);
+  if (e == cudaSuccess) e = mapped_alloc(&L.reqs, kLaneReqs);
+  if (e == cudaSuccess) e = mapped_alloc(&L.kins, kLaneKins);
+  if (e == cudaSuccess) e = mapped_alloc(&L.ctl, 4);
+  if (e == cudaSuccess) e = mapped_alloc(&L.totals, 4 * (size_t)kLaneReqs);
+  if (e == cudaSuccess) e = mapped_alloc(&L.done, kLaneReqs);
+  if (e == cudaSuccess) e = cudaMalloc(&L.d_claim, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&L.d_tiles_done, sizeof(uint32_t) * kLaneReqs);
+  if (e == cudaSuccess) e = cudaMemset(L.d_tiles_done, 0, sizeof(uint32_t) * kLaneReqs);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.ev_end, cudaEventDisableTiming);
+  if (e != cudaSuccess) return e;
+  L.dctl.items = dev_view(L.items);
+  L.dctl.reqs = dev_view(L.reqs);
+  L.dctl.kins = dev_view(L.kins);
+  uint32_t* c = dev_view(L.ctl);
+  L.dctl.published = c;
+  L.dctl.closed = c + 1;
+  L.dctl.timed_out = c + 2;
+  L.dctl.claimed = c + 3;
+  L.dctl.claim = L.d_claim;
+  L.dctl.spin_limit = spin_limit;
+  if (!L.dctl.items || !L.dctl.reqs || !L.dctl.kins || !c) return cudaErrorInvalidValue;
+  for (int i = kLaneReqs - 1; i >= 0; --i) L.free_req.push_back(i);
+  return cudaSuccess;
+}
+
+void lane_free(Lane& L) {
+  for (auto& kv : L.graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  L.graphs.clear();
+  if (L.items) cudaFreeHost(L.items);
+  if (L.reqs) cudaFreeHost(L.reqs);
+  if (L.kins) cudaFreeHost(L.kins);
+  if (L.ctl) cudaFreeHost(L.ctl);
+  if (L.totals) cudaFreeHost(L.totals);
+  if (L.done) cudaFreeHost(L.done);
+  if (L.d_claim) cudaFree(L.d_claim);
+  if (L.d_tiles_done) cudaFree(L.d_tiles_done);
+  if (L.ev_end) cudaEventDestroy(L.ev_end);
+  L = Lane{};
+}
+
+// queue reset for a new kernel (no kernel of the lane running)
+void lane_reset(Lane& L) {
+  L.ctl[0] = L.ctl[1] = L.ctl[2] = L.ctl[3] = 0u;
+  L.n_items = 0;
+  L.n_kins = 0;
+  L.closed = false;
+  L.rr = 0;
+}
+
+// record of request slot r of the lane, pointing the kernel at the request's buffers
+void lane_record(Lane& L, int r, double* partials, double* me2, double* mom, int* status, int64_t tiles) {
+  me::ServeReq& q = L.reqs[r];
+  q.partials = partials;
+  q.me2 = me2;
+  q.mom = mom;
+  q.status = status;
+  q.tiles_done = L.d_tiles_done + r;
+  q.tiles = (int32_t)tiles;
+  q.totals = dev_view(L.totals) + 4 * r;
+  q.done = dev_view(L.done) + r;
+  L.done[r] = 0u;
+}
+
+// kinematics table index of kin in the lane (added if new; -1 if the table is full)
+int lane_kin(Lane& L, const me::KinDev& k) {
+  for (int i = 0; i < L.n_kins; ++i)
+    if (std::memcmp(&L.kins[i], &k, sizeof(k)) == 0) return i;
+  if (L.n_kins >= kLaneKins) return -1;
+  L.kins[L.n_kins] = k;
+  return L.n_kins++;
+}
+
+// item of tile t (points [t * tile, ...)) of a request
+me::ServeItem lane_item(uint64_t seed, uint64_t offset, int64_t n, int64_t tile, int64_t t, int req, int kin) {
+  me::ServeItem it{};
+  it.seed = seed;
+  it.offset = offset;
+  it.n = n;
+  it.first = t * tile;
+  it.count = (int32_t)std::min<int64_t>(tile, n - it.first);
+  it.req = req;
+  it.tile = (int32_t)t;
+  it.kin = kin;
+  return it;
+}
+
+// The lane's kernel for process p with `grid` blocks as a captured graph: the claim counter
+// reset and the persistent kernel (first use per process and grid only).
+cudaGraphExec_t lane_graph(Lane& L, const Proc* p, int grid, int64_t tile, cudaStream_t st) {
+  const auto key = std::make_pair(p, grid);
+  auto it = L.graphs.find(key);
+  if (it != L.graphs.end()) return it->second;
+  me::ServeCtl c = L.dctl;
+  c.tile_points = (int32_t)tile;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    cudaError_t e1 = cudaMemsetAsync(L.d_claim, 0, sizeof(uint32_t), st);
+    cudaError_t e2 = e1 == cudaSuccess ? p->h->desc->launch_serve(p->h->prec, &c, p->h->cvals.data(), st, grid) : e1;
+    cudaError_t e3 = cudaStreamEndCapture(st, &g);
+    if (e2 != cudaSuccess || e3 != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaGetLastError();
+  L.graphs[key] = ex;
+  return ex;
+}
+
+// Start the lane's kernel: the captured graph, or the two operations directly if no graph
+// could be made; ev_end marks its end.
+cudaError_t lane_launch(Lane& L, const Proc* p, int grid, int64_t tile, cudaStream_t st, bool* as_graph) {
+  cudaGraphExec_t ex = lane_graph(L, p, grid, tile, st);
+  cudaError_t e;
+  *as_graph = ex != nullptr;
+  if (ex) {
+    e = cudaGraphLaunch(ex, st);
+  } else {
+    me::ServeCtl c = L.dctl;
+    c.tile_points = (int32_t)tile;
+    e = cudaMemsetAsync(L.d_claim, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = p->h->desc->launch_serve(p->h->prec, &c, p->h->cvals.data(), st, grid);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(L.ev_end, st);
+  return e;
+}
 
 }  // namespace
 
@@ -118,6 +302,10 @@ struct me_server_s {
   std::thread worker;
   size_t rr = 0;
 
+  int n_sms = 0;
+  bool persistent_step();
+  void lane_collect(Lane& L);
+  bool lane_place(Request* q);
   void run();
   bool admit(Request* q);
   bool launch_chunk(Slot& sl, Request* q);
@@ -186,6 +374,78 @@ me_status tune_chunk(me_handle h, const me::KinDev& kin, cudaStream_t s, int64_t
   return ME_OK;
 }
 
+// Persistent mode: the tile (points per queue item) and resident blocks per SM of a process's
+// persistent kernel, by timing it on a temporary lane whose queue holds one request of 2^18
+// points, fully published and closed before the launch (so no block waits): tiles of 256, 1024
+// and 4096 points at one block per SM and at the most that fit; the fastest per point wins, and
+// the smallest tile within 5 % of it (finer tiles interleave requests more finely).
+me_status tune_serve(Proc* p, const me::KinDev& kin, int n_sms, cudaStream_t s) {
+  me_handle h = p->h;
+  const int bmax = h->desc->serve_blocks_per_sm(h->prec);
+  if (bmax < 1) return fail(ME_ERR_CUDA, "server: the persistent kernel does not fit on an SM");
+  const int64_t n = 1 << 18;
+  const int64_t tiles_max = n / 256;
+  Lane L;
+  double* part = nullptr;
+  int* status = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = lane_init(L, 1u << 20);
+  if (e == cudaSuccess) e = cudaMalloc(&part, 3 * sizeof(double) * (size_t)tiles_max);
+  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double best = 0.0;
+  int64_t best_tile = 1024;
+  int best_b = bmax;
+  std::vector<std::pair<double, std::pair<int64_t, int>>> runs;
+  const std::vector<int> blocks = bmax > 1 ? std::vector<int>{1, bmax} : std::vector<int>{1};
+  for (int64_t tile : {256, 1024, 4096}) {
+    for (int b : blocks) {
+      float tbest = 0.0f;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first repetition warms up
+        lane_reset(L);
+        const int64_t tiles = (n + tile - 1) / tile;
+        lane_record(L, 0, part, nullptr, nullptr, status, tiles);
+        const int k = lane_kin(L, kin);
+        for (int64_t t = 0; t < tiles; ++t) L.items[L.n_items++] = lane_item(777u, (uint64_t)rep * n, n, tile, t, 0, k);
+        store_release(&L.ctl[0], L.n_items);
+        store_release(&L.ctl[1], 1u);
+        me::ServeCtl c = L.dctl;
+        c.tile_points = (int32_t)tile;
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.d_claim, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = h->desc->launch_serve(h->prec, &c, h->cvals.data(), s, n_sms * b);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && load_acquire(&L.done[0]) != 1u) e = cudaErrorUnknown;
+        if (rep == 1) tbest = ms;
+      }
+      if (e != cudaSuccess) break;
+      runs.push_back({(double)tbest, {tile, b}});
+    }
+  }
+  if (part) cudaFree(part);
+  if (status) cudaFree(status);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  lane_free(L);
+  if (e != cudaSuccess) return cuda_fail(e, "server persistent autotune");
+  best = runs[0].first;
+  for (auto& r : runs) best = r.first < best ? r.first : best;
+  for (auto& r : runs)
+    if (r.first <= 1.05 * best) {
+      best_tile = r.second.first;
+      best_b = r.second.second;
+      break;
+    }
+  p->tile = best_tile;
+  p->bps = best_b;
+  return ME_OK;
+}
+
 // process handle (cached per process and precision) with its chunk tuned for kin
 me_status get_proc(me_server s, const char* process, int32_t prec, const me_kin* kin, Proc** out, cudaStream_t st) {
   me_handle h = nullptr;
@@ -207,9 +467,15 @@ me_status get_proc(me_server s, const char* process, int32_t prec, const me_kin*
   if (p->chunk == 0) {
     me::KinDev k;
     if ((r = me::rt::make_kin(p->h, kin, k)) != ME_OK) return r;
-    int64_t c = 0;
-    if ((r = tune_chunk(p->h, k, st, &c)) != ME_OK) return r;
-    p->chunk = c;
+    if (s->cfg.persistent && p->h->desc->launch_serve) {
+      if ((r = tune_serve(p, k, s->n_sms, st)) != ME_OK) return r;
+      p->serve = true;
+      p->chunk = p->tile;
+    } else {
+      int64_t c = 0;
+      if ((r = tune_chunk(p->h, k, st, &c)) != ME_OK) return r;
+      p->chunk = c;
+    }
   }
   *out = p;
   return ME_OK;
@@ -246,6 +512,7 @@ bool me_server_s::admit(Request* q) {
     return true;
   }
   q->state = RState::Active;
+  if (q->tiles > 0) q->next_chunk = q->nchunks;  // persistent: no chunk launches
   active.push_back(q);
   return true;
 }
@@ -387,6 +654,158 @@ void me_server_s::release(Request* q) {
   q->bytes = 0;
 }
 
+// completed requests of a lane: the kernel published their sums (done flag, acquire)
+void me_server_s::lane_collect(Lane& L) {
+  for (size_t i = 0; i < L.in.size();) {
+    Request* q = L.in[i];
+    if (load_acquire(&L.done[q->lane_slot]) != 1u) {
+      ++i;
+      continue;
+    }
+    const double* t = L.totals + 4 * q->lane_slot;
+    q->res.acc.sum_w = t[0];
+    q->res.acc.sum_w2 = t[1];
+    q->res.acc.n_acc = q->r.n;
+    q->res.acc.n_try = (int64_t)llround(t[2]);
+    L.free_req.push_back(q->lane_slot);
+    q->lane = nullptr;
+    q->lane_slot = -1;
+    L.in.erase(L.in.begin() + (long)i);
+    finish(q, t[3] != 0.0 ? ME_ERR_TIMEOUT : ME_OK);
+  }
+}
+
+// a lane for an admitted persistent request: a running lane of its process that is still open
+// and has room, else an idle slot whose persistent kernel is started now (graph launch)
+bool me_server_s::lane_place(Request* q) {
+  Lane* L = nullptr;
+  int kin = -1;
+  for (Slot& sl : slots) {
+    Lane& c = *sl.lane;
+    if (!c.running || c.closed || c.proc != q->proc || c.free_req.empty()) continue;
+    int64_t unpublished = 0;  // queue room the lane's requests still need
+    for (Request* x : c.in) unpublished += x->tiles - x->tiles_published;
+    if ((int64_t)c.n_items + unpublished + q->tiles > (int64_t)kLaneItems) continue;
+    if ((kin = lane_kin(c, q->kin)) < 0) continue;
+    L = &c;
+    break;
+  }
+  if (!L) {
+    Slot* free_slot = nullptr;
+    int running = 0;
+    for (Slot& sl : slots) {
+      if (sl.lane->running) ++running;
+      else if (!free_slot && !sl.req) free_slot = &sl;
+    }
+    if (!free_slot || q->tiles > (int64_t)kLaneItems) return false;
+    Lane& c = *free_slot->lane;
+    lane_reset(c);
+    c.proc = q->proc;
+    // the SMs' resident blocks of this kernel, shared among the lanes running
+    c.grid = std::max(1, n_sms * q->proc->bps / (running + 1));
+    bool as_graph = false;
+    const cudaError_t e = lane_launch(c, q->proc, c.grid, q->proc->tile, free_slot->stream, &as_graph);
+    if (e != cudaSuccess) {
+      me::rt::fail(ME_ERR_CUDA, std::string("server lane launch: ") + cudaGetErrorString(e));
+      finish(q, ME_ERR_CUDA);
+      return true;
+    }
+    c.running = true;
+    ++st.lane_launches;
+    if (as_graph) ++st.graph_launches;
+    kin = lane_kin(c, q->kin);
+    L = &c;
+  }
+  const int slot = L->free_req.back();
+  L->free_req.pop_back();
+  lane_record(*L, slot, q->d_partials, q->d_me2, q->d_mom, q->d_status, q->tiles);
+  q->lane = L;
+  q->lane_slot = slot;
+  q->lane_kin = kin;
+  q->tiles_published = 0;
+  q->res.t_start_ms = now_ms(t0);
+  L->in.push_back(q);
+  return true;
+}
+
+// One pass of the persistent lanes: ends of kernels, completed requests, placement of
+// admitted requests, publication of tiles a little ahead of the blocks' claims (round-robin
+// over a lane's requests), and closing of lanes with nothing left to publish.
+bool me_server_s::persistent_step() {
+  bool progress = false;
+  for (Slot& sl : slots) {
+    Lane& L = *sl.lane;
+    if (!L.running || cudaEventQuery(L.ev_end) == cudaErrorNotReady) continue;
+    cudaGetLastError();
+    progress = true;
+    L.running = false;
+    lane_collect(L);
+    const bool timed_out = load_acquire(&L.ctl[2]) != 0u;
+    if (timed_out) ++st.lane_timeouts;
+    for (Request* q : L.in) {
+      L.free_req.push_back(q->lane_slot);
+      q->lane = nullptr;
+      q->lane_slot = -1;
+      me::rt::fail(timed_out ? ME_ERR_TIMEOUT : ME_ERR_CUDA,
+                   timed_out ? "server: a persistent kernel's wait for work ran out"
+                             : "server: a persistent kernel ended before its requests");
+      finish(q, timed_out ? ME_ERR_TIMEOUT : ME_ERR_CUDA);
+    }
+    L.in.clear();
+    L.proc = nullptr;
+  }
+  for (Slot& sl : slots)
+    if (sl.lane->running) lane_collect(*sl.lane);
+  for (Request* q : std::vector<Request*>(active)) {
+    if (stop || q->state != RState::Active || q->tiles == 0 || q->lane) continue;
+    if (cudaEventQuery(q->ready) == cudaErrorNotReady) continue;  // its buffers are still being set up
+    if (lane_place(q)) progress = true;
+  }
+  if (cfg.inject_feeder_stall) return progress;
+  for (Slot& sl : slots) {
+    Lane& L = *sl.lane;
+    if (!L.running || L.closed) continue;
+    const uint32_t claimed = __atomic_load_n(&L.ctl[3], __ATOMIC_RELAXED);
+    const uint32_t window = (uint32_t)(2 * L.grid + 8);
+    const uint32_t target = std::min<uint32_t>(kLaneItems, claimed + window);
+    const uint32_t before = L.n_items;
+    bool more = true;
+    while (more && L.n_items < target) {
+      more = false;
+      for (size_t k = 0; k < L.in.size() && L.n_items < target; ++k) {
+        Request* q = L.in[(L.rr + k) % L.in.size()];
+        if (q->tiles_published >= q->tiles) continue;
+        L.items[L.n_items++] = lane_item(q->r.seed, q->r.counter_offset, q->r.n, q->proc->tile, q->tiles_published++,
+                                         q->lane_slot, q->lane_kin);
+        more = true;
+      }
+      L.rr = L.in.empty() ? 0 : (L.rr + 1) % L.in.size();
+    }
+    if (L.n_items != before) {
+      store_release(&L.ctl[0], L.n_items);
+      st.lane_items += L.n_items - before;
+      progress = true;
+    }
+    // nothing left to publish and no admitted request of its process that this lane could still
+    // take: close (a request that does not fit the lane's remaining queue goes to a new lane)
+    bool left = false;
+    int64_t unpublished = 0;
+    for (Request* q : L.in) {
+      left = left || q->tiles_published < q->tiles;
+      unpublished += q->tiles - q->tiles_published;
+    }
+    for (Request* q : active)
+      left = left || (q->state == RState::Active && q->tiles && !q->lane && q->proc == L.proc &&
+                      (int64_t)L.n_items + unpublished + q->tiles <= (int64_t)kLaneItems && !L.free_req.empty());
+    if (!left || stop) {
+      store_release(&L.ctl[1], 1u);
+      L.closed = true;
+      progress = true;
+    }
+  }
+  return progress;
+}
+
 void me_server_s::run() {
   cudaSetDevice(device);
   std::unique_lock<std::mutex> lock(mu);
@@ -406,6 +825,21 @@ void me_server_s::run() {
       }
       q->proc = p;
       me::rt::make_kin(p->h, &q->r.kin, q->kin);  // checked at submit
+      if (cfg.persistent && p->serve && (q->r.n + p->tile - 1) / p->tile <= (int64_t)kLaneItems / 2) {
+        // a persistent lane takes it in tiles; its partials are one per tile
+        const int n_ext = p->h->desc->n_ext;
+        q->chunk = p->tile;
+        q->tiles = (q->r.n + p->tile - 1) / p->tile;
+        q->nchunks = q->tiles;
+        q->grid_me = 1;
+        q->res.chunk = p->tile;
+        q->ws_need = 0;
+        q->need = 64 + 3 * sizeof(double) * (uint64_t)q->tiles + (q->r.want_me2 ? 8ull * (uint64_t)q->r.n : 0) +
+                  (q->r.want_momenta ? 32ull * (uint64_t)n_ext * (uint64_t)q->r.n : 0);
+        waiting.push_back(q);
+        progress = true;
+        continue;
+      }
       q->chunk = std::min<int64_t>(p->chunk, q->r.n);
       q->nchunks = (q->r.n + q->chunk - 1) / q->chunk;
       // one launch shape per process (its autotuned chunk), so that its captured graph serves
@@ -422,7 +856,7 @@ void me_server_s::run() {
       progress = true;
     }
     bool inflight = false;
-    for (Slot& sl : slots) inflight = inflight || sl.req;
+    for (Slot& sl : slots) inflight = inflight || sl.req || (sl.lane && sl.lane->running);
     // admission, first come first served; a request that does not fit even with nothing
     // else admitted is refused
     while (!stop && !waiting.empty()) {
@@ -475,9 +909,10 @@ void me_server_s::run() {
       sl.req = q;
       sl.final = true;
     }
+    if (cfg.persistent && persistent_step()) progress = true;
     // free slots take the next chunk, round-robin over the admitted requests
     for (Slot& sl : slots) {
-      if (stop || sl.req) continue;
+      if (stop || sl.req || (sl.lane && sl.lane->running)) continue;
       Request* pick = nullptr;
       for (size_t k = 0; k < active.size() && !pick; ++k) {
         Request* q = active[(rr + k) % active.size()];
@@ -498,7 +933,9 @@ void me_server_s::run() {
       }
     }
     inflight = false;
-    for (Slot& sl : slots) inflight = inflight || sl.req;
+    for (Slot& sl : slots) inflight = inflight || sl.req || (sl.lane && sl.lane->running);
+    // admitted persistent requests whose buffers are still being set up: poll, do not sleep
+    for (Request* q : active) inflight = inflight || (q->tiles && !q->lane && q->state == RState::Active);
     st.waiting = (int64_t)waiting.size();
     st.active = (int64_t)active.size();
     if (stop && !inflight) {
@@ -513,7 +950,7 @@ void me_server_s::run() {
     if (!progress) {
       if (inflight) {
         lock.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        std::this_thread::sleep_for(std::chrono::microseconds(cfg.persistent ? 5 : 20));
         lock.lock();
       } else {
         cv_submit.wait_for(lock, std::chrono::milliseconds(2));
@@ -535,6 +972,10 @@ me_status me_server_create(const me_server_config* cfg, me_server* out) {
   if (c.n_slots < 1 || c.n_slots > 16) return fail(ME_ERR_ARG, "me_server_create: n_slots must be 1..16");
   if (c.max_requests < 1 || c.max_requests > 65536)
     return fail(ME_ERR_ARG, "me_server_create: max_requests must be 1..65536");
+  if (c.spin_limit_us == 0) c.spin_limit_us = 500000;
+  if (c.persistent != 0 && c.persistent != 1) return fail(ME_ERR_ARG, "me_server_create: persistent must be 0 or 1");
+  if (c.spin_limit_us < 1 || c.spin_limit_us > 10000000)
+    return fail(ME_ERR_ARG, "me_server_create: spin_limit_us must be 1..10^7");
   auto s = std::make_unique<me_server_s>();
   s->cfg = c;
   s->t0 = std::chrono::steady_clock::now();
@@ -550,12 +991,17 @@ me_status me_server_create(const me_server_config* cfg, me_server* out) {
   cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   if ((e = cudaStreamCreateWithFlags(&s->admin, cudaStreamNonBlocking)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamCreate");
+  if ((e = cudaDeviceGetAttribute(&s->n_sms, cudaDevAttrMultiProcessorCount, s->device)) != cudaSuccess)
+    return cuda_fail(e, "cudaDeviceGetAttribute");
   s->slots.resize(c.n_slots);
   for (Slot& sl : s->slots) {
     if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamCreate");
     if ((e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(e, "cudaEventCreate");
+    sl.lane = std::make_unique<Lane>();
+    if (c.persistent && (e = lane_init(*sl.lane, (uint64_t)c.spin_limit_us)) != cudaSuccess)
+      return fail(ME_ERR_OOM, "me_server_create: lane queues");
   }
   if ((e = cudaMallocHost(&s->h_stage, 8 * sizeof(double) * (size_t)c.max_requests)) != cudaSuccess)
     return fail(ME_ERR_OOM, "me_server_create: pinned staging");
@@ -678,6 +1124,7 @@ void me_server_destroy(me_server s) {
     }
     if (sl.ws) cudaFreeAsync(sl.ws, sl.stream);
     if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.lane) lane_free(*sl.lane);
     if (sl.ev) cudaEventDestroy(sl.ev);
     if (sl.stream) cudaStreamDestroy(sl.stream);
   }

@@ -59,8 +59,9 @@ __host__ __device__ __forceinline__ P4<float> p4f(const df* p) {
   return P4<float>{to_float(p[0]), to_float(p[1]), to_float(p[2]), to_float(p[3])};
 }
 
-// fixed-order block sum of three doubles into out[blockIdx.x * 3 + {0,1,2}]
-__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* out) {
+// fixed-order block sum of three doubles into out[slot * 3 + {0,1,2}] (slot: the block's index by default)
+__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* out, int64_t slot = -1) {
+  if (slot < 0) slot = blockIdx.x;
   __shared__ double sm[3][kThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -74,9 +75,9 @@ __device__ __forceinline__ void block_reduce3(double a, double b, double c, doub
   if (threadIdx.x == 0) {
     double s0 = 0, s1 = 0, s2 = 0;
     for (int w = 0; w < kThreads / 32; ++w) { s0 += sm[0][w]; s1 += sm[1][w]; s2 += sm[2][w]; }
-    out[3 * blockIdx.x + 0] = s0;
-    out[3 * blockIdx.x + 1] = s1;
-    out[3 * blockIdx.x + 2] = s2;
+    out[3 * slot + 0] = s0;
+    out[3 * slot + 1] = s1;
+    out[3 * slot + 2] = s2;
   }
 }
 
@@ -105,143 +106,285 @@ __global__ void __launch_bounds__(kThreads) k_eval(const double* __restrict__ mo
   }
 }
 
+// shared memory of one tile of the fused step: accepted momenta (FP64, or double-float
+// hi and lo), weights, draws and the redraw queue
+template <class P, bool MIXED>
+struct XsecTileSmem {
+  double pd[MIXED ? 1 : P::NEXT * 4][kThreads];
+  float ph[MIXED ? P::NEXT * 4 : 1][kThreads];
+  float pl[MIXED ? P::NEXT * 4 : 1][kThreads];
+  double wps[kThreads], shat[kThreads];
+  int tries[kThreads];
+  int q[2][kThreads];
+  int qn[2];
+};
+
+// a thread's Monte Carlo sums (the mixed path sums FP32 weights as double-floats)
+struct XsecSums {
+  double sw = 0.0, sw2 = 0.0, nt = 0.0;
+  df swf = df{0.0f, 0.0f}, sw2f = df{0.0f, 0.0f};
+};
+
+// One tile of the fused step: points [base, base + cnt) (cnt <= kThreads) of a step over
+// events offset + i whose optional outputs have n points per component.  Phase space with
+// redraws through the shared-memory queue, then every thread evaluates |M|^2 of its own
+// point and adds its weight to acc.  Ends with a block barrier.
+template <class P, bool MIXED>
+__device__ __forceinline__ void xsec_tile(const KinDev& kin, uint64_t seed, uint64_t offset, int64_t n, int64_t base,
+                                          int cnt, const PrmT<P, MIXED>& prm, double* __restrict__ me2_out,
+                                          double* __restrict__ mom_out, double* __restrict__ wps_out,
+                                          double* __restrict__ shat_out, int32_t* __restrict__ tries_out, int* status,
+                                          int eval_me, XsecTileSmem<P, MIXED>& sm, XsecSums& acc) {
+  constexpr int NEXT = P::NEXT;
+  if (threadIdx.x == 0) { sm.qn[0] = 0; sm.qn[1] = 0; }
+  if (threadIdx.x < cnt) { sm.wps[threadIdx.x] = 0.0; sm.tries[threadIdx.x] = kin.max_attempts; }
+  __syncthreads();
+  int cur = 0;
+  for (int att = 0;; ++att) {
+    const int nitems = (att == 0) ? cnt : sm.qn[cur];
+    if (nitems == 0) break;
+    if (att >= kin.max_attempts) {
+      if (threadIdx.x == 0) atomicOr(status, 1);
+      break;
+    }
+    const int nxt = cur ^ 1;
+    for (int j = threadIdx.x; j < nitems; j += kThreads) {
+      const int ev = (att == 0) ? j : sm.q[cur][j];
+      const uint64_t event = offset + (uint64_t)(base + ev);
+      double wps = 0.0, shat = 1.0;
+      bool ok;
+      if constexpr (MIXED) {
+        df pm[NEXT][4];
+        ok = draw_point_df<NEXT>(kin, seed, event, att, pm, wps, shat);
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) { sm.ph[k * 4 + m][ev] = pm[k][m].hi; sm.pl[k * 4 + m][ev] = pm[k][m].lo; }
+          }
+        }
+      } else {
+        double pm[NEXT][4];
+        ok = draw_point<NEXT>(kin, seed, event, att, pm, wps, shat);
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) sm.pd[k * 4 + m][ev] = pm[k][m];
+          }
+        }
+      }
+      if (ok) {
+        sm.wps[ev] = wps;
+        sm.shat[ev] = shat;
+        sm.tries[ev] = att + 1;
+      } else {
+        sm.q[nxt][atomicAdd(&sm.qn[nxt], 1)] = ev;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sm.qn[cur] = 0;
+    cur = nxt;
+    __syncthreads();
+  }
+  if (threadIdx.x < cnt) {
+    const int ev = threadIdx.x;
+    const int64_t i = base + ev;
+    const double wps = sm.wps[ev], shat = sm.shat[ev];
+    const int tries = sm.tries[ev];
+    const bool ok = wps > 0.0;
+    double m2 = 0.0;
+    if constexpr (MIXED) {
+      df pm[NEXT][4];
+#pragma unroll
+      for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) pm[k][m] = df{sm.ph[k * 4 + m][ev], sm.pl[k * 4 + m][ev]};
+      }
+      const float m2f = (eval_me && ok) ? P::evalmx(pm, prm) : 0.0f;
+      m2 = (double)m2f;
+      if (mom_out) {
+#pragma unroll
+        for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) mom_out[((int64_t)(k * 4 + m)) * n + i] = to_double(pm[k][m]);
+        }
+      }
+      if (ok) {
+        const df wf = kin.wfactor > 0.0 ? from_double(kin.wfactor)
+                                        : (from_double(wps) * from_double(kin.s_ident * (0.5 * kGeV2pb))) /
+                                              from_double(shat);
+        const float w = m2f * wf.hi;
+        acc.swf = acc.swf + w;
+        acc.sw2f = acc.sw2f + two_prod(w, w);
+      }
+    } else {
+      double pm[NEXT][4];
+#pragma unroll
+      for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) pm[k][m] = sm.pd[k * 4 + m][ev];
+      }
+      if (eval_me && ok) m2 = P::eval64(pm, prm);
+      if (mom_out) {
+#pragma unroll
+        for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) mom_out[((int64_t)(k * 4 + m)) * n + i] = pm[k][m];
+        }
+      }
+    }
+    if constexpr (!MIXED) {
+      const double w = ok ? wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb : 0.0;
+      acc.sw += w;
+      acc.sw2 += w * w;
+    }
+    acc.nt += (double)tries;
+    if (me2_out) me2_out[i] = m2;
+    if (wps_out) wps_out[i] = wps;
+    if (shat_out) shat_out[i] = shat;
+    if (tries_out) tries_out[i] = tries;
+  }
+  __syncthreads();
+}
+
+template <class P, bool MIXED>
+__device__ __forceinline__ void finish_sums(XsecSums& acc) {
+  if constexpr (MIXED) {
+    acc.sw = to_double(acc.swf);
+    acc.sw2 = to_double(acc.sw2f);
+  }
+}
+
 template <class P, bool MIXED>
 __global__ void __launch_bounds__(kThreads) k_xsec(KinDev kin, uint64_t seed, uint64_t offset, int64_t n,
                                                    PrmT<P, MIXED> prm, double* __restrict__ partials,
                                                    double* __restrict__ me2_out, double* __restrict__ mom_out,
                                                    double* __restrict__ wps_out, double* __restrict__ shat_out,
                                                    int32_t* __restrict__ tries_out, int* status, int eval_me) {
-  constexpr int NEXT = P::NEXT;
-  // accepted momenta of the tile: FP64 (hi) or double-float (hi, lo) per component
-  __shared__ double s_pd[MIXED ? 1 : NEXT * 4][kThreads];
-  __shared__ float s_ph[MIXED ? NEXT * 4 : 1][kThreads];
-  __shared__ float s_pl[MIXED ? NEXT * 4 : 1][kThreads];
-  __shared__ double s_wps[kThreads], s_shat[kThreads];
-  __shared__ int s_tries[kThreads];
-  __shared__ int s_q[2][kThreads];
-  __shared__ int s_qn[2];
-  double sw = 0.0, sw2 = 0.0, nt = 0.0;
-  df swf = dfs(0.0f), sw2f = dfs(0.0f);  // mixed path: weights formed and summed as in k_me
+  __shared__ XsecTileSmem<P, MIXED> sm;
+  XsecSums acc;
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t base = tile * kThreads;
     const int cnt = (int)((n - base) < kThreads ? (n - base) : kThreads);
-    if (threadIdx.x == 0) { s_qn[0] = 0; s_qn[1] = 0; }
-    if (threadIdx.x < cnt) { s_wps[threadIdx.x] = 0.0; s_tries[threadIdx.x] = kin.max_attempts; }
-    __syncthreads();
-    int cur = 0;
-    for (int att = 0;; ++att) {
-      const int nitems = (att == 0) ? cnt : s_qn[cur];
-      if (nitems == 0) break;
-      if (att >= kin.max_attempts) {
-        if (threadIdx.x == 0) atomicOr(status, 1);
-        break;
+    xsec_tile<P, MIXED>(kin, seed, offset, n, base, cnt, prm, me2_out, mom_out, wps_out, shat_out, tries_out, status,
+                        eval_me, sm, acc);
+  }
+  finish_sums<P, MIXED>(acc);
+  if (partials) block_reduce3(acc.sw, acc.sw2, acc.nt, partials);
+}
+
+// ---------------------------------------------------------------------------
+// k_serve: the persistent kernel of the request server.  Each block claims queue
+// items (one tile of one request each) until the host closes the queue, runs the
+// fused step on the tile's points, writes the tile's partial sums, and the block
+// that completes the last tile of a request sums its partials in tile order and
+// publishes the totals to the host.  A block that has waited spin_limit times
+// (about 1 us each) for an item that was neither published nor closed sets
+// timed_out and returns: the host sees the kernel end and fails the requests left.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire_sys_u32(const uint32_t* p) {
+  uint32_t v;
+#ifdef __CUDA_ARCH__
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+#else
+  v = *p;
+#endif
+  return v;
+}
+__device__ __forceinline__ void st_release_sys_u32(uint32_t* p, uint32_t v) {
+#ifdef __CUDA_ARCH__
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+#else
+  *p = v;
+#endif
+}
+
+template <class P, bool MIXED>
+__global__ void __launch_bounds__(kThreads) k_serve(ServeCtl c, PrmT<P, MIXED> prm) {
+  __shared__ XsecTileSmem<P, MIXED> sm;
+  __shared__ KinDev s_kin;
+  __shared__ ServeItem s_it;
+  __shared__ ServeReq s_rq;
+  __shared__ int s_state, s_kin_idx, s_last;
+  if (threadIdx.x == 0) s_kin_idx = -1;
+  for (;;) {
+    __syncthreads();  // the previous item is done with every shared buffer
+    if (threadIdx.x == 0) {
+      const uint32_t idx = atomicAdd(c.claim, 1u);
+#ifdef __CUDA_ARCH__
+      asm volatile("st.relaxed.sys.global.u32 [%0], %1;" ::"l"(c.claimed), "r"(idx + 1u) : "memory");
+#endif
+      int state = -2;
+      for (uint64_t it = 0; it <= c.spin_limit; ++it) {
+        if (idx < ld_acquire_sys_u32(c.published)) {
+          state = (int)idx;
+          break;
+        }
+        if (ld_acquire_sys_u32(c.closed)) {  // the host publishes every item before it closes
+          state = idx < ld_acquire_sys_u32(c.published) ? (int)idx : -1;
+          break;
+        }
+#ifdef __CUDA_ARCH__
+        __nanosleep(1000);
+#endif
       }
-      const int nxt = cur ^ 1;
-      for (int j = threadIdx.x; j < nitems; j += kThreads) {
-        const int ev = (att == 0) ? j : s_q[cur][j];
-        const uint64_t event = offset + (uint64_t)(base + ev);
-        double wps = 0.0, shat = 1.0;
-        bool ok;
-        if constexpr (MIXED) {
-          df pm[NEXT][4];
-          ok = draw_point_df<NEXT>(kin, seed, event, att, pm, wps, shat);
-          if (ok) {
-#pragma unroll
-            for (int k = 0; k < NEXT; ++k) {
-#pragma unroll
-              for (int m = 0; m < 4; ++m) { s_ph[k * 4 + m][ev] = pm[k][m].hi; s_pl[k * 4 + m][ev] = pm[k][m].lo; }
-            }
-          }
-        } else {
-          double pm[NEXT][4];
-          ok = draw_point<NEXT>(kin, seed, event, att, pm, wps, shat);
-          if (ok) {
-#pragma unroll
-            for (int k = 0; k < NEXT; ++k) {
-#pragma unroll
-              for (int m = 0; m < 4; ++m) s_pd[k * 4 + m][ev] = pm[k][m];
-            }
-          }
-        }
-        if (ok) {
-          s_wps[ev] = wps;
-          s_shat[ev] = shat;
-          s_tries[ev] = att + 1;
-        } else {
-          s_q[nxt][atomicAdd(&s_qn[nxt], 1)] = ev;
-        }
+      if (state == -2) {
+        st_release_sys_u32(c.timed_out, 1u);
+      } else if (state >= 0) {
+        s_it = c.items[state];
+        s_rq = c.reqs[s_it.req];
       }
-      __syncthreads();
-      if (threadIdx.x == 0) s_qn[cur] = 0;
-      cur = nxt;
-      __syncthreads();
-    }
-    if (threadIdx.x < cnt) {
-      const int ev = threadIdx.x;
-      const int64_t i = base + ev;
-      const double wps = s_wps[ev], shat = s_shat[ev];
-      const int tries = s_tries[ev];
-      const bool ok = wps > 0.0;
-      double m2 = 0.0;
-      if constexpr (MIXED) {
-        df pm[NEXT][4];
-#pragma unroll
-        for (int k = 0; k < NEXT; ++k) {
-#pragma unroll
-          for (int m = 0; m < 4; ++m) pm[k][m] = df{s_ph[k * 4 + m][ev], s_pl[k * 4 + m][ev]};
-        }
-        const float m2f = (eval_me && ok) ? P::evalmx(pm, prm) : 0.0f;
-        m2 = (double)m2f;
-        if (mom_out) {
-#pragma unroll
-          for (int k = 0; k < NEXT; ++k) {
-#pragma unroll
-            for (int m = 0; m < 4; ++m) mom_out[((int64_t)(k * 4 + m)) * n + i] = to_double(pm[k][m]);
-          }
-        }
-        if (ok) {
-          const df wf = kin.wfactor > 0.0 ? from_double(kin.wfactor)
-                                          : (from_double(wps) * from_double(kin.s_ident * (0.5 * kGeV2pb))) /
-                                                from_double(shat);
-          const float w = m2f * wf.hi;
-          swf = swf + w;
-          sw2f = sw2f + two_prod(w, w);
-        }
-      } else {
-        double pm[NEXT][4];
-#pragma unroll
-        for (int k = 0; k < NEXT; ++k) {
-#pragma unroll
-          for (int m = 0; m < 4; ++m) pm[k][m] = s_pd[k * 4 + m][ev];
-        }
-        if (eval_me && ok) m2 = P::eval64(pm, prm);
-        if (mom_out) {
-#pragma unroll
-          for (int k = 0; k < NEXT; ++k) {
-#pragma unroll
-            for (int m = 0; m < 4; ++m) mom_out[((int64_t)(k * 4 + m)) * n + i] = pm[k][m];
-          }
-        }
-      }
-      if constexpr (!MIXED) {
-        const double w = ok ? wps * m2 * kin.s_ident / (2.0 * shat) * kGeV2pb : 0.0;
-        sw += w;
-        sw2 += w * w;
-      }
-      nt += (double)tries;
-      if (me2_out) me2_out[i] = m2;
-      if (wps_out) wps_out[i] = wps;
-      if (shat_out) shat_out[i] = shat;
-      if (tries_out) tries_out[i] = tries;
+      s_state = state;
     }
     __syncthreads();
+    if (s_state < 0) return;
+    const ServeItem it = s_it;
+    if (it.kin != s_kin_idx) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(c.kins + it.kin);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_kin);
+      for (int w = threadIdx.x; w < (int)(sizeof(KinDev) / 4); w += kThreads) dst[w] = src[w];
+      __syncthreads();
+      if (threadIdx.x == 0) s_kin_idx = it.kin;
+    }
+    XsecSums acc;
+    const int64_t end = it.first + it.count;
+    for (int64_t base = it.first; base < end; base += kThreads) {
+      const int cnt = (int)((end - base) < kThreads ? (end - base) : kThreads);
+      xsec_tile<P, MIXED>(s_kin, it.seed, it.offset, it.n, base, cnt, prm, s_rq.me2, s_rq.mom, nullptr, nullptr,
+                          nullptr, s_rq.status, 1, sm, acc);
+    }
+    finish_sums<P, MIXED>(acc);
+    block_reduce3(acc.sw, acc.sw2, acc.nt, s_rq.partials, it.tile);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(s_rq.tiles_done, 1u) + 1u == (uint32_t)s_rq.tiles;
+    }
+    __syncthreads();
+    if (s_last) {
+      // the request's tile partials in a fixed order: thread t sums tiles t, t + kThreads, ...,
+      // then the block's fixed-order reduction (the same for every run of the request)
+      __threadfence();
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+      for (int k = threadIdx.x; k < s_rq.tiles; k += kThreads) {
+        t0 += __ldcg(s_rq.partials + 3 * k);
+        t1 += __ldcg(s_rq.partials + 3 * k + 1);
+        t2 += __ldcg(s_rq.partials + 3 * k + 2);
+      }
+      __shared__ double s_tot[3];
+      block_reduce3(t0, t1, t2, s_tot, 0);
+      if (threadIdx.x == 0) {
+        s_rq.totals[0] = s_tot[0];
+        s_rq.totals[1] = s_tot[1];
+        s_rq.totals[2] = s_tot[2];
+        s_rq.totals[3] = (double)__ldcg(s_rq.status);
+        *s_rq.tiles_done = 0u;
+        __threadfence_system();
+        st_release_sys_u32(s_rq.done, 1u);
+      }
+    }
   }
-  if constexpr (MIXED) {
-    sw = to_double(swf);
-    sw2 = to_double(sw2f);
-  }
-  if (partials) block_reduce3(sw, sw2, nt, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -625,6 +768,24 @@ cudaError_t launch_eval(int prec, const double* mom, int64_t n, double* out, con
 }
 
 template <class P>
+cudaError_t launch_serve(int prec, const ServeCtl* ctl, const double* params, cudaStream_t s, int grid) {
+  typename P::Params prm;
+  memcpy(&prm, params, sizeof(prm));
+  if (prec == ME_FP64) k_serve<P, false><<<grid, kThreads, 0, s>>>(*ctl, prm);
+  else k_serve<P, true><<<grid, kThreads, 0, s>>>(*ctl, P::mixed_params(prm));
+  return cudaGetLastError();
+}
+
+template <class P>
+int serve_blocks_per_sm(int prec) {
+  int b = 0;
+  const cudaError_t e = prec == ME_FP64
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_serve<P, false>, kThreads, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_serve<P, true>, kThreads, 0);
+  return e == cudaSuccess ? b : 0;
+}
+
+template <class P>
 cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t offset, int64_t n, const double* params,
                         double* partials, double* me2_out, double* mom_out, double* wps_out, double* shat_out,
                         int32_t* tries_out, int* status, int eval_me, cudaStream_t s, int grid) {
@@ -647,4 +808,6 @@ cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t off
     d->launch_eval = me::launch_eval<me::TAG::Traits>;                              \
     d->launch_xsec = me::launch_xsec<me::TAG::Traits>;                              \
     d->launch_step = me::launch_step<me::TAG::Traits>;                              \
+    d->launch_serve = me::launch_serve<me::TAG::Traits>;                            \
+    d->serve_blocks_per_sm = me::serve_blocks_per_sm<me::TAG::Traits>;              \
   }
