@@ -20,7 +20,11 @@ workload's stated generators; the Breit-Wigner mapping is the paper's Eq. 16):
                         (Eq. 16, range |s-m^2|/(m Gamma) < min(20, m/Gamma),
                         App. A.2), isotropic two-body decays in each rest frame
   rambo_massive       : RAMBO with the massive rescaling (Kleiss et al. 1986)
-Cuts (Eqs. 8-11 in form): pT > pt_min, |eta| < eta_max, Delta R > dr_min.
+  ypt_phi             : the paper's y, pT, phi parametrisation at fixed sqrt(s) (Eq. 13,
+                        App. A.1) with the pT mapping of Eq. 17 and Breit-Wigner resonance
+                        objects (App. A.2)
+Cuts: the workloads' form pT > pt_min, |eta| < eta_max, Delta R > dr_min; and the paper's
+selection of Eqs. 8-11 (pass_paper_cuts: jets with the Durham pT_ij, b jets, leptons).
 A point failing the cuts (or the kinematic limits) is redrawn with the next
 attempt number; the MC estimate divides by the number of tries (Eq. 4
 integrated with the efficiency included).
@@ -330,6 +334,114 @@ def ttbar_dilepton(u, par, sqrt_s_range):
 
 
 # ---------------------------------------------------------------------------
+# the paper's parametrisation at fixed sqrt(s): rapidity, transverse momentum and azimuth
+# (Eq. 13, App. A.1), the pT mapping of Eq. 17 and Breit-Wigner resonances (App. A.2)
+# ---------------------------------------------------------------------------
+def ypt_uniforms(objects):
+    """Uniforms one y/pT/phi draw takes: 3 n - 3 for n objects, plus 3 per resonance object."""
+    n = len(objects)
+    return 3 * n - 3 + 3 * sum(1 for o in objects if len(o["legs"]) == 2)
+
+
+def ypt_phi(w, objects, nf, u):
+    """Momenta of nf final legs at partonic energy w in the centre-of-mass frame.
+
+    objects: the n objects of the n-body phase space in generation order, each a dict with
+      legs      (k,) one final leg (index among the final legs), or (k1, k2) a resonance decaying to two
+                massless legs;
+      mass      mass of a one-leg object; res_mass, res_width of a resonance;
+      y_max     |y| < y_max;  pt_min, pt_max  pT range.
+    Following App. A.1, dPhi_n = (2 pi)^(4 - 3n) 2^-n prod dy_i d^2 pT_i delta^4(P - sum p): the first
+    n - 2 objects take y uniform in [-y_max, y_max], the first n - 1 take ln(pT^2 + m^2) uniform over
+    their pT range (Eq. 17: d pT^2 = (pT^2 + m^2) d ln(pT^2 + m^2), m^2 = s_k for a resonance) and phi
+    uniform; the last object's pT balances the others.  With the energy fixed (no x_a, x_b
+    integration), the light-cone components P+- = sum mT_i exp(+-y_i) = w fix the rapidities of the
+    last two objects (two solutions, one chosen by a uniform; Jacobian 2 mT_a mT_b |sinh(y_b - y_a)|).
+    Their y_max and the last object's pT range hold a posteriori.  A resonance object (App. A.2):
+    s = p^2 Breit-Wigner mapped (Eq. 16 range, bw_sample), isotropic two-body decay at rest.
+    Uniform order: the resonances' s, the free rapidities, (pT, phi) of the first n - 1 objects, the
+    solution, then each resonance's decay direction (cos = 2u - 1, phi = 2 pi u).
+    Returns (pf [N, nf, 4], weight [N], ok [N])."""
+    N = u.shape[0]
+    n = len(objects)
+    k = 0
+    m2 = np.zeros((N, n))
+    wt = np.ones(N)
+    ok = np.ones(N, dtype=bool)
+    for j, o in enumerate(objects):
+        if len(o["legs"]) == 2:
+            s, jac = bw_sample(o["res_mass"], o["res_width"], u[:, k])
+            k += 1
+            ok &= s > 0
+            m2[:, j] = np.where(s > 0, s, 1.0)
+            wt = wt * jac
+        else:
+            m2[:, j] = o.get("mass", 0.0) ** 2
+    y = np.zeros((N, n))
+    for j in range(n - 2):
+        Y = objects[j]["y_max"]
+        y[:, j] = (2.0 * u[:, k] - 1.0) * Y
+        k += 1
+        wt = wt * 2.0 * Y
+    px = np.zeros((N, n))
+    py = np.zeros((N, n))
+    for j in range(n - 1):
+        o = objects[j]
+        L0 = np.log(o["pt_min"] ** 2 + m2[:, j])
+        L1 = np.log(o["pt_max"] ** 2 + m2[:, j])
+        L = L0 + u[:, k] * (L1 - L0)
+        pt2 = np.maximum(np.exp(L) - m2[:, j], 0.0)
+        ph = 2.0 * math.pi * u[:, k + 1]
+        k += 2
+        px[:, j] = np.sqrt(pt2) * np.cos(ph)
+        py[:, j] = np.sqrt(pt2) * np.sin(ph)
+        wt = wt * math.pi * (pt2 + m2[:, j]) * (L1 - L0)
+    px[:, n - 1] = -px[:, : n - 1].sum(axis=1)
+    py[:, n - 1] = -py[:, : n - 1].sum(axis=1)
+    mt = np.sqrt(px ** 2 + py ** 2 + m2)
+    Ap = w - (mt[:, : n - 2] * np.exp(y[:, : n - 2])).sum(axis=1)
+    Am = w - (mt[:, : n - 2] * np.exp(-y[:, : n - 2])).sum(axis=1)
+    ok &= (Ap > 0) & (Am > 0)
+    a, b = mt[:, n - 2], mt[:, n - 1]
+    M2 = Ap * Am
+    c = M2 + a * a - b * b
+    D = c * c - 4.0 * M2 * a * a
+    ok &= D >= 0
+    root = np.sqrt(np.maximum(D, 0.0))
+    X = np.where(u[:, k] < 0.5, c + root, c - root) / (2.0 * np.where(Am > 0, Am, 1.0))
+    k += 1
+    Z = Ap - X
+    ok &= (X > 0) & (Z > 0)
+    y[:, n - 2] = np.log(np.where(X > 0, X, 1.0) / a)
+    y[:, n - 1] = np.log(np.where(Z > 0, Z, 1.0) / b)
+    J = 2.0 * a * b * np.abs(np.sinh(y[:, n - 1] - y[:, n - 2]))
+    ok &= J > 0
+    wt = wt * 2.0 / np.where(J > 0, J, 1.0) * 2.0
+    for j in (n - 2, n - 1):
+        ok &= np.abs(y[:, j]) <= objects[j]["y_max"]
+    ptn = np.hypot(px[:, n - 1], py[:, n - 1])
+    ok &= (ptn >= objects[n - 1]["pt_min"]) & (ptn <= objects[n - 1]["pt_max"])
+    wt = wt * (2.0 * math.pi) ** (4 - 3 * n) * 2.0 ** (-n)
+    E = mt * np.cosh(y)
+    pz = mt * np.sinh(y)
+    pf = np.zeros((N, nf, 4))
+    for j, o in enumerate(objects):
+        Pj = np.stack([E[:, j], px[:, j], py[:, j], pz[:, j]], axis=1)
+        if len(o["legs"]) == 1:
+            pf[:, o["legs"][0]] = Pj
+    for j, o in enumerate(objects):
+        if len(o["legs"]) == 2:
+            M = np.sqrt(m2[:, j])
+            Pj = np.stack([E[:, j], px[:, j], py[:, j], pz[:, j]], axis=1)
+            p1, p2, pabs = _iso_pair(M, np.zeros(N), np.zeros(N), 2.0 * u[:, k] - 1.0, 2.0 * math.pi * u[:, k + 1])
+            k += 2
+            pf[:, o["legs"][0]] = _boost_from_rest(p1, Pj, M)
+            pf[:, o["legs"][1]] = _boost_from_rest(p2, Pj, M)
+            wt = wt * pabs / (4.0 * math.pi * M)
+    return pf, np.where(ok, wt, 0.0), ok
+
+
+# ---------------------------------------------------------------------------
 # cuts
 # ---------------------------------------------------------------------------
 def pt(p):
@@ -364,4 +476,30 @@ def pass_cuts(P, legs, pt_min, eta_max, dr_min):
         for j in range(i + 1, len(legs)):
             with np.errstate(divide="ignore", invalid="ignore"):
                 ok &= delta_r(P[:, legs[i]], P[:, legs[j]]) > dr_min
+    return ok
+
+
+# the paper's selection (Eqs. 8-11): jets |eta| < 5, pT > 20, and pT_ij = min(pT_i, pT_j) Delta R_ij > 20
+# for every pair of jets (the Durham relative transverse momentum); b jets from top decays |eta| < 2.5,
+# pT > 20, and charged leptons |eta| < 2.5, pT > 20, neither isolated
+PAPER_CUTS = {"jet_pt": 20.0, "jet_eta": 5.0, "jet_ptij": 20.0, "b_pt": 20.0, "b_eta": 2.5, "lep_pt": 20.0,
+              "lep_eta": 2.5}
+JET, BJET, LEPTON = 1, 2, 3
+
+
+def pass_paper_cuts(P, leg_class, c=PAPER_CUTS):
+    """leg_class: per leg of P, 0 (no cut), JET, BJET or LEPTON."""
+    ok = np.ones(P.shape[0], dtype=bool)
+    jets = [k for k, cl in enumerate(leg_class) if cl == JET]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for k, cl in enumerate(leg_class):
+            if cl == 0:
+                continue
+            ptmin, etamax = {JET: (c["jet_pt"], c["jet_eta"]), BJET: (c["b_pt"], c["b_eta"]),
+                             LEPTON: (c["lep_pt"], c["lep_eta"])}[cl]
+            ok &= (pt(P[:, k]) > ptmin) & (np.abs(eta(P[:, k])) < etamax)
+        for i in range(len(jets)):
+            for j in range(i + 1, len(jets)):
+                a, b = P[:, jets[i]], P[:, jets[j]]
+                ok &= np.minimum(pt(a), pt(b)) * delta_r(a, b) > c["jet_ptij"]
     return ok
