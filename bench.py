@@ -205,8 +205,13 @@ def oracle_kin(w):
     elif w["kind"] == "rambo_bw":
         k = {"kind": "rambo_bw", "sqrt_s": w["sqrt_s"], "n_final": n_ext - 2, "res_mass": w["res_mass"],
              "res_width": w["res_width"]}
+    elif w["kind"] == "ypt":
+        k = {"kind": "ypt", "sqrt_s": w["sqrt_s"], "n_final": n_ext - 2, "objects": w["objects"]}
     else:
         k = {"kind": "ttbar", "sqrt_s_range": w["sqrt_s_range"]}
+    if w.get("leg_class"):
+        from paper_1305_0708_gb300.workloads import PAPER_CUTS
+        k["paper_cuts"] = {"leg_class": list(w["leg_class"]), "thresholds": dict(PAPER_CUTS)}
     if w.get("cuts"):
         c = w["cuts"]
         k["cuts"] = {"legs": list(c["legs"]), "pt_min": c["pt_min"], "eta_max": c["eta_max"], "dr_min": c["dr_min"]}
@@ -299,10 +304,10 @@ def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
     """Every workload and variant: mixed and FP64 xsec_step rates on the full point count, the mixed
     |M|^2 kernel's CUDA-core fraction, and the mixed path's relative error against the FP64
     GPU path on the FP64 path's own momenta (median and max over the accepted points)."""
-    from paper_1305_0708_gb300.workloads import VARIANTS, WORKLOADS, kin_args
+    from paper_1305_0708_gb300.workloads import PAPER_PS, VARIANTS, WORKLOADS, kin_args
     peak = fp32_alu_peak_tflops()
     table = {}
-    for key, w in list(WORKLOADS.items()) + list(VARIANTS.items()):
+    for key, w in list(WORKLOADS.items()) + list(VARIANTS.items()) + list(PAPER_PS.items()):
         try:
             n = w["n"]
             kin = B.make_kin(**kin_args(w))
@@ -322,6 +327,10 @@ def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
                     ev[s_][1].record(stream)
                 torch.cuda.synchronize(dev)
                 ms = sum(a.elapsed_time(b) for a, b in ev) / ns
+                sums = acc_dev.cpu().tolist()  # (sum w, sum w^2, draws, exhausted) over nw + ns steps
+                npts = (nw + ns) * n
+                mean = sums[0] / sums[2]
+                err = math.sqrt(max(sums[1] / sums[2] - mean * mean, 0.0) / max(sums[2] - 1, 1))
                 # per-kernel device time on further steps of the same work
                 nt = 1 if slow else ns
                 B.me_step_timing(h, 1)
@@ -334,7 +343,8 @@ def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
                 fl = (EXECUTED_FLOPS_PER_POINT.get((key, "k_me"), info.flops_amp) if prec == B.ME_MIXED
                       else info.flops_fp64)
                 row[name] = {"evals_per_s": n / (ms * 1e-3), "ms_per_step": ms, "k_me_ms": t_me / ns_t,
-                             "k_me_tflops": fl * n / (t_me / ns_t * 1e-3) / 1e12}
+                             "k_me_tflops": fl * n / (t_me / ns_t * 1e-3) / 1e12,
+                             "sigma_pb": mean, "error_pb": err, "points": npts, "draws_per_point": sums[2] / npts}
                 if prec == B.ME_MIXED:
                     row[name]["k_me_frac_fp32_peak"] = row[name]["k_me_tflops"] / peak
                 else:

@@ -72,10 +72,19 @@ typedef enum {
   ME_PS_TTBAR = 2,     /* g g > t t~ > (b e+ ve)(b~ e- ve~): sqrt_s uniform in [sqrt_s_min,
                           sqrt_s_max], Breit-Wigner t, t~, W+, W- (Eq. 16, App. A.2), isotropic
                           two-body decays in every rest frame */
-  ME_PS_RAMBO_BW = 3   /* massless final state at fixed sqrt_s whose legs 2 and 3 come from a
+  ME_PS_RAMBO_BW = 3,  /* massless final state at fixed sqrt_s whose legs 2 and 3 come from a
                           resonance (res_mass, res_width): dPhi_n = dPhi_{n-1} ds/(2 pi) dPhi_2
                           (App. A.2), s Breit-Wigner mapped over the Eq. 16 range, RAMBO for the
                           resonance and legs 4.., isotropic decay at rest */
+  ME_PS_YPT = 4        /* the paper's parametrisation (Eq. 13, App. A.1) at fixed sqrt_s, in the
+                          centre-of-mass frame: objects (one leg, or a Breit-Wigner resonance that
+                          decays isotropically into two massless legs, App. A.2) in generation order;
+                          the first n-2 take y uniform in [-obj_y_max, obj_y_max], the first n-1 take
+                          ln(pT^2 + m^2) uniform over [obj_pt_min, obj_pt_max] (Eq. 17; m^2 = s of a
+                          resonance) and phi uniform, the last one's pT balances the others, and the
+                          longitudinal momentum balance fixes the last two rapidities (two solutions,
+                          one drawn).  Their y ranges and the last pT range are checked afterwards.
+                          Uniforms: 3 per final leg - 3.  FP64 on both paths. */
 } me_ps_kind;
 
 typedef struct {
@@ -91,6 +100,19 @@ typedef struct {
   double dr_min;           /* Delta R > dr_min for every pair of cut legs */
   double s_ident;          /* identical-particle factor 1/k! applied to the weights */
   double res_mass, res_width;  /* resonance of ME_PS_RAMBO_BW (GeV) */
+  /* ME_PS_YPT objects */
+  int32_t n_obj;           /* 2..8; together the objects hold every final leg once */
+  int32_t cut_mode;        /* 0: the cuts above (pt_min, eta_max, dr_min on cut_legs); 1: the paper's
+                              selection (Eqs. 8-11) by leg_class, with the thresholds below (with
+                              ME_PS_YPT only) */
+  int32_t obj_legs[8][2];  /* legs of each object (>= 2); obj_legs[j][1] = -1 for a one-leg object */
+  int32_t leg_class[16];   /* cut_mode 1: 0 none, 1 jet (|eta| < jet_eta, pT > jet_pt, and
+                              min(pT_i, pT_j) Delta R_ij > jet_ptij for every jet pair), 2 b jet,
+                              3 charged lepton (pT and |eta| only) */
+  double obj_mass[8];      /* mass of a one-leg object */
+  double obj_res_mass[8], obj_res_width[8];  /* a two-leg object: its resonance */
+  double obj_y_max[8], obj_pt_min[8], obj_pt_max[8];
+  double jet_pt, jet_eta, jet_ptij, b_pt, b_eta, lep_pt, lep_eta;  /* cut_mode 1 thresholds */
 } me_kin;
 
 /* Monte Carlo accumulator (host).  xsec_step adds to it. */

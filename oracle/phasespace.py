@@ -399,8 +399,16 @@ def ypt_phi(w, objects, nf, u):
     px[:, n - 1] = -px[:, : n - 1].sum(axis=1)
     py[:, n - 1] = -py[:, : n - 1].sum(axis=1)
     mt = np.sqrt(px ** 2 + py ** 2 + m2)
-    Ap = w - (mt[:, : n - 2] * np.exp(y[:, : n - 2])).sum(axis=1)
-    Am = w - (mt[:, : n - 2] * np.exp(-y[:, : n - 2])).sum(axis=1)
+    # light-cone components P+- = mT exp(+-y) of the free objects; energies and longitudinal
+    # momenta are formed from them, E = (P+ + P-)/2, pz = (P+ - P-)/2, so that the balance
+    # sum P+- = w also holds for the stored momenta (E - pz of a forward particle is not a
+    # difference of two large numbers)
+    lp = np.zeros((N, n))
+    lm = np.zeros((N, n))
+    lp[:, : n - 2] = mt[:, : n - 2] * np.exp(y[:, : n - 2])
+    lm[:, : n - 2] = mt[:, : n - 2] * np.exp(-y[:, : n - 2])
+    Ap = w - lp[:, : n - 2].sum(axis=1)
+    Am = w - lm[:, : n - 2].sum(axis=1)
     ok &= (Ap > 0) & (Am > 0)
     a, b = mt[:, n - 2], mt[:, n - 1]
     M2 = Ap * Am
@@ -408,13 +416,23 @@ def ypt_phi(w, objects, nf, u):
     D = c * c - 4.0 * M2 * a * a
     ok &= D >= 0
     root = np.sqrt(np.maximum(D, 0.0))
-    X = np.where(u[:, k] < 0.5, c + root, c - root) / (2.0 * np.where(Am > 0, Am, 1.0))
+    # the two roots of Am X^2 - c X + a^2 Ap = 0: the larger without cancellation, the smaller from
+    # the product of the roots a^2 Ap / Am (c - root loses the digits the balance of P- needs)
+    Ams = np.where(Am > 0, Am, 1.0)
+    big = (c + root) / (2.0 * Ams)
+    small = a * a * Ap / (Ams * np.where(big > 0, big, 1.0))
+    X = np.where(u[:, k] < 0.5, big, small)
     k += 1
     Z = Ap - X
     ok &= (X > 0) & (Z > 0)
-    y[:, n - 2] = np.log(np.where(X > 0, X, 1.0) / a)
-    y[:, n - 1] = np.log(np.where(Z > 0, Z, 1.0) / b)
-    J = 2.0 * a * b * np.abs(np.sinh(y[:, n - 1] - y[:, n - 2]))
+    Xs, Zs = np.where(X > 0, X, 1.0), np.where(Z > 0, Z, 1.0)
+    y[:, n - 2] = np.log(Xs / a)
+    y[:, n - 1] = np.log(Zs / b)
+    lp[:, n - 2], lm[:, n - 2] = Xs, a * a / Xs
+    lp[:, n - 1], lm[:, n - 1] = Zs, b * b / Zs
+    # Jacobian 2 mT_a mT_b |sinh(y_b - y_a)| with exp(y_b - y_a) = (Z a) / (X b)
+    r = (Zs * a) / (Xs * b)
+    J = a * b * np.abs(r - 1.0 / r)
     ok &= J > 0
     wt = wt * 2.0 / np.where(J > 0, J, 1.0) * 2.0
     for j in (n - 2, n - 1):
@@ -422,8 +440,8 @@ def ypt_phi(w, objects, nf, u):
     ptn = np.hypot(px[:, n - 1], py[:, n - 1])
     ok &= (ptn >= objects[n - 1]["pt_min"]) & (ptn <= objects[n - 1]["pt_max"])
     wt = wt * (2.0 * math.pi) ** (4 - 3 * n) * 2.0 ** (-n)
-    E = mt * np.cosh(y)
-    pz = mt * np.sinh(y)
+    E = 0.5 * (lp + lm)
+    pz = 0.5 * (lp - lm)
     pf = np.zeros((N, nf, 4))
     for j, o in enumerate(objects):
         Pj = np.stack([E[:, j], px[:, j], py[:, j], pz[:, j]], axis=1)

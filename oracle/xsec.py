@@ -20,7 +20,8 @@ from .sm import GEV2_TO_PB
 
 
 def draw(kin, par, u):
-    """One draw for every row of u: (P, W_PS, ok, s-hat)."""
+    """One draw for every row of u: (P, W_PS, ok, s-hat).  Kinds: 2to2, rambo, ttbar, rambo_bw and
+    ypt (the paper's parametrisation: objects with absolute leg indices, as phasespace.ypt_phi)."""
     kind = kin["kind"]
     N = u.shape[0]
     if kind == "2to2":
@@ -41,6 +42,15 @@ def draw(kin, par, u):
         return P, wt, np.ones(N, dtype=bool), np.full(N, w * w)
     if kind == "ttbar":
         return ps.ttbar_dilepton(u, par, kin["sqrt_s_range"])
+    if kind == "ypt":
+        w = kin["sqrt_s"]
+        nf = kin["n_final"]
+        objs = [dict(o, legs=tuple(l - 2 for l in o["legs"])) for o in kin["objects"]]
+        pf, wt, ok = ps.ypt_phi(w, objs, nf, u)
+        P = np.zeros((N, nf + 2, 4))
+        P[:, 0], P[:, 1] = ps.incoming(w, N)
+        P[:, 2:] = pf
+        return P, wt, ok, np.full(N, w * w)
     if kind == "rambo_bw":
         w = kin["sqrt_s"]
         nf = kin["n_final"]
@@ -60,6 +70,8 @@ def grid_dims(kin):
         return 4 * kin["n_final"]
     if kin["kind"] == "rambo_bw":
         return 4 * kin["n_final"] - 1
+    if kin["kind"] == "ypt":
+        return 3 * kin["n_final"] - 3
     return 15
 
 
@@ -107,6 +119,9 @@ def _generate(kin, par, seed, events, max_attempts, grid):
             Wn = Wn * jac
         if cut is not None:
             ok = ok & ps.pass_cuts(Pn, cut["legs"], cut["pt_min"], cut["eta_max"], cut["dr_min"])
+        if kin.get("paper_cuts") is not None:
+            pc = kin["paper_cuts"]
+            ok = ok & ps.pass_paper_cuts(Pn, pc["leg_class"], pc["thresholds"])
         if P is None:
             P = np.zeros((N,) + Pn.shape[1:])
         acc = idx[ok]

@@ -30,7 +30,14 @@ class me_kin(ctypes.Structure):
                 ("sqrt_s_min", ctypes.c_double), ("sqrt_s_max", ctypes.c_double), ("mass", ctypes.c_double * 16),
                 ("n_cut_legs", ctypes.c_int32), ("cut_legs", ctypes.c_int32 * 8), ("pt_min", ctypes.c_double),
                 ("eta_max", ctypes.c_double), ("dr_min", ctypes.c_double), ("s_ident", ctypes.c_double),
-                ("res_mass", ctypes.c_double), ("res_width", ctypes.c_double)]
+                ("res_mass", ctypes.c_double), ("res_width", ctypes.c_double),
+                ("n_obj", ctypes.c_int32), ("cut_mode", ctypes.c_int32), ("obj_legs", (ctypes.c_int32 * 2) * 8),
+                ("leg_class", ctypes.c_int32 * 16), ("obj_mass", ctypes.c_double * 8),
+                ("obj_res_mass", ctypes.c_double * 8), ("obj_res_width", ctypes.c_double * 8),
+                ("obj_y_max", ctypes.c_double * 8), ("obj_pt_min", ctypes.c_double * 8),
+                ("obj_pt_max", ctypes.c_double * 8), ("jet_pt", ctypes.c_double), ("jet_eta", ctypes.c_double),
+                ("jet_ptij", ctypes.c_double), ("b_pt", ctypes.c_double), ("b_eta", ctypes.c_double),
+                ("lep_pt", ctypes.c_double), ("lep_eta", ctypes.c_double)]
 
 
 class me_xsec_acc(ctypes.Structure):
@@ -72,7 +79,7 @@ class me_server_stats(ctypes.Structure):
 
 
 ME_FP64, ME_MIXED = 0, 1
-ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR, ME_PS_RAMBO_BW = 0, 1, 2, 3
+ME_PS_TWO_BODY, ME_PS_RAMBO, ME_PS_TTBAR, ME_PS_RAMBO_BW, ME_PS_YPT = 0, 1, 2, 3, 4
 
 EXPORTS = ["me_create", "me_eval", "me_eval_host", "me_generate", "xsec_step", "xsec_step_async", "xsec_step_noalloc", "me_step_timing",
            "me_xsec_estimate", "me_info", "me_n_processes", "me_process_name", "me_destroy", "me_last_error",
@@ -175,8 +182,30 @@ def make_params(**kw):
 
 
 def make_kin(kind, sqrt_s=0.0, sqrt_s_range=(0.0, 0.0), masses=(), cut_legs=(), pt_min=0.0, eta_max=0.0,
-             dr_min=0.0, s_ident=1.0, max_attempts=0, res_mass=0.0, res_width=0.0):
+             dr_min=0.0, s_ident=1.0, max_attempts=0, res_mass=0.0, res_width=0.0, objects=(), leg_class=None,
+             paper_cuts=None):
+    """me_kin.  objects (ME_PS_YPT): dicts with legs ((k,) or (k1, k2) for a resonance), mass or
+    res_mass/res_width, y_max, pt_min, pt_max.  leg_class (per leg, 0..3) selects the paper's cuts
+    (cut_mode 1) with the thresholds of paper_cuts (keys jet_pt, jet_eta, jet_ptij, b_pt, b_eta,
+    lep_pt, lep_eta)."""
     k = me_kin()
+    k.n_obj = len(objects)
+    for j, o in enumerate(objects):
+        legs = tuple(o["legs"])
+        k.obj_legs[j][0] = legs[0]
+        k.obj_legs[j][1] = legs[1] if len(legs) == 2 else -1
+        k.obj_mass[j] = o.get("mass", 0.0)
+        k.obj_res_mass[j] = o.get("res_mass", 0.0)
+        k.obj_res_width[j] = o.get("res_width", 0.0)
+        k.obj_y_max[j], k.obj_pt_min[j], k.obj_pt_max[j] = o["y_max"], o["pt_min"], o["pt_max"]
+    for j in range(len(objects), 8):
+        k.obj_legs[j][0] = k.obj_legs[j][1] = -1
+    if leg_class is not None:
+        k.cut_mode = 1
+        for i, c in enumerate(leg_class):
+            k.leg_class[i] = c
+        for key, v in (paper_cuts or {}).items():
+            setattr(k, key, v)
     k.kind = kind
     k.max_attempts = max_attempts
     k.sqrt_s = sqrt_s

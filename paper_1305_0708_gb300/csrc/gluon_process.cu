@@ -653,6 +653,15 @@ cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t off
                         int32_t* tries_out, int* status, int eval_me, cudaStream_t s, int grid) {
   (void)params;
   if (eval_me || partials || me2_out) return cudaErrorNotSupported;
+  if (kin->kind == ME_PS_YPT) {
+    if (prec == ME_FP64)
+      k_gen<NoME, false, ME_PS_YPT><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, mom_out, wps_out, shat_out,
+                                                              tries_out, status);
+    else
+      k_gen<NoME, true, ME_PS_YPT><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, mom_out, wps_out, shat_out,
+                                                             tries_out, status);
+    return cudaGetLastError();
+  }
   typename NoME::Params prm{0.0};
   if (prec == ME_FP64)
     k_xsec<NoME, false><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, prm, nullptr, nullptr, mom_out, wps_out,

@@ -27,6 +27,7 @@ int grid_dims_for(int kind, int n_ext) {
   if (kind == ME_PS_TWO_BODY) return 2;
   if (kind == ME_PS_RAMBO) return 4 * (n_ext - 2);
   if (kind == ME_PS_RAMBO_BW) return 4 * (n_ext - 2) - 1;
+  if (kind == ME_PS_YPT) return 3 * (n_ext - 2) - 3;
   return 15;
 }
 

@@ -31,6 +31,13 @@ struct KinDev {
   // adaptive grid over the generator's uniforms (VEGAS); vg_bins == 0: none
   int32_t vg_dims, vg_bins;
   const double* vg_edges;  // device [vg_dims][vg_bins + 1]
+  // ME_PS_YPT objects (me.h) with the Breit-Wigner range of each resonance object
+  int32_t n_obj, cut_mode;
+  int32_t obj_legs[8][2];
+  int32_t leg_class[16];
+  double obj_mass[8], obj_res_mass[8], obj_res_width[8], obj_t0[8], obj_t1[8];
+  double obj_y_max[8], obj_pt_min[8], obj_pt_max[8];
+  double jet_pt, jet_eta, jet_ptij, b_pt, b_eta, lep_pt, lep_eta;
 };
 
 constexpr int kGridMaxDims = 32, kGridMaxBins = 256;

@@ -200,7 +200,7 @@ int grid_for(me_handle h, int64_t n) {
 }
 
 me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
-  if (kin->kind < ME_PS_TWO_BODY || kin->kind > ME_PS_RAMBO_BW) return fail(ME_ERR_ARG, "kin->kind: unknown generator");
+  if (kin->kind < ME_PS_TWO_BODY || kin->kind > ME_PS_YPT) return fail(ME_ERR_ARG, "kin->kind: unknown generator");
   const int next = h->desc->n_ext;
   if (kin->kind == ME_PS_TWO_BODY && next != 4) return fail(ME_ERR_ARG, "two-body generator needs 4 legs");
   if (kin->kind == ME_PS_TTBAR && next != 8) return fail(ME_ERR_ARG, "ttbar generator needs 8 legs");
@@ -209,6 +209,35 @@ me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
     return fail(ME_ERR_ARG, "resonance RAMBO supports 3 to 8 final legs");
   if (kin->kind == ME_PS_RAMBO_BW && !(kin->res_mass > 0 && kin->res_width > 0 && kin->res_mass < kin->sqrt_s))
     return fail(ME_ERR_ARG, "kin: resonance mass and width must be positive, mass below sqrt_s");
+  if (kin->kind == ME_PS_YPT) {
+    if (kin->n_obj < 2 || kin->n_obj > 8 || next > 10) return fail(ME_ERR_ARG, "kin: y/pT generator needs 2..8 objects");
+    uint32_t seen = 0;
+    for (int j = 0; j < kin->n_obj; ++j) {
+      for (int q = 0; q < 2; ++q) {
+        const int l = kin->obj_legs[j][q];
+        if (q == 1 && l == -1) continue;
+        if (l < 2 || l >= next || ((seen >> l) & 1u)) return fail(ME_ERR_ARG, "kin->obj_legs: not a partition of the final legs");
+        seen |= 1u << l;
+      }
+      const bool res = kin->obj_legs[j][1] >= 0;
+      if (res && !(kin->obj_res_mass[j] > 0 && kin->obj_res_width[j] > 0 && kin->obj_res_mass[j] < kin->sqrt_s))
+        return fail(ME_ERR_ARG, "kin: a resonance object needs a positive mass below sqrt_s and a positive width");
+      if (!res && !(kin->obj_mass[j] >= 0)) return fail(ME_ERR_ARG, "kin->obj_mass must be >= 0");
+      if (!(kin->obj_y_max[j] > 0 && kin->obj_pt_max[j] > kin->obj_pt_min[j] && kin->obj_pt_min[j] >= 0))
+        return fail(ME_ERR_ARG, "kin: object ranges need y_max > 0 and 0 <= pt_min < pt_max");
+      if (!res && kin->obj_mass[j] == 0 && j < kin->n_obj - 1 && !(kin->obj_pt_min[j] > 0))
+        return fail(ME_ERR_ARG, "kin: a massless object with a generated pT needs pt_min > 0 (Eq. 17 maps ln pT^2)");
+    }
+    if (seen != (((1u << next) - 1u) & ~3u)) return fail(ME_ERR_ARG, "kin->obj_legs: every final leg belongs to one object");
+  }
+  if (kin->cut_mode != 0 && kin->cut_mode != 1) return fail(ME_ERR_ARG, "kin->cut_mode must be 0 or 1");
+  if (kin->cut_mode == 1 && kin->kind != ME_PS_YPT)
+    return fail(ME_ERR_ARG, "kin->cut_mode 1 (the paper's selection) goes with the y/pT generator");
+  if (kin->cut_mode == 1) {
+    for (int i = 0; i < 16; ++i)
+      if (kin->leg_class[i] < 0 || kin->leg_class[i] > 3 || (kin->leg_class[i] && (i < 2 || i >= next)))
+        return fail(ME_ERR_ARG, "kin->leg_class: 0..3 on final legs only");
+  }
   if (kin->n_cut_legs < 0 || kin->n_cut_legs > 8) return fail(ME_ERR_ARG, "kin->n_cut_legs out of range");
   for (int i = 0; i < kin->n_cut_legs; ++i)
     if (kin->cut_legs[i] < 2 || kin->cut_legs[i] >= next) return fail(ME_ERR_ARG, "kin->cut_legs: not a final-state leg");
@@ -273,6 +302,32 @@ me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
   k.f_chd = (float)k.cosh_dr;
   k.f_shd = (float)k.sinh_dr;
   k.f_dr2 = (float)(k.dr_min * k.dr_min);
+  k.n_obj = kin->kind == ME_PS_YPT ? kin->n_obj : 0;
+  k.cut_mode = kin->cut_mode;
+  for (int j = 0; j < 8; ++j) {
+    k.obj_legs[j][0] = kin->obj_legs[j][0];
+    k.obj_legs[j][1] = j < k.n_obj ? kin->obj_legs[j][1] : -1;
+    k.obj_mass[j] = kin->obj_mass[j];
+    k.obj_res_mass[j] = kin->obj_res_mass[j];
+    k.obj_res_width[j] = kin->obj_res_width[j];
+    if (j < k.n_obj && kin->obj_legs[j][1] >= 0) {
+      const double x = std::min(20.0, kin->obj_res_mass[j] / kin->obj_res_width[j]);
+      k.obj_t0[j] = -std::atan(x);
+      k.obj_t1[j] = std::atan(x);
+    }
+    k.obj_y_max[j] = kin->obj_y_max[j];
+    k.obj_pt_min[j] = kin->obj_pt_min[j];
+    k.obj_pt_max[j] = kin->obj_pt_max[j];
+  }
+  for (int i = 0; i < 16; ++i) k.leg_class[i] = kin->cut_mode == 1 ? kin->leg_class[i] : 0;
+  k.jet_pt = kin->jet_pt;
+  k.jet_eta = kin->jet_eta;
+  k.jet_ptij = kin->jet_ptij;
+  k.b_pt = kin->b_pt;
+  k.b_eta = kin->b_eta;
+  k.lep_pt = kin->lep_pt;
+  k.lep_eta = kin->lep_eta;
+  if (kin->cut_mode == 1) k.cut_mask = 0;  // the per-class selection replaces the uniform cuts
   const double gev2pb = 0.3893793721e9;
   if (kin->kind == ME_PS_TWO_BODY)
     k.wfactor = (1.0 / (8.0 * kPi)) * k.s_ident * gev2pb / (2.0 * k.shat_fixed);
@@ -641,6 +696,8 @@ me_status xsec_step_noalloc(me_handle h, uint64_t seed, uint64_t counter_offset,
   if (h->desc->events_per_block == 1)
     return fail(ME_ERR_ARG, std::string("xsec_step_noalloc: not available for ") + h->desc->name +
                                 " (its |M|^2 kernel takes one event per block and has no fused step)");
+  if (kin->kind == ME_PS_YPT)
+    return fail(ME_ERR_ARG, "xsec_step_noalloc: the y/pT generator is not compiled into the fused step");
   me::KinDev k;
   if ((st = make_kin(h, kin, k)) != ME_OK) return st;
   if (n_accept == 0) return ME_OK;

@@ -825,7 +825,8 @@ void me_server_s::run() {
       }
       q->proc = p;
       me::rt::make_kin(p->h, &q->r.kin, q->kin);  // checked at submit
-      if (cfg.persistent && p->serve && (q->r.n + p->tile - 1) / p->tile <= (int64_t)kLaneItems / 2) {
+      if (cfg.persistent && p->serve && q->kin.kind != ME_PS_YPT &&
+          (q->r.n + p->tile - 1) / p->tile <= (int64_t)kLaneItems / 2) {
         // a persistent lane takes it in tiles; its partials are one per tile
         const int n_ext = p->h->desc->n_ext;
         q->chunk = p->tile;

@@ -291,6 +291,152 @@ __host__ __device__ __forceinline__ bool gen_rambo_bw(const KinDev& kin, const d
   return true;
 }
 
+// The paper's parametrisation at fixed energy (Eq. 13, App. A.1; Eq. 17; App. A.2), in FP64:
+// n objects (kin.n_obj), each one leg or a Breit-Wigner resonance decaying isotropically into two
+// massless legs.  dPhi_n = (2 pi)^(4 - 3n) 2^-n prod dy_i d^2 pT_i delta^4(P - sum p): the first n - 2
+// objects take y uniform in [-y_max, y_max], the first n - 1 take ln(pT^2 + m^2) uniform over their pT
+// range and phi uniform, the last pT balances; P+- = sum mT exp(+-y) = sqrt_s then fixes the last two
+// rapidities (a quadratic in mT_a exp(y_a), one of its two roots drawn; Jacobian
+// 2 mT_a mT_b |sinh(y_b - y_a)|).  Uniforms, in order: resonance virtualities, free rapidities,
+// (pT, phi) pairs, the root, the resonances' decay directions: 3 per final leg - 3 in all.
+template <int NEXT>
+__host__ __device__ __forceinline__ bool gen_ypt(const KinDev& kin, const double* u, double (&p)[NEXT][4],
+                                                 double& wps, double& shat) {
+  constexpr int NF = NEXT - 2;  // objects never outnumber the final legs
+  constexpr double kPi_ = 3.14159265358979323846;
+  const int n = kin.n_obj;
+  const double w = kin.sqrt_s;
+  beams<NEXT>(p, w);
+  double m2[NF], px[NF], py[NF], y[NF];
+  double wt = 1.0;
+  int k = 0;
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    m2[j] = 0.0;
+    px[j] = py[j] = y[j] = 0.0;
+    if (j >= n) continue;
+    if (kin.obj_legs[j][1] >= 0) {
+      double jac;
+      const double sr = bw_draw(kin.obj_res_mass[j], kin.obj_res_width[j], kin.obj_t0[j], kin.obj_t1[j], u[k++], jac);
+      if (!(sr > 0.0)) return false;
+      m2[j] = sr;
+      wt *= jac;
+    } else {
+      m2[j] = kin.obj_mass[j] * kin.obj_mass[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NF - 2; ++j) {
+    if (j >= n - 2) continue;
+    y[j] = (2.0 * u[k++] - 1.0) * kin.obj_y_max[j];
+    wt *= 2.0 * kin.obj_y_max[j];
+  }
+  double sx = 0.0, sy = 0.0;
+#pragma unroll
+  for (int j = 0; j < NF - 1; ++j) {
+    if (j >= n - 1) continue;
+    const double l0 = log(kin.obj_pt_min[j] * kin.obj_pt_min[j] + m2[j]);
+    const double l1 = log(kin.obj_pt_max[j] * kin.obj_pt_max[j] + m2[j]);
+    const double l = l0 + u[k++] * (l1 - l0);
+    const double e = exp(l);
+    const double pt = sqrt(fmax(e - m2[j], 0.0));
+    double sp, cp;
+    sincospi(2.0 * u[k++], &sp, &cp);
+    px[j] = pt * cp;
+    py[j] = pt * sp;
+    sx += px[j];
+    sy += py[j];
+    wt *= kPi_ * e * (l1 - l0);
+  }
+  // light-cone components P+- = mT exp(+-y); E = (P+ + P-)/2 and pz = (P+ - P-)/2 are formed from
+  // them so that the balance sum P+- = sqrt_s also holds for the stored momenta
+  double mt[NF], lp[NF], lm[NF];
+  double ap = w, am = w;
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    if (j == n - 1) { px[j] = -sx; py[j] = -sy; }
+    mt[j] = sqrt(px[j] * px[j] + py[j] * py[j] + m2[j]);
+    lp[j] = lm[j] = 0.0;
+    if (j < n - 2) {
+      const double ey = exp(y[j]);
+      lp[j] = mt[j] * ey;
+      lm[j] = mt[j] / ey;
+      ap -= lp[j];
+      am -= lm[j];
+    }
+  }
+  if (!(ap > 0.0 && am > 0.0)) return false;
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    if (j == n - 2) a = mt[j];
+    if (j == n - 1) b = mt[j];
+  }
+  const double msq = ap * am, c = msq + a * a - b * b, d = c * c - 4.0 * msq * a * a;
+  if (!(d >= 0.0)) return false;
+  // the larger root without cancellation, the smaller one from the product of the roots a^2 ap / am
+  const double big = (c + sqrt(d)) / (2.0 * am);
+  const double x = u[k++] < 0.5 ? big : a * a * ap / (am * big);
+  const double z = ap - x;
+  if (!(x > 0.0 && z > 0.0)) return false;
+  const double ya = log(x / a), yb = log(z / b);
+  const double r = (z * a) / (x * b);  // exp(y_b - y_a): Jacobian 2 mT_a mT_b |sinh(y_b - y_a)|
+  const double jac = a * b * fabs(r - 1.0 / r);
+  if (!(jac > 0.0)) return false;
+  wt *= 4.0 / jac;
+  double ymax_a = 0.0, ymax_b = 0.0, ptmin_b = 0.0, ptmax_b = 0.0, ptb = 0.0;
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    if (j == n - 2) { y[j] = ya; ymax_a = kin.obj_y_max[j]; lp[j] = x; lm[j] = a * a / x; }
+    if (j == n - 1) {
+      y[j] = yb;
+      lp[j] = z;
+      lm[j] = b * b / z;
+      ymax_b = kin.obj_y_max[j];
+      ptmin_b = kin.obj_pt_min[j];
+      ptmax_b = kin.obj_pt_max[j];
+      ptb = sqrt(px[j] * px[j] + py[j] * py[j]);
+    }
+  }
+  if (!(fabs(ya) <= ymax_a && fabs(yb) <= ymax_b && ptb >= ptmin_b && ptb <= ptmax_b)) return false;
+  // (2 pi)^(4 - 3n) 2^-n
+  double f = 1.0;
+#pragma unroll
+  for (int j = 0; j < NF; ++j)
+    if (j < n) f *= 1.0 / (2.0 * (2.0 * kPi_) * (2.0 * kPi_) * (2.0 * kPi_));
+  wt *= f * (2.0 * kPi_) * (2.0 * kPi_) * (2.0 * kPi_) * (2.0 * kPi_);
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    if (j >= n) continue;
+    const double e = 0.5 * (lp[j] + lm[j]), pz = 0.5 * (lp[j] - lm[j]);
+    const int l0 = kin.obj_legs[j][0], l1 = kin.obj_legs[j][1];
+    if (l1 < 0) {
+#pragma unroll
+      for (int q = 2; q < NEXT; ++q)
+        if (q == l0) set4(p[q], e, px[j], py[j], pz);
+      continue;
+    }
+    const double M = sqrt(m2[j]);
+    const double P[4] = {e, px[j], py[j], pz};
+    double nx, ny, nz;
+    direction(u[k], u[k + 1], nx, ny, nz);
+    k += 2;
+    const double kd = 0.5 * M;
+    double d1[4] = {kd, kd * nx, kd * ny, kd * nz}, d2[4] = {kd, -kd * nx, -kd * ny, -kd * nz};
+    boost_from_rest(d1, P, M);
+    boost_from_rest(d2, P, M);
+#pragma unroll
+    for (int q = 2; q < NEXT; ++q) {
+      if (q == l0) set4(p[q], d1[0], d1[1], d1[2], d1[3]);
+      if (q == l1) set4(p[q], d2[0], d2[1], d2[2], d2[3]);
+    }
+    wt *= kd / (4.0 * kPi_ * M);
+  }
+  wps = wt;
+  shat = w * w;
+  return true;
+}
+
 // g g > t t~ > (b (e+ ve)) (b~ (e- ve~)); legs g g b e+ ve b~ e- ve~
 template <int NEXT>
 __host__ __device__ __forceinline__ bool gen_ttbar(const KinDev& kin, const double* u, double (&p)[NEXT][4],
@@ -432,8 +578,44 @@ __host__ __device__ __forceinline__ bool pass_cuts(const KinDev& kin, const doub
   return true;
 }
 
+// The paper's selection (Eqs. 8-11), kin.cut_mode == 1 (with the y/pT generator), in FP64: per leg
+// class, jets |eta| < jet_eta
+// and pT > jet_pt with min(pT_i, pT_j) Delta R_ij > jet_ptij for every pair of jets; b jets and
+// charged leptons pT and |eta| only (not isolated).
+template <int NEXT>
+__host__ __device__ __forceinline__ bool pass_paper_cuts(const KinDev& kin, const double (&p)[NEXT][4]) {
+  if (kin.cut_mode != 1) return true;
+  double pt[NEXT], eta[NEXT], phi[NEXT];
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+    const int cl = kin.leg_class[i];
+    if (cl == 0) continue;
+    pt[i] = sqrt(p[i][1] * p[i][1] + p[i][2] * p[i][2]);
+    if (!(pt[i] > 0.0)) return false;
+    eta[i] = asinh(p[i][3] / pt[i]);
+    phi[i] = atan2(p[i][2], p[i][1]);
+    const double ptmin = cl == 1 ? kin.jet_pt : (cl == 2 ? kin.b_pt : kin.lep_pt);
+    const double etamax = cl == 1 ? kin.jet_eta : (cl == 2 ? kin.b_eta : kin.lep_eta);
+    if (!(pt[i] > ptmin && fabs(eta[i]) < etamax)) return false;
+  }
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < NEXT; ++j) {
+      if (kin.leg_class[i] != 1 || kin.leg_class[j] != 1) continue;
+      const double deta = eta[i] - eta[j];
+      double dphi = fabs(phi[i] - phi[j]);
+      if (dphi > 3.14159265358979323846) dphi = 2.0 * 3.14159265358979323846 - dphi;
+      if (!(fmin(pt[i], pt[j]) * sqrt(deta * deta + dphi * dphi) > kin.jet_ptij)) return false;
+    }
+  }
+  return true;
+}
+
 // Generator kind as a template argument: kKindAny reads kin.kind at run time;
-// a fixed kind compiles only that generator (smaller code, fewer registers).
+// a fixed kind compiles only that generator (smaller code, fewer registers).  The y/pT
+// generator is compiled only where it is the fixed kind (k_ps, k_gen): the fused kernels,
+// which dispatch at run time and hold the |M|^2 program's registers, leave it out.
 // kKindRamboMassive is RAMBO with the massive rescaling; ME_PS_RAMBO as a fixed
 // kind on the mixed path is massless RAMBO.  The grid map runs where `bins` is
 // not null (the caller passes null unless kin carries a grid).
@@ -464,6 +646,14 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
     if (kind == ME_PS_RAMBO) ok = gen_rambo<NEXT>(kin, u, p, wps, shat);
     else if constexpr (NEXT >= 5) ok = gen_rambo_bw<NEXT>(kin, u, p, wps, shat);
     else ok = false;
+  } else if (KIND == ME_PS_YPT && kind == ME_PS_YPT) {
+    constexpr int NU = 3 * (NEXT - 2) - 3;
+    double u[NU];
+    draw_uniforms<NU>(seed, event, (uint64_t)att, u);
+#pragma unroll
+    for (int d = 0; d < NU; ++d)
+      if (bins && d < kin.vg_dims) u[d] = vg_map(kin, d, u[d], jac, bins);
+    ok = gen_ypt<NEXT>(kin, u, p, wps, shat);
   } else {
     double u[16];
     draw_uniforms<16>(seed, event, (uint64_t)att, u);
@@ -473,6 +663,7 @@ __host__ __device__ __forceinline__ bool draw_point(const KinDev& kin, uint64_t 
     ok = gen_ttbar<NEXT>(kin, u, p, wps, shat);
   }
   wps *= jac;
+  if (kind == ME_PS_YPT) return ok && pass_cuts<NEXT>(kin, p) && pass_paper_cuts<NEXT>(kin, p);
   return ok && pass_cuts<NEXT>(kin, p);
 }
 
@@ -919,9 +1110,26 @@ __host__ __device__ __forceinline__ bool rambo_bw_df(const KinDev& kin, uint64_t
   return true;
 }
 
+// the generators that run in FP64 on the mixed path too (two-body, y/pT), their momenta split into
+// double-floats
+template <int NEXT, int KIND>
+__host__ __device__ __forceinline__ bool draw_point_fp64_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
+                                                         df (&p)[NEXT][4], double& wps, double& shat, uint8_t* bins) {
+  double pd[NEXT][4];
+  const bool ok = draw_point<NEXT, KIND>(kin, seed, event, att, pd, wps, shat, bins);
+  if (ok) {
+#pragma unroll
+    for (int k = 0; k < NEXT; ++k) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) p[k][m] = from_double(pd[k][m]);
+    }
+  }
+  return ok;
+}
+
 // one mixed-precision draw: double-float RAMBO (massless, with the massive
-// rescaling, or resonance-mapped) or tt~ chain; the two-body generator in FP64
-// split into double-floats
+// rescaling, or resonance-mapped) or tt~ chain; the two-body and y/pT generators in
+// FP64 split into double-floats
 template <int NEXT, int KIND = kKindAny>
 __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64_t seed, uint64_t event, int att,
                                               df (&p)[NEXT][4], double& wps, double& shat,
@@ -952,16 +1160,7 @@ __host__ __device__ __forceinline__ bool draw_point_df(const KinDev& kin, uint64
     if (bins) wps *= to_double(jac);
     return ok && pass_cuts_df<NEXT>(kin, p);
   }
-  double pd[NEXT][4];
-  const bool ok = draw_point<NEXT, KIND>(kin, seed, event, att, pd, wps, shat, bins);
-  if (ok) {
-#pragma unroll
-    for (int k = 0; k < NEXT; ++k) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) p[k][m] = from_double(pd[k][m]);
-    }
-  }
-  return ok;
+  return draw_point_fp64_df<NEXT, KIND>(kin, seed, event, att, p, wps, shat, bins);
 }
 
 }  // namespace me

@@ -727,6 +727,9 @@ cudaError_t launch_ps_kind(const KinDev* kin, const StepArgs* a, int grid, cudaS
         return cudaSuccess;
       }
       break;
+    case ME_PS_YPT:  // one instantiation with the grid code (it runs without a grid as well)
+      k_ps<P, MIXED, ME_PS_YPT, true><<<grid, kThreads, 0, s>>>(*kin, *a);
+      return cudaSuccess;
     default:
       break;
   }
@@ -767,6 +770,42 @@ cudaError_t launch_eval(int prec, const double* mom, int64_t n, double* out, con
   return cudaGetLastError();
 }
 
+// k_gen: phase-space points only, for a generator compiled as a fixed kind (the y/pT
+// generator, which the fused kernels leave out): each thread redraws its own point until
+// it passes, up to kin.max_attempts; outputs as k_xsec without |M|^2.
+template <class P, bool MIXED, int KIND>
+__global__ void __launch_bounds__(kThreads) k_gen(KinDev kin, uint64_t seed, uint64_t offset, int64_t n,
+                                                  double* __restrict__ mom_out, double* __restrict__ wps_out,
+                                                  double* __restrict__ shat_out, int32_t* __restrict__ tries_out,
+                                                  int* status) {
+  constexpr int NEXT = P::NEXT;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double wps = 0.0, shat = 1.0;
+    double q[NEXT][4];
+    int att = 0;
+    bool ok = false;
+    for (; att < kin.max_attempts && !ok; ++att) ok = draw_point<NEXT, KIND>(kin, seed, offset + (uint64_t)i, att, q, wps, shat);
+    if (!ok) {
+      atomicOr(status, 1);
+      wps = 0.0;
+    }
+    if (MIXED && ok) {  // the mixed path's momenta are the double-float split of the FP64 draw
+#pragma unroll
+      for (int k = 0; k < NEXT; ++k)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) q[k][m] = to_double(from_double(q[k][m]));
+    }
+    if (mom_out)
+#pragma unroll
+      for (int k = 0; k < NEXT; ++k)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) mom_out[(int64_t)(k * 4 + m) * n + i] = q[k][m];
+    if (wps_out) wps_out[i] = wps;
+    if (shat_out) shat_out[i] = shat;
+    if (tries_out) tries_out[i] = ok ? att : kin.max_attempts;
+  }
+}
+
 template <class P>
 cudaError_t launch_serve(int prec, const ServeCtl* ctl, const double* params, cudaStream_t s, int grid) {
   typename P::Params prm;
@@ -791,6 +830,16 @@ cudaError_t launch_xsec(int prec, const KinDev* kin, uint64_t seed, uint64_t off
                         int32_t* tries_out, int* status, int eval_me, cudaStream_t s, int grid) {
   typename P::Params prm;
   memcpy(&prm, params, sizeof(prm));
+  if (kin->kind == ME_PS_YPT) {  // points only (the fused kernel does not compile this generator)
+    if (eval_me) return cudaErrorNotSupported;
+    if (prec == ME_FP64)
+      k_gen<P, false, ME_PS_YPT><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, mom_out, wps_out, shat_out,
+                                                           tries_out, status);
+    else
+      k_gen<P, true, ME_PS_YPT><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, mom_out, wps_out, shat_out,
+                                                          tries_out, status);
+    return cudaGetLastError();
+  }
   if (prec == ME_FP64)
     k_xsec<P, false><<<grid, kThreads, 0, s>>>(*kin, seed, offset, n, prm, partials, me2_out, mom_out, wps_out,
                                                shat_out, tries_out, status, eval_me);

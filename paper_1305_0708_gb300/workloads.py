@@ -165,7 +165,33 @@ VARIANTS = {
                  "massive RAMBO at sqrt(s)=1 TeV, 2^20 points, seed 12"),
 }
 
-KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3}
+KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3, "ypt": 4}
+
+# The paper's selection, Eqs. 8-11: jets |eta| < 5, pT > 20 GeV and pT_ij = min(pT_i, pT_j) Delta R_ij
+# > 20 GeV for every jet pair; b jets from top decays and charged leptons |eta| < 2.5, pT > 20 GeV
+PAPER_CUTS = dict(jet_pt=20.0, jet_eta=5.0, jet_ptij=20.0, b_pt=20.0, b_eta=2.5, lep_pt=20.0, lep_eta=2.5)
+JET, BJET, LEPTON = 1, 2, 3
+
+# Workloads on the paper's own phase-space parametrisation (Eq. 13, App. A.1, Eq. 17, App. A.2) and
+# selection (Eqs. 8-11), at the same partonic energies as the workloads above
+PAPER_PS = {
+    "udx_epvegg_ypt": dict(
+        process="u d~ > e+ ve g g", kind="ypt", sqrt_s=1000.0, n=1 << 20, seed=31, s_ident=0.5,
+        objects=[dict(legs=(4,), y_max=5.0, pt_min=20.0, pt_max=480.0),
+                 dict(legs=(5,), y_max=5.0, pt_min=20.0, pt_max=480.0),
+                 dict(legs=(2, 3), res_mass=80.4, res_width=2.085, y_max=5.0, pt_min=0.0, pt_max=480.0)],
+        leg_class=(0, 0, LEPTON, 0, JET, JET),
+        describe="u d~ > e+ ve g g at sqrt(s)=1 TeV on the paper's y, pT, phi parametrisation: the two "
+                 "gluons and the W -> e+ ve resonance (Breit-Wigner, isotropic decay) as objects, pT "
+                 "mapped by Eq. 17; the paper's cuts (jets |eta|<5, pT>20, pT_ij>20; lepton |eta|<2.5, "
+                 "pT>20), 2^20 accepted points, seed 31"),
+    "gg_gggg_ypt": dict(
+        process="g g > g g g g", kind="ypt", sqrt_s=1500.0, n=1 << 18, seed=33, s_ident=1.0 / 24.0,
+        objects=[dict(legs=(k,), y_max=5.0, pt_min=20.0, pt_max=700.0) for k in (2, 3, 4, 5)],
+        leg_class=(0, 0, JET, JET, JET, JET),
+        describe="g g > g g g g at sqrt(s)=1.5 TeV on the paper's y, pT, phi parametrisation with the "
+                 "paper's jet cuts (|eta|<5, pT>20, pT_ij>20), 2^18 accepted points, seed 33"),
+}
 
 
 def kin_args(w):
@@ -174,4 +200,5 @@ def kin_args(w):
     return dict(kind=KIND[w["kind"]], sqrt_s=w.get("sqrt_s", 0.0), sqrt_s_range=w.get("sqrt_s_range", (0.0, 0.0)),
                 masses=w.get("masses", ()), cut_legs=cut.get("legs", ()), pt_min=cut.get("pt_min", 0.0),
                 eta_max=cut.get("eta_max", 0.0), dr_min=cut.get("dr_min", 0.0), s_ident=w["s_ident"],
-                res_mass=w.get("res_mass", 0.0), res_width=w.get("res_width", 0.0))
+                res_mass=w.get("res_mass", 0.0), res_width=w.get("res_width", 0.0), objects=w.get("objects", ()),
+                leg_class=w.get("leg_class"), paper_cuts=PAPER_CUTS if w.get("leg_class") else None)

@@ -61,8 +61,13 @@ def oracle_kin(w):
     elif w["kind"] == "rambo_bw":
         k = {"kind": "rambo_bw", "sqrt_s": w["sqrt_s"], "n_final": len(opr_legs(w)) - 2,
              "res_mass": w["res_mass"], "res_width": w["res_width"]}
+    elif w["kind"] == "ypt":
+        k = {"kind": "ypt", "sqrt_s": w["sqrt_s"], "n_final": len(opr_legs(w)) - 2, "objects": w["objects"]}
     else:
         k = {"kind": "ttbar", "sqrt_s_range": w["sqrt_s_range"]}
+    if w.get("leg_class"):
+        from paper_1305_0708_gb300.workloads import PAPER_CUTS
+        k["paper_cuts"] = {"leg_class": list(w["leg_class"]), "thresholds": dict(PAPER_CUTS)}
     if w.get("cuts"):
         c = w["cuts"]
         k["cuts"] = {"legs": list(c["legs"]), "pt_min": c["pt_min"], "eta_max": c["eta_max"], "dr_min": c["dr_min"]}
@@ -460,3 +465,53 @@ def test_scalar_quartic_parity(B, prec):
         rel = np.abs(got / ref - 1)
         assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
     assert math.isfinite(float(got.sum()))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("key", ["udx_epvegg_ypt", "gg_gggg_ypt"])
+def test_paper_parametrisation_parity(B, key, prec):
+    """The paper's y, pT, phi parametrisation (Eq. 13, App. A.1, Eq. 17, App. A.2) with its cuts
+    (Eqs. 8-11) on the device against the oracle's: draws per point bit-exact, momenta within
+    4e-12 sqrt(s), weights within 1e-12 (the generator runs in FP64 on both paths); the Monte Carlo
+    sums against the oracle's accumulate."""
+    from paper_1305_0708_gb300.workloads import PAPER_PS
+    w = PAPER_PS[key]
+    n_ext = len(opr_legs(w))
+    n, off = 600 if key == "gg_gggg_ypt" else 2000, 4242
+    kin = B.make_kin(**kin_args(w))
+    h = B.me_create(w["process"], None, prec)
+    mom = torch.empty(n_ext * 4 * n, dtype=torch.float64, device="cuda")
+    wt = torch.empty(n, dtype=torch.float64, device="cuda")
+    sh = torch.empty(n, dtype=torch.float64, device="cuda")
+    tries = torch.empty(n, dtype=torch.int32, device="cuda")
+    B.me_generate(h, w["seed"], off, n, kin, mom, wt, sh, tries)
+    me2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    mom2 = torch.empty(n_ext * 4 * n, dtype=torch.float64, device="cuda")
+    acc = B.xsec_step(h, w["seed"], off, n, kin, None, None, me2, mom2)
+    torch.cuda.synchronize()
+    with pytest.raises(B.MeError):  # the fused allocation-free step does not compile this generator
+        B.xsec_step_noalloc(h, w["seed"], off, n, kin)
+    B.me_destroy(h)
+    P, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(off, off + n))
+    assert np.array_equal(tries.cpu().numpy(), T)
+    assert np.abs(from_soa(mom, n_ext, n) - P).max() <= 4e-12 * w["sqrt_s"]
+    assert np.abs(from_soa(mom2, n_ext, n) - P).max() <= 4e-12 * w["sqrt_s"]
+    assert np.allclose(wt.cpu().numpy(), W, rtol=1e-12, atol=0)
+    fn = ORACLE["udx_epvegg" if key == "udx_epvegg_ypt" else "gg_gggg"]
+    sw, sw2, nacc, ntry = oxs.accumulate(fn(P, PAR), W, S, T, w["s_ident"])
+    assert acc.n_acc == nacc == n and acc.n_try == ntry
+    if prec == 0:
+        # point by point on these points made consistent to rounding (the generated ones conserve
+        # momentum to ~1e-14 of sqrt(s) only), then the sums
+        Pc = consistent(P, (0.0,) * n_ext)
+        ref = fn(Pc, PAR)
+        got = eval_gpu(B, w["process"], Pc, 0)
+        assert np.all(np.abs(got - ref) <= fp64_tolerance(fn, Pc, ref))
+        assert acc.sum_w == pytest.approx(sw, rel=1e-11) and acc.sum_w2 == pytest.approx(sw2, rel=1e-11)
+    else:
+        Pg = from_soa(mom2, n_ext, n).copy()
+        rel = np.abs(me2.cpu().numpy() / fn(Pg, PAR) - 1)
+        assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
+        # a sum of a few hundred heavy-tailed weights carries the relative error of its largest
+        # terms (six gluons: up to ~2e-5 per point there)
+        assert acc.sum_w == pytest.approx(sw, rel=1e-4)
