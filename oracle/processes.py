@@ -53,6 +53,12 @@ Functions and their pins (tests/test_oracle_processes.py):
                    fifteen diagrams cancel only with the quartic WWAA and WWAZ vertices),
                    the soft-photon limit against the eikonal factor times u u~ > w+ w-, boosts
   us_dch          u s > d c h    (WW fusion): closed form from the V-A traces, exact per point
+  us_dchg         u s > d c h g  (WW fusion plus one jet): Ward identity, the soft-gluon limit
+                   against 2 C_F (S_ud + S_sc) times u s > d c h (the lines' colours do not
+                   interfere), boosts
+  udx_wpgg, uux_zgg  u d~ > w+ g g, u u~ > z g g (V plus two jets): Ward identity for each gluon,
+                   Bose symmetry, the soft limit of either gluon against the colour-correlated
+                   eikonal factor of q, q~, g times q q~ > V g (closed form), boosts
   us_dchh         u s > d c h h  (WW fusion): its W W > h h core (_ww_hh, the code
                    it runs) pinned by the gauge cancellation of the longitudinal
                    on-shell W+ W- > h h amplitude (wpwm_hh_amplitudes calls the same
@@ -744,6 +750,37 @@ def us_dch(P, par=SMParams()):
     return tot / 36.0
 
 
+def us_dchg(P, par=SMParams(), eps_override=None):
+    """u(p0) s(p1) > d(p2) c(p3) H(p4) g(p5) by W+ W- fusion plus one jet: the gluon from either quark
+    line, before or after that line's W vertex (four diagrams).  The W seen by the gluon's line is the
+    other line's propagated current through the WWH vertex and a W propagator carrying the momentum the
+    line gives away.  Colour: each line keeps its own, (t^a)_{d u} delta_{c s} or delta_{d u}
+    (t^a)_{c s}.  eps_override replaces the gluon's polarisation vector."""
+    p = [P[:, k] for k in range(6)]
+    gw = par.g / np.sqrt(2.0)
+    gwwh = par.g * par.mW
+    d3 = np.eye(3, dtype=complex)
+    c1 = np.einsum("adu,cs->udsca", _T, d3)
+    c2 = np.einsum("du,acs->udsca", d3, _T)
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_F, HEL_F, HEL_V):
+        ub_d, u_u = bar(u_spinor(p[2], h[2])), u_spinor(p[0], h[0])
+        ub_c, u_s = bar(u_spinor(p[3], h[3])), u_spinor(p[1], h[1])
+        eg = polarisation(p[5], h[4]).conj() if eps_override is None else eps_override.astype(complex)
+        G = (vector_insertion(eg, par.gs, par.gs), p[5])
+        amps = []
+        for (row, col, pin, pout), (orow, ocol, opin, opout) in (((ub_d, u_u, p[0], p[2]), (ub_c, u_s, p[1], p[3])),
+                                                                   ((ub_c, u_s, p[1], p[3]), (ub_d, u_u, p[0], p[2]))):
+            qo = opin - opout
+            Wo = vector_prop(qo, ffv_current(orow, ocol, gw, 0.0), par.mW, par.wW)
+            q = pin - pout - p[5]
+            V = vector_prop(q, 1j * gwwh * Wo, par.mW, par.wW)
+            W = (vector_insertion(V, gw, 0.0), q)
+            amps.append((fermion_line(row, col, pin, [G, W]) + fermion_line(row, col, pin, [W, G])) / 1j)
+        tot = tot + colour.colour_sum(amps, [c1, c2])
+    return tot / 36.0
+
+
 # --------------------------------------------------------------------------
 # W+ W- > h h with on-shell external W bosons (gauge-cancellation pin of the
 # WWH / WWHH / HHH couplings used by u s > d c h h)
@@ -1030,6 +1067,50 @@ def _qqx_vg(P, par, gl, gr, mV):
         A = fermion_line(vb, u, p[0], [G, V]) + fermion_line(vb, u, p[0], [V, G])
         tot = tot + colour.colour_sum([A / 1j], [cT])
     return tot / 36.0
+
+
+def _qqx_vgg(P, par, gl, gr, mV, eps_override=None):
+    """q(p0) q~'(p1) > V(p2) g(p3) g(p4) with an on-shell massive V of coupling i gamma^mu (gl P_L +
+    gr P_R): the V and both gluons in all six orders along the quark line (colour strings of the two
+    gluon orders), and the V with the pair from the three-gluon vertex in both orders (f^{abc} t^c).
+    eps_override: optional {leg: vector[N,4]} replacing a gluon polarisation (Ward identity)."""
+    p = [P[:, k] for k in range(5)]
+    gs = par.gs
+    colours = {o: _colour_string([x for x in o if x != "V"], 2) for o in itertools.permutations(["V", 0, 1])}
+    cG = _colour_string(["G"], 2, with_f=(0, 1))
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, HEL_V, HEL_V):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ev = polarisation(p[2], h[2], mass=mV).conj()
+        eg = [polarisation(p[3], h[3]).conj(), polarisation(p[4], h[4]).conj()]
+        if eps_override:
+            for leg, vec in eps_override.items():
+                eg[leg - 3] = vec.astype(complex)
+        ins = {"V": (vector_insertion(ev, gl, gr), p[2]), 0: (vector_insertion(eg[0], gs, gs), p[3]),
+               1: (vector_insertion(eg[1], gs, gs), p[4])}
+        amps, cols = [], []
+        for order, c in colours.items():
+            amps.append(fermion_line(vb, u, p[0], [ins[x] for x in order]) / 1j)
+            cols.append(c)
+        X = vvv_out(eg[0], -p[3], eg[1], -p[4], p[3] + p[4], gs)
+        insG = (vector_insertion(vector_prop(p[3] + p[4], X), gs, gs), p[3] + p[4])
+        for order in (["V", "G"], ["G", "V"]):
+            amps.append(fermion_line(vb, u, p[0], [ins["V"] if x == "V" else insG for x in order]) / 1j)
+            cols.append(cG)
+        tot = tot + colour.colour_sum(amps, cols)
+    return tot / 36.0
+
+
+def udx_wpgg(P, par=SMParams(), eps_override=None):
+    """u d~ > W+ g g (on-shell W plus two jets)."""
+    return _qqx_vgg(P, par, par.g / np.sqrt(2.0), 0.0, par.mW, eps_override)
+
+
+def uux_zgg(P, par=SMParams(), eps_override=None):
+    """u u~ > Z g g (on-shell Z plus two jets)."""
+    gl, gr = _z_couplings("u", par)
+    return _qqx_vgg(P, par, gl, gr, par.mZ, eps_override)
 
 
 def _uux_va(P, par, gl, gr, mV):
@@ -1372,6 +1453,9 @@ PROCESSES = {
     "u u~ > e+ e-": uux_epem,
     "u d~ > e+ ve": udx_epve,
     "u d~ > e+ ve g": udx_epveg,
+    "u d~ > w+ g g": udx_wpgg,
+    "u u~ > z g g": uux_zgg,
+    "u s > d c h g": us_dchg,
     "u u~ > g g": uux_gg,
     "u d~ > e+ ve g g": udx_epvegg,
     "g g > t t~": gg_ttx,

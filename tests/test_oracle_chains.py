@@ -244,3 +244,92 @@ def test_six_gluon_ward_identity(leg):
     ref = pr.gluons(P)
     bad = pr.gluons(P, eps_override={leg: P[:, leg]})
     assert np.all(bad < 1e-24 * ref * P[:, leg, 0] ** 2)
+
+
+# ---------------------------------------------------------------------------
+# V + 2 jets and WBF H + 1 jet: Ward identity, Bose symmetry, soft limits, boosts
+# ---------------------------------------------------------------------------
+def _add_soft_massive(base, k, masses):
+    """Append a gluon of momentum k to a final state with the given masses (base in its centre-of-mass
+    frame): the final three-momenta are scaled by the xi with sum_i sqrt(m_i^2 + xi^2 |p_i|^2) = M_Q,
+    M_Q the invariant mass of P - k, and boosted to P - k (momentum conservation and masses exact,
+    tending to base as k -> 0)."""
+    n, m = base.shape[:2]
+    P = base[:, 0] + base[:, 1]
+    Q = P - k
+    MQ = np.sqrt(mdot(Q, Q))
+    out = np.zeros((n, m + 1, 4))
+    out[:, :2] = base[:, :2]
+    ms = np.asarray(masses, dtype=float)
+    for i in range(n):
+        q3 = base[i, 2:, 1:]
+        a2 = (q3 ** 2).sum(axis=1)
+        xi = 1.0
+        for _ in range(60):  # Newton on f(xi) = sum sqrt(m^2 + xi^2 a2) - MQ
+            e = np.sqrt(ms ** 2 + xi * xi * a2)
+            xi -= (e.sum() - MQ[i]) / (xi * (a2 / e).sum())
+        fin = np.zeros((m - 2, 4))
+        fin[:, 1:] = xi * q3
+        fin[:, 0] = np.sqrt(ms ** 2 + xi * xi * a2)
+        out[i, 2:m] = boost(fin, Q[i, 1:] / Q[i, 0])
+    out[:, m] = k
+    return out
+
+
+def _massive_points(sqrt_s, masses, n, seed):
+    from kinematics import consistent
+    u = np.random.default_rng(seed).uniform(0.05, 0.95, (n, 4 * len(masses)))
+    pf, _ = ps.rambo_massive(sqrt_s, list(masses), u)
+    P = np.zeros((n, len(masses) + 2, 4))
+    P[:, 0], P[:, 1] = ps.incoming(sqrt_s, n)
+    P[:, 2:] = pf
+    return consistent(P, (0.0, 0.0) + tuple(masses))
+
+
+@pytest.mark.parametrize("which", ["udx_wpgg", "uux_zgg"])
+def test_v_plus_two_jets_ward_bose_soft_and_boosts(which):
+    """q q~ > V g g: each gluon's eps -> k gives zero (exactly on-shell inputs); swapping the gluons
+    leaves |M|^2 unchanged; either gluon soft: |M|^2 -> eikonal(q, q~, g) |M|^2(q q~ > V g) (closed
+    form), the deviation falling in proportion to its energy; boosts."""
+    f = getattr(pr, which)
+    f0 = {"udx_wpgg": pr.udx_wpg, "uux_zgg": pr.uux_zg}[which]
+    mV = PAR.mW if which == "udx_wpgg" else PAR.mZ
+    P = _massive_points(600.0, (mV, 0.0, 0.0), 4, seed=400)
+    ref = f(P, PAR)
+    for leg in (3, 4):
+        bad = f(P, PAR, eps_override={leg: P[:, leg]})
+        assert np.all(bad < 1e-24 * ref * P[:, leg, 0] ** 2)
+    assert np.allclose(f(P[:, [0, 1, 2, 4, 3]], PAR), ref, rtol=1e-12)
+    from test_oracle_processes import random_lorentz
+    assert np.allclose(f(random_lorentz(P, 401), PAR), ref, rtol=1e-10)
+    base = _massive_points(600.0, (mV, 0.0), 4, seed=402)
+    m2 = f0(base, PAR)
+    nhat = np.array([0.48, -0.36, 0.8])
+    devs = []
+    for w in (1e-2, 1e-3):
+        k = np.concatenate([[w], w * nhat])[None, :].repeat(len(base), 0)
+        Q = _add_soft_massive(base, k, (mV, 0.0))
+        devs.append(np.max(np.abs(f(Q, PAR) / (_qqg_eikonal(Q, k, 3) * m2) - 1)))
+    assert devs[1] < 1e-3 and devs[1] < devs[0] / 5, devs
+
+
+def test_wbf_higgs_plus_jet_ward_soft_and_boosts():
+    """u s > d c H g: the gluon's eps -> k gives zero (exactly on-shell inputs); as the gluon gets soft,
+    |M|^2 -> g_s^2 2 C_F (S_ud + S_sc) |M|^2(u s > d c H) (the two lines' colours do not interfere,
+    Tr t^a = 0), the deviation falling in proportion to its energy; boosts."""
+    P = _massive_points(1000.0, (0.0, 0.0, PAR.mH, 0.0), 4, seed=410)
+    ref = pr.us_dchg(P, PAR)
+    bad = pr.us_dchg(P, PAR, eps_override=P[:, 5])
+    assert np.all(bad < 1e-24 * ref * P[:, 5, 0] ** 2)
+    from test_oracle_processes import random_lorentz
+    assert np.allclose(pr.us_dchg(random_lorentz(P, 411), PAR), ref, rtol=1e-10)
+    base = _massive_points(1000.0, (0.0, 0.0, PAR.mH), 4, seed=412)
+    m2 = pr.us_dch(base, PAR)
+    nhat = np.array([0.6, 0.0, 0.8])
+    devs = []
+    for w in (1e-2, 1e-3):
+        k = np.concatenate([[w], w * nhat])[None, :].repeat(len(base), 0)
+        Q = _add_soft_massive(base, k, (0.0, 0.0, PAR.mH))
+        eik = PAR.gs ** 2 * (4.0 / 3.0) * 2 * (_S(Q, 0, 2, k) + _S(Q, 1, 3, k))
+        devs.append(np.max(np.abs(pr.us_dchg(Q, PAR) / (eik * m2) - 1)))
+    assert devs[1] < 1e-3 and devs[1] < devs[0] / 5, devs
