@@ -57,6 +57,9 @@ PROCESSES = [
     ("u u~ > w+ w- g", []),
     ("g g > w+ d u~", []),
     ("g g > z u u~", []),
+    ("u d~ > w+ g g", []),
+    ("u u~ > z g g", []),
+    ("u s > d c h g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -163,6 +163,22 @@ VARIANTS = {
         seed=12, cuts=None, s_ident=1.0,
         describe="g g > t t~ H (eight diagrams: the Higgs from every top line through the FFS Yukawa vertex), "
                  "massive RAMBO at sqrt(s)=1 TeV, 2^20 points, seed 12"),
+    "udx_wpgg": dict(
+        process="u d~ > w+ g g", kind="rambo", sqrt_s=600.0, masses=(0, 0, 80.4, 0, 0), n=1 << 20, seed=41,
+        cuts=dict(legs=(3, 4), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,
+        describe="u d~ > W+ g g (on-shell W plus two jets, eight diagrams), massive RAMBO at sqrt(s)=600 GeV, "
+                 "gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^20 accepted points, seed 41"),
+    "uux_zgg": dict(
+        process="u u~ > z g g", kind="rambo", sqrt_s=600.0, masses=(0, 0, 91.1876, 0, 0), n=1 << 20, seed=42,
+        cuts=dict(legs=(3, 4), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,
+        describe="u u~ > Z g g (on-shell Z plus two jets, eight diagrams), massive RAMBO at sqrt(s)=600 GeV, "
+                 "gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^20 accepted points, seed 42"),
+    "us_dchg": dict(
+        process="u s > d c h g", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 0, 0, 125.0, 0), n=1 << 20, seed=43,
+        cuts=dict(legs=(2, 3, 5), pt_min=20.0, eta_max=5.0, dr_min=0.4), s_ident=1.0,
+        describe="u s > d c H g (W+ W- fusion plus one jet, the gluon from either quark line), massive RAMBO at "
+                 "sqrt(s)=1 TeV, the three jets pT>20, |eta|<5, DeltaR>0.4 (the gluon's collinear limits "
+                 "with the outgoing quarks cut away), 2^20 accepted points, seed 43"),
 }
 
 KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3, "ypt": 4}

@@ -390,7 +390,7 @@ def test_identical_quarks_parity(B, prec):
                                  "uux_zg", "ug_wpd", "uux_zzg", "gg_ttxg", "uux_zhg", "udx_wpzg",
                                  "uux_wpwmg", "gg_wpdux", "gg_zuux", "udx_wphg",
                                  "uux_ttx", "uux_ttxg", "us_dch", "udx_wpa",
-                                 "uux_za", "uux_aa"])
+                                 "uux_za", "uux_aa", "udx_wpgg", "uux_zgg", "us_dchg"])
 def test_massive_final_state_parity(B, key, prec):
     """u u~ > Z Z (identical massive vectors, identical-particle factor 1/2), u u~ > Z H (ZZH vertex,
     external scalar), u d~ > W+ H (WWH vertex), u u~ > W+ W- gamma (the electroweak quartic
@@ -408,7 +408,8 @@ def test_massive_final_state_parity(B, key, prec):
           "udx_wpzg": opr.udx_wpzg, "uux_wpwmg": opr.uux_wpwmg, "gg_wpdux": opr.gg_wpdux,
           "gg_zuux": opr.gg_zuux, "udx_wphg": opr.udx_wphg,
           "uux_ttx": opr.uux_ttx, "uux_ttxg": opr.uux_ttxg, "us_dch": opr.us_dch, "udx_wpa": opr.udx_wpa,
-          "uux_za": opr.uux_za, "uux_aa": opr.uux_aa}[key]
+          "uux_za": opr.uux_za, "uux_aa": opr.uux_aa, "udx_wpgg": opr.udx_wpgg, "uux_zgg": opr.uux_zgg,
+          "us_dchg": opr.us_dchg}[key]
     n = 1500
     P0, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(n))
     P = consistent(P0, masses_of(w, P0.shape[1]))

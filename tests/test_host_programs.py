@@ -60,6 +60,9 @@ CASES = {
     "g g > z u u~": (opr.gg_zuux, 600.0, (91.1876, 0.0, 0.0), (3, 4)),
     "u u~ > t t~": (opr.uux_ttx, 800.0, (175.0, 175.0), ()),
     "u u~ > t t~ g": (opr.uux_ttxg, 1000.0, (175.0, 175.0, 0.0), (4,)),
+    "u d~ > w+ g g": (opr.udx_wpgg, 600.0, (80.4, 0.0, 0.0), (3, 4)),
+    "u u~ > z g g": (opr.uux_zgg, 600.0, (91.1876, 0.0, 0.0), (3, 4)),
+    "u s > d c h g": (opr.us_dchg, 1000.0, (0.0, 0.0, 125.0, 0.0), (5,)),
 }
 
 
