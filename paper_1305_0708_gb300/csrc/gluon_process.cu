@@ -8,12 +8,16 @@
 //
 // Colour sum, Eq. 6 with the exact integer matrix C_num = den C:
 //   FP64 path:  y = C_num x on the FP64 CUDA cores, then x . y;
-//   mixed path: on the tensor cores.  Every row x of the pair is scaled by a
-//   power of two per helicity and split into FP16 hi + lo parts (22 bits); the
-//   off-diagonal part of C_num has integer entries below 2048 and is exact in
-//   FP16; D = C_off [x_hi x_lo]^T accumulates in FP32 (mma.sync m16n8k16);
-//   the constant diagonal of C_num (3641 for six gluons, not exact in FP16) is
-//   added on the CUDA cores in the epilogue, which also forms x . (D + c x).
+//   mixed path: on the tensor cores (tcgen05).  Every row x of the pair is scaled
+//   by a power of two per helicity and split into FP16 hi + lo parts (22 bits);
+//   the off-diagonal part of C_num has integer entries below 2048 and is exact in
+//   FP16.  One thread issues D = C_off [x_hi | x_lo]^T as tcgen05.mma (M = 128
+//   colour rows, N = 16 = 8 rows x hi/lo, K = 16 per instruction, FP32
+//   accumulation in tensor memory), both operands K-major in shared memory; the
+//   commit arrives on an mbarrier, four warps read D back with tcgen05.ld; the
+//   constant diagonal of C_num (3641 for six gluons, not exact in FP16) is added
+//   on the CUDA cores in that epilogue, which also forms x . (D_hi + D_lo + c x).
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <cuda_fp16.h>
@@ -51,10 +55,11 @@ struct Cfg {
   static constexpr int NROW = 4 * HP;
 };
 constexpr int NROW = Cfg<float>::NROW;     // rows of the tensor-core colour step
-constexpr int MP = (T::NAMP + 15) / 16 * 16;  // colour rows padded to the MMA tile
-constexpr int KP = (T::NAMP + 31) / 32 * 32;  // colour columns padded to two MMA k-steps
+constexpr int MT = 128;                    // colour rows of the tcgen05 tile (C zero padded)
+constexpr int NT = 2 * NROW;               // its columns: the pair's rows, hi parts then lo parts
+constexpr int KP = (T::NAMP + 31) / 32 * 32;  // colour columns padded to whole K-steps of 16
 constexpr int XLD = KP + 4;                // FP32 row stride: epilogue reads hit 32 distinct banks
-constexpr int HLD = KP + 8;                // FP16 row stride (272 B for KP = 128): ldmatrix without conflicts
+static_assert(T::NAMP <= MT, "the colour basis fits one tcgen05 tile");
 constexpr float kDiag = ME_CAT(kColourDiag, NGLUON);
 static_assert(ME_CAT(kColourOffFitsHalf, NGLUON), "off-diagonal colour integers must be exact in FP16");
 static_assert(NROW == 8, "one n8 MMA tile per helicity pair");
@@ -154,29 +159,54 @@ struct Shared {
   R red[Cfg<R>::THREADS / 32];
 };
 
-// Tensor-core operands of the mixed path (dynamic shared memory after Shared<float>)
-struct TcShared {
-  __half Xh[NROW][HLD];   // scaled amplitude rows, high and low FP16 parts
-  __half Xl[NROW][HLD];
-  __half Ch[MP][HLD];     // C_num with zero diagonal, zero padded to MP x KP
+// Tensor-core operands of the mixed path (dynamic shared memory after Shared<float>), K-major
+// without swizzle: an element (row r, column k) of an operand sits at byte
+//   (r / 8) * (KP / 8) * 128 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// i.e. 8 x 16-byte core matrices, 128 B apart along K (the descriptor's leading-dimension
+// offset) and (KP / 8) * 128 B apart between groups of 8 rows (its stride-dimension offset).
+struct alignas(128) TcShared {
+  __half C[MT * KP];     // C_num with zero diagonal, zero padded to MT x KP
+  __half X[NT * KP];     // rows 0..7: high FP16 parts of the pair's scaled rows; 8..15: low parts
+  uint64_t mbar;         // completion of the pair's MMAs (tcgen05.commit)
+  uint32_t tmem;         // tensor-memory address of the 128 x 32 FP32 accumulator
+  uint32_t uses;         // completed pairs (the parity of the next wait)
+  int failed;            // a wait ran out (the kernel reports it and stops using the tensor cores)
 };
-
-// ---------------------------------------------------------------------------
-// tensor-core helpers (inline PTX)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
+__device__ __forceinline__ uint32_t tc_off(int r, int k) {
+  return (uint32_t)((r >> 3) * (KP / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+// ---------------------------------------------------------------------------
+// tcgen05 helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (8-row group) byte
+// offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// kind::f16 instruction descriptor: FP32 accumulator, FP16 A and B, both K-major, N >> 3, M >> 4
+constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
+constexpr uint32_t kTmemCols = 32;  // allocation granule (the accumulator uses NT columns)
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait for a phase of the mbarrier: false if it did not complete within about 0.1 s
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
 }
 
 // scale 2^es with es = 141 - emax puts every value of the rows below 2^15
@@ -192,7 +222,7 @@ __device__ __forceinline__ unsigned exp_bits(float x) { return (__float_as_uint(
 __device__ float colour_pair(Shared<float>& sh, TcShared* tcp) {
   TcShared& tc = *tcp;
   const int tid = threadIdx.x;
-  // FP16 hi/lo split of the scaled rows (columns beyond NAMP are zero)
+  // FP16 hi/lo split of the scaled rows (columns beyond NAMP are zero), in the operand layout
   for (int i = tid; i < NROW * (KP / 2); i += blockDim.x) {
     const int n = i / (KP / 2), k = 2 * (i % (KP / 2));
     const float s = pow2f(scale_exp(sh.emax[n >> 2]));
@@ -203,41 +233,66 @@ __device__ float colour_pair(Shared<float>& sh, TcShared* tcp) {
     }
     const __half2 h = __floats2half2_rn(x0, x1);
     const float2 hf = __half22float2(h);
-    *reinterpret_cast<__half2*>(&tc.Xh[n][k]) = h;
-    *reinterpret_cast<__half2*>(&tc.Xl[n][k]) = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    *reinterpret_cast<__half2*>(reinterpret_cast<char*>(tc.X) + tc_off(n, k)) = h;
+    *reinterpret_cast<__half2*>(reinterpret_cast<char*>(tc.X) + tc_off(n + NROW, k)) =
+        __floats2half2_rn(x0 - hf.x, x1 - hf.y);
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the operands, visible to the tensor cores
   __syncthreads();
+  const uint32_t parity = tc.uses & 1u;
+  const bool run = !tc.failed;
+  if (tid == 0 && run) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t a0 = smem_addr(tc.C), b0 = smem_addr(tc.X);
+#pragma unroll
+    for (int kk = 0; kk < KP / 16; ++kk) {  // two core matrices (16 columns) per step
+      const uint64_t a = tc_desc(a0 + 256u * kk, 128u, (KP / 8) * 128u);
+      const uint64_t b = tc_desc(b0 + 256u * kk, 128u, (KP / 8) * 128u);
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tc.tmem),
+          "l"(a), "l"(b), "r"(kTcIdesc), "r"((uint32_t)(kk > 0))
+          : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(&tc.mbar))
+                 : "memory");
+  }
+  // block-uniform outcome: tcgen05.ld below is a whole-warp instruction
+  const bool ok = __syncthreads_and(run && mbar_wait_bounded(&tc.mbar, parity)) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   float part = 0.0f;
   const int warp = tid >> 5, lane = tid & 31;
-  for (int mt = warp; mt < MP / 16; mt += blockDim.x / 32) {
-    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  // D[m][n]: colour row m = 32 warp + lane, columns n (hi parts) and n + NROW (lo parts)
+  if (warp < MT / 32 && ok) {
+    uint32_t r[NT];
+    const uint32_t taddr = tc.tmem + ((uint32_t)(32 * warp) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int m = 32 * warp + lane;
+    if (m < T::NAMP) {
 #pragma unroll
-    for (int kk = 0; kk < KP / 32; ++kk) {
-      uint32_t bh[4], bl[4];
-      // matrices j = 0..3: rows n = 0..7, columns 32 kk + 8 j .. + 7 (B fragments of two k-steps)
-      ldsm_x4(bh, &tc.Xh[lane & 7][32 * kk + 8 * (lane >> 3)]);
-      ldsm_x4(bl, &tc.Xl[lane & 7][32 * kk + 8 * (lane >> 3)]);
-#pragma unroll
-      for (int sub = 0; sub < 2; ++sub) {
-        uint32_t a[4];
-        ldsm_x4(a, &tc.Ch[16 * mt + (lane & 15)][32 * kk + 16 * sub + 8 * (lane >> 4)]);
-        mma_f16(d, a, bh[2 * sub], bh[2 * sub + 1]);
-        mma_f16(d, a, bl[2 * sub], bl[2 * sub + 1]);
+      for (int n = 0; n < NROW; ++n) {
+        const float is = pow2f(-scale_exp(sh.emax[n >> 2]));
+        const float x = sh.X[n][m];
+        part += x * fmaf(__uint_as_float(r[n]) + __uint_as_float(r[n + NROW]), is, kDiag * x);
       }
     }
-    // D[m][n] for m = 16 mt + lane/4 (+8), n = 2 (lane%4) (+1); both n in one helicity
-    const int m = 16 * mt + (lane >> 2), n = 2 * (lane & 3);
-    const float is = pow2f(-scale_exp(sh.emax[n >> 2]));
-    if (m < T::NAMP) {
-      const float x0 = sh.X[n][m], x1 = sh.X[n + 1][m];
-      part += x0 * fmaf(d[0], is, kDiag * x0) + x1 * fmaf(d[1], is, kDiag * x1);
-    }
-    if (m + 8 < T::NAMP) {
-      const float x0 = sh.X[n][m + 8], x1 = sh.X[n + 1][m + 8];
-      part += x0 * fmaf(d[2], is, kDiag * x0) + x1 * fmaf(d[3], is, kDiag * x1);
-    }
   }
+  if (run && !ok && tid == 0) {
+    // the MMAs did not complete in time: wait once more (bounded) for them before the tensor memory
+    // can be released, and stop using the tensor cores in this block
+    mbar_wait_bounded(&tc.mbar, parity);
+    tc.failed = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (tid == 0) tc.uses += 1u;
   if (tid < 2) sh.emax[tid] = 0u;  // next use is behind at least one more barrier
   return part;
 }
@@ -464,14 +519,41 @@ struct ColourSmem;
 template <>
 struct ColourSmem<float> {
   static constexpr size_t bytes = sizeof(TcShared);
+  // the colour operand in the tcgen05 layout, the mbarrier, and the block's tensor memory (warp 0)
   static __device__ TcShared* load(unsigned char* p) {
     TcShared& tc = *reinterpret_cast<TcShared*>(p);
-    for (int i = threadIdx.x; i < MP * KP; i += blockDim.x) {
+    for (int i = threadIdx.x; i < MT * KP; i += blockDim.x) {
       const int m = i / KP, k = i % KP;
       const float v = (m < T::NAMP && k < T::NAMP && m != k) ? colour()[m * T::NAMP + k] : 0.0f;
-      tc.Ch[m][k] = __float2half_rn(v);
+      *reinterpret_cast<__half*>(reinterpret_cast<char*>(tc.C) + tc_off(m, k)) = __float2half_rn(v);
     }
+    if (threadIdx.x < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tc.tmem)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&tc.mbar)), "r"(1) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      tc.uses = 0u;
+      tc.failed = 0;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");  // the kernel's barrier follows
     return &tc;
+  }
+  // release the tensor memory (warp 0); every MMA has completed by now.  Returns whether the
+  // block's tensor-core waits all finished in time.
+  static __device__ bool release(TcShared* tcp) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool ok = !tcp->failed;
+    if (threadIdx.x < 32) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tcp->tmem), "r"(kTmemCols) : "memory");
+    }
+    return ok;
   }
 };
 template <>
@@ -482,6 +564,7 @@ struct ColourSmem<double> {
     for (int i = threadIdx.x; i < T::NAMP * T::NAMP; i += blockDim.x) sC[i] = colour()[i];
     return sC;
   }
+  static __device__ bool release(const float*) { return true; }
 };
 
 template <class R>
@@ -515,6 +598,10 @@ __global__ void __launch_bounds__(Cfg<R>::THREADS, min_blocks<R>())
     const double m2 = event_block<R>(p, (R)gs, sh, cs);
     if (threadIdx.x == 0) out[i] = m2;
     __syncthreads();
+  }
+  if (!ColourSmem<R>::release(cs) && threadIdx.x == 0) {
+    // a tensor-core wait ran out in this block: its results are not to be trusted
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) out[i] = __longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
@@ -571,6 +658,8 @@ __global__ void __launch_bounds__(Cfg<R>::THREADS, min_blocks<R>())
     }
     __syncthreads();
   }
+  // a tensor-core wait that ran out is reported like an exhausted bounded loop (ME_ERR_TIMEOUT)
+  if (!ColourSmem<R>::release(cs) && threadIdx.x == 0) atomicOr(a.status, 1);
   if (threadIdx.x == 0) {
     // this block's sums, and zeros in the slots of blocks the one-wave grid did not launch
     for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
@@ -596,9 +685,30 @@ cudaError_t prepare(K kern, int cap, int& grid) {
   int dev = 0, n_sm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg<R>::THREADS, smem_bytes<R>())) !=
-      cudaSuccess)
+  if constexpr (sizeof(R) == 4) {
+    // the occupancy calculator answers one block per SM for any kernel that allocates tensor memory,
+    // whatever it allocates; blocks of 32 columns do run side by side, so count the limits here:
+    // registers (per-warp allocation in units of 256), shared memory, threads, tensor-memory columns
+    cudaFuncAttributes fa;
+    int regs = 0, smem_sm = 0, reserved = 0, threads_sm = 0;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+      return e;
+    if ((e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess)
+      return e;
+    const int warps = (Cfg<R>::THREADS + 31) / 32;
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = regs / (regs_warp * warps);
+    const int by_smem = smem_sm / (int)(fa.sharedSizeBytes + smem_bytes<R>() + (size_t)reserved);
+    const int by_threads = threads_sm / Cfg<R>::THREADS;
+    const int by_tmem = 512 / (int)kTmemCols;
+    per_sm = std::min(std::min(by_regs, by_smem), std::min(by_threads, by_tmem));
+  } else if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg<R>::THREADS, smem_bytes<R>())) !=
+             cudaSuccess) {
     return e;
+  }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   grid = n_sm * per_sm < cap ? n_sm * per_sm : cap;
   if (grid < 1) grid = 1;
