@@ -66,6 +66,14 @@ Functions and their pins (tests/test_oracle_processes.py):
                    (zero W width: s^2 |M|^2 tends to a constant, a wrong relative
                    sign or coupling of the four diagrams grows like s^2); its W
                    currents by u s > d c h; Higgs-exchange symmetry, boosts
+  us_dchhh        u s > d c h h h (WW fusion) and
+  ud_udh, ud_udhh, ud_udhhh  u d > u d + 1, 2, 3 Higgs (ZZ and WW fusion, Sect. 2.10): the V V > n H
+                   core (vv_higgs) equals _ww_hh at n = 2 and follows the zero-momentum Higgs
+                   theorem from n to n + 1 for W and Z; u d > u d h against its closed form (the
+                   lines, couplings, colour and the exchange sign of the W channel); the W channel
+                   against u s > d c h (h) with the outgoing quarks exchanged; with the complex-mass
+                   card the HHH processes keep the zero-width high-energy behaviour that the
+                   fixed-width card loses; Higgs permutations, boosts (tests/test_oracle_wbf.py)
   udx_epveg       u d~ > e+ ve g : Ward identity; soft-gluon limit against C_F times
                    the eikonal factor times u d~ > e+ ve (closed form); boosts
   gluons          g g > g...g    : Berends-Giele, pinned by the gg > gg closed
@@ -701,7 +709,7 @@ def _ww_hh(W1, q1, W2, q2, pA, pB, par):
     flowing in with momentum q1) and W2 (a W- flowing in with momentum q2), off shell or on shell.
     H wavefunctions are 1; couplings g mW (WWH), g^2/2 (WWHH) and -3 mH^2/v (HHH)."""
     g, mW, wW, mH, wH, v = par.g, par.mW, par.wW, par.mH, par.wH, par.vev
-    gwwh, gwwhh, ghhh = g * mW, g * g / 2.0, -3.0 * mH * mH / v
+    gwwh, gwwhh, ghhh = par.gwwh, g * g / 2.0, -3.0 * mH * mH / v
     w12 = mdot(W1, W2)
     out = [1j * gwwhh * w12, (1j * gwwh * w12) * scalar_prop(q1 + q2, mH, wH) * (1j * ghhh)]
     for ph in (pA, pB):
@@ -738,7 +746,7 @@ def us_dch(P, par=SMParams()):
     W propagator, meet at the WWH vertex (one diagram; no Z fusion for these flavours)."""
     p = [P[:, k] for k in range(5)]
     gw = par.g / np.sqrt(2.0)
-    gwwh = par.g * par.mW
+    gwwh = par.gwwh
     q1 = p[0] - p[2]
     q2 = p[1] - p[3]
     tot = 0.0
@@ -758,7 +766,7 @@ def us_dchg(P, par=SMParams(), eps_override=None):
     (t^a)_{c s}.  eps_override replaces the gluon's polarisation vector."""
     p = [P[:, k] for k in range(6)]
     gw = par.g / np.sqrt(2.0)
-    gwwh = par.g * par.mW
+    gwwh = par.gwwh
     d3 = np.eye(3, dtype=complex)
     c1 = np.einsum("adu,cs->udsca", _T, d3)
     c2 = np.einsum("du,acs->udsca", d3, _T)
@@ -779,6 +787,164 @@ def us_dchg(P, par=SMParams(), eps_override=None):
             amps.append((fermion_line(row, col, pin, [G, W]) + fermion_line(row, col, pin, [W, G])) / 1j)
         tot = tot + colour.colour_sum(amps, [c1, c2])
     return tot / 36.0
+
+
+# --------------------------------------------------------------------------
+# V V > n Higgs bosons (V = W or Z, off shell or on shell), any n: the weak-boson-fusion
+# core of u s > d c h h h and u d > u d h (h (h))
+# --------------------------------------------------------------------------
+def _splits(S, k):
+    """The partitions of the frozenset S into exactly k nonempty unordered blocks."""
+    items = sorted(S)
+    out = []
+
+    def rec(i, blocks):
+        if i == len(items):
+            if len(blocks) == k:
+                out.append([frozenset(b) for b in blocks])
+            return
+        for b in blocks:
+            b.append(items[i])
+            rec(i + 1, blocks)
+            b.pop()
+        if len(blocks) < k:
+            blocks.append([items[i]])
+            rec(i + 1, blocks)
+            blocks.pop()
+
+    rec(0, [])
+    return out
+
+
+def _subsets(S):
+    items = sorted(S)
+    return [frozenset(c) for r in range(1, len(items) + 1) for c in itertools.combinations(items, r)]
+
+
+def wbf_couplings(par, boson):
+    """Couplings and masses of the V V > Higgs core for V = "w" or "z" (the card's scheme: real, or
+    complex with its cms flag): V V H (g mu_W or g_Z mu_Z), V V H H (g^2/2 or g_Z^2/2), H H H
+    (-3 mH^2/v), H H H H (-3 mH^2/v^2)."""
+    v = par.vev
+    c = dict(mH=par.mH, wH=par.wH, ghhh=-3.0 * par.mH ** 2 / v, ghhhh=-3.0 * par.mH ** 2 / v ** 2)
+    if boson == "w":
+        c.update(mV=par.mW, wV=par.wW, gvvh=par.gwwh, gvvhh=par.g ** 2 / 2.0)
+    else:
+        c.update(mV=par.mZ, wV=par.wZ, gvvh=par.gzzh, gvvhh=par.gz ** 2 / 2.0)
+    return c
+
+
+def vv_higgs(V1, q1, V2, q2, pH, cp):
+    """i M of V(q1) V(q2) > H(pH[0]) ... H(pH[n-1]) for vector wavefunctions V1, V2 (upper index) that
+    flow in with momenta q1, q2; the Higgs legs are amputated (wavefunction 1).
+
+    Every tree diagram is a V line from V1 to V2 that gives off its Higgs bosons in an ordered
+    sequence of emissions, each either one Higgs line at a V V H vertex or two at a V V H H vertex,
+    with a V propagator between consecutive emissions.  A Higgs line that ends in the external bosons
+    of a set S is the off-shell current phi(S): 1 for one boson, else the sum over the splits of S
+    into two (H H H vertex) or three (H H H H vertex) parts of the product of their currents, times
+    the Higgs propagator of S's summed momentum.  cp: couplings and masses (wbf_couplings)."""
+    n = len(pH)
+    phi_cache = {}
+
+    def psum(S):
+        return sum(pH[k] for k in sorted(S))
+
+    def phi(S):
+        if len(S) == 1:
+            return 1.0
+        if S not in phi_cache:
+            tot = 0.0
+            for blocks in _splits(S, 2):
+                tot = tot + (1j * cp["ghhh"]) * phi(blocks[0]) * phi(blocks[1])
+            for blocks in _splits(S, 3):
+                tot = tot + (1j * cp["ghhhh"]) * phi(blocks[0]) * phi(blocks[1]) * phi(blocks[2])
+            phi_cache[S] = tot * scalar_prop(psum(S), cp["mH"], cp["wH"])
+        return phi_cache[S]
+
+    def emissions(R):
+        for B in _subsets(R):
+            yield 1j * cp["gvvh"] * phi(B), B
+        for B1 in _subsets(R):
+            for B2 in _subsets(R - B1):
+                if min(B1) < min(B2):  # unordered pair of disjoint blocks
+                    yield 1j * cp["gvvhh"] * phi(B1) * phi(B2), B1 | B2
+
+    def chain(X, q, R):
+        tot = 0.0
+        for f, used in emissions(R):
+            rest = R - used
+            if not rest:
+                tot = tot + f * mdot(X, V2)
+            else:
+                qn = q - psum(used)
+                tot = tot + chain(vector_prop(qn, np.asarray(f)[..., None] * X, cp["mV"], cp["wV"]), qn, rest)
+        return tot
+
+    return chain(V1, q1, frozenset(range(n)))
+
+
+def us_dchhh(P, par=SMParams()):
+    """u(p0) s(p1) > d(p2) c(p3) H(p4) H(p5) H(p6) by W+ W- fusion: the two quark currents, each into its
+    t-channel W propagator, feed the W W > h h h core (vv_higgs, 25 diagrams).  Colour: each line keeps
+    its own (a factor 9 in the colour sum)."""
+    p = [P[:, k] for k in range(P.shape[1])]
+    gw = par.g / np.sqrt(2.0)
+    cp = wbf_couplings(par, "w")
+    q1, q2 = p[0] - p[2], p[1] - p[3]
+    tot = 0.0
+    for h in itertools.product(HEL_F, repeat=4):
+        W1 = vector_prop(q1, ffv_current(bar(u_spinor(p[2], h[2])), u_spinor(p[0], h[0]), gw, 0.0), par.mW, par.wW)
+        W2 = vector_prop(q2, ffv_current(bar(u_spinor(p[3], h[3])), u_spinor(p[1], h[1]), gw, 0.0), par.mW, par.wW)
+        M = vv_higgs(W1, q1, W2, q2, p[4:], cp) / 1j
+        tot = tot + 9.0 * np.abs(M) ** 2
+    return tot / 36.0
+
+
+def ud_udh_n(P, par=SMParams(), bosons=("w", "z")):
+    """u(p0) d(p1) > u(p2) d(p3) + n Higgs bosons (p4...) by weak-boson fusion, the paper's Sect. 2.10
+    processes for n = 2, 3: Z Z fusion, u > u and d > d each giving off a Z (colour delta_{i2 i0}
+    delta_{i3 i1}), and W+ W- fusion, u > d giving off a W+ and d > u a W- (colour delta_{i3 i0}
+    delta_{i2 i1}); exchanging the two outgoing quarks between the lines gives the W diagrams their
+    relative minus sign.  Each pair of currents, through its t-channel propagators, feeds the V V > n H
+    core (vv_higgs).  `bosons` selects the fusion channels (the pins take them one at a time)."""
+    p = [P[:, k] for k in range(P.shape[1])]
+    gw = par.g / np.sqrt(2.0)
+    zu, zd = _z_couplings("u", par), _z_couplings("d", par)
+    cz, cw = wbf_couplings(par, "z"), wbf_couplings(par, "w")
+    d = _DELTA3
+    tens = {"z": np.einsum("ca,db->abcd", d, d), "w": np.einsum("da,cb->abcd", d, d)}
+    tot = 0.0
+    for h in itertools.product(HEL_F, repeat=4):
+        u0, u1 = u_spinor(p[0], h[0]), u_spinor(p[1], h[1])
+        ub2, ub3 = bar(u_spinor(p[2], h[2])), bar(u_spinor(p[3], h[3]))
+        amps, tt = [], []
+        if "z" in bosons:
+            q1, q2 = p[0] - p[2], p[1] - p[3]
+            Z1 = vector_prop(q1, ffv_current(ub2, u0, *zu), par.mZ, par.wZ)
+            Z2 = vector_prop(q2, ffv_current(ub3, u1, *zd), par.mZ, par.wZ)
+            amps.append(vv_higgs(Z1, q1, Z2, q2, p[4:], cz) / 1j)
+            tt.append(tens["z"])
+        if "w" in bosons:
+            q1, q2 = p[0] - p[3], p[1] - p[2]
+            W1 = vector_prop(q1, ffv_current(ub3, u0, gw, 0.0), par.mW, par.wW)
+            W2 = vector_prop(q2, ffv_current(ub2, u1, gw, 0.0), par.mW, par.wW)
+            amps.append(-vv_higgs(W1, q1, W2, q2, p[4:], cw) / 1j)
+            tt.append(tens["w"])
+        tot = tot + colour.colour_sum(amps, tt)
+    return tot / 36.0
+
+
+def ud_udh(P, par=SMParams()):
+    return ud_udh_n(P, par)
+
+
+def ud_udhh(P, par=SMParams()):
+    return ud_udh_n(P, par)
+
+
+def ud_udhhh(P, par=SMParams()):
+    return ud_udh_n(P, par)
 
 
 # --------------------------------------------------------------------------
@@ -892,7 +1058,7 @@ def uux_zhg(P, par=SMParams(), eps_override=None):
     from the quark line before or after it (two diagrams, colour t^a)."""
     p = [P[:, k] for k in range(5)]
     zl, zr = _z_couplings("u", par)
-    gzzh = par.gz * par.mZ
+    gzzh = par.gzzh
     cT = _colour_string([0], 1)
     Q = p[2] + p[3]
     tot = 0.0
@@ -912,7 +1078,7 @@ def udx_wphg(P, par=SMParams(), eps_override=None):
     from the quark line before or after it (two diagrams, colour t^a)."""
     p = [P[:, k] for k in range(5)]
     gw = par.g / np.sqrt(2.0)
-    gwwh = par.g * par.mW
+    gwwh = par.gwwh
     cT = _colour_string([0], 1)
     Q = p[2] + p[3]
     tot = 0.0
@@ -1035,7 +1201,7 @@ def uux_zh(P, par=SMParams()):
     i g_ZZH g^{mu nu}, g_ZZH = gZ mZ (Sect. 4.2 VVS)."""
     p = [P[:, k] for k in range(4)]
     zl, zr = _z_couplings("u", par)
-    gzzh = par.gz * par.mZ
+    gzzh = par.gzzh
     tot = 0.0
     for h in itertools.product(HEL_F, HEL_F, HEL_W):
         u = u_spinor(p[0], h[0])
@@ -1161,7 +1327,7 @@ def udx_wph(P, par=SMParams()):
     i g_WWH g^{mu nu}, g_WWH = g mW (Sect. 4.2 VVS)."""
     p = [P[:, k] for k in range(4)]
     gw = par.g / np.sqrt(2.0)
-    gwwh = par.g * par.mW
+    gwwh = par.gwwh
     tot = 0.0
     for h in itertools.product(HEL_F, HEL_F, HEL_W):
         u = u_spinor(p[0], h[0])
@@ -1483,6 +1649,10 @@ PROCESSES = {
     "u u~ > t t~": uux_ttx,
     "u u~ > t t~ g": uux_ttxg,
     "u s > d c h": us_dch,
+    "u s > d c h h h": us_dchhh,
+    "u d > u d h": ud_udh,
+    "u d > u d h h": ud_udhh,
+    "u d > u d h h h": ud_udhhh,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,
