@@ -59,9 +59,19 @@ typedef enum {
 
 /* Standard Model inputs (GeV).  Electroweak scheme: e = sqrt(4 pi alpha),
  * g = e / s_W, g_Z = e / (s_W c_W), v = 2 mW / g.  Fixed widths in every
- * propagator, including t-channel ones (as the paper's HEGET functions). */
+ * propagator, including t-channel ones (as the paper's HEGET functions).
+ *
+ * complex_mass != 0 selects the complex-mass option of Sect. 7.11: every
+ * vector-boson mass in the couplings becomes mu_V with mu_V^2 = m_V^2 -
+ * i m_V Gamma_V (W W H = g mu_W, Z Z H = g_Z mu_Z, v = 2 mu_W / g in H H H,
+ * H H H H and t t H), and the W is tied to the Z by mu_W^2 = c_W^2 mu_Z^2, so
+ * mW and wW are ignored and c_W mZ, c_W wZ are used everywhere (propagators,
+ * the tt~ generator's W Breit-Wigner).  Propagator denominators are the same in
+ * both schemes.  reserved_ must be 0. */
 typedef struct {
   double alpha, sw2, mZ, wZ, mW, wW, alpha_s, mt, wt, mH, wH;
+  int32_t complex_mass;
+  int32_t reserved_;
 } me_params;
 
 /* Phase-space generators (Sect. 3 and App. A of the paper give its own

@@ -22,7 +22,8 @@ class MeError(RuntimeError):
 
 class me_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
-                ("alpha", "sw2", "mZ", "wZ", "mW", "wW", "alpha_s", "mt", "wt", "mH", "wH")]
+                ("alpha", "sw2", "mZ", "wZ", "mW", "wW", "alpha_s", "mt", "wt", "mH", "wH")] + [
+        ("complex_mass", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class me_kin(ctypes.Structure):
@@ -175,7 +176,7 @@ def _stream(s):
 
 def make_params(**kw):
     p = me_params(alpha=1 / 128, sw2=0.2312, mZ=91.1876, wZ=2.4952, mW=80.4, wW=2.085, alpha_s=0.118, mt=175.0,
-                  wt=1.5, mH=125.0, wH=0.0)
+                  wt=1.5, mH=125.0, wH=0.0, complex_mass=0, reserved_=0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

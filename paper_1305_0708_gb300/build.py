@@ -60,6 +60,10 @@ PROCESSES = [
     ("u d~ > w+ g g", []),
     ("u u~ > z g g", []),
     ("u s > d c h g", []),
+    ("u s > d c h h h", []),
+    ("u d > u d h", []),
+    ("u d > u d h h", []),
+    ("u d > u d h h h", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

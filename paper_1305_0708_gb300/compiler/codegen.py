@@ -21,7 +21,7 @@ kernel instead (colour_gemm.cuh).
 """
 from fractions import Fraction
 
-from .model import PARTICLES, couplings
+from .model import COMPLEX_COUPLINGS, PARTICLES, couplings
 from .program import _ext_chirality, _is_column, _PAIRINGS
 
 _TAG = {frozenset("u"): "me::kUp", frozenset("l"): "me::kLo", frozenset("ul"): "me::kAll"}
@@ -39,13 +39,28 @@ def _hname(h):
     return {-1: "m", 0: "z", 1: "p"}[h]
 
 
+# the variant of every node in the helicity-loop form: helicities known at run time only
+RT = ("rt",)
+
+# straight-line programs above this many FP32 flops per event are emitted in the helicity-loop form
+HEL_LOOP_FLOPS = 100000
+
+
 def _vname(nid, var):
+    if var == RT:
+        return f"w{nid}"
     return f"w{nid}_" + "".join(_hname(h) for h in var) if var else f"w{nid}"
+
+
+def hel_codes(prog):
+    """Live helicity combinations packed 2 bits per leg (h + 1), leg 0 in the lowest bits."""
+    assert prog.n_ext <= 16
+    return [sum((h + 1) << (2 * k) for k, h in enumerate(hs)) for hs in prog.live]
 
 
 def _ident(name):
     """C identifier for a coupling name (e.g. GA_e- -> GA_em)."""
-    return name.replace("-", "m").replace("+", "p").replace("~", "x")
+    return name.replace("-", "m").replace("+", "p").replace("~", "x").replace(".", "_")
 
 
 def _lit(x):
@@ -55,9 +70,10 @@ def _lit(x):
 
 
 class _Emitter:
-    def __init__(self, prog, tag, mode="fp64"):
+    def __init__(self, prog, tag, mode="fp64", hel_loop=False):
         self.p = prog
         self.tag = tag
+        self.hel_loop = hel_loop  # one copy of the program in a loop over the live helicities
         self.mode = mode          # "fp64": FP64 momenta and amplitudes; "mixed": double-float momenta, FP32
         self.lines = []
         self.flops32 = 0      # amplitude-precision flops per event
@@ -71,8 +87,33 @@ class _Emitter:
         self.lines.append(s)
 
     def cpl(self, name):
+        assert name not in COMPLEX_COUPLINGS, name
         self.cpl_names.add(name)
         return f"c_{_ident(name)}"
+
+    def cplx(self, name):
+        """A coupling of COMPLEX_COUPLINGS as a cx<R> expression (parameters name.re, name.im)."""
+        self.cpl_names.add(name + ".re")
+        self.cpl_names.add(name + ".im")
+        return f"me::mk((R)c_{_ident(name)}_re, (R)c_{_ident(name)}_im)"
+
+    def gmul(self, name, expr):
+        """coupling * expr, a complex product for the couplings of COMPLEX_COUPLINGS."""
+        if name in COMPLEX_COUPLINGS:
+            self.flops32 += 4
+            return f"({self.cplx(name)} * ({expr}))"
+        return f"((R){self.cpl(name)} * ({expr}))"
+
+    def ffs_args(self, v, scalar):
+        """Coupling arguments of an FFS vertex and its scalar operand: a complex (gL = gR) coupling is
+        moved onto the scalar (S g (P_L + P_R) = (g S) (P_L + P_R))."""
+        gl, gr = v.couplings
+        if gl in COMPLEX_COUPLINGS or gr in COMPLEX_COUPLINGS:
+            assert gl == gr, "complex FFS couplings need gL = gR"
+            return "(R)1, (R)1, true, true", self.gmul(gl, scalar)
+        has_l, has_r = gl != "ZERO", gr != "ZERO"
+        return (f"(R){self.cpl(gl) if has_l else '0.0'}, (R){self.cpl(gr) if has_r else '0.0'}, "
+                f"{str(has_l).lower()}, {str(has_r).lower()}"), scalar
 
     # ------------------------------------------------------------------
     def generate(self):
@@ -101,12 +142,22 @@ class _Emitter:
             E("  // momenta (no FP64 instructions); massless lines use FP32.")
         else:
             E("  // Massive (resonant) lines form q^2 - m^2 in FP64 from the FP64 momenta.")
+        # lines of different diagrams that carry the same external legs and propagate the same
+        # particle share one momentum and one denominator (the first such line's)
+        line_of = {}
         for nid in used_nodes:
             nd = nodes[nid]
             if nd.external:
                 continue
             kids = nd.children
             part = PARTICLES[nd.ptype]
+            key = (frozenset(nd.legs), part.mass, part.width)
+            if key in line_of:
+                first = line_of[key]
+                E(f"  const me::P4<R> k{nid} = k{first};")
+                E(f"  const {'R' if part.massless else 'me::cx<R>'} inv{nid} = inv{first};")
+                continue
+            line_of[key] = nid
             if not (mixed and not part.massless):
                 E(f"  const me::P4<R> k{nid} = " + " + ".join(f"k{c}" for c in kids) + ";")
                 self.flops32 += 4 * (len(kids) - 1)
@@ -178,6 +229,9 @@ class _Emitter:
 
         K = p.n_colour
         C = p.cmat_num
+        if self.hel_loop:
+            self._hel_loop_body(need)
+            return
         E("  // per helicity: the wavefunctions and sub-currents it needs first, its diagram amplitudes")
         E("  // into colour components, then its colour sum (J^T C J)/den; helicity sum, average")
         E("  R tot = R(0);")
@@ -206,8 +260,59 @@ class _Emitter:
         else:
             E(f"  return (double)tot * {float(p.average / p.cmat_den)!r};")
 
+    def _colour_sum(self, hi):
+        p = self.p
+        E = self.emit
+        C = p.cmat_num
+        E("  {")
+        E("    R s = R(0);")
+        for k in range(p.n_colour):
+            if C[k][k]:
+                E(f"    s += {_lit(C[k][k])} * me::abs2(J{hi}_{k});")
+                self.flops32 += 4
+            for l in range(k + 1, p.n_colour):
+                if C[k][l]:
+                    E(f"    s += {_lit(2 * C[k][l])} * (J{hi}_{k}.re * J{hi}_{l}.re + J{hi}_{k}.im * J{hi}_{l}.im);")
+                    self.flops32 += 5
+        E("    tot += s;")
+        E("  }")
+
+    def _hel_loop_body(self, need):
+        """The helicity-loop form: one copy of every wavefunction, sub-current and amplitude, with the
+        external helicities read from the live-combination table (hel_code) at run time, in a loop
+        over the live combinations.  No helicity recycling and no chirality halves known at compile
+        time, so more flops per helicity, but the program is n_live times shorter (the paper's remedy
+        for amplitude functions too long to compile or to keep in registers, Sect. 5.3)."""
+        p = self.p
+        E = self.emit
+        E("  // helicity loop: the live combinations, 2 bits per leg (h + 1), from hel_code")
+        E("  R tot = R(0);")
+        E("#pragma unroll 1")
+        E(f"  for (int ih = 0; ih < {len(p.live)}; ++ih) {{")
+        E("  const uint32_t hc = hel_code(ih);")
+        for k in range(p.n_ext):
+            E(f"  const int hl{k} = (int)((hc >> {2 * k}) & 3u) - 1;")
+        aids = sorted({aid for terms in p.amp_terms for aid, _ in terms})
+        f0 = self.flops32
+        for aid in aids:
+            for c in p.amps[aid].children:
+                need(c, RT)
+        for k in range(p.n_colour):
+            E(f"  me::cx<R> J_{k} = me::mk(R(0), R(0));")
+        for aid in aids:
+            self.amp_code(aid, [RT] * len(p.amps[aid].children), "")
+        self._colour_sum("")
+        E("  }")
+        self.flops32 = f0 + (self.flops32 - f0) * len(p.live)
+        if self.mode == "mixed":
+            E(f"  return tot * {float(p.average / p.cmat_den)!r}f;")
+        else:
+            E(f"  return (double)tot * {float(p.average / p.cmat_den)!r};")
+
     # ------------------------------------------------------------------
     def child_vars(self, nid, var, child):
+        if var == RT:
+            return RT
         nd = self.p.nodes[nid]
         legs = sorted(nd.legs)
         hmap = dict(zip(legs, var))
@@ -219,7 +324,7 @@ class _Emitter:
         nd = p.nodes[nid]
         leg = p.legs[nd.leg]
         part = PARTICLES[leg.particle]
-        h = var[0]
+        h = f"hl{nd.leg}" if var == RT else var[0]
         name = _vname(nid, var)
         inc = "true" if leg.incoming else "false"
         if part.is_fermion and not part.massless:
@@ -229,13 +334,17 @@ class _Emitter:
             self.half[name] = frozenset("ul")
             self.flops32 += 40
         elif part.is_fermion:
-            chi = _ext_chirality(leg, h)
+            if var == RT:  # the chirality is known at run time only: both halves
+                up, lo = frozenset("ul"), frozenset("ul")
+            else:
+                chi = _ext_chirality(leg, h)
+                up, lo = frozenset("u" if chi == "L" else "l"), frozenset("l" if chi == "L" else "u")
             if _is_column(nd.ptype):
                 self.emit(f"  const me::W4<R> {name} = me::ext_column_massless<R>(r{nid}, {h}, {inc});")
-                self.half[name] = frozenset("u" if chi == "L" else "l")
+                self.half[name] = up
             else:
                 self.emit(f"  const me::W4<R> {name} = me::ext_row_massless<R>(r{nid}, {h}, {inc});")
-                self.half[name] = frozenset("l" if chi == "L" else "u")
+                self.half[name] = lo
             self.flops32 += 12
         elif part.is_vector and part.massless:
             self.emit(f"  const me::PV<R> {name} = me::ext_pol<R>(r{nid}, {h}, {inc});")
@@ -310,11 +419,10 @@ class _Emitter:
         elif v.kind == "FFS":
             gl, gr = v.couplings
             has_l, has_r = gl != "ZERO", gr != "ZERO"
-            cargs = (f"(R){self.cpl(gl) if has_l else '0.0'}, (R){self.cpl(gr) if has_r else '0.0'}, "
-                     f"{str(has_l).lower()}, {str(has_r).lower()}")
             if part.is_fermion:
                 fk = [k for k in kids if k[1] in (0, 1)][0]
                 sk = [k for k in kids if k[1] == 2][0]
+                cargs, sval = self.ffs_args(v, sk[2])
                 m = "R(0)" if part.massless else f"(R){self.cpl(part.mass)}"
                 hin = self.half[fk[2]]
                 # S (gL P_L + gR P_R) keeps the halves: gL acts on the upper, gR on the lower one
@@ -326,17 +434,18 @@ class _Emitter:
                 hx = frozenset(hx)
                 if _is_column(nd.ptype):
                     E(f"  const me::W4<R> {name} = me::prop_col<R, {_tag(hx)}>(me::ffs_col<R, {_tag(hin)}>("
-                      f"{fk[2]}, {sk[2]}, {cargs}), k{nid}, {m}, inv{nid});")
+                      f"{fk[2]}, {sval}, {cargs}), k{nid}, {m}, inv{nid});")
                 else:
                     E(f"  const me::W4<R> {name} = me::prop_row<R, {_tag(hx)}>(me::ffs_row<R, {_tag(hin)}>("
-                      f"{fk[2]}, {sk[2]}, {cargs}), me::neg(k{nid}), {m}, inv{nid});")
+                      f"{fk[2]}, {sval}, {cargs}), me::neg(k{nid}), {m}, inv{nid});")
                 self.half[name] = _flip(hx) if part.massless else frozenset("ul")
                 self.flops32 += (14 + 24 + (32 if not part.massless else 0)) * len(hx) + 2
             else:
                 rk = [k for k in kids if k[1] == 0][0]
                 ck = [k for k in kids if k[1] == 1][0]
                 hr, hc = self.half[rk[2]], self.half[ck[2]]
-                E(f"  const me::cx<R> {name} = me::ffs_scalar<R, {_tag(hr)}, {_tag(hc)}>({rk[2]}, {ck[2]}, "
+                cargs, one = self.ffs_args(v, "R(1)")
+                E(f"  const me::cx<R> {name} = {one} * me::ffs_scalar<R, {_tag(hr)}, {_tag(hc)}>({rk[2]}, {ck[2]}, "
                   f"{cargs}) * inv{nid};")
                 self.flops32 += 34
         elif v.kind == "VVV":
@@ -382,12 +491,11 @@ class _Emitter:
               f"false, me::mk(R(0), R(0)));")
             self.flops32 += 2 * 54 + 16 + 8
         elif v.kind in ("VVS", "VVSS"):
-            g = self.cpl(v.couplings[0])
             vs = [k for k in kids if PARTICLES[v.fields[k[1]]].is_vector]
             ss = [k for k in kids if PARTICLES[v.fields[k[1]]].is_scalar]
             sprod = " * ".join(k[2] for k in ss) if ss else None
             if part.is_vector:
-                s_expr = f"((R){g} * ({sprod}))"
+                s_expr = self.gmul(v.couplings[0], sprod)
                 massive = not part.massless
                 mc2 = f"inv_mc2_{part.mass}" if massive else "me::mk(R(0), R(0))"
                 if massive:
@@ -399,12 +507,11 @@ class _Emitter:
             else:
                 d = f"me::mdot<R>({vs[0][2]}, {vs[1][2]})"
                 extra = f" * {sprod}" if sprod else ""
-                E(f"  const me::cx<R> {name} = ((R){g} * {d}){extra} * inv{nid};")
+                E(f"  const me::cx<R> {name} = {self.gmul(v.couplings[0], d)}{extra} * inv{nid};")
                 self.flops32 += 30 + 12 + 6 * len(ss)
         elif v.kind in ("SSS", "SSSS"):
-            g = self.cpl(v.couplings[0])
             prod = " * ".join(k[2] for k in kids)
-            E(f"  const me::cx<R> {name} = ((R){g} * ({prod})) * inv{nid};")
+            E(f"  const me::cx<R> {name} = {self.gmul(v.couplings[0], prod)} * inv{nid};")
             self.flops32 += 8 + 6 * len(kids)
         else:
             raise NotImplementedError(v.kind)
@@ -442,12 +549,9 @@ class _Emitter:
             nterm = int(has_l and "u" in hc and "l" in hr) + int(has_r and "l" in hc and "u" in hr)
             self.flops32 += (28 if slot[2] in self.pv else 40) * nterm + 16 * nterm
         elif v.kind == "FFS":
-            gl, gr = v.couplings
-            has_l, has_r = gl != "ZERO", gr != "ZERO"
             hr, hc = self.half[slot[0]], self.half[slot[1]]
-            expr = (f"(me::ffs_scalar<R, {_tag(hr)}, {_tag(hc)}>({slot[0]}, {slot[1]}, "
-                    f"(R){self.cpl(gl) if has_l else '0.0'}, (R){self.cpl(gr) if has_r else '0.0'}, "
-                    f"{str(has_l).lower()}, {str(has_r).lower()}) * {slot[2]})")
+            cargs, sval = self.ffs_args(v, slot[2])
+            expr = f"(me::ffs_scalar<R, {_tag(hr)}, {_tag(hc)}>({slot[0]}, {slot[1]}, {cargs}) * {sval})"
             self.flops32 += 34 + 6
         elif v.kind == "VVV":
             g = self.cpl(v.couplings[0])
@@ -469,15 +573,13 @@ class _Emitter:
                     f"me::mdot<R>({slot[x]}, {slot[w]}) * me::mdot<R>({slot[y]}, {slot[z]}))")
             self.flops32 += 4 * 30 + 16
         elif v.kind in ("VVS", "VVSS"):
-            g = self.cpl(v.couplings[0])
             vs = [nm for _, s, nm in kids if PARTICLES[v.fields[s]].is_vector]
             ss = [nm for _, s, nm in kids if PARTICLES[v.fields[s]].is_scalar]
-            expr = f"((R){g} * me::mdot<R>({vs[0]}, {vs[1]}))" + "".join(f" * {s}" for s in ss)
+            expr = self.gmul(v.couplings[0], f"me::mdot<R>({vs[0]}, {vs[1]})") + "".join(f" * {s}" for s in ss)
             self.flops32 += 32 + 6 * len(ss)
         elif v.kind in ("SSS", "SSSS"):
-            g = self.cpl(v.couplings[0])
             prod = " * ".join(slot[s] for s in range(len(v.fields)))
-            expr = f"((R){g} * ({prod}))"
+            expr = self.gmul(v.couplings[0], prod)
             self.flops32 += 2 + 6 * len(v.fields)
         else:
             raise NotImplementedError(v.kind)
@@ -507,12 +609,28 @@ def process_symbol(name):
     return "p_" + "".join(out).strip("_")
 
 
-def generate_source(prog, tag):
-    """CUDA source for one process: the FP64 and mixed evaluators in a traits struct."""
-    em64 = _Emitter(prog, tag, "fp64")
+def generate_source(prog, tag, hel_loop=None):
+    """CUDA source for one process: the FP64 and mixed evaluators in a traits struct.
+
+    hel_loop: True for the helicity-loop form, False for the straight-line form, None to take the
+    loop form when the straight-line mixed program exceeds HEL_LOOP_FLOPS."""
+    if hel_loop is None:
+        probe = _Emitter(prog, tag, "mixed")
+        probe.generate()
+        hel_loop = probe.flops32 > HEL_LOOP_FLOPS
+    em64 = _Emitter(prog, tag, "fp64", hel_loop)
     em64.generate()
-    emmx = _Emitter(prog, tag, "mixed")
+    emmx = _Emitter(prog, tag, "mixed", hel_loop)
     emmx.generate()
+    hel_fn = ""
+    if hel_loop:
+        cases = " ".join(f"case {i}: return {c}u;" for i, c in enumerate(hel_codes(prog)))
+        hel_fn = f"""
+  // live helicity combinations, 2 bits per leg (h + 1)
+  static __host__ __device__ __forceinline__ uint32_t hel_code(int ih) {{
+    switch (ih) {{ {cases} default: return 0u; }}
+  }}
+"""
     cpl = sorted(em64.cpl_names | emmx.cpl_names)
     masses_for_mc2 = sorted({n for n in cpl if n.startswith("M")})
     params = "\n".join(f"    double {_ident(n)};" for n in cpl) or "    double unused;"
@@ -567,7 +685,7 @@ struct Traits {{
 {mx_init}
     return q;
   }}
-
+{hel_fn}
   // FP64 path: FP64 momenta, invariants and amplitudes
   static __host__ __device__ __forceinline__ double eval64(const double (&pm)[{n}][4], const Params& prm) {{
     using R = double;
@@ -590,7 +708,8 @@ struct Traits {{
 
 ME_DEFINE_PROCESS({tag}, {n}, {len(cpl) if cpl else 1})
 """
-    info = {"flops_amp": emmx.flops32, "flops_fp64": em64.flops64 + em64.flops32, "params": cpl}
+    info = {"flops_amp": emmx.flops32, "flops_fp64": em64.flops64 + em64.flops32, "params": cpl,
+            "hel_loop": bool(hel_loop)}
     return src, info
 
 

@@ -144,27 +144,42 @@ VERTICES = _ffv_vertices() + [
 
 
 DEFAULT_PARAMS = dict(alpha=1.0 / 128.0, sw2=0.2312, mZ=91.1876, wZ=2.4952, mW=80.4, wW=2.085,
-                      alpha_s=0.118, mt=175.0, wt=1.50, mH=125.0, wH=0.0)
+                      alpha_s=0.118, mt=175.0, wt=1.50, mH=125.0, wH=0.0, complex_mass=0)
+
+# couplings that carry a vector-boson mass (directly or through v = 2 mW / g): complex under the
+# complex-mass option, so the generated programs take them as complex numbers (name.re, name.im)
+COMPLEX_COUPLINGS = frozenset({"GWWH", "GZZH", "GHHH", "GHHHH", "GHTT"})
 
 
 def couplings(par):
     """Numerical couplings, masses and widths for a parameter dict (electroweak
-    scheme: e = sqrt(4 pi alpha), g = e/sw, gZ = e/(sw cw), v = 2 mW / g)."""
+    scheme: e = sqrt(4 pi alpha), g = e/sw, gZ = e/(sw cw), v = 2 mW / g).
+
+    With par["complex_mass"] (Sect. 7.11): mu_V^2 = m_V^2 - i m_V Gamma_V in the couplings, the W
+    tied to the Z by mu_W^2 = cw^2 mu_Z^2 (so MW = cw mZ, WW = cw wZ), and v = 2 mu_W / g.  The
+    couplings of COMPLEX_COUPLINGS appear as name.re and name.im (imaginary part 0 without the
+    option)."""
     e = math.sqrt(4 * math.pi * par["alpha"])
     sw = math.sqrt(par["sw2"])
     cw = math.sqrt(1 - par["sw2"])
     g = e / sw
     gz = e / (sw * cw)
     gs = math.sqrt(4 * math.pi * par["alpha_s"])
-    v = 2 * par["mW"] / g
+    cms = bool(par.get("complex_mass", 0))
+    mW, wW = (cw * par["mZ"], cw * par["wZ"]) if cms else (par["mW"], par["wW"])
+    muW = complex(mW * mW, -mW * wW) ** 0.5 if cms else complex(mW)
+    muZ = complex(par["mZ"] ** 2, -par["mZ"] * par["wZ"]) ** 0.5 if cms else complex(par["mZ"])
+    v = 2 * muW / g
     c = {"ZERO": 0.0, "GS": gs, "GS2": gs * gs, "GW": g / math.sqrt(2),
-         "GWWH": g * par["mW"], "GZZH": gz * par["mZ"], "GWWHH": g * g / 2, "GZZHH": gz * gz / 2,
+         "GWWHH": g * g / 2, "GZZHH": gz * gz / 2,
          "GWWA": e, "GWWZ": g * cw,
          "GWWWW": -g * g, "GWWAA": g * g * sw * sw, "GWWAZ": g * g * sw * cw, "GWWZZ": g * g * cw * cw,
-         "GHHH": -3 * par["mH"] ** 2 / v, "GHTT": -par["mt"] / v,
-         "GHHHH": -3 * par["mH"] ** 2 / v ** 2,
-         "MT": par["mt"], "WT": par["wt"], "MZ": par["mZ"], "WZ": par["wZ"], "MW": par["mW"], "WW": par["wW"],
+         "MT": par["mt"], "WT": par["wt"], "MZ": par["mZ"], "WZ": par["wZ"], "MW": mW, "WW": wW,
          "MH": par["mH"], "WH": par["wH"], "0": 0.0}
+    cplx = {"GWWH": g * muW, "GZZH": gz * muZ, "GHHH": -3 * par["mH"] ** 2 / v, "GHTT": -par["mt"] / v,
+            "GHHHH": -3 * par["mH"] ** 2 / v ** 2}
+    for n, z in cplx.items():
+        c[n + ".re"], c[n + ".im"] = z.real, z.imag
     for f, q in CHARGE.items():
         c[f"GA_{f}"] = e * q
         c[f"GZL_{f}"] = gz * (QUARK_T3[f] - q * par["sw2"])

@@ -1,6 +1,7 @@
 // C-ABI runtime: handles, parameter resolution, workspace, launches and the
 // deterministic Monte Carlo reduction.  Declarations and contracts: include/me.h.
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -53,42 +54,63 @@ me_params default_params() {
   p.wt = 1.50;
   p.mH = 125.0;
   p.wH = 0.0;
+  p.complex_mass = 0;
+  p.reserved_ = 0;
   return p;
 }
 
-// numerical value of a coupling / mass parameter name used by the generated code
-bool coupling_value(const std::string& n, const me_params& p, double& v) {
+// numerical value of a coupling / mass parameter name used by the generated code.  The couplings
+// that carry a vector-boson mass (W W H, Z Z H, H H H, H H H H, t t H) are complex: the programs
+// take them as name.re and name.im.  With the complex-mass option (Sect. 7.11) mu_V^2 = m_V^2 -
+// i m_V Gamma_V enters those couplings and v = 2 mu_W / g, and the W is tied to the Z by
+// mu_W^2 = c_W^2 mu_Z^2 (MW = c_W mZ, WW = c_W wZ in the propagators too).
+bool coupling_value(const std::string& name, const me_params& p, double& v) {
   const double e = std::sqrt(4 * kPi * p.alpha);
   const double sw = std::sqrt(p.sw2), cw = std::sqrt(1 - p.sw2);
   const double g = e / sw, gz = e / (sw * cw), gs = std::sqrt(4 * kPi * p.alpha_s);
-  const double vev = 2 * p.mW / g;
+  const bool cms = p.complex_mass != 0;
+  const double mW = cms ? cw * p.mZ : p.mW, wW = cms ? cw * p.wZ : p.wW;
+  using C = std::complex<double>;
+  const C muW = cms ? std::sqrt(C(mW * mW, -mW * wW)) : C(mW);
+  const C muZ = cms ? std::sqrt(C(p.mZ * p.mZ, -p.mZ * p.wZ)) : C(p.mZ);
+  const C vev = 2.0 * muW / g;
   struct F { const char* f; double q, t3; };
   static const F ferm[] = {{"u", 2.0 / 3, 0.5}, {"c", 2.0 / 3, 0.5}, {"t", 2.0 / 3, 0.5}, {"d", -1.0 / 3, -0.5},
                            {"s", -1.0 / 3, -0.5}, {"b", -1.0 / 3, -0.5}, {"e-", -1.0, -0.5}, {"mu-", -1.0, -0.5},
                            {"ve", 0.0, 0.5}, {"vm", 0.0, 0.5}};
+  const size_t dot = name.find('.');
+  if (dot != std::string::npos) {
+    const std::string n = name.substr(0, dot), part = name.substr(dot + 1);
+    if (part != "re" && part != "im") return false;
+    C z;
+    if (n == "GWWH") z = g * muW;
+    else if (n == "GZZH") z = gz * muZ;
+    else if (n == "GHHH") z = -3 * p.mH * p.mH / vev;
+    else if (n == "GHHHH") z = -3 * p.mH * p.mH / (vev * vev);
+    else if (n == "GHTT") z = -p.mt / vev;
+    else return false;
+    v = part == "re" ? z.real() : z.imag();
+    return true;
+  }
+  const std::string& n = name;
   if (n == "ZERO" || n == "0") { v = 0; return true; }
   if (n == "GS") { v = gs; return true; }
   if (n == "GS2") { v = gs * gs; return true; }
   if (n == "GW") { v = g / std::sqrt(2.0); return true; }
-  if (n == "GWWH") { v = g * p.mW; return true; }
   if (n == "GWWA") { v = e; return true; }
   if (n == "GWWZ") { v = g * cw; return true; }
   if (n == "GWWWW") { v = -g * g; return true; }
   if (n == "GWWAA") { v = g * g * sw * sw; return true; }
   if (n == "GWWAZ") { v = g * g * sw * cw; return true; }
   if (n == "GWWZZ") { v = g * g * cw * cw; return true; }
-  if (n == "GZZH") { v = gz * p.mZ; return true; }
   if (n == "GWWHH") { v = g * g / 2; return true; }
   if (n == "GZZHH") { v = gz * gz / 2; return true; }
-  if (n == "GHHH") { v = -3 * p.mH * p.mH / vev; return true; }
-  if (n == "GHTT") { v = -p.mt / vev; return true; }
-  if (n == "GHHHH") { v = -3 * p.mH * p.mH / (vev * vev); return true; }
   if (n == "MT") { v = p.mt; return true; }
   if (n == "WT") { v = p.wt; return true; }
   if (n == "MZ") { v = p.mZ; return true; }
   if (n == "WZ") { v = p.wZ; return true; }
-  if (n == "MW") { v = p.mW; return true; }
-  if (n == "WW") { v = p.wW; return true; }
+  if (n == "MW") { v = mW; return true; }
+  if (n == "WW") { v = wW; return true; }
   if (n == "MH") { v = p.mH; return true; }
   if (n == "WH") { v = p.wH; return true; }
   for (const F& f : ferm) {
@@ -281,8 +303,10 @@ me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
   const me_params& p = h->params;
   k.bw_mass[0] = p.mt;
   k.bw_width[0] = p.wt;
-  k.bw_mass[1] = p.mW;
-  k.bw_width[1] = p.wW;
+  // the W of the programs: tied to the Z under the complex-mass option
+  const double cw = std::sqrt(1 - p.sw2);
+  k.bw_mass[1] = p.complex_mass ? cw * p.mZ : p.mW;
+  k.bw_width[1] = p.complex_mass ? cw * p.wZ : p.wW;
   if (kin->kind == ME_PS_RAMBO_BW) {
     k.bw_mass[0] = kin->res_mass;
     k.bw_width[0] = kin->res_width;
@@ -292,7 +316,7 @@ me_status make_kin(me_handle h, const me_kin* kin, me::KinDev& k) {
     k.bw_t0[r] = -std::atan(x);
     k.bw_t1[r] = std::atan(x);
   }
-  if (kin->kind == ME_PS_TTBAR && !(p.wt > 0 && p.wW > 0)) return fail(ME_ERR_ARG, "ttbar generator needs widths");
+  if (kin->kind == ME_PS_TTBAR && !(p.wt > 0 && k.bw_width[1] > 0)) return fail(ME_ERR_ARG, "ttbar generator needs widths");
   k.sqrt_s_f[0] = (float)kin->sqrt_s;
   k.sqrt_s_f[1] = (float)(kin->sqrt_s - (double)k.sqrt_s_f[0]);
   k.shat_fixed = kin->sqrt_s * kin->sqrt_s;
@@ -542,6 +566,8 @@ const char* me_process_name(int32_t i) {
 me_status me_create(const char* process, const me_params* params, int32_t prec, me_handle* out) {
   if (!process || !out) return fail(ME_ERR_ARG, "me_create: null argument");
   if (prec != ME_FP64 && prec != ME_MIXED) return fail(ME_ERR_ARG, "me_create: unknown precision");
+  if (params && (params->reserved_ != 0 || (params->complex_mass != 0 && params->complex_mass != 1)))
+    return fail(ME_ERR_ARG, "me_create: complex_mass must be 0 or 1 and reserved_ 0");
   *out = nullptr;
   const std::string want = normalise(process);
   me::ProcessDesc* d = nullptr;

@@ -179,6 +179,26 @@ VARIANTS = {
         describe="u s > d c H g (W+ W- fusion plus one jet, the gluon from either quark line), massive RAMBO at "
                  "sqrt(s)=1 TeV, the three jets pT>20, |eta|<5, DeltaR>0.4 (the gluon's collinear limits "
                  "with the outgoing quarks cut away), 2^20 accepted points, seed 43"),
+    "us_dchhh": dict(
+        process="u s > d c h h h", kind="rambo", sqrt_s=1500.0, masses=(0, 0, 0, 0, 125.0, 125.0, 125.0),
+        n=1 << 20, seed=44, cuts=None, s_ident=1.0 / 6.0,
+        describe="u s > d c H H H (W+ W- fusion into three Higgs bosons, 25 diagrams), massive RAMBO at "
+                 "sqrt(s)=1.5 TeV, 2^20 points, seed 44"),
+    "ud_udh": dict(
+        process="u d > u d h", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 0, 0, 125.0), n=1 << 20, seed=45,
+        cuts=None, s_ident=1.0,
+        describe="u d > u d H (Z Z and W+ W- fusion, interfering), massive RAMBO at sqrt(s)=1 TeV, 2^20 points, "
+                 "seed 45"),
+    "ud_udhh": dict(
+        process="u d > u d h h", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 0, 0, 125.0, 125.0), n=1 << 20,
+        seed=46, cuts=None, s_ident=0.5,
+        describe="u d > u d H H (Z Z and W+ W- fusion, eight diagrams), massive RAMBO at sqrt(s)=1 TeV, "
+                 "2^20 points, seed 46"),
+    "ud_udhhh": dict(
+        process="u d > u d h h h", kind="rambo", sqrt_s=1500.0, masses=(0, 0, 0, 0, 125.0, 125.0, 125.0),
+        n=1 << 20, seed=47, cuts=None, s_ident=1.0 / 6.0,
+        describe="u d > u d H H H (the paper's Sect. 2.10 process: Z Z and W+ W- fusion, 50 diagrams), "
+                 "massive RAMBO at sqrt(s)=1.5 TeV, 2^20 points, seed 47"),
 }
 
 KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3, "ypt": 4}

@@ -110,9 +110,9 @@ def masses_of(w, n_ext):
     return tuple(w.get("masses", (0.0,) * n_ext))
 
 
-def eval_gpu(B, process, P, prec):
+def eval_gpu(B, process, P, prec, params=None):
     n = P.shape[0]
-    h = B.me_create(process, None, prec)
+    h = B.me_create(process, params, prec)
     out = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
     B.me_eval(h, soa(P), n, out)
     torch.cuda.synchronize()
@@ -390,7 +390,8 @@ def test_identical_quarks_parity(B, prec):
                                  "uux_zg", "ug_wpd", "uux_zzg", "gg_ttxg", "uux_zhg", "udx_wpzg",
                                  "uux_wpwmg", "gg_wpdux", "gg_zuux", "udx_wphg",
                                  "uux_ttx", "uux_ttxg", "us_dch", "udx_wpa",
-                                 "uux_za", "uux_aa", "udx_wpgg", "uux_zgg", "us_dchg"])
+                                 "uux_za", "uux_aa", "udx_wpgg", "uux_zgg", "us_dchg",
+                                 "us_dchhh", "ud_udh", "ud_udhh", "ud_udhhh"])
 def test_massive_final_state_parity(B, key, prec):
     """u u~ > Z Z (identical massive vectors, identical-particle factor 1/2), u u~ > Z H (ZZH vertex,
     external scalar), u d~ > W+ H (WWH vertex), u u~ > W+ W- gamma (the electroweak quartic
@@ -398,7 +399,8 @@ def test_massive_final_state_parity(B, key, prec):
     external spinors), u u~ > t t~ and u u~ > t t~ g (gluon, photon and Z exchange), g g > t t~ H (the FFS Yukawa vertex), u d~ > W+ g, u u~ > Z g, u g > W+ d and
     u u~ > Z Z g, u u~ > Z H g, u d~ > W+ H g, u d~ > W+ Z g, u u~ > W+ W- g (bosons plus one jet, jet cuts), g g > W+ d u~
     and g g > Z u u~ (V plus two jets from two gluons), u s > d c H (W+ W- fusion), u d~ > W+ gamma, u u~ > Z gamma, u u~ > gamma gamma and g g > t t~ g (the
-    four-gluon vertex beside a top line): me_eval on the oracle's massive-RAMBO points and the Monte Carlo sums
+    four-gluon vertex beside a top line), u s > d c H H H and u d > u d + 1, 2, 3 Higgs (weak-boson fusion,
+    Sect. 2.10): me_eval on the oracle's massive-RAMBO points and the Monte Carlo sums
     against the oracle."""
     from paper_1305_0708_gb300.workloads import VARIANTS
     w = VARIANTS[key]
@@ -409,7 +411,8 @@ def test_massive_final_state_parity(B, key, prec):
           "gg_zuux": opr.gg_zuux, "udx_wphg": opr.udx_wphg,
           "uux_ttx": opr.uux_ttx, "uux_ttxg": opr.uux_ttxg, "us_dch": opr.us_dch, "udx_wpa": opr.udx_wpa,
           "uux_za": opr.uux_za, "uux_aa": opr.uux_aa, "udx_wpgg": opr.udx_wpgg, "uux_zgg": opr.uux_zgg,
-          "us_dchg": opr.us_dchg}[key]
+          "us_dchg": opr.us_dchg, "us_dchhh": opr.us_dchhh, "ud_udh": opr.ud_udh, "ud_udhh": opr.ud_udhh,
+          "ud_udhhh": opr.ud_udhhh}[key]
     n = 1500
     P0, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(n))
     P = consistent(P0, masses_of(w, P0.shape[1]))
@@ -430,6 +433,42 @@ def test_massive_final_state_parity(B, key, prec):
     B.me_destroy(h)
     # the Monte Carlo sums: the oracle on its own generated points, as the device generates them
     sw, sw2, nacc, ntry = oxs.accumulate(fn(P0, PAR), W, S, T, w["s_ident"])
+    assert acc.n_acc == nacc == n and acc.n_try == ntry
+    tol = 1e-11 if prec == 0 else 1e-5
+    assert acc.sum_w == pytest.approx(sw, rel=tol) and acc.sum_w2 == pytest.approx(sw2, rel=2 * tol)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("key", ["us_dchh", "us_dchhh", "ud_udhhh", "gg_ttxh", "uux_zh"])
+def test_complex_mass_option_parity(B, key, prec):
+    """The complex-mass option of Sect. 7.11 (me_params.complex_mass = 1: complex V V H, H H H, H H H H
+    and t t H couplings, the W tied to the Z) against the oracle's complex-mass card: me_eval per point
+    and the Monte Carlo sums, at the tolerances of the fixed-width runs."""
+    from paper_1305_0708_gb300.workloads import VARIANTS, WORKLOADS
+    w = {**WORKLOADS, **VARIANTS}[key]
+    fn = {"us_dchh": opr.us_dchh, "us_dchhh": opr.us_dchhh, "ud_udhhh": opr.ud_udhhh, "gg_ttxh": opr.gg_ttxh,
+          "uux_zh": opr.uux_zh}[key]
+    cms = PAR.with_cms()
+    prm = B.make_params(complex_mass=1)
+    n = 1200
+    P0, W, S, T = oxs.generate(oracle_kin(w), cms, w["seed"], np.arange(n))
+    P = consistent(P0, masses_of(w, P0.shape[1]))
+    ref = fn(P, cms)
+    got = eval_gpu(B, w["process"], P, prec, prm)
+    if prec == 0:
+        tol = 1e-12 * np.abs(ref) + 32 * conditioning(fn, P, ref, cms)
+        report(w["process"] + " (complex mass)", 0, got, ref, (tol - 1e-12 * np.abs(ref)) / 32)
+        assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
+        assert np.median(np.abs(got / ref - 1)) <= 1e-12
+    else:
+        report(w["process"] + " (complex mass)", 1, got, ref)
+        rel = np.abs(got / ref - 1)
+        assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
+    kin = B.make_kin(**kin_args(w))
+    h = B.me_create(w["process"], prm, prec)
+    acc = B.xsec_step(h, w["seed"], 0, n, kin)
+    B.me_destroy(h)
+    sw, sw2, nacc, ntry = oxs.accumulate(fn(P0, cms), W, S, T, w["s_ident"])
     assert acc.n_acc == nacc == n and acc.n_try == ntry
     tol = 1e-11 if prec == 0 else 1e-5
     assert acc.sum_w == pytest.approx(sw, rel=tol) and acc.sum_w2 == pytest.approx(sw2, rel=2 * tol)

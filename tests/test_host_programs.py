@@ -63,7 +63,14 @@ CASES = {
     "u d~ > w+ g g": (opr.udx_wpgg, 600.0, (80.4, 0.0, 0.0), (3, 4)),
     "u u~ > z g g": (opr.uux_zgg, 600.0, (91.1876, 0.0, 0.0), (3, 4)),
     "u s > d c h g": (opr.us_dchg, 1000.0, (0.0, 0.0, 125.0, 0.0), (5,)),
+    "u s > d c h h h": (opr.us_dchhh, 1500.0, (0.0, 0.0, 125.0, 125.0, 125.0), ()),
+    "u d > u d h": (opr.ud_udh, 1000.0, (0.0, 0.0, 125.0), ()),
+    "u d > u d h h": (opr.ud_udhh, 1000.0, (0.0, 0.0, 125.0, 125.0), ()),
+    "u d > u d h h h": (opr.ud_udhhh, 1500.0, (0.0, 0.0, 125.0, 125.0, 125.0), ()),
 }
+
+# the complex-mass option (Sect. 7.11): processes whose couplings it makes complex
+CMS_CASES = ["u s > d c h h", "u s > d c h h h", "u d > u d h h h", "g g > t t~ h", "u u~ > z h"]
 
 
 def _nvcc():
@@ -90,19 +97,16 @@ def _tolerance(fn, P, ref):
     return 1e-12 * np.abs(ref) + 32 * conditioning(fn, P, ref, PAR, draws=3)
 
 
-def _build(name, workdir):
+def _build(name, workdir, hel_loop=None):
     from paper_1305_0708_gb300.compiler.codegen import generate_source, process_symbol
-    from paper_1305_0708_gb300.compiler.model import DEFAULT_PARAMS, couplings
     from paper_1305_0708_gb300.compiler.program import compile_process
-    tag = process_symbol(name)
-    src, _ = generate_source(compile_process(name), tag)
+    tag = process_symbol(name) + ("_loop" if hel_loop else "")
+    src, _ = generate_source(compile_process(name), tag, hel_loop=hel_loop)
     cut = src.rindex("ME_DEFINE_PROCESS(")           # kernels and registration stay out of the host build
     unit = os.path.join(workdir, tag + ".cuh")
     with open(unit, "w") as f:
         f.write(src[:cut] + src[src.index("\n", cut):])
     fields = re.findall(r"double (\w+);", src[src.index("struct Params {"):src.index("struct ParamsMx")])
-    c = couplings(DEFAULT_PARAMS)
-    params = [c[x] for x in fields]
     exe = os.path.join(workdir, tag)
     n_ext = int(re.search(r"static constexpr int NEXT = (\d+);", src).group(1))
     cmd = [_nvcc(), "-O1", "-std=c++17", "--expt-relaxed-constexpr", "-gencode", "arch=compute_103a,code=sm_103a",
@@ -110,7 +114,15 @@ def _build(name, workdir):
            f"-DNEXT_H={n_ext}", os.path.join(HERE, "host", "host_eval.cu"), "-o", exe]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-4000:]
-    return exe, params
+    return exe, fields
+
+
+def _params(fields, complex_mass=0):
+    """The parameter block of a unit: its fields (C identifiers of the coupling names) in order."""
+    from paper_1305_0708_gb300.compiler.codegen import _ident
+    from paper_1305_0708_gb300.compiler.model import DEFAULT_PARAMS, couplings
+    c = {_ident(k): v for k, v in couplings(dict(DEFAULT_PARAMS, complex_mass=complex_mass)).items()}
+    return [c[x] for x in fields]
 
 
 @pytest.fixture(scope="module")
@@ -141,14 +153,67 @@ def test_host_program_matches_oracle(programs, name):
     fn, rs, masses, cut_legs = CASES[name]
     P = consistent(_points(rs, masses, cut_legs, 300, seed=7), (0.0, 0.0) + tuple(masses))
     assert P.shape[0] > 200
-    exe, params = built[name]
-    got = _run(exe, params, P, d)
+    exe, fields = built[name]
+    got = _run(exe, _params(fields), P, d)
     ref = fn(P, PAR)
     assert np.all(np.abs(got[:, 0] - ref) <= _tolerance(fn, P, ref)), np.max(np.abs(got[:, 0] - ref) / _tolerance(fn, P, ref))
     assert np.median(np.abs(got[:, 0] / ref - 1)) <= 1e-12
     rel = np.abs(got[:, 1] / ref - 1)
     assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3, (np.median(rel), rel.max())
     assert math.isfinite(float(got.sum()))
+
+
+# processes checked in the helicity-loop form as well (massive fermions and vectors, massless
+# polarisation vectors, the four-gluon and electroweak quartic vertices, complex couplings)
+LOOP_CASES = ["g g > t t~ g", "u u~ > w+ w- a", "u d~ > w+ g g", "u s > d c h h", "g g > t t~ h", "u u > u u"]
+
+
+@pytest.fixture(scope="module")
+def loop_programs():
+    from paper_1305_0708_gb300.compiler import dftables
+    with tempfile.TemporaryDirectory() as d:
+        with open(os.path.join(d, "dfloat_tables.h"), "w") as f:
+            f.write(dftables.header())
+        with ThreadPoolExecutor(max_workers=min(6, os.cpu_count() or 1)) as ex:
+            built = dict(zip(LOOP_CASES, ex.map(lambda n: _build(n, d, hel_loop=True), LOOP_CASES)))
+        yield d, built
+
+
+@pytest.mark.parametrize("name", LOOP_CASES)
+def test_helicity_loop_form_matches_oracle(loop_programs, name):
+    """The helicity-loop form of the generated program (one copy of the diagrams, helicities from
+    the live table at run time) at the tolerances of the straight-line form."""
+    d, built = loop_programs
+    fn, rs, masses, cut_legs = CASES[name]
+    P = consistent(_points(rs, masses, cut_legs, 200, seed=9), (0.0, 0.0) + tuple(masses))
+    exe, fields = built[name]
+    got = _run(exe, _params(fields), P, d)
+    ref = fn(P, PAR)
+    assert np.all(np.abs(got[:, 0] - ref) <= _tolerance(fn, P, ref)), np.max(np.abs(got[:, 0] - ref) / _tolerance(fn, P, ref))
+    assert np.median(np.abs(got[:, 0] / ref - 1)) <= 1e-12
+    rel = np.abs(got[:, 1] / ref - 1)
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3, (np.median(rel), rel.max())
+
+
+@pytest.mark.parametrize("name", CMS_CASES)
+def test_host_program_complex_mass_option(programs, name):
+    """The same programs with the complex-mass parameter block (complex V V H, H H H, H H H H and
+    t t H couplings, the W tied to the Z) against the oracle's complex-mass card; the same
+    tolerances."""
+    d, built = programs
+    fn, rs, masses, cut_legs = CASES[name]
+    cms = PAR.with_cms()
+    P = consistent(_points(rs, masses, cut_legs, 200, seed=8), (0.0, 0.0) + tuple(masses))
+    exe, fields = built[name]
+    got = _run(exe, _params(fields, complex_mass=1), P, d)
+    ref = fn(P, cms)
+    tol = 1e-12 * np.abs(ref) + 32 * conditioning(fn, P, ref, cms, draws=3)
+    assert np.all(np.abs(got[:, 0] - ref) <= tol), np.max(np.abs(got[:, 0] - ref) / tol)
+    assert np.median(np.abs(got[:, 0] / ref - 1)) <= 1e-12
+    rel = np.abs(got[:, 1] / ref - 1)
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3, (np.median(rel), rel.max())
+    # the option changes the result (not a no-op)
+    assert np.median(np.abs(ref / fn(P, PAR) - 1)) > 1e-4
 
 
 # points of the full-size workloads (seed, event) where FP32 amplitudes lost most: near-collinear
@@ -178,8 +243,8 @@ def test_mixed_path_at_the_hardest_full_size_points(key):
         from paper_1305_0708_gb300.compiler import dftables
         with open(os.path.join(d, "dfloat_tables.h"), "w") as f:
             f.write(dftables.header())
-        exe, params = _build(w["process"], d)
-        got = _run(exe, params, P, d)
+        exe, fields = _build(w["process"], d)
+        got = _run(exe, _params(fields), P, d)
     assert np.all(np.abs(got[:, 0] - ref) <= _tolerance(fn, P, ref))
     rel = np.abs(got[:, 1] / ref - 1)
     assert rel.max() <= 1e-3, rel
