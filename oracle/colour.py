@@ -8,7 +8,8 @@ summation to its QCD companion paper, Sect. 2; this is the plain definition.)
 
 Parity: pinned by tests/test_oracle_colour.py (Lie algebra, normalisation,
 Casimirs, known 2x2 colour matrix of q qbar g g, symmetry/PSD of the
-six-gluon trace matrix, U(1) decoupling).
+six-gluon trace matrix, U(1) decoupling); colour_projector against colour_sum
+in tests/test_oracle_vjets.py.
 """
 import itertools
 import numpy as np
@@ -41,6 +42,25 @@ def colour_sum(amps, tensors):
     A = np.stack(amps, axis=0)                   # [D, N]
     M = C.T @ A                                   # [n_colours, N]
     return np.sum(np.abs(M) ** 2, axis=0)
+
+
+def colour_projector(tensors):
+    """B (r x D) with sum over all colour indices c of |sum_d c_d[c] A_d|^2 = |B A|^2 for explicit
+    diagram colour tensors c_d: the rows of the SVD C = U S Vh of the D x n_c matrix of tensors span
+    the colour space the diagrams reach and C^T A = Vh^T S U^T A, so |C^T A| = |S U^T A| and
+    B = S U^T (singular values above 1e-12 of the largest).  Taken once per process; per point and
+    helicity the diagrams still combine linearly before the square, as in colour_sum.  (Vh^T has
+    orthonormal columns, so |Vh^T y| = |y|.)"""
+    C = np.array([t.ravel() for t in tensors])
+    U, S, _ = np.linalg.svd(C, full_matrices=False)   # C = U S Vh: C^T A = Vh^T (S U^T A)
+    keep = S > 1e-12 * S[0]
+    return S[keep, None] * U[:, keep].T
+
+
+def colour_norm(amps, B):
+    """|B A|^2 summed over the colour components, for amps [D] of arrays [N]."""
+    A = np.stack(amps, axis=0)
+    return np.sum(np.abs(B @ A) ** 2, axis=0)
 
 
 def trace_product(labels_matrices):

@@ -56,6 +56,10 @@ Functions and their pins (tests/test_oracle_processes.py):
   us_dchg         u s > d c h g  (WW fusion plus one jet): Ward identity, the soft-gluon limit
                    against 2 C_F (S_ud + S_sc) times u s > d c h (the lines' colours do not
                    interfere), boosts
+  udx_wpggg, uux_zggg  u d~ > w+ g g g, u u~ > z g g g (V plus three jets, 54 diagrams): the generic
+                   q q~ > V + n gluons code (qqx_v_ng) equals q q~ > V g and q q~ > V g g at n = 1, 2;
+                   at n = 3 the Ward identity of each gluon (fails without the four-gluon diagrams),
+                   Bose symmetry, boosts (tests/test_oracle_vjets.py)
   udx_wpgg, uux_zgg  u d~ > w+ g g, u u~ > z g g (V plus two jets): Ward identity for each gluon,
                    Bose symmetry, the soft limit of either gluon against the colour-correlated
                    eikonal factor of q, q~, g times q q~ > V g (closed form), boosts
@@ -1279,6 +1283,153 @@ def uux_zgg(P, par=SMParams(), eps_override=None):
     return _qqx_vgg(P, par, gl, gr, par.mZ, eps_override)
 
 
+# --------------------------------------------------------------------------
+# q q~' > V + n gluons, n = 1, 2, 3 (V plus jets, Sect. 2.1): every Feynman diagram
+# --------------------------------------------------------------------------
+def _gluon_blocks(legs):
+    """The ways a set of gluons joins into one gluon line that meets the quark line: as a list of
+    (kind, spec).  One gluon: ("g", x); two: ("pair", (x, y)) through a three-gluon vertex; three:
+    ("triple", (x, y, z)) through two three-gluon vertices ((x y) first) for each of the three pairs,
+    and ("quartic", s) through the four-gluon vertex for its three colour structures s = 0, 1, 2."""
+    legs = tuple(sorted(legs))
+    if len(legs) == 1:
+        return [("g", legs[0])]
+    if len(legs) == 2:
+        return [("pair", legs)]
+    x, y, z = legs
+    return ([("triple", (a, b, c)) for a, b, c in ((x, y, z), (x, z, y), (y, z, x))]
+            + [("quartic", (legs, s)) for s in range(3)])
+
+
+def _block_colour(kind, spec, A):
+    """Colour matrix (3 x 3) a joined gluon line gives the quark line, for gluon colours A[leg]."""
+    T, F = _T, _F
+    if kind == "g":
+        return T[A[spec]]
+    if kind == "pair":
+        x, y = spec
+        return np.einsum("c,cij->ij", F[A[x], A[y], :], T)
+    if kind == "triple":
+        x, y, z = spec
+        return np.einsum("e,ec,cij->ij", F[A[x], A[y], :], F[:, A[z], :], T)
+    (x, y, z), s = spec   # four-gluon vertex, legs (x, y, z, X): f^{xye} f^{zXe}, f^{xze} f^{yXe}, f^{xXe} f^{yze}
+    if s == 0:
+        return np.einsum("e,ce,cij->ij", F[A[x], A[y], :], F[A[z], :, :], T)
+    if s == 1:
+        return np.einsum("e,ce,cij->ij", F[A[x], A[z], :], F[A[y], :, :], T)
+    return np.einsum("ce,e,cij->ij", F[A[x], :, :], F[A[y], A[z], :], T)
+
+
+def _set_partitions(items):
+    if not items:
+        yield []
+        return
+    first, rest = items[0], items[1:]
+    for part in _set_partitions(rest):
+        for k in range(len(part)):
+            yield part[:k] + [[first] + part[k]] + part[k + 1:]
+        yield [[first]] + part
+
+
+def _vjets_diagrams(n):
+    """Every diagram of q q~' > V + n gluons as a sequence of insertions along the quark line, from
+    the quark's column spinor to the antiquark's row spinor: "V" or a joined gluon line (kind, spec);
+    and its explicit colour tensor [i_start, i_end, a_0 .. a_{n-1}]."""
+    diags = []
+    for part in _set_partitions(list(range(n))):
+        for choice in itertools.product(*[_gluon_blocks(b) for b in part]):
+            for order in itertools.permutations(["V"] + list(choice)):
+                diags.append(order)
+    tensors = []
+    for order in diags:
+        t = np.zeros((3, 3) + (8,) * n, dtype=complex)
+        for a in itertools.product(range(8), repeat=n):
+            M = np.eye(3, dtype=complex)
+            for ins in order:
+                if ins != "V":
+                    M = _block_colour(ins[0], ins[1], a) @ M
+            t[(slice(None), slice(None)) + a] = M.T
+        tensors.append(t)
+    return diags, colour.colour_projector(tensors)
+
+
+_VJETS = {}
+
+
+def qqx_v_ng(P, par, gl, gr, mV, eps_override=None):
+    """q(p0) q~'(p1) > V(p2) g(p3) ... g(p_{2+n}), n = 1, 2, 3, with an on-shell V of mass mV coupling
+    i gamma^mu (gl P_L + gr P_R) to the quark line: every diagram is an ordering along the quark line of
+    the V and of the gluons joined into lines (_gluon_blocks: single gluons, pairs through the
+    three-gluon vertex, triples through two three-gluon vertices or the four-gluon vertex); colour
+    summed over explicit indices (colour_projector of the diagrams' colour tensors).
+    eps_override: {leg: vector[N,4]} replaces a gluon's polarisation (Ward identity)."""
+    n = P.shape[1] - 3
+    if n not in _VJETS:
+        _VJETS[n] = _vjets_diagrams(n)
+    diags, G = _VJETS[n]
+    p = [P[:, k] for k in range(P.shape[1])]
+    gs = par.gs
+    kg = {j: -p[3 + j] for j in range(n)}   # gluon momenta into the gluon vertices
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_W, *([HEL_V] * n)):
+        u = u_spinor(p[0], h[0])
+        vb = bar(v_spinor(p[1], h[1]))
+        ev = polarisation(p[2], h[2], mass=mV).conj()
+        eps = {j: polarisation(p[3 + j], h[3 + j]).conj() for j in range(n)}
+        if eps_override:
+            for leg, vec in eps_override.items():
+                eps[leg - 3] = vec.astype(complex)
+        cache = {}
+
+        def line(kind, spec):
+            """(current [N,4] into the quark line, momentum leaving the quark line)."""
+            key = (kind, spec)
+            if key in cache:
+                return cache[key]
+            if kind == "g":
+                out = (eps[spec], p[3 + spec])
+            elif kind == "pair":
+                x, y = spec
+                k = kg[x] + kg[y]
+                out = (vector_prop(k, vvv_out(eps[x], kg[x], eps[y], kg[y], -k, gs)), -k)
+            elif kind == "triple":
+                x, y, z = spec
+                J, mk = line("pair", (x, y))
+                k = -mk
+                K = k + kg[z]
+                out = (vector_prop(K, vvv_out(J, k, eps[z], kg[z], -K, gs)), -K)
+            else:
+                (x, y, z), s = spec
+                K = kg[x] + kg[y] + kg[z]
+                out = (vector_prop(K, -1j * gs * gs * _vvvv_out(eps[x], eps[y], eps[z])[s]), -K)
+            cache[key] = out
+            return out
+
+        amps = []
+        for order in diags:
+            ins = []
+            for x in order:
+                if x == "V":
+                    ins.append((vector_insertion(ev, gl, gr), p[2]))
+                else:
+                    J, Q = line(*x)
+                    ins.append((vector_insertion(J, gs, gs), Q))
+            amps.append(fermion_line(vb, u, p[0], ins) / 1j)
+        tot = tot + colour.colour_norm(amps, G)
+    return tot / 36.0
+
+
+def udx_wpggg(P, par=SMParams(), eps_override=None):
+    """u d~ > W+ g g g (on-shell W plus three jets, 54 diagrams)."""
+    return qqx_v_ng(P, par, par.g / np.sqrt(2.0), 0.0, par.mW, eps_override)
+
+
+def uux_zggg(P, par=SMParams(), eps_override=None):
+    """u u~ > Z g g g (on-shell Z plus three jets, 54 diagrams)."""
+    gl, gr = _z_couplings("u", par)
+    return qqx_v_ng(P, par, gl, gr, par.mZ, eps_override)
+
+
 def _uux_va(P, par, gl, gr, mV):
     """u(p0) u~(p1) > V(p2) gamma(p3): both orders of the V (coupling gl, gr; mass mV, 0 for a photon)
     and the photon along the quark line, colour delta."""
@@ -1653,6 +1804,8 @@ PROCESSES = {
     "u d > u d h": ud_udh,
     "u d > u d h h": ud_udhh,
     "u d > u d h h h": ud_udhhh,
+    "u d~ > w+ g g g": udx_wpggg,
+    "u u~ > z g g g": uux_zggg,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,
