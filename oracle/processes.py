@@ -56,6 +56,10 @@ Functions and their pins (tests/test_oracle_processes.py):
   us_dchg         u s > d c h g  (WW fusion plus one jet): Ward identity, the soft-gluon limit
                    against 2 C_F (S_ud + S_sc) times u s > d c h (the lines' colours do not
                    interfere), boosts
+  gg_ttxhg        g g > t t~ h g (H t t~ plus one jet, 54 diagrams) on the one-fermion-line engine
+                   (fermion_line_process), which equals gg_ttxh, gg_ttxg and udx_wpggg point by point;
+                   Ward identity for each gluon (fails without the triple-gluon lines), Bose symmetry,
+                   boosts (tests/test_oracle_line.py)
   udx_wpggg, uux_zggg  u d~ > w+ g g g, u u~ > z g g g (V plus three jets, 54 diagrams): the generic
                    q q~ > V + n gluons code (qqx_v_ng) equals q q~ > V g and q q~ > V g g at n = 1, 2;
                    at n = 3 the Ward identity of each gluon (fails without the four-gluon diagrams),
@@ -1419,6 +1423,108 @@ def qqx_v_ng(P, par, gl, gr, mV, eps_override=None):
     return tot / 36.0
 
 
+def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, average=1.0 / 36.0,
+                         eps_override=None):
+    """|M|^2 of a process with one fermion line, colourless bosons attached to it and any number (up
+    to three) of incoming or outgoing gluons, from every Feynman diagram: the orderings along the line
+    of the colourless insertions and of the gluons joined into lines (_gluon_blocks), colour summed
+    over explicit indices (colour_projector), averaged by `average`.
+
+    col: (leg, "u") an incoming quark or (leg, "v") an outgoing antiquark, where the fermion-number
+    arrow starts; row: (leg, "ubar") an outgoing quark or (leg, "vbar") an incoming antiquark, where it
+    ends.  colourless: outgoing bosons as dicts (leg, kind "V" with gl, gr, mass: i gamma^mu (gl P_L +
+    gr P_R); kind "S" with y: i y).  gluons: (leg, incoming) pairs.  Internal fermions carry mass mf
+    and width wf.  eps_override: {leg: vector[N,4]} replaces a gluon's polarisation."""
+    ng = len(gluons)
+    key = ("line", ng, len(colourless))
+    if key not in _VJETS:
+        diags = []
+        for part in _set_partitions(list(range(ng))):
+            for choice in itertools.product(*[_gluon_blocks(b) for b in part]):
+                for order in itertools.permutations([("c", i) for i in range(len(colourless))] + list(choice)):
+                    diags.append(order)
+        tensors = []
+        for order in diags:
+            t = np.zeros((3, 3) + (8,) * ng, dtype=complex)
+            for a in itertools.product(range(8), repeat=ng):
+                M = np.eye(3, dtype=complex)
+                for ins in order:
+                    if ins[0] != "c":
+                        M = _block_colour(ins[0], ins[1], a) @ M
+                t[(slice(None), slice(None)) + a] = M.T
+            tensors.append(t)
+        _VJETS[key] = (diags, colour.colour_projector(tensors))
+    diags, B = _VJETS[key]
+    p = [P[:, k] for k in range(P.shape[1])]
+    gs = par.gs
+    kg = {j: (p[l] if inc else -p[l]) for j, (l, inc) in enumerate(gluons)}
+    p_start = p[col[0]] if col[1] == "u" else -p[col[0]]
+    hels = [HEL_F, HEL_F] + [HEL_W if c["kind"] == "V" else (0,) for c in colourless] + [HEL_V] * ng
+    tot = 0.0
+    for h in itertools.product(*hels):
+        cs = u_spinor(p[col[0]], h[0]) if col[1] == "u" else v_spinor(p[col[0]], h[0])
+        rs = bar(u_spinor(p[row[0]], h[1]) if row[1] == "ubar" else v_spinor(p[row[0]], h[1]))
+        cins = []
+        for c, hc in zip(colourless, h[2:2 + len(colourless)]):
+            pc = p[c["leg"]]
+            if c["kind"] == "V":
+                cins.append((vector_insertion(polarisation(pc, hc, mass=c["mass"]).conj(), c["gl"], c["gr"]), pc))
+            else:
+                cins.append((np.broadcast_to(1j * c["y"] * np.eye(4, dtype=complex), (P.shape[0], 4, 4)), pc))
+        eps = {}
+        for j, ((l, inc), hg) in enumerate(zip(gluons, h[2 + len(colourless):])):
+            e = polarisation(p[l], hg)
+            eps[j] = e if inc else e.conj()
+            if eps_override and l in eps_override:
+                eps[j] = eps_override[l].astype(complex)
+        cache = {}
+
+        def line(kind, spec):
+            """(gluon line [N,4] into the fermion line, momentum leaving the fermion line)."""
+            k_ = (kind, spec)
+            if k_ in cache:
+                return cache[k_]
+            if kind == "g":
+                out = (eps[spec], -kg[spec])
+            elif kind == "pair":
+                x, y = spec
+                k = kg[x] + kg[y]
+                out = (vector_prop(k, vvv_out(eps[x], kg[x], eps[y], kg[y], -k, gs)), -k)
+            elif kind == "triple":
+                x, y, z = spec
+                J, mk = line("pair", (x, y))
+                k = -mk
+                K = k + kg[z]
+                out = (vector_prop(K, vvv_out(J, k, eps[z], kg[z], -K, gs)), -K)
+            else:
+                (x, y, z), s_ = spec
+                K = kg[x] + kg[y] + kg[z]
+                out = (vector_prop(K, -1j * gs * gs * _vvvv_out(eps[x], eps[y], eps[z])[s_]), -K)
+            cache[k_] = out
+            return out
+
+        amps = []
+        for order in diags:
+            ins = []
+            for x in order:
+                if x[0] == "c":
+                    ins.append(cins[x[1]])
+                else:
+                    J, Q = line(*x)
+                    ins.append((vector_insertion(J, gs, gs), Q))
+            amps.append(fermion_line(rs, cs, p_start, ins, mf, wf) / 1j)
+        tot = tot + colour.colour_norm(amps, B)
+    return tot * average
+
+
+def gg_ttxhg(P, par=SMParams(), eps_override=None, widths=True):
+    """g(0) g(1) > t(2) t~(3) H(4) g(5) (H t t~ plus one jet): the top line from v(p3) to ubar(p2) with the
+    Higgs (Yukawa -mt/v) and the three gluons, 54 diagrams (fermion_line_process)."""
+    return fermion_line_process(P, par, (3, "v"), (2, "ubar"), [dict(leg=4, kind="S", y=-par.mt / par.vev)],
+                                [(0, True), (1, True), (5, False)], par.mt, par.wt if widths else 0.0,
+                                1.0 / 256.0, eps_override)
+
+
 def udx_wpggg(P, par=SMParams(), eps_override=None):
     """u d~ > W+ g g g (on-shell W plus three jets, 54 diagrams)."""
     return qqx_v_ng(P, par, par.g / np.sqrt(2.0), 0.0, par.mW, eps_override)
@@ -1806,6 +1912,7 @@ PROCESSES = {
     "u d > u d h h h": ud_udhhh,
     "u d~ > w+ g g g": udx_wpggg,
     "u u~ > z g g g": uux_zggg,
+    "g g > t t~ h g": gg_ttxhg,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,

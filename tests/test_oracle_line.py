@@ -1,0 +1,62 @@
+"""Pins of the oracle's one-fermion-line engine (fermion_line_process: a quark line with colourless
+bosons and up to three incoming or outgoing gluons, every Feynman diagram) and of the process built on
+it, g g > t t~ H g (H t t~ plus one jet, the paper's Sect. 2 Htt~ + jets family).
+
+- The engine equals three independently written oracles point by point: g g > t t~ H (eight
+  diagrams written out), g g > t t~ g (eighteen diagram terms written out, the four-gluon vertex
+  among them) and u d~ > W+ g g g (q q~ > V + n gluons): crossing (incoming and outgoing gluons, a
+  quark or antiquark at either end of the line), massive internal fermions with widths, scalar and
+  vector insertions.
+- g g > t t~ H g: the Ward identity of each gluon at zero top width (fixed-width top propagators break
+  it at O(m Gamma / (p^2 - m^2))), Bose symmetry of the incoming gluons, boosts.
+"""
+import numpy as np
+import pytest
+
+from oracle import processes as pr
+from oracle.sm import SMParams
+from test_oracle_chains import _massive_points
+
+PAR = SMParams()
+
+
+def test_engine_equals_the_written_out_oracles():
+    mt = PAR.mt
+    P = _massive_points(1000.0, (mt, mt, PAR.mH), 6, seed=800)
+    got = pr.fermion_line_process(P, PAR, (3, "v"), (2, "ubar"), [dict(leg=4, kind="S", y=-mt / PAR.vev)],
+                                  [(0, True), (1, True)], mt, PAR.wt, 1.0 / 256.0)
+    assert np.allclose(got, pr.gg_ttxh(P, PAR), rtol=1e-12, atol=0)
+    P = _massive_points(1000.0, (mt, mt, 0.0), 6, seed=801)
+    got = pr.fermion_line_process(P, PAR, (3, "v"), (2, "ubar"), [], [(0, True), (1, True), (4, False)],
+                                  mt, PAR.wt, 1.0 / 256.0)
+    assert np.allclose(got, pr.gg_ttxg(P, PAR), rtol=1e-12, atol=0)
+    P = _massive_points(800.0, (PAR.mW, 0.0, 0.0, 0.0), 6, seed=802)
+    got = pr.fermion_line_process(P, PAR, (0, "u"), (1, "vbar"),
+                                  [dict(leg=2, kind="V", gl=PAR.g / np.sqrt(2.0), gr=0.0, mass=PAR.mW)],
+                                  [(3, False), (4, False), (5, False)], 0.0, 0.0, 1.0 / 36.0)
+    assert np.allclose(got, pr.udx_wpggg(P, PAR), rtol=1e-12, atol=0)
+
+
+def test_ttxhg_ward_bose_and_boosts():
+    P = _massive_points(1500.0, (PAR.mt, PAR.mt, PAR.mH, 0.0), 5, seed=803)
+    ref0 = pr.gg_ttxhg(P, PAR, widths=False)
+    assert np.all(ref0 > 0) and np.all(np.isfinite(ref0))
+    for leg in (0, 1, 5):
+        bad = pr.gg_ttxhg(P, PAR, eps_override={leg: P[:, leg]}, widths=False)
+        assert np.all(np.abs(bad) < 1e-24 * ref0 * P[:, leg, 0] ** 2)
+    ref = pr.gg_ttxhg(P, PAR)
+    assert np.allclose(pr.gg_ttxhg(P[:, [1, 0, 2, 3, 4, 5]], PAR), ref, rtol=1e-12)
+    from test_oracle_processes import random_lorentz
+    assert np.allclose(pr.gg_ttxhg(random_lorentz(P, 804), PAR), ref, rtol=1e-10)
+
+
+def test_ward_identity_catches_dropped_triple_gluon_lines(monkeypatch):
+    """Without the diagrams whose three gluons join through two three-gluon vertices the gluon Ward
+    identity fails (a planted mistake in the engine's diagram set)."""
+    orig = pr._gluon_blocks
+    monkeypatch.setattr(pr, "_gluon_blocks", lambda legs: [b for b in orig(legs) if b[0] != "triple"])
+    monkeypatch.setattr(pr, "_VJETS", {})
+    P = _massive_points(1500.0, (PAR.mt, PAR.mt, PAR.mH, 0.0), 3, seed=805)
+    ref0 = pr.gg_ttxhg(P, PAR, widths=False)
+    bad = pr.gg_ttxhg(P, PAR, eps_override={5: P[:, 5]}, widths=False)
+    assert np.all(np.abs(bad) > 1e-8 * ref0 * P[:, 5, 0] ** 2)
