@@ -56,6 +56,9 @@ Functions and their pins (tests/test_oracle_processes.py):
   us_dchg         u s > d c h g  (WW fusion plus one jet): Ward identity, the soft-gluon limit
                    against 2 C_F (S_ud + S_sc) times u s > d c h (the lines' colours do not
                    interfere), boosts
+  us_dchgg        u s > d c h g g (WBF H plus two jets, 24 diagrams) on the two-line code (us_dch_ng),
+                   which equals us_dch and us_dchg at 0 and 1 gluons; Ward identity for each gluon (fails
+                   without the pair lines), Bose symmetry, boosts (tests/test_oracle_line.py)
   gg_ttxhg        g g > t t~ h g (H t t~ plus one jet, 54 diagrams) on the one-fermion-line engine
                    (fermion_line_process), which equals gg_ttxh, gg_ttxg and udx_wpggg point by point;
                    Ward identity for each gluon (fails without the triple-gluon lines), Bose symmetry,
@@ -1517,6 +1520,107 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
     return tot * average
 
 
+def us_dch_ng(P, par=SMParams(), eps_override=None):
+    """u(p0) s(p1) > d(p2) c(p3) H(p4) + n gluons (p5 ...), n up to 3, by W+ W- fusion (WBF H plus jets):
+    every diagram places the gluons, joined into lines (_gluon_blocks), on either quark line and orders
+    each line's insertions (its W vertex and its gluon lines).  The line s > c, with its W vertex left
+    open, is evaluated against the four basis vectors to give its current J2 (upper index); its W
+    propagator, the W W H vertex and the W propagator of the line u > d turn it into the vector that
+    line absorbs.  Colour: each line keeps its own string, (M1)_{d u} (M2)_{c s}, summed over explicit
+    indices (colour_projector).  eps_override: {leg: vector[N,4]} replaces a gluon's polarisation."""
+    ng = P.shape[1] - 5
+    key = ("wbf", ng)
+    if key not in _VJETS:
+        diags = []
+        for part in _set_partitions(list(range(ng))):
+            for choice in itertools.product(*[_gluon_blocks(b) for b in part]):
+                for side in itertools.product((0, 1), repeat=len(choice)):
+                    on = [[b for b, sd in zip(choice, side) if sd == k] for k in (0, 1)]
+                    for o1 in itertools.permutations([("W",)] + on[0]):
+                        for o2 in itertools.permutations([("W",)] + on[1]):
+                            diags.append((o1, o2))
+        tensors = []
+        for o1, o2 in diags:
+            t = np.zeros((3, 3, 3, 3) + (8,) * ng, dtype=complex)
+            for a in itertools.product(range(8), repeat=ng):
+                M = []
+                for o in (o1, o2):
+                    m_ = np.eye(3, dtype=complex)
+                    for ins in o:
+                        if ins[0] != "W":
+                            m_ = _block_colour(ins[0], ins[1], a) @ m_
+                    M.append(m_.T)   # [i_start, i_end]
+                t[(slice(None),) * 4 + a] = np.einsum("ud,sc->udsc", M[0], M[1])
+            tensors.append(t)
+        _VJETS[key] = (diags, colour.colour_projector(tensors))
+    diags, B = _VJETS[key]
+    p = [P[:, k] for k in range(P.shape[1])]
+    gs, gw, gwwh = par.gs, par.g / np.sqrt(2.0), par.gwwh
+    kg = {j: -p[5 + j] for j in range(ng)}
+    basis = [np.broadcast_to(np.eye(4)[mu], (P.shape[0], 4)).astype(complex) for mu in range(4)]
+    metric = np.array([1.0, -1.0, -1.0, -1.0])
+    tot = 0.0
+    for h in itertools.product(HEL_F, HEL_F, HEL_F, HEL_F, *([HEL_V] * ng)):
+        ub_d, u_u = bar(u_spinor(p[2], h[2])), u_spinor(p[0], h[0])
+        ub_c, u_s = bar(u_spinor(p[3], h[3])), u_spinor(p[1], h[1])
+        eps = {j: polarisation(p[5 + j], h[4 + j]).conj() for j in range(ng)}
+        if eps_override:
+            for leg, vec in eps_override.items():
+                eps[leg - 5] = vec.astype(complex)
+        cache = {}
+
+        def gline(kind, spec):
+            k_ = (kind, spec)
+            if k_ in cache:
+                return cache[k_]
+            if kind == "g":
+                out = (eps[spec], -kg[spec])
+            elif kind == "pair":
+                x, y = spec
+                k = kg[x] + kg[y]
+                out = (vector_prop(k, vvv_out(eps[x], kg[x], eps[y], kg[y], -k, gs)), -k)
+            elif kind == "triple":
+                x, y, z = spec
+                J, mk = gline("pair", (x, y))
+                k = -mk
+                K = k + kg[z]
+                out = (vector_prop(K, vvv_out(J, k, eps[z], kg[z], -K, gs)), -K)
+            else:
+                (x, y, z), s_ = spec
+                K = kg[x] + kg[y] + kg[z]
+                out = (vector_prop(K, -1j * gs * gs * _vvvv_out(eps[x], eps[y], eps[z])[s_]), -K)
+            cache[k_] = out
+            return out
+
+        amps = []
+        for o1, o2 in diags:
+            # W momenta: what each line gives away at its W vertex
+            q = []
+            for o, pin, pout in ((o1, p[0], p[2]), (o2, p[1], p[3])):
+                qq = pin - pout
+                for ins in o:
+                    if ins[0] != "W":
+                        qq = qq - gline(*ins)[1]
+                q.append(qq)
+            # the line s > c with its W vertex open: J2_mu against the basis vectors, raised
+            ins2 = [None if x[0] == "W" else (vector_insertion(gline(*x)[0], gs, gs), gline(*x)[1]) for x in o2]
+            J2 = np.zeros((P.shape[0], 4), dtype=complex)
+            for mu in range(4):
+                seq = [(vector_insertion(basis[mu], gw, 0.0), q[1]) if x is None else x for x in ins2]
+                J2[:, mu] = metric[mu] * fermion_line(ub_c, u_s, p[1], seq)
+            V = vector_prop(q[0], 1j * gwwh * vector_prop(q[1], J2, par.mW, par.wW), par.mW, par.wW)
+            seq1 = [(vector_insertion(V, gw, 0.0), q[0]) if x[0] == "W" else
+                    (vector_insertion(gline(*x)[0], gs, gs), gline(*x)[1]) for x in o1]
+            amps.append(fermion_line(ub_d, u_u, p[0], seq1) / 1j)
+        tot = tot + colour.colour_norm(amps, B)
+    return tot / 36.0
+
+
+def us_dchgg(P, par=SMParams(), eps_override=None):
+    """u s > d c H g g (WBF H plus two jets, 24 diagrams; us_dch_ng)."""
+    return us_dch_ng(P, par, eps_override)
+
+
 def gg_ttxhg(P, par=SMParams(), eps_override=None, widths=True):
     """g(0) g(1) > t(2) t~(3) H(4) g(5) (H t t~ plus one jet): the top line from v(p3) to ubar(p2) with the
     Higgs (Yukawa -mt/v) and the three gluons, 54 diagrams (fermion_line_process)."""
@@ -1913,6 +2017,7 @@ PROCESSES = {
     "u d~ > w+ g g g": udx_wpggg,
     "u u~ > z g g g": uux_zggg,
     "g g > t t~ h g": gg_ttxhg,
+    "u s > d c h g g": us_dchgg,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,

@@ -9,6 +9,9 @@ it, g g > t t~ H g (H t t~ plus one jet, the paper's Sect. 2 Htt~ + jets family)
   vector insertions.
 - g g > t t~ H g: the Ward identity of each gluon at zero top width (fixed-width top propagators break
   it at O(m Gamma / (p^2 - m^2))), Bose symmetry of the incoming gluons, boosts.
+- WBF H plus jets on two quark lines (us_dch_ng, u s > d c H + n gluons): equal to u s > d c H and
+  u s > d c H g at n = 0, 1; at n = 2 the Ward identity of each gluon (fails without the three-gluon
+  pair lines), Bose symmetry, boosts.
 """
 import numpy as np
 import pytest
@@ -60,3 +63,39 @@ def test_ward_identity_catches_dropped_triple_gluon_lines(monkeypatch):
     ref0 = pr.gg_ttxhg(P, PAR, widths=False)
     bad = pr.gg_ttxhg(P, PAR, eps_override={5: P[:, 5]}, widths=False)
     assert np.all(np.abs(bad) > 1e-8 * ref0 * P[:, 5, 0] ** 2)
+
+
+# ---------------------------------------------------------------------------
+# WBF H plus jets: two quark lines (us_dch_ng)
+# ---------------------------------------------------------------------------
+def test_wbf_lines_equal_the_zero_and_one_gluon_oracles():
+    """The two-line code with no gluon equals u s > d c H (closed-form pinned) and with one gluon
+    u s > d c H g (Ward- and soft-limit-pinned), point by point."""
+    P = _massive_points(1000.0, (0.0, 0.0, PAR.mH), 6, seed=900)
+    assert np.allclose(pr.us_dch_ng(P, PAR), pr.us_dch(P, PAR), rtol=1e-12, atol=0)
+    P = _massive_points(1000.0, (0.0, 0.0, PAR.mH, 0.0), 6, seed=901)
+    assert np.allclose(pr.us_dch_ng(P, PAR), pr.us_dchg(P, PAR), rtol=1e-12, atol=0)
+
+
+def test_wbf_h_two_jets_ward_bose_and_boosts():
+    P = _massive_points(1000.0, (0.0, 0.0, PAR.mH, 0.0, 0.0), 5, seed=902)
+    ref = pr.us_dchgg(P, PAR)
+    assert np.all(ref > 0) and np.all(np.isfinite(ref))
+    for leg in (5, 6):
+        bad = pr.us_dchgg(P, PAR, eps_override={leg: P[:, leg]})
+        assert np.all(np.abs(bad) < 1e-24 * ref * P[:, leg, 0] ** 2)
+    assert np.allclose(pr.us_dchgg(P[:, [0, 1, 2, 3, 4, 6, 5]], PAR), ref, rtol=1e-12)
+    from test_oracle_processes import random_lorentz
+    assert np.allclose(pr.us_dchgg(random_lorentz(P, 903), PAR), ref, rtol=1e-10)
+
+
+def test_wbf_ward_identity_catches_dropped_pair_lines(monkeypatch):
+    """Without the diagrams whose two gluons join through the three-gluon vertex the Ward identity of
+    a gluon fails."""
+    orig = pr._gluon_blocks
+    monkeypatch.setattr(pr, "_gluon_blocks", lambda legs: [b for b in orig(legs) if b[0] != "pair"])
+    monkeypatch.setattr(pr, "_VJETS", {})
+    P = _massive_points(1000.0, (0.0, 0.0, PAR.mH, 0.0, 0.0), 3, seed=904)
+    ref = pr.us_dchgg(P, PAR)
+    bad = pr.us_dchgg(P, PAR, eps_override={5: P[:, 5]})
+    assert np.all(np.abs(bad) > 1e-8 * ref * P[:, 5, 0] ** 2)
