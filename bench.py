@@ -312,8 +312,9 @@ def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
             n = w["n"]
             kin = B.make_kin(**kin_args(w))
             row = {"points": n}
+            prm = B.make_params(**w["params"]) if "params" in w else None
             for prec, name in ((B.ME_MIXED, "mixed"), (B.ME_FP64, "fp64")):
-                h = B.me_create(w["process"], None, prec)
+                h = B.me_create(w["process"], prm, prec)
                 slow = prec == B.ME_FP64 and key == "gg_gggg"
                 nw, ns = (1, 2) if slow else (warmup, steps)
                 acc_dev = torch.zeros(4, dtype=torch.float64, device=dev)
@@ -352,7 +353,7 @@ def per_process_table(B, torch, dev, stream, flush, offset0, warmup, steps):
                     mom = torch.empty(info.n_ext * 4 * n, dtype=torch.float64, device=dev)
                     m64 = torch.empty(n, dtype=torch.float64, device=dev)
                     B.xsec_step(h, w["seed"], offset0, n, kin, stream, B.me_xsec_acc(), m64, mom)
-                    hm = B.me_create(w["process"], None, B.ME_MIXED)
+                    hm = B.me_create(w["process"], prm, B.ME_MIXED)
                     mmx = torch.empty(n, dtype=torch.float64, device=dev)
                     B.me_eval(hm, mom, n, mmx, stream)
                     torch.cuda.synchronize(dev)

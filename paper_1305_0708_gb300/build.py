@@ -64,6 +64,10 @@ PROCESSES = [
     ("u d > u d h", []),
     ("u d > u d h h", []),
     ("u d > u d h h h", []),
+    ("u d~ > w+ g g g", []),
+    ("u u~ > z g g g", []),
+    ("g g > t t~ h g", []),
+    ("u s > d c h g g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)
@@ -89,6 +93,19 @@ def _hash(*parts):
     return h.hexdigest()[:16]
 
 
+def _hel_loop_choice(prog):
+    """None (the code generator's threshold on program length), or the form forced for every process
+    whose straight-line program exceeds ME_HEL_LOOP_FLOPS FP32 flops per event when that is set (to
+    compare the two forms on the same process)."""
+    limit = os.environ.get("ME_HEL_LOOP_FLOPS")
+    if not limit:
+        return None
+    from paper_1305_0708_gb300.compiler.codegen import _Emitter
+    probe = _Emitter(prog, "probe", "mixed")
+    probe.generate()
+    return probe.flops32 > float(limit)
+
+
 def generate_units():
     """Run the process compiler; returns [(tag, path, meta)]."""
     sys.path.insert(0, ROOT)
@@ -100,7 +117,7 @@ def generate_units():
     for name, aliases in PROCESSES:
         tag = process_symbol(name)
         prog = compile_process(name)
-        src, info = generate_source(prog, tag)
+        src, info = generate_source(prog, tag, hel_loop=_hel_loop_choice(prog))
         path = os.path.join(GEN, tag + ".cu")
         if not os.path.exists(path) or open(path).read() != src:
             with open(path, "w") as f:

@@ -16,8 +16,13 @@ dispatches to.  Per event it emits, in order:
   6. the colour sum |M_h|^2 = (J^T C J)/den with the integer matrix in the
      code, the helicity sum and the initial-state average.
 
-Processes with a large colour dimension hand J to the tensor-core colour
-kernel instead (colour_gemm.cuh).
+Programs longer than HEL_LOOP_FLOPS (V + 3 jets, t t~ g, t t~ H g, W+ W- gamma) are emitted in the
+helicity-loop form instead: one copy of steps 3-6 inside a loop over the live
+helicity combinations, read from a table at run time (no recycling across
+helicities, but a program n_live times shorter to compile and to hold).
+Internal lines that carry the same external legs and particle share one
+momentum and denominator.  All-gluon processes use the colour-ordered block
+kernel (gluon_process.cu) instead.
 """
 from fractions import Fraction
 
@@ -36,14 +41,15 @@ def _flip(h):
 
 
 def _hname(h):
-    return {-1: "m", 0: "z", 1: "p"}[h]
+    return {-1: "m", 0: "z", 1: "p", "r": "r"}[h]
 
 
 # the variant of every node in the helicity-loop form: helicities known at run time only
 RT = ("rt",)
 
 # straight-line programs above this many FP32 flops per event are emitted in the helicity-loop form
-HEL_LOOP_FLOPS = 100000
+# (g g > t t~ g, 94k: 2.3 times faster in the loop form; u u~ > w+ w- a, 73k: 3 % faster)
+HEL_LOOP_FLOPS = 50000
 
 
 def _vname(nid, var):
@@ -230,7 +236,7 @@ class _Emitter:
         K = p.n_colour
         C = p.cmat_num
         if self.hel_loop:
-            self._hel_loop_body(need)
+            self._hel_loop_body(need, emitted)
             return
         E("  // per helicity: the wavefunctions and sub-currents it needs first, its diagram amplitudes")
         E("  // into colour components, then its colour sum (J^T C J)/den; helicity sum, average")
@@ -277,33 +283,58 @@ class _Emitter:
         E("    tot += s;")
         E("  }")
 
-    def _hel_loop_body(self, need):
-        """The helicity-loop form: one copy of every wavefunction, sub-current and amplitude, with the
-        external helicities read from the live-combination table (hel_code) at run time, in a loop
-        over the live combinations.  No helicity recycling and no chirality halves known at compile
-        time, so more flops per helicity, but the program is n_live times shorter (the paper's remedy
-        for amplitude functions too long to compile or to keep in registers, Sect. 5.3)."""
+    def fermion_groups(self):
+        """Live combinations grouped by the helicities of the massless external fermions: one loop
+        body per group, with those helicities (so the spinor halves) fixed at compile time."""
+        p = self.p
+        fl = [k for k, leg in enumerate(p.legs) if PARTICLES[leg.particle].is_fermion
+              and PARTICLES[leg.particle].massless]
+        groups = {}
+        for i, hs in enumerate(p.live):
+            groups.setdefault(tuple(hs[k] for k in fl), []).append(i)
+        return fl, list(groups.items())
+
+    def _hel_loop_body(self, need, emitted):
+        """The helicity-loop form: one copy of every wavefunction, sub-current and amplitude per group of
+        live combinations that share the massless fermions' helicities (fixed in the code, so the zero
+        spinor halves stay known), with the other helicities read from the group's table (hel_code_g)
+        at run time, in a loop over the group.  No helicity recycling across the loop, so more flops
+        per helicity, but the program is many times shorter (the paper's remedy for amplitude functions
+        too long to compile or to keep in registers, Sect. 5.3)."""
         p = self.p
         E = self.emit
-        E("  // helicity loop: the live combinations, 2 bits per leg (h + 1), from hel_code")
+        fl, groups = self.fermion_groups()
         E("  R tot = R(0);")
-        E("#pragma unroll 1")
-        E(f"  for (int ih = 0; ih < {len(p.live)}; ++ih) {{")
-        E("  const uint32_t hc = hel_code(ih);")
-        for k in range(p.n_ext):
-            E(f"  const int hl{k} = (int)((hc >> {2 * k}) & 3u) - 1;")
-        aids = sorted({aid for terms in p.amp_terms for aid, _ in terms})
         f0 = self.flops32
-        for aid in aids:
-            for c in p.amps[aid].children:
-                need(c, RT)
-        for k in range(p.n_colour):
-            E(f"  me::cx<R> J_{k} = me::mk(R(0), R(0));")
-        for aid in aids:
-            self.amp_code(aid, [RT] * len(p.amps[aid].children), "")
-        self._colour_sum("")
-        E("  }")
-        self.flops32 = f0 + (self.flops32 - f0) * len(p.live)
+        total = 0
+        for gi, (key, idxs) in enumerate(groups):
+            fixed = dict(zip(fl, key))
+            E(f"  {{  // massless fermion helicities {key}: the other legs' from hel_code_g{gi}, 2 bits per leg (h + 1)")
+            E("#pragma unroll 1")
+            E(f"  for (int ih = 0; ih < {len(idxs)}; ++ih) {{")
+            E(f"  const uint32_t hc = hel_code_g{gi}(ih);")
+            for k in range(p.n_ext):
+                if k not in fixed:
+                    E(f"  const int hl{k} = (int)((hc >> {2 * k}) & 3u) - 1;")
+            emitted.clear()
+
+            def var_of(nid):
+                return tuple(fixed.get(l, "r") for l in sorted(p.nodes[nid].legs))
+            aids = sorted({aid for hi in idxs for aid, _ in p.amp_terms[hi]})
+            g0 = self.flops32
+            for aid in aids:
+                for c in p.amps[aid].children:
+                    need(c, var_of(c))
+            for k in range(p.n_colour):
+                E(f"  me::cx<R> J_{k} = me::mk(R(0), R(0));")
+            for aid in aids:
+                self.amp_code(aid, [var_of(c) for c in p.amps[aid].children], "")
+            self._colour_sum("")
+            E("  }")
+            E("  }")
+            total += (self.flops32 - g0) * len(idxs)
+            self.flops32 = g0
+        self.flops32 = f0 + total
         if self.mode == "mixed":
             E(f"  return tot * {float(p.average / p.cmat_den)!r}f;")
         else:
@@ -324,7 +355,8 @@ class _Emitter:
         nd = p.nodes[nid]
         leg = p.legs[nd.leg]
         part = PARTICLES[leg.particle]
-        h = f"hl{nd.leg}" if var == RT else var[0]
+        rt = var == RT or var[0] == "r"
+        h = f"hl{nd.leg}" if rt else var[0]
         name = _vname(nid, var)
         inc = "true" if leg.incoming else "false"
         if part.is_fermion and not part.massless:
@@ -334,7 +366,7 @@ class _Emitter:
             self.half[name] = frozenset("ul")
             self.flops32 += 40
         elif part.is_fermion:
-            if var == RT:  # the chirality is known at run time only: both halves
+            if rt:  # the chirality is known at run time only: both halves
                 up, lo = frozenset("ul"), frozenset("ul")
             else:
                 chi = _ext_chirality(leg, h)
@@ -624,10 +656,13 @@ def generate_source(prog, tag, hel_loop=None):
     emmx.generate()
     hel_fn = ""
     if hel_loop:
-        cases = " ".join(f"case {i}: return {c}u;" for i, c in enumerate(hel_codes(prog)))
-        hel_fn = f"""
-  // live helicity combinations, 2 bits per leg (h + 1)
-  static __host__ __device__ __forceinline__ uint32_t hel_code(int ih) {{
+        codes = hel_codes(prog)
+        _, groups = emmx.fermion_groups()
+        for gi, (key, idxs) in enumerate(groups):
+            cases = " ".join(f"case {i}: return {codes[c]}u;" for i, c in enumerate(idxs))
+            hel_fn += f"""
+  // live helicity combinations with massless fermion helicities {key}, 2 bits per leg (h + 1)
+  static __host__ __device__ __forceinline__ uint32_t hel_code_g{gi}(int ih) {{
     switch (ih) {{ {cases} default: return 0u; }}
   }}
 """

@@ -199,6 +199,31 @@ VARIANTS = {
         n=1 << 20, seed=47, cuts=None, s_ident=1.0 / 6.0,
         describe="u d > u d H H H (the paper's Sect. 2.10 process: Z Z and W+ W- fusion, 50 diagrams), "
                  "massive RAMBO at sqrt(s)=1.5 TeV, 2^20 points, seed 47"),
+    "ud_udhhh_cms": dict(
+        process="u d > u d h h h", kind="rambo", sqrt_s=1500.0, masses=(0, 0, 0, 0, 125.0, 125.0, 125.0),
+        n=1 << 20, seed=47, cuts=None, s_ident=1.0 / 6.0, params=dict(complex_mass=1),
+        describe="u d > u d H H H with the complex-mass option of Sect. 7.11 (me_params.complex_mass = 1), "
+                 "the same points as ud_udhhh"),
+    "udx_wpggg": dict(
+        process="u d~ > w+ g g g", kind="rambo", sqrt_s=800.0, masses=(0, 0, 80.4, 0, 0, 0), n=1 << 18, seed=48,
+        cuts=dict(legs=(3, 4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=1.0 / 6.0,
+        describe="u d~ > W+ g g g (on-shell W plus three jets, 54 diagrams, helicity-loop program), massive "
+                 "RAMBO at sqrt(s)=800 GeV, gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^18 accepted points, seed 48"),
+    "gg_ttxhg": dict(
+        process="g g > t t~ h g", kind="rambo", sqrt_s=1500.0, masses=(0, 0, 175.0, 175.0, 125.0, 0), n=1 << 18,
+        seed=50, cuts=dict(legs=(5,), pt_min=20.0, eta_max=2.5, dr_min=0.0), s_ident=1.0,
+        describe="g g > t t~ H g (H t t~ plus one jet, 54 diagrams, helicity-loop program), massive RAMBO at "
+                 "sqrt(s)=1.5 TeV, gluon pT>20, |eta|<2.5, 2^18 accepted points, seed 50"),
+    "us_dchgg": dict(
+        process="u s > d c h g g", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 0, 0, 125.0, 0, 0), n=1 << 20,
+        seed=51, cuts=dict(legs=(2, 3, 5, 6), pt_min=20.0, eta_max=5.0, dr_min=0.4), s_ident=0.5,
+        describe="u s > d c H g g (W+ W- fusion plus two jets, 24 diagrams), massive RAMBO at sqrt(s)=1 TeV, "
+                 "the four jets pT>20, |eta|<5, DeltaR>0.4, 2^20 accepted points, seed 51"),
+    "uux_zggg": dict(
+        process="u u~ > z g g g", kind="rambo", sqrt_s=800.0, masses=(0, 0, 91.1876, 0, 0, 0), n=1 << 18,
+        seed=49, cuts=dict(legs=(3, 4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=1.0 / 6.0,
+        describe="u u~ > Z g g g (on-shell Z plus three jets, 54 diagrams, helicity-loop program), massive "
+                 "RAMBO at sqrt(s)=800 GeV, gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^18 accepted points, seed 49"),
 }
 
 KIND = {"two_body": 0, "rambo": 1, "ttbar": 2, "rambo_bw": 3, "ypt": 4}

@@ -67,6 +67,10 @@ CASES = {
     "u d > u d h": (opr.ud_udh, 1000.0, (0.0, 0.0, 125.0), ()),
     "u d > u d h h": (opr.ud_udhh, 1000.0, (0.0, 0.0, 125.0, 125.0), ()),
     "u d > u d h h h": (opr.ud_udhhh, 1500.0, (0.0, 0.0, 125.0, 125.0, 125.0), ()),
+    "u d~ > w+ g g g": (opr.udx_wpggg, 800.0, (80.4, 0.0, 0.0, 0.0), (3, 4, 5)),
+    "u u~ > z g g g": (opr.uux_zggg, 800.0, (91.1876, 0.0, 0.0, 0.0), (3, 4, 5)),
+    "g g > t t~ h g": (opr.gg_ttxhg, 1500.0, (175.0, 175.0, 125.0, 0.0), (5,)),
+    "u s > d c h g g": (opr.us_dchgg, 1000.0, (0.0, 0.0, 125.0, 0.0, 0.0), (2, 3, 5, 6)),
 }
 
 # the complex-mass option (Sect. 7.11): processes whose couplings it makes complex
