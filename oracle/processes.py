@@ -59,6 +59,9 @@ Functions and their pins (tests/test_oracle_processes.py):
   us_dchgg        u s > d c h g g (WBF H plus two jets, 24 diagrams) on the two-line code (us_dch_ng),
                    which equals us_dch and us_dchg at 0 and 1 gluons; Ward identity for each gluon (fails
                    without the pair lines), Bose symmetry, boosts (tests/test_oracle_line.py)
+  uux_zzgg        u u~ > z z g g (V V plus two jets, 30 diagrams) on the one-fermion-line engine, which
+                   equals uux_zz and uux_zzg with no and one gluon; Ward identity for each gluon, Bose
+                   symmetry of the gluons and of the Z bosons, boosts (tests/test_oracle_line.py)
   gg_ttxhg        g g > t t~ h g (H t t~ plus one jet, 54 diagrams) on the one-fermion-line engine
                    (fermion_line_process), which equals gg_ttxh, gg_ttxg and udx_wpggg point by point;
                    Ward identity for each gluon (fails without the triple-gluon lines), Bose symmetry,
@@ -1621,6 +1624,15 @@ def us_dchgg(P, par=SMParams(), eps_override=None):
     return us_dch_ng(P, par, eps_override)
 
 
+def uux_zzgg(P, par=SMParams(), eps_override=None):
+    """u(p0) u~(p1) > Z(p2) Z(p3) g(p4) g(p5) (V V plus two jets, 30 diagrams): the quark line from u(p0)
+    to vbar(p1) with both Z bosons and the gluons (fermion_line_process)."""
+    gl, gr = _z_couplings("u", par)
+    z = [dict(leg=k, kind="V", gl=gl, gr=gr, mass=par.mZ) for k in (2, 3)]
+    return fermion_line_process(P, par, (0, "u"), (1, "vbar"), z, [(4, False), (5, False)], 0.0, 0.0, 1.0 / 36.0,
+                                eps_override)
+
+
 def gg_ttxhg(P, par=SMParams(), eps_override=None, widths=True):
     """g(0) g(1) > t(2) t~(3) H(4) g(5) (H t t~ plus one jet): the top line from v(p3) to ubar(p2) with the
     Higgs (Yukawa -mt/v) and the three gluons, 54 diagrams (fermion_line_process)."""
@@ -2018,6 +2030,7 @@ PROCESSES = {
     "u u~ > z g g g": uux_zggg,
     "g g > t t~ h g": gg_ttxhg,
     "u s > d c h g g": us_dchgg,
+    "u u~ > z z g g": uux_zzgg,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,

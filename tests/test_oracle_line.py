@@ -9,6 +9,9 @@ it, g g > t t~ H g (H t t~ plus one jet, the paper's Sect. 2 Htt~ + jets family)
   vector insertions.
 - g g > t t~ H g: the Ward identity of each gluon at zero top width (fixed-width top propagators break
   it at O(m Gamma / (p^2 - m^2))), Bose symmetry of the incoming gluons, boosts.
+- V V plus jets (u u~ > Z Z g g) on the same engine: equal to u u~ > Z Z (closed form) and u u~ > Z Z g
+  with no and one gluon; Ward identity of each gluon, Bose symmetry of the gluons and of the Z bosons,
+  boosts.
 - WBF H plus jets on two quark lines (us_dch_ng, u s > d c H + n gluons): equal to u s > d c H and
   u s > d c H g at n = 0, 1; at n = 2 the Ward identity of each gluon (fails without the three-gluon
   pair lines), Bose symmetry, boosts.
@@ -99,3 +102,30 @@ def test_wbf_ward_identity_catches_dropped_pair_lines(monkeypatch):
     ref = pr.us_dchgg(P, PAR)
     bad = pr.us_dchgg(P, PAR, eps_override={5: P[:, 5]})
     assert np.all(np.abs(bad) > 1e-8 * ref * P[:, 5, 0] ** 2)
+
+
+# ---------------------------------------------------------------------------
+# V V plus jets on the one-line engine: u u~ > Z Z g g
+# ---------------------------------------------------------------------------
+def test_zz_plus_jets_engine_equals_the_zero_and_one_gluon_oracles():
+    gl, gr = pr._z_couplings("u", PAR)
+    z = [dict(leg=k, kind="V", gl=gl, gr=gr, mass=PAR.mZ) for k in (2, 3)]
+    P = _massive_points(500.0, (PAR.mZ, PAR.mZ), 6, seed=950)
+    got = pr.fermion_line_process(P, PAR, (0, "u"), (1, "vbar"), z, [], 0.0, 0.0, 1.0 / 36.0)
+    assert np.allclose(got, pr.uux_zz(P, PAR), rtol=1e-12, atol=0)
+    P = _massive_points(500.0, (PAR.mZ, PAR.mZ, 0.0), 6, seed=951)
+    got = pr.fermion_line_process(P, PAR, (0, "u"), (1, "vbar"), z, [(4, False)], 0.0, 0.0, 1.0 / 36.0)
+    assert np.allclose(got, pr.uux_zzg(P, PAR), rtol=1e-12, atol=0)
+
+
+def test_zzgg_ward_bose_and_boosts():
+    P = _massive_points(600.0, (PAR.mZ, PAR.mZ, 0.0, 0.0), 5, seed=952)
+    ref = pr.uux_zzgg(P, PAR)
+    assert np.all(ref > 0) and np.all(np.isfinite(ref))
+    for leg in (4, 5):
+        bad = pr.uux_zzgg(P, PAR, eps_override={leg: P[:, leg]})
+        assert np.all(np.abs(bad) < 1e-24 * ref * P[:, leg, 0] ** 2)
+    assert np.allclose(pr.uux_zzgg(P[:, [0, 1, 2, 3, 5, 4]], PAR), ref, rtol=1e-12)
+    assert np.allclose(pr.uux_zzgg(P[:, [0, 1, 3, 2, 4, 5]], PAR), ref, rtol=1e-12)
+    from test_oracle_processes import random_lorentz
+    assert np.allclose(pr.uux_zzgg(random_lorentz(P, 953), PAR), ref, rtol=1e-10)
