@@ -68,6 +68,7 @@ PROCESSES = [
     ("u u~ > z g g g", []),
     ("g g > t t~ h g", []),
     ("u s > d c h g g", []),
+    ("u u~ > z z g g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

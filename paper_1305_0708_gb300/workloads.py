@@ -219,6 +219,11 @@ VARIANTS = {
         seed=51, cuts=dict(legs=(2, 3, 5, 6), pt_min=20.0, eta_max=5.0, dr_min=0.4), s_ident=0.5,
         describe="u s > d c H g g (W+ W- fusion plus two jets, 24 diagrams), massive RAMBO at sqrt(s)=1 TeV, "
                  "the four jets pT>20, |eta|<5, DeltaR>0.4, 2^20 accepted points, seed 51"),
+    "uux_zzgg": dict(
+        process="u u~ > z z g g", kind="rambo", sqrt_s=600.0, masses=(0, 0, 91.1876, 91.1876, 0, 0), n=1 << 18,
+        seed=52, cuts=dict(legs=(4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.25,
+        describe="u u~ > Z Z g g (V V plus two jets, 30 diagrams, helicity-loop program), massive RAMBO at "
+                 "sqrt(s)=600 GeV, gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^18 accepted points, seed 52"),
     "uux_zggg": dict(
         process="u u~ > z g g g", kind="rambo", sqrt_s=800.0, masses=(0, 0, 91.1876, 0, 0, 0), n=1 << 18,
         seed=49, cuts=dict(legs=(3, 4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=1.0 / 6.0,
