@@ -60,8 +60,8 @@ EXECUTED_FLOPS_PER_POINT = {
 # DRAM bytes per point of the mixed-path kernels (dram__bytes_read.sum + dram__bytes_write.sum of one
 # ncu capture, divided by the points of that launch; profiles/ holds the captures).  A launch's
 # traffic is this times its points: the kernels stream their points, so traffic grows in proportion.
-TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (85.306112e6 + 282.752e6) / 2 ** 20,
-                     ("udx_epvegg", "k_me"): (214.006016e6 + 3.457536e6) / 2 ** 20,
+TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (85.316608e6 + 282.551296e6) / 2 ** 20,
+                     ("udx_epvegg", "k_me"): (214.00448e6 + 3.760384e6) / 2 ** 20,
                      ("gg_gggg", "k_me"): (3.478784e6 + 0.07552e6) / 16384}
 
 # Warp instructions issued per accepted point (smsp__inst_executed.sum of the same ncu captures,
