@@ -39,8 +39,8 @@ sys.path.insert(0, ROOT)
 # removes the repeated subexpressions of the helicity variants; it is the fallback where no
 # capture exists.
 EXECUTED_FLOPS_PER_POINT = {
-    ("udx_epvegg", "k_ps"): 3912.1,
-    ("udx_epvegg", "k_me"): 3121.0,
+    ("udx_epvegg", "k_ps"): 3916.3,
+    ("udx_epvegg", "k_me"): 3039.0,
     ("gg_ttx_dilep", "k_ps"): 7003.3,
     ("gg_ttx_dilep", "k_me"): 6758.0,
     ("us_dchh", "k_ps"): 5216.0,
@@ -52,7 +52,7 @@ EXECUTED_FLOPS_PER_POINT = {
     ("uux_wpwm", "k_ps"): 3200.0,
     ("uux_wpwm", "k_me"): 3691.7,
     ("udx_epvegg_bw", "k_ps"): 6256.0,
-    ("udx_epvegg_bw", "k_me"): 3121.0,
+    ("udx_epvegg_bw", "k_me"): 3039.0,
     ("udx_wpz", "k_ps"): 3224.0,
     ("udx_wpz", "k_me"): 2346.6,
 }
@@ -60,16 +60,16 @@ EXECUTED_FLOPS_PER_POINT = {
 # DRAM bytes per point of the mixed-path kernels (dram__bytes_read.sum + dram__bytes_write.sum of one
 # ncu capture, divided by the points of that launch; profiles/ holds the captures).  A launch's
 # traffic is this times its points: the kernels stream their points, so traffic grows in proportion.
-TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (85.316608e6 + 282.551296e6) / 2 ** 20,
+TRAFFIC_PER_POINT = {("udx_epvegg", "k_ps"): (4.913152e6 + 229.596928e6) / 2 ** 20,
                      ("udx_epvegg", "k_me"): (214.00448e6 + 3.760384e6) / 2 ** 20,
-                     ("gg_gggg", "k_me"): (3.478784e6 + 0.07552e6) / 16384}
+                     ("gg_gggg", "k_me"): (3.488256e6 + 0.070912e6) / 16384}
 
 # Warp instructions issued per accepted point (smsp__inst_executed.sum of the same ncu captures,
 # divided by the points of the launch).  The phase-space kernel mixes integer (Philox), FP32 and
 # control instructions and is bound by instruction issue, so its roofline is also stated against
 # the issue rate.
-WARP_INSTRUCTIONS_PER_POINT = {("udx_epvegg", "k_ps"): 175110311.0 / 2 ** 20,
-                               ("udx_epvegg", "k_me"): 97712128.0 / 2 ** 20}
+WARP_INSTRUCTIONS_PER_POINT = {("udx_epvegg", "k_ps"): 174954989.0 / 2 ** 20,
+                               ("udx_epvegg", "k_me"): 94714880.0 / 2 ** 20}
 
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128

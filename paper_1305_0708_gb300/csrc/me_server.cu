@@ -299,6 +299,7 @@ struct me_server_s {
   std::map<std::pair<const void*, int>, std::unique_ptr<Proc>> procs;
   std::mutex proc_mu;                      // process cache and autotuning
   me_server_stats st{};
+  uint64_t req_bytes = 0;  // budget held by admitted requests' buffers (until the client collects them)
   std::thread worker;
   size_t rr = 0;
 
@@ -504,6 +505,7 @@ bool me_server_s::admit(Request* q) {
   q->stage = free_stage.back();
   free_stage.pop_back();
   st.bytes_in_use += bytes;
+  req_bytes += bytes;
   st.bytes_peak = st.bytes_in_use > st.bytes_peak ? st.bytes_in_use : st.bytes_peak;
   ++st.admitted;
   q->res.t_admit_ms = now_ms(t0);
@@ -650,7 +652,10 @@ void me_server_s::release(Request* q) {
   q->ready = nullptr;
   if (q->stage >= 0) free_stage.push_back(q->stage);
   q->stage = -1;
-  if (q->bytes) st.bytes_in_use -= q->bytes;
+  if (q->bytes) {
+    st.bytes_in_use -= q->bytes;
+    req_bytes -= q->bytes;
+  }
   q->bytes = 0;
 }
 
@@ -863,7 +868,9 @@ void me_server_s::run() {
     while (!stop && !waiting.empty()) {
       Request* q = waiting.front();
       if (!grow_workspaces(q->ws_need) || !admit(q)) {
-        if (active.empty() && !inflight) {  // it cannot fit beside the slot workspaces alone
+        // it cannot fit beside the slot workspaces alone: nothing runs, and no finished request
+        // still holds buffers that its client has yet to collect
+        if (active.empty() && !inflight && req_bytes == 0) {
           waiting.pop_front();
           finish(q, ME_ERR_OOM);
           progress = true;
@@ -1095,6 +1102,7 @@ me_status me_server_wait(me_server s, int64_t ticket, double timeout_s, me_reque
   s->release(q);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->admin);
   s->all.erase(it);
+  s->cv_submit.notify_one();  // freed budget: the scheduler may admit a waiting request
   if (e != cudaSuccess) return cuda_fail(e, "me_server_wait copy");
   if (st != ME_OK) return fail(st, "me_server_wait: request failed");
   return ME_OK;

@@ -452,28 +452,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
       bool ok;
       uint8_t vbins[GRID ? kGridMaxDims : 1];  // grid steps: bin of every mapped uniform
       uint8_t* vb = GRID && kin.vg_bins ? vbins : nullptr;
+      // Every lane stores its point's slots, accepted or not: a warp's stores then fill whole
+      // 32-byte sectors, and the redraw of a rejected point (one of the next few rounds, through the
+      // queue) overwrites its slots while their lines are still in L2.  Stores from lanes that skip
+      // them leave partly written sectors, which L2 completes with reads from DRAM.
       if constexpr (MIXED) {
-        df q[NEXT][4];
+        df q[NEXT][4] = {};
         ok = draw_point_df<NEXT, KIND>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat, vb);
-        if (ok) {
 #pragma unroll
-          for (int k = 0; k < NEXT; ++k) {
+        for (int k = 0; k < NEXT; ++k) {
 #pragma unroll
-            for (int mu = 0; mu < 4; ++mu) {
-              ph[(int64_t)(k * 4 + mu) * m + ev] = q[k][mu].hi;
-              pl[(int64_t)(k * 4 + mu) * m + ev] = q[k][mu].lo;
-            }
+          for (int mu = 0; mu < 4; ++mu) {
+            ph[(int64_t)(k * 4 + mu) * m + ev] = q[k][mu].hi;
+            pl[(int64_t)(k * 4 + mu) * m + ev] = q[k][mu].lo;
           }
         }
       } else {
-        double q[NEXT][4];
+        double q[NEXT][4] = {};
         ok = draw_point<NEXT, KIND>(kin, seed, offset + (uint64_t)ev, att, q, wps, shat, vb);
-        if (ok) {
 #pragma unroll
-          for (int k = 0; k < NEXT; ++k) {
+        for (int k = 0; k < NEXT; ++k) {
 #pragma unroll
-            for (int mu = 0; mu < 4; ++mu) pd[(int64_t)(k * 4 + mu) * m + ev] = q[k][mu];
-          }
+          for (int mu = 0; mu < 4; ++mu) pd[(int64_t)(k * 4 + mu) * m + ev] = q[k][mu];
         }
       }
       if (GRID && a.vg_idx && (ok || att + 1 >= kin.max_attempts))
@@ -493,15 +493,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_ps(KinDev kin, StepArgs a) {
         }
         shat_a[ev] = shat;
         tries_a[ev] = att + 1;
-      } else if (att + 1 >= kin.max_attempts) {
+      } else {
+        // exhausted: the final zero weight; otherwise placeholders that the redraw overwrites
+        const bool last = att + 1 >= kin.max_attempts;
         wps_a[ev] = 0.0;
         shat_a[ev] = 1.0;
-        tries_a[ev] = att + 1;
-        atomicOr(status, 1);
-      } else {
-        const int pos = atomicAdd(&s_tail, 1);
-        s_ev[pos & (QCAP - 1)] = ev;
-        s_att[pos & (QCAP - 1)] = att + 1;
+        tries_a[ev] = last ? att + 1 : 0;
+        if (last) {
+          atomicOr(status, 1);
+        } else {
+          const int pos = atomicAdd(&s_tail, 1);
+          s_ev[pos & (QCAP - 1)] = ev;
+          s_att[pos & (QCAP - 1)] = att + 1;
+        }
       }
     }
     __syncthreads();

@@ -121,6 +121,28 @@ def test_memory_budget_and_refusal(B):
         B.me_server_destroy(s)
 
 
+def test_waiting_request_is_not_refused_while_results_are_uncollected(B):
+    """Requests that wait for budget held by finished but uncollected requests are admitted once
+    their clients collect them, not refused: the client collects nothing until everything that fits
+    has finished, then waits for every ticket in order."""
+    import time
+    cap = 1 << 30
+    s = B.me_server_create(mem_cap_bytes=cap, n_slots=2)
+    try:
+        key = "uux_epem"
+        proc = WORKLOADS[key]["process"]
+        B.me_server_warm(s, proc, B.ME_MIXED, kin(B, key))
+        n = 1 << 21
+        ts = [B.me_server_submit(s, proc, B.ME_MIXED, i, 0, n, kin(B, key), want_me2=True, want_momenta=True)
+              for i in range(6)]
+        time.sleep(2.0)  # the admitted requests finish; the rest wait for their budget
+        for t in ts:
+            assert B.me_server_wait(s, t, 300.0).status == 0
+        assert B.me_server_get_stats(s).bytes_peak <= cap
+    finally:
+        B.me_server_destroy(s)
+
+
 def test_fp64_requests_and_momenta(B):
     import torch
     s = B.me_server_create(n_slots=2)
