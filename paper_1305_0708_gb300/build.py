@@ -118,7 +118,10 @@ def generate_units():
     for name, aliases in PROCESSES:
         tag = process_symbol(name)
         prog = compile_process(name)
-        src, info = generate_source(prog, tag, hel_loop=_hel_loop_choice(prog))
+        # ME_INTERLEAVE=1 emits the straight-line programs in the helicity loop's order (each
+        # amplitude after its new sub-currents), to compare the two orders on the same processes
+        src, info = generate_source(prog, tag, hel_loop=_hel_loop_choice(prog),
+                                    interleave=os.environ.get("ME_INTERLEAVE") == "1")
         path = os.path.join(GEN, tag + ".cu")
         if not os.path.exists(path) or open(path).read() != src:
             with open(path, "w") as f:

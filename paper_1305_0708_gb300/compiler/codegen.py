@@ -76,10 +76,11 @@ def _lit(x):
 
 
 class _Emitter:
-    def __init__(self, prog, tag, mode="fp64", hel_loop=False):
+    def __init__(self, prog, tag, mode="fp64", hel_loop=False, interleave=False):
         self.p = prog
         self.tag = tag
         self.hel_loop = hel_loop  # one copy of the program in a loop over the live helicities
+        self.interleave = interleave  # straight-line form: each amplitude right after its new sub-currents
         self.mode = mode          # "fp64": FP64 momenta and amplitudes; "mixed": double-float momenta, FP32
         self.lines = []
         self.flops32 = 0      # amplitude-precision flops per event
@@ -242,13 +243,21 @@ class _Emitter:
         E("  // into colour components, then its colour sum (J^T C J)/den; helicity sum, average")
         E("  R tot = R(0);")
         for hi, terms in enumerate(p.amp_terms):
-            for aid, chvars in terms:
-                for c, cv in zip(p.amps[aid].children, chvars):
-                    need(c, cv)
-            for k in range(K):
-                E(f"  me::cx<R> J{hi}_{k} = me::mk(R(0), R(0));")
-            for aid, chvars in terms:
-                self.amp_code(aid, chvars, hi)
+            if self.interleave:
+                for k in range(K):
+                    E(f"  me::cx<R> J{hi}_{k} = me::mk(R(0), R(0));")
+                for aid, chvars in terms:
+                    for c, cv in zip(p.amps[aid].children, chvars):
+                        need(c, cv)
+                    self.amp_code(aid, chvars, hi)
+            else:
+                for aid, chvars in terms:
+                    for c, cv in zip(p.amps[aid].children, chvars):
+                        need(c, cv)
+                for k in range(K):
+                    E(f"  me::cx<R> J{hi}_{k} = me::mk(R(0), R(0));")
+                for aid, chvars in terms:
+                    self.amp_code(aid, chvars, hi)
             E("  {")
             E("    R s = R(0);")
             for k in range(K):
@@ -322,12 +331,13 @@ class _Emitter:
                 return tuple(fixed.get(l, "r") for l in sorted(p.nodes[nid].legs))
             aids = sorted({aid for hi in idxs for aid, _ in p.amp_terms[hi]})
             g0 = self.flops32
+            for k in range(p.n_colour):
+                E(f"  me::cx<R> J_{k} = me::mk(R(0), R(0));")
+            # each amplitude right after the sub-currents it needs first: a sub-current lives from
+            # its first to its last use instead of across the whole body
             for aid in aids:
                 for c in p.amps[aid].children:
                     need(c, var_of(c))
-            for k in range(p.n_colour):
-                E(f"  me::cx<R> J_{k} = me::mk(R(0), R(0));")
-            for aid in aids:
                 self.amp_code(aid, [var_of(c) for c in p.amps[aid].children], "")
             self._colour_sum("")
             E("  }")
@@ -641,7 +651,7 @@ def process_symbol(name):
     return "p_" + "".join(out).strip("_")
 
 
-def generate_source(prog, tag, hel_loop=None):
+def generate_source(prog, tag, hel_loop=None, interleave=False):
     """CUDA source for one process: the FP64 and mixed evaluators in a traits struct.
 
     hel_loop: True for the helicity-loop form, False for the straight-line form, None to take the
@@ -650,9 +660,9 @@ def generate_source(prog, tag, hel_loop=None):
         probe = _Emitter(prog, tag, "mixed")
         probe.generate()
         hel_loop = probe.flops32 > HEL_LOOP_FLOPS
-    em64 = _Emitter(prog, tag, "fp64", hel_loop)
+    em64 = _Emitter(prog, tag, "fp64", hel_loop, interleave)
     em64.generate()
-    emmx = _Emitter(prog, tag, "mixed", hel_loop)
+    emmx = _Emitter(prog, tag, "mixed", hel_loop, interleave)
     emmx.generate()
     hel_fn = ""
     if hel_loop:
