@@ -59,6 +59,9 @@ Functions and their pins (tests/test_oracle_processes.py):
   us_dchgg        u s > d c h g g (WBF H plus two jets, 24 diagrams) on the two-line code (us_dch_ng),
                    which equals us_dch and us_dchg at 0 and 1 gluons; Ward identity for each gluon (fails
                    without the pair lines), Bose symmetry, boosts (tests/test_oracle_line.py)
+  udx_wphgg       u d~ > w+ h g g (H V plus two jets, 8 diagrams) on the one-fermion-line engine (a W* > W+ H
+                   insertion), which equals udx_wph and udx_wphg with no and one gluon; Ward identity for
+                   each gluon, Bose symmetry, boosts (tests/test_oracle_line.py)
   uux_zzgg        u u~ > z z g g (V V plus two jets, 30 diagrams) on the one-fermion-line engine, which
                    equals uux_zz and uux_zzg with no and one gluon; Ward identity for each gluon, Bose
                    symmetry of the gluons and of the Z bosons, boosts (tests/test_oracle_line.py)
@@ -1439,7 +1442,9 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
     col: (leg, "u") an incoming quark or (leg, "v") an outgoing antiquark, where the fermion-number
     arrow starts; row: (leg, "ubar") an outgoing quark or (leg, "vbar") an incoming antiquark, where it
     ends.  colourless: outgoing bosons as dicts (leg, kind "V" with gl, gr, mass: i gamma^mu (gl P_L +
-    gr P_R); kind "S" with y: i y).  gluons: (leg, incoming) pairs.  Internal fermions carry mass mf
+    gr P_R); kind "S" with y: i y; kind "VS" with legs (vector, scalar), gl, gr, mass, width, gvvs: an
+    off-shell vector of that mass and width from the line into the external vector and scalar through
+    the i gvvs g^{mu nu} vertex).  gluons: (leg, incoming) pairs.  Internal fermions carry mass mf
     and width wf.  eps_override: {leg: vector[N,4]} replaces a gluon's polarisation."""
     ng = len(gluons)
     key = ("line", ng, len(colourless))
@@ -1465,13 +1470,20 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
     gs = par.gs
     kg = {j: (p[l] if inc else -p[l]) for j, (l, inc) in enumerate(gluons)}
     p_start = p[col[0]] if col[1] == "u" else -p[col[0]]
-    hels = [HEL_F, HEL_F] + [HEL_W if c["kind"] == "V" else (0,) for c in colourless] + [HEL_V] * ng
+    hels = [HEL_F, HEL_F] + [(0,) if c["kind"] == "S" else HEL_W for c in colourless] + [HEL_V] * ng
     tot = 0.0
     for h in itertools.product(*hels):
         cs = u_spinor(p[col[0]], h[0]) if col[1] == "u" else v_spinor(p[col[0]], h[0])
         rs = bar(u_spinor(p[row[0]], h[1]) if row[1] == "ubar" else v_spinor(p[row[0]], h[1]))
         cins = []
         for c, hc in zip(colourless, h[2:2 + len(colourless)]):
+            if c["kind"] == "VS":
+                # an off-shell V* from the line into the external V and scalar through the V V S vertex
+                pv, pss = p[c["legs"][0]], p[c["legs"][1]]
+                X = vector_prop(pv + pss, 1j * c["gvvs"] * polarisation(pv, hc, mass=c["mass"]).conj(), c["mass"],
+                                c["width"])
+                cins.append((vector_insertion(X, c["gl"], c["gr"]), pv + pss))
+                continue
             pc = p[c["leg"]]
             if c["kind"] == "V":
                 cins.append((vector_insertion(polarisation(pc, hc, mass=c["mass"]).conj(), c["gl"], c["gr"]), pc))
@@ -1631,6 +1643,14 @@ def uux_zzgg(P, par=SMParams(), eps_override=None):
     z = [dict(leg=k, kind="V", gl=gl, gr=gr, mass=par.mZ) for k in (2, 3)]
     return fermion_line_process(P, par, (0, "u"), (1, "vbar"), z, [(4, False), (5, False)], 0.0, 0.0, 1.0 / 36.0,
                                 eps_override)
+
+
+def udx_wphgg(P, par=SMParams(), eps_override=None):
+    """u(p0) d~(p1) > W+(p2) H(p3) g(p4) g(p5) (H V plus two jets, 8 diagrams): the quark line from u(p0)
+    to vbar(p1) with the W* > W+ H insertion and the gluons (fermion_line_process)."""
+    wh = dict(kind="VS", legs=(2, 3), gl=par.g / np.sqrt(2.0), gr=0.0, mass=par.mW, width=par.wW, gvvs=par.gwwh)
+    return fermion_line_process(P, par, (0, "u"), (1, "vbar"), [wh], [(4, False), (5, False)], 0.0, 0.0,
+                                1.0 / 36.0, eps_override)
 
 
 def gg_ttxhg(P, par=SMParams(), eps_override=None, widths=True):
@@ -2031,6 +2051,7 @@ PROCESSES = {
     "g g > t t~ h g": gg_ttxhg,
     "u s > d c h g g": us_dchgg,
     "u u~ > z z g g": uux_zzgg,
+    "u d~ > w+ h g g": udx_wphgg,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,

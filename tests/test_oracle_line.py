@@ -12,6 +12,9 @@ it, g g > t t~ H g (H t t~ plus one jet, the paper's Sect. 2 Htt~ + jets family)
 - V V plus jets (u u~ > Z Z g g) on the same engine: equal to u u~ > Z Z (closed form) and u u~ > Z Z g
   with no and one gluon; Ward identity of each gluon, Bose symmetry of the gluons and of the Z bosons,
   boosts.
+- H V plus jets (u d~ > W+ H g g, the W* > W+ H insertion) on the same engine: equal to u d~ > W+ H
+  (closed form) and u d~ > W+ H g with no and one gluon; Ward identity of each gluon, Bose symmetry,
+  boosts.
 - WBF H plus jets on two quark lines (us_dch_ng, u s > d c H + n gluons): equal to u s > d c H and
   u s > d c H g at n = 0, 1; at n = 2 the Ward identity of each gluon (fails without the three-gluon
   pair lines), Bose symmetry, boosts.
@@ -129,3 +132,31 @@ def test_zzgg_ward_bose_and_boosts():
     assert np.allclose(pr.uux_zzgg(P[:, [0, 1, 3, 2, 4, 5]], PAR), ref, rtol=1e-12)
     from test_oracle_processes import random_lorentz
     assert np.allclose(pr.uux_zzgg(random_lorentz(P, 953), PAR), ref, rtol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# H V plus jets on the one-line engine: u d~ > W+ H g g (a W* > W+ H insertion)
+# ---------------------------------------------------------------------------
+def _wh(par):
+    return dict(kind="VS", legs=(2, 3), gl=par.g / np.sqrt(2.0), gr=0.0, mass=par.mW, width=par.wW, gvvs=par.gwwh)
+
+
+def test_wh_plus_jets_engine_equals_the_zero_and_one_gluon_oracles():
+    P = _massive_points(500.0, (PAR.mW, PAR.mH), 6, seed=960)
+    got = pr.fermion_line_process(P, PAR, (0, "u"), (1, "vbar"), [_wh(PAR)], [], 0.0, 0.0, 1.0 / 36.0)
+    assert np.allclose(got, pr.udx_wph(P, PAR), rtol=1e-12, atol=0)
+    P = _massive_points(600.0, (PAR.mW, PAR.mH, 0.0), 6, seed=961)
+    got = pr.fermion_line_process(P, PAR, (0, "u"), (1, "vbar"), [_wh(PAR)], [(4, False)], 0.0, 0.0, 1.0 / 36.0)
+    assert np.allclose(got, pr.udx_wphg(P, PAR), rtol=1e-12, atol=0)
+
+
+def test_whgg_ward_bose_and_boosts():
+    P = _massive_points(700.0, (PAR.mW, PAR.mH, 0.0, 0.0), 5, seed=962)
+    ref = pr.udx_wphgg(P, PAR)
+    assert np.all(ref > 0) and np.all(np.isfinite(ref))
+    for leg in (4, 5):
+        bad = pr.udx_wphgg(P, PAR, eps_override={leg: P[:, leg]})
+        assert np.all(np.abs(bad) < 1e-24 * ref * P[:, leg, 0] ** 2)
+    assert np.allclose(pr.udx_wphgg(P[:, [0, 1, 2, 3, 5, 4]], PAR), ref, rtol=1e-12)
+    from test_oracle_processes import random_lorentz
+    assert np.allclose(pr.udx_wphgg(random_lorentz(P, 963), PAR), ref, rtol=1e-10)
