@@ -69,6 +69,7 @@ PROCESSES = [
     ("g g > t t~ h g", []),
     ("u s > d c h g g", []),
     ("u u~ > z z g g", []),
+    ("u d~ > w+ h g g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

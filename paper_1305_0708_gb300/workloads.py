@@ -224,6 +224,11 @@ VARIANTS = {
         seed=52, cuts=dict(legs=(4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.25,
         describe="u u~ > Z Z g g (V V plus two jets, 30 diagrams, helicity-loop program), massive RAMBO at "
                  "sqrt(s)=600 GeV, gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^18 accepted points, seed 52"),
+    "udx_wphgg": dict(
+        process="u d~ > w+ h g g", kind="rambo", sqrt_s=700.0, masses=(0, 0, 80.4, 125.0, 0, 0), n=1 << 20,
+        seed=53, cuts=dict(legs=(4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,
+        describe="u d~ > W+ H g g (H V plus two jets, 8 diagrams), massive RAMBO at sqrt(s)=700 GeV, gluons "
+                 "pT>20, |eta|<2.5, DeltaR>0.4, 2^20 accepted points, seed 53"),
     "uux_zggg": dict(
         process="u u~ > z g g g", kind="rambo", sqrt_s=800.0, masses=(0, 0, 91.1876, 0, 0, 0), n=1 << 18,
         seed=49, cuts=dict(legs=(3, 4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=1.0 / 6.0,
