@@ -61,6 +61,7 @@ def test_issue_roofline_arithmetic():
     import bench
     r = bench.issue_roofline("udx_epvegg", "k_ps", 0.222, 2 ** 20)
     assert r["peak"] == pytest.approx(152 * 4 * 2.07)
-    assert r["achieved"] == pytest.approx(175110311.0 / 0.222e-3 / 1e9)
+    per_point = bench.WARP_INSTRUCTIONS_PER_POINT[("udx_epvegg", "k_ps")]
+    assert r["achieved"] == pytest.approx(per_point * 2 ** 20 / 0.222e-3 / 1e9)
     assert 0.5 < r["frac"] < 0.8
     assert bench.issue_roofline("uux_epem", "k_ps", 0.1, 65536) is None
