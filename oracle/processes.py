@@ -94,7 +94,9 @@ Functions and their pins (tests/test_oracle_processes.py):
   udx_epveg       u d~ > e+ ve g : Ward identity; soft-gluon limit against C_F times
                    the eikonal factor times u d~ > e+ ve (closed form); boosts
   gluons          g g > g...g    : Berends-Giele, pinned by the gg > gg closed
-                   form, Parke-Taylor MHV amplitudes, Ward, Bose, boosts
+                   form, Parke-Taylor MHV amplitudes, the soft-gluon limit of every
+                   NMHV six-gluon partial amplitude onto the Parke-Taylor-pinned
+                   five-gluon ones, Ward, Bose, boosts
 """
 import itertools
 import numpy as np

@@ -982,3 +982,51 @@ def test_uux_va_closed_form(which):
     assert np.allclose(fn(P, PAR), want, rtol=1e-12, atol=0)
     if which == "aa":
         assert np.allclose(want, (2.0 / 3.0) * qa ** 4 * (t / u + u / t), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# NMHV six-gluon amplitudes: the soft-gluon limit of every colour-ordered amplitude
+# ---------------------------------------------------------------------------
+def test_nmhv_six_gluon_soft_limit():
+    """A colour-ordered amplitude with a soft positive-helicity gluon s between its neighbours a and b
+    tends to g <a b> / (<a s> <s b>) times the amplitude without s (the universal soft factor in the
+    normalisation of the Parke-Taylor pin above), with a deviation that falls in proportion to the
+    soft energy.  With three negative helicities among the six, every one of the 120 orderings of
+    this NMHV helicity reduces to a five-gluon anti-MHV amplitude, itself pinned by Parke-Taylor."""
+    from test_oracle_chains import _add_soft_massive
+    from oracle.lorentz import polarisation
+    g = PAR.gs
+    base = rambo_points(1500.0, 3, 6, seed=31)
+    out_hel = [-1, -1, 1, -1, 1]                    # five hard gluons (outgoing convention)
+
+    def amps(P, hels):
+        n = P.shape[1]
+        K = np.stack([-P[:, 0], -P[:, 1]] + [P[:, k] for k in range(2, n)], axis=0)
+        phys = [(-h if k < 2 else h) for k, h in enumerate(hels)]
+        E = []
+        for k in range(n):
+            eps = polarisation(P[:, k], phys[k])
+            E.append(eps if k < 2 else eps.conj())
+        orders, A = pr.gluon_partial_amplitudes(K, np.stack(E), g)
+        return K, orders, A
+
+    _, orders5, A5 = amps(base, out_hel)
+    index5 = {o: i for i, o in enumerate(orders5)}
+    nhat = np.array([0.36, -0.48, 0.8])
+    devs = []
+    for lam in (1e-4, 1e-5):
+        w = lam * 1500.0
+        k = np.concatenate([[w], w * nhat])[None, :].repeat(len(base), 0)
+        P6 = _add_soft_massive(base, k, (0.0, 0.0, 0.0))
+        K6, orders6, A6 = amps(P6, out_hel + [1])
+        ang = _angle_products(K6)
+        dev = 0.0
+        for i6, o in enumerate(orders6):
+            pos = o.index(5)
+            a, b = o[pos - 1], o[(pos + 1) % 6]
+            o5 = tuple(x for x in o if x != 5)
+            soft = g * np.abs(ang[a, b] / (ang[a, 5] * ang[5, b]))
+            want = soft * np.abs(A5[index5[o5]])
+            dev = max(dev, float(np.max(np.abs(np.abs(A6[i6]) / want - 1))))
+        devs.append(dev)
+    assert devs[1] < 1e-3 and devs[1] < devs[0] / 5, devs
