@@ -91,6 +91,12 @@ Functions and their pins (tests/test_oracle_processes.py):
                    against u s > d c h (h) with the outgoing quarks exchanged; with the complex-mass
                    card the HHH processes keep the zero-width high-energy behaviour that the
                    fixed-width card loses; Higgs permutations, boosts (tests/test_oracle_wbf.py)
+  uu_uuh_n, uu_uuhh, uu_uuhhh  u u > u u + 1, 2, 3 Higgs (Z Z fusion with the outgoing quarks
+                   exchanged): u u > u u h against its closed form (the chiral Fierz identity turns the
+                   exchanged left-handed spinor product into minus the direct one, so the exchange sign
+                   makes the two channels interfere constructively); the core as for u d > u d + Higgs;
+                   Fermi symmetry of the outgoing quarks, Higgs permutations, boosts
+                   (tests/test_oracle_wbf.py)
   udx_epveg       u d~ > e+ ve g : Ward identity; soft-gluon limit against C_F times
                    the eikonal factor times u d~ > e+ ve (closed form); boosts
   gluons          g g > g...g    : Berends-Giele, pinned by the gg > gg closed
@@ -952,6 +958,40 @@ def ud_udh_n(P, par=SMParams(), bosons=("w", "z")):
             tt.append(tens["w"])
         tot = tot + colour.colour_sum(amps, tt)
     return tot / 36.0
+
+
+def uu_uuh_n(P, par=SMParams()):
+    """u(p0) u(p1) > u(p2) u(p3) + n Higgs bosons (p4...) by Z Z fusion, the paper's Sect. 2.10 u u > H H (H)
+    u u family: the lines u0 > u2, u1 > u3 (colour delta_{i2 i0} delta_{i3 i1}) and, with the identical
+    outgoing quarks exchanged and a relative minus sign, u0 > u3, u1 > u2 (delta_{i3 i0} delta_{i2 i1});
+    each pair of Z currents, through its t-channel propagators, feeds the Z Z > n H core (vv_higgs).
+    No W fusion: u > d W+ on both lines would leave d d."""
+    p = [P[:, k] for k in range(P.shape[1])]
+    zu = _z_couplings("u", par)
+    cz = wbf_couplings(par, "z")
+    d = _DELTA3
+    tens = [np.einsum("ca,db->abcd", d, d), np.einsum("da,cb->abcd", d, d)]
+    tot = 0.0
+    for h in itertools.product(HEL_F, repeat=4):
+        u0, u1 = u_spinor(p[0], h[0]), u_spinor(p[1], h[1])
+        ub2, ub3 = bar(u_spinor(p[2], h[2])), bar(u_spinor(p[3], h[3]))
+        amps = []
+        for sign, (ra, rb) in ((1.0, (ub2, ub3)), (-1.0, (ub3, ub2))):
+            pa, pb = (p[2], p[3]) if sign > 0 else (p[3], p[2])
+            q1, q2 = p[0] - pa, p[1] - pb
+            Z1 = vector_prop(q1, ffv_current(ra, u0, *zu), par.mZ, par.wZ)
+            Z2 = vector_prop(q2, ffv_current(rb, u1, *zu), par.mZ, par.wZ)
+            amps.append(sign * vv_higgs(Z1, q1, Z2, q2, p[4:], cz) / 1j)
+        tot = tot + colour.colour_sum(amps, tens)
+    return tot / 36.0
+
+
+def uu_uuhh(P, par=SMParams()):
+    return uu_uuh_n(P, par)
+
+
+def uu_uuhhh(P, par=SMParams()):
+    return uu_uuh_n(P, par)
 
 
 def ud_udh(P, par=SMParams()):
@@ -2048,6 +2088,9 @@ PROCESSES = {
     "u d > u d h": ud_udh,
     "u d > u d h h": ud_udhh,
     "u d > u d h h h": ud_udhhh,
+    "u u > u u h": uu_uuh_n,
+    "u u > u u h h": uu_uuhh,
+    "u u > u u h h h": uu_uuhhh,
     "u d~ > w+ g g g": udx_wpggg,
     "u u~ > z g g g": uux_zggg,
     "g g > t t~ h g": gg_ttxhg,

@@ -263,3 +263,40 @@ def test_complex_mass_restores_the_high_energy_behaviour(fn, monkeypatch):
     monkeypatch.setattr(SMParams, "gwwh", property(lambda self: self.g * self.mW))
     monkeypatch.setattr(SMParams, "gzzh", property(lambda self: self.gz * self.mZ))
     assert np.all(fn(P32, cms) > 10 * z32)
+
+
+# ---------------------------------------------------------------------------
+# u u > u u + Higgs bosons: Z Z fusion with the outgoing quarks exchanged
+# ---------------------------------------------------------------------------
+def test_uu_uuh_closed_form():
+    """Per helicity the amplitude is g_ZZH g^{h0} g^{h1} times a spinor product over the Z
+    denominators.  Same-chirality lines: both pairings contribute, and by the chiral Fierz identity
+    the exchanged product is minus the direct one, so with the exchange sign
+      16 (p0.p1)(p2.p3) (g_L^4 + g_R^4) |g_ZZH|^2 (9/|Dt|^2 + 9/|Du|^2 + 6 Re 1/(Dt Du*));
+    opposite chiralities: only the pairing that keeps each line's helicity,
+      16 (p0.p3)(p1.p2) 9 |g_ZZH g_L g_R / Dt|^2 x 2 and 16 (p0.p2)(p1.p3) 9 |g_ZZH g_L g_R / Du|^2 x 2,
+    Dt = D_Z(p0 - p2) D_Z(p1 - p3), Du = D_Z(p0 - p3) D_Z(p1 - p2); averaged by 1/36."""
+    for par in (PAR, PAR.with_cms()):
+        P = _points(1000.0, 1, 40, seed=470)
+        p = [P[:, k] for k in range(5)]
+        d = lambda a, b: mdot(p[a], p[b])
+        gL, gR = pr._z_couplings("u", par)
+        Dt = den(mdot(p[0] - p[2], p[0] - p[2]), par.mZ, par.wZ) * den(mdot(p[1] - p[3], p[1] - p[3]), par.mZ, par.wZ)
+        Du = den(mdot(p[0] - p[3], p[0] - p[3]), par.mZ, par.wZ) * den(mdot(p[1] - p[2], p[1] - p[2]), par.mZ, par.wZ)
+        g2 = abs(par.gzzh) ** 2
+        same = 16 * d(0, 1) * d(2, 3) * (gL ** 4 + gR ** 4) * g2 * (
+            9 / np.abs(Dt) ** 2 + 9 / np.abs(Du) ** 2 + 6 * np.real(1 / (Dt * np.conj(Du))))
+        opp = 2 * 9 * g2 * gL ** 2 * gR ** 2 * (16 * d(0, 3) * d(1, 2) / np.abs(Dt) ** 2
+                                                   + 16 * d(0, 2) * d(1, 3) / np.abs(Du) ** 2)
+        assert np.allclose(pr.uu_uuh_n(P, par), (same + opp) / 36.0, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("nh", [2, 3])
+def test_uu_uu_higgs_fermi_symmetry_permutations_and_boosts(nh):
+    P = _points(1500.0, nh, 5, seed=480 + nh)
+    ref = pr.uu_uuh_n(P)
+    assert np.all(ref > 0) and np.all(np.isfinite(ref))
+    assert np.allclose(pr.uu_uuh_n(P[:, [0, 1, 3, 2] + list(range(4, 4 + nh))]), ref, rtol=1e-12)
+    assert np.allclose(pr.uu_uuh_n(P[:, [1, 0, 2, 3] + list(range(4, 4 + nh))]), ref, rtol=1e-12)
+    assert np.allclose(pr.uu_uuh_n(P[:, [0, 1, 2, 3] + list(range(4, 4 + nh))[::-1]]), ref, rtol=1e-11)
+    assert np.allclose(pr.uu_uuh_n(boost(P, np.array([0.2, 0.4, -0.5]))), ref, rtol=1e-9)
