@@ -70,6 +70,8 @@ PROCESSES = [
     ("u s > d c h g g", []),
     ("u u~ > z z g g", []),
     ("u d~ > w+ h g g", []),
+    ("u u > u u h h", []),
+    ("u u > u u h h h", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

@@ -224,6 +224,16 @@ VARIANTS = {
         seed=52, cuts=dict(legs=(4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.25,
         describe="u u~ > Z Z g g (V V plus two jets, 30 diagrams, helicity-loop program), massive RAMBO at "
                  "sqrt(s)=600 GeV, gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^18 accepted points, seed 52"),
+    "uu_uuhh": dict(
+        process="u u > u u h h", kind="rambo", sqrt_s=1000.0, masses=(0, 0, 0, 0, 125.0, 125.0), n=1 << 20,
+        seed=54, cuts=None, s_ident=0.25,
+        describe="u u > u u H H (Z Z fusion, identical quarks), massive RAMBO at sqrt(s)=1 TeV, 2^20 points, "
+                 "seed 54"),
+    "uu_uuhhh": dict(
+        process="u u > u u h h h", kind="rambo", sqrt_s=1500.0, masses=(0, 0, 0, 0, 125.0, 125.0, 125.0),
+        n=1 << 20, seed=55, cuts=None, s_ident=1.0 / 12.0,
+        describe="u u > u u H H H (the paper's Sect. 2.10 process: Z Z fusion, identical quarks, 50 diagrams), "
+                 "massive RAMBO at sqrt(s)=1.5 TeV, 2^20 points, seed 55"),
     "udx_wphgg": dict(
         process="u d~ > w+ h g g", kind="rambo", sqrt_s=700.0, masses=(0, 0, 80.4, 125.0, 0, 0), n=1 << 20,
         seed=53, cuts=dict(legs=(4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,

@@ -73,6 +73,8 @@ CASES = {
     "u s > d c h g g": (opr.us_dchgg, 1000.0, (0.0, 0.0, 125.0, 0.0, 0.0), (2, 3, 5, 6)),
     "u u~ > z z g g": (opr.uux_zzgg, 600.0, (91.1876, 91.1876, 0.0, 0.0), (4, 5)),
     "u d~ > w+ h g g": (opr.udx_wphgg, 700.0, (80.4, 125.0, 0.0, 0.0), (4, 5)),
+    "u u > u u h h": (opr.uu_uuhh, 1000.0, (0.0, 0.0, 125.0, 125.0), ()),
+    "u u > u u h h h": (opr.uu_uuhhh, 1500.0, (0.0, 0.0, 125.0, 125.0, 125.0), ()),
 }
 
 # the complex-mass option (Sect. 7.11): processes whose couplings it makes complex
