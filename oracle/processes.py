@@ -59,6 +59,10 @@ Functions and their pins (tests/test_oracle_processes.py):
   us_dchgg        u s > d c h g g (WBF H plus two jets, 24 diagrams) on the two-line code (us_dch_ng),
                    which equals us_dch and us_dchg at 0 and 1 gluons; Ward identity for each gluon (fails
                    without the pair lines), Bose symmetry, boosts (tests/test_oracle_line.py)
+  uux_wpwmgg      u u~ > w+ w- g g (W+ W- plus two jets, 31 diagrams) on the one-fermion-line engine (the
+                   t-channel W pair in its fixed order, or an s-channel photon or Z into the W W V vertex),
+                   which equals uux_wpwm and uux_wpwmg with no and one gluon; Ward identity for each
+                   gluon, Bose symmetry, boosts (tests/test_oracle_line.py)
   udx_wphgg       u d~ > w+ h g g (H V plus two jets, 8 diagrams) on the one-fermion-line engine (a W* > W+ H
                    insertion), which equals udx_wph and udx_wphg with no and one gluon; Ward identity for
                    each gluon, Bose symmetry, boosts (tests/test_oracle_line.py)
@@ -1475,7 +1479,7 @@ def qqx_v_ng(P, par, gl, gr, mV, eps_override=None):
 
 
 def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, average=1.0 / 36.0,
-                         eps_override=None):
+                         eps_override=None, alternatives=None, keep_order=False):
     """|M|^2 of a process with one fermion line, colourless bosons attached to it and any number (up
     to three) of incoming or outgoing gluons, from every Feynman diagram: the orderings along the line
     of the colourless insertions and of the gluons joined into lines (_gluon_blocks), colour summed
@@ -1486,18 +1490,29 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
     ends.  colourless: outgoing bosons as dicts (leg, kind "V" with gl, gr, mass: i gamma^mu (gl P_L +
     gr P_R); kind "S" with y: i y; kind "VS" with legs (vector, scalar), gl, gr, mass, width, gvvs: an
     off-shell vector of that mass and width from the line into the external vector and scalar through
-    the i gvvs g^{mu nu} vertex).  gluons: (leg, incoming) pairs.  Internal fermions carry mass mf
-    and width wf.  eps_override: {leg: vector[N,4]} replaces a gluon's polarisation."""
+    the i gvvs g^{mu nu} vertex; kind "VV" with legs (V2, V1), gl, gr, mass, width, gv, vmass: an
+    off-shell vector from the line into two external vectors of mass vmass through the three-vector
+    vertex -i gv [...] with (V1, V2, V) = (legs[1], legs[0], line), the W W gamma / W W Z rule of Sect.
+    4.2).  alternatives: several such lists whose diagrams add coherently (for instance t-channel W
+    emissions and an s-channel photon or Z); keep_order: an alternative's insertions stay in their
+    listed order along the line (the t-channel quark between two W emissions fixes it).  gluons:
+    (leg, incoming) pairs.  Internal fermions carry mass mf and width wf.  eps_override: {leg:
+    vector[N,4]} replaces a gluon's polarisation."""
+    confs = alternatives if alternatives is not None else [colourless]
     ng = len(gluons)
-    key = ("line", ng, len(colourless))
+    key = ("line", ng, tuple(len(c) for c in confs), keep_order)
     if key not in _VJETS:
         diags = []
-        for part in _set_partitions(list(range(ng))):
-            for choice in itertools.product(*[_gluon_blocks(b) for b in part]):
-                for order in itertools.permutations([("c", i) for i in range(len(colourless))] + list(choice)):
-                    diags.append(order)
+        for ci, conf in enumerate(confs):
+            for part in _set_partitions(list(range(ng))):
+                for choice in itertools.product(*[_gluon_blocks(b) for b in part]):
+                    for order in itertools.permutations([("c", i) for i in range(len(conf))] + list(choice)):
+                        seq = [x[1] for x in order if x[0] == "c"]
+                        if keep_order and seq != sorted(seq):
+                            continue
+                        diags.append((ci, order))
         tensors = []
-        for order in diags:
+        for _, order in diags:
             t = np.zeros((3, 3) + (8,) * ng, dtype=complex)
             for a in itertools.product(range(8), repeat=ng):
                 M = np.eye(3, dtype=complex)
@@ -1512,31 +1527,53 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
     gs = par.gs
     kg = {j: (p[l] if inc else -p[l]) for j, (l, inc) in enumerate(gluons)}
     p_start = p[col[0]] if col[1] == "u" else -p[col[0]]
-    hels = [HEL_F, HEL_F] + [(0,) if c["kind"] == "S" else HEL_W for c in colourless] + [HEL_V] * ng
+    # external colourless legs: (leg, mass) of vectors, scalars; helicities per leg, shared by the
+    # alternatives
+    vlegs = {}
+    for conf in confs:
+        for c in conf:
+            if c["kind"] == "V":
+                vlegs[c["leg"]] = c["mass"]
+            elif c["kind"] == "VS":
+                vlegs[c["legs"][0]] = c["mass"]
+            elif c["kind"] == "VV":
+                vlegs[c["legs"][0]] = c["vmass"]
+                vlegs[c["legs"][1]] = c["vmass"]
+    vl = sorted(vlegs)
+    hels = [HEL_F, HEL_F] + [HEL_W] * len(vl) + [HEL_V] * ng
     tot = 0.0
     for h in itertools.product(*hels):
         cs = u_spinor(p[col[0]], h[0]) if col[1] == "u" else v_spinor(p[col[0]], h[0])
         rs = bar(u_spinor(p[row[0]], h[1]) if row[1] == "ubar" else v_spinor(p[row[0]], h[1]))
+        pol = {l: polarisation(p[l], hv, mass=vlegs[l]).conj() for l, hv in zip(vl, h[2:2 + len(vl)])}
         cins = []
-        for c, hc in zip(colourless, h[2:2 + len(colourless)]):
-            if c["kind"] == "VS":
-                # an off-shell V* from the line into the external V and scalar through the V V S vertex
-                pv, pss = p[c["legs"][0]], p[c["legs"][1]]
-                X = vector_prop(pv + pss, 1j * c["gvvs"] * polarisation(pv, hc, mass=c["mass"]).conj(), c["mass"],
-                                c["width"])
-                cins.append((vector_insertion(X, c["gl"], c["gr"]), pv + pss))
-                continue
-            pc = p[c["leg"]]
-            if c["kind"] == "V":
-                cins.append((vector_insertion(polarisation(pc, hc, mass=c["mass"]).conj(), c["gl"], c["gr"]), pc))
-            else:
-                cins.append((np.broadcast_to(1j * c["y"] * np.eye(4, dtype=complex), (P.shape[0], 4, 4)), pc))
+        for conf in confs:
+            ci_list = []
+            for c in conf:
+                if c["kind"] == "VS":
+                    # an off-shell V* from the line into the external V and scalar through V V S
+                    pv, pss = p[c["legs"][0]], p[c["legs"][1]]
+                    X = vector_prop(pv + pss, 1j * c["gvvs"] * pol[c["legs"][0]], c["mass"], c["width"])
+                    ci_list.append((vector_insertion(X, c["gl"], c["gr"]), pv + pss))
+                elif c["kind"] == "VV":
+                    # an off-shell V* from the line into two external vectors through V V V
+                    l2, l1 = c["legs"]
+                    Q = p[l2] + p[l1]
+                    X = vvv_out(pol[l1], -p[l1], pol[l2], -p[l2], Q, 1.0)
+                    Y = vector_prop(Q, -1j * c["gv"] * X, c["mass"], c["width"])
+                    ci_list.append((vector_insertion(Y, c["gl"], c["gr"]), Q))
+                elif c["kind"] == "V":
+                    ci_list.append((vector_insertion(pol[c["leg"]], c["gl"], c["gr"]), p[c["leg"]]))
+                else:
+                    ci_list.append((np.broadcast_to(1j * c["y"] * np.eye(4, dtype=complex), (P.shape[0], 4, 4)),
+                                    p[c["leg"]]))
+            cins.append(ci_list)
         eps = {}
-        for j, ((l, inc), hg) in enumerate(zip(gluons, h[2 + len(colourless):])):
+        for j_, ((l, inc), hg) in enumerate(zip(gluons, h[2 + len(vl):])):
             e = polarisation(p[l], hg)
-            eps[j] = e if inc else e.conj()
+            eps[j_] = e if inc else e.conj()
             if eps_override and l in eps_override:
-                eps[j] = eps_override[l].astype(complex)
+                eps[j_] = eps_override[l].astype(complex)
         cache = {}
 
         def line(kind, spec):
@@ -1564,11 +1601,11 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
             return out
 
         amps = []
-        for order in diags:
+        for ci, order in diags:
             ins = []
             for x in order:
                 if x[0] == "c":
-                    ins.append(cins[x[1]])
+                    ins.append(cins[ci][x[1]])
                 else:
                     J, Q = line(*x)
                     ins.append((vector_insertion(J, gs, gs), Q))
@@ -1693,6 +1730,25 @@ def udx_wphgg(P, par=SMParams(), eps_override=None):
     wh = dict(kind="VS", legs=(2, 3), gl=par.g / np.sqrt(2.0), gr=0.0, mass=par.mW, width=par.wW, gvvs=par.gwwh)
     return fermion_line_process(P, par, (0, "u"), (1, "vbar"), [wh], [(4, False), (5, False)], 0.0, 0.0,
                                 1.0 / 36.0, eps_override)
+
+
+def wpwm_line_alternatives(par):
+    """The colourless parts of u u~ > W+(p2) W-(p3) on the quark line: the two W emissions in the order
+    the t-channel d quark fixes (W+ nearer the u), or an s-channel photon or Z into the W W V vertex."""
+    gw = par.g / np.sqrt(2.0)
+    ga = _a_coupling("u", par)
+    zl, zr = _z_couplings("u", par)
+    t = [dict(leg=2, kind="V", gl=gw, gr=0.0, mass=par.mW), dict(leg=3, kind="V", gl=gw, gr=0.0, mass=par.mW)]
+    a = [dict(kind="VV", legs=(2, 3), gl=ga, gr=ga, mass=0.0, width=0.0, gv=par.e, vmass=par.mW)]
+    z = [dict(kind="VV", legs=(2, 3), gl=zl, gr=zr, mass=par.mZ, width=par.wZ, gv=par.g * par.cw, vmass=par.mW)]
+    return [t, a, z]
+
+
+def uux_wpwmgg(P, par=SMParams(), eps_override=None):
+    """u(p0) u~(p1) > W+(p2) W-(p3) g(p4) g(p5) (W+ W- plus two jets, 31 diagrams): the quark line with the
+    t-channel W pair or the s-channel photon or Z, and the gluons (fermion_line_process)."""
+    return fermion_line_process(P, par, (0, "u"), (1, "vbar"), None, [(4, False), (5, False)], 0.0, 0.0,
+                                1.0 / 36.0, eps_override, alternatives=wpwm_line_alternatives(par), keep_order=True)
 
 
 def gg_ttxhg(P, par=SMParams(), eps_override=None, widths=True):
@@ -2097,6 +2153,7 @@ PROCESSES = {
     "u s > d c h g g": us_dchgg,
     "u u~ > z z g g": uux_zzgg,
     "u d~ > w+ h g g": udx_wphgg,
+    "u u~ > w+ w- g g": uux_wpwmgg,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,
