@@ -72,6 +72,7 @@ PROCESSES = [
     ("u d~ > w+ h g g", []),
     ("u u > u u h h", []),
     ("u u > u u h h h", []),
+    ("u u~ > w+ w- g g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

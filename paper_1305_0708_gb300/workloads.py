@@ -234,6 +234,11 @@ VARIANTS = {
         n=1 << 20, seed=55, cuts=None, s_ident=1.0 / 12.0,
         describe="u u > u u H H H (the paper's Sect. 2.10 process: Z Z fusion, identical quarks, 50 diagrams), "
                  "massive RAMBO at sqrt(s)=1.5 TeV, 2^20 points, seed 55"),
+    "uux_wpwmgg": dict(
+        process="u u~ > w+ w- g g", kind="rambo", sqrt_s=700.0, masses=(0, 0, 80.4, 80.4, 0, 0), n=1 << 18,
+        seed=56, cuts=dict(legs=(4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,
+        describe="u u~ > W+ W- g g (W+ W- plus two jets, 31 diagrams, helicity-loop program), massive RAMBO at "
+                 "sqrt(s)=700 GeV, gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^18 accepted points, seed 56"),
     "udx_wphgg": dict(
         process="u d~ > w+ h g g", kind="rambo", sqrt_s=700.0, masses=(0, 0, 80.4, 125.0, 0, 0), n=1 << 20,
         seed=53, cuts=dict(legs=(4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,

@@ -75,6 +75,7 @@ CASES = {
     "u d~ > w+ h g g": (opr.udx_wphgg, 700.0, (80.4, 125.0, 0.0, 0.0), (4, 5)),
     "u u > u u h h": (opr.uu_uuhh, 1000.0, (0.0, 0.0, 125.0, 125.0), ()),
     "u u > u u h h h": (opr.uu_uuhhh, 1500.0, (0.0, 0.0, 125.0, 125.0, 125.0), ()),
+    "u u~ > w+ w- g g": (opr.uux_wpwmgg, 700.0, (80.4, 80.4, 0.0, 0.0), (4, 5)),
 }
 
 # the complex-mass option (Sect. 7.11): processes whose couplings it makes complex
