@@ -59,6 +59,10 @@ Functions and their pins (tests/test_oracle_processes.py):
   us_dchgg        u s > d c h g g (WBF H plus two jets, 24 diagrams) on the two-line code (us_dch_ng),
                    which equals us_dch and us_dchg at 0 and 1 gluons; Ward identity for each gluon (fails
                    without the pair lines), Bose symmetry, boosts (tests/test_oracle_line.py)
+  udx_wpzgg       u d~ > w+ z g g (W+ Z plus two jets) on the one-fermion-line engine (the Z before or after
+                   the W emission, with the u or the d couplings, or an s-channel W into W W Z), which
+                   equals udx_wpz and udx_wpzg with no and one gluon; Ward identity for each gluon, Bose
+                   symmetry, boosts (tests/test_oracle_line.py)
   uux_wpwmgg      u u~ > w+ w- g g (W+ W- plus two jets, 31 diagrams) on the one-fermion-line engine (the
                    t-channel W pair in its fixed order, or an s-channel photon or Z into the W W V vertex),
                    which equals uux_wpwm and uux_wpwmg with no and one gluon; Ward identity for each
@@ -1490,8 +1494,8 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
     ends.  colourless: outgoing bosons as dicts (leg, kind "V" with gl, gr, mass: i gamma^mu (gl P_L +
     gr P_R); kind "S" with y: i y; kind "VS" with legs (vector, scalar), gl, gr, mass, width, gvvs: an
     off-shell vector of that mass and width from the line into the external vector and scalar through
-    the i gvvs g^{mu nu} vertex; kind "VV" with legs (V2, V1), gl, gr, mass, width, gv, vmass: an
-    off-shell vector from the line into two external vectors of mass vmass through the three-vector
+    the i gvvs g^{mu nu} vertex; kind "VV" with legs (V2, V1), gl, gr, mass, width, gv, vmass (one mass,
+    or one per leg): an off-shell vector from the line into two external vectors through the three-vector
     vertex -i gv [...] with (V1, V2, V) = (legs[1], legs[0], line), the W W gamma / W W Z rule of Sect.
     4.2).  alternatives: several such lists whose diagrams add coherently (for instance t-channel W
     emissions and an s-channel photon or Z); keep_order: an alternative's insertions stay in their
@@ -1537,8 +1541,8 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
             elif c["kind"] == "VS":
                 vlegs[c["legs"][0]] = c["mass"]
             elif c["kind"] == "VV":
-                vlegs[c["legs"][0]] = c["vmass"]
-                vlegs[c["legs"][1]] = c["vmass"]
+                vm = c["vmass"] if isinstance(c["vmass"], tuple) else (c["vmass"], c["vmass"])
+                vlegs[c["legs"][0]], vlegs[c["legs"][1]] = vm
     vl = sorted(vlegs)
     hels = [HEL_F, HEL_F] + [HEL_W] * len(vl) + [HEL_V] * ng
     tot = 0.0
@@ -1749,6 +1753,25 @@ def uux_wpwmgg(P, par=SMParams(), eps_override=None):
     t-channel W pair or the s-channel photon or Z, and the gluons (fermion_line_process)."""
     return fermion_line_process(P, par, (0, "u"), (1, "vbar"), None, [(4, False), (5, False)], 0.0, 0.0,
                                 1.0 / 36.0, eps_override, alternatives=wpwm_line_alternatives(par), keep_order=True)
+
+
+def wpz_line_alternatives(par):
+    """The colourless parts of u d~ > W+(p2) Z(p3) on the quark line: the Z from the u before the W+
+    turns it into a d, the Z from the d after it, or an s-channel W into the W W Z vertex."""
+    gw = par.g / np.sqrt(2.0)
+    zu, zd = _z_couplings("u", par), _z_couplings("d", par)
+    w = dict(leg=2, kind="V", gl=gw, gr=0.0, mass=par.mW)
+    return [[dict(leg=3, kind="V", gl=zu[0], gr=zu[1], mass=par.mZ), w],
+            [w, dict(leg=3, kind="V", gl=zd[0], gr=zd[1], mass=par.mZ)],
+            [dict(kind="VV", legs=(3, 2), gl=gw, gr=0.0, mass=par.mW, width=par.wW, gv=par.g * par.cw,
+                  vmass=(par.mZ, par.mW))]]
+
+
+def udx_wpzgg(P, par=SMParams(), eps_override=None):
+    """u(p0) d~(p1) > W+(p2) Z(p3) g(p4) g(p5) (W+ Z plus two jets, 38 diagrams): the three u d~ > W+ Z graphs
+    with the gluons (fermion_line_process)."""
+    return fermion_line_process(P, par, (0, "u"), (1, "vbar"), None, [(4, False), (5, False)], 0.0, 0.0,
+                                1.0 / 36.0, eps_override, alternatives=wpz_line_alternatives(par), keep_order=True)
 
 
 def gg_ttxhg(P, par=SMParams(), eps_override=None, widths=True):
@@ -2154,6 +2177,7 @@ PROCESSES = {
     "u u~ > z z g g": uux_zzgg,
     "u d~ > w+ h g g": udx_wphgg,
     "u u~ > w+ w- g g": uux_wpwmgg,
+    "u d~ > w+ z g g": udx_wpzgg,
     "g g > t t~ g": gg_ttxg,
     "h h > h h": hh_hh,
     "u u~ > w+ w-": uux_wpwm,

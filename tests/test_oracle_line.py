@@ -18,6 +18,9 @@ it, g g > t t~ H g (H t t~ plus one jet, the paper's Sect. 2 Htt~ + jets family)
 - W+ W- plus jets (u u~ > W+ W- g g): the t-channel W pair in the order its d quark fixes, or an
   s-channel photon or Z into the W W V vertex, as alternatives whose diagrams add: equal to u u~ > W+ W-
   and u u~ > W+ W- g with no and one gluon; Ward identity of each gluon, Bose symmetry, boosts.
+- W+ Z plus jets (u d~ > W+ Z g g): the Z with the u couplings before the W emission, with the d
+  couplings after it, or an s-channel W into W W Z; equal to u d~ > W+ Z and u d~ > W+ Z g with no and
+  one gluon; Ward identity of each gluon, Bose symmetry, boosts.
 - WBF H plus jets on two quark lines (us_dch_ng, u s > d c H + n gluons): equal to u s > d c H and
   u s > d c H g at n = 0, 1; at n = 2 the Ward identity of each gluon (fails without the three-gluon
   pair lines), Bose symmetry, boosts.
@@ -195,3 +198,34 @@ def test_wpwmgg_ward_bose_and_boosts():
     assert np.allclose(pr.uux_wpwmgg(P[:, [0, 1, 2, 3, 5, 4]], PAR), ref, rtol=1e-12)
     from test_oracle_processes import random_lorentz
     assert np.allclose(pr.uux_wpwmgg(random_lorentz(P, 973), PAR), ref, rtol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# W+ Z plus jets: the Z with the u couplings before the W emission, the d couplings after it, or an
+# s-channel W into W W Z
+# ---------------------------------------------------------------------------
+def test_wpz_plus_jets_engine_equals_the_zero_and_one_gluon_oracles():
+    alts = pr.wpz_line_alternatives(PAR)
+    P = _massive_points(500.0, (PAR.mW, PAR.mZ), 6, seed=980)
+    got = pr.fermion_line_process(P, PAR, (0, "u"), (1, "vbar"), None, [], 0.0, 0.0, 1.0 / 36.0,
+                                  alternatives=alts, keep_order=True)
+    assert np.allclose(got, pr.udx_wpz(P, PAR), rtol=1e-12, atol=0)
+    P = _massive_points(600.0, (PAR.mW, PAR.mZ, 0.0), 6, seed=981)
+    got = pr.fermion_line_process(P, PAR, (0, "u"), (1, "vbar"), None, [(4, False)], 0.0, 0.0, 1.0 / 36.0,
+                                  alternatives=alts, keep_order=True)
+    assert np.allclose(got, pr.udx_wpzg(P, PAR), rtol=1e-12, atol=0)
+
+
+def test_wpzgg_ward_bose_and_boosts():
+    P = _massive_points(700.0, (PAR.mW, PAR.mZ, 0.0, 0.0), 16, seed=982)
+    pt = np.hypot(P[:, 4:, 1], P[:, 4:, 2])
+    P = P[np.all(pt > 20.0, axis=1)][:5]
+    assert len(P) == 5
+    ref = pr.udx_wpzgg(P, PAR)
+    assert np.all(ref > 0) and np.all(np.isfinite(ref))
+    for leg in (4, 5):
+        bad = pr.udx_wpzgg(P, PAR, eps_override={leg: P[:, leg]})
+        assert np.all(np.abs(bad) < 1e-24 * ref * P[:, leg, 0] ** 2)
+    assert np.allclose(pr.udx_wpzgg(P[:, [0, 1, 2, 3, 5, 4]], PAR), ref, rtol=1e-12)
+    from test_oracle_processes import random_lorentz
+    assert np.allclose(pr.udx_wpzgg(random_lorentz(P, 983), PAR), ref, rtol=1e-10)
