@@ -76,6 +76,7 @@ CASES = {
     "u u > u u h h": (opr.uu_uuhh, 1000.0, (0.0, 0.0, 125.0, 125.0), ()),
     "u u > u u h h h": (opr.uu_uuhhh, 1500.0, (0.0, 0.0, 125.0, 125.0, 125.0), ()),
     "u u~ > w+ w- g g": (opr.uux_wpwmgg, 700.0, (80.4, 80.4, 0.0, 0.0), (4, 5)),
+    "u d~ > w+ z g g": (opr.udx_wpzgg, 700.0, (80.4, 91.1876, 0.0, 0.0), (4, 5)),
 }
 
 # the complex-mass option (Sect. 7.11): processes whose couplings it makes complex
