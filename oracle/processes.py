@@ -67,6 +67,9 @@ Functions and their pins (tests/test_oracle_processes.py):
                    t-channel W pair in its fixed order, or an s-channel photon or Z into the W W V vertex),
                    which equals uux_wpwm and uux_wpwmg with no and one gluon; Ward identity for each
                    gluon, Bose symmetry, boosts (tests/test_oracle_line.py)
+  udx_wphggg      u d~ > w+ h g g g (H V plus three jets, 54 diagrams) on the same engine: Ward identity for
+                   each gluon (fails without the four-gluon lines), Bose symmetry, boosts
+                   (tests/test_oracle_line.py)
   udx_wphgg       u d~ > w+ h g g (H V plus two jets, 8 diagrams) on the one-fermion-line engine (a W* > W+ H
                    insertion), which equals udx_wph and udx_wphg with no and one gluon; Ward identity for
                    each gluon, Bose symmetry, boosts (tests/test_oracle_line.py)
@@ -1774,6 +1777,14 @@ def udx_wpzgg(P, par=SMParams(), eps_override=None):
                                 1.0 / 36.0, eps_override, alternatives=wpz_line_alternatives(par), keep_order=True)
 
 
+def udx_wphggg(P, par=SMParams(), eps_override=None):
+    """u(p0) d~(p1) > W+(p2) H(p3) g(p4) g(p5) g(p6) (H V plus three jets, 54 diagrams): the quark line with the
+    W* > W+ H insertion and the three gluons (fermion_line_process)."""
+    wh = dict(kind="VS", legs=(2, 3), gl=par.g / np.sqrt(2.0), gr=0.0, mass=par.mW, width=par.wW, gvvs=par.gwwh)
+    return fermion_line_process(P, par, (0, "u"), (1, "vbar"), [wh], [(4, False), (5, False), (6, False)], 0.0,
+                                0.0, 1.0 / 36.0, eps_override)
+
+
 def gg_ttxhg(P, par=SMParams(), eps_override=None, widths=True):
     """g(0) g(1) > t(2) t~(3) H(4) g(5) (H t t~ plus one jet): the top line from v(p3) to ubar(p2) with the
     Higgs (Yukawa -mt/v) and the three gluons, 54 diagrams (fermion_line_process)."""
@@ -2176,6 +2187,7 @@ PROCESSES = {
     "u s > d c h g g": us_dchgg,
     "u u~ > z z g g": uux_zzgg,
     "u d~ > w+ h g g": udx_wphgg,
+    "u d~ > w+ h g g g": udx_wphggg,
     "u u~ > w+ w- g g": uux_wpwmgg,
     "u d~ > w+ z g g": udx_wpzgg,
     "g g > t t~ g": gg_ttxg,

@@ -21,6 +21,8 @@ it, g g > t t~ H g (H t t~ plus one jet, the paper's Sect. 2 Htt~ + jets family)
 - W+ Z plus jets (u d~ > W+ Z g g): the Z with the u couplings before the W emission, with the d
   couplings after it, or an s-channel W into W W Z; equal to u d~ > W+ Z and u d~ > W+ Z g with no and
   one gluon; Ward identity of each gluon, Bose symmetry, boosts.
+- H V plus three jets (u d~ > W+ H g g g): Ward identity of each gluon (fails without the four-gluon
+  lines), Bose symmetry of the gluons, boosts.
 - WBF H plus jets on two quark lines (us_dch_ng, u s > d c H + n gluons): equal to u s > d c H and
   u s > d c H g at n = 0, 1; at n = 2 the Ward identity of each gluon (fails without the three-gluon
   pair lines), Bose symmetry, boosts.
@@ -229,3 +231,29 @@ def test_wpzgg_ward_bose_and_boosts():
     assert np.allclose(pr.udx_wpzgg(P[:, [0, 1, 2, 3, 5, 4]], PAR), ref, rtol=1e-12)
     from test_oracle_processes import random_lorentz
     assert np.allclose(pr.udx_wpzgg(random_lorentz(P, 983), PAR), ref, rtol=1e-10)
+
+
+def test_whggg_ward_bose_and_boosts():
+    """H V plus three jets (the engine with three gluons and the W* > W+ H insertion)."""
+    P = _massive_points(900.0, (PAR.mW, PAR.mH, 0.0, 0.0, 0.0), 16, seed=990)
+    pt = np.hypot(P[:, 4:, 1], P[:, 4:, 2])
+    P = P[np.all(pt > 20.0, axis=1)][:4]
+    assert len(P) == 4
+    ref = pr.udx_wphggg(P, PAR)
+    assert np.all(ref > 0) and np.all(np.isfinite(ref))
+    for leg in (4, 5, 6):
+        bad = pr.udx_wphggg(P, PAR, eps_override={leg: P[:, leg]})
+        assert np.all(np.abs(bad) < 1e-24 * ref * P[:, leg, 0] ** 2)
+    assert np.allclose(pr.udx_wphggg(P[:, [0, 1, 2, 3, 6, 4, 5]], PAR), ref, rtol=1e-12)
+    from test_oracle_processes import random_lorentz
+    assert np.allclose(pr.udx_wphggg(random_lorentz(P, 991), PAR), ref, rtol=1e-10)
+
+
+def test_whggg_ward_identity_catches_dropped_four_gluon_lines(monkeypatch):
+    orig = pr._gluon_blocks
+    monkeypatch.setattr(pr, "_gluon_blocks", lambda legs: [b for b in orig(legs) if b[0] != "quartic"])
+    monkeypatch.setattr(pr, "_VJETS", {})
+    P = _massive_points(900.0, (PAR.mW, PAR.mH, 0.0, 0.0, 0.0), 3, seed=992)
+    ref = pr.udx_wphggg(P, PAR)
+    bad = pr.udx_wphggg(P, PAR, eps_override={4: P[:, 4]})
+    assert np.all(np.abs(bad) > 1e-8 * ref * P[:, 4, 0] ** 2)
