@@ -74,6 +74,7 @@ PROCESSES = [
     ("u u > u u h h h", []),
     ("u u~ > w+ w- g g", []),
     ("u d~ > w+ z g g", []),
+    ("u d~ > w+ h g g g", []),
 ]
 
 # all-gluon processes run by the colour-ordered block kernel (gluon_process.cu, one unit per count)

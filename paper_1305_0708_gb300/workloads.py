@@ -244,6 +244,11 @@ VARIANTS = {
         seed=57, cuts=dict(legs=(4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,
         describe="u d~ > W+ Z g g (W+ Z plus two jets, 38 diagrams, helicity-loop program), massive RAMBO at "
                  "sqrt(s)=700 GeV, gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^18 accepted points, seed 57"),
+    "udx_wphggg": dict(
+        process="u d~ > w+ h g g g", kind="rambo", sqrt_s=900.0, masses=(0, 0, 80.4, 125.0, 0, 0, 0), n=1 << 18,
+        seed=58, cuts=dict(legs=(4, 5, 6), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=1.0 / 6.0,
+        describe="u d~ > W+ H g g g (H V plus three jets, 54 diagrams, helicity-loop program), massive RAMBO "
+                 "at sqrt(s)=900 GeV, gluons pT>20, |eta|<2.5, DeltaR>0.4, 2^18 accepted points, seed 58"),
     "udx_wphgg": dict(
         process="u d~ > w+ h g g", kind="rambo", sqrt_s=700.0, masses=(0, 0, 80.4, 125.0, 0, 0), n=1 << 20,
         seed=53, cuts=dict(legs=(4, 5), pt_min=20.0, eta_max=2.5, dr_min=0.4), s_ident=0.5,

@@ -391,7 +391,7 @@ def test_identical_quarks_parity(B, prec):
                                  "uux_wpwmg", "gg_wpdux", "gg_zuux", "udx_wphg",
                                  "uux_ttx", "uux_ttxg", "us_dch", "udx_wpa",
                                  "uux_za", "uux_aa", "udx_wpgg", "uux_zgg", "us_dchg",
-                                 "us_dchhh", "ud_udh", "ud_udhh", "ud_udhhh", "udx_wpggg", "uux_zggg", "gg_ttxhg", "us_dchgg", "uux_zzgg", "udx_wphgg", "uu_uuhh", "uu_uuhhh", "uux_wpwmgg", "udx_wpzgg"])
+                                 "us_dchhh", "ud_udh", "ud_udhh", "ud_udhhh", "udx_wpggg", "uux_zggg", "gg_ttxhg", "us_dchgg", "uux_zzgg", "udx_wphgg", "uu_uuhh", "uu_uuhhh", "uux_wpwmgg", "udx_wpzgg", "udx_wphggg"])
 def test_massive_final_state_parity(B, key, prec):
     """u u~ > Z Z (identical massive vectors, identical-particle factor 1/2), u u~ > Z H (ZZH vertex,
     external scalar), u d~ > W+ H (WWH vertex), u u~ > W+ W- gamma (the electroweak quartic
@@ -402,7 +402,7 @@ def test_massive_final_state_parity(B, key, prec):
     four-gluon vertex beside a top line), u s > d c H H H and u d > u d + 1, 2, 3 Higgs (weak-boson fusion,
     Sect. 2.10), u d~ > W+ g g g and u u~ > Z g g g (V plus three jets) and g g > t t~ H g (H t t~ plus a
     jet) and u u~ > Z Z g g (V V plus two jets), helicity-loop programs, u s > d c H g g (WBF H plus two
-    jets), u d~ > W+ H g g (H V plus two jets), u u~ > W+ W- g g and u d~ > W+ Z g g (V V plus two jets) and u u > u u H H (H)
+    jets), u d~ > W+ H g g and W+ H g g g (H V plus two and three jets), u u~ > W+ W- g g and u d~ > W+ Z g g (V V plus two jets) and u u > u u H H (H)
     (Z Z fusion, identical quarks): me_eval on the oracle's massive-RAMBO points and the Monte Carlo sums
     against the oracle."""
     from paper_1305_0708_gb300.workloads import VARIANTS
@@ -418,9 +418,9 @@ def test_massive_final_state_parity(B, key, prec):
           "ud_udhhh": opr.ud_udhhh, "udx_wpggg": opr.udx_wpggg, "uux_zggg": opr.uux_zggg,
           "gg_ttxhg": opr.gg_ttxhg, "us_dchgg": opr.us_dchgg, "uux_zzgg": opr.uux_zzgg,
           "udx_wphgg": opr.udx_wphgg, "uu_uuhh": opr.uu_uuhh, "uu_uuhhh": opr.uu_uuhhh,
-          "uux_wpwmgg": opr.uux_wpwmgg, "udx_wpzgg": opr.udx_wpzgg}[key]
+          "uux_wpwmgg": opr.uux_wpwmgg, "udx_wpzgg": opr.udx_wpzgg, "udx_wphggg": opr.udx_wphggg}[key]
     n = {"udx_wpggg": 300, "uux_zggg": 300, "gg_ttxhg": 300, "uux_zzgg": 300, "uux_wpwmgg": 300,
-         "udx_wpzgg": 300}.get(key, 1500)
+         "udx_wpzgg": 300, "udx_wphggg": 300}.get(key, 1500)
     P0, W, S, T = oxs.generate(oracle_kin(w), PAR, w["seed"], np.arange(n))
     P = consistent(P0, masses_of(w, P0.shape[1]))
     ref = fn(P, PAR)

@@ -77,6 +77,7 @@ CASES = {
     "u u > u u h h h": (opr.uu_uuhhh, 1500.0, (0.0, 0.0, 125.0, 125.0, 125.0), ()),
     "u u~ > w+ w- g g": (opr.uux_wpwmgg, 700.0, (80.4, 80.4, 0.0, 0.0), (4, 5)),
     "u d~ > w+ z g g": (opr.udx_wpzgg, 700.0, (80.4, 91.1876, 0.0, 0.0), (4, 5)),
+    "u d~ > w+ h g g g": (opr.udx_wphggg, 900.0, (80.4, 125.0, 0.0, 0.0, 0.0), (4, 5, 6)),
 }
 
 # the complex-mass option (Sect. 7.11): processes whose couplings it makes complex
