@@ -76,6 +76,11 @@ Functions and their pins (tests/test_oracle_processes.py):
   uux_zzgg        u u~ > z z g g (V V plus two jets, 30 diagrams) on the one-fermion-line engine, which
                    equals uux_zz and uux_zzg with no and one gluon; Ward identity for each gluon, Bose
                    symmetry of the gluons and of the Z bosons, boosts (tests/test_oracle_line.py)
+  gg_ttxgg        g g > t t~ g g (t t~ plus two jets, 159 diagrams) on the one-fermion-line engine with
+                   four-gluon trees (_gluon_trees; recursive currents and vectorised colour tensors, both
+                   checked against the three-gluon forms); Ward identity for each gluon at zero top width
+                   (fails without the four-gluon vertex in the trees), Bose symmetry, boosts
+                   (tests/test_oracle_line.py)
   gg_ttxhg        g g > t t~ h g (H t t~ plus one jet, 54 diagrams) on the one-fermion-line engine
                    (fermion_line_process), which equals gg_ttxh, gg_ttxg and udx_wpggg point by point;
                    Ward identity for each gluon (fails without the triple-gluon lines), Bose symmetry,
@@ -1362,14 +1367,118 @@ def _gluon_blocks(legs):
         return [("g", legs[0])]
     if len(legs) == 2:
         return [("pair", legs)]
+    if len(legs) >= 4:
+        return _gluon_trees(legs)
     x, y, z = legs
     return ([("triple", (a, b, c)) for a, b, c in ((x, y, z), (x, z, y), (y, z, x))]
             + [("quartic", (legs, s)) for s in range(3)])
 
 
+def _gluon_trees(legs):
+    """Four or more gluons joined into one line: every tree of three- and four-gluon vertices, as
+    ("tree", t) with t = ("c3", block_a, block_b) (a three-gluon vertex joining the lines of two
+    disjoint sets, the one holding the smallest leg first) or ("c4", s, block_a, block_b, block_c) (the
+    four-gluon vertex joining three lines, colour structure s as for "quartic"); the sub-blocks are
+    those of _gluon_blocks.  Four gluons: 15 trees of three-gluon vertices and 10 with one four-gluon
+    vertex (30 with its colour structures)."""
+    S = tuple(sorted(legs))
+    out = []
+    for part in _set_partitions(list(S)):
+        blocks = sorted((tuple(sorted(b)) for b in part), key=lambda b: b[0])
+        if len(blocks) == 2:
+            for ba in _gluon_blocks(blocks[0]):
+                for bb in _gluon_blocks(blocks[1]):
+                    out.append(("tree", ("c3", ba, bb)))
+        elif len(blocks) == 3:
+            for ba in _gluon_blocks(blocks[0]):
+                for bb in _gluon_blocks(blocks[1]):
+                    for bc in _gluon_blocks(blocks[2]):
+                        for s in range(3):
+                            out.append(("tree", ("c4", s, ba, bb, bc)))
+    return out
+
+
+def _block_legs(kind, spec):
+    if kind == "g":
+        return (spec,)
+    if kind in ("pair", "triple"):
+        return tuple(sorted(spec))
+    if kind == "quartic":
+        return tuple(spec[0])
+    if spec[0] == "c3":
+        return tuple(sorted(_block_legs(*spec[1]) + _block_legs(*spec[2])))
+    return tuple(sorted(_block_legs(*spec[2]) + _block_legs(*spec[3]) + _block_legs(*spec[4])))
+
+
+def _block_adjoint(kind, spec, A):
+    """The adjoint colour vector v[c] of a joined gluon line (its line meets the quark line as
+    sum_c v[c] t^c), for gluon colours A[leg]."""
+    F = _F
+    if kind == "g":
+        return np.eye(8)[A[spec]]
+    if kind == "pair":
+        x, y = spec
+        return F[A[x], A[y], :]
+    if kind == "triple":
+        x, y, z = spec
+        return np.einsum("e,ec->c", F[A[x], A[y], :], F[:, A[z], :])
+    if kind == "quartic":
+        (x, y, z), s = spec
+        va, vb, vc = np.eye(8)[A[x]], np.eye(8)[A[y]], np.eye(8)[A[z]]
+    elif spec[0] == "c3":
+        va, vb = _block_adjoint(*spec[1], A), _block_adjoint(*spec[2], A)
+        return np.einsum("a,b,abc->c", va, vb, F)
+    else:
+        s = spec[1]
+        va, vb, vc = (_block_adjoint(*b, A) for b in spec[2:])
+    # four-gluon vertex, legs (a, b, c, X): f^{abe} f^{cXe}, f^{ace} f^{bXe}, f^{aXe} f^{bce}
+    if s == 0:
+        return np.einsum("a,b,c,abe,cXe->X", va, vb, vc, F, F)
+    if s == 1:
+        return np.einsum("a,b,c,ace,bXe->X", va, vb, vc, F, F)
+    return np.einsum("a,b,c,aXe,bce->X", va, vb, vc, F, F)
+
+
+def _block_vtensor(kind, spec):
+    """The adjoint vectors of a joined gluon line for every colour assignment of its legs, at once:
+    an array with one axis of 8 per leg (in _block_legs order) and the adjoint axis last."""
+    F = _F
+    if kind == "g":
+        return np.eye(8)
+    if kind == "pair":
+        return F.copy()
+    if kind == "triple":
+        x, y, z = spec
+        v = np.einsum("xye,ezc->xyzc", F, F)          # legs in the order (x, y, z)
+        return np.moveaxis(v, [0, 1, 2], [sorted(spec).index(x), sorted(spec).index(y), sorted(spec).index(z)])
+    if kind == "quartic":
+        s = spec[1]
+        va = vb = vc = np.eye(8)
+        la, lb, lc = (spec[0][0],), (spec[0][1],), (spec[0][2],)
+    elif spec[0] == "c3":
+        la, lb = _block_legs(*spec[1]), _block_legs(*spec[2])
+        va, vb = _block_vtensor(*spec[1]), _block_vtensor(*spec[2])
+    else:
+        s = spec[1]
+        la, lb, lc = (_block_legs(*b) for b in spec[2:])
+        va, vb, vc = (_block_vtensor(*b) for b in spec[2:])
+    letters = "ijklmnopqrstuvw"
+    legs = sorted(la + lb + (lc if kind == "quartic" or spec[0] == "c4" else ()))
+    L = {leg: letters[k] for k, leg in enumerate(legs)}
+    sa, sb = "".join(L[l] for l in la), "".join(L[l] for l in lb)
+    out = "".join(L[l] for l in legs)
+    if kind != "quartic" and spec[0] == "c3":
+        return np.einsum(f"{sa}a,{sb}b,abZ->{out}Z", va, vb, F)
+    sc = "".join(L[l] for l in lc)
+    rule = {0: "abe,cZe", 1: "ace,bZe", 2: "aZe,bce"}[s]
+    return np.einsum(f"{sa}a,{sb}b,{sc}c,{rule}->{out}Z", va, vb, vc, F, F)
+
+
 def _block_colour(kind, spec, A):
     """Colour matrix (3 x 3) a joined gluon line gives the quark line, for gluon colours A[leg]."""
     T, F = _T, _F
+    if kind == "tree":
+        return np.einsum("c,cij->ij", _block_adjoint(kind, spec, A), T)
     if kind == "g":
         return T[A[spec]]
     if kind == "pair":
@@ -1485,6 +1594,23 @@ def qqx_v_ng(P, par, gl, gr, mV, eps_override=None):
     return tot / 36.0
 
 
+def _line_colour_tensor(blocks, ng):
+    """Explicit colour tensor [i_start, i_end, a_0 .. a_{ng-1}] of a quark line with the joined gluon
+    lines `blocks` in order from the start of the fermion arrow: (t_last ... t_first)_{i_end i_start},
+    each block's matrix sum_c v[c] t^c built for all colour assignments at once (_block_vtensor)."""
+    letters = "abcdefgh"
+    R = np.eye(3, dtype=complex)          # axes: current index, start index
+    rs = "xz"
+    for kind, spec in blocks:
+        legs = _block_legs(kind, spec)
+        Mb = np.einsum("...c,cij->...ij", _block_vtensor(kind, spec), _T)   # legs..., row, column
+        ls = "".join(letters[l] for l in legs)
+        R = np.einsum(f"{ls}yx,{rs}->y{rs[1:]}{ls}", Mb, R)
+        rs = "x" + rs[1:] + ls
+    order = "".join(letters[l] for l in range(ng))
+    return np.einsum(f"{rs}->zx{order}", R)
+
+
 def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, average=1.0 / 36.0,
                          eps_override=None, alternatives=None, keep_order=False):
     """|M|^2 of a process with one fermion line, colourless bosons attached to it and any number (up
@@ -1520,6 +1646,9 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
                         diags.append((ci, order))
         tensors = []
         for _, order in diags:
+            if ng >= 4:
+                tensors.append(_line_colour_tensor([ins for ins in order if ins[0] != "c"], ng))
+                continue
             t = np.zeros((3, 3) + (8,) * ng, dtype=complex)
             for a in itertools.product(range(8), repeat=ng):
                 M = np.eye(3, dtype=complex)
@@ -1600,10 +1729,18 @@ def fermion_line_process(P, par, col, row, colourless, gluons, mf=0.0, wf=0.0, a
                 k = -mk
                 K = k + kg[z]
                 out = (vector_prop(K, vvv_out(J, k, eps[z], kg[z], -K, gs)), -K)
-            else:
+            elif kind == "quartic":
                 (x, y, z), s_ = spec
                 K = kg[x] + kg[y] + kg[z]
                 out = (vector_prop(K, -1j * gs * gs * _vvvv_out(eps[x], eps[y], eps[z])[s_]), -K)
+            elif spec[0] == "c3":
+                (JA, mA), (JB, mB) = line(*spec[1]), line(*spec[2])
+                K = -(mA + mB)
+                out = (vector_prop(K, vvv_out(JA, -mA, JB, -mB, -K, gs)), -K)
+            else:
+                sub = [line(*b) for b in spec[2:]]
+                K = -(sub[0][1] + sub[1][1] + sub[2][1])
+                out = (vector_prop(K, -1j * gs * gs * _vvvv_out(sub[0][0], sub[1][0], sub[2][0])[spec[1]]), -K)
             cache[k_] = out
             return out
 
@@ -1783,6 +1920,13 @@ def udx_wphggg(P, par=SMParams(), eps_override=None):
     wh = dict(kind="VS", legs=(2, 3), gl=par.g / np.sqrt(2.0), gr=0.0, mass=par.mW, width=par.wW, gvvs=par.gwwh)
     return fermion_line_process(P, par, (0, "u"), (1, "vbar"), [wh], [(4, False), (5, False), (6, False)], 0.0,
                                 0.0, 1.0 / 36.0, eps_override)
+
+
+def gg_ttxgg(P, par=SMParams(), eps_override=None, widths=True):
+    """g(0) g(1) > t(2) t~(3) g(4) g(5) (t t~ plus two jets, 159 diagrams): the top line from v(p3) to ubar(p2)
+    with the four gluons joined into lines, four-gluon trees included (fermion_line_process)."""
+    return fermion_line_process(P, par, (3, "v"), (2, "ubar"), [], [(0, True), (1, True), (4, False), (5, False)],
+                                par.mt, par.wt if widths else 0.0, 1.0 / 256.0, eps_override)
 
 
 def gg_ttxhg(P, par=SMParams(), eps_override=None, widths=True):
@@ -2184,6 +2328,7 @@ PROCESSES = {
     "u d~ > w+ g g g": udx_wpggg,
     "u u~ > z g g g": uux_zggg,
     "g g > t t~ h g": gg_ttxhg,
+    "g g > t t~ g g": gg_ttxgg,
     "u s > d c h g g": us_dchgg,
     "u u~ > z z g g": uux_zzgg,
     "u d~ > w+ h g g": udx_wphgg,

@@ -23,6 +23,9 @@ it, g g > t t~ H g (H t t~ plus one jet, the paper's Sect. 2 Htt~ + jets family)
   one gluon; Ward identity of each gluon, Bose symmetry, boosts.
 - H V plus three jets (u d~ > W+ H g g g): Ward identity of each gluon (fails without the four-gluon
   lines), Bose symmetry of the gluons, boosts.
+- Four gluons (g g > t t~ g g, t t~ plus two jets): the recursive gluon trees built for three gluons
+  reproduce g g > t t~ g, the vectorised colour tensors equal the explicit loop, and g g > t t~ g g
+  satisfies each gluon's Ward identity at zero top width, Bose symmetry and boosts.
 - WBF H plus jets on two quark lines (us_dch_ng, u s > d c H + n gluons): equal to u s > d c H and
   u s > d c H g at n = 0, 1; at n = 2 the Ward identity of each gluon (fails without the three-gluon
   pair lines), Bose symmetry, boosts.
@@ -257,3 +260,50 @@ def test_whggg_ward_identity_catches_dropped_four_gluon_lines(monkeypatch):
     ref = pr.udx_wphggg(P, PAR)
     bad = pr.udx_wphggg(P, PAR, eps_override={4: P[:, 4]})
     assert np.all(np.abs(bad) > 1e-8 * ref * P[:, 4, 0] ** 2)
+
+
+# ---------------------------------------------------------------------------
+# four gluons: recursive gluon trees and vectorised colour tensors (t t~ plus two jets)
+# ---------------------------------------------------------------------------
+def test_gluon_trees_at_three_gluons_reproduce_gg_ttxg(monkeypatch):
+    """The recursive trees (three- and four-gluon vertices joining sub-blocks) built for a set of three
+    gluons in place of the written-out triple and quartic blocks give g g > t t~ g point by point: the
+    tree currents, their momenta and their colour (adjoint vectors) as the four-gluon case uses them."""
+    orig = pr._gluon_blocks
+    monkeypatch.setattr(pr, "_gluon_blocks", lambda legs: pr._gluon_trees(legs) if len(legs) == 3 else orig(legs))
+    monkeypatch.setattr(pr, "_VJETS", {})
+    P = _massive_points(1000.0, (PAR.mt, PAR.mt, 0.0), 5, seed=801)
+    got = pr.fermion_line_process(P, PAR, (3, "v"), (2, "ubar"), [], [(0, True), (1, True), (4, False)],
+                                  PAR.mt, PAR.wt, 1.0 / 256.0)
+    assert np.allclose(got, pr.gg_ttxg(P, PAR), rtol=1e-12, atol=0)
+
+
+def test_vectorised_colour_tensor_equals_the_explicit_loop():
+    import itertools
+    rng = np.random.default_rng(11)
+    for blocks in ([("g", 2), ("pair", (0, 1))], [("quartic", ((0, 1, 2), 1))], [("triple", (0, 2, 1))],
+                   [("g", 1), ("g", 0), ("g", 2)]):
+        T3 = pr._line_colour_tensor(blocks, 3)
+        for _ in range(20):
+            a = tuple(int(x) for x in rng.integers(0, 8, 3))
+            M = np.eye(3, dtype=complex)
+            for k, sp in blocks:
+                M = pr._block_colour(k, sp, a) @ M
+            assert np.allclose(T3[(slice(None), slice(None)) + a], M.T, atol=1e-14)
+    assert len(pr._gluon_trees((0, 1, 2, 3))) == 45   # 15 cubic trees, 10 with a quartic vertex x 3
+
+
+def test_ttxgg_ward_bose_and_boosts():
+    P = _massive_points(1500.0, (PAR.mt, PAR.mt, 0.0, 0.0), 12, seed=1000)
+    pt = np.hypot(P[:, 4:, 1], P[:, 4:, 2])
+    P = P[np.all(pt > 20.0, axis=1)][:3]
+    assert len(P) == 3
+    ref0 = pr.gg_ttxgg(P, PAR, widths=False)
+    assert np.all(ref0 > 0) and np.all(np.isfinite(ref0))
+    for leg in (0, 5):
+        bad = pr.gg_ttxgg(P, PAR, eps_override={leg: P[:, leg]}, widths=False)
+        assert np.all(np.abs(bad) < 1e-24 * ref0 * P[:, leg, 0] ** 2)
+    ref = pr.gg_ttxgg(P, PAR)
+    assert np.allclose(pr.gg_ttxgg(P[:, [0, 1, 2, 3, 5, 4]], PAR), ref, rtol=1e-12)
+    from test_oracle_processes import random_lorentz
+    assert np.allclose(pr.gg_ttxgg(random_lorentz(P, 1001), PAR), ref, rtol=1e-10)
